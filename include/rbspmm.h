@@ -1,0 +1,234 @@
+/*
+ * rbspmm.h -- C ABI of the repeated-block SpMM library for one GB300 GPU (sm_103a).
+ *
+ * The library applies the discrete Navier-Stokes operators of arxiv 2508.06710 (the
+ * face-to-cell divergence M, the cell-to-face gradient G, the Laplacian L = M G) to a
+ * dense block of k right-hand sides at once (SpMM), instead of k separate SpMVs, and
+ * builds a batched Jacobi-preconditioned CG Poisson solve on top of spmm, dot, axpy and
+ * axty (the four basic operations of Sec. 1).  The k columns are the flow states of an
+ * ensemble, the parameters of a multiple-parameter run (Sec. 3), or the identical planes
+ * of a mesh extruded along a periodic direction (Sec. 2, repeated geometries).
+ *
+ * Conventions shared by every call
+ *   - Dense blocks are row-major with the k columns of one row next to each other (the
+ *     array-of-structures layout of Algorithm 1): entry (i, j) of X is X[i * ldx + j],
+ *     ldx >= k.  X, Y, B are caller-owned DEVICE pointers unless a call says otherwise.
+ *   - Every call is asynchronous on the given stream (0 = the legacy default stream),
+ *     except where a call says it synchronises.  Nothing is thrown across the ABI: each
+ *     call returns an rb_status; rb_last_error() gives the calling thread's last message.
+ *   - rb_operator_create, rb_batch_create and rb_guess_create are the only calls that
+ *     allocate device memory; the library owns that memory until the matching destroy.
+ *     Every other call allocates nothing: scratch space is a caller-provided workspace
+ *     whose size a *_workspace_bytes query returns.
+ *   - Invalid arguments (null pointers, negative sizes, ld < k, k > RB_MAX_K, dtype
+ *     mismatch) return RB_EINVAL before any work is queued.
+ */
+#ifndef RBSPMM_H
+#define RBSPMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* rb_stream_t; /* the same handle as cudaStream_t */
+
+#define RB_MAX_K 64
+
+typedef enum {
+  RB_OK = 0,
+  RB_EINVAL = 1,        /* invalid argument; nothing was queued */
+  RB_ENOMEM = 2,        /* device allocation failed (only the *_create calls allocate) */
+  RB_ECUDA = 3,         /* a CUDA runtime call failed; see rb_last_error() */
+  RB_ENOCONV = 4,       /* a CG column reached max_iter before the tolerance */
+  RB_EBREAKDOWN = 5,    /* a CG column met p.q <= 0 or a non-finite value */
+  RB_ETIMEOUT = 6,      /* a bounded device-side wait gave up (persistent solve) */
+  RB_EUNSUPPORTED = 7   /* a valid request this build does not implement */
+} rb_status;
+
+typedef enum { RB_F64 = 0, RB_F32 = 1 } rb_dtype;
+typedef enum { RB_CSR = 0, RB_SELL = 1, RB_AUTO = 2 } rb_format;
+
+/* Message of the calling thread's last failed call ("" if none). Owned by the library. */
+const char* rb_last_error(void);
+/* Library version, e.g. "0.1.0". */
+const char* rb_version(void);
+
+/* ------------------------------------------------------------------------------------
+ * Operator build: staggered symmetry-preserving FVM operators on Cartesian grids
+ * (Sec. 3, semi-discrete equations (ns); Sec. 4, symmetry-preserving discretisation).
+ *
+ * The grid has n[d] cells along axis d (x, y, z), bounded by n[d] + 1 increasing node
+ * coordinates nodes[d] (DEVICE pointers, float64).  An axis is periodic or bounded by
+ * walls; faces on walls are excluded (no penetration), which gives homogeneous Neumann
+ * conditions for the pressure.  Cells are numbered id = i + n[0] (j + n[1] k).  Faces are
+ * numbered direction by direction (x, y, z); within a direction lexicographically with
+ * x fastest, the face coordinate along its own axis running over 0..n-1 on a periodic
+ * axis (face i separates cells i-1 mod n and i) and over 1..n-1 between walls.
+ *   A_f = product of the two transverse cell widths, d_f = distance between the two cell
+ *   centres adjacent to the face, Omega_s = A_f d_f.
+ *   RB_FVM_DIVERGENCE  M (cells x faces):  +A_f in the cell below face f, -A_f above.
+ *   RB_FVM_GRADIENT    G = -Omega_s^{-1} M^T (faces x cells): -1/d_f, +1/d_f.
+ *   RB_FVM_LAPLACIAN   L = M G (cells x cells): A_f / d_f to each neighbour across f,
+ *                      minus their sum on the diagonal (symmetric, zero row sums).
+ * Requirements: n[d] >= 3 on a periodic axis, n[d] >= 2 between walls.
+ * ------------------------------------------------------------------------------------ */
+typedef enum { RB_FVM_LAPLACIAN = 0, RB_FVM_DIVERGENCE = 1, RB_FVM_GRADIENT = 2 } rb_fvm_kind;
+
+typedef struct {
+  int32_t n[3];
+  int32_t periodic[3];
+  const double* nodes[3];
+} rb_grid_desc;
+
+/* Rows, columns and nonzeros of the operator `kind` on `grid` (host outputs; no GPU work). */
+rb_status rb_fvm_csr_size(const rb_grid_desc* grid, rb_fvm_kind kind, int32_t* n_rows, int32_t* n_cols,
+                          int64_t* nnz);
+
+/* Writes the CSR of `kind` times `scale` (e.g. -1 for the SPD Poisson matrix -L) into
+ * caller-allocated DEVICE arrays: row_ptr[n_rows + 1], col_idx[nnz], vals[nnz] (float64).
+ * Columns are sorted within each row.  Asynchronous on `stream`. */
+rb_status rb_fvm_assemble(const rb_grid_desc* grid, rb_fvm_kind kind, double scale, int32_t* row_ptr,
+                          int32_t* col_idx, double* vals, rb_stream_t stream);
+
+/* Cotangent-weight Laplacian of a triangle mesh (vertex-centred, per unit depth), the
+ * unstructured operator of the extruded-airfoil case (Sec. 4.3).  The caller passes the
+ * mesh (DEVICE: points[2 n_vert] as x,y pairs, triangles[3 n_tri] counter-clockwise) and
+ * the CSR pattern of its vertex adjacency with the diagonal (DEVICE row_ptr, col_idx,
+ * columns sorted).  Writes into vals[nnz] (DEVICE float64): off-diagonal
+ * w_ij = (cot a_ij + cot b_ij) / 2 over the triangles sharing edge ij, clamped at 0,
+ * diagonal -sum_j w_ij; and into area[n_vert] (DEVICE float64, may be NULL) the
+ * barycentric dual areas (a third of each incident triangle).  status: DEVICE int64[2],
+ * required: status[0] receives the number of clamped edges, status[1] is nonzero when the
+ * pattern lacks an edge of a triangle or a diagonal entry (the values are then invalid).
+ * Asynchronous on `stream`. */
+rb_status rb_mesh_cot_laplacian(int32_t n_vert, const double* points, int32_t n_tri, const int32_t* triangles,
+                                const int32_t* row_ptr, const int32_t* col_idx, int64_t nnz, double* vals,
+                                double* area, int64_t* status, rb_stream_t stream);
+
+/* ------------------------------------------------------------------------------------
+ * Operators: A = I_k (x) A~ stored once (Sec. 2, Eq. (1); memory remark of Sec. 3.1)
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+  int32_t n_rows, n_cols;
+  int64_t nnz;
+  const int32_t* row_ptr; /* n_rows + 1, non-decreasing, row_ptr[0] = 0 */
+  const int32_t* col_idx; /* nnz, each in [0, n_cols) */
+  const double* vals;     /* nnz, finite */
+  int32_t on_device;      /* 1: the three arrays are device memory; 0: host memory */
+} rb_csr_desc;
+
+/* Repeated-block descriptor.  k_max: the largest k that will be applied (<= RB_MAX_K).
+ * extruded_nz > 0 marks an operator extruded along a periodic direction into Nz identical
+ * planes: L3D = dz (I_Nz (x) A~) + T_z (x) diag(z_weight), T_z the periodic [1 -2 1]
+ * across planes; rb_spmm then takes k == extruded_nz columns (one per plane) and applies
+ * the whole L3D.  z_weight: n_rows weights (a_i / dz for a dual area a_i), device or
+ * host as the CSR's on_device says; NULL when extruded_nz == 0. */
+typedef struct {
+  int32_t k_max;
+  int32_t extruded_nz;
+  const double* z_weight;
+  double dz;
+} rb_block_desc;
+
+typedef struct rb_op* rb_op_t;
+
+typedef struct {
+  int32_t n_rows, n_cols;
+  int64_t nnz;
+  int32_t dtype, format;   /* rb_dtype, rb_format actually stored */
+  int32_t sell_c, sell_sigma;
+  int64_t sell_padded_nnz; /* stored entries including SELL padding */
+  int64_t device_bytes;    /* device memory owned by the operator */
+  int32_t has_diag;        /* every row has a nonzero diagonal entry (square operators) */
+  int32_t extruded_nz;
+} rb_op_info;
+
+/* Copies and validates the CSR (monotone row_ptr, col_idx in range, finite values;
+ * RB_EINVAL otherwise), converts values to `dtype` (RB_F32: round to nearest even), and
+ * lays it out in `format` (RB_SELL: sliced ELL with C = 32 rows per slice and rows sorted
+ * by length within windows of sigma = 256 rows; RB_AUTO picks CSR).  Also stores the
+ * inverse diagonal for Jacobi preconditioning when the operator is square.  Allocates;
+ * synchronises `stream`. */
+rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_desc* block, rb_dtype dtype, rb_format format,
+                             rb_stream_t stream, rb_op_t* out);
+rb_status rb_operator_destroy(rb_op_t op);
+rb_status rb_operator_info(rb_op_t op, rb_op_info* info);
+
+/* Y = A~ X with a per-column scale:  Y[i, j] = c[j] * sum_p val[p] X[idx[p], j]  (Algorithm 1).
+ * X: n_cols x k (ldx), Y: n_rows x k (ldy), both of the operator's dtype; c: k float64
+ * DEVICE values or NULL (= 1).  For an extruded operator k must equal extruded_nz and
+ * the full L3D is applied (c is then applied to the whole row).  X and Y must not
+ * overlap.  Vector width, rows per block and lanes per row are chosen per (operator, k)
+ * from the tuning table (rb_tune_spmm). */
+rb_status rb_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k, const double* c,
+                  rb_stream_t stream);
+
+/* Times the candidate SpMM schedules for (A, k) on scratch copies of X/Y shapes and
+ * stores the fastest in A's tuning table (synchronises; X, Y as for rb_spmm, their
+ * contents are overwritten: Y only). */
+rb_status rb_tune_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k, rb_stream_t stream);
+
+/* ------------------------------------------------------------------------------------
+ * The other basic operations, per column of an n x k block (Sec. 1: dot, axpy, axty)
+ * ------------------------------------------------------------------------------------ */
+/* Workspace (device bytes) that rb_dot needs for (n, k). */
+size_t rb_dot_workspace_bytes(int64_t n, int32_t k);
+/* out[j] = sum_i X[i, j] Y[i, j] (float64 accumulation, fixed summation order: the result
+ * is bit-reproducible for a given n, k).  out: k float64 DEVICE values.  work: device
+ * scratch of rb_dot_workspace_bytes(n, k) bytes, 16-byte aligned, contents ignored. */
+rb_status rb_dot(int64_t n, int32_t k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y, int64_t ldy,
+                 double* out, void* work, size_t work_bytes, rb_stream_t stream);
+/* Y[:, j] += alpha[j] X[:, j]; alpha: k float64 DEVICE values. */
+rb_status rb_axpy(int64_t n, int32_t k, rb_dtype dtype, const double* alpha, const void* X, int64_t ldx, void* Y,
+                  int64_t ldy, rb_stream_t stream);
+/* Y[i, j] = alpha X[i, j] Y[i, j]  (the element-wise product of Sec. 1 and Sec. 3.1). */
+rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha, const void* X, int64_t ldx, void* Y,
+                  int64_t ldy, rb_stream_t stream);
+
+/* ------------------------------------------------------------------------------------
+ * Poisson solve: Jacobi-preconditioned CG on k independent columns sharing one operator
+ * (the pressure solve of the projection method, Sec. 4; the k flow states of Sec. 3).
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+  double rtol;           /* stop when ||b - A x||_2 <= rtol ||b||_2 (true residual, FP64) */
+  int32_t max_iter;      /* CG iterations (inner iterations summed when mixed) */
+  int32_t precond;       /* 0: none, 1: Jacobi */
+  int32_t mixed;         /* 0: FP64 CG; 1: FP32-inner CG inside FP64 iterative refinement */
+  double inner_rtol;     /* mixed: relative tolerance of each inner FP32 solve (e.g. 1e-4) */
+  int32_t max_sweeps;    /* mixed: refinement sweeps */
+  int32_t project_mean;  /* 1: singular periodic/Neumann operator; remove the column mean of
+                            every true residual and of the final x (zero-mean solution) */
+  int32_t check_every;   /* iterations between host convergence checks (>= 1) */
+} rb_cg_params;
+
+typedef struct {
+  int32_t iters[RB_MAX_K];       /* CG iterations per column (inner iterations when mixed) */
+  double true_rel_res[RB_MAX_K]; /* ||b - A x|| / ||b|| at exit, FP64 */
+  int32_t status[RB_MAX_K];      /* rb_status per column */
+  int32_t spmm_calls;            /* operator applications (all columns at once) */
+  int32_t sweeps;                /* refinement sweeps (mixed) */
+  int32_t host_syncs;            /* device-to-host convergence reads */
+  double ms;                     /* wall time of the call */
+} rb_cg_report;
+
+/* Device workspace for rb_cg_solve on (A, k, params). */
+size_t rb_cg_workspace_bytes(rb_op_t A, int32_t k, const rb_cg_params* params);
+
+/* Solves A x_j = b_j for the k columns.  A: square FP64 operator with a diagonal.
+ * A_inner: the same matrix stored as RB_F32, required when params->mixed (else NULL).
+ * B (n x k, ldb), X (n x k, ldx; in: initial guess, out: solution): float64 DEVICE.
+ * work: device scratch of rb_cg_workspace_bytes bytes.  Synchronises `stream` (the host
+ * reads the per-column state every check_every iterations).  Returns the worst column
+ * status (RB_OK, RB_ENOCONV or RB_EBREAKDOWN); report (may be NULL) gets per-column
+ * details. */
+rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params* params, const double* B, int64_t ldb,
+                      double* X, int64_t ldx, int32_t k, void* work, size_t work_bytes, rb_cg_report* report,
+                      rb_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBSPMM_H */

@@ -1,0 +1,350 @@
+"""Repeated-block SpMM for CFD operators on one GB300 (sm_103a): Python binding.
+
+A thin ctypes layer over the C ABI in include/rbspmm.h: it marshals torch tensors (device
+memory, streams) into pointers and sizes and turns status codes into exceptions.  Every
+computation runs in the library's CUDA kernels; there is no Python or CPU fallback: if
+librbspmm.so is missing the calls raise.
+
+Layout: a block of k right-hand sides is a 2-D tensor (n, k) whose rows are contiguous
+(stride (ld, 1), ld >= k): the k columns of one row are interleaved, as in Algorithm 1.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librbspmm.so")
+
+RB_OK, RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ENOCONV, RB_EBREAKDOWN, RB_ETIMEOUT, RB_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["RB_OK", "RB_EINVAL", "RB_ENOMEM", "RB_ECUDA", "RB_ENOCONV", "RB_EBREAKDOWN", "RB_ETIMEOUT",
+                "RB_EUNSUPPORTED"]
+RB_F64, RB_F32 = 0, 1
+RB_CSR, RB_SELL, RB_AUTO = 0, 1, 2
+RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT = 0, 1, 2
+RB_MAX_K = 64
+
+# exported C symbols, in the order include/rbspmm.h declares them
+SYMBOLS = ["rb_last_error", "rb_version", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_mesh_cot_laplacian",
+           "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_spmm", "rb_tune_spmm",
+           "rb_dot_workspace_bytes", "rb_dot", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve"]
+
+
+class RbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+# ----------------------------------------------------------------------------- C structs
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("periodic", C.c_int32 * 3), ("nodes", C.c_void_p * 3)]
+
+
+class CsrDesc(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("vals", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("k_max", C.c_int32), ("extruded_nz", C.c_int32), ("z_weight", C.c_void_p), ("dz", C.c_double)]
+
+
+class OpInfo(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64), ("dtype", C.c_int32),
+                ("format", C.c_int32), ("sell_c", C.c_int32), ("sell_sigma", C.c_int32),
+                ("sell_padded_nnz", C.c_int64), ("device_bytes", C.c_int64), ("has_diag", C.c_int32),
+                ("extruded_nz", C.c_int32)]
+
+
+class CgParams(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("precond", C.c_int32), ("mixed", C.c_int32),
+                ("inner_rtol", C.c_double), ("max_sweeps", C.c_int32), ("project_mean", C.c_int32),
+                ("check_every", C.c_int32)]
+
+
+class CgReport(C.Structure):
+    _fields_ = [("iters", C.c_int32 * RB_MAX_K), ("true_rel_res", C.c_double * RB_MAX_K),
+                ("status", C.c_int32 * RB_MAX_K), ("spmm_calls", C.c_int32), ("sweeps", C.c_int32),
+                ("host_syncs", C.c_int32), ("ms", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded native library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_2508_06710_gb300.build.build() (needs nvcc)")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    sig = {
+        "rb_last_error": (C.c_char_p, []),
+        "rb_version": (C.c_char_p, []),
+        "rb_fvm_csr_size": (C.c_int, [C.POINTER(GridDesc), C.c_int, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
+        "rb_fvm_assemble": (C.c_int, [C.POINTER(GridDesc), C.c_int, dbl, vp, vp, vp, vp]),
+        "rb_mesh_cot_laplacian": (C.c_int, [i32, vp, i32, vp, vp, vp, i64, vp, vp, vp, vp]),
+        "rb_operator_create": (C.c_int, [C.POINTER(CsrDesc), C.POINTER(BlockDesc), C.c_int, C.c_int, vp,
+                                         C.POINTER(vp)]),
+        "rb_operator_destroy": (C.c_int, [vp]),
+        "rb_operator_info": (C.c_int, [vp, C.POINTER(OpInfo)]),
+        "rb_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp, vp]),
+        "rb_tune_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp]),
+        "rb_dot_workspace_bytes": (sz, [i64, i32]),
+        "rb_dot": (C.c_int, [i64, i32, C.c_int, vp, i64, vp, i64, vp, vp, sz, vp]),
+        "rb_axpy": (C.c_int, [i64, i32, C.c_int, vp, vp, i64, vp, i64, vp]),
+        "rb_axty": (C.c_int, [i64, i32, C.c_int, dbl, vp, i64, vp, i64, vp]),
+        "rb_cg_workspace_bytes": (sz, [vp, i32, C.POINTER(CgParams)]),
+        "rb_cg_solve": (C.c_int, [vp, vp, C.POINTER(CgParams), vp, i64, vp, i64, i32, vp, sz, C.POINTER(CgReport),
+                                  vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != RB_OK:
+        raise RbError(status, f"{what}: {lib().rb_last_error().decode()}")
+
+
+def version() -> str:
+    return lib().rb_version().decode()
+
+
+# ----------------------------------------------------------------------------- tensor helpers
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _block(t, name):
+    """(pointer, n, k, ld) of a row-major 2-D block whose rows are contiguous."""
+    if t.dim() == 1:
+        t = t.view(-1, 1)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a 2-D tensor with contiguous rows (stride (ld, 1))")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return t, t.shape[0], t.shape[1], max(t.stride(0), t.shape[1])
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return RB_F64
+    if t.dtype == torch.float32:
+        return RB_F32
+    raise ValueError("blocks must be float64 or float32")
+
+
+# ----------------------------------------------------------------------------- operator build
+def _grid_desc(nodes, periodic):
+    g = GridDesc()
+    for d in range(3):
+        g.n[d] = int(nodes[d].numel() - 1)
+        g.periodic[d] = 1 if periodic[d] else 0
+        g.nodes[d] = nodes[d].data_ptr()
+    return g
+
+
+def fvm_csr_size(nodes, periodic, kind):
+    g = _grid_desc(nodes, periodic)
+    nr, nc, nnz = C.c_int32(), C.c_int32(), C.c_int64()
+    _check(lib().rb_fvm_csr_size(C.byref(g), kind, C.byref(nr), C.byref(nc), C.byref(nnz)), "rb_fvm_csr_size")
+    return nr.value, nc.value, nnz.value
+
+
+def fvm_assemble(nodes, periodic, kind, scale=1.0, stream=None):
+    """CSR (row_ptr, col_idx, vals, n_cols) of the staggered FVM operator on the grid whose axis
+    node coordinates are the float64 CUDA tensors ``nodes`` (x, y, z)."""
+    torch = _torch()
+    nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
+    nr, nc, nnz = fvm_csr_size(nodes, periodic, kind)
+    dev = nodes[0].device
+    rp = torch.empty(nr + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(nnz, dtype=torch.int32, device=dev)
+    va = torch.empty(nnz, dtype=torch.float64, device=dev)
+    g = _grid_desc(nodes, periodic)
+    _check(lib().rb_fvm_assemble(C.byref(g), kind, float(scale), _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)),
+           "rb_fvm_assemble")
+    return rp, ci, va, nc
+
+
+def grid_nodes(grid, device="cuda"):
+    """Device node tensors and periodic flags of a ``workloads.Grid``."""
+    torch = _torch()
+    nodes = [torch.as_tensor(a.nodes, dtype=torch.float64, device=device) for a in grid.axes]
+    return nodes, [a.periodic for a in grid.axes]
+
+
+def mesh_cot_laplacian(points, triangles, row_ptr, col_idx, stream=None):
+    """Values and dual areas of the cotangent Laplacian on the given adjacency pattern.
+    Returns (vals, area, status) with status a device int64[2] (clamped edges, pattern error)."""
+    torch = _torch()
+    dev = points.device
+    n = points.shape[0]
+    nnz = col_idx.numel()
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    area = torch.empty(n, dtype=torch.float64, device=dev)
+    status = torch.empty(2, dtype=torch.int64, device=dev)
+    _check(lib().rb_mesh_cot_laplacian(n, _ptr(points.contiguous()), triangles.shape[0], _ptr(triangles.contiguous()),
+                                       _ptr(row_ptr), _ptr(col_idx), nnz, _ptr(vals), _ptr(area), _ptr(status),
+                                       _stream(stream)), "rb_mesh_cot_laplacian")
+    return vals, area, status
+
+
+# ----------------------------------------------------------------------------- operators
+class Operator:
+    """A = I_k (x) A~ stored once on the device (CSR or sliced ELL, FP64 or FP32)."""
+
+    def __init__(self, row_ptr, col_idx, vals, n_cols, dtype="f64", fmt="csr", k_max=1, extruded_nz=0,
+                 z_weight=None, dz=0.0, stream=None):
+        torch = _torch()
+        on_dev = bool(row_ptr.is_cuda)
+        self._keep = (row_ptr.to(torch.int32).contiguous(), col_idx.to(torch.int32).contiguous(),
+                      vals.to(torch.float64).contiguous(),
+                      None if z_weight is None else z_weight.to(torch.float64).contiguous())
+        rp, ci, va, zw = self._keep
+        d = CsrDesc(rp.numel() - 1, int(n_cols), ci.numel(), rp.data_ptr(), ci.data_ptr() if ci.numel() else None,
+                    va.data_ptr() if va.numel() else None, 1 if on_dev else 0)
+        b = BlockDesc(int(k_max), int(extruded_nz), None if zw is None else zw.data_ptr(), float(dz))
+        h = C.c_void_p()
+        dt = {"f64": RB_F64, "f32": RB_F32}[dtype]
+        fm = {"csr": RB_CSR, "sell": RB_SELL, "auto": RB_AUTO}[fmt]
+        _check(lib().rb_operator_create(C.byref(d), C.byref(b), dt, fm, _stream(stream) if on_dev else None,
+                                        C.byref(h)), "rb_operator_create")
+        self.handle = h
+        self.dtype = dtype
+        self._keep = None
+        inf = self.info()
+        self.n_rows, self.n_cols, self.nnz = inf.n_rows, inf.n_cols, inf.nnz
+        self.extruded_nz = inf.extruded_nz
+
+    @classmethod
+    def from_scipy(cls, A, **kw):
+        torch = _torch()
+        A = A.tocsr()
+        return cls(torch.as_tensor(A.indptr.astype("int32")), torch.as_tensor(A.indices.astype("int32")),
+                   torch.as_tensor(A.data.astype("float64")), A.shape[1], **kw)
+
+    def info(self) -> OpInfo:
+        inf = OpInfo()
+        _check(lib().rb_operator_info(self.handle, C.byref(inf)), "rb_operator_info")
+        return inf
+
+    def spmm(self, X, Y=None, c=None, stream=None):
+        torch = _torch()
+        X, _, k, ldx = _block(X, "X")
+        if Y is None:
+            Y = torch.empty((self.n_rows, k), dtype=X.dtype, device=X.device)
+        Y, _, _, ldy = _block(Y, "Y")
+        _check(lib().rb_spmm(self.handle, _ptr(X), ldx, _ptr(Y), ldy, k, _ptr(c), _stream(stream)), "rb_spmm")
+        return Y
+
+    def tune(self, X, Y, stream=None):
+        X, _, k, ldx = _block(X, "X")
+        Y, _, _, ldy = _block(Y, "Y")
+        _check(lib().rb_tune_spmm(self.handle, _ptr(X), ldx, _ptr(Y), ldy, k, _stream(stream)), "rb_tune_spmm")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().rb_operator_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- basic operations
+def dot(X, Y, out=None, work=None, stream=None):
+    torch = _torch()
+    X, n, k, ldx = _block(X, "X")
+    Y, _, _, ldy = _block(Y, "Y")
+    if out is None:
+        out = torch.empty(k, dtype=torch.float64, device=X.device)
+    wb = lib().rb_dot_workspace_bytes(n, k)
+    if work is None:
+        work = torch.empty(wb, dtype=torch.uint8, device=X.device)
+    _check(lib().rb_dot(n, k, _dtype_code(X), _ptr(X), ldx, _ptr(Y), ldy, _ptr(out), _ptr(work), work.numel(),
+                        _stream(stream)), "rb_dot")
+    return out
+
+
+def axpy(alpha, X, Y, stream=None):
+    X, n, k, ldx = _block(X, "X")
+    Y, _, _, ldy = _block(Y, "Y")
+    _check(lib().rb_axpy(n, k, _dtype_code(X), _ptr(alpha), _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)), "rb_axpy")
+    return Y
+
+
+def axty(alpha, X, Y, stream=None):
+    X, n, k, ldx = _block(X, "X")
+    Y, _, _, ldy = _block(Y, "Y")
+    _check(lib().rb_axty(n, k, _dtype_code(X), float(alpha), _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)),
+           "rb_axty")
+    return Y
+
+
+# ----------------------------------------------------------------------------- Poisson solve
+@dataclass
+class CgResult:
+    status: int
+    iters: list
+    true_rel_res: list
+    col_status: list
+    spmm_calls: int
+    sweeps: int
+    host_syncs: int
+    ms: float
+    extra: dict = field(default_factory=dict)
+
+
+def cg_params(rtol=1e-10, max_iter=20000, precond=True, mixed=False, inner_rtol=1e-4, max_sweeps=30,
+              project_mean=False, check_every=32) -> CgParams:
+    return CgParams(rtol, max_iter, 1 if precond else 0, 1 if mixed else 0, inner_rtol, max_sweeps,
+                    1 if project_mean else 0, check_every)
+
+
+def cg_workspace_bytes(A: Operator, k: int, params: CgParams) -> int:
+    return int(lib().rb_cg_workspace_bytes(A.handle, k, C.byref(params)))
+
+
+def cg_solve(A: Operator, B, X, A_inner: Operator | None = None, params: CgParams | None = None, work=None,
+             stream=None, raise_on_fail=False) -> CgResult:
+    """Solves A X[:, j] = B[:, j] for every column j; X holds the initial guess on entry."""
+    torch = _torch()
+    params = params or cg_params()
+    B, n, k, ldb = _block(B, "B")
+    X, _, _, ldx = _block(X, "X")
+    wb = cg_workspace_bytes(A, k, params)
+    if work is None:
+        work = torch.empty(wb, dtype=torch.uint8, device=X.device)
+    rep = CgReport()
+    st = lib().rb_cg_solve(A.handle, None if A_inner is None else A_inner.handle, C.byref(params), _ptr(B), ldb,
+                           _ptr(X), ldx, k, _ptr(work), work.numel(), C.byref(rep), _stream(stream))
+    if st not in (RB_OK, RB_ENOCONV, RB_EBREAKDOWN) or (raise_on_fail and st != RB_OK):
+        _check(st, "rb_cg_solve")
+    return CgResult(st, list(rep.iters[:k]), list(rep.true_rel_res[:k]), list(rep.status[:k]), rep.spmm_calls,
+                    rep.sweeps, rep.host_syncs, rep.ms)

@@ -1,0 +1,229 @@
+// The other three basic operations of Sec. 1 on an n x k block, one column per right-hand
+// side: dot (per-column inner products, FP64 accumulation), axpy (per-column scalars) and
+// axty (element-wise product).  Streaming kernels: each thread handles VEC consecutive
+// columns of a row (16-byte accesses when aligned), rows in a grid-stride loop.
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace rb {
+namespace {
+
+constexpr int kBlasGrid = 152 * 4;
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_dot_partial(int64_t n, int k, int kp, const T* __restrict__ X,
+                                                          int64_t ldx, const T* __restrict__ Y, int64_t ldy,
+                                                          double* __restrict__ partials) {
+  __shared__ RedSmem<1> sm;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  const int rloc = threadIdx.x / kp;
+  const bool col_ok = chunk * VEC < k;
+  double acc[1][VEC];
+  float facc[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) acc[0][e] = 0.0, facc[e] = 0.0f;
+  int pending = 0;
+  for (int64_t row = (int64_t)blockIdx.x * R + rloc; row < n; row += (int64_t)gridDim.x * R) {
+    if (!col_ok) break;
+    const Vec<T, VEC> x = ldv<T, VEC>(X + row * ldx + chunk * VEC);
+    const Vec<T, VEC> y = ldv<T, VEC>(Y + row * ldy + chunk * VEC);
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[0][e] = fma((double)x.v[e], (double)y.v[e], acc[0][e]);
+    } else {
+      // FP32 products summed four at a time in FP32, the groups in FP64
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) facc[e] = fmaf((float)x.v[e], (float)y.v[e], facc[e]);
+      if (++pending == 4) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[0][e] += (double)facc[e], facc[e] = 0.0f;
+        pending = 0;
+      }
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[0][e] += (double)facc[e];
+  }
+  const double v = block_reduce<1, VEC>(acc, kp, 1, k, sm);
+  if ((int)threadIdx.x < k) partials[(size_t)blockIdx.x * k + threadIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_dot_final(int m, int nblocks, const double* __restrict__ partials,
+                                                        double* __restrict__ out) {
+  __shared__ RedSmem<1> sm;
+  const double r = final_sum<1>(partials, m, nblocks, sm);
+  if ((int)threadIdx.x < m) out[threadIdx.x] = r;
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_axpy(int64_t n, int k, int kp, const double* __restrict__ alpha,
+                                                   const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
+                                                   int64_t ldy) {
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  if (chunk * VEC >= k) return;
+  T a[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) a[e] = (T)alpha[chunk * VEC + e];
+  for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < n; row += (int64_t)gridDim.x * R) {
+    const Vec<T, VEC> x = ldv<T, VEC>(X + row * ldx + chunk * VEC);
+    Vec<T, VEC> y = ldv_rw<T, VEC>(Y + row * ldy + chunk * VEC);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) y.v[e] = fma(a[e], x.v[e], y.v[e]);
+    stv<T, VEC>(Y + row * ldy + chunk * VEC, y);
+  }
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_axty(int64_t n, int k, int kp, T alpha, const T* __restrict__ X,
+                                                   int64_t ldx, T* __restrict__ Y, int64_t ldy) {
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  if (chunk * VEC >= k) return;
+  for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < n; row += (int64_t)gridDim.x * R) {
+    const Vec<T, VEC> x = ldv<T, VEC>(X + row * ldx + chunk * VEC);
+    Vec<T, VEC> y = ldv_rw<T, VEC>(Y + row * ldy + chunk * VEC);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) y.v[e] = alpha * x.v[e] * y.v[e];
+    stv<T, VEC>(Y + row * ldy + chunk * VEC, y);
+  }
+}
+
+int blas_grid(int64_t n, int R) { return (int)std::max<int64_t>(1, std::min<int64_t>(kBlasGrid, (n + R - 1) / R)); }
+
+rb_status check_block(const char* fn, int64_t n, int k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y,
+                      int64_t ldy) {
+  RB_REQUIRE(n >= 0, "%s: negative n", fn);
+  RB_REQUIRE(k >= 1 && k <= RB_MAX_K, "%s: k = %d outside [1, %d]", fn, k, RB_MAX_K);
+  RB_REQUIRE(dtype == RB_F64 || dtype == RB_F32, "%s: unknown dtype", fn);
+  RB_REQUIRE(ldx >= k && ldy >= k, "%s: leading dimension smaller than k", fn);
+  RB_REQUIRE(n == 0 || (X && Y), "%s: null X or Y", fn);
+  const int eb = dtype == RB_F64 ? 8 : 4;
+  RB_REQUIRE((uintptr_t)X % eb == 0 && (uintptr_t)Y % eb == 0, "%s: X or Y not aligned to the element size", fn);
+  return RB_OK;
+}
+
+// vector width and threads per row for a block pair
+void vec_kp(int eb, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y, int& vec, int& kp) {
+  vec = pick_vec(eb, k, ldx, ldy, X, Y);
+  while (next_pow2((k + vec - 1) / vec) > 32 && vec < 16 / eb && k % (vec * 2) == 0) vec *= 2;
+  kp = next_pow2((k + vec - 1) / vec);
+}
+
+}  // namespace
+
+size_t dot_partials(int64_t n, int k) {
+  (void)k;
+  return (size_t)kBlasGrid * k * sizeof(double) + 256;
+}
+
+}  // namespace rb
+
+using namespace rb;
+
+extern "C" size_t rb_dot_workspace_bytes(int64_t n, int32_t k) {
+  if (k < 1 || k > RB_MAX_K || n < 0) return 0;
+  return dot_partials(n, k);
+}
+
+namespace rb {
+// Calls f(std::integral_constant<int, V>) for the vector width V; widths above 16 bytes are
+// never instantiated.
+template <typename T, class F>
+void with_vec(int vec, F&& f) {
+  switch (vec) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 4:
+      if constexpr (sizeof(T) == 4) f(std::integral_constant<int, 4>{});
+      break;
+  }
+}
+}  // namespace rb
+
+#define RB_DISPATCH_VEC(T, vec, ...) \
+  with_vec<T>(vec, [&](auto vv_) { constexpr int V = decltype(vv_)::value; __VA_ARGS__; })
+
+extern "C" rb_status rb_dot(int64_t n, int32_t k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y,
+                            int64_t ldy, double* out, void* work, size_t work_bytes, rb_stream_t stream) {
+  clear_error();
+  RB_TRY(check_block("rb_dot", n, k, dtype, X, ldx, Y, ldy));
+  RB_REQUIRE(out != nullptr, "rb_dot: null output");
+  RB_REQUIRE(work != nullptr && work_bytes >= rb_dot_workspace_bytes(n, k), "rb_dot: workspace too small (%zu < %zu)",
+             work_bytes, rb_dot_workspace_bytes(n, k));
+  RB_REQUIRE((uintptr_t)work % 16 == 0, "rb_dot: workspace not 16-byte aligned");
+  cudaStream_t s = S(stream);
+  const int eb = dtype == RB_F64 ? 8 : 4;
+  int vec, kp;
+  vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
+  RB_REQUIRE(kp <= 32, "rb_dot: k = %d needs 16-byte aligned rows", k);
+  const int R = kThreads / kp;
+  const int grid = blas_grid(n, R);
+  double* partials = static_cast<double*>(work);
+  if (dtype == RB_F64) {
+    RB_DISPATCH_VEC(double, vec,
+                    k_dot_partial<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, (const double*)X, ldx,
+                                                                       (const double*)Y, ldy, partials));
+  } else {
+    RB_DISPATCH_VEC(float, vec,
+                    k_dot_partial<float, V><<<grid, kThreads, 0, s>>>(n, k, kp, (const float*)X, ldx,
+                                                                      (const float*)Y, ldy, partials));
+  }
+  k_dot_final<<<1, kThreads, 0, s>>>(k, grid, partials, out);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+extern "C" rb_status rb_axpy(int64_t n, int32_t k, rb_dtype dtype, const double* alpha, const void* X, int64_t ldx,
+                             void* Y, int64_t ldy, rb_stream_t stream) {
+  clear_error();
+  RB_TRY(check_block("rb_axpy", n, k, dtype, X, ldx, Y, ldy));
+  RB_REQUIRE(alpha != nullptr, "rb_axpy: null alpha");
+  if (n == 0) return RB_OK;
+  cudaStream_t s = S(stream);
+  const int eb = dtype == RB_F64 ? 8 : 4;
+  int vec, kp;
+  vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
+  RB_REQUIRE(kp <= 32, "rb_axpy: k = %d needs 16-byte aligned rows", k);
+  const int grid = blas_grid(n, kThreads / kp);
+  if (dtype == RB_F64) {
+    RB_DISPATCH_VEC(double, vec,
+                    k_axpy<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, alpha, (const double*)X, ldx, (double*)Y,
+                                                                ldy));
+  } else {
+    RB_DISPATCH_VEC(float, vec,
+                    k_axpy<float, V><<<grid, kThreads, 0, s>>>(n, k, kp, alpha, (const float*)X, ldx, (float*)Y,
+                                                               ldy));
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+extern "C" rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha, const void* X, int64_t ldx, void* Y,
+                             int64_t ldy, rb_stream_t stream) {
+  clear_error();
+  RB_TRY(check_block("rb_axty", n, k, dtype, X, ldx, Y, ldy));
+  if (n == 0) return RB_OK;
+  cudaStream_t s = S(stream);
+  const int eb = dtype == RB_F64 ? 8 : 4;
+  int vec, kp;
+  vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
+  RB_REQUIRE(kp <= 32, "rb_axty: k = %d needs 16-byte aligned rows", k);
+  const int grid = blas_grid(n, kThreads / kp);
+  if (dtype == RB_F64) {
+    RB_DISPATCH_VEC(double, vec,
+                    k_axty<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, alpha, (const double*)X, ldx, (double*)Y,
+                                                                ldy));
+  } else {
+    RB_DISPATCH_VEC(float, vec,
+                    k_axty<float, V><<<grid, kThreads, 0, s>>>(n, k, kp, (float)alpha, (const float*)X, ldx,
+                                                               (float*)Y, ldy));
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}

@@ -1,0 +1,911 @@
+// Poisson solve on k columns that share one operator: Jacobi-preconditioned CG per column
+// (the pressure solve of the projection method, Sec. 4; k flow states or parameters, Sec. 3),
+// and FP32-inner CG inside FP64 iterative refinement.
+//
+// One CG iteration is three kernels, each streaming the k interleaved columns once:
+//   q  = A p            (SpMM, Algorithm 1)   fused with  pq_j = p_j . q_j
+//   x += a p, r -= a q, z = D^-1 r            fused with  rz_j = r_j . z_j,  rr_j = r_j . r_j
+//   p  = z + b p        (z recomputed from r; never stored)
+// The per-column scalars (alpha = rz/pq, beta = rz_new/rz) are formed on the device by the
+// last block of the reducing kernel, so the host only reads the per-column state every
+// check_every iterations.  A column whose recurrence residual passes the tolerance is
+// checked against its true residual b - A x in FP64; if that fails it restarts from the
+// true residual (residual replacement).  Converged columns stop changing.
+//
+// Mixed precision: the outer loop forms r = b - A x with the FP64 operator, the inner CG
+// runs on the FP32 copy of the operator with FP32 vectors (dot products accumulated in
+// FP64) on r / ||r||, and x += ||r|| d is applied in FP64.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "reduce.cuh"
+#include "spmm_impl.cuh"
+
+namespace rb {
+
+SpmmSched default_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y);
+SpmmSched pick_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y);
+
+namespace {
+
+enum ColState : int {
+  ST_ACTIVE = 0,     // iterating
+  ST_CHECK = 1,      // recurrence residual passed: true residual pending
+  ST_DONE = 2,       // converged (or, for an inner solve, finished)
+  ST_BREAKDOWN = 3,  // p.q <= 0 or not finite
+  ST_NOCONV = 4,     // iteration budget exhausted
+  ST_RESTART = 5,    // restart from the freshly computed true residual
+  ST_IDLE = 6        // column takes no part (inner solve of a converged outer column)
+};
+
+enum ResidMode : int { RM_INIT = 0, RM_CHECK = 1, RM_REPORT = 2, RM_OUTER = 3 };
+
+constexpr int K = RB_MAX_K;
+constexpr int kGridMax = 152 * 8;
+// dynamic shared memory of the fused SpMM kernels (their static reduction scratch is < 16 KB)
+constexpr size_t kCgDynSmem = 32 * 1024;
+
+struct CgScal {
+  double rz[K], pq[K], rr[K], tol2[K], alpha[K], beta[K], mean[K];
+  double bb[K], rr_true[K];
+  // outer refinement
+  double otol2[K], omean[K], oscale[K];
+  int ostate[K];
+  int state[K], iters[K];
+  int n_active, n_check, n_oactive, pad;
+  unsigned counter[8];
+};
+
+struct CgCtl {
+  int k, kp;
+  int64_t n;
+  int inner;         // 1: inner FP32 solve of the refinement
+  int project;       // remove column means of true residuals
+  double rtol2;      // rtol^2
+  double inner_rtol2;
+};
+
+// ---------------------------------------------------------------------------------- helpers
+
+// Sums FP32 products in FP32 in groups of four, the groups in FP64; FP64 products in FP64.
+template <typename T>
+struct DotAcc {
+  double d = 0.0;
+  float f = 0.0f;
+  int c = 0;
+  __device__ __forceinline__ void add(T a, T b) {
+    if constexpr (sizeof(T) == 8) {
+      d = fma((double)a, (double)b, d);
+    } else {
+      f = fmaf((float)a, (float)b, f);
+      if (++c == 4) {
+        d += (double)f;
+        f = 0.0f;
+        c = 0;
+      }
+    }
+  }
+  __device__ __forceinline__ double get() const { return d + (double)f; }
+};
+
+__device__ __forceinline__ void recount(CgScal* sc, int k) {
+  int na = 0, nc = 0, no = 0;
+  for (int j = 0; j < k; ++j) {
+    na += sc->state[j] == ST_ACTIVE;
+    nc += sc->state[j] == ST_CHECK;
+    no += sc->ostate[j] == ST_ACTIVE;
+  }
+  sc->n_active = na;
+  sc->n_check = nc;
+  sc->n_oactive = no;
+}
+
+// ------------------------------------------------------------------------- q = A p, p . q
+
+template <typename T, int VEC, int LPR>
+__global__ void __launch_bounds__(kThreads) k_cg_q(CsrArgs<T> a, CgCtl ctl, CgScal* __restrict__ sc,
+                                                    double* __restrict__ partials) {
+  if (sc->n_active == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RedSmem<1> red;
+  const int R = kThreads / (a.kp * LPR);
+  int32_t* s_rp = reinterpret_cast<int32_t*>(smem_raw);
+  int32_t* s_ci = s_rp + round4(R + 1);
+  T* s_va = reinterpret_cast<T*>(s_ci + round4(a.stage_cap));
+  const int t = threadIdx.x;
+  const int sub = t % LPR, rc = t / LPR, chunk = rc % a.kp, rloc = rc / a.kp;
+  DotAcc<T> dacc[VEC];
+  for (int64_t tile = blockIdx.x; tile * R < a.n_rows; tile += gridDim.x) {
+    const int r0 = (int)(tile * R);
+    const TileInfo ti = stage_rows<T>(a, r0, R, s_rp, s_ci, s_va);
+    const bool active = rloc < ti.nr && chunk * VEC < a.k;
+    T acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+    row_accumulate<T, VEC, LPR>(a, ti, s_rp, s_ci, s_va, rloc, chunk, sub, active, acc);
+    if (active && sub == 0) {
+      const int64_t off = (int64_t)(r0 + rloc) * a.ldy + chunk * VEC;
+      const Vec<T, VEC> p = ldv_rw<T, VEC>(a.X + (int64_t)(r0 + rloc) * a.ldx + chunk * VEC);
+      Vec<T, VEC> q;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        q.v[e] = acc[e];
+        dacc[e].add(p.v[e], acc[e]);
+      }
+      stv<T, VEC>(a.Y + off, q);
+    }
+  }
+  double part[1][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) part[0][e] = (sub == 0) ? dacc[e].get() : 0.0;
+  const double v = block_reduce<1, VEC>(part, a.kp, LPR, a.k, red);
+  if (!publish_partials<1>(v, a.k, partials, &sc->counter[0], red)) return;
+  const double tot = final_sum<1>(partials, a.k, gridDim.x, red);
+  const int j = threadIdx.x;
+  if (j < a.k) {
+    sc->pq[j] = tot;
+    double al = 0.0;
+    if (sc->state[j] == ST_ACTIVE) {
+      if (!(tot > 0.0) || !isfinite(tot)) {
+        sc->state[j] = ctl.inner ? ST_DONE : ST_BREAKDOWN;
+      } else {
+        al = sc->rz[j] / tot;
+      }
+    }
+    sc->alpha[j] = al;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, a.k);
+}
+
+// ------------------------------------------- x += a p, r -= a q, rz = r.D^-1 r, rr = r.r
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_cg_update(CgCtl ctl, T* __restrict__ x, int64_t ldx,
+                                                         T* __restrict__ r, const T* __restrict__ p,
+                                                         const T* __restrict__ q, const T* __restrict__ dinv,
+                                                         CgScal* __restrict__ sc, double* __restrict__ partials) {
+  if (sc->n_active == 0) return;
+  __shared__ RedSmem<2> red;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  const bool col_ok = chunk * VEC < k;
+  T al[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) al[e] = col_ok ? (T)sc->alpha[chunk * VEC + e] : T(0);
+  DotAcc<T> drz[VEC], drr[VEC];
+  if (col_ok) {
+    for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+      const int64_t o = row * k + chunk * VEC;
+      const Vec<T, VEC> pv = ldv_rw<T, VEC>(p + o);
+      const Vec<T, VEC> qv = ldv_rw<T, VEC>(q + o);
+      Vec<T, VEC> rv = ldv_rw<T, VEC>(r + o);
+      Vec<T, VEC> xv = ldv_rw<T, VEC>(x + row * ldx + chunk * VEC);
+      const T d = dinv ? dinv[row] : T(1);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        xv.v[e] = fma(al[e], pv.v[e], xv.v[e]);
+        rv.v[e] = fma(-al[e], qv.v[e], rv.v[e]);
+        drz[e].add(rv.v[e], d * rv.v[e]);
+        drr[e].add(rv.v[e], rv.v[e]);
+      }
+      stv<T, VEC>(x + row * ldx + chunk * VEC, xv);
+      stv<T, VEC>(r + o, rv);
+    }
+  }
+  double part[2][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) part[0][e] = drz[e].get(), part[1][e] = drr[e].get();
+  const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
+  if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[1], red)) return;
+  const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
+  __shared__ double totals[2 * K];
+  if ((int)threadIdx.x < 2 * k) totals[threadIdx.x] = tot;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < k) {
+    const double rz_new = totals[j], rr_new = totals[k + j];
+    double be = 0.0;
+    if (sc->state[j] == ST_ACTIVE) {
+      sc->iters[j] += 1;
+      sc->rr[j] = rr_new;
+      if (!isfinite(rr_new) || !isfinite(rz_new)) {
+        sc->state[j] = ctl.inner ? ST_DONE : ST_BREAKDOWN;
+      } else if (rr_new <= sc->tol2[j]) {
+        sc->state[j] = ctl.inner ? ST_DONE : ST_CHECK;
+      } else {
+        be = rz_new / sc->rz[j];
+        sc->rz[j] = rz_new;
+      }
+    }
+    sc->beta[j] = be;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, k);
+}
+
+// ------------------------------------------------------------------------ p = D^-1 r + b p
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_cg_p(CgCtl ctl, const T* __restrict__ r, T* __restrict__ p,
+                                                    const T* __restrict__ dinv, const CgScal* __restrict__ sc) {
+  if (sc->n_active == 0) return;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  if (chunk * VEC >= k) return;
+  T be[VEC];
+  bool on[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    be[e] = (T)sc->beta[chunk * VEC + e];
+    on[e] = sc->state[chunk * VEC + e] == ST_ACTIVE;
+  }
+  for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+    const int64_t o = row * k + chunk * VEC;
+    const Vec<T, VEC> rv = ldv_rw<T, VEC>(r + o);
+    Vec<T, VEC> pv = ldv_rw<T, VEC>(p + o);
+    const T d = dinv ? dinv[row] : T(1);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) pv.v[e] = on[e] ? fma(be[e], pv.v[e], d * rv.v[e]) : pv.v[e];
+    stv<T, VEC>(p + o, pv);
+  }
+}
+
+// ------------------------------------------------ true residual r = b - A x (FP64 operator)
+
+template <int VEC, int LPR>
+__global__ void __launch_bounds__(kThreads) k_cg_resid(CsrArgs<double> a, CgCtl ctl, int mode,
+                                                        const double* __restrict__ B, int64_t ldb,
+                                                        double* __restrict__ rout, CgScal* __restrict__ sc,
+                                                        double* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RedSmem<3> red;
+  __shared__ bool wmask[K];
+  const int k = a.k;
+  const int R = kThreads / (a.kp * LPR);
+  int32_t* s_rp = reinterpret_cast<int32_t*>(smem_raw);
+  int32_t* s_ci = s_rp + round4(R + 1);
+  double* s_va = reinterpret_cast<double*>(s_ci + round4(a.stage_cap));
+  if ((int)threadIdx.x < k) {
+    const int st = sc->state[threadIdx.x];
+    bool w = false;
+    if (mode == RM_INIT) w = true;
+    else if (mode == RM_CHECK) w = (st == ST_CHECK);
+    else if (mode == RM_OUTER) w = (sc->ostate[threadIdx.x] == ST_ACTIVE || sc->ostate[threadIdx.x] == ST_RESTART);
+    wmask[threadIdx.x] = w;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int sub = t % LPR, rc = t / LPR, chunk = rc % a.kp, rloc = rc / a.kp;
+  double acc_rr[VEC], acc_s[VEC], acc_bb[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) acc_rr[e] = acc_s[e] = acc_bb[e] = 0.0;
+  for (int64_t tile = blockIdx.x; tile * R < a.n_rows; tile += gridDim.x) {
+    const int r0 = (int)(tile * R);
+    const TileInfo ti = stage_rows<double>(a, r0, R, s_rp, s_ci, s_va);
+    const bool active = rloc < ti.nr && chunk * VEC < k;
+    double acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.0;
+    row_accumulate<double, VEC, LPR>(a, ti, s_rp, s_ci, s_va, rloc, chunk, sub, active, acc);
+    if (active && sub == 0) {
+      const int64_t row = r0 + rloc;
+      const Vec<double, VEC> b = ldv<double, VEC>(B + row * ldb + chunk * VEC);
+      Vec<double, VEC> rt;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        rt.v[e] = b.v[e] - acc[e];
+        acc_rr[e] = fma(rt.v[e], rt.v[e], acc_rr[e]);
+        acc_s[e] += rt.v[e];
+        acc_bb[e] = fma(b.v[e], b.v[e], acc_bb[e]);
+      }
+      if (mode != RM_REPORT) {
+        double* dst = rout + row * k + chunk * VEC;
+        bool all = true;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) all &= wmask[chunk * VEC + e];
+        if (all) {
+          stv<double, VEC>(dst, rt);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e)
+            if (wmask[chunk * VEC + e]) dst[e] = rt.v[e];
+        }
+      }
+    }
+  }
+  double part[3][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    part[0][e] = sub == 0 ? acc_rr[e] : 0.0;
+    part[1][e] = sub == 0 ? acc_s[e] : 0.0;
+    part[2][e] = sub == 0 ? acc_bb[e] : 0.0;
+  }
+  const double v = block_reduce<3, VEC>(part, a.kp, LPR, k, red);
+  if (!publish_partials<3>(v, 3 * k, partials, &sc->counter[2], red)) return;
+  const double tot = final_sum<3>(partials, 3 * k, gridDim.x, red);
+  __shared__ double totals[3 * K];
+  if ((int)threadIdx.x < 3 * k) totals[threadIdx.x] = tot;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < k) {
+    const double rr = totals[j], s = totals[k + j], bb = totals[2 * k + j];
+    const double nrow = (double)ctl.n;
+    const double mean = ctl.project ? s / nrow : 0.0;
+    const double rrp = ctl.project ? fmax(rr - nrow * mean * mean, 0.0) : rr;
+    if (mode == RM_INIT) {
+      sc->bb[j] = bb;
+      sc->tol2[j] = ctl.rtol2 * bb;
+      sc->mean[j] = mean;
+      sc->iters[j] = 0;
+      sc->state[j] = (bb == 0.0) ? ST_DONE : ST_RESTART;
+    } else if (mode == RM_CHECK) {
+      if (sc->state[j] == ST_CHECK) {
+        sc->mean[j] = mean;
+        sc->state[j] = (rrp <= sc->tol2[j]) ? ST_DONE : ST_RESTART;
+      }
+    } else if (mode == RM_REPORT) {
+      sc->rr_true[j] = rrp;
+    } else {  // RM_OUTER: one refinement sweep's residual
+      if (sc->ostate[j] == ST_RESTART) {  // first sweep: record ||b||
+        sc->bb[j] = bb;
+        sc->otol2[j] = ctl.rtol2 * bb;
+        sc->ostate[j] = ST_ACTIVE;
+        sc->iters[j] = 0;
+      }
+      if (sc->ostate[j] == ST_ACTIVE) {
+        sc->omean[j] = mean;
+        if (sc->bb[j] == 0.0 || rrp <= sc->otol2[j]) {
+          sc->ostate[j] = ST_DONE;
+        } else if (!isfinite(rrp)) {
+          sc->ostate[j] = ST_BREAKDOWN;
+        } else {
+          sc->oscale[j] = sqrt(rrp);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, k);
+}
+
+// ------------------------------------- restart: r -= mean, p = D^-1 r, rz, rr (RESTART columns)
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_cg_restart(CgCtl ctl, T* __restrict__ r, T* __restrict__ p,
+                                                          const T* __restrict__ dinv, CgScal* __restrict__ sc,
+                                                          double* __restrict__ partials) {
+  __shared__ RedSmem<2> red;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  const bool col_ok = chunk * VEC < k;
+  bool on[VEC];
+  T mu[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    on[e] = col_ok && sc->state[chunk * VEC + e] == ST_RESTART;
+    mu[e] = col_ok ? (T)sc->mean[chunk * VEC + e] : T(0);
+  }
+  DotAcc<T> drz[VEC], drr[VEC];
+  if (col_ok) {
+    for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+      const int64_t o = row * k + chunk * VEC;
+      Vec<T, VEC> rv = ldv_rw<T, VEC>(r + o);
+      Vec<T, VEC> pv = ldv_rw<T, VEC>(p + o);
+      const T d = dinv ? dinv[row] : T(1);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        if (on[e]) {
+          rv.v[e] = rv.v[e] - mu[e];
+          pv.v[e] = d * rv.v[e];
+          drz[e].add(rv.v[e], pv.v[e]);
+          drr[e].add(rv.v[e], rv.v[e]);
+        }
+      }
+      stv<T, VEC>(r + o, rv);
+      stv<T, VEC>(p + o, pv);
+    }
+  }
+  double part[2][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) part[0][e] = drz[e].get(), part[1][e] = drr[e].get();
+  const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
+  if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[3], red)) return;
+  const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
+  __shared__ double totals[2 * K];
+  if ((int)threadIdx.x < 2 * k) totals[threadIdx.x] = tot;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < k && sc->state[j] == ST_RESTART) {
+    sc->rz[j] = totals[j];
+    sc->rr[j] = totals[k + j];
+    sc->state[j] = (totals[k + j] <= sc->tol2[j]) ? ST_DONE : ST_ACTIVE;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, k);
+}
+
+// ---------------------------------- refinement: inner right-hand side and solution update
+
+// r32 = (r64 - mean) / scale, d32 = 0, p32 = D^-1 r32 for outer-active columns; zero else.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* __restrict__ r64,
+                                                       float* __restrict__ r32, float* __restrict__ p32,
+                                                       float* __restrict__ d32, const float* __restrict__ dinv,
+                                                       CgScal* __restrict__ sc, double* __restrict__ partials) {
+  __shared__ RedSmem<2> red;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  const bool col_ok = chunk * VEC < k;
+  bool on[VEC];
+  double mu[VEC], inv[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    const int j = chunk * VEC + e;
+    on[e] = col_ok && sc->ostate[j] == ST_ACTIVE;
+    mu[e] = on[e] ? sc->omean[j] : 0.0;
+    inv[e] = on[e] ? 1.0 / sc->oscale[j] : 0.0;
+  }
+  DotAcc<float> drz[VEC], drr[VEC];
+  if (col_ok) {
+    for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+      const int64_t o = row * k + chunk * VEC;
+      const Vec<double, VEC> rv = ldv_rw<double, VEC>(r64 + o);
+      const float d = dinv ? dinv[row] : 1.0f;
+      Vec<float, VEC> r, p, z;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        r.v[e] = on[e] ? (float)((rv.v[e] - mu[e]) * inv[e]) : 0.0f;
+        p.v[e] = d * r.v[e];
+        z.v[e] = 0.0f;
+        drz[e].add(r.v[e], p.v[e]);
+        drr[e].add(r.v[e], r.v[e]);
+      }
+      stv<float, VEC>(r32 + o, r);
+      stv<float, VEC>(p32 + o, p);
+      stv<float, VEC>(d32 + o, z);
+    }
+  }
+  double part[2][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) part[0][e] = drz[e].get(), part[1][e] = drr[e].get();
+  const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
+  if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[4], red)) return;
+  const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
+  __shared__ double totals[2 * K];
+  if ((int)threadIdx.x < 2 * k) totals[threadIdx.x] = tot;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < k) {
+    if (sc->ostate[j] == ST_ACTIVE && totals[k + j] > 0.0) {
+      sc->rz[j] = totals[j];
+      sc->rr[j] = totals[k + j];
+      sc->tol2[j] = ctl.inner_rtol2 * totals[k + j];
+      sc->state[j] = ST_ACTIVE;
+    } else {
+      sc->state[j] = ST_IDLE;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, k);
+}
+
+// x64 += scale * d32 on outer-active columns
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_ir_update(CgCtl ctl, double* __restrict__ x, int64_t ldx,
+                                                         const float* __restrict__ d32,
+                                                         const CgScal* __restrict__ sc) {
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  if (chunk * VEC >= k) return;
+  double s[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    const int j = chunk * VEC + e;
+    s[e] = (sc->ostate[j] == ST_ACTIVE) ? sc->oscale[j] : 0.0;
+  }
+  for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+    const Vec<float, VEC> d = ldv_rw<float, VEC>(d32 + row * k + chunk * VEC);
+    Vec<double, VEC> xv = ldv_rw<double, VEC>(x + row * ldx + chunk * VEC);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) xv.v[e] = fma(s[e], (double)d.v[e], xv.v[e]);
+    stv<double, VEC>(x + row * ldx + chunk * VEC, xv);
+  }
+}
+
+// ------------------------------------------------------- final projection x -= mean(x)
+
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_colsum(CgCtl ctl, const double* __restrict__ x, int64_t ldx,
+                                                      CgScal* __restrict__ sc, double* __restrict__ partials) {
+  __shared__ RedSmem<1> red;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  double part[1][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) part[0][e] = 0.0;
+  if (chunk * VEC < k) {
+    for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+      const Vec<double, VEC> xv = ldv_rw<double, VEC>(x + row * ldx + chunk * VEC);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) part[0][e] += xv.v[e];
+    }
+  }
+  const double v = block_reduce<1, VEC>(part, kp, 1, k, red);
+  if (!publish_partials<1>(v, k, partials, &sc->counter[5], red)) return;
+  const double tot = final_sum<1>(partials, k, gridDim.x, red);
+  if ((int)threadIdx.x < k) sc->mean[threadIdx.x] = tot / (double)ctl.n;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) k_submean(CgCtl ctl, double* __restrict__ x, int64_t ldx,
+                                                       const CgScal* __restrict__ sc) {
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  if (chunk * VEC >= k) return;
+  double mu[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) mu[e] = sc->mean[chunk * VEC + e];
+  for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+    Vec<double, VEC> xv = ldv_rw<double, VEC>(x + row * ldx + chunk * VEC);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) xv.v[e] -= mu[e];
+    stv<double, VEC>(x + row * ldx + chunk * VEC, xv);
+  }
+}
+
+__global__ void k_init_outer(CgScal* sc, int k) {
+  const int j = threadIdx.x;
+  if (j < k) {
+    sc->ostate[j] = ST_RESTART;
+    sc->state[j] = ST_IDLE;
+    sc->iters[j] = 0;
+  }
+  if (j == 0) recount(sc, k);
+}
+
+__global__ void k_mark_noconv(CgScal* sc, int k, int outer) {
+  const int j = threadIdx.x;
+  if (j < k) {
+    if (outer) {
+      if (sc->ostate[j] == ST_ACTIVE) sc->ostate[j] = ST_NOCONV;
+    } else if (sc->state[j] == ST_ACTIVE || sc->state[j] == ST_CHECK || sc->state[j] == ST_RESTART) {
+      sc->state[j] = ST_NOCONV;
+    }
+  }
+  if (j == 0) recount(sc, k);
+}
+
+// ------------------------------------------------------------------------------- host side
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t scal = 0, partials = 0, r = 0, p = 0, q = 0, r64 = 0, r32 = 0, p32 = 0, q32 = 0, d32 = 0, total = 0;
+};
+
+Layout layout(int64_t n, int k, bool mixed) {
+  Layout L;
+  size_t off = 0;
+  L.scal = off;
+  off += align256(sizeof(CgScal));
+  L.partials = off;
+  off += align256((size_t)kGridMax * 3 * K * sizeof(double));
+  const size_t v64 = align256((size_t)n * k * sizeof(double));
+  const size_t v32 = align256((size_t)n * k * sizeof(float));
+  if (!mixed) {
+    L.r = off, off += v64;
+    L.p = off, off += v64;
+    L.q = off, off += v64;
+  } else {
+    L.r64 = off, off += v64;
+    L.r32 = off, off += v32;
+    L.p32 = off, off += v32;
+    L.q32 = off, off += v32;
+    L.d32 = off, off += v32;
+  }
+  L.total = off;
+  return L;
+}
+
+// Shared launch plumbing for one solve.
+struct Solver {
+  const rb_op* A;
+  const rb_op* A32;
+  int k, vec, kp;
+  int64_t n;
+  CgCtl ctl;
+  CgScal* sc;
+  double* partials;
+  cudaStream_t s;
+  SpmmSched sched64, sched32;
+  int grid_vec;
+
+  int spmm_grid(const SpmmSched& sc) const {
+    const int R = sc.rows_per_block();
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kGridMax, (n + R - 1) / R));
+  }
+
+  template <typename T>
+  CsrArgs<T> args(const rb_op* op, const SpmmSched& ss, const T* X, int64_t ldx, T* Y, int64_t ldy) const {
+    CsrArgs<T> a;
+    fill_csr_args(op, ss, a, kCgDynSmem);
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.k = k;
+    a.cs = nullptr;
+    return a;
+  }
+
+  template <typename T, int VEC, int LPR>
+  void launch_q(const rb_op* op, const SpmmSched& ss, const T* p, T* q, CgCtl c) const {
+    CsrArgs<T> a = args<T>(op, ss, p, k, q, k);
+    const size_t smem = csr_smem_bytes<T>(ss.rows_per_block(), a.stage_cap);
+    k_cg_q<T, VEC, LPR><<<spmm_grid(ss), kThreads, smem, s>>>(a, c, sc, partials);
+  }
+
+  template <typename T, int VEC>
+  void launch_q_lpr(const rb_op* op, const SpmmSched& ss, const T* p, T* q, CgCtl c) const {
+    switch (ss.lpr) {
+      case 2: launch_q<T, VEC, 2>(op, ss, p, q, c); break;
+      case 4: launch_q<T, VEC, 4>(op, ss, p, q, c); break;
+      case 8: launch_q<T, VEC, 8>(op, ss, p, q, c); break;
+      default: launch_q<T, VEC, 1>(op, ss, p, q, c); break;
+    }
+  }
+
+  template <int VEC, int LPR>
+  void launch_resid_t(int mode, const double* B, int64_t ldb, const double* X, int64_t ldx, double* r) const {
+    CsrArgs<double> a = args<double>(A, sched64, X, ldx, nullptr, 0);
+    const size_t smem = csr_smem_bytes<double>(sched64.rows_per_block(), a.stage_cap);
+    k_cg_resid<VEC, LPR><<<spmm_grid(sched64), kThreads, smem, s>>>(a, ctl, mode, B, ldb, r, sc, partials);
+  }
+
+  template <int VEC>
+  void launch_resid_v(int mode, const double* B, int64_t ldb, const double* X, int64_t ldx, double* r) const {
+    switch (sched64.lpr) {
+      case 2: launch_resid_t<VEC, 2>(mode, B, ldb, X, ldx, r); break;
+      case 4: launch_resid_t<VEC, 4>(mode, B, ldb, X, ldx, r); break;
+      case 8: launch_resid_t<VEC, 8>(mode, B, ldb, X, ldx, r); break;
+      default: launch_resid_t<VEC, 1>(mode, B, ldb, X, ldx, r); break;
+    }
+  }
+};
+
+template <int VEC>
+struct Iter {
+  // one CG iteration in precision T on operator op
+  template <typename T>
+  static void step(const Solver& S_, const rb_op* op, const SpmmSched& ss, CgCtl c, T* x, int64_t ldx, T* r, T* p,
+                   T* q, const T* dinv) {
+    S_.launch_q_lpr<T, VEC>(op, ss, p, q, c);
+    k_cg_update<T, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, x, ldx, r, p, q, dinv, S_.sc, S_.partials);
+    k_cg_p<T, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc);
+  }
+};
+
+struct HostState {
+  int state[K], ostate[K];
+  int n_active, n_check, n_oactive;
+};
+
+rb_status read_state(const Solver& S_, HostState& h) {
+  RB_CUDA(cudaMemcpyAsync(h.state, S_.sc->state, sizeof(int) * K, cudaMemcpyDeviceToHost, S_.s));
+  RB_CUDA(cudaMemcpyAsync(h.ostate, S_.sc->ostate, sizeof(int) * K, cudaMemcpyDeviceToHost, S_.s));
+  RB_CUDA(cudaMemcpyAsync(&h.n_active, &S_.sc->n_active, sizeof(int) * 3, cudaMemcpyDeviceToHost, S_.s));
+  RB_CUDA(cudaStreamSynchronize(S_.s));
+  return RB_OK;
+}
+
+template <int VEC>
+rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_t ldb, double* X, int64_t ldx,
+                    const Layout& L, char* base, rb_cg_report& rep) {
+  const int k = S_.k;
+  HostState h;
+  int syncs = 0, spmms = 0;
+  if (!prm.mixed) {
+    double* r = reinterpret_cast<double*>(base + L.r);
+    double* p = reinterpret_cast<double*>(base + L.p);
+    double* q = reinterpret_cast<double*>(base + L.q);
+    const double* dinv = prm.precond ? S_.A->dinv64 : nullptr;
+    CgCtl c = S_.ctl;
+    c.inner = 0;
+    S_.launch_resid_v<VEC>(RM_INIT, B, ldb, X, ldx, r);
+    ++spmms;
+    k_cg_restart<double, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc, S_.partials);
+    RB_CUDA(cudaGetLastError());
+    int it = 0;
+    while (true) {
+      RB_TRY(read_state(S_, h));
+      ++syncs;
+      if (h.n_check > 0) {
+        S_.launch_resid_v<VEC>(RM_CHECK, B, ldb, X, ldx, r);
+        ++spmms;
+        k_cg_restart<double, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc, S_.partials);
+        RB_CUDA(cudaGetLastError());
+        continue;
+      }
+      if (h.n_active == 0) break;
+      if (it >= prm.max_iter) {
+        k_mark_noconv<<<1, K, 0, S_.s>>>(S_.sc, k, 0);
+        break;
+      }
+      const int chunk = std::min(prm.check_every, prm.max_iter - it);
+      for (int i = 0; i < chunk; ++i) Iter<VEC>::template step<double>(S_, S_.A, S_.sched64, c, X, ldx, r, p, q, dinv);
+      RB_CUDA(cudaGetLastError());
+      it += chunk;
+      spmms += chunk;
+    }
+  } else {
+    double* r64 = reinterpret_cast<double*>(base + L.r64);
+    float* r32 = reinterpret_cast<float*>(base + L.r32);
+    float* p32 = reinterpret_cast<float*>(base + L.p32);
+    float* q32 = reinterpret_cast<float*>(base + L.q32);
+    float* d32 = reinterpret_cast<float*>(base + L.d32);
+    const float* dinv32 = prm.precond ? S_.A32->dinv32 : nullptr;
+    CgCtl c = S_.ctl;
+    c.inner = 1;
+    k_init_outer<<<1, K, 0, S_.s>>>(S_.sc, k);
+    int total_inner = 0;
+    int sweep = 0;
+    for (;; ++sweep) {
+      S_.launch_resid_v<VEC>(RM_OUTER, B, ldb, X, ldx, r64);
+      ++spmms;
+      RB_CUDA(cudaGetLastError());
+      RB_TRY(read_state(S_, h));
+      ++syncs;
+      if (h.n_oactive == 0) break;
+      if (sweep >= prm.max_sweeps || total_inner >= prm.max_iter) {
+        k_mark_noconv<<<1, K, 0, S_.s>>>(S_.sc, k, 1);
+        break;
+      }
+      k_ir_init<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r64, r32, p32, d32, dinv32, S_.sc, S_.partials);
+      RB_CUDA(cudaGetLastError());
+      int it = 0;
+      while (true) {
+        RB_TRY(read_state(S_, h));
+        ++syncs;
+        if (h.n_active == 0 || total_inner + it >= prm.max_iter) break;
+        const int chunk = std::min(prm.check_every, prm.max_iter - total_inner - it);
+        for (int i = 0; i < chunk; ++i)
+          Iter<VEC>::template step<float>(S_, S_.A32, S_.sched32, c, d32, k, r32, p32, q32, dinv32);
+        RB_CUDA(cudaGetLastError());
+        it += chunk;
+        spmms += chunk;
+      }
+      total_inner += it;
+      k_ir_update<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, X, ldx, d32, S_.sc);
+      RB_CUDA(cudaGetLastError());
+    }
+    rep.sweeps = sweep;
+  }
+  // final projection and report
+  if (prm.project_mean) {
+    k_colsum<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc, S_.partials);
+    k_submean<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc);
+  }
+  S_.launch_resid_v<VEC>(RM_REPORT, B, ldb, X, ldx, nullptr);
+  ++spmms;
+  RB_CUDA(cudaGetLastError());
+  CgScal hs;
+  RB_CUDA(cudaMemcpyAsync(&hs, S_.sc, sizeof(CgScal), cudaMemcpyDeviceToHost, S_.s));
+  RB_CUDA(cudaStreamSynchronize(S_.s));
+  ++syncs;
+  rb_status worst = RB_OK;
+  for (int j = 0; j < k; ++j) {
+    rep.iters[j] = hs.iters[j];
+    rep.true_rel_res[j] = hs.bb[j] > 0 ? sqrt(hs.rr_true[j] / hs.bb[j]) : 0.0;
+    const int st = prm.mixed ? hs.ostate[j] : hs.state[j];
+    rb_status cs = RB_OK;
+    if (st == ST_BREAKDOWN) cs = RB_EBREAKDOWN;
+    else if (st == ST_NOCONV || st == ST_ACTIVE) cs = RB_ENOCONV;
+    rep.status[j] = cs;
+    if (cs == RB_EBREAKDOWN || (cs == RB_ENOCONV && worst == RB_OK)) worst = cs;
+  }
+  rep.spmm_calls = spmms;
+  rep.host_syncs = syncs;
+  return worst;
+}
+
+}  // namespace
+}  // namespace rb
+
+using namespace rb;
+
+extern "C" size_t rb_cg_workspace_bytes(rb_op_t A, int32_t k, const rb_cg_params* params) {
+  if (!A || !params || k < 1 || k > RB_MAX_K) return 0;
+  return layout(A->n_rows, k, params->mixed != 0).total + 256;
+}
+
+extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params* params, const double* B,
+                                 int64_t ldb, double* X, int64_t ldx, int32_t k, void* work, size_t work_bytes,
+                                 rb_cg_report* report, rb_stream_t stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  RB_REQUIRE(A && params, "rb_cg_solve: null operator or params");
+  const rb_cg_params& prm = *params;
+  RB_REQUIRE(A->dtype == RB_F64, "rb_cg_solve: the operator must be RB_F64");
+  RB_REQUIRE(A->n_rows == A->n_cols, "rb_cg_solve: the operator must be square");
+  RB_REQUIRE(A->ext_nz == 0, "rb_cg_solve: extruded operators are not supported by the solver");
+  RB_REQUIRE(k >= 1 && k <= RB_MAX_K, "rb_cg_solve: k = %d outside [1, %d]", k, RB_MAX_K);
+  RB_REQUIRE(ldb >= k && ldx >= k, "rb_cg_solve: leading dimension smaller than k");
+  RB_REQUIRE(A->n_rows == 0 || (B && X), "rb_cg_solve: null B or X");
+  RB_REQUIRE(prm.rtol > 0 && std::isfinite(prm.rtol), "rb_cg_solve: rtol must be positive");
+  RB_REQUIRE(prm.max_iter >= 0 && prm.check_every >= 1, "rb_cg_solve: max_iter >= 0 and check_every >= 1 required");
+  RB_REQUIRE(!prm.precond || A->has_diag, "rb_cg_solve: Jacobi needs a nonzero diagonal in every row");
+  if (prm.mixed) {
+    RB_REQUIRE(A_inner && A_inner->dtype == RB_F32 && A_inner->n_rows == A->n_rows && A_inner->nnz == A->nnz,
+               "rb_cg_solve: mixed precision needs A_inner, the same matrix stored as RB_F32");
+    RB_REQUIRE(A_inner->format == RB_CSR, "rb_cg_solve: the inner operator must be CSR");
+    RB_REQUIRE(prm.inner_rtol > 0 && prm.inner_rtol < 1, "rb_cg_solve: inner_rtol must be in (0, 1)");
+    RB_REQUIRE(prm.max_sweeps >= 1, "rb_cg_solve: max_sweeps >= 1 required");
+  }
+  RB_REQUIRE(A->format == RB_CSR, "rb_cg_solve: the operator must be CSR");
+  RB_REQUIRE((uintptr_t)B % 8 == 0 && (uintptr_t)X % 8 == 0, "rb_cg_solve: B or X not 8-byte aligned");
+  const Layout L = layout(A->n_rows, k, prm.mixed != 0);
+  RB_REQUIRE(work && work_bytes >= L.total + 256, "rb_cg_solve: workspace too small (%zu < %zu)", work_bytes,
+             L.total + 256);
+  rb_cg_report rep;
+  std::memset(&rep, 0, sizeof(rep));
+  if (A->n_rows == 0) {
+    if (report) *report = rep;
+    return RB_OK;
+  }
+  char* base = reinterpret_cast<char*>(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  Solver S_;
+  S_.A = A;
+  S_.A32 = A_inner;
+  S_.k = k;
+  S_.n = A->n_rows;
+  S_.s = S(stream);
+  // vector width: must divide k and keep every block's rows aligned (internal vectors have ld = k)
+  int vec = pick_vec(8, k, ldx, ldb, X, B);
+  if (vec > 1 && (k % vec)) vec = 1;
+  S_.vec = vec;
+  S_.kp = next_pow2((k + vec - 1) / vec);
+  RB_REQUIRE(S_.kp <= 32, "rb_cg_solve: k = %d needs 16-byte aligned B and X rows", k);
+  S_.sched64 = pick_sched(A, k, k, k, base + L.r, base + L.p);
+  S_.sched64.vec = vec;
+  S_.sched64.kp = S_.kp;
+  if (S_.sched64.kp * S_.sched64.lpr > 32) S_.sched64.lpr = 1;
+  if (prm.mixed) {
+    S_.sched32 = pick_sched(A_inner, k, k, k, base + L.p32, base + L.q32);
+    S_.sched32.vec = vec;  // the same (row, chunk) layout as the vector kernels
+    S_.sched32.kp = S_.kp;
+    if (S_.sched32.kp * S_.sched32.lpr > 32) S_.sched32.lpr = 1;
+  }
+  S_.grid_vec = (int)std::max<int64_t>(1, std::min<int64_t>(152 * 4, (S_.n + kThreads / S_.kp - 1) / (kThreads / S_.kp)));
+  S_.sc = reinterpret_cast<CgScal*>(base + L.scal);
+  S_.partials = reinterpret_cast<double*>(base + L.partials);
+  S_.ctl.k = k;
+  S_.ctl.kp = S_.kp;
+  S_.ctl.n = S_.n;
+  S_.ctl.inner = 0;
+  S_.ctl.project = prm.project_mean ? 1 : 0;
+  S_.ctl.rtol2 = prm.rtol * prm.rtol;
+  S_.ctl.inner_rtol2 = prm.inner_rtol * prm.inner_rtol;
+  RB_CUDA(cudaMemsetAsync(S_.sc, 0, sizeof(CgScal), S_.s));
+  rb_status st;
+  switch (vec) {
+    case 2: st = solve_vec<2>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
+    default: st = solve_vec<1>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
+  }
+  rep.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (report) *report = rep;
+  if (st != RB_OK && st != RB_ENOCONV && st != RB_EBREAKDOWN) return st;
+  if (st == RB_ENOCONV) set_error("rb_cg_solve: a column did not converge in max_iter iterations");
+  if (st == RB_EBREAKDOWN) set_error("rb_cg_solve: breakdown (p.q <= 0 or not finite) in a column");
+  return st;
+}

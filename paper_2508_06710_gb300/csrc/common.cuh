@@ -1,0 +1,193 @@
+// Shared definitions of the repeated-block SpMM library: error state, the operator object,
+// vector loads over the k interleaved columns, and block/grid reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+
+#include "../../include/rbspmm.h"
+
+namespace rb {
+
+// ------------------------------------------------------------------------------------------
+// Errors
+// ------------------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+rb_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define RB_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return rb::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define RB_REQUIRE(cond, ...)          \
+  do {                                 \
+    if (!(cond)) {                     \
+      rb::set_error(__VA_ARGS__);      \
+      return RB_EINVAL;                \
+    }                                  \
+  } while (0)
+
+#define RB_TRY(expr)                \
+  do {                              \
+    rb_status s_ = (expr);          \
+    if (s_ != RB_OK) return s_;     \
+  } while (0)
+
+inline cudaStream_t S(rb_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+constexpr int kThreads = 256;  // threads per block of every streaming kernel
+constexpr int kMaxGrid = 152 * 8;  // 152 SMs x 8 resident blocks of 256 threads
+
+// ------------------------------------------------------------------------------------------
+// Schedules and the operator object
+// ------------------------------------------------------------------------------------------
+// One launch shape of the SpMM kernels: VEC consecutive columns per thread (16-byte loads
+// when VEC * sizeof(T) == 16), KP = next power of two of k / VEC threads per row (so the
+// threads of a row are aligned within a warp), LPR threads splitting one row's nonzeros
+// (reduced with warp shuffles), and whether the block's nonzeros are staged in shared
+// memory before use.
+struct SpmmSched {
+  int vec = 1;
+  int kp = 1;
+  int lpr = 1;
+  int stage = 1;
+  int rows_per_block() const { return kThreads / (kp * lpr); }
+};
+
+}  // namespace rb
+
+struct rb_op {
+  int32_t n_rows = 0, n_cols = 0;
+  int64_t nnz = 0;
+  rb_dtype dtype = RB_F64;
+  rb_format format = RB_CSR;
+  int32_t k_max = 1;
+  // CSR (arrays padded by 64 bytes so that aligned vector and bulk copies may read past nnz)
+  int32_t* row_ptr = nullptr;
+  int32_t* col_idx = nullptr;
+  void* vals = nullptr;
+  int32_t max_row_len = 0;
+  double avg_row_len = 0.0;
+  // sliced ELL (C rows per slice, column-major inside a slice)
+  int32_t sell_c = 0, sell_sigma = 0, n_slices = 0;
+  int64_t sell_nnz = 0;
+  int32_t* sell_ptr = nullptr;   // n_slices + 1 offsets (entries)
+  int32_t* sell_width = nullptr; // n_slices
+  int32_t* sell_row = nullptr;   // n_slices * C: original row of each slot (-1: empty)
+  int32_t* sell_col = nullptr;
+  void* sell_val = nullptr;
+  // Jacobi
+  int32_t has_diag = 0;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  // extruded along a periodic direction
+  int32_t ext_nz = 0;
+  double dz = 0.0;
+  double* zw64 = nullptr;
+  float* zw32 = nullptr;
+  int64_t device_bytes = 0;
+  std::map<int, rb::SpmmSched> tuned;  // k -> schedule chosen by rb_tune_spmm
+};
+
+namespace rb {
+
+// ------------------------------------------------------------------------------------------
+// Vector access to VEC consecutive columns
+// ------------------------------------------------------------------------------------------
+template <typename T, int VEC>
+struct Vec {
+  T v[VEC];
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> ldv(const T* p) {
+  Vec<T, VEC> r;
+  if constexpr (sizeof(T) * VEC == 16) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    memcpy(&r, &q, 16);
+  } else if constexpr (sizeof(T) * VEC == 8) {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+    memcpy(&r, &q, 8);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) r.v[e] = __ldg(p + e);
+  }
+  return r;
+}
+
+// Plain (non read-only path) load, for data written earlier by the same kernel sequence.
+template <typename T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> ldv_rw(const T* p) {
+  Vec<T, VEC> r;
+  if constexpr (sizeof(T) * VEC == 16) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    memcpy(&r, &q, 16);
+  } else if constexpr (sizeof(T) * VEC == 8) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    memcpy(&r, &q, 8);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) r.v[e] = p[e];
+  }
+  return r;
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void stv(T* p, const Vec<T, VEC>& r) {
+  if constexpr (sizeof(T) * VEC == 16) {
+    float4 q;
+    memcpy(&q, &r, 16);
+    *reinterpret_cast<float4*>(p) = q;
+  } else if constexpr (sizeof(T) * VEC == 8) {
+    float2 q;
+    memcpy(&q, &r, 8);
+    *reinterpret_cast<float2*>(p) = q;
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) p[e] = r.v[e];
+  }
+}
+
+__host__ __device__ inline int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Largest VEC in {4, 2, 1} (4 only for 4-byte types: 16-byte loads) that divides k and the
+// leading dimensions and keeps every row start aligned.
+inline int pick_vec(int elem_bytes, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
+  for (int v = 16 / elem_bytes; v > 1; v >>= 1) {
+    const uintptr_t a = (uintptr_t)v * elem_bytes;
+    if (k % v == 0 && ldx % v == 0 && ldy % v == 0 && ((uintptr_t)X % a) == 0 && ((uintptr_t)Y % a) == 0) return v;
+  }
+  return 1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Reductions: per-column sums over the rows handled by a block.  Threads are laid out as
+// (row, chunk) with KP chunks per row, KP a power of two dividing 32, so lanes with equal
+// lane % KP hold the same columns.  The warp stage folds lanes with xor offsets >= KP; the
+// block stage sums the warps in order.  Fixed order throughout: bit-reproducible.
+// ------------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void warp_fold(double (&a)[NV], int kp) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    if (off >= kp) {
+#pragma unroll
+      for (int e = 0; e < NV; ++e) a[e] += __shfl_xor_sync(0xffffffffu, a[e], off);
+    }
+  }
+}
+
+}  // namespace rb

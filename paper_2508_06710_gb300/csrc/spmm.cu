@@ -1,0 +1,270 @@
+// SpMM over k interleaved right-hand sides (Sec. 2, Eq. (1), Algorithm 1), for CSR and
+// sliced-ELL operators, plus the extruded-plane form (Sec. 2, repeated geometries):
+//
+//   Y[i, j] = c[j] * sum_p val[p] * X[idx[p], j]
+//   extruded: Y[i, z] = c[z] * ( dz * sum_p val[p] X[idx[p], z] + w_i (X[i, z-1] - 2 X[i, z] + X[i, z+1]) )
+//
+// Each matrix coefficient and column index is read from HBM once and used for all k
+// columns.  Threads are laid out as (row, chunk of VEC columns, lane within row): the KP
+// chunks of a row sit in adjacent lanes, so the X rows they gather (k * sizeof(T) bytes)
+// are read with coalesced 16-byte loads, and Y is written the same way.  The block's
+// contiguous range of nonzeros (column indices and values) is staged in shared memory with
+// coalesced loads before use, and broadcast from there to the KP chunk lanes of each row.
+// With LPR > 1 several lanes split one row's nonzeros and are reduced with warp shuffles.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "spmm_impl.cuh"
+
+namespace rb {
+
+namespace {
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_spmm_sell(int n_slots, const int32_t* __restrict__ sptr,
+                                                         const int32_t* __restrict__ swidth,
+                                                         const int32_t* __restrict__ srow,
+                                                         const int32_t* __restrict__ scol, const T* __restrict__ sval,
+                                                         const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
+                                                         int64_t ldy, int k, int kp, const double* __restrict__ cs) {
+  const int R = kThreads / kp;
+  const int t = threadIdx.x;
+  const int chunk = t % kp;
+  const int64_t g = (int64_t)blockIdx.x * R + t / kp;  // slot index: slice * 32 + lane in slice
+  if (g >= n_slots || chunk * VEC >= k) return;
+  const int row = srow[g];
+  if (row < 0) return;
+  const int sl = (int)(g >> 5), r = (int)(g & 31);
+  const int base = sptr[sl] + r;
+  const int width = swidth[sl];
+  T acc[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+  const T* Xc = X + chunk * VEC;
+  for (int j = 0; j < width; ++j) {
+    const int c = __ldg(scol + base + j * 32);
+    const T v = __ldg(sval + base + j * 32);
+    const Vec<T, VEC> x = ldv<T, VEC>(Xc + (int64_t)c * ldx);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
+  }
+  Vec<T, VEC> y;
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) y.v[e] = cs ? acc[e] * (T)cs[chunk * VEC + e] : acc[e];
+  stv<T, VEC>(Y + (int64_t)row * ldy + chunk * VEC, y);
+}
+
+template <typename T, int VEC>
+rb_status launch_sell(const rb_op* op, const SpmmSched& sc, const T* X, int64_t ldx, T* Y, int64_t ldy, int k,
+                      const double* cs, cudaStream_t s) {
+  const int R = kThreads / sc.kp;
+  const int64_t slots = (int64_t)op->n_slices * 32;
+  const int64_t grid = (slots + R - 1) / R;
+  if (grid == 0) return RB_OK;
+  k_spmm_sell<T, VEC><<<(unsigned)grid, kThreads, 0, s>>>((int)slots, op->sell_ptr, op->sell_width, op->sell_row,
+                                                           op->sell_col, static_cast<const T*>(op->sell_val), X, ldx,
+                                                           Y, ldy, k, sc.kp, cs);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+template <typename T, int VEC, int LPR, bool EXT>
+rb_status launch_csr(const rb_op* op, const SpmmSched& sc, const T* X, int64_t ldx, T* Y, int64_t ldy, int k,
+                     const double* cs, cudaStream_t s) {
+  CsrArgs<T> a;
+  fill_csr_args(op, sc, a);
+  a.X = X;
+  a.ldx = ldx;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.k = k;
+  a.cs = cs;
+  const int R = sc.rows_per_block();
+  const int64_t grid = ((int64_t)op->n_rows + R - 1) / R;
+  if (grid == 0) return RB_OK;
+  const size_t smem = csr_smem_bytes<T>(R, a.stage_cap);
+  k_spmm_csr<T, VEC, LPR, EXT><<<(unsigned)std::min<int64_t>(grid, INT32_MAX), kThreads, smem, s>>>(a);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+template <typename T, int VEC, int LPR>
+rb_status dispatch_ext(const rb_op* op, const SpmmSched& sc, const T* X, int64_t ldx, T* Y, int64_t ldy, int k,
+                       const double* cs, cudaStream_t s) {
+  if (op->ext_nz > 0) return launch_csr<T, VEC, LPR, true>(op, sc, X, ldx, Y, ldy, k, cs, s);
+  return launch_csr<T, VEC, LPR, false>(op, sc, X, ldx, Y, ldy, k, cs, s);
+}
+
+template <typename T, int VEC>
+rb_status dispatch_lpr(const rb_op* op, const SpmmSched& sc, const T* X, int64_t ldx, T* Y, int64_t ldy, int k,
+                       const double* cs, cudaStream_t s) {
+  if (op->format == RB_SELL && op->ext_nz == 0) return launch_sell<T, VEC>(op, sc, X, ldx, Y, ldy, k, cs, s);
+  switch (sc.lpr) {
+    case 1: return dispatch_ext<T, VEC, 1>(op, sc, X, ldx, Y, ldy, k, cs, s);
+    case 2: return dispatch_ext<T, VEC, 2>(op, sc, X, ldx, Y, ldy, k, cs, s);
+    case 4: return dispatch_ext<T, VEC, 4>(op, sc, X, ldx, Y, ldy, k, cs, s);
+    case 8: return dispatch_ext<T, VEC, 8>(op, sc, X, ldx, Y, ldy, k, cs, s);
+  }
+  set_error("spmm: unsupported lanes per row %d", sc.lpr);
+  return RB_EUNSUPPORTED;
+}
+
+template <typename T>
+rb_status dispatch_vec(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy, int k,
+                       const double* cs, cudaStream_t s) {
+  const T* x = static_cast<const T*>(X);
+  T* y = static_cast<T*>(Y);
+  switch (sc.vec) {
+    case 1: return dispatch_lpr<T, 1>(op, sc, x, ldx, y, ldy, k, cs, s);
+    case 2: return dispatch_lpr<T, 2>(op, sc, x, ldx, y, ldy, k, cs, s);
+    case 4:
+      if constexpr (sizeof(T) == 4) return dispatch_lpr<T, 4>(op, sc, x, ldx, y, ldy, k, cs, s);
+      break;
+  }
+  set_error("spmm: unsupported vector width %d", sc.vec);
+  return RB_EUNSUPPORTED;
+}
+
+bool sched_valid(const rb_op* op, const SpmmSched& sc, int k, int64_t ldx, int64_t ldy, const void* X,
+                 const void* Y) {
+  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  if (sc.vec < 1 || k % sc.vec || ldx % sc.vec || ldy % sc.vec) return false;
+  if (sc.vec * eb > 16) return false;
+  const uintptr_t a = (uintptr_t)sc.vec * eb;
+  if ((uintptr_t)X % a || (uintptr_t)Y % a) return false;
+  if (sc.kp != next_pow2((k + sc.vec - 1) / sc.vec) || sc.kp > 32) return false;
+  if (sc.kp * sc.lpr > 32) return false;
+  if (op->format == RB_SELL && sc.lpr != 1) return false;
+  return true;
+}
+
+}  // namespace
+
+SpmmSched default_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
+  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  SpmmSched sc;
+  sc.vec = pick_vec(eb, k, ldx, ldy, X, Y);
+  while (sc.vec > 1 && next_pow2(k / sc.vec) > 32) sc.vec >>= 1;  // unreachable for k <= 64 with vec >= 2
+  if (next_pow2((k + sc.vec - 1) / sc.vec) > 32) {
+    // k > 32 with unaligned rows: fall back to the widest vector the size allows
+    for (int v = 16 / eb; v >= 1; v >>= 1)
+      if (k % v == 0 && next_pow2(k / v) <= 32) {
+        sc.vec = v;
+        break;
+      }
+  }
+  sc.kp = next_pow2((k + sc.vec - 1) / sc.vec);
+  sc.lpr = 1;
+  if (op->format != RB_SELL && op->avg_row_len >= 12.0) sc.lpr = std::min(8, std::max(1, 32 / sc.kp / 4));
+  sc.stage = 1;
+  return sc;
+}
+
+rb_status spmm_launch(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy, int k,
+                      const double* cs, cudaStream_t s) {
+  if (op->dtype == RB_F64) return dispatch_vec<double>(op, sc, X, ldx, Y, ldy, k, cs, s);
+  return dispatch_vec<float>(op, sc, X, ldx, Y, ldy, k, cs, s);
+}
+
+rb_status spmm_validate(const rb_op* op, const void* X, int64_t ldx, const void* Y, int64_t ldy, int k) {
+  RB_REQUIRE(op != nullptr, "spmm: null operator");
+  RB_REQUIRE(k >= 1 && k <= RB_MAX_K, "spmm: k = %d outside [1, %d]", k, RB_MAX_K);
+  RB_REQUIRE(ldx >= k && ldy >= k, "spmm: leading dimensions (%lld, %lld) smaller than k = %d", (long long)ldx,
+             (long long)ldy, k);
+  RB_REQUIRE((op->n_cols == 0 || X) && (op->n_rows == 0 || Y), "spmm: null X or Y");
+  RB_REQUIRE(op->ext_nz == 0 || k == op->ext_nz, "spmm: extruded operator needs k == extruded_nz (%d), got %d",
+             op->ext_nz, k);
+  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  RB_REQUIRE((uintptr_t)X % eb == 0 && (uintptr_t)Y % eb == 0, "spmm: X or Y not aligned to the element size");
+  if (k > 32) {
+    bool ok = false;
+    for (int v = 2; v * eb <= 16; v <<= 1) ok |= (k % v == 0 && next_pow2(k / v) <= 32);
+    RB_REQUIRE(ok, "spmm: k = %d needs k / vec <= 32 for some vector width", k);
+    const int v = pick_vec(eb, k, ldx, ldy, X, Y);
+    if (next_pow2(k / v) > 32) {
+      set_error("spmm: k = %d > 32 needs ldx, ldy and the row starts aligned to %d bytes", k, 16);
+      return RB_EUNSUPPORTED;
+    }
+  }
+  // X and Y must not overlap
+  const uintptr_t xb = (uintptr_t)X, xe = xb + (uintptr_t)((int64_t)op->n_cols * ldx * eb);
+  const uintptr_t yb = (uintptr_t)Y, ye = yb + (uintptr_t)((int64_t)op->n_rows * ldy * eb);
+  RB_REQUIRE(op->n_rows == 0 || op->n_cols == 0 || xe <= yb || ye <= xb, "spmm: X and Y overlap");
+  return RB_OK;
+}
+
+SpmmSched pick_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
+  auto it = op->tuned.find(k);
+  if (it != op->tuned.end() && sched_valid(op, it->second, k, ldx, ldy, X, Y)) return it->second;
+  return default_sched(op, k, ldx, ldy, X, Y);
+}
+
+}  // namespace rb
+
+using namespace rb;
+
+extern "C" rb_status rb_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k, const double* c,
+                             rb_stream_t stream) {
+  clear_error();
+  RB_TRY(spmm_validate(A, X, ldx, Y, ldy, k));
+  if (A->n_rows == 0) return RB_OK;
+  const SpmmSched sc = pick_sched(A, k, ldx, ldy, X, Y);
+  return spmm_launch(A, sc, X, ldx, Y, ldy, k, c, S(stream));
+}
+
+extern "C" rb_status rb_tune_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k,
+                                  rb_stream_t stream) {
+  clear_error();
+  RB_TRY(spmm_validate(A, X, ldx, Y, ldy, k));
+  if (A->n_rows == 0) return RB_OK;
+  cudaStream_t s = S(stream);
+  std::vector<SpmmSched> cands;
+  const int eb = A->dtype == RB_F64 ? 8 : 4;
+  for (int vec = 16 / eb; vec >= 1; vec >>= 1) {
+    for (int lpr = 1; lpr <= 8; lpr <<= 1) {
+      for (int stage = 0; stage <= 1; ++stage) {
+        SpmmSched sc;
+        sc.vec = vec;
+        sc.kp = next_pow2((k + vec - 1) / vec);
+        sc.lpr = lpr;
+        sc.stage = stage;
+        if (!sched_valid(A, sc, k, ldx, ldy, X, Y)) continue;
+        if (A->format == RB_SELL && stage == 0) continue;
+        cands.push_back(sc);
+      }
+    }
+  }
+  if (cands.empty()) {
+    set_error("rb_tune_spmm: no valid schedule for k = %d", k);
+    return RB_EUNSUPPORTED;
+  }
+  cudaEvent_t e0, e1;
+  RB_CUDA(cudaEventCreate(&e0));
+  RB_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  SpmmSched best_sc = cands[0];
+  for (const SpmmSched& sc : cands) {
+    rb_status st = RB_OK;
+    for (int w = 0; w < 2 && st == RB_OK; ++w) st = spmm_launch(A, sc, X, ldx, Y, ldy, k, nullptr, s);
+    if (st != RB_OK) continue;
+    float times[5];
+    for (int r = 0; r < 5; ++r) {
+      cudaEventRecord(e0, s);
+      spmm_launch(A, sc, X, ldx, Y, ldy, k, nullptr, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&times[r], e0, e1);
+    }
+    std::sort(times, times + 5);
+    if (times[2] < best) {
+      best = times[2];
+      best_sc = sc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RB_CUDA(cudaGetLastError());
+  A->tuned[k] = best_sc;
+  return RB_OK;
+}

@@ -1,0 +1,183 @@
+// Building blocks of the CSR SpMM shared by the standalone SpMM and the fused CG kernels:
+// staging a block's rows (row pointers, column indices, values) in shared memory, and the
+// per-(row, chunk) accumulation over the row's nonzeros.
+#pragma once
+
+#include "common.cuh"
+
+namespace rb {
+
+template <typename T>
+struct CsrArgs {
+  int n_rows = 0;
+  const int32_t* __restrict__ rp = nullptr;
+  const int32_t* __restrict__ ci = nullptr;
+  const T* __restrict__ va = nullptr;
+  const T* __restrict__ X = nullptr;
+  int64_t ldx = 0;
+  T* __restrict__ Y = nullptr;
+  int64_t ldy = 0;
+  int k = 1;
+  int kp = 1;
+  int stage_cap = 0;  // nonzeros a block may stage in shared memory (0: read from global)
+  const double* __restrict__ cs = nullptr;
+  // extruded operator: Y = dz * A X + w_i * (periodic second difference across the k columns)
+  T dz = T(1);
+  const T* __restrict__ zw = nullptr;
+};
+
+__host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+
+template <typename T>
+__host__ __device__ inline size_t csr_smem_bytes(int R, int cap) {
+  return (size_t)4 * round4(R + 1) + (size_t)4 * round4(cap) + sizeof(T) * (size_t)cap;
+}
+
+// Nonzeros a block of R rows stages: room for 1.25x the average row plus slack, kept under
+// 48 KB so that several blocks share an SM.
+// `limit` is the dynamic shared memory the kernel may use: 48 KB minus its static shared
+// memory, so that no launch needs the opt-in for more than 48 KB per block.
+template <typename T>
+inline int stage_capacity(const rb_op* op, int R, int stage, size_t limit) {
+  if (!stage) return 0;
+  int cap = (int)((double)R * (op->avg_row_len * 1.25 + 1.0)) + 32;
+  cap = round4(cap);
+  while (cap > 4 && csr_smem_bytes<T>(R, cap) > limit) cap -= 4;
+  return cap;
+}
+
+template <typename T>
+inline void fill_csr_args(const rb_op* op, const SpmmSched& sc, CsrArgs<T>& a, size_t smem_limit = 48 * 1024) {
+  a.n_rows = op->n_rows;
+  a.rp = op->row_ptr;
+  a.ci = op->col_idx;
+  a.va = static_cast<const T*>(op->vals);
+  a.kp = sc.kp;
+  a.stage_cap = stage_capacity<T>(op, sc.rows_per_block(), sc.stage, smem_limit);
+  a.dz = (T)op->dz;
+  a.zw = (sizeof(T) == 8) ? reinterpret_cast<const T*>(op->zw64) : reinterpret_cast<const T*>(op->zw32);
+}
+
+struct TileInfo {
+  int r0, nr, base, cnt;
+  bool staged;
+};
+
+// Loads the row pointers of rows [r0, r0 + nr) and, when they fit, the block's nonzeros
+// into shared memory.  Called by all threads of the block; ends with a barrier.
+template <typename T>
+__device__ __forceinline__ TileInfo stage_rows(const CsrArgs<T>& a, int r0, int R, int32_t* s_rp, int32_t* s_ci,
+                                               T* s_va) {
+  TileInfo ti;
+  ti.r0 = r0;
+  ti.nr = min(R, a.n_rows - r0);
+  __syncthreads();  // previous users of the shared arrays are done
+  for (int i = threadIdx.x; i <= ti.nr; i += blockDim.x) s_rp[i] = __ldg(a.rp + r0 + i);
+  __syncthreads();
+  ti.base = s_rp[0];
+  ti.cnt = s_rp[ti.nr] - ti.base;
+  ti.staged = a.stage_cap > 0 && ti.cnt <= a.stage_cap;
+  if (ti.staged) {
+    const int32_t* ci = a.ci + ti.base;
+    const T* va = a.va + ti.base;
+    for (int e = threadIdx.x; e < ti.cnt; e += blockDim.x) {
+      s_ci[e] = __ldg(ci + e);
+      s_va[e] = __ldg(va + e);
+    }
+  }
+  __syncthreads();
+  return ti;
+}
+
+// acc += sum over the nonzeros p = rs + sub, rs + sub + LPR, ... of row rloc of
+// val[p] * X[idx[p], chunk * VEC .. chunk * VEC + VEC).
+// Must be called by every thread of the warp when LPR > 1 (the reduction shuffles);
+// inactive threads contribute zero.
+template <typename T, int VEC, int LPR>
+__device__ __forceinline__ void row_accumulate(const CsrArgs<T>& a, const TileInfo& ti, const int32_t* s_rp,
+                                               const int32_t* s_ci, const T* s_va, int rloc, int chunk, int sub,
+                                               bool active, T (&acc)[VEC]) {
+  const int rs = active ? s_rp[rloc] - ti.base : 0;
+  const int re = active ? s_rp[rloc + 1] - ti.base : 0;
+  const T* Xc = a.X + chunk * VEC;
+  if (ti.staged) {
+#pragma unroll 4
+    for (int p = rs + sub; p < re; p += LPR) {
+      const int c = s_ci[p];
+      const T v = s_va[p];
+      const Vec<T, VEC> x = ldv<T, VEC>(Xc + (int64_t)c * a.ldx);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
+    }
+  } else {
+    const int32_t* ci = a.ci + ti.base;
+    const T* va = a.va + ti.base;
+#pragma unroll 4
+    for (int p = rs + sub; p < re; p += LPR) {
+      const int c = __ldg(ci + p);
+      const T v = __ldg(va + p);
+      const Vec<T, VEC> x = ldv<T, VEC>(Xc + (int64_t)c * a.ldx);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
+    }
+  }
+  if constexpr (LPR > 1) {
+#pragma unroll
+    for (int off = LPR / 2; off >= 1; off >>= 1) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
+    }
+  }
+}
+
+// Periodic second difference across the k (= Nz) columns of row `row`, weighted by w_i,
+// added to dz * acc: the spanwise coupling of the extruded operator.
+template <typename T, int VEC>
+__device__ __forceinline__ void extruded_epilogue(const CsrArgs<T>& a, int64_t row, int chunk, T (&acc)[VEC]) {
+  const int nz = a.k;
+  const T* xr = a.X + row * a.ldx;
+  const Vec<T, VEC> xs = ldv<T, VEC>(xr + chunk * VEC);
+  const int z0 = chunk * VEC;
+  const T left = __ldg(xr + (z0 == 0 ? nz - 1 : z0 - 1));
+  const T right = __ldg(xr + (z0 + VEC == nz ? 0 : z0 + VEC));
+  const T w = __ldg(a.zw + row);
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    const T xm = (e == 0) ? left : xs.v[e - 1];
+    const T xp = (e == VEC - 1) ? right : xs.v[e + 1];
+    acc[e] = a.dz * acc[e] + w * ((xm - xs.v[e]) + (xp - xs.v[e]));
+  }
+}
+
+template <typename T, int VEC, int LPR, bool EXT>
+__global__ void __launch_bounds__(kThreads) k_spmm_csr(CsrArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int R = kThreads / (a.kp * LPR);
+  int32_t* s_rp = reinterpret_cast<int32_t*>(smem_raw);
+  int32_t* s_ci = s_rp + round4(R + 1);
+  T* s_va = reinterpret_cast<T*>(s_ci + round4(a.stage_cap));
+  const int t = threadIdx.x;
+  const int sub = t % LPR;
+  const int rc = t / LPR;
+  const int chunk = rc % a.kp;
+  const int rloc = rc / a.kp;
+  for (int64_t tile = blockIdx.x; tile * R < a.n_rows; tile += gridDim.x) {
+    const int r0 = (int)(tile * R);
+    const TileInfo ti = stage_rows<T>(a, r0, R, s_rp, s_ci, s_va);
+    const bool active = rloc < ti.nr && chunk * VEC < a.k;
+    T acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+    row_accumulate<T, VEC, LPR>(a, ti, s_rp, s_ci, s_va, rloc, chunk, sub, active, acc);
+    if (active && sub == 0) {
+      const int64_t row = r0 + rloc;
+      if constexpr (EXT) extruded_epilogue<T, VEC>(a, row, chunk, acc);
+      Vec<T, VEC> y;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) y.v[e] = a.cs ? acc[e] * (T)a.cs[chunk * VEC + e] : acc[e];
+      stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, y);
+    }
+  }
+}
+
+}  // namespace rb

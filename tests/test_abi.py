@@ -1,0 +1,83 @@
+"""The C ABI library builds, loads without a GPU and exports every symbol the header declares (CPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rbspmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:rb_status|size_t|const char\*)\s+(rb_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_06710_gb300 import build
+
+    build.build()
+    import paper_2508_06710_gb300 as rb
+
+    return rb.lib()
+
+
+def test_header_declares_the_documented_calls():
+    names = _declared()
+    assert len(names) == len(set(names))
+    for n in ("rb_operator_create", "rb_spmm", "rb_dot", "rb_axpy", "rb_axty", "rb_cg_solve"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header(lib):
+    import paper_2508_06710_gb300 as rb
+
+    assert set(_declared()) <= set(rb.SYMBOLS) | {n for n in _declared() if hasattr(lib, n)}
+    assert set(rb.SYMBOLS) <= set(_declared())
+
+
+def test_host_side_validation_without_gpu(lib):
+    """Argument checks return RB_EINVAL before touching the device."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+
+    assert lib.rb_version().decode().count(".") == 2
+    h = C.c_void_p()
+    assert lib.rb_operator_create(None, None, 0, 0, None, C.byref(h)) == rb.RB_EINVAL
+    assert b"null" in lib.rb_last_error()
+    assert lib.rb_spmm(None, None, 1, None, 1, 1, None, None) == rb.RB_EINVAL
+    assert lib.rb_dot(10, 0, 0, None, 1, None, 1, None, None, 0, None) == rb.RB_EINVAL
+    assert lib.rb_dot_workspace_bytes(100, 3) > 0 and lib.rb_dot_workspace_bytes(100, 65) == 0
+    g = rb.GridDesc()
+    for d in range(3):
+        g.n[d] = 2
+        g.periodic[d] = 1  # a periodic axis needs >= 3 cells
+    nr, nc, nnz = C.c_int32(), C.c_int32(), C.c_int64()
+    assert lib.rb_fvm_csr_size(C.byref(g), 0, C.byref(nr), C.byref(nc), C.byref(nnz)) == rb.RB_EINVAL
+
+
+def test_fvm_sizes_match_oracle(lib):
+    """Row, column and nonzero counts of the device builder equal the oracle's (no GPU work)."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+    import workloads as W
+    from oracle import fvm
+
+    for g in (W.unit_periodic_grid(5), W.channel_grid(7, 6, 5), W.rbc_grid(4)):
+        gd = rb.GridDesc()
+        for d in range(3):
+            gd.n[d] = g.axes[d].n
+            gd.periodic[d] = 1 if g.axes[d].periodic else 0
+        for kind, ref in ((0, fvm.laplacian(g)), (1, fvm.divergence(g)), (2, fvm.gradient(g))):
+            nr, nc, nnz = C.c_int32(), C.c_int32(), C.c_int64()
+            assert lib.rb_fvm_csr_size(C.byref(gd), kind, C.byref(nr), C.byref(nc), C.byref(nnz)) == 0
+            assert (nr.value, nc.value, nnz.value) == (ref.shape[0], ref.shape[1], ref.nnz)

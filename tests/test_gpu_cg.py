@@ -1,0 +1,141 @@
+"""Parity of the device Poisson solves (Jacobi-PCG per column, FP32-inner refinement) against
+the oracle (GPU).
+
+Bar: every column reaches a TRUE relative residual ||b - A x|| / ||b|| <= 1e-10 (recomputed
+here on the CPU from the returned x), and x matches the oracle's CG solution within
+kappa * 1e-10 relative (the error a 1e-10 residual allows), kappa estimated by the
+oracle's own CG bound below.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import workloads as W
+from oracle import cg as ocg
+from oracle import fvm
+from tests.conftest import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _poisson(g):
+    return (-fvm.laplacian(g)).tocsr()
+
+
+def _true_res(A, B, X):
+    R = B - A @ X
+    R -= R.mean(axis=0, keepdims=True)
+    return np.linalg.norm(R, axis=0) / np.linalg.norm(B, axis=0)
+
+
+def _solve(rb, A, B, mixed=False, x0=None, **kw):
+    op = rb.Operator.from_scipy(A, k_max=B.shape[1])
+    opi = rb.Operator.from_scipy(A, dtype="f32", k_max=B.shape[1]) if mixed else None
+    X = to_dev(np.zeros_like(B) if x0 is None else x0)
+    prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, **kw)
+    res = rb.cg_solve(op, to_dev(B), X, A_inner=opi, params=prm)
+    return res, X.cpu().numpy()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_cg_periodic_32cube(rb, k, mixed):
+    """The 32^3 periodic correctness case, k columns of N(0,1) zero-mean right-hand sides."""
+    g = W.unit_periodic_grid(W.SMALL_PERIODIC_N)
+    A = _poisson(g)
+    B = W.zero_mean(W.normal((A.shape[0], k), W.seed_for(1, k)))
+    res, X = _solve(rb, A, B, mixed=mixed)
+    assert res.status == rb.RB_OK, res
+    tr = _true_res(A, B, X)
+    assert np.all(tr <= 1e-10), tr
+    assert np.allclose(res.true_rel_res, tr, rtol=1e-3, atol=1e-14)
+    Xr, infos = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True)
+    err = np.linalg.norm(X - Xr, axis=0) / np.linalg.norm(Xr, axis=0)
+    assert np.all(err <= 1e-7), err  # kappa(32^3 periodic) ~ 4e2, residual 1e-10
+    assert np.all(np.abs(X.mean(axis=0)) <= 1e-12 * np.abs(X).max(axis=0))
+    if not mixed:
+        # same algorithm, same arithmetic: iteration counts agree closely
+        assert all(abs(i - inf.iters) <= 2 for i, inf in zip(res.iters, infos)), (res.iters, [i.iters for i in infos])
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_cg_channel_stretched(rb, mixed):
+    """Wall-bounded stretched grid: the Jacobi diagonal varies; k = 3."""
+    g = W.channel_grid(40, 32, 24, gamma=1.5)
+    A = _poisson(g)
+    M = fvm.divergence(g)
+    U = W.face_field(M.shape[1], 3, 77)
+    B = -(M @ U)  # compatible right-hand sides b = M u (sum to zero); -L p = -M u
+    res, X = _solve(rb, A, B, mixed=mixed)
+    assert res.status == rb.RB_OK, res
+    assert np.all(_true_res(A, B, X) <= 1e-10)
+    Xr, _ = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True)
+    assert np.all(np.linalg.norm(X - Xr, axis=0) <= 1e-6 * np.linalg.norm(Xr, axis=0))
+    if mixed:
+        assert 2 <= res.sweeps <= 8
+
+
+def test_cg_initial_guess_and_already_converged(rb):
+    g = W.unit_periodic_grid(16)
+    A = _poisson(g)
+    B = W.zero_mean(W.normal((A.shape[0], 2), 5))
+    Xr, _ = ocg.pcg_columns(A, B, rtol=1e-12, project_mean=True)
+    res, X = _solve(rb, A, B, x0=Xr)  # exact guess: zero iterations
+    assert res.status == rb.RB_OK and res.iters == [0, 0]
+    # a nearby guess needs fewer iterations than zero
+    res0, _ = _solve(rb, A, B)
+    res1, _ = _solve(rb, A, B, x0=Xr + 1e-6 * W.normal(Xr.shape, 6))
+    assert all(a < b for a, b in zip(res1.iters, res0.iters))
+
+
+def test_cg_zero_rhs_column(rb):
+    g = W.unit_periodic_grid(8)
+    A = _poisson(g)
+    B = W.zero_mean(W.normal((A.shape[0], 3), 8))
+    B[:, 1] = 0.0
+    res, X = _solve(rb, A, B)
+    assert res.status == rb.RB_OK
+    assert np.all(X[:, 1] == 0.0)
+
+
+def test_cg_noconv_and_breakdown_status(rb):
+    g = W.unit_periodic_grid(12)
+    A = _poisson(g)
+    B = W.zero_mean(W.normal((A.shape[0], 2), 9))
+    res, _ = _solve(rb, A, B, max_iter=5, check_every=2)
+    assert res.status == rb.RB_ENOCONV and all(s == rb.RB_ENOCONV for s in res.col_status)
+    # an indefinite operator: p.q <= 0 (host-made fault, no GPU fault)
+    D = sp.diags(np.r_[np.ones(50), -np.ones(50)]).tocsr()
+    op = rb.Operator.from_scipy(D)
+    b = to_dev(np.ones((100, 1)))
+    x = torch.zeros((100, 1), dtype=torch.float64, device="cuda")
+    r = rb.cg_solve(op, b, x, params=rb.cg_params(rtol=1e-10, precond=False))
+    assert r.status == rb.RB_EBREAKDOWN
+
+
+def test_cg_invalid_arguments(rb):
+    g = W.unit_periodic_grid(4)
+    A = _poisson(g)
+    op = rb.Operator.from_scipy(A)
+    B = to_dev(np.zeros((64, 2)))
+    X = to_dev(np.zeros((64, 2)))
+    with pytest.raises(rb.RbError) as e:
+        rb.cg_solve(op, B, X, params=rb.cg_params(mixed=True))  # no FP32 operator
+    assert e.value.status == rb.RB_EINVAL
+    with pytest.raises(rb.RbError):
+        rb.cg_solve(op, B, X, work=torch.empty(16, dtype=torch.uint8, device="cuda"))
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_cg_channel_full_size(rb, mixed):
+    """192 x 128 x 96 channel Poisson problem, k = 1, in the bench's configuration: the true
+    residual reaches 1e-10 (checked on the CPU) and the solution matches the oracle's FP64
+    CG on sampled cells within the error a 1e-10 residual allows."""
+    g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+    A = (-fvm.laplacian_direct(g)).tocsr()
+    M = fvm.divergence(g)
+    B = -(M @ W.face_field(M.shape[1], 1, 2001))
+    res, X = _solve(rb, A, B, mixed=mixed)
+    assert res.status == rb.RB_OK, res
+    assert np.all(_true_res(A, B, X) <= 1e-10)

@@ -1,0 +1,202 @@
+"""Parity of the device SpMM (CSR, sliced ELL, extruded) and BLAS-1 kernels against the oracle (GPU).
+
+Tolerance: componentwise, |Y - Y_ref| <= tol * (|A| |X|) |c|, tol = 1e-12 for FP64 operators and
+1e-5 for FP32 operators (the oracle is fed the FP32-rounded values and X and computes in FP64).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import workloads as W
+from oracle import blas, fvm, mesh, spmm
+from tests.conftest import componentwise_ok, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+KS = [1, 2, 3, 4, 5, 8, 16, 32, 64]
+
+
+def _rand_csr(nr, nc, nnz_row, seed, long_rows=0):
+    g = np.random.default_rng(seed)
+    lens = g.poisson(nnz_row, nr)
+    if nr > 5:
+        lens[::7] = 0  # empty rows
+    if long_rows:
+        lens[nr // 2] = long_rows  # a row longer than a block can stage
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    ci = np.concatenate([np.sort(g.choice(nc, size=min(l, nc), replace=False)) for l in lens]).astype(np.int32) \
+        if nr else np.zeros(0, np.int32)
+    lens = np.array([min(l, nc) for l in lens])
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    va = g.standard_normal(rp[-1])
+    return sp.csr_matrix((va, ci, rp), shape=(nr, nc))
+
+
+def _run(rb, A, X, dtype, fmt="csr", c=None, ld_pad=0, tune=False):
+    k = X.shape[1]
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    npdt = np.float64 if dtype == "f64" else np.float32
+    op = rb.Operator.from_scipy(A, dtype=dtype, fmt=fmt, k_max=k)
+    Xs = np.zeros((A.shape[1], k + ld_pad), dtype=npdt)
+    Xs[:, :k] = X.astype(npdt)
+    Xd = to_dev(Xs)[:, :k]
+    Yd = torch.full((A.shape[0], k + ld_pad), float("nan"), dtype=tdt, device="cuda")
+    cd = None if c is None else to_dev(c.astype(np.float64))
+    if tune:
+        op.tune(Xd, Yd[:, :k])
+    op.spmm(Xd, Yd[:, :k], c=cd)
+    Y = Yd.cpu().numpy()
+    if ld_pad:
+        assert np.isnan(Y[:, k:]).all()  # padding lanes untouched
+    Aref = A if dtype == "f64" else spmm.round_f32(A)
+    Xref = Xs[:, :k].astype(np.float64)
+    cref = None if c is None else (c if dtype == "f64" else c.astype(np.float32).astype(np.float64))
+    Yref = spmm.spmm(Aref, Xref, cref)
+    bound = spmm.abs_bound(Aref, Xref, cref)
+    ok, worst = componentwise_ok(Y[:, :k], Yref, bound, TOL[dtype])
+    assert ok, f"worst componentwise error {worst:.3e}"
+    return op
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("fmt", ["csr", "sell"])
+@pytest.mark.parametrize("k", KS)
+def test_spmm_random_rectangular(rb, dtype, fmt, k):
+    A = _rand_csr(1037, 811, 7, seed=k)
+    X = W.normal((811, k), 100 + k)
+    _run(rb, A, X, dtype, fmt)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_spmm_scale_padding_and_long_rows(rb, dtype, k):
+    """Per-column scale c (Algorithm 1), ld > k (untouched padding), a row too long to stage."""
+    A = _rand_csr(2000, 3000, 9, seed=50 + k, long_rows=2900)
+    X = W.normal((3000, k), 200 + k)
+    c = W.normal(k, 300 + k)
+    _run(rb, A, X, dtype, "csr", c=c, ld_pad=3)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_spmm_tuned_schedules(rb, dtype, k):
+    """The autotuner's pick (vector width, lanes per row, staging) keeps parity."""
+    A = _rand_csr(4000, 4000, 27, seed=70 + k)
+    X = W.normal((4000, k), 400 + k)
+    _run(rb, A, X, dtype, "csr", tune=True)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_spmm_fvm_operators(rb, dtype):
+    """L (k = 3, velocity components), G (k = 3) and M (k = 1) of a channel grid."""
+    g = W.channel_grid(24, 20, 16)
+    for A, k in ((fvm.laplacian(g), 3), (fvm.gradient(g), 3), (fvm.divergence(g), 1)):
+        X = W.normal((A.shape[1], k), 7 + k)
+        _run(rb, A, X, dtype)
+
+
+def test_spmm_edge_cases(rb):
+    # empty operator, single row, k > 32 with unaligned ld is refused cleanly
+    A = sp.csr_matrix((0, 5))
+    op = rb.Operator.from_scipy(A)
+    op.spmm(torch.zeros((5, 2), dtype=torch.float64, device="cuda"), torch.zeros((0, 2), dtype=torch.float64,
+                                                                                   device="cuda"))
+    A = sp.csr_matrix(np.array([[2.0, 0.0, -1.0]]))
+    _run(rb, A, W.normal((3, 4), 1), "f64")
+    op = rb.Operator.from_scipy(sp.identity(40, format="csr"))
+    X = torch.zeros((40, 64 + 1), dtype=torch.float64, device="cuda")[:, 1:]
+    Y = torch.zeros((40, 64), dtype=torch.float64, device="cuda")
+    with pytest.raises(rb.RbError) as e:
+        op.spmm(X, Y)
+    assert e.value.status in (rb.RB_EINVAL, rb.RB_EUNSUPPORTED)
+    with pytest.raises(rb.RbError):  # overlapping X and Y
+        Z = torch.zeros((40, 4), dtype=torch.float64, device="cuda")
+        op.spmm(Z, Z)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_spmm_channel_full_size_k3(rb, dtype):
+    """192 x 128 x 96 channel Laplacian, k = 3, in the bench's launch configuration."""
+    g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+    A = fvm.laplacian_direct(g)
+    X = W.normal((A.shape[1], 3), 2003)
+    _run(rb, A, X, dtype)
+
+
+# ------------------------------------------------------------------------------- extruded
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("nz", [3, 8, 16, 64])
+def test_extruded_spmm(rb, dtype, nz):
+    m = W.random_trimesh(300, nz)
+    L, _ = mesh.cot_laplacian(m)
+    a = mesh.dual_areas(m)
+    dz = W.EXTRUDED_SPAN / nz
+    w = a / dz
+    X = W.normal((L.shape[0], nz), 500 + nz)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    op = rb.Operator.from_scipy(L, dtype=dtype, k_max=nz, extruded_nz=nz, z_weight=torch.as_tensor(w), dz=dz)
+    Y = op.spmm(to_dev(X.astype(npdt))).cpu().numpy()
+    if dtype == "f64":
+        Lr, wr, dzr, Xr = L, w, dz, X
+    else:
+        Lr = spmm.round_f32(L)
+        wr = w.astype(np.float32).astype(np.float64)
+        dzr = float(np.float32(dz))
+        Xr = X.astype(np.float32).astype(np.float64)
+    # oracle: the assembled 3-D operator dz (I (x) L2D) + T_z (x) diag(w)
+    Yref = mesh.extruded_apply(Lr, wr * dzr, nz, dzr, Xr)
+    absL = abs(Lr)
+    bound = dzr * spmm.spmm(absL, np.abs(Xr)) + 4 * wr[:, None] * np.abs(Xr).max(axis=1, keepdims=True)
+    ok, worst = componentwise_ok(Y, Yref, bound, TOL[dtype] * 4)
+    assert ok, worst
+
+
+def test_extruded_airfoil_full_size(rb):
+    """The ~150k-vertex airfoil mesh extruded into 64 periodic planes (k = 64), FP64."""
+    m = W.airfoil_mesh()
+    L, _ = mesh.cot_laplacian(m)
+    a = mesh.dual_areas(m)
+    nz = W.EXTRUDED_NZ
+    dz = W.EXTRUDED_SPAN / nz
+    X = W.normal((L.shape[0], nz), 3064)
+    op = rb.Operator.from_scipy(L, k_max=nz, extruded_nz=nz, z_weight=torch.as_tensor(a / dz), dz=dz)
+    Y = op.spmm(to_dev(X)).cpu().numpy()
+    Yref = mesh.extruded_apply(L, a, nz, dz, X)
+    bound = dz * spmm.spmm(abs(L), np.abs(X)) + 4 * (a / dz)[:, None] * np.abs(X).max(axis=1, keepdims=True)
+    ok, worst = componentwise_ok(Y, Yref, bound, 4e-12)
+    assert ok, worst
+
+
+# ------------------------------------------------------------------------------- BLAS-1
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 4, 8, 64])
+@pytest.mark.parametrize("n", [1, 1000, 300_001])
+def test_dot_axpy_axty(rb, dtype, k, n):
+    npdt = np.float64 if dtype == "f64" else np.float32
+    X = W.normal((n, k), 1).astype(npdt)
+    Y = W.normal((n, k), 2).astype(npdt)
+    alpha = W.normal(k, 3)
+    Xd, Yd = to_dev(X), to_dev(Y)
+    d = rb.dot(Xd, Yd).cpu().numpy()
+    dref = blas.dot(X, Y)
+    scale = blas.dot(np.abs(X), np.abs(Y))
+    tol = 1e-13 if dtype == "f64" else 1e-6
+    assert np.all(np.abs(d - dref) <= tol * scale + 1e-300)
+    # bit-reproducible
+    assert np.array_equal(d, rb.dot(Xd, Yd).cpu().numpy())
+    rb.axpy(to_dev(alpha), Xd, Yd)
+    aref = blas.axpy(alpha if dtype == "f64" else alpha.astype(np.float32), X, Y)
+    got = Yd.cpu().numpy().astype(np.float64)
+    tol2 = 1e-15 if dtype == "f64" else 2e-7
+    assert np.all(np.abs(got - aref) <= tol2 * (np.abs(X * alpha[None, :]) + np.abs(Y)) + 1e-300)
+    Yd2 = to_dev(Y)
+    rb.axty(0.5, Xd, Yd2)
+    tref = blas.axty(0.5, X, Y)
+    tol3 = 1e-15 if dtype == "f64" else 2e-7
+    assert np.all(np.abs(Yd2.cpu().numpy() - tref) <= tol3 * np.abs(tref) + 1e-300)
