@@ -1,0 +1,409 @@
+"""Benchmark of the repeated-block SpMM hot path on one GB300 (or N independent replicas).
+
+Workload: the channel-flow-shaped staggered grid 192 x 128 x 96 (n = 2,359,296 cells,
+7,059,456 faces; periodic x and z, walls in y refined by tanh with factor 1.5).  One step
+applies the discrete operators as SpMM over k right-hand sides, in FP64 and in FP32:
+    Laplacian L (k = 3, velocity components), gradient G (k = 3), divergence M (k = 1).
+metric value = effective GFLOP/s of the step: sum over its SpMMs of 2 nnz k, divided by the
+device time of the step.  Beside it the same run reports, each timed with CUDA events:
+  * spmm: per operator / dtype / k: time, GFLOP/s, algorithmic GB/s, fraction of the
+    measured HBM copy bandwidth, and the k-sweep of the Laplacian (k = 1 .. 32);
+  * poisson: ms to a 1e-10 true relative residual, FP64 Jacobi-CG vs FP32-inner FP64
+    refinement, on the compatible right-hand sides b = M u (k = 3 flow states);
+  * roofline of the dominant kernel, e2e through host buffers, the oracle on the host
+    cores (cpu_baseline), and the SM clocks sampled during the timed region.
+
+--impl reference times the CPU oracle (plain FP64 scipy, one core) on the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (the path does not shard
+across GPUs here); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SpMM effective GFLOP/s & HBM GB/s vs k; Poisson solve ms to 1e-10 residual vs FP64 CG"
+WORKLOAD = "channel 192x128x96 staggered FVM: L,G SpMM k=3 + M SpMM k=1, FP64 and FP32"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 FMA throughput of a GB300: the nominal dense FP64 rate (1.25 TFLOP/s).  The path's
+# FP64 SpMM with k >= 2 is bound by it rather than by HBM.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def spmm_bytes(nnz, n_r, n_c, k, s):
+    """Algorithmic bytes of one CSR SpMM: matrix once (value + index), row pointers, X read once, Y written."""
+    return nnz * (s + 4) + 4 * (n_r + 1) + s * k * (n_r + n_c)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_ops(rb, torch, dev):
+    """Operators of the channel workload, assembled on the device by the library."""
+    g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+    nodes, per = rb.grid_nodes(g, dev)
+    ops = {}
+    for name, kind, k in (("L", rb.RB_FVM_LAPLACIAN, 3), ("G", rb.RB_FVM_GRADIENT, 3), ("M", rb.RB_FVM_DIVERGENCE, 1)):
+        rp, ci, va, nc = rb.fvm_assemble(nodes, per, kind)
+        for dt in ("f64", "f32"):
+            ops[(name, dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, k_max=32), k)
+        if name == "L":
+            ops[("A", "f64")] = (rb.Operator(rp, ci, -va, nc, dtype="f64", k_max=3), 3)
+            ops[("A", "f32")] = (rb.Operator(rp, ci, -va, nc, dtype="f32", k_max=3), 3)
+    torch.cuda.synchronize()
+    return g, ops
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_2508_06710_gb300 as rb
+    from paper_2508_06710_gb300 import build as rbbuild
+
+    rbbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    g, ops = build_ops(rb, torch, dev)
+    hbm, hbm_src = peaks()
+    # inputs (seeded, resident in HBM before timing)
+    step_items = []  # (label, op, X, Y, k, dtype)
+    for name in ("L", "G", "M"):
+        for dt in ("f64", "f32"):
+            op, k = ops[(name, dt)]
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            X = torch.as_tensor(W.normal((op.n_cols, k), W.seed_for(2, k, salt=len(step_items))), device=dev).to(tdt)
+            Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
+            op.tune(X, Y)
+            step_items.append((f"{name}-{dt}-k{k}", op, X, Y, k, dt))
+    flops_step = sum(2 * it[1].nnz * it[4] for it in step_items)
+
+    def step(evs=None):
+        for i, (_, op, X, Y, k, _) in enumerate(step_items):
+            if evs is not None:
+                evs[i][0].record(stream)
+            op.spmm(X, Y)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    per_kernel = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in step_items] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0.record(stream)
+    for s in range(args.steps):
+        step(per_kernel[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = world * flops_step / (ms_step * 1e-3) / 1e9
+    # per kernel: average device time over the timed steps
+    kern = []
+    for i, (label, op, X, Y, k, dt) in enumerate(step_items):
+        ts = [per_kernel[s][i][0].elapsed_time(per_kernel[s][i][1]) for s in range(args.steps)]
+        ms = sum(ts) / len(ts)
+        s_b = 8 if dt == "f64" else 4
+        by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, s_b)
+        fl = 2 * op.nnz * k
+        kern.append({"kernel": label, "ms": ms, "gflops": fl / ms / 1e6, "gbs": by / ms / 1e6,
+                     "frac_hbm": by / ms / 1e6 / hbm, "bytes": by, "flops": fl,
+                     "fp64_frac": (fl / ms / 1e9 / FP64_PEAK_TFLOPS) if dt == "f64" else None})
+    dom = max(kern, key=lambda r: r["ms"])
+    if dom["kernel"].split("-")[1] == "f64" and dom["flops"] / (FP64_PEAK_TFLOPS * 1e12) > dom["bytes"] / (hbm * 1e9):
+        roof = {"bound": "alu", "achieved": dom["gflops"] / 1e3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": dom["gflops"] / 1e3 / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                "kernel": dom["kernel"], "peak_source": "nominal FP64 FMA rate of GB300 (measured 1.19)",
+                "hbm_gbs": dom["gbs"], "hbm_frac_of_measured": dom["frac_hbm"]}
+    else:
+        roof = {"bound": "hbm", "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s", "frac": dom["frac_hbm"],
+                "traffic": args.traffic, "kernel": dom["kernel"], "peak_source": hbm_src}
+    out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_cells": g.n_cells, "k": {"L": 3, "G": 3, "M": 1},
+                      "l2": "inputs larger than L2: every SpMM streams >= 160 MB", "parallelism": "replicas"},
+           "roofline": roof, "kernels": kern, "gpu_launches": len(step_items) * args.steps,
+           "clocks": clk}
+    if rank == 0 and not args.quick:
+        out["e2e"] = e2e(args, torch, step_items, stream, dev, flops_step)
+        out["ksweep"] = k_sweep(torch, rb, ops, dev, hbm)
+        out["poisson"] = poisson(torch, rb, ops, g, dev)
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(g)
+    return out
+
+
+def e2e(args, torch, step_items, stream, dev, flops_step):
+    """The same step through the public API from pinned host buffers: H2D of every input,
+    the six SpMMs, D2H of every result, all inside the timed region."""
+    hx = [torch.empty(X.shape, dtype=X.dtype, pin_memory=True).copy_(X.cpu()) for (_, _, X, _, _, _) in step_items]
+    hy = [torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True) for (_, _, _, Y, _, _) in step_items]
+    h2d = sum(t.numel() * t.element_size() for t in hx)
+    d2h = sum(t.numel() * t.element_size() for t in hy)
+
+    def one():
+        for (_, op, X, Y, _, _), a, b in zip(step_items, hx, hy):
+            X.copy_(a, non_blocking=True)
+            op.spmm(X, Y)
+            b.copy_(Y, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        one()
+    ts = []
+    for _ in range(10):
+        t = time.perf_counter()
+        one()
+        ts.append(time.perf_counter() - t)
+    ms = statistics.median(ts) * 1e3
+    return {"value": flops_step / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def k_sweep(torch, rb, ops, dev, hbm):
+    """Laplacian SpMM for k = 1 .. 32 in FP64 and FP32 (events, median of 10 after tuning)."""
+    res = []
+    for dt in ("f64", "f32"):
+        op, _ = ops[("L", dt)]
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        base = None
+        for k in W.ks_sweep():
+            X = torch.randn((op.n_cols, k), dtype=tdt, device=dev)
+            Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
+            op.tune(X, Y)
+            ms = time_events(torch, lambda: op.spmm(X, Y), 10)
+            s_b = 8 if dt == "f64" else 4
+            by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, s_b)
+            if k == 1:
+                base = ms
+            res.append({"dtype": dt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6,
+                        "frac_hbm": by / ms / 1e6 / hbm, "speedup_vs_k_spmv": k * base / ms})
+            del X, Y
+    return res
+
+
+def time_events(torch, fn, reps):
+    s = torch.cuda.current_stream()
+    ts = []
+    for _ in range(2):
+        fn()
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def poisson(torch, rb, ops, g, dev):
+    """Poisson solves to a 1e-10 true relative residual on b = M u (k = 3): FP64 CG vs FP32-inner refinement."""
+    Aop, k = ops[("A", "f64")]
+    A32, _ = ops[("A", "f32")]
+    Mop, _ = ops[("M", "f64")]
+    U = torch.as_tensor(W.face_field(Mop.n_cols, k, 2002), device=dev)
+    B = torch.empty((Mop.n_rows, k), dtype=torch.float64, device=dev)
+    Mop.spmm(U, B)
+    B.neg_()
+    out = {"k": k, "rtol": 1e-10}
+    for name, mixed in (("fp64_cg", False), ("ir_fp32_inner", True)):
+        prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, inner_rtol=1e-4, check_every=50)
+        work = torch.empty(rb.cg_workspace_bytes(Aop, k, prm), dtype=torch.uint8, device=dev)
+        times = []
+        for rep in range(2):
+            X = torch.zeros((Mop.n_rows, k), dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = rb.cg_solve(Aop, B, X, A_inner=A32 if mixed else None, params=prm, work=work)
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t) * 1e3)
+        out[name] = {"ms": min(times), "iters": r.iters, "true_rel_res": r.true_rel_res, "status": r.status,
+                     "sweeps": r.sweeps, "spmm_calls": r.spmm_calls, "host_syncs": r.host_syncs}
+    out["speedup_ir_vs_fp64"] = out["fp64_cg"]["ms"] / out["ir_fp32_inner"]["ms"]
+    return out
+
+
+def cpu_baseline(g, budget_s=15.0):
+    """The oracle (scipy FP64, one core) on the same step: each SpMM as k separate SpMVs."""
+    from oracle import fvm, spmm
+
+    ops = [(fvm.laplacian_direct(g), 3), (fvm.gradient(g), 3), (fvm.divergence(g), 1)]
+    Xs = [W.normal((A.shape[1], k), 7 + k) for A, k in ops]
+    flops = 0
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s or steps == 0:
+        for (A, k), X in zip(ops, Xs):
+            spmm.spmm(A, X)
+            spmm.spmm(A.astype(np.float32), X.astype(np.float32))
+            flops += 2 * 2 * A.nnz * k
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full steps of the same workload (6 SpMMs, scipy CSR, single thread)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+    from oracle import fvm, spmm
+
+    ops = [(fvm.laplacian_direct(g), 3), (fvm.gradient(g), 3), (fvm.divergence(g), 1)]
+    Xs = [W.normal((A.shape[1], k), 7 + k) for A, k in ops]
+    ops32 = [A.astype(np.float32) for A, _ in ops]
+    Xs32 = [X.astype(np.float32) for X in Xs]
+    flops = sum(2 * 2 * A.nnz * k for A, k in ops)
+
+    def step():
+        for (A, k), A32, X, X32 in zip(ops, ops32, Xs, Xs32):
+            spmm.spmm(A, X)
+            spmm.spmm(A32, X32)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    ms = (time.perf_counter() - t) * 1e3 / args.steps
+    v = flops / (ms * 1e-3) / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_cells": g.n_cells, "k": {"L": 3, "G": 3, "M": 1},
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": "the full step: 6 SpMMs (scipy CSR, single thread), every step"},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="timed step only (no e2e, sweeps, solves, CPU baseline)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the dominant kernel, if captured for this build")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.warmup < 3:
+        args.warmup = 3
+    if world > 1:
+        import torch
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        torch.distributed.init_process_group(backend)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
