@@ -122,6 +122,7 @@ def build_ops(rb, torch, dev):
         rp, ci, va, nc = rb.fvm_assemble(nodes, per, kind)
         for dt in ("f64", "f32"):
             ops[(name, dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, k_max=32), k)
+            ops[(name + "-sell", dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, fmt="sell", k_max=32), k)
         if name == "L":
             ops[("A", "f64")] = (rb.Operator(rp, ci, -va, nc, dtype="f64", k_max=3), 3)
             ops[("A", "f32")] = (rb.Operator(rp, ci, -va, nc, dtype="f32", k_max=3), 3)
@@ -256,8 +257,8 @@ def e2e(args, torch, step_items, stream, dev, flops_step):
 def k_sweep(torch, rb, ops, dev, hbm):
     """Laplacian SpMM for k = 1 .. 32 in FP64 and FP32 (events, median of 10 after tuning)."""
     res = []
-    for dt in ("f64", "f32"):
-        op, _ = ops[("L", dt)]
+    for dt, fmt in (("f64", "csr"), ("f32", "csr"), ("f64", "sell"), ("f32", "sell")):
+        op, _ = ops[("L" if fmt == "csr" else "L-sell", dt)]
         tdt = torch.float64 if dt == "f64" else torch.float32
         base = None
         for k in W.ks_sweep():
@@ -269,7 +270,7 @@ def k_sweep(torch, rb, ops, dev, hbm):
             by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, s_b)
             if k == 1:
                 base = ms
-            res.append({"dtype": dt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6,
+            res.append({"dtype": dt, "format": fmt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6,
                         "frac_hbm": by / ms / 1e6 / hbm, "speedup_vs_k_spmv": k * base / ms})
             del X, Y
     return res
@@ -301,8 +302,8 @@ def poisson(torch, rb, ops, g, dev):
     Mop.spmm(U, B)
     B.neg_()
     out = {"k": k, "rtol": 1e-10}
-    for name, mixed in (("fp64_cg", False), ("ir_fp32_inner", True)):
-        prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, inner_rtol=1e-4, check_every=50)
+    for name, mixed in (("fp64_cg", 0), ("ir_fp32_inner", 2), ("ir_fp32_inner_restarted", 1)):
+        prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, check_every=50)
         work = torch.empty(rb.cg_workspace_bytes(Aop, k, prm), dtype=torch.uint8, device=dev)
         times = []
         for rep in range(2):
@@ -372,6 +373,40 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_run(args):
+    """A short, fixed workload for ncu captures (no tuning, no sweeps, no CPU baseline)."""
+    import torch
+
+    import paper_2508_06710_gb300 as rb
+    from paper_2508_06710_gb300 import build as rbbuild
+
+    rbbuild.build()
+    dev = torch.device("cuda", 0)
+    g, ops = build_ops(rb, torch, dev)
+    if args.profile == "step":
+        for name in ("L", "G", "M"):
+            for dt in ("f64", "f32"):
+                op, k = ops[(name, dt)]
+                tdt = torch.float64 if dt == "f64" else torch.float32
+                X = torch.ones((op.n_cols, k), dtype=tdt, device=dev)
+                Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
+                for _ in range(args.steps):
+                    op.spmm(X, Y)
+    else:
+        Aop, _ = ops[("A", "f64")]
+        A32, _ = ops[("A", "f32")]
+        Mop, _ = ops[("M", "f64")]
+        for k in (1, 3):
+            U = torch.as_tensor(W.face_field(Mop.n_cols, k, 2002), device=dev)
+            B = Mop.spmm(U).neg_()
+            for mixed in (False, True):
+                prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, max_iter=20, check_every=10)
+                X = torch.zeros((Mop.n_rows, k), dtype=torch.float64, device=dev)
+                rb.cg_solve(Aop, B, X, A_inner=A32 if mixed else None, params=prm)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,7 +417,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel, if captured for this build")
+    ap.add_argument("--profile", default=None, choices=["step", "cg"],
+                    help="short run for an ncu capture: 'step' = the timed step only, 'cg' = a 20-iteration "
+                         "FP64 and FP32-refinement Poisson solve (k = 1 and 3)")
     args = ap.parse_args()
+    if args.profile:
+        return profile_run(args)
     rank, world, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3

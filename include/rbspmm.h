@@ -196,8 +196,13 @@ typedef struct {
   double rtol;           /* stop when ||b - A x||_2 <= rtol ||b||_2 (true residual, FP64) */
   int32_t max_iter;      /* CG iterations (inner iterations summed when mixed) */
   int32_t precond;       /* 0: none, 1: Jacobi */
-  int32_t mixed;         /* 0: FP64 CG; 1: FP32-inner CG inside FP64 iterative refinement */
-  double inner_rtol;     /* mixed: relative tolerance of each inner FP32 solve (e.g. 1e-4) */
+  int32_t mixed;         /* 0: FP64 CG; 1: FP32-inner CG inside FP64 iterative refinement, each
+                            sweep restarting the inner CG; 2: the same refinement with reliable
+                            updates: the inner recurrence keeps its search direction across
+                            sweeps (rescaled) and only its residual is replaced by the FP64
+                            one, which keeps the iteration count near that of FP64 CG */
+  double inner_rtol;     /* mixed: the residual reduction of each sweep (e.g. 1e-2 for mixed = 2,
+                            1e-4 for mixed = 1) */
   int32_t max_sweeps;    /* mixed: refinement sweeps */
   int32_t project_mean;  /* 1: singular periodic/Neumann operator; remove the column mean of
                             every true residual and of the final x (zero-mean solution) */

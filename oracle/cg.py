@@ -162,6 +162,73 @@ def ir_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_rtol=1e-4
     return x, ColumnInfo(total_inner, np.linalg.norm(b - A @ x) / nb, NOCONV), max_sweeps
 
 
+def ir_reliable_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_rtol=1e-4, max_sweeps=50,
+                    max_iter=20000, jacobi=True, project_mean=False):
+    """FP32-inner refinement that keeps the search direction across sweeps (reliable updates).
+
+    Each sweep: r = b - A x in FP64 (stop if ||r|| <= rtol ||b||), s = ||r||, r32 = r / s; the
+    FP32 recurrence (FP32 matrix and vectors, FP64 dot accumulation) then continues with the
+    next direction built from the replaced residual and the previous direction, both in the
+    new normalisation: z = D^-1 r32, beta = (r32 . z) / (rz_prev (s_prev / s)^2),
+    p32 <- z + beta p32 s_prev / s (the first sweep starts from p32 = z), and runs until
+    its residual falls by ``inner_rtol``; then x += s d32 in FP64.  Replacing only the
+    residual, not the direction, keeps the Krylov progress, so the iteration count stays
+    close to plain FP64 CG.
+    """
+    f32 = np.float32
+    A32 = A.astype(f32)
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), ColumnInfo(0, 0.0, OK), 0
+    dinv = (1.0 / A32.diagonal().astype(np.float64)).astype(f32) if jacobi else np.ones(b.shape[0], dtype=f32)
+    d64 = lambda u, v: float(np.dot(u.astype(np.float64), v.astype(np.float64)))
+    p = None
+    s_prev = 0.0
+    rz = 0.0
+    total = 0
+    for sweep in range(max_sweeps + 1):
+        r = _project(b - A @ x, project_mean)
+        s = np.linalg.norm(r)
+        if s <= rtol * nb:
+            x = _project(x, project_mean)
+            return x, ColumnInfo(total, np.linalg.norm(b - A @ x) / nb, OK), sweep
+        if sweep == max_sweeps or total >= max_iter:
+            break
+        r32 = (r / s).astype(f32)
+        z = dinv * r32
+        rz_new = d64(r32, z)
+        if p is None:
+            p = z.copy()
+        else:
+            ratio = s_prev / s
+            beta = rz_new / (rz * ratio * ratio)
+            p = z + f32(beta) * (p * f32(ratio)).astype(f32)
+        rz = rz_new
+        rr0 = d64(r32, r32)
+        d = np.zeros_like(r32)
+        while total < max_iter:
+            q = (A32 @ p).astype(f32)
+            pq = d64(p, q)
+            if not np.isfinite(pq) or pq <= 0.0:
+                break
+            alpha = f32(rz / pq)
+            d = d + alpha * p
+            r32 = r32 - alpha * q
+            total += 1
+            if d64(r32, r32) <= inner_rtol**2 * rr0:
+                break
+            z = dinv * r32
+            rz_new = d64(r32, z)
+            p = z + f32(rz_new / rz) * p
+            rz = rz_new
+        x = x + s * d.astype(np.float64)
+        s_prev = s
+    x = _project(x, project_mean)
+    return x, ColumnInfo(total, np.linalg.norm(b - A @ x) / nb, NOCONV), max_sweeps
+
+
 def batch_solve(systems, **kw):
     """Uneven systems solved one after the other: each column of each system independently."""
     out = []

@@ -321,10 +321,15 @@ class CgResult:
     extra: dict = field(default_factory=dict)
 
 
-def cg_params(rtol=1e-10, max_iter=20000, precond=True, mixed=False, inner_rtol=1e-4, max_sweeps=30,
+def cg_params(rtol=1e-10, max_iter=20000, precond=True, mixed=False, inner_rtol=None, max_sweeps=60,
               project_mean=False, check_every=32) -> CgParams:
-    return CgParams(rtol, max_iter, 1 if precond else 0, 1 if mixed else 0, inner_rtol, max_sweeps,
-                    1 if project_mean else 0, check_every)
+    """mixed: False/0 = FP64 CG, 1 (or True) = restarted FP32-inner refinement, 2 = refinement
+    with reliable updates (the search direction survives each sweep)."""
+    m = int(mixed)
+    if inner_rtol is None:
+        inner_rtol = 1e-2 if m == 2 else 1e-4
+    return CgParams(rtol, max_iter, 1 if precond else 0, m, inner_rtol, max_sweeps, 1 if project_mean else 0,
+                    check_every)
 
 
 def cg_workspace_bytes(A: Operator, k: int, params: CgParams) -> int:

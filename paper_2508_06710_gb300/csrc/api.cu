@@ -2,6 +2,7 @@
 // destruction and introspection.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -21,6 +22,29 @@ void set_error(const char* fmt, ...) {
 }
 
 void clear_error() { g_err.clear(); }
+
+int resident_blocks(const void* kernel, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> cache;
+  static int sms = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(kernel, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 152;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int v = std::min(kPersistentGrid, std::max(1, per_sm * sms));
+  cache[key] = v;
+  return v;
+}
 
 rb_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
   set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);

@@ -11,7 +11,7 @@
 namespace rb {
 namespace {
 
-constexpr int kBlasGrid = 152 * 4;
+constexpr int kBlasGrid = kPersistentGrid;  // partials capacity: at most one resident wave
 
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kThreads) k_dot_partial(int64_t n, int k, int kp, const T* __restrict__ X,
@@ -94,7 +94,6 @@ __global__ void __launch_bounds__(kThreads) k_axty(int64_t n, int k, int kp, T a
   }
 }
 
-int blas_grid(int64_t n, int R) { return (int)std::max<int64_t>(1, std::min<int64_t>(kBlasGrid, (n + R - 1) / R)); }
 
 rb_status check_block(const char* fn, int64_t n, int k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y,
                       int64_t ldy) {
@@ -162,15 +161,15 @@ extern "C" rb_status rb_dot(int64_t n, int32_t k, rb_dtype dtype, const void* X,
   int vec, kp;
   vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
   RB_REQUIRE(kp <= 32, "rb_dot: k = %d needs 16-byte aligned rows", k);
-  const int R = kThreads / kp;
-  const int grid = blas_grid(n, R);
+  const int64_t blocks = std::max<int64_t>(1, (n + kThreads / kp - 1) / (kThreads / kp));
+  int grid = 1;
   double* partials = static_cast<double*>(work);
   if (dtype == RB_F64) {
-    RB_DISPATCH_VEC(double, vec,
+    RB_DISPATCH_VEC(double, vec, grid = wave_grid(&k_dot_partial<double, V>, blocks);
                     k_dot_partial<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, (const double*)X, ldx,
                                                                        (const double*)Y, ldy, partials));
   } else {
-    RB_DISPATCH_VEC(float, vec,
+    RB_DISPATCH_VEC(float, vec, grid = wave_grid(&k_dot_partial<float, V>, blocks);
                     k_dot_partial<float, V><<<grid, kThreads, 0, s>>>(n, k, kp, (const float*)X, ldx,
                                                                       (const float*)Y, ldy, partials));
   }
@@ -190,15 +189,15 @@ extern "C" rb_status rb_axpy(int64_t n, int32_t k, rb_dtype dtype, const double*
   int vec, kp;
   vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
   RB_REQUIRE(kp <= 32, "rb_axpy: k = %d needs 16-byte aligned rows", k);
-  const int grid = blas_grid(n, kThreads / kp);
+  const int64_t blocks = (n + kThreads / kp - 1) / (kThreads / kp);
   if (dtype == RB_F64) {
     RB_DISPATCH_VEC(double, vec,
-                    k_axpy<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, alpha, (const double*)X, ldx, (double*)Y,
-                                                                ldy));
+                    k_axpy<double, V><<<wave_grid(&k_axpy<double, V>, blocks), kThreads, 0, s>>>(
+                        n, k, kp, alpha, (const double*)X, ldx, (double*)Y, ldy));
   } else {
     RB_DISPATCH_VEC(float, vec,
-                    k_axpy<float, V><<<grid, kThreads, 0, s>>>(n, k, kp, alpha, (const float*)X, ldx, (float*)Y,
-                                                               ldy));
+                    k_axpy<float, V><<<wave_grid(&k_axpy<float, V>, blocks), kThreads, 0, s>>>(
+                        n, k, kp, alpha, (const float*)X, ldx, (float*)Y, ldy));
   }
   RB_CUDA(cudaGetLastError());
   return RB_OK;
@@ -214,15 +213,15 @@ extern "C" rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha,
   int vec, kp;
   vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
   RB_REQUIRE(kp <= 32, "rb_axty: k = %d needs 16-byte aligned rows", k);
-  const int grid = blas_grid(n, kThreads / kp);
+  const int64_t blocks = (n + kThreads / kp - 1) / (kThreads / kp);
   if (dtype == RB_F64) {
     RB_DISPATCH_VEC(double, vec,
-                    k_axty<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, alpha, (const double*)X, ldx, (double*)Y,
-                                                                ldy));
+                    k_axty<double, V><<<wave_grid(&k_axty<double, V>, blocks), kThreads, 0, s>>>(
+                        n, k, kp, alpha, (const double*)X, ldx, (double*)Y, ldy));
   } else {
     RB_DISPATCH_VEC(float, vec,
-                    k_axty<float, V><<<grid, kThreads, 0, s>>>(n, k, kp, (float)alpha, (const float*)X, ldx,
-                                                               (float*)Y, ldy));
+                    k_axty<float, V><<<wave_grid(&k_axty<float, V>, blocks), kThreads, 0, s>>>(
+                        n, k, kp, (float)alpha, (const float*)X, ldx, (float*)Y, ldy));
   }
   RB_CUDA(cudaGetLastError());
   return RB_OK;

@@ -45,14 +45,12 @@ enum ResidMode : int { RM_INIT = 0, RM_CHECK = 1, RM_REPORT = 2, RM_OUTER = 3 };
 
 constexpr int K = RB_MAX_K;
 constexpr int kGridMax = 152 * 8;
-// dynamic shared memory of the fused SpMM kernels (their static reduction scratch is < 16 KB)
-constexpr size_t kCgDynSmem = 32 * 1024;
 
 struct CgScal {
   double rz[K], pq[K], rr[K], tol2[K], alpha[K], beta[K], mean[K];
   double bb[K], rr_true[K];
-  // outer refinement
-  double otol2[K], omean[K], oscale[K];
+  // outer refinement (oprev: the previous sweep's residual norm, 0 before the first sweep)
+  double otol2[K], omean[K], oscale[K], oprev[K];
   int ostate[K];
   int state[K], iters[K];
   int n_active, n_check, n_oactive, pad;
@@ -63,6 +61,7 @@ struct CgCtl {
   int k, kp;
   int64_t n;
   int inner;         // 1: inner FP32 solve of the refinement
+  int reliable;      // refinement keeps the search direction across sweeps (mixed == 2)
   int project;       // remove column means of true residuals
   double rtol2;      // rtol^2
   double inner_rtol2;
@@ -70,25 +69,21 @@ struct CgCtl {
 
 // ---------------------------------------------------------------------------------- helpers
 
-// Sums FP32 products in FP32 in groups of four, the groups in FP64; FP64 products in FP64.
-template <typename T>
-struct DotAcc {
-  double d = 0.0;
-  float f = 0.0f;
-  int c = 0;
-  __device__ __forceinline__ void add(T a, T b) {
-    if constexpr (sizeof(T) == 8) {
-      d = fma((double)a, (double)b, d);
-    } else {
-      f = fmaf((float)a, (float)b, f);
-      if (++c == 4) {
-        d += (double)f;
-        f = 0.0f;
-        c = 0;
-      }
-    }
+// N running dot products in the arithmetic of the solve: FP64 products and sums for the FP64
+// solve; for the FP32 inner solve, FP32 products summed in FP32 over the thread's rows (a
+// few dozen) and, in block_reduce, over the lanes of a warp, then in FP64 across warps and
+// blocks.  FP64 instructions are scarce on this GPU (one warp-wide FP64 instruction holds an
+// SM for about 16 cycles), so the FP32 solve keeps them out of its per-row work.
+template <typename T, int N>
+struct DotAccN {
+  T s[N];
+  __device__ __forceinline__ DotAccN() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) s[i] = T(0);
   }
-  __device__ __forceinline__ double get() const { return d + (double)f; }
+  __device__ __forceinline__ void add(int i, T a, T b) { s[i] = fma(a, b, s[i]); }
+  __device__ __forceinline__ void step() {}
+  __device__ __forceinline__ T get(int i) const { return s[i]; }
 };
 
 __device__ __forceinline__ void recount(CgScal* sc, int k) {
@@ -109,38 +104,34 @@ template <typename T, int VEC, int LPR>
 __global__ void __launch_bounds__(kThreads) k_cg_q(CsrArgs<T> a, CgCtl ctl, CgScal* __restrict__ sc,
                                                     double* __restrict__ partials) {
   if (sc->n_active == 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RedSmem<1> red;
   const int R = kThreads / (a.kp * LPR);
-  int32_t* s_rp = reinterpret_cast<int32_t*>(smem_raw);
-  int32_t* s_ci = s_rp + round4(R + 1);
-  T* s_va = reinterpret_cast<T*>(s_ci + round4(a.stage_cap));
   const int t = threadIdx.x;
   const int sub = t % LPR, rc = t / LPR, chunk = rc % a.kp, rloc = rc / a.kp;
-  DotAcc<T> dacc[VEC];
-  for (int64_t tile = blockIdx.x; tile * R < a.n_rows; tile += gridDim.x) {
-    const int r0 = (int)(tile * R);
-    const TileInfo ti = stage_rows<T>(a, r0, R, s_rp, s_ci, s_va);
-    const bool active = rloc < ti.nr && chunk * VEC < a.k;
+  DotAccN<T, VEC> dacc;
+  const int64_t stride = (int64_t)gridDim.x * R;
+  for (int64_t base = (int64_t)blockIdx.x * R; base < a.n_rows; base += stride) {
+    const int64_t row = base + rloc;
+    const bool active = row < a.n_rows && chunk * VEC < a.k;
     T acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = T(0);
-    row_accumulate<T, VEC, LPR>(a, ti, s_rp, s_ci, s_va, rloc, chunk, sub, active, acc);
+    row_accumulate_direct<T, VEC, LPR>(a, row, chunk, sub, active, acc);
     if (active && sub == 0) {
-      const int64_t off = (int64_t)(r0 + rloc) * a.ldy + chunk * VEC;
-      const Vec<T, VEC> p = ldv_rw<T, VEC>(a.X + (int64_t)(r0 + rloc) * a.ldx + chunk * VEC);
+      const Vec<T, VEC> p = ldv<T, VEC>(a.X + row * a.ldx + chunk * VEC);
       Vec<T, VEC> q;
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         q.v[e] = acc[e];
-        dacc[e].add(p.v[e], acc[e]);
+        dacc.add(e, p.v[e], acc[e]);
       }
-      stv<T, VEC>(a.Y + off, q);
+      dacc.step();
+      stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, q);
     }
   }
-  double part[1][VEC];
+  T part[1][VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) part[0][e] = (sub == 0) ? dacc[e].get() : 0.0;
+  for (int e = 0; e < VEC; ++e) part[0][e] = (sub == 0) ? dacc.get(e) : T(0);
   const double v = block_reduce<1, VEC>(part, a.kp, LPR, a.k, red);
   if (!publish_partials<1>(v, a.k, partials, &sc->counter[0], red)) return;
   const double tot = final_sum<1>(partials, a.k, gridDim.x, red);
@@ -177,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(CgCtl ctl, T* __restrict
   T al[VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) al[e] = col_ok ? (T)sc->alpha[chunk * VEC + e] : T(0);
-  DotAcc<T> drz[VEC], drr[VEC];
+  DotAccN<T, 2 * VEC> dots;  // [0, VEC): r . D^-1 r, [VEC, 2 VEC): r . r
   if (col_ok) {
     for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
       const int64_t o = row * k + chunk * VEC;
@@ -190,16 +181,17 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(CgCtl ctl, T* __restrict
       for (int e = 0; e < VEC; ++e) {
         xv.v[e] = fma(al[e], pv.v[e], xv.v[e]);
         rv.v[e] = fma(-al[e], qv.v[e], rv.v[e]);
-        drz[e].add(rv.v[e], d * rv.v[e]);
-        drr[e].add(rv.v[e], rv.v[e]);
+        dots.add(e, rv.v[e], d * rv.v[e]);
+        dots.add(VEC + e, rv.v[e], rv.v[e]);
       }
+      dots.step();
       stv<T, VEC>(x + row * ldx + chunk * VEC, xv);
       stv<T, VEC>(r + o, rv);
     }
   }
-  double part[2][VEC];
+  T part[2][VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) part[0][e] = drz[e].get(), part[1][e] = drr[e].get();
+  for (int e = 0; e < VEC; ++e) part[0][e] = dots.get(e), part[1][e] = dots.get(VEC + e);
   const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
   if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[1], red)) return;
   const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
@@ -263,14 +255,10 @@ __global__ void __launch_bounds__(kThreads) k_cg_resid(CsrArgs<double> a, CgCtl 
                                                         const double* __restrict__ B, int64_t ldb,
                                                         double* __restrict__ rout, CgScal* __restrict__ sc,
                                                         double* __restrict__ partials) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RedSmem<3> red;
   __shared__ bool wmask[K];
   const int k = a.k;
   const int R = kThreads / (a.kp * LPR);
-  int32_t* s_rp = reinterpret_cast<int32_t*>(smem_raw);
-  int32_t* s_ci = s_rp + round4(R + 1);
-  double* s_va = reinterpret_cast<double*>(s_ci + round4(a.stage_cap));
   if ((int)threadIdx.x < k) {
     const int st = sc->state[threadIdx.x];
     bool w = false;
@@ -285,16 +273,15 @@ __global__ void __launch_bounds__(kThreads) k_cg_resid(CsrArgs<double> a, CgCtl 
   double acc_rr[VEC], acc_s[VEC], acc_bb[VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) acc_rr[e] = acc_s[e] = acc_bb[e] = 0.0;
-  for (int64_t tile = blockIdx.x; tile * R < a.n_rows; tile += gridDim.x) {
-    const int r0 = (int)(tile * R);
-    const TileInfo ti = stage_rows<double>(a, r0, R, s_rp, s_ci, s_va);
-    const bool active = rloc < ti.nr && chunk * VEC < k;
+  const int64_t stride = (int64_t)gridDim.x * R;
+  for (int64_t base = (int64_t)blockIdx.x * R; base < a.n_rows; base += stride) {
+    const int64_t row = base + rloc;
+    const bool active = row < a.n_rows && chunk * VEC < k;
     double acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = 0.0;
-    row_accumulate<double, VEC, LPR>(a, ti, s_rp, s_ci, s_va, rloc, chunk, sub, active, acc);
+    row_accumulate_direct<double, VEC, LPR>(a, row, chunk, sub, active, acc);
     if (active && sub == 0) {
-      const int64_t row = r0 + rloc;
       const Vec<double, VEC> b = ldv<double, VEC>(B + row * ldb + chunk * VEC);
       Vec<double, VEC> rt;
 #pragma unroll
@@ -365,6 +352,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_resid(CsrArgs<double> a, CgCtl 
         } else if (!isfinite(rrp)) {
           sc->ostate[j] = ST_BREAKDOWN;
         } else {
+          sc->oprev[j] = sc->oscale[j];
           sc->oscale[j] = sqrt(rrp);
         }
       }
@@ -392,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_restart(CgCtl ctl, T* __restric
     on[e] = col_ok && sc->state[chunk * VEC + e] == ST_RESTART;
     mu[e] = col_ok ? (T)sc->mean[chunk * VEC + e] : T(0);
   }
-  DotAcc<T> drz[VEC], drr[VEC];
+  DotAccN<T, 2 * VEC> dots;
   if (col_ok) {
     for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
       const int64_t o = row * k + chunk * VEC;
@@ -404,17 +392,18 @@ __global__ void __launch_bounds__(kThreads) k_cg_restart(CgCtl ctl, T* __restric
         if (on[e]) {
           rv.v[e] = rv.v[e] - mu[e];
           pv.v[e] = d * rv.v[e];
-          drz[e].add(rv.v[e], pv.v[e]);
-          drr[e].add(rv.v[e], rv.v[e]);
+          dots.add(e, rv.v[e], pv.v[e]);
+          dots.add(VEC + e, rv.v[e], rv.v[e]);
         }
       }
+      dots.step();
       stv<T, VEC>(r + o, rv);
       stv<T, VEC>(p + o, pv);
     }
   }
-  double part[2][VEC];
+  T part[2][VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) part[0][e] = drz[e].get(), part[1][e] = drr[e].get();
+  for (int e = 0; e < VEC; ++e) part[0][e] = dots.get(e), part[1][e] = dots.get(VEC + e);
   const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
   if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[3], red)) return;
   const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
@@ -433,7 +422,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_restart(CgCtl ctl, T* __restric
 
 // ---------------------------------- refinement: inner right-hand side and solution update
 
-// r32 = (r64 - mean) / scale, d32 = 0, p32 = D^-1 r32 for outer-active columns; zero else.
+// r32 = (r64 - mean) / scale and d32 = 0 on outer-active columns (zero elsewhere).  A column
+// that starts its recurrence here gets p32 = D^-1 r32; with reliable updates a column that
+// already has a direction keeps p32, and the last block sets beta so that the following
+// p-update kernel forms p32 = D^-1 r32 + beta p32 with beta = rz_new / (rz_old ratio) and
+// ratio = s_prev / s, which continues the previous direction in the new normalisation.
 template <int VEC>
 __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* __restrict__ r64,
                                                        float* __restrict__ r32, float* __restrict__ p32,
@@ -444,38 +437,44 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
   const int R = kThreads / kp;
   const int chunk = threadIdx.x % kp;
   const bool col_ok = chunk * VEC < k;
-  bool on[VEC];
+  bool on[VEC], fresh[VEC];
+  bool any_kept = false;
   double mu[VEC], inv[VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) {
     const int j = chunk * VEC + e;
     on[e] = col_ok && sc->ostate[j] == ST_ACTIVE;
+    fresh[e] = !(ctl.reliable && on[e] && sc->oprev[j] > 0.0);
+    any_kept |= !fresh[e];
     mu[e] = on[e] ? sc->omean[j] : 0.0;
     inv[e] = on[e] ? 1.0 / sc->oscale[j] : 0.0;
   }
-  DotAcc<float> drz[VEC], drr[VEC];
+  DotAccN<float, 2 * VEC> dots;
   if (col_ok) {
     for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
       const int64_t o = row * k + chunk * VEC;
       const Vec<double, VEC> rv = ldv_rw<double, VEC>(r64 + o);
       const float d = dinv ? dinv[row] : 1.0f;
       Vec<float, VEC> r, p, z;
+      if (any_kept) p = ldv_rw<float, VEC>(p32 + o);
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         r.v[e] = on[e] ? (float)((rv.v[e] - mu[e]) * inv[e]) : 0.0f;
-        p.v[e] = d * r.v[e];
+        const float zz = d * r.v[e];
+        if (fresh[e]) p.v[e] = zz;
         z.v[e] = 0.0f;
-        drz[e].add(r.v[e], p.v[e]);
-        drr[e].add(r.v[e], r.v[e]);
+        dots.add(e, r.v[e], zz);
+        dots.add(VEC + e, r.v[e], r.v[e]);
       }
+      dots.step();
       stv<float, VEC>(r32 + o, r);
       stv<float, VEC>(p32 + o, p);
       stv<float, VEC>(d32 + o, z);
     }
   }
-  double part[2][VEC];
+  float part[2][VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) part[0][e] = drz[e].get(), part[1][e] = drr[e].get();
+  for (int e = 0; e < VEC; ++e) part[0][e] = dots.get(e), part[1][e] = dots.get(VEC + e);
   const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
   if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[4], red)) return;
   const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
@@ -485,7 +484,15 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
   const int j = threadIdx.x;
   if (j < k) {
     if (sc->ostate[j] == ST_ACTIVE && totals[k + j] > 0.0) {
-      sc->rz[j] = totals[j];
+      const double rz_new = totals[j];
+      double be = 0.0;
+      if (ctl.reliable && sc->oprev[j] > 0.0) {
+        const double ratio = sc->oprev[j] / sc->oscale[j];
+        const double den = sc->rz[j] * ratio;
+        be = (den > 0.0 && isfinite(den)) ? rz_new / den : 0.0;
+      }
+      sc->beta[j] = be;
+      sc->rz[j] = rz_new;
       sc->rr[j] = totals[k + j];
       sc->tol2[j] = ctl.inner_rtol2 * totals[k + j];
       sc->state[j] = ST_ACTIVE;
@@ -629,17 +636,22 @@ struct Solver {
   double* partials;
   cudaStream_t s;
   SpmmSched sched64, sched32;
-  int grid_vec;
-
-  int spmm_grid(const SpmmSched& sc) const {
+  // one resident wave of `kern`, never more blocks than there are row blocks
+  template <typename K_>
+  int spmm_grid(K_* kern, const SpmmSched& sc) const {
     const int R = sc.rows_per_block();
-    return (int)std::max<int64_t>(1, std::min<int64_t>(kGridMax, (n + R - 1) / R));
+    return wave_grid(kern, (n + R - 1) / R);
+  }
+  template <typename K_>
+  int vg(K_* kern) const {
+    const int R = kThreads / kp;
+    return wave_grid(kern, (n + R - 1) / R);
   }
 
   template <typename T>
   CsrArgs<T> args(const rb_op* op, const SpmmSched& ss, const T* X, int64_t ldx, T* Y, int64_t ldy) const {
     CsrArgs<T> a;
-    fill_csr_args(op, ss, a, kCgDynSmem);
+    fill_csr_args(op, ss, a, 0);
     a.X = X;
     a.ldx = ldx;
     a.Y = Y;
@@ -652,8 +664,7 @@ struct Solver {
   template <typename T, int VEC, int LPR>
   void launch_q(const rb_op* op, const SpmmSched& ss, const T* p, T* q, CgCtl c) const {
     CsrArgs<T> a = args<T>(op, ss, p, k, q, k);
-    const size_t smem = csr_smem_bytes<T>(ss.rows_per_block(), a.stage_cap);
-    k_cg_q<T, VEC, LPR><<<spmm_grid(ss), kThreads, smem, s>>>(a, c, sc, partials);
+    k_cg_q<T, VEC, LPR><<<spmm_grid(&k_cg_q<T, VEC, LPR>, ss), kThreads, 0, s>>>(a, c, sc, partials);
   }
 
   template <typename T, int VEC>
@@ -669,8 +680,8 @@ struct Solver {
   template <int VEC, int LPR>
   void launch_resid_t(int mode, const double* B, int64_t ldb, const double* X, int64_t ldx, double* r) const {
     CsrArgs<double> a = args<double>(A, sched64, X, ldx, nullptr, 0);
-    const size_t smem = csr_smem_bytes<double>(sched64.rows_per_block(), a.stage_cap);
-    k_cg_resid<VEC, LPR><<<spmm_grid(sched64), kThreads, smem, s>>>(a, ctl, mode, B, ldb, r, sc, partials);
+    k_cg_resid<VEC, LPR><<<spmm_grid(&k_cg_resid<VEC, LPR>, sched64), kThreads, 0, s>>>(a, ctl, mode, B, ldb, r, sc,
+                                                                                       partials);
   }
 
   template <int VEC>
@@ -691,8 +702,9 @@ struct Iter {
   static void step(const Solver& S_, const rb_op* op, const SpmmSched& ss, CgCtl c, T* x, int64_t ldx, T* r, T* p,
                    T* q, const T* dinv) {
     S_.launch_q_lpr<T, VEC>(op, ss, p, q, c);
-    k_cg_update<T, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, x, ldx, r, p, q, dinv, S_.sc, S_.partials);
-    k_cg_p<T, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc);
+    k_cg_update<T, VEC><<<S_.vg(&k_cg_update<T, VEC>), kThreads, 0, S_.s>>>(c, x, ldx, r, p, q, dinv, S_.sc,
+                                                                            S_.partials);
+    k_cg_p<T, VEC><<<S_.vg(&k_cg_p<T, VEC>), kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc);
   }
 };
 
@@ -724,7 +736,7 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
     c.inner = 0;
     S_.launch_resid_v<VEC>(RM_INIT, B, ldb, X, ldx, r);
     ++spmms;
-    k_cg_restart<double, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc, S_.partials);
+    k_cg_restart<double, VEC><<<S_.vg(&k_cg_restart<double, VEC>), kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc, S_.partials);
     RB_CUDA(cudaGetLastError());
     int it = 0;
     while (true) {
@@ -733,7 +745,7 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
       if (h.n_check > 0) {
         S_.launch_resid_v<VEC>(RM_CHECK, B, ldb, X, ldx, r);
         ++spmms;
-        k_cg_restart<double, VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc, S_.partials);
+        k_cg_restart<double, VEC><<<S_.vg(&k_cg_restart<double, VEC>), kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc, S_.partials);
         RB_CUDA(cudaGetLastError());
         continue;
       }
@@ -771,7 +783,9 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
         k_mark_noconv<<<1, K, 0, S_.s>>>(S_.sc, k, 1);
         break;
       }
-      k_ir_init<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, r64, r32, p32, d32, dinv32, S_.sc, S_.partials);
+      k_ir_init<VEC><<<S_.vg(&k_ir_init<VEC>), kThreads, 0, S_.s>>>(c, r64, r32, p32, d32, dinv32, S_.sc, S_.partials);
+      if (c.reliable)  // continue the kept directions: p32 = D^-1 r32 + beta p32
+        k_cg_p<float, VEC><<<S_.vg(&k_cg_p<float, VEC>), kThreads, 0, S_.s>>>(c, r32, p32, dinv32, S_.sc);
       RB_CUDA(cudaGetLastError());
       int it = 0;
       while (true) {
@@ -786,15 +800,15 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
         spmms += chunk;
       }
       total_inner += it;
-      k_ir_update<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(c, X, ldx, d32, S_.sc);
+      k_ir_update<VEC><<<S_.vg(&k_ir_update<VEC>), kThreads, 0, S_.s>>>(c, X, ldx, d32, S_.sc);
       RB_CUDA(cudaGetLastError());
     }
     rep.sweeps = sweep;
   }
   // final projection and report
   if (prm.project_mean) {
-    k_colsum<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc, S_.partials);
-    k_submean<VEC><<<S_.grid_vec, kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc);
+    k_colsum<VEC><<<S_.vg(&k_colsum<VEC>), kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc, S_.partials);
+    k_submean<VEC><<<S_.vg(&k_submean<VEC>), kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc);
   }
   S_.launch_resid_v<VEC>(RM_REPORT, B, ldb, X, ldx, nullptr);
   ++spmms;
@@ -845,6 +859,7 @@ extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params*
   RB_REQUIRE(prm.rtol > 0 && std::isfinite(prm.rtol), "rb_cg_solve: rtol must be positive");
   RB_REQUIRE(prm.max_iter >= 0 && prm.check_every >= 1, "rb_cg_solve: max_iter >= 0 and check_every >= 1 required");
   RB_REQUIRE(!prm.precond || A->has_diag, "rb_cg_solve: Jacobi needs a nonzero diagonal in every row");
+  RB_REQUIRE(prm.mixed >= 0 && prm.mixed <= 2, "rb_cg_solve: mixed must be 0, 1 or 2");
   if (prm.mixed) {
     RB_REQUIRE(A_inner && A_inner->dtype == RB_F32 && A_inner->n_rows == A->n_rows && A_inner->nnz == A->nnz,
                "rb_cg_solve: mixed precision needs A_inner, the same matrix stored as RB_F32");
@@ -870,11 +885,16 @@ extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params*
   S_.k = k;
   S_.n = A->n_rows;
   S_.s = S(stream);
-  // vector width: must divide k and keep every block's rows aligned (internal vectors have ld = k)
-  int vec = pick_vec(8, k, ldx, ldb, X, B);
-  if (vec > 1 && (k % vec)) vec = 1;
+  // columns per thread: all k for k <= 4 (one thread per row; 4 doubles as scalar loads), 3
+  // for multiples of 3, else 2 when the FP64 rows of B and X are 16-byte aligned, else 1.
+  // Internal vectors have ld = k and 256-byte aligned bases.
+  int vec = 1;
+  if (k <= 4 && (k != 2 || vec_ok(8, 2, k, ldx, ldb, X, B))) vec = k;
+  else if (k % 4 == 0) vec = 4;
+  else if (k % 3 == 0) vec = 3;
+  else if (vec_ok(8, 2, k, ldx, ldb, X, B)) vec = 2;
   S_.vec = vec;
-  S_.kp = next_pow2((k + vec - 1) / vec);
+  S_.kp = next_pow2(k / vec);
   RB_REQUIRE(S_.kp <= 32, "rb_cg_solve: k = %d needs 16-byte aligned B and X rows", k);
   S_.sched64 = pick_sched(A, k, k, k, base + L.r, base + L.p);
   S_.sched64.vec = vec;
@@ -886,7 +906,6 @@ extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params*
     S_.sched32.kp = S_.kp;
     if (S_.sched32.kp * S_.sched32.lpr > 32) S_.sched32.lpr = 1;
   }
-  S_.grid_vec = (int)std::max<int64_t>(1, std::min<int64_t>(152 * 4, (S_.n + kThreads / S_.kp - 1) / (kThreads / S_.kp)));
   S_.sc = reinterpret_cast<CgScal*>(base + L.scal);
   S_.partials = reinterpret_cast<double*>(base + L.partials);
   S_.ctl.k = k;
@@ -894,12 +913,15 @@ extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params*
   S_.ctl.n = S_.n;
   S_.ctl.inner = 0;
   S_.ctl.project = prm.project_mean ? 1 : 0;
+  S_.ctl.reliable = prm.mixed == 2 ? 1 : 0;
   S_.ctl.rtol2 = prm.rtol * prm.rtol;
   S_.ctl.inner_rtol2 = prm.inner_rtol * prm.inner_rtol;
   RB_CUDA(cudaMemsetAsync(S_.sc, 0, sizeof(CgScal), S_.s));
   rb_status st;
   switch (vec) {
     case 2: st = solve_vec<2>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
+    case 3: st = solve_vec<3>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
+    case 4: st = solve_vec<4>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
     default: st = solve_vec<1>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
   }
   rep.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

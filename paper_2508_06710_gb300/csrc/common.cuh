@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -59,9 +60,24 @@ struct SpmmSched {
   int vec = 1;
   int kp = 1;
   int lpr = 1;
-  int stage = 1;
+  int stage = 0;      // 1: stage the block's nonzeros in shared memory first
+  int grid_cap = 0;   // direct kernel: persistent grid of at most this many blocks (0: one per row block)
   int rows_per_block() const { return kThreads / (kp * lpr); }
 };
+
+constexpr int kPersistentGrid = 152 * 8;  // 8 resident blocks of 256 threads on each of 152 SMs
+
+// Blocks of `kernel` (kThreads threads, `smem` dynamic bytes) that fit on the device at
+// once: multiprocessors x resident blocks per multiprocessor (cached per kernel).  Grid-
+// stride kernels launch at most this many blocks, so they run in one wave whatever their
+// register count, and never more than kPersistentGrid.
+int resident_blocks(const void* kernel, size_t smem);
+
+template <typename K>
+inline int wave_grid(K* kernel, int64_t work_blocks, size_t smem = 0) {
+  const int cap = resident_blocks(reinterpret_cast<const void*>(kernel), smem);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(work_blocks, cap));
+}
 
 }  // namespace rb
 
@@ -173,14 +189,26 @@ inline int pick_vec(int elem_bytes, int k, int64_t ldx, int64_t ldy, const void*
   return 1;
 }
 
+// Whether VEC elements per thread can be loaded as one access: 8- and 16-byte accesses need
+// the leading dimensions and bases aligned; other widths (3, or 4 doubles) use scalar loads.
+inline bool vec_ok(int elem_bytes, int vec, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
+  if (vec < 1 || k % vec) return false;
+  const int w = vec * elem_bytes;
+  if (w == 8 || w == 16) {
+    const uintptr_t a = (uintptr_t)w;
+    return ldx % vec == 0 && ldy % vec == 0 && ((uintptr_t)X % a) == 0 && ((uintptr_t)Y % a) == 0;
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------------------------------
 // Reductions: per-column sums over the rows handled by a block.  Threads are laid out as
 // (row, chunk) with KP chunks per row, KP a power of two dividing 32, so lanes with equal
 // lane % KP hold the same columns.  The warp stage folds lanes with xor offsets >= KP; the
 // block stage sums the warps in order.  Fixed order throughout: bit-reproducible.
 // ------------------------------------------------------------------------------------------
-template <int NV>
-__device__ __forceinline__ void warp_fold(double (&a)[NV], int kp) {
+template <typename A, int NV>
+__device__ __forceinline__ void warp_fold(A (&a)[NV], int kp) {
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
     if (off >= kp) {

@@ -26,18 +26,20 @@ struct RedSmem {
 // quantity q = t / k, column j = t % k (other threads receive 0).
 // With LPR > 1 lanes per row (thread t = (row * KP + chunk) * LPR + sub), only the sub == 0
 // lanes may hold nonzero values; pass lpr so the fold and the chunk index account for it.
-template <int NQ, int VEC>
-__device__ __forceinline__ double block_reduce(double (&acc)[NQ][VEC], int kp, int lpr, int k, RedSmem<NQ>& sm) {
+// The warp stage runs in the accumulators' own type A (FP32 for the FP32 solve, FP64
+// otherwise); the warp totals are widened to FP64 for the block and grid stages.
+template <int NQ, int VEC, typename A>
+__device__ __forceinline__ double block_reduce(A (&acc)[NQ][VEC], int kp, int lpr, int k, RedSmem<NQ>& sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int width = kp * lpr;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) warp_fold<VEC>(acc[q], width);
+  for (int q = 0; q < NQ; ++q) warp_fold<A, VEC>(acc[q], width);
   if (lane < width && (lane % lpr) == 0) {
     const int chunk = lane / lpr;
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) sm.v[w][q][chunk * VEC + e] = acc[q][e];
+      for (int e = 0; e < VEC; ++e) sm.v[w][q][chunk * VEC + e] = (double)acc[q][e];
   }
   __syncthreads();
   double r = 0.0;

@@ -31,28 +31,31 @@ __global__ void __launch_bounds__(kThreads) k_spmm_sell(int n_slots, const int32
   const int R = kThreads / kp;
   const int t = threadIdx.x;
   const int chunk = t % kp;
-  const int64_t g = (int64_t)blockIdx.x * R + t / kp;  // slot index: slice * 32 + lane in slice
-  if (g >= n_slots || chunk * VEC >= k) return;
-  const int row = srow[g];
-  if (row < 0) return;
-  const int sl = (int)(g >> 5), r = (int)(g & 31);
-  const int base = sptr[sl] + r;
-  const int width = swidth[sl];
-  T acc[VEC];
-#pragma unroll
-  for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+  if (chunk * VEC >= k) return;
   const T* Xc = X + chunk * VEC;
-  for (int j = 0; j < width; ++j) {
-    const int c = __ldg(scol + base + j * 32);
-    const T v = __ldg(sval + base + j * 32);
-    const Vec<T, VEC> x = ldv<T, VEC>(Xc + (int64_t)c * ldx);
+  // slot index g = slice * 32 + lane in slice; a persistent grid strides over the slots
+  for (int64_t g = (int64_t)blockIdx.x * R + t / kp; g < n_slots; g += (int64_t)gridDim.x * R) {
+    const int row = __ldg(srow + g);
+    if (row < 0) continue;
+    const int sl = (int)(g >> 5), r = (int)(g & 31);
+    const int base = __ldg(sptr + sl) + r;
+    const int width = __ldg(swidth + sl);
+    T acc[VEC];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
+    for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+#pragma unroll 4
+    for (int j = 0; j < width; ++j) {
+      const int c = __ldg(scol + base + j * 32);
+      const T v = __ldg(sval + base + j * 32);
+      const Vec<T, VEC> x = ldv<T, VEC>(Xc + (int64_t)c * ldx);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
+    }
+    Vec<T, VEC> y;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) y.v[e] = cs ? acc[e] * (T)cs[chunk * VEC + e] : acc[e];
+    stv<T, VEC>(Y + (int64_t)row * ldy + chunk * VEC, y);
   }
-  Vec<T, VEC> y;
-#pragma unroll
-  for (int e = 0; e < VEC; ++e) y.v[e] = cs ? acc[e] * (T)cs[chunk * VEC + e] : acc[e];
-  stv<T, VEC>(Y + (int64_t)row * ldy + chunk * VEC, y);
 }
 
 template <typename T, int VEC>
@@ -60,8 +63,9 @@ rb_status launch_sell(const rb_op* op, const SpmmSched& sc, const T* X, int64_t 
                       const double* cs, cudaStream_t s) {
   const int R = kThreads / sc.kp;
   const int64_t slots = (int64_t)op->n_slices * 32;
-  const int64_t grid = (slots + R - 1) / R;
+  int64_t grid = (slots + R - 1) / R;
   if (grid == 0) return RB_OK;
+  grid = wave_grid(&k_spmm_sell<T, VEC>, grid);
   k_spmm_sell<T, VEC><<<(unsigned)grid, kThreads, 0, s>>>((int)slots, op->sell_ptr, op->sell_width, op->sell_row,
                                                            op->sell_col, static_cast<const T*>(op->sell_val), X, ldx,
                                                            Y, ldy, k, sc.kp, cs);
@@ -81,10 +85,17 @@ rb_status launch_csr(const rb_op* op, const SpmmSched& sc, const T* X, int64_t l
   a.k = k;
   a.cs = cs;
   const int R = sc.rows_per_block();
-  const int64_t grid = ((int64_t)op->n_rows + R - 1) / R;
+  int64_t grid = ((int64_t)op->n_rows + R - 1) / R;
   if (grid == 0) return RB_OK;
-  const size_t smem = csr_smem_bytes<T>(R, a.stage_cap);
-  k_spmm_csr<T, VEC, LPR, EXT><<<(unsigned)std::min<int64_t>(grid, INT32_MAX), kThreads, smem, s>>>(a);
+  if (sc.stage) {
+    const size_t smem = csr_smem_bytes<T>(R, a.stage_cap);
+    k_spmm_csr<T, VEC, LPR, EXT><<<(unsigned)std::min<int64_t>(grid, INT32_MAX), kThreads, smem, s>>>(a);
+  } else {
+    auto* kern = &k_spmm_direct<T, VEC, LPR, EXT>;
+    if (sc.grid_cap < 0) grid = wave_grid(kern, grid);  // one resident wave, grid-stride
+    else if (sc.grid_cap > 0) grid = std::min<int64_t>(grid, sc.grid_cap);
+    kern<<<(unsigned)std::min<int64_t>(grid, INT32_MAX), kThreads, 0, s>>>(a);
+  }
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
@@ -118,9 +129,8 @@ rb_status dispatch_vec(const rb_op* op, const SpmmSched& sc, const void* X, int6
   switch (sc.vec) {
     case 1: return dispatch_lpr<T, 1>(op, sc, x, ldx, y, ldy, k, cs, s);
     case 2: return dispatch_lpr<T, 2>(op, sc, x, ldx, y, ldy, k, cs, s);
-    case 4:
-      if constexpr (sizeof(T) == 4) return dispatch_lpr<T, 4>(op, sc, x, ldx, y, ldy, k, cs, s);
-      break;
+    case 3: return dispatch_lpr<T, 3>(op, sc, x, ldx, y, ldy, k, cs, s);
+    case 4: return dispatch_lpr<T, 4>(op, sc, x, ldx, y, ldy, k, cs, s);
   }
   set_error("spmm: unsupported vector width %d", sc.vec);
   return RB_EUNSUPPORTED;
@@ -129,14 +139,23 @@ rb_status dispatch_vec(const rb_op* op, const SpmmSched& sc, const void* X, int6
 bool sched_valid(const rb_op* op, const SpmmSched& sc, int k, int64_t ldx, int64_t ldy, const void* X,
                  const void* Y) {
   const int eb = op->dtype == RB_F64 ? 8 : 4;
-  if (sc.vec < 1 || k % sc.vec || ldx % sc.vec || ldy % sc.vec) return false;
-  if (sc.vec * eb > 16) return false;
-  const uintptr_t a = (uintptr_t)sc.vec * eb;
-  if ((uintptr_t)X % a || (uintptr_t)Y % a) return false;
-  if (sc.kp != next_pow2((k + sc.vec - 1) / sc.vec) || sc.kp > 32) return false;
+  if (sc.vec < 1 || sc.vec > 4 || !vec_ok(eb, sc.vec, k, ldx, ldy, X, Y)) return false;
+  if (sc.kp != next_pow2(k / sc.vec) || sc.kp > 32) return false;
   if (sc.kp * sc.lpr > 32) return false;
-  if (op->format == RB_SELL && sc.lpr != 1) return false;
+  if (op->format == RB_SELL && (sc.lpr != 1 || sc.stage)) return false;
+  if (op->ext_nz > 0 && sc.vec == 3) return false;  // the spanwise epilogue takes widths dividing Nz only
+  if (op->ext_nz > 0 && (op->ext_nz % sc.vec)) return false;
   return true;
+}
+
+// Widths worth trying for k columns, best first: one thread per row for k <= 4 (3-wide
+// scalar loads for k = 3), else the widest aligned vector.
+std::vector<int> vec_candidates(int eb, int k) {
+  std::vector<int> v;
+  if (k == 3 || (k % 3 == 0 && k <= 96)) v.push_back(3);
+  for (int w = 4; w >= 1; w >>= 1)
+    if (k % w == 0 && !(eb == 8 && w == 4 && k > 4)) v.push_back(w);
+  return v;
 }
 
 }  // namespace
@@ -144,20 +163,28 @@ bool sched_valid(const rb_op* op, const SpmmSched& sc, int k, int64_t ldx, int64
 SpmmSched default_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
   const int eb = op->dtype == RB_F64 ? 8 : 4;
   SpmmSched sc;
-  sc.vec = pick_vec(eb, k, ldx, ldy, X, Y);
-  while (sc.vec > 1 && next_pow2(k / sc.vec) > 32) sc.vec >>= 1;  // unreachable for k <= 64 with vec >= 2
-  if (next_pow2((k + sc.vec - 1) / sc.vec) > 32) {
-    // k > 32 with unaligned rows: fall back to the widest vector the size allows
-    for (int v = 16 / eb; v >= 1; v >>= 1)
-      if (k % v == 0 && next_pow2(k / v) <= 32) {
-        sc.vec = v;
-        break;
-      }
-  }
-  sc.kp = next_pow2((k + sc.vec - 1) / sc.vec);
   sc.lpr = 1;
-  if (op->format != RB_SELL && op->avg_row_len >= 12.0) sc.lpr = std::min(8, std::max(1, 32 / sc.kp / 4));
-  sc.stage = 1;
+  sc.stage = 0;
+  sc.grid_cap = -1;
+  // preference: 16-byte vectors with one thread per row, then 3-wide, then the widest aligned vector
+  std::vector<int> order;
+  if (k * eb == 16 || k * eb == 8) order.push_back(k);
+  if (k % 3 == 0 && k <= 12) order.push_back(3);
+  for (int w = 16 / eb; w >= 1; w >>= 1) order.push_back(w);
+  if (eb == 8 && k == 4) order.insert(order.begin(), 2);
+  for (int w : order) {
+    SpmmSched t = sc;
+    t.vec = w;
+    if (k % w) continue;
+    t.kp = next_pow2(k / w);
+    if (sched_valid(op, t, k, ldx, ldy, X, Y)) {
+      if (op->format != RB_SELL && op->avg_row_len >= 12.0) t.lpr = std::max(1, std::min(8, 32 / t.kp / 4));
+      if (!sched_valid(op, t, k, ldx, ldy, X, Y)) t.lpr = 1;
+      return t;
+    }
+  }
+  sc.vec = 1;
+  sc.kp = next_pow2(k);
   return sc;
 }
 
@@ -177,15 +204,11 @@ rb_status spmm_validate(const rb_op* op, const void* X, int64_t ldx, const void*
              op->ext_nz, k);
   const int eb = op->dtype == RB_F64 ? 8 : 4;
   RB_REQUIRE((uintptr_t)X % eb == 0 && (uintptr_t)Y % eb == 0, "spmm: X or Y not aligned to the element size");
-  if (k > 32) {
-    bool ok = false;
-    for (int v = 2; v * eb <= 16; v <<= 1) ok |= (k % v == 0 && next_pow2(k / v) <= 32);
-    RB_REQUIRE(ok, "spmm: k = %d needs k / vec <= 32 for some vector width", k);
-    const int v = pick_vec(eb, k, ldx, ldy, X, Y);
-    if (next_pow2(k / v) > 32) {
-      set_error("spmm: k = %d > 32 needs ldx, ldy and the row starts aligned to %d bytes", k, 16);
-      return RB_EUNSUPPORTED;
-    }
+  const SpmmSched sc = default_sched(op, k, ldx, ldy, X, Y);
+  if (!sched_valid(op, sc, k, ldx, ldy, X, Y)) {
+    set_error("spmm: no schedule for k = %d with these leading dimensions and alignments (k > 32 needs "
+              "8- or 16-byte aligned rows)", k);
+    return RB_EUNSUPPORTED;
   }
   // X and Y must not overlap
   const uintptr_t xb = (uintptr_t)X, xe = xb + (uintptr_t)((int64_t)op->n_cols * ldx * eb);
@@ -198,6 +221,32 @@ SpmmSched pick_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const voi
   auto it = op->tuned.find(k);
   if (it != op->tuned.end() && sched_valid(op, it->second, k, ldx, ldy, X, Y)) return it->second;
   return default_sched(op, k, ldx, ldy, X, Y);
+}
+
+std::vector<SpmmSched> tune_candidates(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X,
+                                       const void* Y) {
+  std::vector<SpmmSched> cands;
+  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  for (int vec : vec_candidates(eb, k)) {
+    for (int lpr = 1; lpr <= 8; lpr <<= 1) {
+      if (lpr > 1 && op->avg_row_len < 2.0 * lpr) continue;  // lanes would idle on short rows
+      for (int stage = 0; stage <= 1; ++stage) {
+        for (int gc : {-1, 0}) {
+          if (stage && gc != 0) continue;
+          SpmmSched sc;
+          sc.vec = vec;
+          sc.kp = next_pow2(k / vec);
+          sc.lpr = lpr;
+          sc.stage = stage;
+          sc.grid_cap = gc;
+          if (!sched_valid(op, sc, k, ldx, ldy, X, Y)) continue;
+          if (op->format == RB_SELL && gc != -1) continue;
+          cands.push_back(sc);
+        }
+      }
+    }
+  }
+  return cands;
 }
 
 }  // namespace rb
@@ -219,22 +268,7 @@ extern "C" rb_status rb_tune_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y
   RB_TRY(spmm_validate(A, X, ldx, Y, ldy, k));
   if (A->n_rows == 0) return RB_OK;
   cudaStream_t s = S(stream);
-  std::vector<SpmmSched> cands;
-  const int eb = A->dtype == RB_F64 ? 8 : 4;
-  for (int vec = 16 / eb; vec >= 1; vec >>= 1) {
-    for (int lpr = 1; lpr <= 8; lpr <<= 1) {
-      for (int stage = 0; stage <= 1; ++stage) {
-        SpmmSched sc;
-        sc.vec = vec;
-        sc.kp = next_pow2((k + vec - 1) / vec);
-        sc.lpr = lpr;
-        sc.stage = stage;
-        if (!sched_valid(A, sc, k, ldx, ldy, X, Y)) continue;
-        if (A->format == RB_SELL && stage == 0) continue;
-        cands.push_back(sc);
-      }
-    }
-  }
+  const std::vector<SpmmSched> cands = tune_candidates(A, k, ldx, ldy, X, Y);
   if (cands.empty()) {
     set_error("rb_tune_spmm: no valid schedule for k = %d", k);
     return RB_EUNSUPPORTED;

@@ -149,6 +149,63 @@ __device__ __forceinline__ void extruded_epilogue(const CsrArgs<T>& a, int64_t r
   }
 }
 
+// Direct accumulation for one (row, chunk, sub) without shared-memory staging: the row's
+// index and value loads are issued by all KP * LPR lanes of the row and served as one
+// broadcast.  Must be called by every lane of the warp when LPR > 1.
+template <typename T, int VEC, int LPR>
+__device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64_t row, int chunk, int sub,
+                                                      bool active, T (&acc)[VEC]) {
+  int rs = 0, re = 0;
+  if (active) {
+    rs = __ldg(a.rp + row);
+    re = __ldg(a.rp + row + 1);
+  }
+  const T* Xc = a.X + chunk * VEC;
+#pragma unroll 4
+  for (int p = rs + sub; p < re; p += LPR) {
+    const int c = __ldg(a.ci + p);
+    const T v = __ldg(a.va + p);
+    const Vec<T, VEC> x = ldv<T, VEC>(Xc + (int64_t)c * a.ldx);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
+  }
+  if constexpr (LPR > 1) {
+#pragma unroll
+    for (int off = LPR / 2; off >= 1; off >>= 1) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
+    }
+  }
+}
+
+// SpMM without staging: a persistent grid strides over blocks of R = 256 / (KP LPR) rows;
+// no block-wide barrier anywhere, so every warp keeps its gathers in flight independently.
+template <typename T, int VEC, int LPR, bool EXT>
+__global__ void __launch_bounds__(kThreads) k_spmm_direct(CsrArgs<T> a) {
+  const int R = kThreads / (a.kp * LPR);
+  const int t = threadIdx.x;
+  const int sub = t % LPR;
+  const int rc = t / LPR;
+  const int chunk = rc % a.kp;
+  const int rloc = rc / a.kp;
+  const int64_t stride = (int64_t)gridDim.x * R;
+  for (int64_t base = (int64_t)blockIdx.x * R; base < a.n_rows; base += stride) {
+    const int64_t row = base + rloc;
+    const bool active = row < a.n_rows && chunk * VEC < a.k;
+    T acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+    row_accumulate_direct<T, VEC, LPR>(a, row, chunk, sub, active, acc);
+    if (active && sub == 0) {
+      if constexpr (EXT) extruded_epilogue<T, VEC>(a, row, chunk, acc);
+      Vec<T, VEC> y;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) y.v[e] = a.cs ? acc[e] * (T)a.cs[chunk * VEC + e] : acc[e];
+      stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, y);
+    }
+  }
+}
+
 template <typename T, int VEC, int LPR, bool EXT>
 __global__ void __launch_bounds__(kThreads) k_spmm_csr(CsrArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -39,7 +39,7 @@ def _solve(rb, A, B, mixed=False, x0=None, **kw):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 8])
-@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("mixed", [0, 1, 2])
 def test_cg_periodic_32cube(rb, k, mixed):
     """The 32^3 periodic correctness case, k columns of N(0,1) zero-mean right-hand sides."""
     g = W.unit_periodic_grid(W.SMALL_PERIODIC_N)
@@ -59,7 +59,7 @@ def test_cg_periodic_32cube(rb, k, mixed):
         assert all(abs(i - inf.iters) <= 2 for i, inf in zip(res.iters, infos)), (res.iters, [i.iters for i in infos])
 
 
-@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("mixed", [0, 1, 2])
 def test_cg_channel_stretched(rb, mixed):
     """Wall-bounded stretched grid: the Jacobi diagonal varies; k = 3."""
     g = W.channel_grid(40, 32, 24, gamma=1.5)
@@ -70,10 +70,16 @@ def test_cg_channel_stretched(rb, mixed):
     res, X = _solve(rb, A, B, mixed=mixed)
     assert res.status == rb.RB_OK, res
     assert np.all(_true_res(A, B, X) <= 1e-10)
-    Xr, _ = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True)
+    Xr, infos = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True)
     assert np.all(np.linalg.norm(X - Xr, axis=0) <= 1e-6 * np.linalg.norm(Xr, axis=0))
     if mixed:
         assert 2 <= res.sweeps <= 8
+    if mixed == 2:
+        # the reliable-update refinement follows the oracle's algorithm step for step
+        for j in range(B.shape[1]):
+            _, info, sweeps = ocg.ir_reliable_pcg(A, B[:, j], rtol=1e-10, inner_rtol=1e-2, project_mean=True)
+            assert abs(res.iters[j] - info.iters) <= max(5, info.iters // 20), (res.iters[j], info.iters)
+            assert res.iters[j] <= 1.3 * infos[j].iters
 
 
 def test_cg_initial_guess_and_already_converged(rb):
@@ -127,11 +133,11 @@ def test_cg_invalid_arguments(rb):
         rb.cg_solve(op, B, X, work=torch.empty(16, dtype=torch.uint8, device="cuda"))
 
 
-@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("mixed", [0, 1, 2])
 def test_cg_channel_full_size(rb, mixed):
     """192 x 128 x 96 channel Poisson problem, k = 1, in the bench's configuration: the true
-    residual reaches 1e-10 (checked on the CPU) and the solution matches the oracle's FP64
-    CG on sampled cells within the error a 1e-10 residual allows."""
+    residual, recomputed on the CPU from the returned x, reaches 1e-10 (a property that
+    holds at any size; the oracle's own solve at this size would take minutes)."""
     g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
     A = (-fvm.laplacian_direct(g)).tocsr()
     M = fvm.divergence(g)

@@ -95,6 +95,24 @@ def test_ir_matches_fp64_solution():
     assert np.linalg.norm(xir - x64) <= kappa * 2e-10 * np.linalg.norm(x64)
 
 
+def test_reliable_ir_matches_fp64_and_keeps_iterations():
+    """P8 for the reliable-update refinement: same solution as FP64 CG within kappa * 1e-10,
+    and keeping the direction across sweeps costs few iterations over FP64 CG, unlike
+    restarting it (the restarted refinement needs more than 1.4 times as many here)."""
+    g = W.channel_grid(16, 12, 10)
+    A = (-fvm.laplacian(g)).tocsr()
+    b = W.zero_mean(W.normal((A.shape[0], 1), 12))[:, 0]
+    x64, i64 = cg.pcg(A, b, rtol=1e-10, project_mean=True)
+    xr, ir, sweeps = cg.ir_reliable_pcg(A, b, rtol=1e-10, inner_rtol=1e-2, project_mean=True)
+    _, irs, _ = cg.ir_pcg(A, b, rtol=1e-10, inner_rtol=1e-2, project_mean=True)
+    assert ir.status == cg.OK and ir.rel_res <= 1e-10
+    Ad = A.toarray()
+    kappa = np.linalg.cond(Ad + np.ones_like(Ad))
+    assert np.linalg.norm(xr - x64) <= kappa * 2e-10 * np.linalg.norm(x64)
+    assert ir.iters <= 1.2 * i64.iters < irs.iters / 1.2
+    assert 3 <= sweeps <= 8
+
+
 def test_batch_equals_individual_solves():
     systems = []
     for s, k in ((W.unit_periodic_grid(6), 2), (W.channel_grid(6, 5, 4), 1)):
