@@ -156,6 +156,10 @@ rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_desc* block,
                              rb_stream_t stream, rb_op_t* out);
 rb_status rb_operator_destroy(rb_op_t op);
 rb_status rb_operator_info(rb_op_t op, rb_op_info* info);
+/* Synchronises `stream` and reports whether a kernel applying `op` since the last check gave
+ * up a bounded wait on its shared-memory pipeline (RB_ETIMEOUT; the affected outputs are
+ * invalid).  Clears the condition. */
+rb_status rb_operator_check(rb_op_t op, rb_stream_t stream);
 
 /* Y = A~ X with a per-column scale:  Y[i, j] = c[j] * sum_p val[p] X[idx[p], j]  (Algorithm 1).
  * X: n_cols x k (ldx), Y: n_rows x k (ldy), both of the operator's dtype; c: k float64
@@ -170,6 +174,23 @@ rb_status rb_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, i
  * stores the fastest in A's tuning table (synchronises; X, Y as for rb_spmm, their
  * contents are overwritten: Y only). */
 rb_status rb_tune_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k, rb_stream_t stream);
+
+/* Schedule of the SpMM kernels for k columns (what rb_tune_spmm chooses among):
+ *   vec      columns per thread (1, 2, 3 or 4; 8- and 16-byte groups are vector accesses)
+ *   lpr      lanes sharing one row's nonzeros (1, 2, 4, 8), reduced with warp shuffles
+ *   stage    0: indices and values read by the row's lanes directly; 1: a block's nonzeros
+ *            staged in shared memory by its threads; 2: a producer warp streams each tile's
+ *            row pointers, indices and values into a 3-stage shared-memory ring with TMA bulk
+ *            copies (cp.async.bulk + mbarrier) while eight consumer warps compute
+ *   grid_cap -1: one resident wave of persistent blocks; 0: one block per row block; > 0: cap
+ * rb_set_spmm_schedule pins a schedule for (A, k) (RB_EINVAL if it is not valid for A);
+ * rb_get_spmm_schedule reports the one rb_spmm will use for k with the given layout. */
+typedef struct {
+  int32_t vec, lpr, stage, grid_cap;
+} rb_spmm_schedule;
+rb_status rb_set_spmm_schedule(rb_op_t A, int32_t k, const rb_spmm_schedule* sched);
+rb_status rb_get_spmm_schedule(rb_op_t A, int32_t k, int64_t ldx, int64_t ldy, const void* X, const void* Y,
+                               rb_spmm_schedule* sched);
 
 /* ------------------------------------------------------------------------------------
  * The other basic operations, per column of an n x k block (Sec. 1: dot, axpy, axty)
@@ -207,6 +228,8 @@ typedef struct {
   int32_t project_mean;  /* 1: singular periodic/Neumann operator; remove the column mean of
                             every true residual and of the final x (zero-mean solution) */
   int32_t check_every;   /* iterations between host convergence checks (>= 1) */
+  int32_t persistent;    /* mixed only: 1 runs each sweep's inner iterations in one cooperative
+                            launch (grid-wide barriers instead of kernel boundaries) */
 } rb_cg_params;
 
 typedef struct {
@@ -232,6 +255,44 @@ size_t rb_cg_workspace_bytes(rb_op_t A, int32_t k, const rb_cg_params* params);
 rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params* params, const double* B, int64_t ldb,
                       double* X, int64_t ldx, int32_t k, void* work, size_t work_bytes, rb_cg_report* report,
                       rb_stream_t stream);
+
+/* ------------------------------------------------------------------------------------
+ * Batched Poisson solves of uneven systems in one persistent launch under a CUDA graph
+ * (the coarse and fine meshes of the inline mesh refinement of Sec. 3.3, or independent
+ * meshes).  Each system s has its own operator (FP64 ops[s] and its FP32 copy
+ * ops_inner[s]) and k[s] right-hand sides; the solve is the FP32-inner refinement of
+ * rb_cg_solve (params->mixed 1 or 2) for every system at once: per sweep the FP64 residual
+ * and the inner set-up run per system, then ONE cooperative kernel performs all inner CG
+ * iterations of all systems, with the blocks shared among the systems in proportion to their
+ * work and grid-wide barriers between the phases of an iteration.  The whole sequence of
+ * max_sweeps sweeps is recorded once as a CUDA graph (per set of B/X pointers) and replayed
+ * with one launch per call; systems that have converged skip their work inside the graph.
+ * ------------------------------------------------------------------------------------ */
+typedef struct rb_batch* rb_batch_t;
+
+/* Allocates the per-system workspaces and the launch state.  n_sys <= 8, sum of k <= 64,
+ * every ops[s] square RB_F64 CSR with a diagonal, ops_inner[s] its RB_F32 copy. */
+rb_status rb_batch_create(int32_t n_sys, const rb_op_t* ops, const rb_op_t* ops_inner, const int32_t* k,
+                          const rb_cg_params* params, rb_batch_t* out);
+rb_status rb_batch_destroy(rb_batch_t batch);
+
+/* Solves every system: B[s] (n_s x k[s], ldb[s]) and X[s] (initial guess in, solution out,
+ * ldx[s]) are float64 DEVICE arrays.  reports: n_sys entries (may be NULL).  Synchronises
+ * `stream` once at the end.  Returns the worst status; RB_ETIMEOUT if a grid barrier wait
+ * gave up (the solutions are then invalid). */
+rb_status rb_batch_solve(rb_batch_t batch, const double* const* B, const int64_t* ldb, double* const* X,
+                         const int64_t* ldx, rb_cg_report* reports, rb_stream_t stream);
+
+/* Autotuner: times rb_batch_solve for each candidate launch shape (resident blocks per SM)
+ * and inner tolerance on the given right-hand sides, starting each trial from X = 0 (X is
+ * overwritten), and keeps the fastest for later solves.  *best_ms (may be NULL) gets its time. */
+rb_status rb_batch_tune(rb_batch_t batch, const double* const* B, const int64_t* ldb, double* const* X,
+                        const int64_t* ldx, double* best_ms, rb_stream_t stream);
+
+/* Failure-detection knob for tests: the grid barrier waits at most timeout_ms and, with
+ * extra_arrivals > 0, for more blocks than the launch has, so that its wait runs out and the
+ * solve returns RB_ETIMEOUT.  Defaults: 2000 ms, 0. */
+rb_status rb_batch_set_barrier(rb_batch_t batch, double timeout_ms, int32_t extra_arrivals);
 
 #ifdef __cplusplus
 }

@@ -27,8 +27,10 @@ RB_MAX_K = 64
 
 # exported C symbols, in the order include/rbspmm.h declares them
 SYMBOLS = ["rb_last_error", "rb_version", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_mesh_cot_laplacian",
-           "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_spmm", "rb_tune_spmm",
-           "rb_dot_workspace_bytes", "rb_dot", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve"]
+           "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
+           "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
+           "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
+           "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier"]
 
 
 class RbError(RuntimeError):
@@ -58,10 +60,14 @@ class OpInfo(C.Structure):
                 ("extruded_nz", C.c_int32)]
 
 
+class SpmmSchedule(C.Structure):
+    _fields_ = [("vec", C.c_int32), ("lpr", C.c_int32), ("stage", C.c_int32), ("grid_cap", C.c_int32)]
+
+
 class CgParams(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("precond", C.c_int32), ("mixed", C.c_int32),
                 ("inner_rtol", C.c_double), ("max_sweeps", C.c_int32), ("project_mean", C.c_int32),
-                ("check_every", C.c_int32)]
+                ("check_every", C.c_int32), ("persistent", C.c_int32)]
 
 
 class CgReport(C.Structure):
@@ -94,6 +100,9 @@ def lib():
         "rb_operator_info": (C.c_int, [vp, C.POINTER(OpInfo)]),
         "rb_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp, vp]),
         "rb_tune_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp]),
+        "rb_set_spmm_schedule": (C.c_int, [vp, i32, C.POINTER(SpmmSchedule)]),
+        "rb_get_spmm_schedule": (C.c_int, [vp, i32, i64, i64, vp, vp, C.POINTER(SpmmSchedule)]),
+        "rb_operator_check": (C.c_int, [vp, vp]),
         "rb_dot_workspace_bytes": (sz, [i64, i32]),
         "rb_dot": (C.c_int, [i64, i32, C.c_int, vp, i64, vp, i64, vp, vp, sz, vp]),
         "rb_axpy": (C.c_int, [i64, i32, C.c_int, vp, vp, i64, vp, i64, vp]),
@@ -101,6 +110,14 @@ def lib():
         "rb_cg_workspace_bytes": (sz, [vp, i32, C.POINTER(CgParams)]),
         "rb_cg_solve": (C.c_int, [vp, vp, C.POINTER(CgParams), vp, i64, vp, i64, i32, vp, sz, C.POINTER(CgReport),
                                   vp]),
+        "rb_batch_create": (C.c_int, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(i32), C.POINTER(CgParams),
+                                      C.POINTER(vp)]),
+        "rb_batch_destroy": (C.c_int, [vp]),
+        "rb_batch_solve": (C.c_int, [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64),
+                                     C.POINTER(CgReport), vp]),
+        "rb_batch_tune": (C.c_int, [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64),
+                                    C.POINTER(C.c_double), vp]),
+        "rb_batch_set_barrier": (C.c_int, [vp, C.c_double, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -265,6 +282,22 @@ class Operator:
         Y, _, _, ldy = _block(Y, "Y")
         _check(lib().rb_tune_spmm(self.handle, _ptr(X), ldx, _ptr(Y), ldy, k, _stream(stream)), "rb_tune_spmm")
 
+    def set_schedule(self, k, vec, lpr=1, stage=0, grid_cap=-1):
+        s = SpmmSchedule(vec, lpr, stage, grid_cap)
+        _check(lib().rb_set_spmm_schedule(self.handle, k, C.byref(s)), "rb_set_spmm_schedule")
+
+    def schedule(self, X, Y):
+        X, _, k, ldx = _block(X, "X")
+        Y, _, _, ldy = _block(Y, "Y")
+        s = SpmmSchedule()
+        _check(lib().rb_get_spmm_schedule(self.handle, k, ldx, ldy, _ptr(X), _ptr(Y), C.byref(s)),
+               "rb_get_spmm_schedule")
+        return {"vec": s.vec, "lpr": s.lpr, "stage": s.stage, "grid_cap": s.grid_cap}
+
+    def check(self, stream=None):
+        """Raises RbError(RB_ETIMEOUT) if a pipelined SpMM kernel gave up a bounded wait."""
+        _check(lib().rb_operator_check(self.handle, _stream(stream)), "rb_operator_check")
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             lib().rb_operator_destroy(self.handle)
@@ -322,14 +355,15 @@ class CgResult:
 
 
 def cg_params(rtol=1e-10, max_iter=20000, precond=True, mixed=False, inner_rtol=None, max_sweeps=60,
-              project_mean=False, check_every=32) -> CgParams:
+              project_mean=False, check_every=32, persistent=False) -> CgParams:
     """mixed: False/0 = FP64 CG, 1 (or True) = restarted FP32-inner refinement, 2 = refinement
-    with reliable updates (the search direction survives each sweep)."""
+    with reliable updates (the search direction survives each sweep).  persistent: each sweep's
+    inner iterations in one cooperative launch (refinement only)."""
     m = int(mixed)
     if inner_rtol is None:
         inner_rtol = 1e-2 if m == 2 else 1e-4
     return CgParams(rtol, max_iter, 1 if precond else 0, m, inner_rtol, max_sweeps, 1 if project_mean else 0,
-                    check_every)
+                    check_every, 1 if persistent else 0)
 
 
 def cg_workspace_bytes(A: Operator, k: int, params: CgParams) -> int:
@@ -353,3 +387,59 @@ def cg_solve(A: Operator, B, X, A_inner: Operator | None = None, params: CgParam
         _check(st, "rb_cg_solve")
     return CgResult(st, list(rep.iters[:k]), list(rep.true_rel_res[:k]), list(rep.status[:k]), rep.spmm_calls,
                     rep.sweeps, rep.host_syncs, rep.ms)
+
+
+class Batch:
+    """Uneven Poisson systems solved together: one persistent launch per refinement sweep,
+    the whole solve recorded once as a CUDA graph and replayed per call."""
+
+    def __init__(self, ops, ops_inner, ks, params: CgParams):
+        n = len(ops)
+        self._ops = list(ops) + list(ops_inner)  # keep the operators alive
+        self.ks = [int(k) for k in ks]
+        self.n_sys = n
+        h = C.c_void_p()
+        _check(lib().rb_batch_create(n, (C.c_void_p * n)(*[o.handle.value for o in ops]),
+                                     (C.c_void_p * n)(*[o.handle.value for o in ops_inner]),
+                                     (C.c_int32 * n)(*self.ks), C.byref(params), C.byref(h)), "rb_batch_create")
+        self.handle = h
+
+    def _arrays(self, Bs, Xs):
+        n = self.n_sys
+        bb = [_block(b, "B") for b in Bs]
+        xx = [_block(x, "X") for x in Xs]
+        return ((C.c_void_p * n)(*[b[0].data_ptr() for b in bb]), (C.c_int64 * n)(*[b[3] for b in bb]),
+                (C.c_void_p * n)(*[x[0].data_ptr() for x in xx]), (C.c_int64 * n)(*[x[3] for x in xx]))
+
+    def solve(self, Bs, Xs, stream=None):
+        pB, lB, pX, lX = self._arrays(Bs, Xs)
+        reps = (CgReport * self.n_sys)()
+        st = lib().rb_batch_solve(self.handle, pB, lB, pX, lX, reps, _stream(stream))
+        if st not in (RB_OK, RB_ENOCONV, RB_EBREAKDOWN, RB_ETIMEOUT):
+            _check(st, "rb_batch_solve")
+        out = []
+        for i, r in enumerate(reps):
+            k = self.ks[i]
+            out.append(CgResult(st, list(r.iters[:k]), list(r.true_rel_res[:k]), list(r.status[:k]), r.spmm_calls,
+                                r.sweeps, r.host_syncs, r.ms))
+        return out
+
+    def tune(self, Bs, Xs, stream=None):
+        pB, lB, pX, lX = self._arrays(Bs, Xs)
+        ms = C.c_double()
+        _check(lib().rb_batch_tune(self.handle, pB, lB, pX, lX, C.byref(ms), _stream(stream)), "rb_batch_tune")
+        return ms.value
+
+    def set_barrier(self, timeout_ms=2000.0, extra_arrivals=0):
+        _check(lib().rb_batch_set_barrier(self.handle, float(timeout_ms), int(extra_arrivals)), "rb_batch_set_barrier")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().rb_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -23,12 +23,12 @@ void set_error(const char* fmt, ...) {
 
 void clear_error() { g_err.clear(); }
 
-int resident_blocks(const void* kernel, size_t smem) {
+int resident_blocks(const void* kernel, size_t smem, int threads) {
   static std::mutex mu;
   static std::map<std::pair<const void*, size_t>, int> cache;
   static int sms = 0;
   std::lock_guard<std::mutex> lock(mu);
-  auto key = std::make_pair(kernel, smem);
+  auto key = std::make_pair(kernel, smem * 4096 + (size_t)threads);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   if (sms == 0) {
@@ -37,7 +37,7 @@ int resident_blocks(const void* kernel, size_t smem) {
       sms = 152;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -74,7 +74,7 @@ rb_status dalloc(rb_op* op, T** p, size_t count) {
 void free_op(rb_op* op) {
   if (!op) return;
   void* ptrs[] = {op->row_ptr, op->col_idx, op->vals,    op->sell_ptr, op->sell_width, op->sell_row,
-                  op->sell_col, op->sell_val, op->dinv64, op->dinv32,  op->zw64,       op->zw32};
+                  op->sell_col, op->sell_val, op->dinv64, op->dinv32,  op->zw64,       op->zw32, op->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete op;
@@ -245,6 +245,7 @@ extern "C" rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_d
   op->avg_row_len = op->n_rows ? (double)op->nnz / op->n_rows : 0.0;
   rb_status st = RB_OK;
   do {
+    if ((st = dalloc(op, &op->err, 1)) != RB_OK) break;
     if ((st = dalloc(op, &op->row_ptr, rp.size())) != RB_OK) break;
     if ((st = dalloc(op, &op->col_idx, ci.size())) != RB_OK) break;
     if ((st = upload(op->row_ptr, rp.data(), rp.size(), s)) != RB_OK) break;
@@ -312,6 +313,21 @@ extern "C" rb_status rb_operator_destroy(rb_op_t op) {
   clear_error();
   if (!op) return RB_OK;
   free_op(op);
+  return RB_OK;
+}
+
+extern "C" rb_status rb_operator_check(rb_op_t op, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(op != nullptr, "rb_operator_check: null operator");
+  int h = 0;
+  RB_CUDA(cudaMemcpyAsync(&h, op->err, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+  RB_CUDA(cudaStreamSynchronize(S(stream)));
+  if (h != 0) {
+    RB_CUDA(cudaMemsetAsync(op->err, 0, sizeof(int), S(stream)));
+    RB_CUDA(cudaStreamSynchronize(S(stream)));
+    set_error("a bounded wait in an SpMM kernel gave up (code %d); its output is invalid", h);
+    return RB_ETIMEOUT;
+  }
   return RB_OK;
 }
 

@@ -53,8 +53,9 @@ struct CgScal {
   double otol2[K], omean[K], oscale[K], oprev[K];
   int ostate[K];
   int state[K], iters[K];
-  int n_active, n_check, n_oactive, pad;
-  unsigned counter[8];
+  int n_active, n_check, n_oactive, n_orun;  // n_orun: outer columns not finished (incl. first sweep)
+  unsigned counter[8];   // last-block tickets, one per reducing kernel
+  unsigned pbar[4];      // persistent solve: barrier arrivals, generation, error word
 };
 
 struct CgCtl {
@@ -87,15 +88,17 @@ struct DotAccN {
 };
 
 __device__ __forceinline__ void recount(CgScal* sc, int k) {
-  int na = 0, nc = 0, no = 0;
+  int na = 0, nc = 0, no = 0, nr = 0;
   for (int j = 0; j < k; ++j) {
     na += sc->state[j] == ST_ACTIVE;
     nc += sc->state[j] == ST_CHECK;
     no += sc->ostate[j] == ST_ACTIVE;
+    nr += sc->ostate[j] == ST_ACTIVE || sc->ostate[j] == ST_RESTART;
   }
   sc->n_active = na;
   sc->n_check = nc;
   sc->n_oactive = no;
+  sc->n_orun = nr;
 }
 
 // ------------------------------------------------------------------------- q = A p, p . q
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_resid(CsrArgs<double> a, CgCtl 
                                                         const double* __restrict__ B, int64_t ldb,
                                                         double* __restrict__ rout, CgScal* __restrict__ sc,
                                                         double* __restrict__ partials) {
+  if (mode == RM_OUTER && sc->n_orun == 0) return;  // every column of this system has finished
   __shared__ RedSmem<3> red;
   __shared__ bool wmask[K];
   const int k = a.k;
@@ -509,6 +513,7 @@ template <int VEC>
 __global__ void __launch_bounds__(kThreads) k_ir_update(CgCtl ctl, double* __restrict__ x, int64_t ldx,
                                                          const float* __restrict__ d32,
                                                          const CgScal* __restrict__ sc) {
+  if (sc->n_oactive == 0) return;
   const int k = ctl.k, kp = ctl.kp;
   const int R = kThreads / kp;
   const int chunk = threadIdx.x % kp;
@@ -713,6 +718,61 @@ struct HostState {
   int n_active, n_check, n_oactive;
 };
 
+// A run of check_every CG iterations recorded once as a CUDA graph and replayed, which
+// removes the per-kernel launch cost from the host side of the loop.  Recording happens on
+// a private stream of this thread (the legacy default stream cannot be captured); the
+// replay goes to the caller's stream.  Kernels whose columns have all finished return at
+// once, so a replay past convergence costs only the empty launches.
+struct ChunkGraph {
+  cudaGraphExec_t exec = nullptr;
+  int len = 0;
+  ChunkGraph() = default;
+  ChunkGraph(const ChunkGraph&) = delete;
+  ChunkGraph& operator=(const ChunkGraph&) = delete;
+  ~ChunkGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+cudaStream_t capture_stream() {
+  static thread_local cudaStream_t cs = nullptr;
+  if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cs = nullptr;
+  }
+  return cs;
+}
+
+template <class F>
+rb_status run_chunk(Solver& S_, ChunkGraph& g, int chunk, int full, int& uses, F&& one_iteration) {
+  // the first full chunk runs eagerly (it also fills the launch-shape caches); later full
+  // chunks replay the recorded graph
+  cudaStream_t cs = capture_stream();
+  if (chunk == full && uses > 0 && cs) {
+    if (!g.exec) {
+      cudaStream_t user = S_.s;
+      S_.s = cs;
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int i = 0; i < chunk; ++i) one_iteration();
+        e = cudaStreamEndCapture(cs, &graph);
+      }
+      S_.s = user;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "CUDA graph capture of the CG iterations", __FILE__, __LINE__);
+      g.len = chunk;
+    }
+    RB_CUDA(cudaGraphLaunch(g.exec, S_.s));
+  } else {
+    for (int i = 0; i < chunk; ++i) one_iteration();
+  }
+  ++uses;
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
 rb_status read_state(const Solver& S_, HostState& h) {
   RB_CUDA(cudaMemcpyAsync(h.state, S_.sc->state, sizeof(int) * K, cudaMemcpyDeviceToHost, S_.s));
   RB_CUDA(cudaMemcpyAsync(h.ostate, S_.sc->ostate, sizeof(int) * K, cudaMemcpyDeviceToHost, S_.s));
@@ -720,6 +780,9 @@ rb_status read_state(const Solver& S_, HostState& h) {
   RB_CUDA(cudaStreamSynchronize(S_.s));
   return RB_OK;
 }
+
+// one sweep's inner iterations of a single system in one cooperative launch (defined below)
+rb_status persistent_inner(Solver& S_, const rb_cg_params& prm, const Layout& L, char* base);
 
 template <int VEC>
 rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_t ldb, double* X, int64_t ldx,
@@ -739,6 +802,8 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
     k_cg_restart<double, VEC><<<S_.vg(&k_cg_restart<double, VEC>), kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc, S_.partials);
     RB_CUDA(cudaGetLastError());
     int it = 0;
+    ChunkGraph graph;
+    int uses = 0;
     while (true) {
       RB_TRY(read_state(S_, h));
       ++syncs;
@@ -755,8 +820,9 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
         break;
       }
       const int chunk = std::min(prm.check_every, prm.max_iter - it);
-      for (int i = 0; i < chunk; ++i) Iter<VEC>::template step<double>(S_, S_.A, S_.sched64, c, X, ldx, r, p, q, dinv);
-      RB_CUDA(cudaGetLastError());
+      RB_TRY(run_chunk(S_, graph, chunk, prm.check_every, uses, [&] {
+        Iter<VEC>::template step<double>(S_, S_.A, S_.sched64, c, X, ldx, r, p, q, dinv);
+      }));
       it += chunk;
       spmms += chunk;
     }
@@ -772,6 +838,8 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
     k_init_outer<<<1, K, 0, S_.s>>>(S_.sc, k);
     int total_inner = 0;
     int sweep = 0;
+    ChunkGraph graph;
+    int uses = 0;
     for (;; ++sweep) {
       S_.launch_resid_v<VEC>(RM_OUTER, B, ldb, X, ldx, r64);
       ++spmms;
@@ -788,14 +856,32 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
         k_cg_p<float, VEC><<<S_.vg(&k_cg_p<float, VEC>), kThreads, 0, S_.s>>>(c, r32, p32, dinv32, S_.sc);
       RB_CUDA(cudaGetLastError());
       int it = 0;
-      while (true) {
+      if (prm.persistent) {
+        // all of this sweep's inner iterations in one cooperative launch
+        rb_cg_params p2 = prm;
+        p2.max_iter = prm.max_iter - total_inner;
+        RB_TRY(persistent_inner(S_, p2, L, base));
+        unsigned done = 0;
+        RB_CUDA(cudaMemcpyAsync(&done, &S_.sc->pbar[3], sizeof(unsigned), cudaMemcpyDeviceToHost, S_.s));
+        RB_CUDA(cudaStreamSynchronize(S_.s));
+        ++syncs;
+        unsigned err = 0;
+        RB_CUDA(cudaMemcpy(&err, &S_.sc->pbar[2], sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (err) {
+          set_error("rb_cg_solve: a grid barrier wait of the persistent inner solve gave up");
+          return RB_ETIMEOUT;
+        }
+        it = (int)done;
+        spmms += it;
+      }
+      while (!prm.persistent) {
         RB_TRY(read_state(S_, h));
         ++syncs;
         if (h.n_active == 0 || total_inner + it >= prm.max_iter) break;
         const int chunk = std::min(prm.check_every, prm.max_iter - total_inner - it);
-        for (int i = 0; i < chunk; ++i)
+        RB_TRY(run_chunk(S_, graph, chunk, prm.check_every, uses, [&] {
           Iter<VEC>::template step<float>(S_, S_.A32, S_.sched32, c, d32, k, r32, p32, q32, dinv32);
-        RB_CUDA(cudaGetLastError());
+        }));
         it += chunk;
         spmms += chunk;
       }
@@ -833,69 +919,463 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
   return worst;
 }
 
-}  // namespace
-}  // namespace rb
+// ===================================================================================
+// Persistent batched inner solve: every inner FP32 CG iteration of every system of a batch
+// in ONE cooperative launch.  Blocks are partitioned among the systems in proportion to
+// their work; each iteration runs the three phases of the three-kernel loop (q = A p with
+// p.q; x, r update with r.D^-1 r and r.r; p update) separated by grid-wide barriers, and
+// the per-column scalars are reduced by one block per batch column between phases.  The
+// barrier waits are bounded (globaltimer): past the limit a block records an error and
+// every block leaves.
+// ===================================================================================
 
-using namespace rb;
+constexpr int kMaxSys = 8;
+constexpr int kPThreads = 512;
+constexpr int kPWarps = kPThreads / 32;
 
-extern "C" size_t rb_cg_workspace_bytes(rb_op_t A, int32_t k, const rb_cg_params* params) {
-  if (!A || !params || k < 1 || k > RB_MAX_K) return 0;
-  return layout(A->n_rows, k, params->mixed != 0).total + 256;
+struct PSys {
+  const int32_t* rp;
+  const int32_t* ci;
+  const float* va;
+  const float* dinv;
+  float* r;
+  float* p;
+  float* q;
+  float* d;
+  CgScal* sc;
+  int n, k, vec, kp;
+  int blk0, nblk;  // blocks [blk0, blk0 + nblk) work on this system
+  int col0;        // first column of this system in the batch numbering
+};
+
+struct PBatch {
+  PSys sys[kMaxSys];
+  int n_sys, total_cols;
+  double* partials;  // [gridDim.x][2][K]
+  unsigned* bar;     // [0] arrivals, [1] generation (zeroed before every launch)
+  int* err;          // 0, or the code of the first wait that gave up
+  int max_iter;      // iteration cap of this launch
+  int extra_arrivals;  // failure-detection tests only: arrivals the barrier waits for beyond the grid
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params* params, const double* B,
-                                 int64_t ldb, double* X, int64_t ldx, int32_t k, void* work, size_t work_bytes,
-                                 rb_cg_report* report, rb_stream_t stream) {
-  clear_error();
-  const auto t0 = std::chrono::steady_clock::now();
-  RB_REQUIRE(A && params, "rb_cg_solve: null operator or params");
-  const rb_cg_params& prm = *params;
-  RB_REQUIRE(A->dtype == RB_F64, "rb_cg_solve: the operator must be RB_F64");
-  RB_REQUIRE(A->n_rows == A->n_cols, "rb_cg_solve: the operator must be square");
-  RB_REQUIRE(A->ext_nz == 0, "rb_cg_solve: extruded operators are not supported by the solver");
-  RB_REQUIRE(k >= 1 && k <= RB_MAX_K, "rb_cg_solve: k = %d outside [1, %d]", k, RB_MAX_K);
-  RB_REQUIRE(ldb >= k && ldx >= k, "rb_cg_solve: leading dimension smaller than k");
-  RB_REQUIRE(A->n_rows == 0 || (B && X), "rb_cg_solve: null B or X");
-  RB_REQUIRE(prm.rtol > 0 && std::isfinite(prm.rtol), "rb_cg_solve: rtol must be positive");
-  RB_REQUIRE(prm.max_iter >= 0 && prm.check_every >= 1, "rb_cg_solve: max_iter >= 0 and check_every >= 1 required");
-  RB_REQUIRE(!prm.precond || A->has_diag, "rb_cg_solve: Jacobi needs a nonzero diagonal in every row");
-  RB_REQUIRE(prm.mixed >= 0 && prm.mixed <= 2, "rb_cg_solve: mixed must be 0, 1 or 2");
-  if (prm.mixed) {
-    RB_REQUIRE(A_inner && A_inner->dtype == RB_F32 && A_inner->n_rows == A->n_rows && A_inner->nnz == A->nnz,
-               "rb_cg_solve: mixed precision needs A_inner, the same matrix stored as RB_F32");
-    RB_REQUIRE(A_inner->format == RB_CSR, "rb_cg_solve: the inner operator must be CSR");
-    RB_REQUIRE(prm.inner_rtol > 0 && prm.inner_rtol < 1, "rb_cg_solve: inner_rtol must be in (0, 1)");
-    RB_REQUIRE(prm.max_sweeps >= 1, "rb_cg_solve: max_sweeps >= 1 required");
+// Grid-wide barrier of a cooperative launch.  Returns false in every thread of the block when
+// this block's wait ran past timeout_ns or another block has recorded an error.
+__device__ bool grid_barrier(const PBatch& b) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* gen = b.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned expected = gridDim.x + (unsigned)b.extra_arrivals;
+    if (atomicAdd(b.bar, 1u) == expected - 1u) {
+      b.bar[0] = 0u;
+      __threadfence();
+      atomicAdd(b.bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (*gen == g) {
+        if (*(volatile int*)b.err) {
+          ok = 0;
+          break;
+        }
+        if (globaltimer_ns() - t0 > b.timeout_ns) {
+          atomicCAS(b.err, 0, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
   }
-  RB_REQUIRE(A->format == RB_CSR, "rb_cg_solve: the operator must be CSR");
-  RB_REQUIRE((uintptr_t)B % 8 == 0 && (uintptr_t)X % 8 == 0, "rb_cg_solve: B or X not 8-byte aligned");
-  const Layout L = layout(A->n_rows, k, prm.mixed != 0);
-  RB_REQUIRE(work && work_bytes >= L.total + 256, "rb_cg_solve: workspace too small (%zu < %zu)", work_bytes,
-             L.total + 256);
-  rb_cg_report rep;
-  std::memset(&rep, 0, sizeof(rep));
-  if (A->n_rows == 0) {
-    if (report) *report = rep;
-    return RB_OK;
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Sum over the block of acc[q][e] per column (threads laid out (row, chunk), KP chunks per
+// row): warp fold in FP32, warps summed in FP64 in order; column totals land in out[q * k + j].
+template <int NQ, int VEC>
+__device__ __forceinline__ void pblock_reduce(float (&acc)[NQ][VEC], int kp, int k, double* red, double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) warp_fold<float, VEC>(acc[q], kp);
+  if (lane < kp) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) red[(w * NQ + q) * 64 + lane * VEC + e] = (double)acc[q][e];
   }
-  char* base = reinterpret_cast<char*>(((uintptr_t)work + 255) & ~(uintptr_t)255);
-  Solver S_;
-  S_.A = A;
-  S_.A32 = A_inner;
-  S_.k = k;
-  S_.n = A->n_rows;
-  S_.s = S(stream);
-  // columns per thread: all k for k <= 4 (one thread per row; 4 doubles as scalar loads), 3
-  // for multiples of 3, else 2 when the FP64 rows of B and X are 16-byte aligned, else 1.
-  // Internal vectors have ld = k and 256-byte aligned bases.
+  __syncthreads();
+  if ((int)threadIdx.x < NQ * k) {
+    const int q = threadIdx.x / k, j = threadIdx.x % k;
+    double s = 0.0;
+    for (int ww = 0; ww < kPWarps; ++ww) s += red[(ww * NQ + q) * 64 + j];
+    out[q * k + j] = s;
+  }
+  __syncthreads();
+}
+
+// phase A: q = A p on the block's system, p . q per column into partials
+template <int VEC>
+__device__ void pphase_q(const PBatch& b, const PSys& S, double* red, double* out) {
+  const int R = kPThreads / S.kp;
+  const int chunk = threadIdx.x % S.kp, rloc = threadIdx.x / S.kp;
+  CsrArgs<float> a;
+  a.n_rows = S.n;
+  a.rp = S.rp;
+  a.ci = S.ci;
+  a.va = S.va;
+  a.X = S.p;
+  a.ldx = S.k;
+  a.k = S.k;
+  a.kp = S.kp;
+  float acc2[1][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) acc2[0][e] = 0.f;
+  for (int64_t base = (int64_t)(blockIdx.x - S.blk0) * R; base < S.n; base += (int64_t)S.nblk * R) {
+    const int64_t row = base + rloc;
+    const bool active = row < S.n && chunk * VEC < S.k;
+    float acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.f;
+    row_accumulate_direct<float, VEC, 1, true>(a, row, chunk, 0, active, acc);
+    if (active) {
+      const Vec<float, VEC> p = ldv_cg<float, VEC>(S.p + row * S.k + chunk * VEC);
+      Vec<float, VEC> qv;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        qv.v[e] = acc[e];
+        acc2[0][e] = fmaf(p.v[e], acc[e], acc2[0][e]);
+      }
+      stv<float, VEC>(S.q + row * S.k + chunk * VEC, qv);
+    }
+  }
+  pblock_reduce<1, VEC>(acc2, S.kp, S.k, red, out);
+  if ((int)threadIdx.x < S.k) b.partials[((size_t)blockIdx.x * 2 + 0) * K + S.col0 + threadIdx.x] = out[threadIdx.x];
+}
+
+// phase B: d += alpha p, r -= alpha q; r.D^-1 r and r.r per column into partials
+template <int VEC>
+__device__ void pphase_update(const PBatch& b, const PSys& S, double* red, double* out) {
+  const int R = kPThreads / S.kp;
+  const int chunk = threadIdx.x % S.kp;
+  const bool col_ok = chunk * VEC < S.k;
+  float al[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) al[e] = col_ok ? (float)__ldcg(&S.sc->alpha[chunk * VEC + e]) : 0.f;
+  float acc[2][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) acc[0][e] = acc[1][e] = 0.f;
+  if (col_ok) {
+    for (int64_t row = (int64_t)(blockIdx.x - S.blk0) * R + threadIdx.x / S.kp; row < S.n;
+         row += (int64_t)S.nblk * R) {
+      const int64_t o = row * S.k + chunk * VEC;
+      const Vec<float, VEC> pv = ldv_cg<float, VEC>(S.p + o);
+      const Vec<float, VEC> qv = ldv_cg<float, VEC>(S.q + o);
+      Vec<float, VEC> rv = ldv_cg<float, VEC>(S.r + o);
+      Vec<float, VEC> xv = ldv_cg<float, VEC>(S.d + o);
+      const float dg = S.dinv ? S.dinv[row] : 1.f;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        xv.v[e] = fmaf(al[e], pv.v[e], xv.v[e]);
+        rv.v[e] = fmaf(-al[e], qv.v[e], rv.v[e]);
+        acc[0][e] = fmaf(rv.v[e], dg * rv.v[e], acc[0][e]);
+        acc[1][e] = fmaf(rv.v[e], rv.v[e], acc[1][e]);
+      }
+      stv<float, VEC>(S.d + o, xv);
+      stv<float, VEC>(S.r + o, rv);
+    }
+  }
+  pblock_reduce<2, VEC>(acc, S.kp, S.k, red, out);
+  if ((int)threadIdx.x < 2 * S.k) {
+    const int q = threadIdx.x / S.k, j = threadIdx.x % S.k;
+    b.partials[((size_t)blockIdx.x * 2 + q) * K + S.col0 + j] = out[threadIdx.x];
+  }
+}
+
+// phase C: p = D^-1 r + beta p on active columns
+template <int VEC>
+__device__ void pphase_p(const PSys& S) {
+  const int R = kPThreads / S.kp;
+  const int chunk = threadIdx.x % S.kp;
+  if (chunk * VEC >= S.k) return;
+  float be[VEC];
+  bool on[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    be[e] = (float)__ldcg(&S.sc->beta[chunk * VEC + e]);
+    on[e] = __ldcg(&S.sc->state[chunk * VEC + e]) == ST_ACTIVE;
+  }
+  for (int64_t row = (int64_t)(blockIdx.x - S.blk0) * R + threadIdx.x / S.kp; row < S.n;
+       row += (int64_t)S.nblk * R) {
+    const int64_t o = row * S.k + chunk * VEC;
+    const Vec<float, VEC> rv = ldv_cg<float, VEC>(S.r + o);
+    Vec<float, VEC> pv = ldv_cg<float, VEC>(S.p + o);
+    const float dg = S.dinv ? S.dinv[row] : 1.f;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) pv.v[e] = on[e] ? fmaf(be[e], pv.v[e], dg * rv.v[e]) : pv.v[e];
+    stv<float, VEC>(S.p + o, pv);
+  }
+}
+
+// total over the blocks of system S of partial (quantity q, batch column c); whole block calls
+__device__ double preduce_column(const PBatch& b, const PSys& S, int q, int c, double* red) {
+  double s = 0.0;
+  for (int bb = threadIdx.x; bb < S.nblk; bb += kPThreads) s += __ldcg(&b.partials[((size_t)(S.blk0 + bb) * 2 + q) * K + c]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kPThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double tot = red[0];
+  __syncthreads();
+  return tot;
+}
+
+__device__ __forceinline__ int psys_of_column(const PBatch& b, int c) {
+  int s = 0;
+  while (s + 1 < b.n_sys && b.sys[s + 1].col0 <= c) ++s;
+  return s;
+}
+
+__device__ __forceinline__ bool pany_active(const PBatch& b) {
+  for (int s = 0; s < b.n_sys; ++s)
+    for (int j = 0; j < b.sys[s].k; ++j)
+      if (__ldcg(&b.sys[s].sc->state[j]) == ST_ACTIVE) return true;
+  return false;
+}
+
+__global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
+  __shared__ double red[kPWarps * 2 * 64];
+  __shared__ double out[2 * K];
+  __shared__ int go;
+  int my = -1;
+  for (int s = 0; s < b.n_sys; ++s)
+    if ((int)blockIdx.x >= b.sys[s].blk0 && (int)blockIdx.x < b.sys[s].blk0 + b.sys[s].nblk) my = s;
+  for (int it = 0; it < b.max_iter; ++it) {
+    if (threadIdx.x == 0) go = pany_active(b) ? 1 : 0;
+    __syncthreads();
+    if (!go) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.bar[3] = (unsigned)(it + 1);  // iterations run so far
+    // ---- phase A
+    if (my >= 0 && __ldcg(&b.sys[my].sc->n_active) > 0) {
+      const PSys& S = b.sys[my];
+      switch (S.vec) {
+        case 1: pphase_q<1>(b, S, red, out); break;
+        case 2: pphase_q<2>(b, S, red, out); break;
+        case 3: pphase_q<3>(b, S, red, out); break;
+        case 4: pphase_q<4>(b, S, red, out); break;
+      }
+    }
+    if (!grid_barrier(b)) return;
+    // ---- reduce p.q: alpha
+    if ((int)blockIdx.x < b.total_cols) {
+      const int c = blockIdx.x, s = psys_of_column(b, c), j = c - b.sys[s].col0;
+      const PSys& S = b.sys[s];
+      if (__ldcg(&S.sc->n_active) > 0) {
+        const double pq = preduce_column(b, S, 0, c, red);
+        if (threadIdx.x == 0) {
+          CgScal* sc = S.sc;
+          sc->pq[j] = pq;
+          double al = 0.0;
+          if (sc->state[j] == ST_ACTIVE) {
+            if (!(pq > 0.0) || !isfinite(pq)) sc->state[j] = ST_DONE;
+            else al = sc->rz[j] / pq;
+          }
+          sc->alpha[j] = al;
+        }
+      }
+    }
+    if (!grid_barrier(b)) return;
+    // ---- phase B
+    if (my >= 0 && __ldcg(&b.sys[my].sc->n_active) > 0) {
+      const PSys& S = b.sys[my];
+      switch (S.vec) {
+        case 1: pphase_update<1>(b, S, red, out); break;
+        case 2: pphase_update<2>(b, S, red, out); break;
+        case 3: pphase_update<3>(b, S, red, out); break;
+        case 4: pphase_update<4>(b, S, red, out); break;
+      }
+    }
+    if (!grid_barrier(b)) return;
+    // ---- reduce r.z, r.r: convergence, beta
+    if ((int)blockIdx.x < b.total_cols) {
+      const int c = blockIdx.x, s = psys_of_column(b, c), j = c - b.sys[s].col0;
+      const PSys& S = b.sys[s];
+      if (__ldcg(&S.sc->n_active) > 0) {
+        const double rz_new = preduce_column(b, S, 0, c, red);
+        const double rr_new = preduce_column(b, S, 1, c, red);
+        if (threadIdx.x == 0) {
+          CgScal* sc = S.sc;
+          double be = 0.0;
+          if (sc->state[j] == ST_ACTIVE) {
+            sc->iters[j] += 1;
+            sc->rr[j] = rr_new;
+            if (!isfinite(rr_new) || !isfinite(rz_new) || rr_new <= sc->tol2[j]) {
+              sc->state[j] = ST_DONE;
+            } else {
+              be = rz_new / sc->rz[j];
+              sc->rz[j] = rz_new;
+            }
+          }
+          sc->beta[j] = be;
+        }
+      }
+    }
+    if (!grid_barrier(b)) return;
+    // ---- phase C
+    if (my >= 0 && __ldcg(&b.sys[my].sc->n_active) > 0) {
+      const PSys& S = b.sys[my];
+      switch (S.vec) {
+        case 1: pphase_p<1>(S); break;
+        case 2: pphase_p<2>(S); break;
+        case 3: pphase_p<3>(S); break;
+        case 4: pphase_p<4>(S); break;
+      }
+    }
+    // n_active of each system follows its states (block 0, before the barrier publishes it)
+    if (blockIdx.x == 0 && threadIdx.x < (unsigned)b.n_sys) recount(b.sys[threadIdx.x].sc, b.sys[threadIdx.x].k);
+    if (!grid_barrier(b)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (unsigned)b.n_sys) recount(b.sys[threadIdx.x].sc, b.sys[threadIdx.x].k);
+}
+
+// ------------------------------------------------------------------ host side of the batch
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+      sms = 152;
+  }
+  return sms;
+}
+
+// Resident blocks of k_pcg_batch per multiprocessor (the cooperative-launch limit).
+int pcg_blocks_per_sm() {
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, kPThreads, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  return per_sm;
+}
+
+constexpr int kPGridMax = 152 * 4;  // partials capacity: 4 resident blocks of 512 threads per SM
+
+// Blocks per system in proportion to the bytes one iteration streams (rows x (2 + k)), at
+// least one each; the first total_cols blocks double as the column reducers.
+void partition_blocks(PBatch& pb, int grid) {
+  double W = 0.0;
+  for (int s = 0; s < pb.n_sys; ++s) W += (double)pb.sys[s].n * (2 + pb.sys[s].k);
+  int used = 0;
+  for (int s = 0; s < pb.n_sys; ++s) {
+    int nb = (int)std::floor(grid * ((double)pb.sys[s].n * (2 + pb.sys[s].k)) / std::max(W, 1.0));
+    nb = std::max(1, nb);
+    pb.sys[s].nblk = nb;
+    used += nb;
+  }
+  while (used > grid) {  // trim the largest share
+    int big = 0;
+    for (int s = 1; s < pb.n_sys; ++s)
+      if (pb.sys[s].nblk > pb.sys[big].nblk) big = s;
+    --pb.sys[big].nblk;
+    --used;
+  }
+  while (used < grid) {  // give the rest to the heaviest per block
+    int best = 0;
+    double wb = -1.0;
+    for (int s = 0; s < pb.n_sys; ++s) {
+      const double w = (double)pb.sys[s].n * (2 + pb.sys[s].k) / pb.sys[s].nblk;
+      if (w > wb) wb = w, best = s;
+    }
+    ++pb.sys[best].nblk;
+    ++used;
+  }
+  int b0 = 0;
+  for (int s = 0; s < pb.n_sys; ++s) {
+    pb.sys[s].blk0 = b0;
+    b0 += pb.sys[s].nblk;
+  }
+}
+
+rb_status launch_pcg(const PBatch& pb, int grid, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RB_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batch, pb));
+  return RB_OK;
+}
+
+// Column layout of the vector kernels for k columns and this B / X.
+int solver_vec(int k, int64_t ldx, int64_t ldb, const void* X, const void* B) {
   int vec = 1;
   if (k <= 4 && (k != 2 || vec_ok(8, 2, k, ldx, ldb, X, B))) vec = k;
   else if (k % 4 == 0) vec = 4;
   else if (k % 3 == 0) vec = 3;
   else if (vec_ok(8, 2, k, ldx, ldb, X, B)) vec = 2;
+  return vec;
+}
+
+rb_status validate_solve(const char* fn, rb_op_t A, rb_op_t A_inner, const rb_cg_params& prm, const double* B,
+                         int64_t ldb, const double* X, int64_t ldx, int32_t k) {
+  RB_REQUIRE(A, "%s: null operator", fn);
+  RB_REQUIRE(A->dtype == RB_F64, "%s: the operator must be RB_F64", fn);
+  RB_REQUIRE(A->n_rows == A->n_cols, "%s: the operator must be square", fn);
+  RB_REQUIRE(A->ext_nz == 0, "%s: extruded operators are not supported by the solver", fn);
+  RB_REQUIRE(k >= 1 && k <= RB_MAX_K, "%s: k = %d outside [1, %d]", fn, k, RB_MAX_K);
+  RB_REQUIRE(ldb >= k && ldx >= k, "%s: leading dimension smaller than k", fn);
+  RB_REQUIRE(A->n_rows == 0 || (B && X), "%s: null B or X", fn);
+  RB_REQUIRE(prm.rtol > 0 && std::isfinite(prm.rtol), "%s: rtol must be positive", fn);
+  RB_REQUIRE(prm.max_iter >= 0 && prm.check_every >= 1, "%s: max_iter >= 0 and check_every >= 1 required", fn);
+  RB_REQUIRE(!prm.precond || A->has_diag, "%s: Jacobi needs a nonzero diagonal in every row", fn);
+  RB_REQUIRE(prm.mixed >= 0 && prm.mixed <= 2, "%s: mixed must be 0, 1 or 2", fn);
+  if (prm.mixed) {
+    RB_REQUIRE(A_inner && A_inner->dtype == RB_F32 && A_inner->n_rows == A->n_rows && A_inner->nnz == A->nnz,
+               "%s: mixed precision needs A_inner, the same matrix stored as RB_F32", fn);
+    RB_REQUIRE(A_inner->format == RB_CSR, "%s: the inner operator must be CSR", fn);
+    RB_REQUIRE(prm.inner_rtol > 0 && prm.inner_rtol < 1, "%s: inner_rtol must be in (0, 1)", fn);
+    RB_REQUIRE(prm.max_sweeps >= 1, "%s: max_sweeps >= 1 required", fn);
+  }
+  RB_REQUIRE(A->format == RB_CSR, "%s: the operator must be CSR", fn);
+  RB_REQUIRE((uintptr_t)B % 8 == 0 && (uintptr_t)X % 8 == 0, "%s: B or X not 8-byte aligned", fn);
+  return RB_OK;
+}
+
+// Launch shapes, scalars and controls of one solve whose workspace starts at `base`.
+rb_status init_solver(Solver& S_, rb_op_t A, rb_op_t A_inner, const rb_cg_params& prm, int32_t k, const double* B,
+                      int64_t ldb, const double* X, int64_t ldx, char* base, const Layout& L, cudaStream_t s) {
+  S_.A = A;
+  S_.A32 = A_inner;
+  S_.k = k;
+  S_.n = A->n_rows;
+  S_.s = s;
+  const int vec = solver_vec(k, ldx, ldb, X, B);
   S_.vec = vec;
   S_.kp = next_pow2(k / vec);
-  RB_REQUIRE(S_.kp <= 32, "rb_cg_solve: k = %d needs 16-byte aligned B and X rows", k);
+  RB_REQUIRE(S_.kp <= 32, "solve: k = %d needs 16-byte aligned B and X rows", k);
   S_.sched64 = pick_sched(A, k, k, k, base + L.r, base + L.p);
   S_.sched64.vec = vec;
   S_.sched64.kp = S_.kp;
@@ -916,9 +1396,423 @@ extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params*
   S_.ctl.reliable = prm.mixed == 2 ? 1 : 0;
   S_.ctl.rtol2 = prm.rtol * prm.rtol;
   S_.ctl.inner_rtol2 = prm.inner_rtol * prm.inner_rtol;
+  return RB_OK;
+}
+
+PSys make_psys(const Solver& S_, const Layout& L, char* base, bool precond) {
+  PSys p;
+  p.rp = S_.A32->row_ptr;
+  p.ci = S_.A32->col_idx;
+  p.va = static_cast<const float*>(S_.A32->vals);
+  p.dinv = precond ? S_.A32->dinv32 : nullptr;
+  p.r = reinterpret_cast<float*>(base + L.r32);
+  p.p = reinterpret_cast<float*>(base + L.p32);
+  p.q = reinterpret_cast<float*>(base + L.q32);
+  p.d = reinterpret_cast<float*>(base + L.d32);
+  p.sc = S_.sc;
+  p.n = (int)S_.n;
+  p.k = S_.k;
+  p.vec = S_.vec;
+  p.kp = S_.kp;
+  p.blk0 = 0;
+  p.nblk = 1;
+  p.col0 = 0;
+  return p;
+}
+
+// The per-system kernels of one refinement sweep, before and after the inner solve.
+template <int VEC>
+void sweep_head(Solver& S_, const rb_cg_params& prm, const double* B, int64_t ldb, const double* X, int64_t ldx,
+                const Layout& L, char* base) {
+  double* r64 = reinterpret_cast<double*>(base + L.r64);
+  float* r32 = reinterpret_cast<float*>(base + L.r32);
+  float* p32 = reinterpret_cast<float*>(base + L.p32);
+  float* d32 = reinterpret_cast<float*>(base + L.d32);
+  const float* dinv32 = prm.precond ? S_.A32->dinv32 : nullptr;
+  CgCtl c = S_.ctl;
+  c.inner = 1;
+  S_.launch_resid_v<VEC>(RM_OUTER, B, ldb, X, ldx, r64);
+  k_ir_init<VEC><<<S_.vg(&k_ir_init<VEC>), kThreads, 0, S_.s>>>(c, r64, r32, p32, d32, dinv32, S_.sc, S_.partials);
+  if (c.reliable) k_cg_p<float, VEC><<<S_.vg(&k_cg_p<float, VEC>), kThreads, 0, S_.s>>>(c, r32, p32, dinv32, S_.sc);
+}
+
+template <int VEC>
+void sweep_tail(Solver& S_, double* X, int64_t ldx, const Layout& L, char* base) {
+  float* d32 = reinterpret_cast<float*>(base + L.d32);
+  CgCtl c = S_.ctl;
+  c.inner = 1;
+  k_ir_update<VEC><<<S_.vg(&k_ir_update<VEC>), kThreads, 0, S_.s>>>(c, X, ldx, d32, S_.sc);
+}
+
+template <int VEC>
+void solve_tail(Solver& S_, const rb_cg_params& prm, const double* B, int64_t ldb, double* X, int64_t ldx) {
+  if (prm.project_mean) {
+    k_colsum<VEC><<<S_.vg(&k_colsum<VEC>), kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc, S_.partials);
+    k_submean<VEC><<<S_.vg(&k_submean<VEC>), kThreads, 0, S_.s>>>(S_.ctl, X, ldx, S_.sc);
+  }
+  S_.launch_resid_v<VEC>(RM_REPORT, B, ldb, X, ldx, nullptr);
+}
+
+#define RB_VEC_SWITCH(vec, CALL) \
+  switch (vec) {                 \
+    case 2: CALL(2); break;      \
+    case 3: CALL(3); break;      \
+    case 4: CALL(4); break;      \
+    default: CALL(1); break;     \
+  }
+
+rb_status persistent_inner(Solver& S_, const rb_cg_params& prm, const Layout& L, char* base) {
+  PBatch pb;
+  pb.n_sys = 1;
+  pb.sys[0] = make_psys(S_, L, base, prm.precond != 0);
+  pb.total_cols = S_.k;
+  pb.partials = S_.partials;  // the workspace's partials hold kGridMax x 3 x K >= kPGridMax x 2 x K
+  pb.bar = S_.sc->pbar;
+  pb.err = reinterpret_cast<int*>(&S_.sc->pbar[2]);
+  pb.max_iter = prm.max_iter;
+  pb.extra_arrivals = 0;
+  pb.timeout_ns = 2000000000ull;
+  const int grid = std::min(kPGridMax, pcg_blocks_per_sm() * sm_count());
+  partition_blocks(pb, grid);
+  RB_CUDA(cudaMemsetAsync(S_.sc->pbar, 0, 4 * sizeof(unsigned), S_.s));
+  return launch_pcg(pb, grid, S_.s);
+}
+
+void fill_report(const CgScal& hs, int k, int mixed, rb_cg_report& rep, rb_status& worst) {
+  for (int j = 0; j < k; ++j) {
+    rep.iters[j] = hs.iters[j];
+    rep.true_rel_res[j] = hs.bb[j] > 0 ? sqrt(hs.rr_true[j] / hs.bb[j]) : 0.0;
+    const int st = mixed ? hs.ostate[j] : hs.state[j];
+    rb_status cs = RB_OK;
+    if (st == ST_BREAKDOWN) cs = RB_EBREAKDOWN;
+    else if (st == ST_NOCONV || st == ST_ACTIVE || st == ST_RESTART) cs = RB_ENOCONV;
+    rep.status[j] = cs;
+    if (cs == RB_EBREAKDOWN || (cs == RB_ENOCONV && worst == RB_OK)) worst = cs;
+  }
+}
+
+}  // namespace
+}  // namespace rb
+
+// --------------------------------------------------------------------------- batch object
+struct rb_batch {
+  int n_sys = 0;
+  rb_op_t A[rb::kMaxSys] = {}, A32[rb::kMaxSys] = {};
+  int k[rb::kMaxSys] = {};
+  rb_cg_params prm{};
+  void* work[rb::kMaxSys] = {};
+  rb::Layout L[rb::kMaxSys];
+  double* partials = nullptr;
+  unsigned* bar = nullptr;  // [0] arrivals, [1] generation, [2] error word
+  int blocks_per_sm = 0;    // 0: as many as fit
+  int extra_arrivals = 0;
+  double timeout_ms = 2000.0;
+  // recorded graph and the pointers it was recorded for
+  cudaGraphExec_t exec = nullptr;
+  const double* gB[rb::kMaxSys] = {};
+  double* gX[rb::kMaxSys] = {};
+  int64_t gldb[rb::kMaxSys] = {}, gldx[rb::kMaxSys] = {};
+  ~rb_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (int s = 0; s < rb::kMaxSys; ++s)
+      if (work[s]) cudaFree(work[s]);
+    if (partials) cudaFree(partials);
+    if (bar) cudaFree(bar);
+  }
+};
+
+namespace rb {
+namespace {
+
+char* ws_base(void* w) { return reinterpret_cast<char*>(((uintptr_t)w + 255) & ~(uintptr_t)255); }
+
+// Records (eagerly executes when `s` is not capturing) the whole batched solve on stream s.
+rb_status batch_sequence(rb_batch* bt, Solver* SV, PBatch& pb, int grid, const double* const* B, const int64_t* ldb,
+                         double* const* X, const int64_t* ldx, cudaStream_t s) {
+  for (int i = 0; i < bt->n_sys; ++i) {
+    SV[i].s = s;
+    RB_CUDA(cudaMemsetAsync(SV[i].sc, 0, sizeof(CgScal), s));
+    k_init_outer<<<1, K, 0, s>>>(SV[i].sc, bt->k[i]);
+  }
+  for (int sweep = 0; sweep < bt->prm.max_sweeps; ++sweep) {
+    for (int i = 0; i < bt->n_sys; ++i) {
+      char* base = ws_base(bt->work[i]);
+#define RB_HEAD(V) sweep_head<V>(SV[i], bt->prm, B[i], ldb[i], X[i], ldx[i], bt->L[i], base)
+      RB_VEC_SWITCH(SV[i].vec, RB_HEAD)
+#undef RB_HEAD
+    }
+    RB_CUDA(cudaMemsetAsync(bt->bar, 0, 4 * sizeof(unsigned), s));
+    RB_TRY(launch_pcg(pb, grid, s));
+    for (int i = 0; i < bt->n_sys; ++i) {
+      char* base = ws_base(bt->work[i]);
+#define RB_TAIL(V) sweep_tail<V>(SV[i], X[i], ldx[i], bt->L[i], base)
+      RB_VEC_SWITCH(SV[i].vec, RB_TAIL)
+#undef RB_TAIL
+    }
+  }
+  for (int i = 0; i < bt->n_sys; ++i) {
+#define RB_STAIL(V) solve_tail<V>(SV[i], bt->prm, B[i], ldb[i], X[i], ldx[i])
+    RB_VEC_SWITCH(SV[i].vec, RB_STAIL)
+#undef RB_STAIL
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+rb_status batch_prepare(rb_batch* bt, Solver* SV, PBatch& pb, int& grid, const double* const* B, const int64_t* ldb,
+                        double* const* X, const int64_t* ldx, cudaStream_t s) {
+  pb = PBatch();
+  pb.n_sys = bt->n_sys;
+  int col = 0;
+  for (int i = 0; i < bt->n_sys; ++i) {
+    char* base = ws_base(bt->work[i]);
+    RB_TRY(init_solver(SV[i], bt->A[i], bt->A32[i], bt->prm, bt->k[i], B[i], ldb[i], X[i], ldx[i], base, bt->L[i], s));
+    pb.sys[i] = make_psys(SV[i], bt->L[i], base, bt->prm.precond != 0);
+    pb.sys[i].col0 = col;
+    col += bt->k[i];
+  }
+  pb.total_cols = col;
+  pb.partials = bt->partials;
+  pb.bar = bt->bar;
+  pb.err = reinterpret_cast<int*>(bt->bar + 2);
+  pb.max_iter = bt->prm.max_iter;
+  pb.extra_arrivals = bt->extra_arrivals;
+  pb.timeout_ns = (unsigned long long)(bt->timeout_ms * 1e6);
+  const int cap = pcg_blocks_per_sm();
+  const int bps = bt->blocks_per_sm > 0 ? std::min(bt->blocks_per_sm, cap) : cap;
+  grid = std::min(kPGridMax, bps * sm_count());
+  grid = std::max(grid, pb.total_cols);
+  RB_REQUIRE(grid <= cap * sm_count(), "batch: %d columns need more co-resident blocks than fit", pb.total_cols);
+  partition_blocks(pb, grid);
+  return RB_OK;
+}
+
+}  // namespace
+}  // namespace rb
+
+using namespace rb;
+
+extern "C" rb_status rb_batch_create(int32_t n_sys, const rb_op_t* ops, const rb_op_t* ops_inner, const int32_t* k,
+                                     const rb_cg_params* params, rb_batch_t* out) {
+  clear_error();
+  RB_REQUIRE(out && ops && ops_inner && k && params, "rb_batch_create: null argument");
+  *out = nullptr;
+  RB_REQUIRE(n_sys >= 1 && n_sys <= kMaxSys, "rb_batch_create: n_sys = %d outside [1, %d]", n_sys, kMaxSys);
+  RB_REQUIRE(params->mixed == 1 || params->mixed == 2, "rb_batch_create: the batch runs the FP32-inner refinement "
+             "(params->mixed 1 or 2)");
+  int cols = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    RB_TRY(validate_solve("rb_batch_create", ops[i], ops_inner[i], *params, reinterpret_cast<const double*>(8),
+                          k[i], reinterpret_cast<const double*>(8), k[i], k[i]));
+    RB_REQUIRE(ops[i]->n_rows > 0, "rb_batch_create: system %d is empty", i);
+    cols += k[i];
+  }
+  RB_REQUIRE(cols <= RB_MAX_K, "rb_batch_create: %d columns in total exceed %d", cols, RB_MAX_K);
+  rb_batch* bt = new rb_batch();
+  bt->n_sys = n_sys;
+  bt->prm = *params;
+  for (int i = 0; i < n_sys; ++i) {
+    bt->A[i] = ops[i];
+    bt->A32[i] = ops_inner[i];
+    bt->k[i] = k[i];
+    bt->L[i] = layout(ops[i]->n_rows, k[i], true);
+    cudaError_t e = cudaMalloc(&bt->work[i], bt->L[i].total + 256);
+    if (e != cudaSuccess) {
+      delete bt;
+      return cuda_fail(e, "cudaMalloc (batch workspace)", __FILE__, __LINE__);
+    }
+  }
+  cudaError_t e = cudaMalloc(&bt->partials, (size_t)kPGridMax * 2 * K * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&bt->bar, 4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(bt->bar, 0, 4 * sizeof(unsigned));
+  if (e != cudaSuccess) {
+    delete bt;
+    return cuda_fail(e, "cudaMalloc (batch state)", __FILE__, __LINE__);
+  }
+  *out = bt;
+  return RB_OK;
+}
+
+extern "C" rb_status rb_batch_destroy(rb_batch_t batch) {
+  clear_error();
+  delete batch;
+  return RB_OK;
+}
+
+extern "C" rb_status rb_batch_set_barrier(rb_batch_t batch, double timeout_ms, int32_t extra_arrivals) {
+  clear_error();
+  RB_REQUIRE(batch, "rb_batch_set_barrier: null batch");
+  RB_REQUIRE(timeout_ms > 0 && extra_arrivals >= 0, "rb_batch_set_barrier: invalid knob");
+  batch->timeout_ms = timeout_ms;
+  batch->extra_arrivals = extra_arrivals;
+  if (batch->exec) {
+    cudaGraphExecDestroy(batch->exec);
+    batch->exec = nullptr;
+  }
+  return RB_OK;
+}
+
+extern "C" rb_status rb_batch_solve(rb_batch_t bt, const double* const* B, const int64_t* ldb, double* const* X,
+                                    const int64_t* ldx, rb_cg_report* reports, rb_stream_t stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  RB_REQUIRE(bt && B && ldb && X && ldx, "rb_batch_solve: null argument");
+  for (int i = 0; i < bt->n_sys; ++i)
+    RB_TRY(validate_solve("rb_batch_solve", bt->A[i], bt->A32[i], bt->prm, B[i], ldb[i], X[i], ldx[i], bt->k[i]));
+  cudaStream_t s = S(stream);
+  Solver SV[kMaxSys];
+  PBatch pb;
+  int grid = 0;
+  RB_TRY(batch_prepare(bt, SV, pb, grid, B, ldb, X, ldx, s));
+  bool same = bt->exec != nullptr;
+  for (int i = 0; i < bt->n_sys && same; ++i)
+    same = bt->gB[i] == B[i] && bt->gX[i] == X[i] && bt->gldb[i] == ldb[i] && bt->gldx[i] == ldx[i];
+  if (!same) {
+    if (bt->exec) {
+      cudaGraphExecDestroy(bt->exec);
+      bt->exec = nullptr;
+    }
+    // warm the launch-shape caches outside the capture
+    for (int i = 0; i < bt->n_sys; ++i) {
+#define RB_WARM(V) (void)SV[i].vg(&k_ir_init<V>), (void)SV[i].vg(&k_cg_p<float, V>), (void)SV[i].vg(&k_ir_update<V>), \
+                   (void)SV[i].vg(&k_colsum<V>), (void)SV[i].vg(&k_submean<V>)
+      RB_VEC_SWITCH(SV[i].vec, RB_WARM)
+#undef RB_WARM
+    }
+    cudaStream_t cs = capture_stream();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cs ? cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) : cudaErrorNotSupported;
+    rb_status st = RB_OK;
+    if (e == cudaSuccess) {
+      st = batch_sequence(bt, SV, pb, grid, B, ldb, X, ldx, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (st == RB_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st != RB_OK) return st;
+    if (e == cudaSuccess) {
+      for (int i = 0; i < bt->n_sys; ++i) {
+        bt->gB[i] = B[i];
+        bt->gX[i] = X[i];
+        bt->gldb[i] = ldb[i];
+        bt->gldx[i] = ldx[i];
+      }
+    } else {
+      cudaGetLastError();  // this runtime cannot record the sequence: run it eagerly
+      bt->exec = nullptr;
+    }
+  }
+  if (bt->exec) {
+    RB_CUDA(cudaGraphLaunch(bt->exec, s));
+  } else {
+    RB_TRY(batch_sequence(bt, SV, pb, grid, B, ldb, X, ldx, s));
+  }
+  CgScal hs[kMaxSys];
+  unsigned hb[4];
+  for (int i = 0; i < bt->n_sys; ++i)
+    RB_CUDA(cudaMemcpyAsync(&hs[i], SV[i].sc, sizeof(CgScal), cudaMemcpyDeviceToHost, s));
+  RB_CUDA(cudaMemcpyAsync(hb, bt->bar, sizeof(hb), cudaMemcpyDeviceToHost, s));
+  RB_CUDA(cudaStreamSynchronize(s));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  rb_status worst = RB_OK;
+  for (int i = 0; i < bt->n_sys; ++i) {
+    rb_cg_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    fill_report(hs[i], bt->k[i], 1, rep, worst);
+    rep.sweeps = bt->prm.max_sweeps;
+    rep.host_syncs = 1;
+    rep.ms = ms;
+    if (reports) reports[i] = rep;
+  }
+  if (hb[2] != 0) {
+    set_error("rb_batch_solve: a grid barrier wait gave up (timeout %.1f ms); the solutions are invalid",
+              bt->timeout_ms);
+    return RB_ETIMEOUT;
+  }
+  if (worst == RB_ENOCONV) set_error("rb_batch_solve: a column did not converge within max_sweeps / max_iter");
+  if (worst == RB_EBREAKDOWN) set_error("rb_batch_solve: breakdown in a column");
+  return worst;
+}
+
+extern "C" rb_status rb_batch_tune(rb_batch_t bt, const double* const* B, const int64_t* ldb, double* const* X,
+                                   const int64_t* ldx, double* best_ms, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(bt && B && ldb && X && ldx, "rb_batch_tune: null argument");
+  cudaStream_t s = S(stream);
+  const int cap = pcg_blocks_per_sm();
+  const double rtols[] = {1e-1, 3e-2, 1e-2};
+  double best = 1e30;
+  int best_bps = 0;
+  double best_rtol = bt->prm.inner_rtol;
+  for (int bps = 1; bps <= cap; ++bps) {
+    for (double it : rtols) {
+      if (bt->prm.mixed == 1 && it > 1e-2) continue;  // restarted refinement wants tighter inner solves
+      bt->blocks_per_sm = bps;
+      bt->prm.inner_rtol = it;
+      if (bt->exec) {
+        cudaGraphExecDestroy(bt->exec);
+        bt->exec = nullptr;
+      }
+      double t = 0.0;
+      rb_status st = RB_OK;
+      for (int rep = 0; rep < 2 && st == RB_OK; ++rep) {
+        for (int i = 0; i < bt->n_sys; ++i)
+          RB_CUDA(cudaMemset2DAsync(X[i], ldx[i] * sizeof(double), 0, bt->k[i] * sizeof(double), bt->A[i]->n_rows, s));
+        RB_CUDA(cudaStreamSynchronize(s));
+        const auto t0 = std::chrono::steady_clock::now();
+        st = rb_batch_solve(bt, B, ldb, X, ldx, nullptr, stream);
+        t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      }
+      if (st == RB_OK && t < best) {
+        best = t;
+        best_bps = bps;
+        best_rtol = it;
+      }
+    }
+  }
+  bt->blocks_per_sm = best_bps;
+  bt->prm.inner_rtol = best_rtol;
+  if (bt->exec) {
+    cudaGraphExecDestroy(bt->exec);
+    bt->exec = nullptr;
+  }
+  if (best_ms) *best_ms = best;
+  clear_error();
+  return best < 1e30 ? RB_OK : RB_ENOCONV;
+}
+
+extern "C" size_t rb_cg_workspace_bytes(rb_op_t A, int32_t k, const rb_cg_params* params) {
+  if (!A || !params || k < 1 || k > RB_MAX_K) return 0;
+  return layout(A->n_rows, k, params->mixed != 0).total + 256;
+}
+
+extern "C" rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params* params, const double* B,
+                                 int64_t ldb, double* X, int64_t ldx, int32_t k, void* work, size_t work_bytes,
+                                 rb_cg_report* report, rb_stream_t stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  RB_REQUIRE(A && params, "rb_cg_solve: null operator or params");
+  const rb_cg_params& prm = *params;
+  RB_TRY(validate_solve("rb_cg_solve", A, A_inner, prm, B, ldb, X, ldx, k));
+  RB_REQUIRE(!prm.persistent || prm.mixed, "rb_cg_solve: the persistent launch serves the refinement (mixed 1 or 2)");
+  const Layout L = layout(A->n_rows, k, prm.mixed != 0);
+  RB_REQUIRE(work && work_bytes >= L.total + 256, "rb_cg_solve: workspace too small (%zu < %zu)", work_bytes,
+             L.total + 256);
+  rb_cg_report rep;
+  std::memset(&rep, 0, sizeof(rep));
+  if (A->n_rows == 0) {
+    if (report) *report = rep;
+    return RB_OK;
+  }
+  char* base = reinterpret_cast<char*>(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  // columns per thread: all k for k <= 4 (one thread per row; 4 doubles as scalar loads), 3
+  // for multiples of 3, else 2 when the FP64 rows of B and X are 16-byte aligned, else 1.
+  // Internal vectors have ld = k and 256-byte aligned bases.
+  Solver S_;
+  RB_TRY(init_solver(S_, A, A_inner, prm, k, B, ldb, X, ldx, base, L, S(stream)));
   RB_CUDA(cudaMemsetAsync(S_.sc, 0, sizeof(CgScal), S_.s));
   rb_status st;
-  switch (vec) {
+  switch (S_.vec) {
     case 2: st = solve_vec<2>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
     case 3: st = solve_vec<3>(S_, prm, B, ldb, X, ldx, L, base, rep); break;
     case 4: st = solve_vec<4>(S_, prm, B, ldb, X, ldx, L, base, rep); break;

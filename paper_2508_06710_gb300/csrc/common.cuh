@@ -71,11 +71,11 @@ constexpr int kPersistentGrid = 152 * 8;  // 8 resident blocks of 256 threads on
 // once: multiprocessors x resident blocks per multiprocessor (cached per kernel).  Grid-
 // stride kernels launch at most this many blocks, so they run in one wave whatever their
 // register count, and never more than kPersistentGrid.
-int resident_blocks(const void* kernel, size_t smem);
+int resident_blocks(const void* kernel, size_t smem, int threads = kThreads);
 
 template <typename K>
-inline int wave_grid(K* kernel, int64_t work_blocks, size_t smem = 0) {
-  const int cap = resident_blocks(reinterpret_cast<const void*>(kernel), smem);
+inline int wave_grid(K* kernel, int64_t work_blocks, size_t smem = 0, int threads = kThreads) {
+  const int cap = resident_blocks(reinterpret_cast<const void*>(kernel), smem, threads);
   return (int)std::max<int64_t>(1, std::min<int64_t>(work_blocks, cap));
 }
 
@@ -111,6 +111,7 @@ struct rb_op {
   double* zw64 = nullptr;
   float* zw32 = nullptr;
   int64_t device_bytes = 0;
+  int* err = nullptr;  // device status word: nonzero after a bounded wait in a kernel gave up
   std::map<int, rb::SpmmSched> tuned;  // k -> schedule chosen by rb_tune_spmm
 };
 
@@ -153,6 +154,24 @@ __device__ __forceinline__ Vec<T, VEC> ldv_rw(const T* p) {
   } else {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) r.v[e] = p[e];
+  }
+  return r;
+}
+
+// L2-coherent load (bypasses L1 and the read-only path): for data other blocks of the same
+// launch have written, as in the persistent solver between grid barriers.
+template <typename T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> ldv_cg(const T* p) {
+  Vec<T, VEC> r;
+  if constexpr (sizeof(T) * VEC == 16) {
+    const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+    memcpy(&r, &q, 16);
+  } else if constexpr (sizeof(T) * VEC == 8) {
+    const float2 q = __ldcg(reinterpret_cast<const float2*>(p));
+    memcpy(&r, &q, 8);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) r.v[e] = __ldcg(p + e);
   }
   return r;
 }

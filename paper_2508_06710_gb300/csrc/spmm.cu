@@ -16,10 +16,14 @@
 
 #include "common.cuh"
 #include "spmm_impl.cuh"
+#include "spmm_tma.cuh"
 
 namespace rb {
 
 namespace {
+
+// shared memory of one block of the TMA pipeline (the ring of stages); two blocks fit on an SM
+constexpr size_t kTmaSmemLimit = 100 * 1024;
 
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kThreads) k_spmm_sell(int n_slots, const int32_t* __restrict__ sptr,
@@ -87,6 +91,24 @@ rb_status launch_csr(const rb_op* op, const SpmmSched& sc, const T* X, int64_t l
   const int R = sc.rows_per_block();
   int64_t grid = ((int64_t)op->n_rows + R - 1) / R;
   if (grid == 0) return RB_OK;
+  if (sc.stage == 2) {
+    if constexpr (LPR == 1) {
+      auto* kern = &k_spmm_tma<T, VEC, EXT>;
+      const int cap = tma_capacity<T>(op, R, kTmaSmemLimit);
+      const size_t smem = tma_layout<T>(R, cap).total;
+      static size_t opted = 0;  // largest dynamic shared memory requested so far (per instantiation)
+      if (smem > 48 * 1024 && smem > opted) {
+        RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemLimit));
+        opted = kTmaSmemLimit;
+      }
+      grid = wave_grid(kern, grid, smem, kTmaThreads);
+      kern<<<(unsigned)grid, kTmaThreads, smem, s>>>(a, R, cap, op->err);
+      RB_CUDA(cudaGetLastError());
+      return RB_OK;
+    }
+    set_error("spmm: the TMA pipeline takes one lane per row");
+    return RB_EUNSUPPORTED;
+  }
   if (sc.stage) {
     const size_t smem = csr_smem_bytes<T>(R, a.stage_cap);
     k_spmm_csr<T, VEC, LPR, EXT><<<(unsigned)std::min<int64_t>(grid, INT32_MAX), kThreads, smem, s>>>(a);
@@ -143,6 +165,7 @@ bool sched_valid(const rb_op* op, const SpmmSched& sc, int k, int64_t ldx, int64
   if (sc.kp != next_pow2(k / sc.vec) || sc.kp > 32) return false;
   if (sc.kp * sc.lpr > 32) return false;
   if (op->format == RB_SELL && (sc.lpr != 1 || sc.stage)) return false;
+  if (sc.stage == 2 && sc.lpr != 1) return false;
   if (op->ext_nz > 0 && sc.vec == 3) return false;  // the spanwise epilogue takes widths dividing Nz only
   if (op->ext_nz > 0 && (op->ext_nz % sc.vec)) return false;
   return true;
@@ -230,7 +253,7 @@ std::vector<SpmmSched> tune_candidates(const rb_op* op, int k, int64_t ldx, int6
   for (int vec : vec_candidates(eb, k)) {
     for (int lpr = 1; lpr <= 8; lpr <<= 1) {
       if (lpr > 1 && op->avg_row_len < 2.0 * lpr) continue;  // lanes would idle on short rows
-      for (int stage = 0; stage <= 1; ++stage) {
+      for (int stage = 0; stage <= 2; ++stage) {
         for (int gc : {-1, 0}) {
           if (stage && gc != 0) continue;
           SpmmSched sc;
@@ -300,5 +323,39 @@ extern "C" rb_status rb_tune_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y
   cudaEventDestroy(e1);
   RB_CUDA(cudaGetLastError());
   A->tuned[k] = best_sc;
+  return RB_OK;
+}
+
+extern "C" rb_status rb_set_spmm_schedule(rb_op_t A, int32_t k, const rb_spmm_schedule* sched) {
+  clear_error();
+  RB_REQUIRE(A && sched, "rb_set_spmm_schedule: null argument");
+  RB_REQUIRE(k >= 1 && k <= RB_MAX_K, "rb_set_spmm_schedule: k = %d outside [1, %d]", k, RB_MAX_K);
+  SpmmSched sc;
+  sc.vec = sched->vec;
+  sc.lpr = sched->lpr;
+  sc.stage = sched->stage;
+  sc.grid_cap = sched->grid_cap;
+  RB_REQUIRE(sc.vec >= 1 && sc.vec <= 4 && k % sc.vec == 0, "rb_set_spmm_schedule: vec %d does not divide k", sc.vec);
+  sc.kp = next_pow2(k / sc.vec);
+  RB_REQUIRE(sc.lpr == 1 || sc.lpr == 2 || sc.lpr == 4 || sc.lpr == 8, "rb_set_spmm_schedule: lpr must be 1, 2, 4 or 8");
+  RB_REQUIRE(sc.stage >= 0 && sc.stage <= 2, "rb_set_spmm_schedule: stage must be 0, 1 or 2");
+  RB_REQUIRE(sc.kp * sc.lpr <= 32, "rb_set_spmm_schedule: (k / vec) * lpr exceeds a warp");
+  RB_REQUIRE(!(A->format == RB_SELL && (sc.lpr != 1 || sc.stage)), "rb_set_spmm_schedule: sliced ELL takes lpr 1, stage 0");
+  RB_REQUIRE(!(sc.stage == 2 && sc.lpr != 1), "rb_set_spmm_schedule: the TMA pipeline takes lpr 1");
+  RB_REQUIRE(!(A->ext_nz > 0 && (sc.vec == 3 || A->ext_nz % sc.vec)), "rb_set_spmm_schedule: vec must divide Nz");
+  A->tuned[k] = sc;
+  return RB_OK;
+}
+
+extern "C" rb_status rb_get_spmm_schedule(rb_op_t A, int32_t k, int64_t ldx, int64_t ldy, const void* X,
+                                          const void* Y, rb_spmm_schedule* sched) {
+  clear_error();
+  RB_REQUIRE(A && sched, "rb_get_spmm_schedule: null argument");
+  RB_REQUIRE(k >= 1 && k <= RB_MAX_K, "rb_get_spmm_schedule: k = %d outside [1, %d]", k, RB_MAX_K);
+  const SpmmSched sc = pick_sched(A, k, ldx, ldy, X, Y);
+  sched->vec = sc.vec;
+  sched->lpr = sc.lpr;
+  sched->stage = sc.stage;
+  sched->grid_cap = sc.grid_cap;
   return RB_OK;
 }

@@ -152,7 +152,8 @@ __device__ __forceinline__ void extruded_epilogue(const CsrArgs<T>& a, int64_t r
 // Direct accumulation for one (row, chunk, sub) without shared-memory staging: the row's
 // index and value loads are issued by all KP * LPR lanes of the row and served as one
 // broadcast.  Must be called by every lane of the warp when LPR > 1.
-template <typename T, int VEC, int LPR>
+// COHERENT: gather X through L2 only (X written by other blocks of the same launch).
+template <typename T, int VEC, int LPR, bool COHERENT = false>
 __device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64_t row, int chunk, int sub,
                                                       bool active, T (&acc)[VEC]) {
   int rs = 0, re = 0;
@@ -165,7 +166,7 @@ __device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64
   for (int p = rs + sub; p < re; p += LPR) {
     const int c = __ldg(a.ci + p);
     const T v = __ldg(a.va + p);
-    const Vec<T, VEC> x = ldv<T, VEC>(Xc + (int64_t)c * a.ldx);
+    const Vec<T, VEC> x = COHERENT ? ldv_cg<T, VEC>(Xc + (int64_t)c * a.ldx) : ldv<T, VEC>(Xc + (int64_t)c * a.ldx);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
   }

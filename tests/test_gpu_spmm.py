@@ -88,6 +88,60 @@ def test_spmm_tuned_schedules(rb, dtype, k):
     _run(rb, A, X, dtype, "csr", tune=True)
 
 
+SCHEDULES = [  # (vec, lpr, stage, grid_cap) for k = 4
+    (1, 1, 0, -1), (2, 1, 0, 0), (4, 1, 0, -1), (1, 2, 0, -1), (2, 4, 0, -1), (1, 8, 0, 0),
+    (1, 1, 1, 0), (2, 2, 1, 0), (4, 1, 1, 0),
+    (1, 1, 2, -1), (2, 1, 2, -1), (4, 1, 2, -1),
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: "v%d-l%d-s%d-g%d" % s)
+def test_spmm_every_schedule(rb, dtype, sched):
+    """Each kernel variant (direct, block-staged, TMA-pipelined; lanes per row; grids) pinned in
+    turn: parity on a ragged random matrix with empty rows and one row too long to stage."""
+    A = _rand_csr(5003, 4001, 7, seed=90, long_rows=3000)
+    k = 4
+    X = W.normal((4001, k), 91)
+    c = W.normal(k, 92)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    npdt = np.float64 if dtype == "f64" else np.float32
+    op = rb.Operator.from_scipy(A, dtype=dtype, k_max=k)
+    vec, lpr, stage, gc = sched
+    op.set_schedule(k, vec, lpr, stage, gc)
+    Xd = to_dev(X.astype(npdt))
+    Yd = torch.full((A.shape[0], k), float("nan"), dtype=tdt, device="cuda")
+    assert op.schedule(Xd, Yd) == {"vec": vec, "lpr": lpr, "stage": stage, "grid_cap": gc}
+    op.spmm(Xd, Yd, c=to_dev(c))
+    op.check()
+    Aref = A if dtype == "f64" else spmm.round_f32(A)
+    Xref = X.astype(npdt).astype(np.float64)
+    cref = c if dtype == "f64" else c.astype(np.float32).astype(np.float64)
+    ok, worst = componentwise_ok(Yd.cpu().numpy(), spmm.spmm(Aref, Xref, cref), spmm.abs_bound(Aref, Xref, cref),
+                                 TOL[dtype])
+    assert ok, worst
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8, 64])
+def test_spmm_tma_pipeline_channel(rb, dtype, k):
+    """The TMA-pipelined kernel on a stencil operator at several k (3-wide rows, 16-byte rows)."""
+    g = W.channel_grid(40, 31, 23)
+    A = fvm.laplacian(g)
+    X = W.normal((A.shape[1], k), 300 + k)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    op = rb.Operator.from_scipy(A, dtype=dtype, k_max=k)
+    vec = 3 if k == 3 else min(k, 16 // (8 if dtype == "f64" else 4))
+    op.set_schedule(k, vec, 1, 2, -1)
+    Y = op.spmm(to_dev(X.astype(npdt)))
+    op.check()
+    Aref = A if dtype == "f64" else spmm.round_f32(A)
+    Xref = X.astype(npdt).astype(np.float64)
+    ok, worst = componentwise_ok(Y.cpu().numpy(), spmm.spmm(Aref, Xref), spmm.abs_bound(Aref, Xref), TOL[dtype])
+    assert ok, worst
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_spmm_fvm_operators(rb, dtype):
     """L (k = 3, velocity components), G (k = 3) and M (k = 1) of a channel grid."""
