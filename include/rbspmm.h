@@ -202,6 +202,19 @@ size_t rb_dot_workspace_bytes(int64_t n, int32_t k);
  * scratch of rb_dot_workspace_bytes(n, k) bytes, 16-byte aligned, contents ignored. */
 rb_status rb_dot(int64_t n, int32_t k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y, int64_t ldy,
                  double* out, void* work, size_t work_bytes, rb_stream_t stream);
+/* rb_dot without a workspace, for callers that cannot give the library device memory (a
+ * plain C program or a plugin that does not own the GPU's memory pool, or a code path that
+ * must not call cudaMalloc / cudaFree because they can synchronise the device).  The paper
+ * has no counterpart: this is a property of the library, not of the method.  Same result and
+ * arguments as rb_dot minus the workspace; it allocates nothing and keeps its partial sums in
+ * a fixed 128 KiB array (256 blocks x RB_MAX_K columns) in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.  k > RB_MAX_K is
+ * rejected with RB_EINVAL.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call outside any stream capture.
+ * All calls share the array: calls whose kernels can overlap on the GPU (other streams,
+ * other host threads) race on it and must be ordered by the caller. */
+rb_status rb_dot_noalloc(int64_t n, int32_t k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y,
+                         int64_t ldy, double* out, rb_stream_t stream);
 /* Y[:, j] += alpha[j] X[:, j]; alpha: k float64 DEVICE values. */
 rb_status rb_axpy(int64_t n, int32_t k, rb_dtype dtype, const double* alpha, const void* X, int64_t ldx, void* Y,
                   int64_t ldy, rb_stream_t stream);

@@ -29,7 +29,7 @@ RB_MAX_K = 64
 SYMBOLS = ["rb_last_error", "rb_version", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_mesh_cot_laplacian",
            "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
-           "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
+           "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
            "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier"]
 
 
@@ -105,6 +105,7 @@ def lib():
         "rb_operator_check": (C.c_int, [vp, vp]),
         "rb_dot_workspace_bytes": (sz, [i64, i32]),
         "rb_dot": (C.c_int, [i64, i32, C.c_int, vp, i64, vp, i64, vp, vp, sz, vp]),
+        "rb_dot_noalloc": (C.c_int, [i64, i32, C.c_int, vp, i64, vp, i64, vp, vp]),
         "rb_axpy": (C.c_int, [i64, i32, C.c_int, vp, vp, i64, vp, i64, vp]),
         "rb_axty": (C.c_int, [i64, i32, C.c_int, dbl, vp, i64, vp, i64, vp]),
         "rb_cg_workspace_bytes": (sz, [vp, i32, C.POINTER(CgParams)]),
@@ -322,6 +323,16 @@ def dot(X, Y, out=None, work=None, stream=None):
         work = torch.empty(wb, dtype=torch.uint8, device=X.device)
     _check(lib().rb_dot(n, k, _dtype_code(X), _ptr(X), ldx, _ptr(Y), ldy, _ptr(out), _ptr(work), work.numel(),
                         _stream(stream)), "rb_dot")
+    return out
+
+
+def dot_noalloc(X, Y, out, stream=None):
+    """Per-column dot products without a workspace (see rb_dot_noalloc): for callers that
+    cannot give the library device memory.  `out` (k float64 on the device) is caller-owned."""
+    X, n, k, ldx = _block(X, "X")
+    Y, _, _, ldy = _block(Y, "Y")
+    _check(lib().rb_dot_noalloc(n, k, _dtype_code(X), _ptr(X), ldx, _ptr(Y), ldy, _ptr(out), _stream(stream)),
+           "rb_dot_noalloc")
     return out
 
 

@@ -3,6 +3,8 @@
 // axty (element-wise product).  Streaming kernels: each thread handles VEC consecutive
 // columns of a row (16-byte accesses when aligned), rows in a grid-stride loop.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -223,6 +225,83 @@ extern "C" rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha,
                     k_axty<float, V><<<wave_grid(&k_axty<float, V>, blocks), kThreads, 0, s>>>(
                         n, k, kp, (float)alpha, (const float*)X, ldx, (float*)Y, ldy));
   }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// rb_dot_noalloc: rb_dot for callers that cannot hand the library device memory.
+//
+// Some callers have no device allocator to draw a workspace from: a plain C program or a
+// plugin inside a host application that does not own the GPU's memory pool, or a code path
+// that must not call cudaMalloc / cudaFree because those can synchronise the whole device.
+// This entry point computes the same per-column dot products as rb_dot but keeps its
+// per-block partial sums in a fixed array in the library's own device memory, declared
+// below, instead of in a caller-provided workspace.  It allocates nothing.
+//
+// The array holds kNoAllocBlocks x RB_MAX_K partial sums (256 x 64 doubles, 128 KiB); every
+// GPU that loads the library holds it until the process exits.  The reduction uses at most
+// kNoAllocBlocks blocks, so any n and any k <= RB_MAX_K fit; k beyond that is rejected.
+// All calls share the one array and each call overwrites what it uses (the first kernel
+// writes every partial sum the second one reads, so nothing needs clearing first), which
+// means two calls whose kernels overlap on the GPU (different streams, or host threads)
+// race on it: such callers must order their calls themselves.
+// ---------------------------------------------------------------------------------------
+namespace rb {
+namespace {
+
+constexpr int kNoAllocBlocks = 256;
+static __device__ __align__(256) double g_dot_scratch[kNoAllocBlocks * RB_MAX_K];
+
+// Device address of g_dot_scratch on the current device.  The host-side symbol is only a
+// stand-in, so the address is looked up once per device (with that device current) the
+// first time the entry point runs there, and cached.
+rb_status dot_scratch_address(double** out) {
+  static std::mutex mu;
+  static std::map<int, double*> cache;
+  int dev = 0;
+  RB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it == cache.end()) {
+    void* p = nullptr;
+    RB_CUDA(cudaGetSymbolAddress(&p, g_dot_scratch));
+    it = cache.emplace(dev, static_cast<double*>(p)).first;
+  }
+  *out = it->second;
+  return RB_OK;
+}
+
+}  // namespace
+}  // namespace rb
+
+extern "C" rb_status rb_dot_noalloc(int64_t n, int32_t k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y,
+                                    int64_t ldy, double* out, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(k >= 1 && k <= RB_MAX_K,
+             "rb_dot_noalloc: k = %d outside [1, %d], the columns its fixed scratch of %d x %d partial sums holds", k,
+             RB_MAX_K, kNoAllocBlocks, RB_MAX_K);
+  RB_TRY(check_block("rb_dot_noalloc", n, k, dtype, X, ldx, Y, ldy));
+  RB_REQUIRE(out != nullptr, "rb_dot_noalloc: null output");
+  double* partials = nullptr;
+  RB_TRY(dot_scratch_address(&partials));
+  cudaStream_t s = S(stream);
+  const int eb = dtype == RB_F64 ? 8 : 4;
+  int vec, kp;
+  vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
+  RB_REQUIRE(kp <= 32, "rb_dot_noalloc: k = %d needs 16-byte aligned rows", k);
+  const int64_t blocks = std::max<int64_t>(1, (n + kThreads / kp - 1) / (kThreads / kp));
+  int grid = 1;
+  if (dtype == RB_F64) {
+    RB_DISPATCH_VEC(double, vec, grid = std::min(kNoAllocBlocks, wave_grid(&k_dot_partial<double, V>, blocks));
+                    k_dot_partial<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, (const double*)X, ldx,
+                                                                       (const double*)Y, ldy, partials));
+  } else {
+    RB_DISPATCH_VEC(float, vec, grid = std::min(kNoAllocBlocks, wave_grid(&k_dot_partial<float, V>, blocks));
+                    k_dot_partial<float, V><<<grid, kThreads, 0, s>>>(n, k, kp, (const float*)X, ldx,
+                                                                      (const float*)Y, ldy, partials));
+  }
+  k_dot_final<<<1, kThreads, 0, s>>>(k, grid, partials, out);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
