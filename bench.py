@@ -155,10 +155,14 @@ def run_ours(args, rank, world, local):
     flops_step = sum(2 * it[1].nnz * it[4] for it in step_items)
 
     def step(evs=None):
-        for i, (_, op, X, Y, k, _) in enumerate(step_items):
+        for i, (label, op, X, Y, k, _) in enumerate(step_items):
             if evs is not None:
                 evs[i][0].record(stream)
+            if args.nvtx:
+                torch.cuda.nvtx.range_push(label)
             op.spmm(X, Y)
+            if args.nvtx:
+                torch.cuda.nvtx.range_pop()
             if evs is not None:
                 evs[i][1].record(stream)
 
@@ -176,10 +180,14 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("timed_step")
     t0.record(stream)
     for s in range(args.steps):
         step(per_kernel[s])
     t1.record(stream)
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -201,7 +209,8 @@ def run_ours(args, rank, world, local):
         fl = 2 * op.nnz * k
         kern.append({"kernel": label, "ms": ms, "gflops": fl / ms / 1e6, "gbs": by / ms / 1e6,
                      "frac_hbm": by / ms / 1e6 / hbm, "bytes": by, "flops": fl,
-                     "fp64_frac": (fl / ms / 1e9 / FP64_PEAK_TFLOPS) if dt == "f64" else None})
+                     "fp64_frac": (fl / ms / 1e9 / FP64_PEAK_TFLOPS) if dt == "f64" else None,
+                     "schedule": op.schedule(X, Y)})
     dom = max(kern, key=lambda r: r["ms"])
     if dom["kernel"].split("-")[1] == "f64" and dom["flops"] / (FP64_PEAK_TFLOPS * 1e12) > dom["bytes"] / (hbm * 1e9):
         roof = {"bound": "alu", "achieved": dom["gflops"] / 1e3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -222,9 +231,156 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e(args, torch, step_items, stream, dev, flops_step)
         out["ksweep"] = k_sweep(torch, rb, ops, dev, hbm)
         out["poisson"] = poisson(torch, rb, ops, g, dev)
+        out["operator_build"] = operator_build(torch, rb, g, dev)
+        out["blas1"] = blas1(torch, rb, dev, g.n_cells, hbm)
+        del ops, step_items
+        torch.cuda.empty_cache()
+        out["batch"] = batch_bench(torch, rb, dev)
+        out["extruded"] = extruded_bench(torch, rb, dev, hbm)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(g)
     return out
+
+
+def operator_build(torch, rb, g, dev):
+    """Device assembly of L, G, M on the channel grid (events, median of 5)."""
+    nodes, per = rb.grid_nodes(g, dev)
+    res = {}
+    for name, kind in (("L", rb.RB_FVM_LAPLACIAN), ("G", rb.RB_FVM_GRADIENT), ("M", rb.RB_FVM_DIVERGENCE)):
+        nr, nc, nnz = rb.fvm_csr_size(nodes, per, kind)
+        rp = torch.empty(nr + 1, dtype=torch.int32, device=dev)
+        ci = torch.empty(nnz, dtype=torch.int32, device=dev)
+        va = torch.empty(nnz, dtype=torch.float64, device=dev)
+        gd = rb._grid_desc(nodes, per)
+        import ctypes as C
+
+        def run():
+            rb._check(rb.lib().rb_fvm_assemble(C.byref(gd), kind, 1.0, rb._ptr(rp), rb._ptr(ci), rb._ptr(va),
+                                               rb._stream()), "rb_fvm_assemble")
+
+        ms = time_events(torch, run, 5)
+        res[name] = {"ms": ms, "nnz": nnz, "gbs_written": (nnz * 12 + 4 * (nr + 1)) / ms / 1e6}
+    return res
+
+
+def blas1(torch, rb, dev, n, hbm):
+    """dot, axpy, axty on n x 3 blocks (FP64 and FP32): algorithmic GB/s."""
+    res = []
+    for dt in (torch.float64, torch.float32):
+        k = 3
+        X = torch.randn((n, k), dtype=dt, device=dev)
+        Y = torch.randn((n, k), dtype=dt, device=dev)
+        alpha = torch.full((k,), 1e-3, dtype=torch.float64, device=dev)
+        out = torch.empty(k, dtype=torch.float64, device=dev)
+        work = torch.empty(rb.lib().rb_dot_workspace_bytes(n, k), dtype=torch.uint8, device=dev)
+        s = X.element_size()
+        for name, fn, by in (("dot", lambda: rb.dot(X, Y, out=out, work=work), 2 * n * k * s),
+                             ("axpy", lambda: rb.axpy(alpha, X, Y), 3 * n * k * s),
+                             ("axty", lambda: rb.axty(1.0, X, Y), 3 * n * k * s)):
+            ms = time_events(torch, fn, 10)
+            res.append({"op": name, "dtype": "f64" if s == 8 else "f32", "k": k, "ms": ms, "gbs": by / ms / 1e6,
+                        "frac_hbm": by / ms / 1e6 / hbm})
+    return res
+
+
+def batch_bench(torch, rb, dev):
+    """Uneven systems (64^3 k=8, 128^3 k=1, three 96x64x48 channels k=3): the persistent batched
+    refinement under one CUDA graph vs the same refinement per system and vs FP64 CG per system."""
+    systems = []
+    for g, k in zip(W.batch_grids(), W.BATCH_K_DEFAULT):
+        nodes, per = rb.grid_nodes(g, dev)
+        rp, ci, va, nc = rb.fvm_assemble(nodes, per, rb.RB_FVM_LAPLACIAN, scale=-1.0)
+        A64 = rb.Operator(rp, ci, va, nc, dtype="f64", k_max=k)
+        A32 = rb.Operator(rp, ci, va, nc, dtype="f32", k_max=k)
+        B = torch.as_tensor(W.zero_mean(W.normal((g.n_cells, k), W.seed_for(4, k, salt=len(systems)))), device=dev)
+        systems.append((g, k, A64, A32, B))
+    prm = rb.cg_params(rtol=1e-10, mixed=2, project_mean=True, max_sweeps=8)
+    batch = rb.Batch([s[2] for s in systems], [s[3] for s in systems], [s[1] for s in systems], prm)
+    Bs = [s[4] for s in systems]
+    Xs = [torch.zeros_like(b) for b in Bs]
+    tuned_ms = batch.tune(Bs, Xs)
+
+    def run_batch():
+        for x in Xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = batch.solve(Bs, Xs)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3, r
+
+    run_batch()
+    t_batch, rep = min((run_batch() for _ in range(3)), key=lambda x: x[0])
+
+    def run_seq(mixed):
+        t = 0.0
+        its = []
+        for g, k, A64, A32, B in systems:
+            X = torch.zeros_like(B)
+            p = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, check_every=50)
+            w = torch.empty(rb.cg_workspace_bytes(A64, k, p), dtype=torch.uint8, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = rb.cg_solve(A64, B, X, A_inner=A32 if mixed else None, params=p, work=w)
+            torch.cuda.synchronize()
+            t += (time.perf_counter() - t0) * 1e3
+            its.append(r.iters)
+        return t, its
+
+    run_seq(2)
+    t_seq_ir, it_seq = min((run_seq(2) for _ in range(2)), key=lambda x: x[0])
+    t_seq_64, it_64 = min((run_seq(0) for _ in range(2)), key=lambda x: x[0])
+    return {"systems": [{"grid": g.name, "n": g.n_cells, "k": k} for g, k, *_ in systems],
+            "batch_graph_ms": t_batch, "tuned_ms": tuned_ms, "sequential_ir_ms": t_seq_ir,
+            "sequential_fp64_cg_ms": t_seq_64, "speedup_vs_sequential_ir": t_seq_ir / t_batch,
+            "speedup_vs_fp64_cg": t_seq_64 / t_batch, "batch_iters": [r.iters for r in rep],
+            "batch_true_rel_res": [max(r.true_rel_res) for r in rep], "batch_status": [r.status for r in rep],
+            "sequential_ir_iters": it_seq, "fp64_cg_iters": it_64}
+
+
+def extruded_bench(torch, rb, dev, hbm):
+    """Airfoil-shaped mesh (~150k vertices) extruded into 64 periodic planes: the SpMM over the
+    k = 64 plane columns vs one SpMV with the same operator assembled as a 3-D CSR."""
+    import scipy.sparse as sp
+
+    m = W.airfoil_mesh()
+    rp, ci = W.mesh_adjacency(m)
+    to = lambda a: torch.as_tensor(a, device=dev)
+    vals, area, status = rb.mesh_cot_laplacian(to(m.points), to(m.triangles), to(rp), to(ci))
+    nz = W.EXTRUDED_NZ
+    dz = W.EXTRUDED_SPAN / nz
+    n2 = m.points.shape[0]
+    res = {"n2d": n2, "nnz2d": int(ci.shape[0]), "nz": nz, "clamped_edges": int(status[0].item()), "runs": []}
+    # the same operator as a 3-D CSR (planes outermost): dz (I (x) L2D) + T_z (x) diag(a / dz)
+    L2 = sp.csr_matrix((vals.cpu().numpy(), ci, rp), shape=(n2, n2))
+    a = area.cpu().numpy()
+    e = np.ones(nz)
+    T = sp.diags([e[:-1], -2 * e, e[:-1]], [-1, 0, 1], shape=(nz, nz), format="lil")
+    T[0, nz - 1] = 1.0
+    T[nz - 1, 0] = 1.0
+    L3 = (dz * sp.kron(sp.identity(nz), L2) + sp.kron(T.tocsr(), sp.diags(a / dz))).tocsr()
+    L3.sort_indices()
+    for dt in ("f64", "f32"):
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        s = 8 if dt == "f64" else 4
+        op = rb.Operator(to(rp), to(ci), vals, n2, dtype=dt, k_max=nz, extruded_nz=nz, z_weight=area / dz, dz=dz)
+        X = torch.randn((n2, nz), dtype=tdt, device=dev)
+        Y = torch.empty_like(X)
+        op.tune(X, Y)
+        ms = time_events(torch, lambda: op.spmm(X, Y), 10)
+        by = int(ci.shape[0]) * (s + 4) + 4 * (n2 + 1) + s * n2 + 2 * s * n2 * nz
+        fl = 2 * int(ci.shape[0]) * nz + 4 * n2 * nz
+        op3 = rb.Operator.from_scipy(L3, dtype=dt, k_max=1)
+        x1 = torch.randn((L3.shape[0], 1), dtype=tdt, device=dev)
+        y1 = torch.empty_like(x1)
+        op3.tune(x1, y1)
+        ms3 = time_events(torch, lambda: op3.spmm(x1, y1), 10)
+        by3 = L3.nnz * (s + 4) + 4 * (L3.shape[0] + 1) + 2 * s * L3.shape[0]
+        res["runs"].append({"dtype": dt, "spmm_k64_ms": ms, "gflops": fl / ms / 1e6, "gbs": by / ms / 1e6,
+                            "frac_hbm": by / ms / 1e6 / hbm, "spmv_3d_ms": ms3, "spmv_3d_gbs": by3 / ms3 / 1e6,
+                            "speedup_vs_3d_spmv": ms3 / ms, "schedule": op.schedule(X, Y)})
+        del op, op3
+    return res
 
 
 def e2e(args, torch, step_items, stream, dev, flops_step):
@@ -302,8 +458,9 @@ def poisson(torch, rb, ops, g, dev):
     Mop.spmm(U, B)
     B.neg_()
     out = {"k": k, "rtol": 1e-10}
-    for name, mixed in (("fp64_cg", 0), ("ir_fp32_inner", 2), ("ir_fp32_inner_restarted", 1)):
-        prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, check_every=50)
+    for name, mixed, pers in (("fp64_cg", 0, False), ("ir_fp32_inner", 2, False),
+                              ("ir_fp32_inner_persistent", 2, True), ("ir_fp32_inner_restarted", 1, False)):
+        prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, check_every=50, persistent=pers)
         work = torch.empty(rb.cg_workspace_bytes(Aop, k, prm), dtype=torch.uint8, device=dev)
         times = []
         for rep in range(2):
@@ -415,6 +572,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="timed step only (no e2e, sweeps, solves, CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nvtx", action="store_true",
+                    help="NVTX ranges around the timed region ('timed_step') and each SpMM (its label), for ncu filters")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel, if captured for this build")
     ap.add_argument("--profile", default=None, choices=["step", "cg"],
