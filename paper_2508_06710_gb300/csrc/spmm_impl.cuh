@@ -179,9 +179,26 @@ __device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64
   }
 }
 
+// Epilogue variants, chosen at compile time so that a launch without a column scale or
+// without the spanwise coupling issues none of their instructions (not even predicated off).
+constexpr int kEpiExt = 1;    // extruded operator: add the periodic spanwise second difference
+constexpr int kEpiScale = 2;  // per-column scale c (Algorithm 1), NULL otherwise
+
+template <typename T, int VEC, int EPI>
+__device__ __forceinline__ void store_row(const CsrArgs<T>& a, int64_t row, int chunk, T (&acc)[VEC]) {
+  if constexpr ((EPI & kEpiExt) != 0) extruded_epilogue<T, VEC>(a, row, chunk, acc);
+  Vec<T, VEC> y;
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    if constexpr ((EPI & kEpiScale) != 0) y.v[e] = acc[e] * (T)a.cs[chunk * VEC + e];
+    else y.v[e] = acc[e];
+  }
+  stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, y);
+}
+
 // SpMM without staging: a persistent grid strides over blocks of R = 256 / (KP LPR) rows;
 // no block-wide barrier anywhere, so every warp keeps its gathers in flight independently.
-template <typename T, int VEC, int LPR, bool EXT>
+template <typename T, int VEC, int LPR, int EPI>
 __global__ void __launch_bounds__(kThreads) k_spmm_direct(CsrArgs<T> a) {
   const int R = kThreads / (a.kp * LPR);
   const int t = threadIdx.x;
@@ -197,17 +214,11 @@ __global__ void __launch_bounds__(kThreads) k_spmm_direct(CsrArgs<T> a) {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = T(0);
     row_accumulate_direct<T, VEC, LPR>(a, row, chunk, sub, active, acc);
-    if (active && sub == 0) {
-      if constexpr (EXT) extruded_epilogue<T, VEC>(a, row, chunk, acc);
-      Vec<T, VEC> y;
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) y.v[e] = a.cs ? acc[e] * (T)a.cs[chunk * VEC + e] : acc[e];
-      stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, y);
-    }
+    if (active && sub == 0) store_row<T, VEC, EPI>(a, row, chunk, acc);
   }
 }
 
-template <typename T, int VEC, int LPR, bool EXT>
+template <typename T, int VEC, int LPR, int EPI>
 __global__ void __launch_bounds__(kThreads) k_spmm_csr(CsrArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int R = kThreads / (a.kp * LPR);
@@ -227,14 +238,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm_csr(CsrArgs<T> a) {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = T(0);
     row_accumulate<T, VEC, LPR>(a, ti, s_rp, s_ci, s_va, rloc, chunk, sub, active, acc);
-    if (active && sub == 0) {
-      const int64_t row = r0 + rloc;
-      if constexpr (EXT) extruded_epilogue<T, VEC>(a, row, chunk, acc);
-      Vec<T, VEC> y;
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) y.v[e] = a.cs ? acc[e] * (T)a.cs[chunk * VEC + e] : acc[e];
-      stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, y);
-    }
+    if (active && sub == 0) store_row<T, VEC, EPI>(a, (int64_t)r0 + rloc, chunk, acc);
   }
 }
 

@@ -58,7 +58,7 @@ inline int tma_capacity(const rb_op* op, int R, size_t limit) {
   return cap;
 }
 
-template <typename T, int VEC, bool EXT>
+template <typename T, int VEC, int EPI>
 __global__ void __launch_bounds__(kTmaThreads) k_spmm_tma(CsrArgs<T> a, int R, int cap, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char sm[];
   const TmaLayout L = tma_layout<T>(R, cap);
@@ -179,13 +179,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_spmm_tma(CsrArgs<T> a, int R, i
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);  // this warp no longer reads the stage
-    if (active) {
-      if constexpr (EXT) extruded_epilogue<T, VEC>(a, row, chunk, acc);
-      Vec<T, VEC> y;
-#pragma unroll
-      for (int ee = 0; ee < VEC; ++ee) y.v[ee] = a.cs ? acc[ee] * (T)a.cs[chunk * VEC + ee] : acc[ee];
-      stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, y);
-    }
+    if (active) store_row<T, VEC, EPI>(a, row, chunk, acc);
   }
 }
 

@@ -209,6 +209,40 @@ def test_extruded_spmm(rb, dtype, nz):
     assert ok, worst
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_extruded_spmm_scaled(rb, dtype):
+    """Extruded operator with a per-column (per-plane) scale c: Y = c * (dz L X + spanwise term)."""
+    nz = 8
+    m = W.random_trimesh(257, 11)
+    L, _ = mesh.cot_laplacian(m)
+    a = mesh.dual_areas(m)
+    dz = W.EXTRUDED_SPAN / nz
+    w = a / dz
+    X = W.normal((L.shape[0], nz), 611)
+    c = W.normal(nz, 612)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    op = rb.Operator.from_scipy(L, dtype=dtype, k_max=nz, extruded_nz=nz, z_weight=torch.as_tensor(w), dz=dz)
+    Y = op.spmm(to_dev(X.astype(npdt)), c=to_dev(c)).cpu().numpy()
+    rnd = (lambda v: v) if dtype == "f64" else (lambda v: np.asarray(v, np.float32).astype(np.float64))
+    Lr = L if dtype == "f64" else spmm.round_f32(L)
+    wr, dzr, Xr, cr = rnd(w), float(rnd(dz)), rnd(X), rnd(c)
+    Yref = mesh.extruded_apply(Lr, wr * dzr, nz, dzr, Xr) * cr[None, :]
+    bound = (dzr * spmm.spmm(abs(Lr), np.abs(Xr)) + 4 * wr[:, None] * np.abs(Xr).max(axis=1, keepdims=True)) \
+        * np.abs(cr)[None, :]
+    ok, worst = componentwise_ok(Y, Yref, bound, TOL[dtype] * 4)
+    assert ok, worst
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 4])
+def test_spmm_sell_scaled(rb, dtype, k):
+    """Sliced ELL with a per-column scale c."""
+    A = _rand_csr(777, 901, 6, seed=130 + k)
+    X = W.normal((901, k), 131 + k)
+    c = W.normal(k, 132 + k)
+    _run(rb, A, X, dtype, "sell", c=c)
+
+
 def test_extruded_airfoil_full_size(rb):
     """The ~150k-vertex airfoil mesh extruded into 64 periodic planes (k = 64), FP64."""
     m = W.airfoil_mesh()
