@@ -101,7 +101,7 @@ __device__ __forceinline__ void row_accumulate(const CsrArgs<T>& a, const TileIn
   const int re = active ? s_rp[rloc + 1] - ti.base : 0;
   const T* Xc = a.X + chunk * VEC;
   if (ti.staged) {
-#pragma unroll 4
+#pragma unroll 2
     for (int p = rs + sub; p < re; p += LPR) {
       const int c = s_ci[p];
       const T v = s_va[p];
@@ -112,7 +112,7 @@ __device__ __forceinline__ void row_accumulate(const CsrArgs<T>& a, const TileIn
   } else {
     const int32_t* ci = a.ci + ti.base;
     const T* va = a.va + ti.base;
-#pragma unroll 4
+#pragma unroll 2
     for (int p = rs + sub; p < re; p += LPR) {
       const int c = __ldg(ci + p);
       const T v = __ldg(va + p);
@@ -162,7 +162,9 @@ __device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64
     re = __ldg(a.rp + row + 1);
   }
   const T* Xc = a.X + chunk * VEC;
-#pragma unroll 4
+  // Unrolled by two only: with four, rows of 2 or 6 nonzeros (gradient, divergence) run a
+  // remainder whose predicated-off FMAs still take FP64-pipe issue slots (+50% on G, k = 3).
+#pragma unroll 2
   for (int p = rs + sub; p < re; p += LPR) {
     const int c = __ldg(a.ci + p);
     const T v = __ldg(a.va + p);

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm_sell(int n_slots, const int32
     T acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = T(0);
-#pragma unroll 4
+#pragma unroll 2
     for (int j = 0; j < width; ++j) {
       const int c = __ldg(scol + base + j * 32);
       const T v = __ldg(sval + base + j * 32);

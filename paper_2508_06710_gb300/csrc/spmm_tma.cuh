@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_spmm_tma(CsrArgs<T> a, int R, i
       const int re = s_rp[rloc + 1] - p0a;
       const T* Xc = a.X + chunk * VEC;
       if (staged) {
-#pragma unroll 4
+#pragma unroll 2
         for (int p = rs; p < re; ++p) {
           const int c = s_ci[p];
           const T v = s_va[p];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_spmm_tma(CsrArgs<T> a, int R, i
           for (int ee = 0; ee < VEC; ++ee) acc[ee] = fma(v, x.v[ee], acc[ee]);
         }
       } else {
-#pragma unroll 4
+#pragma unroll 2
         for (int p = rs; p < re; ++p) {
           const int c = __ldg(a.ci + p0a + p);
           const T v = __ldg(a.va + p0a + p);
