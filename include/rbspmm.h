@@ -307,6 +307,95 @@ rb_status rb_batch_tune(rb_batch_t batch, const double* const* B, const int64_t*
  * solve returns RB_ETIMEOUT.  Defaults: 2000 ms, 0. */
 rb_status rb_batch_set_barrier(rb_batch_t batch, double timeout_ms, int32_t extra_arrivals);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned initial guess for the pressure Poisson solve.
+ *
+ * The paper's projection step (Sec. 3; the Poisson solve that dominates Sec. 4) solves
+ * A p_t = b_t every time step.  The paper has no learned component: this is an addition on
+ * top of it.  A 3-D U-Net maps the right-hand side b_t and the two previous pressures
+ * p_{t-1}, p_{t-2} on a Cartesian grid to a guess of p_t; CG then always runs from the
+ * better of that guess and p_{t-1} (rb_guess_select) to the same tolerance, so the guess
+ * can only change the iteration count, never the answer.
+ *
+ * Network (levels L, channels c_0..c_{L-1}): at level l (the grid coarsened 2^l times) two
+ * 3x3x3 convolutions with bias and ReLU; 2x2x2 average pooling between levels; on the way up
+ * a 2x2x2 stride-2 transposed convolution (with bias, no activation) whose c_l outputs are
+ * concatenated with the level's encoder output (up-sampled channels first), then two 3x3x3
+ * convolutions with ReLU; a 1x1x1 head to one channel.  Padding is circular along periodic
+ * axes and zero along walled ones.  Inputs are scaled, x = (b / s_b, p_{t-1} / s_p,
+ * p_{t-2} / s_p) with s_b = rms(b), s_p = rms(p_{t-1}) (1 for a zero field), and the guess is
+ * p = p_{t-1} - mean(p_{t-1}) + s_p (y - mean(y)) for the head output y.
+ *
+ * Precision: weights and activations in BF16 (round to nearest even), products accumulated
+ * in FP32 on the tensor cores (tcgen05, accumulators in tensor memory); FP32 master weights,
+ * gradients and Adam moments; FP64 scalars (scales, means, loss).
+ *
+ * Parameter vector (FP32, rb_guess_param_count entries), layer by layer in the order
+ *   enc0a enc0b enc1a enc1b ... enc{L-1}a enc{L-1}b,
+ *   then for l = L-2 down to 0: up{l} dec{l}a dec{l}b, and the head;
+ * each layer its weights then its biases; a 3x3x3 convolution's weights as
+ * [c_out][dz][dy][dx][c_in] (offsets -1..1, x fastest), a transposed convolution's as
+ * [c_out][a][b][c][c_in] (a, b, c the z, y, x offsets 0..1 of the fine cell), the head's as
+ * [c_0].  enc0a has c_in = 3.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+  int32_t nx, ny, nz;  /* cells, x fastest; each divisible by 2^(levels-1) */
+  int32_t levels;      /* 2 .. 4 */
+  int32_t channels[4]; /* c_l per level, multiples of 8; each 3x3x3 convolution's BF16 weights,
+                          54 c_in roundup16(c_out) bytes (also with c_in and c_out swapped),
+                          must fit in 160 KB of shared memory (e.g. c = 8, 16, 32, 48) */
+  int32_t periodic[3]; /* x, y, z: 1 circular padding (periodic axis), 0 zero padding (walls) */
+} rb_guess_cfg;
+
+typedef struct rb_guess* rb_guess_t;
+
+typedef struct {
+  double lr, beta1, beta2, eps; /* Adam (Kingma and Ba 2015, Algorithm 1) */
+} rb_adam_params;
+
+/* Number of FP32 parameters of the network that cfg describes. */
+rb_status rb_guess_param_count(const rb_guess_cfg* cfg, int64_t* n);
+
+/* Allocates the network for one grid: parameters (zero until rb_guess_set_params), Adam
+ * moments, gradients and every activation buffer (about 40 bytes per cell and channel of
+ * level 0).  Synchronises.  RB_EINVAL for a grid or channel list outside the limits above. */
+rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out);
+rb_status rb_guess_destroy(rb_guess_t g);
+
+/* Copy the FP32 parameter vector in / out (device pointers, rb_guess_param_count entries).
+ * Setting parameters also refreshes the BF16 copies and resets the Adam step count. */
+rb_status rb_guess_set_params(rb_guess_t g, const float* theta, rb_stream_t stream);
+rb_status rb_guess_get_params(rb_guess_t g, float* theta, rb_stream_t stream);
+/* The accumulated parameter gradient (device, rb_guess_param_count entries). */
+rb_status rb_guess_get_grad(rb_guess_t g, float* grad, rb_stream_t stream);
+
+/* Guess p_out (device, n = nx ny nz doubles) from b, p1 = p_{t-1}, p2 = p_{t-2}. */
+rb_status rb_guess_predict(rb_guess_t g, const double* b, const double* p1, const double* p2, double* p_out,
+                           rb_stream_t stream);
+
+/* Forward and backward pass for one training pair with target p (the solver's p_t): the
+ * loss is mean_i (y_i - mean(y) - t_i + mean(t))^2 with t = (p - p1) / s_p, and its gradient
+ * is added to the gradient buffer (zeroed first when accumulate == 0).  *loss (device, may
+ * be NULL) receives the loss. */
+rb_status rb_guess_loss_grad(rb_guess_t g, const double* b, const double* p1, const double* p2, const double* p,
+                             int32_t accumulate, double* loss, rb_stream_t stream);
+
+/* One Adam step on the accumulated gradient times grad_scale (e.g. 1 / batch), then zeroes
+ * the gradient and refreshes the BF16 weights. */
+rb_status rb_guess_adam_step(rb_guess_t g, const rb_adam_params* h, double grad_scale, rb_stream_t stream);
+
+/* Inspection for tests: the output of layer `index` (flat-parameter order; -1 the scaled
+ * input x with its 3 channels) of the last forward pass, as FP32 [cells of its level][c_out]
+ * into out (device; NULL to query); *count receives the number of floats. */
+rb_status rb_guess_read_activation(rb_guess_t g, int32_t index, float* out, int64_t* count, rb_stream_t stream);
+
+/* The fallback and judge: x0 = the candidate (cand0 or cand1, device, n doubles) with the
+ * smaller ||b - A c||_2, computed on the device with rb_spmm and FP64 dots; res[2] (device)
+ * receives ||b - A c_i||_2 / ||b||_2 and *choice (device) the index taken.  A is the FP64
+ * operator of the solve (n x n); uses g's scratch, so calls on one g must not overlap. */
+rb_status rb_guess_select(rb_guess_t g, rb_op_t A, const double* b, const double* cand0, const double* cand1,
+                          double* x0, double* res, int32_t* choice, rb_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

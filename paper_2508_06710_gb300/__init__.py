@@ -30,7 +30,9 @@ SYMBOLS = ["rb_last_error", "rb_version", "rb_fvm_csr_size", "rb_fvm_assemble", 
            "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
-           "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier"]
+           "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier", "rb_guess_param_count", "rb_guess_create",
+           "rb_guess_destroy", "rb_guess_set_params", "rb_guess_get_params", "rb_guess_get_grad", "rb_guess_predict",
+           "rb_guess_loss_grad", "rb_guess_adam_step", "rb_guess_read_activation", "rb_guess_select"]
 
 
 class RbError(RuntimeError):
@@ -62,6 +64,15 @@ class OpInfo(C.Structure):
 
 class SpmmSchedule(C.Structure):
     _fields_ = [("vec", C.c_int32), ("lpr", C.c_int32), ("stage", C.c_int32), ("grid_cap", C.c_int32)]
+
+
+class GuessCfg(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("levels", C.c_int32),
+                ("channels", C.c_int32 * 4), ("periodic", C.c_int32 * 3)]
+
+
+class AdamParams(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double)]
 
 
 class CgParams(C.Structure):
@@ -119,6 +130,17 @@ def lib():
         "rb_batch_tune": (C.c_int, [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64),
                                     C.POINTER(C.c_double), vp]),
         "rb_batch_set_barrier": (C.c_int, [vp, C.c_double, i32]),
+        "rb_guess_param_count": (C.c_int, [C.POINTER(GuessCfg), C.POINTER(i64)]),
+        "rb_guess_create": (C.c_int, [C.POINTER(GuessCfg), C.POINTER(vp)]),
+        "rb_guess_destroy": (C.c_int, [vp]),
+        "rb_guess_set_params": (C.c_int, [vp, vp, vp]),
+        "rb_guess_get_params": (C.c_int, [vp, vp, vp]),
+        "rb_guess_get_grad": (C.c_int, [vp, vp, vp]),
+        "rb_guess_predict": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "rb_guess_loss_grad": (C.c_int, [vp, vp, vp, vp, vp, i32, vp, vp]),
+        "rb_guess_adam_step": (C.c_int, [vp, C.POINTER(AdamParams), dbl, vp]),
+        "rb_guess_read_activation": (C.c_int, [vp, i32, vp, C.POINTER(i64), vp]),
+        "rb_guess_select": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -447,6 +469,95 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             lib().rb_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def guess_cfg(nx, ny, nz, channels=(8, 16, 32, 48), periodic=(1, 1, 0)) -> GuessCfg:
+    """Network of len(channels) levels on an nx x ny x nz grid (x fastest); periodic = (x, y, z)."""
+    ch = list(channels) + [0] * (4 - len(channels))
+    return GuessCfg(nx, ny, nz, len(channels), (C.c_int32 * 4)(*ch), (C.c_int32 * 3)(*periodic))
+
+
+def guess_param_count(cfg: GuessCfg) -> int:
+    n = C.c_int64()
+    _check(lib().rb_guess_param_count(C.byref(cfg), C.byref(n)), "rb_guess_param_count")
+    return n.value
+
+
+class Guess:
+    """The learned initial guess network (3-D U-Net) of one grid: parameters, Adam state and
+    activation buffers live in the library; vectors are FP64 device tensors of n cells."""
+
+    def __init__(self, cfg: GuessCfg):
+        self.cfg = cfg
+        self.n_params = guess_param_count(cfg)
+        self.n = cfg.nx * cfg.ny * cfg.nz
+        h = C.c_void_p()
+        _check(lib().rb_guess_create(C.byref(cfg), C.byref(h)), "rb_guess_create")
+        self.handle = h
+
+    def set_params(self, theta, stream=None):
+        assert theta.dtype == _torch().float32 and theta.numel() == self.n_params and theta.is_contiguous()
+        _check(lib().rb_guess_set_params(self.handle, _ptr(theta), _stream(stream)), "rb_guess_set_params")
+
+    def params(self, stream=None):
+        t = _torch().empty(self.n_params, dtype=_torch().float32, device="cuda")
+        _check(lib().rb_guess_get_params(self.handle, _ptr(t), _stream(stream)), "rb_guess_get_params")
+        return t
+
+    def grad(self, stream=None):
+        t = _torch().empty(self.n_params, dtype=_torch().float32, device="cuda")
+        _check(lib().rb_guess_get_grad(self.handle, _ptr(t), _stream(stream)), "rb_guess_get_grad")
+        return t
+
+    def _vec(self, v, name):
+        assert v.dtype == _torch().float64 and v.is_cuda and v.numel() == self.n and v.is_contiguous(), name
+        return _ptr(v)
+
+    def predict(self, b, p1, p2, out=None, stream=None):
+        out = _torch().empty(self.n, dtype=_torch().float64, device="cuda") if out is None else out
+        _check(lib().rb_guess_predict(self.handle, self._vec(b, "b"), self._vec(p1, "p1"), self._vec(p2, "p2"),
+                                      self._vec(out, "out"), _stream(stream)), "rb_guess_predict")
+        return out
+
+    def loss_grad(self, b, p1, p2, p, accumulate=False, loss=None, stream=None):
+        _check(lib().rb_guess_loss_grad(self.handle, self._vec(b, "b"), self._vec(p1, "p1"), self._vec(p2, "p2"),
+                                        self._vec(p, "p"), int(bool(accumulate)), _ptr(loss), _stream(stream)),
+               "rb_guess_loss_grad")
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0, stream=None):
+        h = AdamParams(lr, beta1, beta2, eps)
+        _check(lib().rb_guess_adam_step(self.handle, C.byref(h), float(grad_scale), _stream(stream)),
+               "rb_guess_adam_step")
+
+    def activation(self, index, stream=None):
+        n = C.c_int64()
+        _check(lib().rb_guess_read_activation(self.handle, index, None, C.byref(n), _stream(stream)),
+               "rb_guess_read_activation")
+        t = _torch().empty(n.value, dtype=_torch().float32, device="cuda")
+        _check(lib().rb_guess_read_activation(self.handle, index, _ptr(t), C.byref(n), _stream(stream)),
+               "rb_guess_read_activation")
+        return t
+
+    def select(self, A: Operator, b, cand0, cand1, x0, stream=None):
+        """x0 = the candidate with the smaller residual; returns (res tensor[2], choice tensor[1]) on the device."""
+        torch = _torch()
+        res = torch.empty(2, dtype=torch.float64, device="cuda")
+        choice = torch.empty(1, dtype=torch.int32, device="cuda")
+        _check(lib().rb_guess_select(self.handle, A.handle, self._vec(b, "b"), self._vec(cand0, "c0"),
+                                     self._vec(cand1, "c1"), self._vec(x0, "x0"), _ptr(res), _ptr(choice),
+                                     _stream(stream)), "rb_guess_select")
+        return res, choice
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().rb_guess_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,1582 @@
+// Learned initial guess for the Poisson solve: a 3-D U-Net trained and evaluated with
+// hand-written kernels.  The 3x3x3 convolutions (forward, input gradient, weight gradient)
+// run on the tensor cores (tcgen05.mma, BF16 operands in shared memory, FP32 accumulators
+// in tensor memory); pooling, the 2x2x2 transposed convolution, the head, the loss and Adam
+// are streaming kernels on the CUDA cores.
+//
+// Activations are BF16, channel-last: the c channels of cell v at base[v * ld + c], ld a
+// multiple of 8 so that every 8-channel group is one aligned 16-byte chunk (one row of a
+// tensor-core core matrix).  A decoder level's input is one buffer [cells][2 c]: the
+// transposed convolution writes channels [0, c), the encoder writes its output into
+// channels [c, 2 c) directly, so the skip concatenation costs nothing.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace rb {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------------------------ geometry
+
+struct Dims {
+  int nx = 1, ny = 1, nz = 1;
+  int px = 1, py = 1, pz = 0;  // periodic flags
+  __host__ __device__ int n() const { return nx * ny * nz; }
+};
+
+// Neighbour (x + dx, y + dy, z + dz) of cell v: its index, or -1 outside a walled axis.
+__device__ __forceinline__ int neighbour(const Dims& d, int x, int y, int z, int dx, int dy, int dz) {
+  x += dx;
+  y += dy;
+  z += dz;
+  if (x < 0 || x >= d.nx) {
+    if (!d.px) return -1;
+    x = x < 0 ? x + d.nx : x - d.nx;
+  }
+  if (y < 0 || y >= d.ny) {
+    if (!d.py) return -1;
+    y = y < 0 ? y + d.ny : y - d.ny;
+  }
+  if (z < 0 || z >= d.nz) {
+    if (!d.pz) return -1;
+    z = z < 0 ? z + d.nz : z - d.nz;
+  }
+  return x + d.nx * (y + d.ny * z);
+}
+
+// tap index (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1), offsets in -1..1
+__device__ __forceinline__ void tap_offsets(int tap, int& dx, int& dy, int& dz) {
+  dz = tap / 9 - 1;
+  dy = (tap / 3) % 3 - 1;
+  dx = tap % 3 - 1;
+}
+
+// ------------------------------------------------------------------ 3x3x3 convolution (MMA)
+//
+// Implicit GEMM: D[cell m][out channel n] = sum_K A[m][K] B[n][K], K = tap * c_in + ci.
+// A is gathered from the input cells' neighbours (16 bytes = 8 channels of one tap per
+// copy, zeros past a wall), B is the weight matrix [NP][kpad] (K-major, zero padded), held
+// in shared memory for the whole launch.  One CTA of 128 threads (thread = cell row of the
+// 128-cell tile) runs a ring of kStages A stages of kKS K-columns: cp.async gathers fill a
+// stage, one thread issues its two MMAs and commits them to the stage's mbarrier, which frees
+// the stage for the gather kStages - 1 stages later.  Two TMEM accumulators alternate
+// between tiles, and a tile's epilogue (TMEM -> registers -> bias, ReLU / mask -> BF16) runs
+// after the next tile's first MMAs have been issued.
+//
+// The same kernel computes the input gradient of a convolution: correlation of the output
+// gradient with the weights flipped in all three offsets and transposed (c_in <-> c_out),
+// with the padding rules unchanged.
+
+constexpr int kConvThreads = 128;
+constexpr int kKS = 32;                     // K columns per stage (two K = 16 MMAs)
+constexpr int kStages = 4;                  // A ring depth
+constexpr int kAStage = 128 * kKS * 2;      // bytes of one A stage (8 KB)
+constexpr uint32_t kSboA = (kKS / 8) * 128; // A: core matrices adjacent along M
+constexpr size_t kMaxConvSmem = 200 * 1024;
+
+struct Conv3Args {
+  const bf16* x = nullptr;
+  int ldx = 0, cin = 0;  // input channels (multiple of 8)
+  Dims d;
+  int n_vox = 0;
+  const bf16* w = nullptr;  // [NP][kpad]
+  int kpad = 0;             // multiple of kKS, >= 27 cin
+  const float* bias = nullptr;
+  int relu = 0;
+  const bf16* mask = nullptr;  // zero the output where mask <= 0 (input-gradient pass)
+  int ldm = 0;
+  bf16* y = nullptr;
+  int ldy = 0, cout = 0;  // output channels (multiple of 8, <= NP)
+  int* err = nullptr;
+};
+
+__host__ __device__ constexpr uint32_t tmem_cols_for(int np2) {
+  return np2 <= 32 ? 32u : (np2 <= 64 ? 64u : (np2 <= 128 ? 128u : 256u));
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t slot_bar[kStages];
+  __shared__ __align__(8) uint64_t acc_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_slot;
+  constexpr uint32_t kCols = tmem_cols_for(2 * NP);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sB = smem_u32(smem);
+  const uint32_t sA = sB + (uint32_t)(NP * a.kpad * 2);
+  const uint32_t sbo_b = (uint32_t)(a.kpad / 8) * 128;
+  const int S = a.kpad / kKS;
+  const int n_tiles = (a.n_vox + 127) / 128;
+  const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int T = my_tiles * S;
+  const uint32_t idesc = umma_idesc_bf16(128, NP, false, false);
+
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&slot_bar[i], 1);
+    mbar_init(&acc_bar[0], 1);
+    mbar_init(&acc_bar[1], 1);
+    mbar_init(&drain_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+
+  // weights -> shared, K-major canonical layout: core (n / 8, q) at (n / 8) sbo_b + 128 q
+  const int kc = a.kpad / 8;
+  for (int i = tid; i < NP * kc; i += kConvThreads) {
+    const int n = i / kc, q = i - n * kc;
+    cp_async16(sB + (uint32_t)(n >> 3) * sbo_b + (uint32_t)q * 128 + (uint32_t)(n & 7) * 16,
+               a.w + (size_t)n * a.kpad + (size_t)q * 8, 16);
+  }
+
+  // gather of stage j (tile j / S, K columns [(j % S) kKS, +kKS)) into ring slot j % kStages
+  auto load_stage = [&](int j) {
+    const int ti = j / S, s = j - ti * S;
+    const int t = (int)blockIdx.x + ti * (int)gridDim.x;
+    const int v = t * 128 + tid;
+    const bool valid = v < a.n_vox;
+    int x = 0, y = 0, z = 0;
+    if (valid) {
+      x = v % a.d.nx;
+      const int r = v / a.d.nx;
+      y = r % a.d.ny;
+      z = r / a.d.ny;
+    }
+    const uint32_t dst = sA + (uint32_t)(j % kStages) * kAStage + (uint32_t)(tid >> 3) * kSboA + (uint32_t)(tid & 7) * 16;
+#pragma unroll
+    for (int jq = 0; jq < kKS / 8; ++jq) {
+      const int kk = (s * (kKS / 8) + jq) * 8;
+      const int tap = kk / a.cin;
+      const int ci0 = kk - tap * a.cin;
+      const bf16* src = a.x;
+      uint32_t bytes = 0;
+      if (valid && tap < 27) {
+        int dx, dy, dz;
+        tap_offsets(tap, dx, dy, dz);
+        const int nb = neighbour(a.d, x, y, z, dx, dy, dz);
+        if (nb >= 0) {
+          src = a.x + (size_t)nb * a.ldx + ci0;
+          bytes = 16;
+        }
+      }
+      cp_async16(dst + (uint32_t)jq * 128, src, bytes);
+    }
+  };
+
+  uint32_t tmem = 0;
+  int fail = 0;
+  auto epilogue = [&](int e) {
+    const int b = e & 1;
+    if (!mbar_wait(&acc_bar[b], (uint32_t)(e >> 1) & 1u)) fail = 1;
+    tc_fence_after();
+    const int t = (int)blockIdx.x + e * (int)gridDim.x;
+    const int v = t * 128 + tid;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NP);
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+      float acc[16];
+      tmem_ld16(taddr + (uint32_t)c0, acc);  // whole warp, valid cell or not
+      if (fail || v >= a.n_vox) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cb = c0 + 8 * h;
+        if (cb >= a.cout) continue;
+        float o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float val = acc[8 * h + i];
+          if (a.bias) val += __ldg(a.bias + cb + i);
+          if (a.relu) val = fmaxf(val, 0.0f);
+          o[i] = val;
+        }
+        if (a.mask) {
+          const uint4 mq = *reinterpret_cast<const uint4*>(a.mask + (size_t)v * a.ldm + cb);
+          const bf16* mv = reinterpret_cast<const bf16*>(&mq);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (!(__bfloat162float(mv[i]) > 0.0f)) o[i] = 0.0f;
+        }
+        uint4 q;
+        __nv_bfloat162* qp = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) qp[i] = __floats2bfloat162_rn(o[2 * i], o[2 * i + 1]);
+        *reinterpret_cast<uint4*>(a.y + (size_t)v * a.ldy + cb) = q;
+      }
+    }
+  };
+
+  // prologue: weights and the first kStages - 1 stages (the weights ride in group 0)
+  for (int j = 0; j < kStages - 1; ++j) {
+    if (j < T) load_stage(j);
+    cp_async_commit();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tmem = tmem_slot;
+
+  for (int j = 0; j < T; ++j) {
+    const int ti = j / S, s = j - ti * S;
+    cp_async_wait<kStages - 2>();  // stage j has landed (this thread's copies)
+    fence_proxy_async();
+    if (__syncthreads_or(fail)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const int slot = j % kStages;
+      const uint32_t d = tmem + (uint32_t)((ti & 1) * NP);
+#pragma unroll
+      for (int ks = 0; ks < kKS / 16; ++ks) {
+        const uint64_t ad = umma_sdesc(sA + (uint32_t)slot * kAStage + (uint32_t)ks * 256, 128, kSboA);
+        const uint64_t bd = umma_sdesc(sB + (uint32_t)(s * (kKS / 16) + ks) * 256, 128, sbo_b);
+        umma_bf16(d, ad, bd, idesc, (s > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(&slot_bar[slot]);
+      if (s == S - 1) umma_commit(&acc_bar[ti & 1]);
+    }
+    // refill the slot of stage j - 1 with stage j + kStages - 1 once stage j - 1's MMAs are done
+    const int jn = j + kStages - 1;
+    if (jn < T) {
+      if (j >= 1 && !mbar_wait(&slot_bar[(j - 1) % kStages], (uint32_t)((j - 1) / kStages) & 1u)) fail = 1;
+      if (!fail) load_stage(jn);
+    }
+    cp_async_commit();
+    if (s == 0 && ti > 0) epilogue(ti - 1);
+    if (j == T - 1) epilogue(ti);
+  }
+  cp_async_wait_all();
+  // drain: every MMA this CTA issued has completed before TMEM is released
+  if (tid == 0) {
+    umma_commit(&drain_bar);
+    if (!mbar_wait(&drain_bar, 0)) fail = 1;
+  }
+  if (fail && a.err) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// ------------------------------------------------------- weight gradient of a 3x3x3 conv (MMA)
+//
+// D[m][n] = sum over cells v of A[m][v] B[n][v] with m = tap * c_in + ci (plus one row
+// m = 27 c_in of ones, which yields the bias gradient) and n the output channel:
+// A[m][v] = x[neighbour(v, tap)][ci], B[n][v] = g[v][n] (g the ReLU-masked output gradient).
+// Both operands are MN-major in shared memory (8 consecutive channels of one cell form a
+// 16-byte row), K = cells.  CTA (m tile, split) accumulates its share of the cells in TMEM and
+// writes an FP32 partial [split][mpad][NP]; a second kernel sums the splits in a fixed order.
+
+constexpr int kWS = 32;                          // cells per stage
+constexpr uint32_t kLboWA = 16 * 128;            // A: core matrices adjacent along K (cells)
+constexpr int kWAStage = 128 * kWS * 2;          // 8 KB
+
+struct WgradArgs {
+  const bf16* x = nullptr;
+  int ldx = 0, cin = 0;  // convolution input (channels, multiple of 8)
+  const bf16* g = nullptr;
+  int ldg = 0, cout = 0;  // masked output gradient
+  Dims d;
+  int n_vox = 0;
+  int rows = 0;  // 27 cin: index of the ones row
+  int mpad = 0;
+  int cells_per_split = 0;  // multiple of kWS
+  float* part = nullptr;
+  int* err = nullptr;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t slot_bar[kStages];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  constexpr uint32_t kCols = tmem_cols_for(NP);
+  constexpr uint32_t kLboWB = (NP / 8) * 128;
+  constexpr int kWBStage = NP * kWS * 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t sA = smem_u32(smem);
+  const uint32_t sB = sA + (uint32_t)kStages * kWAStage;
+  const int mt = blockIdx.x, split = blockIdx.y;
+  const int v0 = split * a.cells_per_split;
+  const int v1 = min(a.n_vox, v0 + a.cells_per_split);
+  const int T = v1 > v0 ? (v1 - v0 + kWS - 1) / kWS : 0;
+  const uint32_t idesc = umma_idesc_bf16(128, NP, true, true);
+
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&slot_bar[i], 1);
+    mbar_init(&done_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+
+  auto load_stage = [&](int j) {
+    const int slot = j % kStages;
+    const uint32_t a_base = sA + (uint32_t)slot * kWAStage;
+    const uint32_t b_base = sB + (uint32_t)slot * kWBStage;
+    // A: 32 cells x 16 groups of 8 rows
+#pragma unroll
+    for (int r = 0; r < (kWS * 16) / kConvThreads; ++r) {
+      const int i = tid + r * kConvThreads;
+      const int k = i % kWS, grp = i / kWS;
+      const int v = v0 + j * kWS + k;
+      const int m = mt * 128 + grp * 8;
+      const uint32_t dst = a_base + (uint32_t)(k >> 3) * kLboWA + (uint32_t)grp * 128 + (uint32_t)(k & 7) * 16;
+      if (m == a.rows) {  // the ones row (bias gradient), then zeros
+        uint4 q = make_uint4(0, 0, 0, 0);
+        if (v < v1) q.x = 0x3F80u;  // BF16 1.0 in the low half
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(q.x), "r"(q.y), "r"(q.z), "r"(q.w)
+                     : "memory");
+        continue;
+      }
+      const bf16* src = a.x;
+      uint32_t bytes = 0;
+      if (m < a.rows && v < v1) {
+        const int tap = m / a.cin;
+        const int ci0 = m - tap * a.cin;
+        int dx, dy, dz;
+        tap_offsets(tap, dx, dy, dz);
+        const int x = v % a.d.nx, rr = v / a.d.nx;
+        const int nb = neighbour(a.d, x, rr % a.d.ny, rr / a.d.ny, dx, dy, dz);
+        if (nb >= 0) {
+          src = a.x + (size_t)nb * a.ldx + ci0;
+          bytes = 16;
+        }
+      }
+      cp_async16(dst, src, bytes);
+    }
+    // B: 32 cells x NP / 8 groups
+    for (int i = tid; i < kWS * (NP / 8); i += kConvThreads) {
+      const int k = i % kWS, grp = i / kWS;
+      const int v = v0 + j * kWS + k;
+      const uint32_t dst = b_base + (uint32_t)(k >> 3) * kLboWB + (uint32_t)grp * 128 + (uint32_t)(k & 7) * 16;
+      const bool ok = v < v1 && grp * 8 < a.cout;
+      cp_async16(dst, ok ? (const void*)(a.g + (size_t)v * a.ldg + grp * 8) : (const void*)a.g, ok ? 16u : 0u);
+    }
+  };
+
+  for (int j = 0; j < kStages - 1; ++j) {
+    if (j < T) load_stage(j);
+    cp_async_commit();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  int fail = 0;
+  for (int j = 0; j < T; ++j) {
+    cp_async_wait<kStages - 2>();
+    fence_proxy_async();
+    if (__syncthreads_or(fail)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const int slot = j % kStages;
+#pragma unroll
+      for (int ks = 0; ks < kWS / 16; ++ks) {
+        const uint64_t ad = umma_sdesc(sA + (uint32_t)slot * kWAStage + (uint32_t)ks * 2 * kLboWA, kLboWA, 128);
+        const uint64_t bd = umma_sdesc(sB + (uint32_t)slot * kWBStage + (uint32_t)ks * 2 * kLboWB, kLboWB, 128);
+        umma_bf16(tmem, ad, bd, idesc, (j > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(&slot_bar[slot]);
+    }
+    const int jn = j + kStages - 1;
+    if (jn < T) {
+      if (j >= 1 && !mbar_wait(&slot_bar[(j - 1) % kStages], (uint32_t)((j - 1) / kStages) & 1u)) fail = 1;
+      if (!fail) load_stage(jn);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait_all();
+  if (tid == 0) {
+    umma_commit(&done_bar);
+    if (!mbar_wait(&done_bar, 0)) fail = 1;
+  }
+  fail = __syncthreads_or(fail);
+  tc_fence_after();
+  // epilogue: lane = row m of the tile, NP FP32 columns -> partial (zeros when T == 0)
+  const int m = warp * 32 + lane;
+  float* dst = a.part + ((size_t)split * a.mpad + (size_t)mt * 128 + m) * NP;
+#pragma unroll
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float acc[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      float4 q = (T > 0 && !fail) ? make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]) : make_float4(0, 0, 0, 0);
+      *reinterpret_cast<float4*>(dst + c0 + i) = q;
+    }
+  }
+  if (fail && a.err) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// Sums the splits of a weight-gradient partial and adds it into the parameter gradient in
+// the [c_out][tap][c_in] layout (+ biases).  cin_pad: channels of the GEMM input (>= cin).
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int splits, int mpad, int np, int cin_pad, int cin,
+                               int cout, float* __restrict__ gw, float* __restrict__ gb) {
+  const int rows = 27 * cin_pad;
+  const int total = (rows + 1) * cout;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int m = i / cout, n = i - m * cout;
+    float s = 0.0f;
+    for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * mpad + m) * np + n];
+    if (m == rows) {
+      gb[n] += s;
+    } else {
+      const int tap = m / cin_pad, ci = m - tap * cin_pad;
+      if (ci < cin) gw[((size_t)n * 27 + tap) * cin + ci] += s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ streaming kernels
+
+constexpr int kRedThreads = 256;
+constexpr int kRedGrid = 608;
+
+template <int NQ>
+__device__ void block_sum_store(double (&v)[NQ], double* __restrict__ part) {
+  __shared__ double sh[kRedThreads / 32][NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    for (int o = 16; o >= 1; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[w][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double s = 0.0;
+    for (int i = 0; i < kRedThreads / 32; ++i) s += sh[i][threadIdx.x];
+    part[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
+  }
+}
+
+// out[q] = scale * sum over blocks (fixed order); one block
+__global__ void k_finish(const double* __restrict__ part, int nblk, int nq, double* __restrict__ out, double scale) {
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * nq + q];
+    out[q] = scale * s;
+  }
+}
+
+// sums of b^2 and p1^2 (for the scales s_b, s_p)
+__global__ void k_sumsq2(const double* __restrict__ b, const double* __restrict__ p1, int n, double* part) {
+  double v[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double bb = b[i], pp = p1[i];
+    v[0] += bb * bb;
+    v[1] += pp * pp;
+  }
+  block_sum_store<2>(v, part);
+}
+
+// s[0] = mean b^2, s[1] = mean p1^2 -> scales; x0[v] = (b / s_b, p1 / s_p, p2 / s_p, 0 ...) in BF16, ld 8
+__global__ void k_make_input(const double* __restrict__ b, const double* __restrict__ p1, const double* __restrict__ p2,
+                             int n, const double* __restrict__ ms, double* __restrict__ scal, bf16* __restrict__ x0) {
+  const double sb = ms[0] > 0.0 ? sqrt(ms[0]) : 1.0;
+  const double sp = ms[1] > 0.0 ? sqrt(ms[1]) : 1.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scal[0] = sb;
+    scal[1] = sp;
+  }
+  const double ib = 1.0 / sb, ip = 1.0 / sp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint4 q;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+    h[0] = __floats2bfloat162_rn((float)(b[i] * ib), (float)(p1[i] * ip));
+    h[1] = __floats2bfloat162_rn((float)(p2[i] * ip), 0.0f);
+    h[2] = __floats2bfloat162_rn(0.0f, 0.0f);
+    h[3] = h[2];
+    *reinterpret_cast<uint4*>(x0 + (size_t)i * 8) = q;
+  }
+}
+
+// 2x2x2 average pooling: out[coarse][c] = mean of the 8 fine cells; thread per (coarse, 8 channels)
+__global__ void k_pool(const bf16* __restrict__ in, int ldi, Dims fine, int c, bf16* __restrict__ out, int ldo) {
+  const int cx = fine.nx / 2, cy = fine.ny / 2, cz = fine.nz / 2;
+  const int groups = c / 8;
+  const int total = cx * cy * cz * groups;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int gq = i % groups, v = i / groups;
+    const int x = v % cx, r = v / cx, y = r % cy, z = r / cy;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int o = 0; o < 8; ++o) {
+      const int fv = (2 * x + (o & 1)) + fine.nx * ((2 * y + ((o >> 1) & 1)) + fine.ny * (2 * z + (o >> 2)));
+      const uint4 q = *reinterpret_cast<const uint4*>(in + (size_t)fv * ldi + gq * 8);
+      const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) s[e] += __bfloat162float(h[e]);
+    }
+    uint4 q;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(s[2 * e] * 0.125f, s[2 * e + 1] * 0.125f);
+    *reinterpret_cast<uint4*>(out + (size_t)v * ldo + gq * 8) = q;
+  }
+}
+
+// fine cell index of coarse cell (x, y, z) and offset o = a * 4 + b * 2 + c (z, y, x offsets)
+__device__ __forceinline__ int fine_of(const Dims& fine, int x, int y, int z, int o) {
+  return (2 * x + (o & 1)) + fine.nx * ((2 * y + ((o >> 1) & 1)) + fine.ny * (2 * z + (o >> 2)));
+}
+
+// 2x2x2 stride-2 transposed convolution, W [cout][8][cin] BF16 in shared memory; thread per
+// (fine cell, 8 output channels); writes channels [0, cout) of the decoder input (ld ldo)
+__global__ void k_up(const bf16* __restrict__ in, int ldi, int cin, const bf16* __restrict__ W,
+                     const float* __restrict__ bias, Dims fine, int cout, bf16* __restrict__ out, int ldo) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  bf16* sw = reinterpret_cast<bf16*>(sm_raw);
+  for (int i = threadIdx.x; i < cout * 8 * cin; i += blockDim.x) sw[i] = W[i];
+  __syncthreads();
+  const int groups = cout / 8;
+  const int total = fine.n() * groups;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int gq = i % groups, fv = i / groups;
+    const int x = fv % fine.nx, r = fv / fine.nx, y = r % fine.ny, z = r / fine.ny;
+    const int o = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    const int cv = (x >> 1) + (fine.nx >> 1) * ((y >> 1) + (fine.ny >> 1) * (z >> 1));
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = bias[gq * 8 + e];
+    const bf16* xin = in + (size_t)cv * ldi;
+    for (int ci = 0; ci < cin; ci += 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(xin + ci);
+      const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float xv = __bfloat162float(h[u]);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(sw[((gq * 8 + e) * 8 + o) * cin + ci + u]) * xv;
+      }
+    }
+    uint4 q;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(acc[2 * e], acc[2 * e + 1]);
+    *reinterpret_cast<uint4*>(out + (size_t)fv * ldo + gq * 8) = q;
+  }
+}
+
+// input gradient of the transposed convolution, masked by the ReLU of its input:
+// g_in[v][ci] = bf16(sum_{o, co} gu[fine(v, o)][co] W[co][o][ci]) * (x[v][ci] > 0)
+__global__ void k_up_dx(const bf16* __restrict__ gu, int ldg, int cout, const bf16* __restrict__ W, int cin,
+                        const bf16* __restrict__ xin, int ldx, Dims fine, bf16* __restrict__ gin, int ldgi) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  bf16* sw = reinterpret_cast<bf16*>(sm_raw);
+  for (int i = threadIdx.x; i < cout * 8 * cin; i += blockDim.x) sw[i] = W[i];
+  __syncthreads();
+  const int cx = fine.nx / 2, cy = fine.ny / 2, cz = fine.nz / 2;
+  const int groups = cin / 8;
+  const int total = cx * cy * cz * groups;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int gq = i % groups, v = i / groups;
+    const int x = v % cx, r = v / cx, y = r % cy, z = r / cy;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int o = 0; o < 8; ++o) {
+      const bf16* g = gu + (size_t)fine_of(fine, x, y, z, o) * ldg;
+      for (int co = 0; co < cout; co += 8) {
+        const uint4 q = *reinterpret_cast<const uint4*>(g + co);
+        const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float gv = __bfloat162float(h[u]);
+          const bf16* wr = sw + ((co + u) * 8 + o) * cin + gq * 8;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(wr[e]) * gv;
+        }
+      }
+    }
+    const uint4 mq = *reinterpret_cast<const uint4*>(xin + (size_t)v * ldx + gq * 8);
+    const bf16* mh = reinterpret_cast<const bf16*>(&mq);
+    uint4 q;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      // round first (the stored gradient), then mask: the same as masking the rounded value
+      __nv_bfloat162 rv = __floats2bfloat162_rn(acc[2 * e], acc[2 * e + 1]);
+      if (!(__bfloat162float(mh[2 * e]) > 0.0f)) rv.x = __float2bfloat16(0.0f);
+      if (!(__bfloat162float(mh[2 * e + 1]) > 0.0f)) rv.y = __float2bfloat16(0.0f);
+      h[e] = rv;
+    }
+    *reinterpret_cast<uint4*>(gin + (size_t)v * ldgi + gq * 8) = q;
+  }
+}
+
+// weight and bias gradient of the transposed convolution: per block partial sums over a
+// grid-stride share of the coarse cells, outputs (co, o, ci) and then the cout biases.
+// Thread t owns outputs t, t + 256, ... (at most kUpOut of them).
+constexpr int kUpOut = 64;
+constexpr int kUpChunk = 16;
+__global__ void __launch_bounds__(256) k_up_dw(const bf16* __restrict__ x, int ldx, int cin,
+                                               const bf16* __restrict__ gu, int ldg, int cout, Dims fine,
+                                               float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* sx = reinterpret_cast<float*>(sm_raw);        // [kUpChunk][cin]
+  float* sg = sx + kUpChunk * cin;                     // [kUpChunk][8][cout]
+  const int cx = fine.nx / 2, cy = fine.ny / 2, cz = fine.nz / 2;
+  const int nc = cx * cy * cz;
+  const int n_w = cout * 8 * cin;
+  const int n_out = n_w + cout;
+  float acc[kUpOut];
+#pragma unroll
+  for (int r = 0; r < kUpOut; ++r) acc[r] = 0.0f;
+  for (int c0 = blockIdx.x * kUpChunk; c0 < nc; c0 += gridDim.x * kUpChunk) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kUpChunk * cin; i += blockDim.x) {
+      const int k = i / cin, ci = i - k * cin;
+      const int v = c0 + k;
+      sx[i] = v < nc ? __bfloat162float(x[(size_t)v * ldx + ci]) : 0.0f;
+    }
+    for (int i = threadIdx.x; i < kUpChunk * 8 * cout; i += blockDim.x) {
+      const int co = i % cout, r = i / cout, o = r % 8, k = r / 8;
+      const int v = c0 + k;
+      float gv = 0.0f;
+      if (v < nc) {
+        const int xx = v % cx, rr = v / cx;
+        gv = __bfloat162float(gu[(size_t)fine_of(fine, xx, rr % cy, rr / cy, o) * ldg + co]);
+      }
+      sg[i] = gv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < kUpOut; ++r) {
+      const int idx = threadIdx.x + r * blockDim.x;
+      if (idx >= n_out) break;
+      float s = 0.0f;
+      if (idx < n_w) {
+        const int ci = idx % cin, rr = idx / cin, o = rr % 8, co = rr / 8;
+        for (int k = 0; k < kUpChunk; ++k) s += sx[k * cin + ci] * sg[(k * 8 + o) * cout + co];
+      } else {
+        const int co = idx - n_w;
+        for (int k = 0; k < kUpChunk * 8; ++k) s += sg[k * cout + co];
+      }
+      acc[r] += s;
+    }
+  }
+  for (int r = 0; r < kUpOut; ++r) {
+    const int idx = threadIdx.x + r * blockDim.x;
+    if (idx >= n_out) break;
+    part[(size_t)blockIdx.x * n_out + idx] = acc[r];
+  }
+}
+
+// gw[i] += sum over blocks part[b][i] for the transposed convolution's (co, o, ci) + bias layout
+__global__ void k_sum_parts(const float* __restrict__ part, int nblk, int n, float* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * n + i];
+    dst[i] += s;
+  }
+}
+
+// head: y[v] = sum_c W[c] x[v][c] + b (FP32), with per-block partial sums of y
+__global__ void k_head(const bf16* __restrict__ x, int ldx, int c, const float* __restrict__ W,
+                       const float* __restrict__ b, int n, float* __restrict__ y, double* part) {
+  double v[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float s = b[0];
+    for (int cc = 0; cc < c; cc += 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(x + (size_t)i * ldx + cc);
+      const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) s += W[cc + e] * __bfloat162float(h[e]);
+    }
+    y[i] = s;
+    v[0] += s;
+  }
+  block_sum_store<1>(v, part);
+}
+
+// sums of p1 (for the mean of the guess)
+__global__ void k_sum1(const double* __restrict__ a, int n, double* part) {
+  double v[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[0] += a[i];
+  block_sum_store<1>(v, part);
+}
+
+// guess = p1 - mean(p1) + s_p (y - mean(y)); means[0] = mean y, means[1] = mean p1
+__global__ void k_guess_out(const double* __restrict__ p1, const float* __restrict__ y, int n,
+                            const double* __restrict__ scal, const double* __restrict__ means, double* __restrict__ out) {
+  const double sp = scal[1], my = means[0], mp = means[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = p1[i] - mp + sp * ((double)y[i] - my);
+}
+
+// sum of (p - p1) (mean of the scaled target, times s_p)
+__global__ void k_sum_diff(const double* __restrict__ p, const double* __restrict__ p1, int n, double* part) {
+  double v[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[0] += p[i] - p1[i];
+  block_sum_store<1>(v, part);
+}
+
+// d = (y - mean y) - (t - mean t), t = (p - p1) / s_p; gy = 2 d / n; partial sums of d^2.
+// means[0] = mean y, means[2] = mean (p - p1)
+__global__ void k_loss(const double* __restrict__ p, const double* __restrict__ p1, const float* __restrict__ y, int n,
+                       const double* __restrict__ scal, const double* __restrict__ means, float* __restrict__ gy,
+                       double* part) {
+  const double isp = 1.0 / scal[1], my = means[0], mt = means[2] * isp;
+  double v[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double d = ((double)y[i] - my) - ((p[i] - p1[i]) * isp - mt);
+    gy[i] = (float)(2.0 * d / n);
+    v[0] += d * d;
+  }
+  block_sum_store<1>(v, part);
+}
+
+// head backward: partial sums of gy * x[c] (c < C) and of gy; g_pre = bf16(W[c] gy) masked by x > 0
+template <int C>
+__global__ void k_head_bwd(const bf16* __restrict__ x, int ldx, const float* __restrict__ W,
+                           const float* __restrict__ gy, int n, bf16* __restrict__ gpre, int ldg, double* part) {
+  double v[C + 1];
+#pragma unroll
+  for (int q = 0; q <= C; ++q) v[q] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float g = gy[i];
+#pragma unroll
+    for (int cc = 0; cc < C; cc += 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(x + (size_t)i * ldx + cc);
+      const bf16* h = reinterpret_cast<const bf16*>(&q);
+      uint4 o;
+      __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const float x0 = __bfloat162float(h[e]), x1 = __bfloat162float(h[e + 1]);
+        v[cc + e] += (double)g * x0;
+        v[cc + e + 1] += (double)g * x1;
+        __nv_bfloat162 r = __floats2bfloat162_rn(W[cc + e] * g, W[cc + e + 1] * g);
+        if (!(x0 > 0.0f)) r.x = __float2bfloat16(0.0f);
+        if (!(x1 > 0.0f)) r.y = __float2bfloat16(0.0f);
+        oh[e / 2] = r;
+      }
+      *reinterpret_cast<uint4*>(gpre + (size_t)i * ldg + cc) = o;
+    }
+    v[C] += g;
+  }
+  block_sum_store<C + 1>(v, part);
+}
+
+// encoder output gradient: bf16((g_skip + g_pool / 8) * (act > 0)); thread per (cell, 8 channels).
+// g_skip = channels [c, 2c) of the decoder-input gradient (ld lds), act = channels [c, 2c) of
+// the decoder input (the encoder output), g_pool the coarse gradient of the pooled tensor.
+__global__ void k_combine(const bf16* __restrict__ gskip, int lds, const bf16* __restrict__ gpool, int ldp,
+                          const bf16* __restrict__ act, int lda, Dims fine, int c, bf16* __restrict__ out, int ldo) {
+  const int groups = c / 8;
+  const int total = fine.n() * groups;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int gq = i % groups, v = i / groups;
+    const int x = v % fine.nx, r = v / fine.nx, y = r % fine.ny, z = r / fine.ny;
+    const int cv = (x >> 1) + (fine.nx >> 1) * ((y >> 1) + (fine.ny >> 1) * (z >> 1));
+    const uint4 qs = *reinterpret_cast<const uint4*>(gskip + (size_t)v * lds + gq * 8);
+    const uint4 qp = *reinterpret_cast<const uint4*>(gpool + (size_t)cv * ldp + gq * 8);
+    const uint4 qa = *reinterpret_cast<const uint4*>(act + (size_t)v * lda + gq * 8);
+    const bf16* hs = reinterpret_cast<const bf16*>(&qs);
+    const bf16* hp = reinterpret_cast<const bf16*>(&qp);
+    const bf16* ha = reinterpret_cast<const bf16*>(&qa);
+    uint4 o;
+    __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      float a0 = __bfloat162float(hs[e]) + __bfloat162float(hp[e]) * 0.125f;
+      float a1 = __bfloat162float(hs[e + 1]) + __bfloat162float(hp[e + 1]) * 0.125f;
+      if (!(__bfloat162float(ha[e]) > 0.0f)) a0 = 0.0f;
+      if (!(__bfloat162float(ha[e + 1]) > 0.0f)) a1 = 0.0f;
+      oh[e / 2] = __floats2bfloat162_rn(a0, a1);
+    }
+    *reinterpret_cast<uint4*>(out + (size_t)v * ldo + gq * 8) = o;
+  }
+}
+
+// Adam (Kingma and Ba 2015, Algorithm 1) on FP32 masters; c1 = 1 / (1 - beta1^t),
+// c2 = 1 / (1 - beta2^t); the gradient is scaled first and zeroed after use.
+__global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __restrict__ v, float* __restrict__ g,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, float gscale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i] * gscale;
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    g[i] = 0.0f;
+  }
+}
+
+// BF16 copies of a 3x3x3 convolution's weights W[co][tap][ci] (ci < cin):
+//   forward  wf[n][k]: n = co < np, k = tap * cin_pad + ci < kpad (zero elsewhere)
+//   gradient wd[n][k]: n = ci < npd, k = tap' * cout + co < kpadd with tap' = 26 - tap
+__global__ void k_pack_conv3(const float* __restrict__ W, int cin, int cin_pad, int cout, bf16* __restrict__ wf,
+                             int np, int kpad, bf16* __restrict__ wd, int npd, int kpadd) {
+  const int tf = np * kpad, td = npd * kpadd;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tf + td; i += gridDim.x * blockDim.x) {
+    if (i < tf) {
+      const int n = i / kpad, k = i - n * kpad;
+      const int tap = k / cin_pad, ci = k - tap * cin_pad;
+      float val = 0.0f;
+      if (n < cout && tap < 27 && ci < cin) val = W[((size_t)n * 27 + tap) * cin + ci];
+      wf[i] = __float2bfloat16(val);
+    } else {
+      const int j = i - tf;
+      const int n = j / kpadd, k = j - n * kpadd;
+      const int tp = k / cout, co = k - tp * cout;
+      float val = 0.0f;
+      if (n < cin && tp < 27) val = W[((size_t)co * 27 + (26 - tp)) * cin + n];
+      wd[j] = __float2bfloat16(val);
+    }
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, int n, bf16* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = __float2bfloat16(a[i]);
+}
+
+// activation inspection: [n][c] of a BF16 buffer with leading dimension ld -> FP32
+__global__ void k_bf16_to_f32(const bf16* __restrict__ a, int lda, int n, int c, float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * c; i += gridDim.x * blockDim.x) {
+    const int v = i / c, cc = i - v * c;
+    out[i] = __bfloat162float(a[(size_t)v * lda + cc]);
+  }
+}
+
+// guess selection: r = b - A c for two candidates (A c already in ac0 / ac1), sums of r^2, b^2
+__global__ void k_resid2(const double* __restrict__ b, const double* __restrict__ ac0, const double* __restrict__ ac1,
+                         int n, double* part) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double bi = b[i], r0 = bi - ac0[i], r1 = bi - ac1[i];
+    v[0] += r0 * r0;
+    v[1] += r1 * r1;
+    v[2] += bi * bi;
+  }
+  block_sum_store<3>(v, part);
+}
+
+__global__ void k_pick(const double* __restrict__ c0, const double* __restrict__ c1, int n,
+                       const double* __restrict__ sums, double* __restrict__ res, int* __restrict__ choice,
+                       double* __restrict__ x0) {
+  const double bb = sums[2] > 0.0 ? sums[2] : 1.0;
+  const int pick = sums[1] < sums[0] ? 1 : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    res[0] = sqrt(sums[0] / bb);
+    res[1] = sqrt(sums[1] / bb);
+    *choice = pick;
+  }
+  const double* src = pick ? c1 : c0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x0[i] = src[i];
+}
+
+// ------------------------------------------------------------------------------ host side
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+enum LayerKind { kConv3 = 0, kUp = 1, kHead = 2 };
+
+struct Layer {
+  LayerKind kind;
+  int level = 0;
+  int cin = 0, cout = 0;  // cin as in the parameter vector (3 for enc0a)
+  int cin_pad = 0;        // channels of the GEMM input
+  int64_t w_off = 0, b_off = 0;
+  int np = 0, kpad = 0, npd = 0, kpadd = 0, mpad = 0;  // conv3 packing
+  bf16* wf = nullptr;
+  bf16* wd = nullptr;
+  bf16* wu = nullptr;  // up: BF16 [cout][8][cin]
+};
+
+}  // namespace
+}  // namespace rb
+
+struct rb_guess {
+  rb_guess_cfg cfg{};
+  int L = 0;
+  std::vector<int> ch;
+  std::vector<rb::Dims> dims;
+  std::vector<rb::Layer> layers;
+  int64_t n_params = 0;
+  int64_t adam_t = 0;
+  float* theta = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* grad = nullptr;
+  // activations (BF16)
+  rb::bf16* x0 = nullptr;                 // [n0][8]
+  std::vector<rb::bf16*> enc_a, cat, pooled, dec_a, dec_b;
+  rb::bf16* bottom = nullptr;
+  float* y = nullptr;
+  float* gy = nullptr;
+  // gradients (BF16)
+  std::vector<rb::bf16*> g_b, g_a, g_cat, g_eb, g_ea, g_pool;
+  rb::bf16* g_bottom = nullptr;
+  // scratch
+  double* red = nullptr;    // reduction partials
+  double* scal = nullptr;   // [0] s_b, [1] s_p, [2..5] sums / means, [6] loss
+  float* wpart = nullptr;   // weight-gradient partials
+  size_t wpart_floats = 0;
+  double* sel = nullptr;    // [2 n] A c0, A c1 for the guess selection
+  int* err = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace rb {
+namespace {
+
+template <typename T>
+rb_status galloc(rb_guess* g, T** p, size_t count) {
+  void* q = nullptr;
+  RB_CUDA(cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
+  RB_CUDA(cudaMemset(q, 0, std::max<size_t>(count, 1) * sizeof(T)));
+  g->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return RB_OK;
+}
+
+int conv_np(int c) { return round_up(c, 16); }
+
+rb_status check_cfg(const rb_guess_cfg* c) {
+  RB_REQUIRE(c != nullptr, "rb_guess: null configuration");
+  RB_REQUIRE(c->levels >= 2 && c->levels <= 4, "rb_guess: levels must be 2..4 (got %d)", c->levels);
+  const int f = 1 << (c->levels - 1);
+  RB_REQUIRE(c->nx > 0 && c->ny > 0 && c->nz > 0 && c->nx % f == 0 && c->ny % f == 0 && c->nz % f == 0,
+             "rb_guess: grid %d x %d x %d not divisible by 2^(levels-1) = %d", c->nx, c->ny, c->nz, f);
+  RB_REQUIRE((int64_t)c->nx * c->ny * c->nz < (1LL << 30), "rb_guess: grid too large");
+  for (int l = 0; l < c->levels; ++l)
+    RB_REQUIRE(c->channels[l] >= 8 && c->channels[l] % 8 == 0, "rb_guess: channels[%d] = %d not a positive multiple of 8",
+               l, c->channels[l]);
+  return RB_OK;
+}
+
+void build_layers(const rb_guess_cfg& c, std::vector<Layer>& out, int64_t& n) {
+  out.clear();
+  n = 0;
+  auto add = [&](LayerKind k, int level, int cin, int cout) {
+    Layer ly;
+    ly.kind = k;
+    ly.level = level;
+    ly.cin = cin;
+    ly.cout = cout;
+    ly.cin_pad = round_up(cin, 8);
+    ly.w_off = n;
+    n += (k == kConv3 ? 27LL * cin * cout : (k == kUp ? 8LL * cin * cout : cin));
+    ly.b_off = n;
+    n += cout;
+    if (k == kConv3) {
+      ly.np = conv_np(cout);
+      ly.kpad = round_up(27 * ly.cin_pad, kKS);
+      ly.npd = conv_np(ly.cin_pad);
+      ly.kpadd = round_up(27 * cout, kKS);
+      ly.mpad = round_up(27 * ly.cin_pad + 1, 128);
+    }
+    out.push_back(ly);
+  };
+  const int L = c.levels;
+  int cin = 3;
+  for (int l = 0; l < L; ++l) {
+    add(kConv3, l, cin, c.channels[l]);
+    add(kConv3, l, c.channels[l], c.channels[l]);
+    cin = c.channels[l];
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    add(kUp, l, c.channels[l + 1], c.channels[l]);
+    add(kConv3, l, 2 * c.channels[l], c.channels[l]);
+    add(kConv3, l, c.channels[l], c.channels[l]);
+  }
+  add(kHead, 0, c.channels[0], 1);
+}
+
+int guess_sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 152;
+  }
+  return sms;
+}
+
+size_t conv_smem(int np, int kpad) { return (size_t)np * kpad * 2 + (size_t)kStages * kAStage; }
+
+template <int NP>
+rb_status launch_conv3_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
+  auto* kern = &k_conv3_mma<NP>;
+  static size_t opted = 0;
+  if (smem > opted) {
+    RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxConvSmem));
+    opted = kMaxConvSmem;
+  }
+  const int n_tiles = (a.n_vox + 127) / 128;
+  // TMEM: 512 columns per SM, so at most 512 / cols of these CTAs may hold an allocation at once
+  const int per_sm_tmem = (int)(512 / tmem_cols_for(2 * NP));
+  const int cap = std::min(resident_blocks(reinterpret_cast<const void*>(kern), smem, kConvThreads),
+                           per_sm_tmem * guess_sm_count());
+  const int grid = std::max(1, std::min(n_tiles, cap));
+  kern<<<grid, kConvThreads, smem, s>>>(a);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+}  // namespace
+}  // namespace rb
+
+namespace rb {
+namespace {
+
+// layer indices in the flat order
+int enc_idx(int l, int s) { return 2 * l + s; }
+int dec_base(const rb_guess* g, int l) { return 2 * g->L + 3 * (g->L - 2 - l); }
+int head_idx(const rb_guess* g) { return 2 * g->L + 3 * (g->L - 1); }
+
+rb_status conv3_launch(const Conv3Args& a, int np, cudaStream_t s) {
+  const size_t smem = conv_smem(np, a.kpad);
+  RB_REQUIRE(smem <= kMaxConvSmem, "rb_guess: convolution weights (%d x %d) exceed shared memory", np, a.kpad);
+  switch (np) {
+    case 16: return launch_conv3_np<16>(a, smem, s);
+    case 32: return launch_conv3_np<32>(a, smem, s);
+    case 48: return launch_conv3_np<48>(a, smem, s);
+    case 64: return launch_conv3_np<64>(a, smem, s);
+    case 96: return launch_conv3_np<96>(a, smem, s);
+    case 128: return launch_conv3_np<128>(a, smem, s);
+  }
+  set_error("rb_guess: no convolution kernel for %d output channels", np);
+  return RB_EUNSUPPORTED;
+}
+
+// y = relu?(conv(x) + b): forward of layer ly at its level
+rb_status conv3_fwd(rb_guess* g, const Layer& ly, const bf16* x, int ldx, bf16* y, int ldy, cudaStream_t s) {
+  Conv3Args a;
+  a.x = x;
+  a.ldx = ldx;
+  a.cin = ly.cin_pad;
+  a.d = g->dims[ly.level];
+  a.n_vox = a.d.n();
+  a.w = ly.wf;
+  a.kpad = ly.kpad;
+  a.bias = g->theta + ly.b_off;
+  a.relu = 1;
+  a.y = y;
+  a.ldy = ldy;
+  a.cout = ly.cout;
+  a.err = g->err;
+  return conv3_launch(a, ly.np, s);
+}
+
+// gin = conv^T(gpre) (masked by mask > 0 when mask != nullptr)
+rb_status conv3_dgrad(rb_guess* g, const Layer& ly, const bf16* gpre, int ldg, const bf16* mask, int ldm, bf16* gin,
+                      int ldgi, cudaStream_t s) {
+  Conv3Args a;
+  a.x = gpre;
+  a.ldx = ldg;
+  a.cin = ly.cout;
+  a.d = g->dims[ly.level];
+  a.n_vox = a.d.n();
+  a.w = ly.wd;
+  a.kpad = ly.kpadd;
+  a.mask = mask;
+  a.ldm = ldm;
+  a.y = gin;
+  a.ldy = ldgi;
+  a.cout = ly.cin_pad;
+  a.err = g->err;
+  return conv3_launch(a, ly.npd, s);
+}
+
+struct WgradPlan {
+  int m_tiles = 0, splits = 0, cells = 0;
+};
+
+WgradPlan wgrad_plan(const Layer& ly, int n) {
+  WgradPlan p;
+  p.m_tiles = ly.mpad / 128;
+  const int target = std::max(1, (4 * guess_sm_count()) / p.m_tiles);
+  p.cells = round_up(std::max(1, (n + target - 1) / target), kWS);
+  p.splits = (n + p.cells - 1) / p.cells;
+  return p;
+}
+
+template <int NP>
+rb_status launch_wgrad_np(const WgradArgs& a, const WgradPlan& p, cudaStream_t s) {
+  const size_t smem = (size_t)kStages * (kWAStage + NP * kWS * 2);
+  k_wgrad_mma<NP><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, const bf16* gpre, int ldg, cudaStream_t s) {
+  const Dims d = g->dims[ly.level];
+  const WgradPlan p = wgrad_plan(ly, d.n());
+  WgradArgs a;
+  a.x = x;
+  a.ldx = ldx;
+  a.cin = ly.cin_pad;
+  a.g = gpre;
+  a.ldg = ldg;
+  a.cout = ly.cout;
+  a.d = d;
+  a.n_vox = d.n();
+  a.rows = 27 * ly.cin_pad;
+  a.mpad = ly.mpad;
+  a.cells_per_split = p.cells;
+  a.part = g->wpart;
+  a.err = g->err;
+  rb_status st;
+  switch (ly.np) {
+    case 16: st = launch_wgrad_np<16>(a, p, s); break;
+    case 32: st = launch_wgrad_np<32>(a, p, s); break;
+    case 48: st = launch_wgrad_np<48>(a, p, s); break;
+    case 64: st = launch_wgrad_np<64>(a, p, s); break;
+    default:
+      set_error("rb_guess: no weight-gradient kernel for %d output channels", ly.np);
+      return RB_EUNSUPPORTED;
+  }
+  RB_TRY(st);
+  const int total = (a.rows + 1) * ly.cout;
+  k_wgrad_reduce<<<std::min(1024, (total + 255) / 256), 256, 0, s>>>(g->wpart, p.splits, ly.mpad, ly.np, ly.cin_pad,
+                                                                      ly.cin, ly.cout, g->grad + ly.w_off,
+                                                                      g->grad + ly.b_off);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+int up_dw_grid(const rb_guess* g, const Layer& ly) {
+  const Dims& f = g->dims[ly.level];
+  const int nc = f.n() / 8;
+  return std::max(1, std::min(kRedGrid, (nc + kUpChunk - 1) / kUpChunk));
+}
+
+size_t wpart_need(const rb_guess* g) {
+  size_t need = 1;
+  for (const Layer& ly : g->layers) {
+    if (ly.kind == kConv3) {
+      const WgradPlan p = wgrad_plan(ly, g->dims[ly.level].n());
+      need = std::max(need, (size_t)p.splits * ly.mpad * ly.np);
+    } else if (ly.kind == kUp) {
+      need = std::max(need, (size_t)up_dw_grid(g, ly) * (8 * ly.cin * ly.cout + ly.cout));
+    }
+  }
+  return need;
+}
+
+rb_status refresh_weights(rb_guess* g, cudaStream_t s) {
+  for (Layer& ly : g->layers) {
+    if (ly.kind == kConv3) {
+      const int total = ly.np * ly.kpad + ly.npd * ly.kpadd;
+      k_pack_conv3<<<std::min(1024, (total + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cin_pad, ly.cout,
+                                                                       ly.wf, ly.np, ly.kpad, ly.wd, ly.npd, ly.kpadd);
+    } else if (ly.kind == kUp) {
+      const int total = 8 * ly.cin * ly.cout;
+      k_to_bf16<<<std::min(1024, (total + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, total, ly.wu);
+    }
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+int grid_for(int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>(kRedGrid, (work + 255) / 256)); }
+
+rb_status forward(rb_guess* g, const double* b, const double* p1, const double* p2, cudaStream_t s) {
+  const int L = g->L;
+  const int n0 = g->dims[0].n();
+  k_sumsq2<<<kRedGrid, kRedThreads, 0, s>>>(b, p1, n0, g->red);
+  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 2, g->scal + 2, 1.0 / n0);
+  k_make_input<<<grid_for(n0), 256, 0, s>>>(b, p1, p2, n0, g->scal + 2, g->scal, g->x0);
+  RB_CUDA(cudaGetLastError());
+  for (int l = 0; l < L; ++l) {
+    const int c = g->ch[l];
+    const bf16* in = l == 0 ? g->x0 : g->pooled[l - 1];
+    const int ldin = l == 0 ? 8 : g->ch[l - 1];
+    RB_TRY(conv3_fwd(g, g->layers[enc_idx(l, 0)], in, ldin, g->enc_a[l], c, s));
+    bf16* out = l < L - 1 ? g->cat[l] + c : g->bottom;
+    const int ldo = l < L - 1 ? 2 * c : c;
+    RB_TRY(conv3_fwd(g, g->layers[enc_idx(l, 1)], g->enc_a[l], c, out, ldo, s));
+    if (l < L - 1) {
+      k_pool<<<grid_for((int64_t)g->dims[l + 1].n() * (c / 8)), 256, 0, s>>>(out, ldo, g->dims[l], c, g->pooled[l], c);
+      RB_CUDA(cudaGetLastError());
+    }
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const int c = g->ch[l], cc = g->ch[l + 1];
+    const int base = dec_base(g, l);
+    const Layer& up = g->layers[base];
+    const bf16* in = l == L - 2 ? g->bottom : g->dec_b[l + 1];
+    const size_t sm = (size_t)up.cout * 8 * up.cin * 2;
+    k_up<<<grid_for((int64_t)g->dims[l].n() * (c / 8)), 256, sm, s>>>(in, cc, cc, up.wu, g->theta + up.b_off, g->dims[l],
+                                                                      c, g->cat[l], 2 * c);
+    RB_CUDA(cudaGetLastError());
+    RB_TRY(conv3_fwd(g, g->layers[base + 1], g->cat[l], 2 * c, g->dec_a[l], c, s));
+    RB_TRY(conv3_fwd(g, g->layers[base + 2], g->dec_a[l], c, g->dec_b[l], c, s));
+  }
+  const Layer& hd = g->layers[head_idx(g)];
+  k_head<<<kRedGrid, kRedThreads, 0, s>>>(g->dec_b[0], g->ch[0], g->ch[0], g->theta + hd.w_off, g->theta + hd.b_off, n0,
+                                          g->y, g->red);
+  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 2, 1.0 / n0);  // scal[2] = mean y
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+template <int C>
+rb_status head_bwd_c(rb_guess* g, cudaStream_t s) {
+  const Layer& hd = g->layers[head_idx(g)];
+  const int n0 = g->dims[0].n();
+  k_head_bwd<C><<<kRedGrid, kRedThreads, 0, s>>>(g->dec_b[0], C, g->theta + hd.w_off, g->gy, n0, g->g_b[0], C, g->red);
+  // parameter gradient: head W (C sums) and b, added into grad
+  k_finish<<<1, 64, 0, s>>>(g->red, kRedGrid, C + 1, g->scal + 8, 1.0);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+__global__ void k_add_head_grad(const double* __restrict__ sums, int c, float* __restrict__ gw, float* __restrict__ gb) {
+  const int i = threadIdx.x;
+  if (i < c) gw[i] += (float)sums[i];
+  if (i == c) gb[0] += (float)sums[c];
+}
+
+rb_status backward(rb_guess* g, cudaStream_t s) {
+  const int L = g->L;
+  const Layer& hd = g->layers[head_idx(g)];
+  switch (g->ch[0]) {
+    case 8: RB_TRY(head_bwd_c<8>(g, s)); break;
+    case 16: RB_TRY(head_bwd_c<16>(g, s)); break;
+    case 24: RB_TRY(head_bwd_c<24>(g, s)); break;
+    case 32: RB_TRY(head_bwd_c<32>(g, s)); break;
+    default:
+      set_error("rb_guess: the head takes 8, 16, 24 or 32 channels at level 0");
+      return RB_EUNSUPPORTED;
+  }
+  k_add_head_grad<<<1, 64, 0, s>>>(g->scal + 8, g->ch[0], g->grad + hd.w_off, g->grad + hd.b_off);
+  // decoder, finest level first
+  for (int l = 0; l <= L - 2; ++l) {
+    const int c = g->ch[l], cc = g->ch[l + 1];
+    const int base = dec_base(g, l);
+    const Layer& up = g->layers[base];
+    const Layer& la = g->layers[base + 1];
+    const Layer& lb = g->layers[base + 2];
+    RB_TRY(conv3_wgrad(g, lb, g->dec_a[l], c, g->g_b[l], c, s));
+    RB_TRY(conv3_dgrad(g, lb, g->g_b[l], c, g->dec_a[l], c, g->g_a[l], c, s));
+    RB_TRY(conv3_wgrad(g, la, g->cat[l], 2 * c, g->g_a[l], c, s));
+    RB_TRY(conv3_dgrad(g, la, g->g_a[l], c, nullptr, 0, g->g_cat[l], 2 * c, s));
+    // transposed convolution: input gradient (masked by its input's ReLU) and weight gradient
+    const bf16* upin = l == L - 2 ? g->bottom : g->dec_b[l + 1];
+    bf16* gin = l == L - 2 ? g->g_bottom : g->g_b[l + 1];
+    const size_t sm = (size_t)up.cout * 8 * up.cin * 2;
+    k_up_dx<<<grid_for((int64_t)g->dims[l + 1].n() * (cc / 8)), 256, sm, s>>>(g->g_cat[l], 2 * c, c, up.wu, cc, upin,
+                                                                                cc, g->dims[l], gin, cc);
+    const int ug = up_dw_grid(g, up);
+    const size_t smw = (size_t)kUpChunk * (cc + 8 * c) * 4;
+    k_up_dw<<<ug, 256, smw, s>>>(upin, cc, cc, g->g_cat[l], 2 * c, c, g->dims[l], g->wpart);
+    const int n_out = 8 * cc * c + c;
+    k_sum_parts<<<grid_for(n_out), 256, 0, s>>>(g->wpart, ug, n_out, g->grad + up.w_off);  // W then b, contiguous
+    RB_CUDA(cudaGetLastError());
+  }
+  // encoder, bottom first
+  for (int l = L - 1; l >= 0; --l) {
+    const int c = g->ch[l];
+    const Layer& la = g->layers[enc_idx(l, 0)];
+    const Layer& lb = g->layers[enc_idx(l, 1)];
+    bf16* geb = l == L - 1 ? g->g_bottom : g->g_eb[l];
+    if (l < L - 1) {
+      k_combine<<<grid_for((int64_t)g->dims[l].n() * (c / 8)), 256, 0, s>>>(g->g_cat[l] + c, 2 * c, g->g_pool[l + 1], c,
+                                                                            g->cat[l] + c, 2 * c, g->dims[l], c, geb, c);
+      RB_CUDA(cudaGetLastError());
+    }
+    RB_TRY(conv3_wgrad(g, lb, g->enc_a[l], c, geb, c, s));
+    RB_TRY(conv3_dgrad(g, lb, geb, c, g->enc_a[l], c, g->g_ea[l], c, s));
+    const bf16* in = l == 0 ? g->x0 : g->pooled[l - 1];
+    const int ldin = l == 0 ? 8 : g->ch[l - 1];
+    RB_TRY(conv3_wgrad(g, la, in, ldin, g->g_ea[l], c, s));
+    if (l > 0) RB_TRY(conv3_dgrad(g, la, g->g_ea[l], c, nullptr, 0, g->g_pool[l], g->ch[l - 1], s));
+  }
+  return RB_OK;
+}
+
+rb_status guess_check(rb_guess* g, cudaStream_t s) {
+  int h = 0;
+  RB_CUDA(cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RB_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    RB_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+    set_error("rb_guess: a tensor-core kernel gave up a bounded wait");
+    return RB_ETIMEOUT;
+  }
+  return RB_OK;
+}
+
+}  // namespace
+}  // namespace rb
+
+using namespace rb;
+
+extern "C" rb_status rb_guess_param_count(const rb_guess_cfg* cfg, int64_t* n) {
+  clear_error();
+  RB_TRY(check_cfg(cfg));
+  RB_REQUIRE(n != nullptr, "rb_guess_param_count: null output");
+  std::vector<Layer> ls;
+  build_layers(*cfg, ls, *n);
+  return RB_OK;
+}
+
+extern "C" rb_status rb_guess_destroy(rb_guess_t g) {
+  clear_error();
+  if (!g) return RB_OK;
+  for (void* p : g->allocs) cudaFree(p);
+  delete g;
+  return RB_OK;
+}
+
+extern "C" rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out) {
+  clear_error();
+  RB_TRY(check_cfg(cfg));
+  RB_REQUIRE(out != nullptr, "rb_guess_create: null output");
+  *out = nullptr;
+  rb_guess* g = new rb_guess();
+  g->cfg = *cfg;
+  g->L = cfg->levels;
+  for (int l = 0; l < g->L; ++l) {
+    g->ch.push_back(cfg->channels[l]);
+    Dims d;
+    d.nx = cfg->nx >> l;
+    d.ny = cfg->ny >> l;
+    d.nz = cfg->nz >> l;
+    d.px = cfg->periodic[0] != 0;
+    d.py = cfg->periodic[1] != 0;
+    d.pz = cfg->periodic[2] != 0;
+    g->dims.push_back(d);
+  }
+  build_layers(*cfg, g->layers, g->n_params);
+  auto fail = [&](rb_status st) {
+    const std::string msg = rb_last_error();
+    rb_guess_destroy(g);
+    set_error("%s", msg.c_str());
+    return st;
+  };
+  for (const Layer& ly : g->layers) {
+    if (ly.kind != kConv3) continue;
+    if (conv_smem(ly.np, ly.kpad) > kMaxConvSmem || conv_smem(ly.npd, ly.kpadd) > kMaxConvSmem) {
+      set_error("rb_guess_create: a %d -> %d convolution's weights exceed shared memory", ly.cin, ly.cout);
+      return fail(RB_EINVAL);
+    }
+    if (ly.np > 64) {
+      set_error("rb_guess_create: at most 64 output channels per convolution (got %d)", ly.cout);
+      return fail(RB_EINVAL);
+    }
+  }
+  for (const Layer& ly : g->layers)
+    if (ly.kind == kUp && 8 * ly.cin * ly.cout + ly.cout > 256 * kUpOut) {
+      set_error("rb_guess_create: a %d -> %d up-sampling has too many weights", ly.cin, ly.cout);
+      return fail(RB_EINVAL);
+    }
+  const int L = g->L;
+  rb_status st = RB_OK;
+  auto A = [&](auto** p, size_t count) {
+    if (st == RB_OK) st = galloc(g, p, count);
+  };
+  A(&g->theta, g->n_params);
+  A(&g->adam_m, g->n_params);
+  A(&g->adam_v, g->n_params);
+  A(&g->grad, g->n_params);
+  const size_t n0 = g->dims[0].n();
+  A(&g->x0, n0 * 8);
+  g->enc_a.assign(L, nullptr);
+  g->cat.assign(L, nullptr);
+  g->pooled.assign(L, nullptr);
+  g->dec_a.assign(L, nullptr);
+  g->dec_b.assign(L, nullptr);
+  g->g_b.assign(L, nullptr);
+  g->g_a.assign(L, nullptr);
+  g->g_cat.assign(L, nullptr);
+  g->g_eb.assign(L, nullptr);
+  g->g_ea.assign(L, nullptr);
+  g->g_pool.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    const size_t n = g->dims[l].n();
+    const int c = g->ch[l];
+    A(&g->enc_a[l], n * c);
+    A(&g->g_ea[l], n * c);
+    if (l > 0) A(&g->g_pool[l], n * g->ch[l - 1]);
+    if (l < L - 1) {
+      A(&g->cat[l], n * 2 * c);
+      A(&g->pooled[l], (size_t)g->dims[l + 1].n() * c);
+      A(&g->dec_a[l], n * c);
+      A(&g->dec_b[l], n * c);
+      A(&g->g_b[l], n * c);
+      A(&g->g_a[l], n * c);
+      A(&g->g_cat[l], n * 2 * c);
+      A(&g->g_eb[l], n * c);
+    } else {
+      A(&g->bottom, n * c);
+      A(&g->g_bottom, n * c);
+    }
+  }
+  A(&g->y, n0);
+  A(&g->gy, n0);
+  A(&g->red, (size_t)kRedGrid * 64);
+  A(&g->scal, 128);
+  A(&g->sel, 2 * n0);
+  A(&g->err, 1);
+  for (Layer& ly : g->layers) {
+    if (ly.kind == kConv3) {
+      A(&ly.wf, (size_t)ly.np * ly.kpad);
+      A(&ly.wd, (size_t)ly.npd * ly.kpadd);
+    } else if (ly.kind == kUp) {
+      A(&ly.wu, (size_t)8 * ly.cin * ly.cout);
+    }
+  }
+  if (st == RB_OK) {
+    g->wpart_floats = wpart_need(g);
+    A(&g->wpart, g->wpart_floats);
+  }
+  if (st == RB_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaDeviceSynchronize", __FILE__, __LINE__);
+  }
+  if (st != RB_OK) return fail(st);
+  *out = g;
+  return RB_OK;
+}
+
+extern "C" rb_status rb_guess_set_params(rb_guess_t g, const float* theta, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && theta, "rb_guess_set_params: null argument");
+  cudaStream_t s = S(stream);
+  RB_CUDA(cudaMemcpyAsync(g->theta, theta, g->n_params * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  RB_CUDA(cudaMemsetAsync(g->adam_m, 0, g->n_params * sizeof(float), s));
+  RB_CUDA(cudaMemsetAsync(g->adam_v, 0, g->n_params * sizeof(float), s));
+  RB_CUDA(cudaMemsetAsync(g->grad, 0, g->n_params * sizeof(float), s));
+  g->adam_t = 0;
+  return refresh_weights(g, s);
+}
+
+extern "C" rb_status rb_guess_get_params(rb_guess_t g, float* theta, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && theta, "rb_guess_get_params: null argument");
+  RB_CUDA(cudaMemcpyAsync(theta, g->theta, g->n_params * sizeof(float), cudaMemcpyDeviceToDevice, S(stream)));
+  return RB_OK;
+}
+
+extern "C" rb_status rb_guess_get_grad(rb_guess_t g, float* grad, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && grad, "rb_guess_get_grad: null argument");
+  RB_CUDA(cudaMemcpyAsync(grad, g->grad, g->n_params * sizeof(float), cudaMemcpyDeviceToDevice, S(stream)));
+  return RB_OK;
+}
+
+extern "C" rb_status rb_guess_predict(rb_guess_t g, const double* b, const double* p1, const double* p2, double* p_out,
+                                      rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && b && p1 && p2 && p_out, "rb_guess_predict: null argument");
+  cudaStream_t s = S(stream);
+  const int n0 = g->dims[0].n();
+  RB_TRY(forward(g, b, p1, p2, s));
+  k_sum1<<<kRedGrid, kRedThreads, 0, s>>>(p1, n0, g->red);
+  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 3, 1.0 / n0);  // scal[3] = mean p1
+  k_guess_out<<<grid_for(n0), 256, 0, s>>>(p1, g->y, n0, g->scal, g->scal + 2, p_out);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+__global__ void k_copy_loss(const double* __restrict__ sum, double* __restrict__ dst) { *dst = *sum; }
+
+extern "C" rb_status rb_guess_loss_grad(rb_guess_t g, const double* b, const double* p1, const double* p2,
+                                        const double* p, int32_t accumulate, double* loss, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && b && p1 && p2 && p, "rb_guess_loss_grad: null argument");
+  cudaStream_t s = S(stream);
+  const int n0 = g->dims[0].n();
+  if (!accumulate) RB_CUDA(cudaMemsetAsync(g->grad, 0, g->n_params * sizeof(float), s));
+  RB_TRY(forward(g, b, p1, p2, s));
+  k_sum_diff<<<kRedGrid, kRedThreads, 0, s>>>(p, p1, n0, g->red);
+  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 4, 1.0 / n0);  // scal[4] = mean (p - p1)
+  // k_loss reads means[0] = mean y (scal[2]) and means[2] = mean (p - p1) (scal[4])
+  k_loss<<<kRedGrid, kRedThreads, 0, s>>>(p, p1, g->y, n0, g->scal, g->scal + 2, g->gy, g->red);
+  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 6, 1.0 / n0);  // scal[6] = loss
+  RB_CUDA(cudaGetLastError());
+  if (loss) {
+    k_copy_loss<<<1, 1, 0, s>>>(g->scal + 6, loss);
+    RB_CUDA(cudaGetLastError());
+  }
+  return backward(g, s);
+}
+
+extern "C" rb_status rb_guess_adam_step(rb_guess_t g, const rb_adam_params* h, double grad_scale, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && h, "rb_guess_adam_step: null argument");
+  RB_REQUIRE(h->lr > 0 && h->beta1 >= 0 && h->beta1 < 1 && h->beta2 >= 0 && h->beta2 < 1 && h->eps > 0,
+             "rb_guess_adam_step: invalid hyper-parameters");
+  cudaStream_t s = S(stream);
+  RB_TRY(guess_check(g, s));
+  g->adam_t += 1;
+  const double c1 = 1.0 / (1.0 - std::pow(h->beta1, (double)g->adam_t));
+  const double c2 = 1.0 / (1.0 - std::pow(h->beta2, (double)g->adam_t));
+  k_adam<<<grid_for(g->n_params), 256, 0, s>>>(g->theta, g->adam_m, g->adam_v, g->grad, g->n_params, (float)h->lr,
+                                               (float)h->beta1, (float)h->beta2, (float)h->eps, (float)c1, (float)c2,
+                                               (float)grad_scale);
+  RB_CUDA(cudaGetLastError());
+  return refresh_weights(g, s);
+}
+
+extern "C" rb_status rb_guess_read_activation(rb_guess_t g, int32_t index, float* out, int64_t* count,
+                                              rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && count, "rb_guess_read_activation: null argument");
+  RB_REQUIRE(index >= -1 && index < (int)g->layers.size(), "rb_guess_read_activation: index %d out of range", index);
+  const int L = g->L;
+  const bf16* src = nullptr;
+  int ld = 0, c = 0, n = 0;
+  if (index == -1) {
+    src = g->x0, ld = 8, c = 3, n = g->dims[0].n();
+  } else {
+    const Layer& ly = g->layers[index];
+    const int l = ly.level;
+    n = g->dims[l].n();
+    c = ly.cout;
+    if (ly.kind == kHead) {
+      *count = n;
+      if (out) RB_CUDA(cudaMemcpyAsync(out, g->y, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, S(stream)));
+      return RB_OK;
+    }
+    if (index < 2 * L) {
+      if (index % 2 == 0) src = g->enc_a[l], ld = c;
+      else if (l < L - 1) src = g->cat[l] + c, ld = 2 * c;
+      else src = g->bottom, ld = c;
+    } else {
+      const int r = (index - 2 * L) % 3;
+      if (r == 0) src = g->cat[l], ld = 2 * c;
+      else if (r == 1) src = g->dec_a[l], ld = c;
+      else src = g->dec_b[l], ld = c;
+    }
+  }
+  *count = (int64_t)n * c;
+  if (out) {
+    k_bf16_to_f32<<<grid_for((int64_t)n * c), 256, 0, S(stream)>>>(src, ld, n, c, out);
+    RB_CUDA(cudaGetLastError());
+  }
+  return RB_OK;
+}
+
+extern "C" rb_status rb_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k, const double* c,
+                             rb_stream_t stream);
+
+extern "C" rb_status rb_guess_select(rb_guess_t g, rb_op_t A, const double* b, const double* cand0,
+                                     const double* cand1, double* x0, double* res, int32_t* choice,
+                                     rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && A && b && cand0 && cand1 && x0 && res && choice, "rb_guess_select: null argument");
+  const int n0 = g->dims[0].n();
+  RB_REQUIRE(A->n_rows == n0 && A->n_cols == n0 && A->dtype == RB_F64,
+             "rb_guess_select: A must be the FP64 %d x %d operator of the grid", n0, n0);
+  cudaStream_t s = S(stream);
+  RB_TRY(rb_spmm(A, cand0, 1, g->sel, 1, 1, nullptr, stream));
+  RB_TRY(rb_spmm(A, cand1, 1, g->sel + n0, 1, 1, nullptr, stream));
+  k_resid2<<<kRedGrid, kRedThreads, 0, s>>>(b, g->sel, g->sel + n0, n0, g->red);
+  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 3, g->scal + 16, 1.0);
+  k_pick<<<grid_for(n0), 256, 0, s>>>(cand0, cand1, n0, g->scal + 16, res, choice, x0);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}

@@ -1,0 +1,156 @@
+"""The learned initial guess on the GPU (tcgen05 convolutions, streaming kernels, Adam) against
+the FP64 U-Net oracle with BF16 rounding emulated at the same points."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import unet as U
+from oracle import fvm
+from tests.conftest import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(rb, shape_xyz, channels, seed, periodic=(1, 1, 0)):
+    nx, ny, nz = shape_xyz
+    cfg = rb.guess_cfg(nx, ny, nz, channels, periodic)
+    spec = U.Spec(channels=tuple(channels), periodic=(bool(periodic[2]), bool(periodic[1]), bool(periodic[0])))
+    n_par = U.param_count(spec)
+    assert rb.guess_param_count(cfg) == n_par
+    p = U.init_params(spec, W.normal(n_par, seed))
+    for k in p:  # non-zero biases so that they are exercised
+        if k.endswith(".b"):
+            p[k] = 0.05 * W.normal(p[k].shape, seed + 1 + len(k))
+    theta = U.to_flat(spec, p).astype(np.float32)
+    pref = U.from_flat(spec, theta.astype(np.float64))
+    g = rb.Guess(cfg)
+    g.set_params(to_dev(theta))
+    n = nx * ny * nz
+    b, p1, p2 = (W.normal(n, seed + 10 + i) for i in range(3))
+    target = p1 + 0.3 * W.normal(n, seed + 20)
+    return g, spec, pref, theta, (b, p1, p2, target), (nz, ny, nx)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _layer_out(g, i, level_shape, c):
+    a = g.activation(i).cpu().numpy().astype(np.float64)
+    return a.reshape(level_shape + (c,)).transpose(3, 0, 1, 2)
+
+
+CASES = [((16, 16, 8), (8, 16, 32, 48)), ((10, 6, 6), (8, 16)), ((8, 8, 8), (8, 16, 24))]
+
+
+@pytest.mark.parametrize("shape,channels", CASES, ids=["16x16x8-4lvl", "ragged-10x6x6", "8cube-3lvl"])
+def test_forward_matches_oracle(rb, shape, channels):
+    g, spec, pref, _, (b, p1, p2, _), zyx = _setup(rb, shape, channels, 1100)
+    out = g.predict(to_dev(b), to_dev(p1), to_dev(p2)).cpu().numpy()
+    x0, sb, sp = U.net_input(b, p1, p2, zyx, bf=True)
+    y, cache = U.forward(spec, pref, x0, bf=True)
+    L = spec.levels
+    # every layer's BF16 output against the emulated oracle (differences: FP32 vs FP64 sums
+    # and the occasional BF16 rounding flip they cause)
+    names = [n for n, *_ in U.layers(spec)]
+    errs = {}
+    for i, name in enumerate(names[:-1]):
+        kind = U.layers(spec)[i][1]
+        lvl = int(name[3]) if name[:3] in ("enc", "dec") else int(name[2])
+        ls = tuple(s >> lvl for s in zyx)
+        c = U.layers(spec)[i][3]
+        got = _layer_out(g, i, ls, c)
+        if kind == "up":
+            ref = cache[f"dec{lvl}a.in"][:c]
+        else:
+            ref = cache[name + ".out"]
+        errs[name] = _rel(got, ref)
+        assert errs[name] < 2e-2, (name, errs[name])
+    yg = g.activation(len(names) - 1).cpu().numpy().astype(np.float64)
+    errs["head"] = _rel(yg, y.ravel())
+    print("relative activation errors:", {k: round(v, 5) for k, v in errs.items()})
+    assert errs["head"] < 2e-2
+    ref = U.predict(spec, pref, b, p1, p2, zyx, bf=True)
+    contribution = ref - (p1 - p1.mean())  # s_p (y - mean y)
+    assert np.linalg.norm(out - ref) < 2e-2 * np.linalg.norm(contribution)
+    assert abs(out.mean()) < 1e-9 * np.abs(out).max()
+
+
+@pytest.mark.parametrize("shape,channels", CASES, ids=["16x16x8-4lvl", "ragged-10x6x6", "8cube-3lvl"])
+def test_gradient_matches_oracle(rb, shape, channels):
+    g, spec, pref, _, (b, p1, p2, t), zyx = _setup(rb, shape, channels, 1200)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.loss_grad(to_dev(b), to_dev(p1), to_dev(p2), to_dev(t), accumulate=False, loss=loss)
+    lref, gref = U.loss_and_grad(spec, pref, b, p1, p2, t, zyx, bf=True)
+    assert abs(loss.item() - lref) <= 1e-2 * lref
+    grad = g.grad().cpu().numpy().astype(np.float64)
+    gg = U.from_flat(spec, grad)
+    worst = {}
+    for name, *_ in U.layers(spec):
+        for part in ("W", "b"):
+            key = f"{name}.{part}"
+            if key == "head.b":  # sum of a zero-mean output gradient: zero up to rounding
+                assert abs(gg[key][0]) <= 1e-5 * np.linalg.norm(gref["head.W"])
+                continue
+            worst[key] = _rel(gg[key], gref[key])
+    print("relative gradient errors:", {k: round(v, 5) for k, v in worst.items()})
+    assert max(worst.values()) < 5e-2, worst
+    # accumulation: a second call with accumulate adds the same gradient again
+    g.loss_grad(to_dev(b), to_dev(p1), to_dev(p2), to_dev(t), accumulate=True)
+    assert _rel(g.grad().cpu().numpy().astype(np.float64), 2 * grad) < 1e-5
+
+
+def test_adam_step_matches_oracle(rb):
+    g, spec, pref, theta, (b, p1, p2, t), zyx = _setup(rb, (8, 8, 8), (8, 16), 1300)
+    g.loss_grad(to_dev(b), to_dev(p1), to_dev(p2), to_dev(t))
+    grad = g.grad().cpu().numpy().astype(np.float64)
+    g.adam_step(lr=1e-3, grad_scale=0.5)
+    new = g.params().cpu().numpy().astype(np.float64)
+    ref, _, _ = U.adam_step(theta.astype(np.float64), 0.5 * grad, 0.0, 0.0, 1, U.Adam(lr=1e-3))
+    assert np.allclose(new, ref, rtol=1e-6, atol=1e-7)
+    assert np.count_nonzero(g.grad().cpu().numpy()) == 0  # the step consumes the gradient
+
+
+def test_training_reduces_the_loss(rb):
+    """A few dozen Adam steps on one pair: the kernels' gradients point downhill."""
+    g, spec, pref, _, (b, p1, p2, t), zyx = _setup(rb, (16, 16, 8), (8, 16, 32), 1400)
+    bd, p1d, p2d, td = (to_dev(v) for v in (b, p1, p2, t))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.loss_grad(bd, p1d, p2d, td, loss=loss)
+    first = loss.item()
+    for _ in range(60):
+        g.loss_grad(bd, p1d, p2d, td, loss=loss)
+        g.adam_step(lr=3e-3)
+    assert loss.item() < 0.5 * first, (first, loss.item())
+
+
+def test_select_takes_the_better_candidate(rb):
+    grid = W.rbc_grid(8, 1.4)
+    A = -fvm.laplacian(grid)
+    n = A.shape[0]
+    x = W.zero_mean(W.normal((n, 1), 1500))[:, 0]
+    b = A @ x
+    good, bad = x + 1e-6 * W.normal(n, 1501), x + 1e-2 * W.normal(n, 1502)
+    g = rb.Guess(rb.guess_cfg(8, 8, 8, (8, 16), (1, 1, 0)))
+    op = rb.Operator.from_scipy(A.tocsr())
+    x0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    for c0, c1, want in ((bad, good, 1), (good, bad, 0)):
+        res, choice = g.select(op, to_dev(b), to_dev(c0), to_dev(c1), x0)
+        assert choice.item() == want
+        ref = [np.linalg.norm(b - A @ c) / np.linalg.norm(b) for c in (c0, c1)]
+        assert np.allclose(res.cpu().numpy(), ref, rtol=1e-10)
+        assert np.array_equal(x0.cpu().numpy(), (c1 if want else c0))
+
+
+def test_invalid_configurations(rb):
+    lib = rb.lib()
+    import ctypes as C
+    h = C.c_void_p()
+    for cfg in (rb.guess_cfg(8, 8, 8, (8, 16, 32, 48, 64)[:4], (1, 1, 0)),):
+        cfg.levels = 5
+        assert lib.rb_guess_create(C.byref(cfg), C.byref(h)) == rb.RB_EINVAL
+    cfg = rb.guess_cfg(8, 8, 8, (12, 16), (1, 1, 0))
+    assert lib.rb_guess_create(C.byref(cfg), C.byref(h)) == rb.RB_EINVAL
+    cfg = rb.guess_cfg(10, 8, 8, (8, 16, 32), (1, 1, 0))  # 10 not divisible by 4
+    assert lib.rb_guess_create(C.byref(cfg), C.byref(h)) == rb.RB_EINVAL
