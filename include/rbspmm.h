@@ -362,6 +362,12 @@ rb_status rb_guess_param_count(const rb_guess_cfg* cfg, int64_t* n);
 rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out);
 rb_status rb_guess_destroy(rb_guess_t g);
 
+/* He initialisation from given N(0, 1) draws (device, rb_guess_param_count floats): every
+ * weight = draw * sqrt(2 / fan_in) (fan_in 27 c_in for a 3x3x3 convolution, c_in for the
+ * transposed convolution and the head), the head's weights further times head_scale, biases
+ * zero; then as rb_guess_set_params. */
+rb_status rb_guess_init_params(rb_guess_t g, const float* normals, double head_scale, rb_stream_t stream);
+
 /* Copy the FP32 parameter vector in / out (device pointers, rb_guess_param_count entries).
  * Setting parameters also refreshes the BF16 copies and resets the Adam step count. */
 rb_status rb_guess_set_params(rb_guess_t g, const float* theta, rb_stream_t stream);
@@ -389,12 +395,16 @@ rb_status rb_guess_adam_step(rb_guess_t g, const rb_adam_params* h, double grad_
  * into out (device; NULL to query); *count receives the number of floats. */
 rb_status rb_guess_read_activation(rb_guess_t g, int32_t index, float* out, int64_t* count, rb_stream_t stream);
 
-/* The fallback and judge: x0 = the candidate (cand0 or cand1, device, n doubles) with the
- * smaller ||b - A c||_2, computed on the device with rb_spmm and FP64 dots; res[2] (device)
- * receives ||b - A c_i||_2 / ||b||_2 and *choice (device) the index taken.  A is the FP64
- * operator of the solve (n x n); uses g's scratch, so calls on one g must not overlap. */
+/* The fallback and judge: each candidate (cand0, cand1: device, n doubles, not modified) is
+ * first smoothed by `sweeps` damped Jacobi sweeps x <- x + omega D^-1 (b - A x) (D the
+ * diagonal of A; 0 sweeps leaves it as is), then x0 = the smoothed candidate with the smaller
+ * ||b - A x||_2, all on the device with rb_spmm and FP64 sums.  res[2] (device) receives
+ * ||b - A x_i||_2 / ||b||_2 of both, *choice (device) the index taken.  A is the FP64
+ * operator of the solve (n x n, with a diagonal when sweeps > 0); uses g's scratch, so calls
+ * on one g must not overlap. */
 rb_status rb_guess_select(rb_guess_t g, rb_op_t A, const double* b, const double* cand0, const double* cand1,
-                          double* x0, double* res, int32_t* choice, rb_stream_t stream);
+                          int32_t sweeps, double omega, double* x0, double* res, int32_t* choice,
+                          rb_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -161,8 +161,10 @@ def param_count(spec: Spec) -> int:
     return n
 
 
-def init_params(spec: Spec, normals: np.ndarray) -> dict:
-    """He-scaled weights from given N(0,1) draws (``normals``, one per parameter), zero biases."""
+def init_params(spec: Spec, normals: np.ndarray, head_scale: float = 1.0) -> dict:
+    """He-scaled weights from given N(0,1) draws (``normals``, one per parameter, in the flat
+    order), zero biases; the head's weights are further multiplied by ``head_scale``
+    (He, Zhang, Ren & Sun 2015: variance 2 / fan_in)."""
     p = {}
     i = 0
     for name, kind, ci, co in layers(spec):
@@ -173,7 +175,16 @@ def init_params(spec: Spec, normals: np.ndarray) -> dict:
         else:
             shape, fan = (ci,), ci
         n = int(np.prod(shape))
-        p[name + ".W"] = normals[i:i + n].reshape(shape) * np.sqrt(2.0 / fan)
+        scale = np.sqrt(2.0 / fan) * (head_scale if kind == "head" else 1.0)
+        # the draws are consumed in the flat layout's order ([co][taps][ci] for conv3,
+        # [co][offsets][ci] for the transposed convolution)
+        flat = normals[i:i + n]
+        if kind == "conv3":
+            p[name + ".W"] = np.ascontiguousarray(np.transpose(flat.reshape(co, 3, 3, 3, ci), (0, 4, 1, 2, 3))) * scale
+        elif kind == "up":
+            p[name + ".W"] = np.ascontiguousarray(np.transpose(flat.reshape(co, 2, 2, 2, ci), (4, 0, 1, 2, 3))) * scale
+        else:
+            p[name + ".W"] = flat.copy() * scale
         i += n
         p[name + ".b"] = np.zeros(co)
         i += co

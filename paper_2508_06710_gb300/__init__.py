@@ -31,7 +31,7 @@ SYMBOLS = ["rb_last_error", "rb_version", "rb_fvm_csr_size", "rb_fvm_assemble", 
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
            "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier", "rb_guess_param_count", "rb_guess_create",
-           "rb_guess_destroy", "rb_guess_set_params", "rb_guess_get_params", "rb_guess_get_grad", "rb_guess_predict",
+           "rb_guess_destroy", "rb_guess_init_params", "rb_guess_set_params", "rb_guess_get_params", "rb_guess_get_grad", "rb_guess_predict",
            "rb_guess_loss_grad", "rb_guess_adam_step", "rb_guess_read_activation", "rb_guess_select"]
 
 
@@ -133,6 +133,7 @@ def lib():
         "rb_guess_param_count": (C.c_int, [C.POINTER(GuessCfg), C.POINTER(i64)]),
         "rb_guess_create": (C.c_int, [C.POINTER(GuessCfg), C.POINTER(vp)]),
         "rb_guess_destroy": (C.c_int, [vp]),
+        "rb_guess_init_params": (C.c_int, [vp, vp, dbl, vp]),
         "rb_guess_set_params": (C.c_int, [vp, vp, vp]),
         "rb_guess_get_params": (C.c_int, [vp, vp, vp]),
         "rb_guess_get_grad": (C.c_int, [vp, vp, vp]),
@@ -140,7 +141,7 @@ def lib():
         "rb_guess_loss_grad": (C.c_int, [vp, vp, vp, vp, vp, i32, vp, vp]),
         "rb_guess_adam_step": (C.c_int, [vp, C.POINTER(AdamParams), dbl, vp]),
         "rb_guess_read_activation": (C.c_int, [vp, i32, vp, C.POINTER(i64), vp]),
-        "rb_guess_select": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "rb_guess_select": (C.c_int, [vp, vp, vp, vp, vp, i32, dbl, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -502,6 +503,12 @@ class Guess:
         _check(lib().rb_guess_create(C.byref(cfg), C.byref(h)), "rb_guess_create")
         self.handle = h
 
+    def init_params(self, normals, head_scale=1.0, stream=None):
+        """He initialisation from given N(0, 1) draws (float32 device tensor, n_params entries)."""
+        assert normals.dtype == _torch().float32 and normals.numel() == self.n_params and normals.is_contiguous()
+        _check(lib().rb_guess_init_params(self.handle, _ptr(normals), float(head_scale), _stream(stream)),
+               "rb_guess_init_params")
+
     def set_params(self, theta, stream=None):
         assert theta.dtype == _torch().float32 and theta.numel() == self.n_params and theta.is_contiguous()
         _check(lib().rb_guess_set_params(self.handle, _ptr(theta), _stream(stream)), "rb_guess_set_params")
@@ -545,14 +552,15 @@ class Guess:
                "rb_guess_read_activation")
         return t
 
-    def select(self, A: Operator, b, cand0, cand1, x0, stream=None):
-        """x0 = the candidate with the smaller residual; returns (res tensor[2], choice tensor[1]) on the device."""
+    def select(self, A: Operator, b, cand0, cand1, x0, sweeps=0, omega=2.0 / 3.0, stream=None):
+        """x0 = the candidate (after `sweeps` damped Jacobi sweeps) with the smaller residual;
+        returns (res tensor[2], choice tensor[1]) on the device."""
         torch = _torch()
         res = torch.empty(2, dtype=torch.float64, device="cuda")
         choice = torch.empty(1, dtype=torch.int32, device="cuda")
         _check(lib().rb_guess_select(self.handle, A.handle, self._vec(b, "b"), self._vec(cand0, "c0"),
-                                     self._vec(cand1, "c1"), self._vec(x0, "x0"), _ptr(res), _ptr(choice),
-                                     _stream(stream)), "rb_guess_select")
+                                     self._vec(cand1, "c1"), int(sweeps), float(omega), self._vec(x0, "x0"),
+                                     _ptr(res), _ptr(choice), _stream(stream)), "rb_guess_select")
         return res, choice
 
     def close(self):

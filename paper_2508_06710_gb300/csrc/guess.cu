@@ -921,7 +921,7 @@ struct rb_guess {
   double* scal = nullptr;   // [0] s_b, [1] s_p, [2..5] sums / means, [6] loss
   float* wpart = nullptr;   // weight-gradient partials
   size_t wpart_floats = 0;
-  double* sel = nullptr;    // [2 n] A c0, A c1 for the guess selection
+  double* sel = nullptr;    // [4 n] A x0, A x1 and the smoothed candidates of the guess selection
   int* err = nullptr;
   std::vector<void*> allocs;
 };
@@ -1418,7 +1418,7 @@ extern "C" rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out) {
   A(&g->gy, n0);
   A(&g->red, (size_t)kRedGrid * 64);
   A(&g->scal, 128);
-  A(&g->sel, 2 * n0);
+  A(&g->sel, 4 * n0);
   A(&g->err, 1);
   for (Layer& ly : g->layers) {
     if (ly.kind == kConv3) {
@@ -1446,6 +1446,32 @@ extern "C" rb_status rb_guess_set_params(rb_guess_t g, const float* theta, rb_st
   RB_REQUIRE(g && theta, "rb_guess_set_params: null argument");
   cudaStream_t s = S(stream);
   RB_CUDA(cudaMemcpyAsync(g->theta, theta, g->n_params * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  RB_CUDA(cudaMemsetAsync(g->adam_m, 0, g->n_params * sizeof(float), s));
+  RB_CUDA(cudaMemsetAsync(g->adam_v, 0, g->n_params * sizeof(float), s));
+  RB_CUDA(cudaMemsetAsync(g->grad, 0, g->n_params * sizeof(float), s));
+  g->adam_t = 0;
+  return refresh_weights(g, s);
+}
+
+__global__ void k_init_layer(const float* __restrict__ nrm, int64_t n_w, int64_t n_b, float scale,
+                             float* __restrict__ th) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_w + n_b; i += (int64_t)gridDim.x * blockDim.x)
+    th[i] = i < n_w ? nrm[i] * scale : 0.0f;
+}
+
+extern "C" rb_status rb_guess_init_params(rb_guess_t g, const float* normals, double head_scale, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(g && normals, "rb_guess_init_params: null argument");
+  cudaStream_t s = S(stream);
+  for (const Layer& ly : g->layers) {
+    const int64_t n_w = ly.b_off - ly.w_off;
+    const double fan = ly.kind == kConv3 ? 27.0 * ly.cin : (double)ly.cin;
+    double scale = std::sqrt(2.0 / fan);
+    if (ly.kind == kHead) scale *= head_scale;
+    k_init_layer<<<grid_for(n_w + ly.cout), 256, 0, s>>>(normals + ly.w_off, n_w, ly.cout, (float)scale,
+                                                         g->theta + ly.w_off);
+  }
+  RB_CUDA(cudaGetLastError());
   RB_CUDA(cudaMemsetAsync(g->adam_m, 0, g->n_params * sizeof(float), s));
   RB_CUDA(cudaMemsetAsync(g->adam_v, 0, g->n_params * sizeof(float), s));
   RB_CUDA(cudaMemsetAsync(g->grad, 0, g->n_params * sizeof(float), s));
@@ -1563,20 +1589,42 @@ extern "C" rb_status rb_guess_read_activation(rb_guess_t g, int32_t index, float
 extern "C" rb_status rb_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k, const double* c,
                              rb_stream_t stream);
 
+// damped Jacobi sweep on two vectors: x_i += omega dinv (b - (A x)_i)
+__global__ void k_jacobi2(const double* __restrict__ b, const double* __restrict__ ax, const double* __restrict__ dinv,
+                          double omega, int n, double* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double w = omega * dinv[i];
+    x[i] += w * (b[i] - ax[i]);
+    x[n + i] += w * (b[i] - ax[n + i]);
+  }
+}
+
 extern "C" rb_status rb_guess_select(rb_guess_t g, rb_op_t A, const double* b, const double* cand0,
-                                     const double* cand1, double* x0, double* res, int32_t* choice,
-                                     rb_stream_t stream) {
+                                     const double* cand1, int32_t sweeps, double omega, double* x0, double* res,
+                                     int32_t* choice, rb_stream_t stream) {
   clear_error();
   RB_REQUIRE(g && A && b && cand0 && cand1 && x0 && res && choice, "rb_guess_select: null argument");
   const int n0 = g->dims[0].n();
   RB_REQUIRE(A->n_rows == n0 && A->n_cols == n0 && A->dtype == RB_F64,
              "rb_guess_select: A must be the FP64 %d x %d operator of the grid", n0, n0);
+  RB_REQUIRE(sweeps >= 0 && sweeps <= 1000, "rb_guess_select: sweeps = %d outside [0, 1000]", sweeps);
+  RB_REQUIRE(sweeps == 0 || (A->has_diag && A->dinv64), "rb_guess_select: smoothing needs A's diagonal");
   cudaStream_t s = S(stream);
-  RB_TRY(rb_spmm(A, cand0, 1, g->sel, 1, 1, nullptr, stream));
-  RB_TRY(rb_spmm(A, cand1, 1, g->sel + n0, 1, 1, nullptr, stream));
-  k_resid2<<<kRedGrid, kRedThreads, 0, s>>>(b, g->sel, g->sel + n0, n0, g->red);
+  double* ax = g->sel;             // [2][n]: A x_0, A x_1
+  double* xs = g->sel + 2 * (size_t)n0;  // [2][n]: the (smoothed) candidates
+  RB_CUDA(cudaMemcpyAsync(xs, cand0, (size_t)n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RB_CUDA(cudaMemcpyAsync(xs + n0, cand1, (size_t)n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (int it = 0; it <= sweeps; ++it) {
+    RB_TRY(rb_spmm(A, xs, 1, ax, 1, 1, nullptr, stream));
+    RB_TRY(rb_spmm(A, xs + n0, 1, ax + n0, 1, 1, nullptr, stream));
+    if (it < sweeps) {
+      k_jacobi2<<<grid_for(n0), 256, 0, s>>>(b, ax, A->dinv64, omega, n0, xs);
+      RB_CUDA(cudaGetLastError());
+    }
+  }
+  k_resid2<<<kRedGrid, kRedThreads, 0, s>>>(b, ax, ax + n0, n0, g->red);
   k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 3, g->scal + 16, 1.0);
-  k_pick<<<grid_for(n0), 256, 0, s>>>(cand0, cand1, n0, g->scal + 16, res, choice, x0);
+  k_pick<<<grid_for(n0), 256, 0, s>>>(xs, xs + n0, n0, g->scal + 16, res, choice, x0);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }

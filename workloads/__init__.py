@@ -256,11 +256,59 @@ def face_field(n_faces: int, k: int, seed: int, dtype=np.float64) -> np.ndarray:
     return normal((n_faces, k), seed, dtype)
 
 
-def smooth_forcing_modes(n: int, kmax: int, seed: int) -> np.ndarray:
-    """Random complex amplitudes of Fourier modes |kappa| <= kmax (seeded), used by the learned-guess data sequence."""
+# Learned-guess data: a Rayleigh-Benard-shaped 128^3 grid, 8 independent forcing sequences
+# (the k = 8 columns of each solve) of 252 steps; pairs start at step 2 (two previous
+# pressures), the last 25 steps of every sequence are held out: 8 x 225 = 1800 training and
+# 8 x 25 = 200 test pairs.
+GUESS_N = 128
+GUESS_CHAINS = 8
+GUESS_STEPS = 252
+GUESS_HOLDOUT = 25
+GUESS_KMAX = 4
+GUESS_RHO = 0.95
+
+
+def forcing_spectra(steps: int, chains: int, kmax: int = GUESS_KMAX, rho: float = GUESS_RHO,
+                    seed: int = 5000) -> np.ndarray:
+    """Seeded random amplitudes of the Fourier modes 0 < |kappa| <= kmax of three smooth scalar
+    fields (one per face direction) for `chains` independent sequences, AR(1) in time:
+    a_t = rho a_{t-1} + sqrt(1 - rho^2) xi_t, xi complex N(0, 1).  Shape
+    [steps, chains, 3, 2 kmax + 1, 2 kmax + 1, kmax + 1] (z, y wavenumbers -kmax..kmax, x 0..kmax)."""
     g = rng(seed)
     m = 2 * kmax + 1
-    return (g.standard_normal((3, m, m, m)) + 1j * g.standard_normal((3, m, m, m))) / m**1.5
+    kz, ky, kx = np.meshgrid(np.arange(-kmax, kmax + 1), np.arange(-kmax, kmax + 1), np.arange(kmax + 1),
+                             indexing="ij")
+    mask = (kz**2 + ky**2 + kx**2 <= kmax * kmax) & ((kz != 0) | (ky != 0) | (kx != 0))
+    shape = (chains, 3, m, m, kmax + 1)
+    out = np.zeros((steps,) + shape, dtype=np.complex128)
+    a = (g.standard_normal(shape) + 1j * g.standard_normal(shape)) * mask
+    s = np.sqrt(1.0 - rho * rho)
+    for t in range(steps):
+        if t:
+            a = rho * a + s * (g.standard_normal(shape) + 1j * g.standard_normal(shape)) * mask
+        out[t] = a
+    return out
+
+
+def face_fields(spec_t: np.ndarray, cells: tuple, torch_mod, device) -> "object":
+    """Synthesise the face velocities of one step from its spectra (inverse real FFT on the
+    cell-index grid, scaled to unit rms per mode count): returns a float64 tensor
+    [n_faces, chains] in the face order x faces, y faces, z faces (each x fastest), with
+    periodic x and y (nx, ny faces per line) and walls in z (nz - 1 interior z faces)."""
+    torch = torch_mod
+    nx, ny, nz = cells
+    chains, _, m, _, kx1 = spec_t.shape
+    kmax = (m - 1) // 2
+    full = torch.zeros((chains, 3, nz, ny, nx // 2 + 1), dtype=torch.complex128, device=device)
+    sp = torch.as_tensor(spec_t, device=device)
+    zi = torch.as_tensor(np.arange(-kmax, kmax + 1) % nz, device=device)
+    yi = torch.as_tensor(np.arange(-kmax, kmax + 1) % ny, device=device)
+    full[:, :, zi[:, None], yi[None, :], :kx1] = sp
+    f = torch.fft.irfftn(full, s=(nz, ny, nx), dim=(2, 3, 4)) * (nx * ny * nz / np.sqrt(4.0 * m * m * kx1))
+    fx = f[:, 0].reshape(chains, -1)
+    fy = f[:, 1].reshape(chains, -1)
+    fz = f[:, 2, : nz - 1].reshape(chains, -1)
+    return torch.cat([fx, fy, fz], dim=1).t().contiguous()
 
 
 def as_columns(x: np.ndarray) -> np.ndarray:
