@@ -237,6 +237,9 @@ def run_ours(args, rank, world, local):
         torch.cuda.empty_cache()
         out["batch"] = batch_bench(torch, rb, dev)
         out["extruded"] = extruded_bench(torch, rb, dev, hbm)
+        if not args.no_guess:
+            torch.cuda.empty_cache()
+            out["learned_guess"] = learned_guess(torch, rb, dev, args)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(g)
     return out
@@ -476,6 +479,59 @@ def poisson(torch, rb, ops, g, dev):
     return out
 
 
+def learned_guess(torch, rb, dev, args):
+    """Learned initial guess on the Rayleigh-Benard-shaped 128^3 grid: solver-generated pairs
+    (8 forcing sequences solved together, k = 8), training with the library's tcgen05 kernels,
+    then CG to 1e-10 on held-out steps from zero (FP64 CG), from p_{t-1} (FP64 CG and
+    FP32-inner refinement) and from the judged learned guess (refinement)."""
+    from paper_2508_06710_gb300 import guess_pipeline as gp
+
+    n = W.GUESS_N
+    chains = W.GUESS_CHAINS
+    steps = W.GUESS_STEPS if args.guess_full else 40
+    holdout = W.GUESS_HOLDOUT if args.guess_full else 4
+    epochs = args.guess_epochs if args.guess_epochs else (6 if args.guess_full else 3)
+    grid = W.rbc_grid(n, 1.4)
+    prob = gp.make_problem(torch, grid, chains, dev)
+    spectra = W.forcing_spectra(steps, chains, seed=5000)
+    Bs, Ps, gen = gp.generate(torch, prob, spectra, W.face_fields, dev)
+    train_pairs, _ = gp.pairs(steps, chains, holdout)
+    net = gp.network(grid)
+    net.init_params(torch.as_tensor(W.normal(net.n_params, 5001).astype(np.float32), device=dev), head_scale=0.1)
+    # one forward and one training sample, timed alone
+    out1 = torch.empty(prob["n"], dtype=torch.float64, device=dev)
+    lacc = torch.zeros(1, dtype=torch.float64, device=dev)
+    t_pred = time_events(torch, lambda: net.predict(Bs[3, 0], Ps[2, 0], Ps[1, 0], out=out1), 5)
+    t_lg = time_events(torch, lambda: net.loss_grad(Bs[3, 0], Ps[2, 0], Ps[1, 0], Ps[3, 0], loss=lacc), 5)
+    net.init_params(torch.as_tensor(W.normal(net.n_params, 5001).astype(np.float32), device=dev), head_scale=0.1)
+    tr = gp.train(torch, net, Bs, Ps, train_pairs, epochs=epochs, batch=4, lr=2e-3, lr_final=2e-4, seed=5002)
+    ev = gp.evaluate(torch, prob, net, Bs, Ps, range(steps - holdout, steps), chains)
+    conv_flops = 0
+    for name, kind, ci, co in _unet_layers():
+        if kind == "conv3":
+            lvl = int(name[3])
+            conv_flops += 2 * 27 * ci * co * (prob["n"] >> (3 * lvl))
+    return {"grid": f"rbc {n}^3 tanh 1.4", "params": net.n_params, "chains": chains, "steps": steps,
+            "holdout": holdout, "full_config": bool(args.guess_full), "generate": gen,
+            "predict_ms": t_pred, "train_sample_ms": t_lg,
+            "forward_conv_tflops": conv_flops / (t_pred * 1e-3) / 1e12,
+            "train": {k: v for k, v in tr.items()}, "eval": ev}
+
+
+def _unet_layers(channels=(8, 16, 32, 48)):
+    """(name, kind, c_in, c_out) of the guess network (3x3x3 convolutions only matter for the
+    flop count)."""
+    out = []
+    cin = 3
+    for l, c in enumerate(channels):
+        out += [(f"enc{l}a", "conv3", cin, c), (f"enc{l}b", "conv3", c, c)]
+        cin = c
+    for l in range(len(channels) - 2, -1, -1):
+        out += [(f"up{l}", "up", channels[l + 1], channels[l]), (f"dec{l}a", "conv3", 2 * channels[l], channels[l]),
+                (f"dec{l}b", "conv3", channels[l], channels[l])]
+    return out
+
+
 def cpu_baseline(g, budget_s=15.0):
     """The oracle (scipy FP64, one core) on the same step: each SpMM as k separate SpMVs."""
     from oracle import fvm, spmm
@@ -572,6 +628,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="timed step only (no e2e, sweeps, solves, CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-guess", action="store_true", help="skip the learned-guess section")
+    ap.add_argument("--guess-full", action="store_true",
+                    help="learned guess on the full data set: 8 sequences x 252 steps (1800 training, 200 test "
+                         "pairs); the default uses 8 x 40 steps to keep the run within minutes")
+    ap.add_argument("--guess-epochs", type=int, default=None)
     ap.add_argument("--nvtx", action="store_true",
                     help="NVTX ranges around the timed region ('timed_step') and each SpMM (its label), for ncu filters")
     ap.add_argument("--traffic", type=float, default=None,

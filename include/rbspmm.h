@@ -381,8 +381,8 @@ rb_status rb_guess_predict(rb_guess_t g, const double* b, const double* p1, cons
 
 /* Forward and backward pass for one training pair with target p (the solver's p_t): the
  * loss is mean_i (y_i - mean(y) - t_i + mean(t))^2 with t = (p - p1) / s_p, and its gradient
- * is added to the gradient buffer (zeroed first when accumulate == 0).  *loss (device, may
- * be NULL) receives the loss. */
+ * is added to the gradient buffer (zeroed first when accumulate == 0).  The loss is added
+ * to *loss (device, may be NULL), so that one scalar can sum a minibatch or an epoch. */
 rb_status rb_guess_loss_grad(rb_guess_t g, const double* b, const double* p1, const double* p2, const double* p,
                              int32_t accumulate, double* loss, rb_stream_t stream);
 

@@ -1507,7 +1507,7 @@ extern "C" rb_status rb_guess_predict(rb_guess_t g, const double* b, const doubl
   return RB_OK;
 }
 
-__global__ void k_copy_loss(const double* __restrict__ sum, double* __restrict__ dst) { *dst = *sum; }
+__global__ void k_add_loss(const double* __restrict__ sum, double* __restrict__ dst) { *dst += *sum; }
 
 extern "C" rb_status rb_guess_loss_grad(rb_guess_t g, const double* b, const double* p1, const double* p2,
                                         const double* p, int32_t accumulate, double* loss, rb_stream_t stream) {
@@ -1524,7 +1524,7 @@ extern "C" rb_status rb_guess_loss_grad(rb_guess_t g, const double* b, const dou
   k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 6, 1.0 / n0);  // scal[6] = loss
   RB_CUDA(cudaGetLastError());
   if (loss) {
-    k_copy_loss<<<1, 1, 0, s>>>(g->scal + 6, loss);
+    k_add_loss<<<1, 1, 0, s>>>(g->scal + 6, loss);
     RB_CUDA(cudaGetLastError());
   }
   return backward(g, s);

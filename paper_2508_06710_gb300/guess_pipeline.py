@@ -81,7 +81,6 @@ def train(torch, net: Guess, Bs, Ps, train_pairs, epochs, batch=4, lr=1e-3, seed
     learning rate decays geometrically from lr to lr_final over the run.  Returns the
     per-epoch mean loss and the wall time."""
     rng = np.random.default_rng(seed)
-    loss = torch.zeros(1, dtype=torch.float64, device=Bs.device)
     acc = torch.zeros(1, dtype=torch.float64, device=Bs.device)
     history = []
     total = epochs * (len(train_pairs) // batch)
@@ -96,8 +95,7 @@ def train(torch, net: Guess, Bs, Ps, train_pairs, epochs, batch=4, lr=1e-3, seed
         for bi in range(nb):
             for j in range(batch):
                 t, c = train_pairs[order[bi * batch + j]]
-                net.loss_grad(Bs[t, c], Ps[t - 1, c], Ps[t - 2, c], Ps[t, c], accumulate=j > 0, loss=loss)
-                acc.add_(loss)
+                net.loss_grad(Bs[t, c], Ps[t - 1, c], Ps[t - 2, c], Ps[t, c], accumulate=j > 0, loss=acc)
             rate = lr * (lr_final / lr) ** (step / max(1, total - 1))
             net.adam_step(lr=rate, grad_scale=1.0 / batch)
             step += 1

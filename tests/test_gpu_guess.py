@@ -120,6 +120,7 @@ def test_training_reduces_the_loss(rb):
     g.loss_grad(bd, p1d, p2d, td, loss=loss)
     first = loss.item()
     for _ in range(60):
+        loss.zero_()
         g.loss_grad(bd, p1d, p2d, td, loss=loss)
         g.adam_step(lr=3e-3)
     assert loss.item() < 0.5 * first, (first, loss.item())
