@@ -65,9 +65,9 @@ __device__ __forceinline__ void tap_offsets(int tap, int& dx, int& dy, int& dz) 
 // A is gathered from the input cells' neighbours (16 bytes = 8 channels of one tap per
 // copy, zeros past a wall), B is the weight matrix [NP][kpad] (K-major, zero padded), held
 // in shared memory for the whole launch.  One CTA of 128 threads (thread = cell row of the
-// 128-cell tile) runs a ring of kStages A stages of kKS K-columns: cp.async gathers fill a
-// stage, one thread issues its two MMAs and commits them to the stage's mbarrier, which frees
-// the stage for the gather kStages - 1 stages later.  Two TMEM accumulators alternate
+// 128-cell tile) runs a ring of kStages A slots of kKS K-columns: cp.async gathers run
+// kAhead stages ahead, one thread issues a stage's two MMAs and commits them to the slot's
+// mbarrier, which frees the slot for the gather kStages - kAhead stages later.  Two TMEM accumulators alternate
 // between tiles, and a tile's epilogue (TMEM -> registers -> bias, ReLU / mask -> BF16) runs
 // after the next tile's first MMAs have been issued.
 //
@@ -77,10 +77,14 @@ __device__ __forceinline__ void tap_offsets(int tap, int& dx, int& dy, int& dz) 
 
 constexpr int kConvThreads = 128;
 constexpr int kKS = 32;                     // K columns per stage (two K = 16 MMAs)
-constexpr int kStages = 4;                  // A ring depth
+constexpr int kStages = 8;                  // A ring slots
+constexpr int kAhead = 4;                   // stages gathered ahead of the one being issued
+// A slot is refilled kStages - kAhead stages after its MMAs were issued, so the gathers never
+// wait for the tensor cores' latency of the stage just issued.
 constexpr int kAStage = 128 * kKS * 2;      // bytes of one A stage (8 KB)
 constexpr uint32_t kSboA = (kKS / 8) * 128; // A: core matrices adjacent along M
 constexpr size_t kMaxConvSmem = 200 * 1024;
+constexpr int kMaxChunks = 512;             // K_pad / 8 of any convolution (27 c_in <= 4096)
 
 struct Conv3Args {
   const bf16* x = nullptr;
@@ -109,6 +113,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
   __shared__ __align__(8) uint64_t acc_bar[2];
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ int chunk_tab[kMaxChunks];
   constexpr uint32_t kCols = tmem_cols_for(2 * NP);
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t sB = smem_u32(smem);
@@ -137,33 +142,39 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
                a.w + (size_t)n * a.kpad + (size_t)q * 8, 16);
   }
 
+  // per 16-byte K chunk q (8 channels of one tap): packed (dx+1) | (dy+1) << 2 | (dz+1) << 4 |
+  // ci0 << 8, or -1 past the 27 taps; built once per CTA so the gathers divide nothing
+  for (int q = tid; q < kc; q += kConvThreads) {
+    const int kk = q * 8, tap = kk / a.cin;
+    chunk_tab[q] = tap < 27 ? ((tap % 3) | ((tap / 3) % 3) << 2 | (tap / 9) << 4 | (kk - tap * a.cin) << 8) : -1;
+  }
+  __syncthreads();
+  // the cell of this thread in the tile last decomposed (tiles change every S stages)
+  int cur_ti = -1, cx = 0, cy = 0, cz = 0;
+  bool cvalid = false;
+
   // gather of stage j (tile j / S, K columns [(j % S) kKS, +kKS)) into ring slot j % kStages
   auto load_stage = [&](int j) {
     const int ti = j / S, s = j - ti * S;
-    const int t = (int)blockIdx.x + ti * (int)gridDim.x;
-    const int v = t * 128 + tid;
-    const bool valid = v < a.n_vox;
-    int x = 0, y = 0, z = 0;
-    if (valid) {
-      x = v % a.d.nx;
+    if (ti != cur_ti) {
+      cur_ti = ti;
+      const int v = ((int)blockIdx.x + ti * (int)gridDim.x) * 128 + tid;
+      cvalid = v < a.n_vox;
       const int r = v / a.d.nx;
-      y = r % a.d.ny;
-      z = r / a.d.ny;
+      cx = v - r * a.d.nx;
+      cz = r / a.d.ny;
+      cy = r - cz * a.d.ny;
     }
     const uint32_t dst = sA + (uint32_t)(j % kStages) * kAStage + (uint32_t)(tid >> 3) * kSboA + (uint32_t)(tid & 7) * 16;
 #pragma unroll
     for (int jq = 0; jq < kKS / 8; ++jq) {
-      const int kk = (s * (kKS / 8) + jq) * 8;
-      const int tap = kk / a.cin;
-      const int ci0 = kk - tap * a.cin;
+      const int e = chunk_tab[s * (kKS / 8) + jq];
       const bf16* src = a.x;
       uint32_t bytes = 0;
-      if (valid && tap < 27) {
-        int dx, dy, dz;
-        tap_offsets(tap, dx, dy, dz);
-        const int nb = neighbour(a.d, x, y, z, dx, dy, dz);
+      if (cvalid && e >= 0) {
+        const int nb = neighbour(a.d, cx, cy, cz, (e & 3) - 1, ((e >> 2) & 3) - 1, ((e >> 4) & 3) - 1);
         if (nb >= 0) {
-          src = a.x + (size_t)nb * a.ldx + ci0;
+          src = a.x + (size_t)nb * a.ldx + (e >> 8);
           bytes = 16;
         }
       }
@@ -213,8 +224,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
     }
   };
 
-  // prologue: weights and the first kStages - 1 stages (the weights ride in group 0)
-  for (int j = 0; j < kStages - 1; ++j) {
+  // prologue: weights and the first kAhead stages (the weights ride in group 0)
+  for (int j = 0; j < kAhead; ++j) {
     if (j < T) load_stage(j);
     cp_async_commit();
   }
@@ -225,7 +236,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
 
   for (int j = 0; j < T; ++j) {
     const int ti = j / S, s = j - ti * S;
-    cp_async_wait<kStages - 2>();  // stage j has landed (this thread's copies)
+    cp_async_wait<kAhead - 1>();  // stage j has landed (this thread's copies)
     fence_proxy_async();
     if (__syncthreads_or(fail)) break;
     if (tid == 0) {
@@ -241,10 +252,11 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
       umma_commit(&slot_bar[slot]);
       if (s == S - 1) umma_commit(&acc_bar[ti & 1]);
     }
-    // refill the slot of stage j - 1 with stage j + kStages - 1 once stage j - 1's MMAs are done
-    const int jn = j + kStages - 1;
+    // gather stage j + kAhead into the slot of stage j + kAhead - kStages once its MMAs are done
+    const int jn = j + kAhead;
     if (jn < T) {
-      if (j >= 1 && !mbar_wait(&slot_bar[(j - 1) % kStages], (uint32_t)((j - 1) / kStages) & 1u)) fail = 1;
+      const int jo = jn - kStages;
+      if (jo >= 0 && !mbar_wait(&slot_bar[jo % kStages], (uint32_t)(jo / kStages) & 1u)) fail = 1;
       if (!fail) load_stage(jn);
     }
     cp_async_commit();
@@ -253,6 +265,204 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
   }
   cp_async_wait_all();
   // drain: every MMA this CTA issued has completed before TMEM is released
+  if (tid == 0) {
+    umma_commit(&drain_bar);
+    if (!mbar_wait(&drain_bar, 0)) fail = 1;
+  }
+  if (fail && a.err) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// ------------------------------------------------ 3x3x3 convolution on 128-cell rows (MMA)
+//
+// When a grid row holds exactly 128 cells (the MMA's M), the 27 taps need no gathered copy:
+// each CTA keeps the three input lines (z - 1, z, z + 1) of four consecutive y rows in a
+// shared-memory ring, one line = 130 cells (the row plus its x neighbours, wrapped or zero)
+// of 8 channels (16 bytes) per channel group, and the A operand of tap (dz, dy, dx) is a
+// descriptor into line (z + dz, y + dy) starting at cell dx + 1: core matrices of 8 cells are
+// 128 bytes apart (SBO), and the second K core of an MMA is the next channel group (LBO =
+// the group stride) or, with 8 channels, the next x offset (LBO = 16 bytes; the third x
+// offset of a line pairs with zero weights).  Each input line is loaded for three y rows
+// instead of being gathered for 27 taps.  A CTA walks kRowChunk consecutive rows of one z
+// plane; the loads of row y + 2 overlap the MMAs of row y and the epilogue of row y - 1.
+constexpr int kRowW = 128;
+constexpr int kRowPos = kRowW + 2;
+constexpr int kRowChunk = 16;
+constexpr uint32_t kLineBytes = kRowPos * 16;
+constexpr uint32_t kGroupBytes = 12 * kLineBytes;  // 3 z lines x 4 ring slots
+
+__host__ __device__ inline int row_k(int cin) { return cin == 8 ? 9 * 4 * 8 : 27 * cin; }
+inline size_t row_smem(int np, int cin) {
+  return (size_t)np * row_k(cin) * 2 + (size_t)(cin / 8) * kGroupBytes + 256;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t acc_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_slot;
+  constexpr uint32_t kCols = tmem_cols_for(2 * NP);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int G = a.cin / 8;
+  const int krow = row_k(a.cin);
+  const uint32_t sB = smem_u32(smem);
+  const uint32_t sL = sB + (uint32_t)(NP * krow * 2);
+  const uint32_t sbo_b = (uint32_t)(krow / 8) * 128;
+  const int ny = a.d.ny, nz = a.d.nz;
+  const int chunks_y = (ny + kRowChunk - 1) / kRowChunk;
+  const int items = nz * chunks_y;
+  const uint32_t idesc = umma_idesc_bf16(128, NP, false, false);
+
+  if (tid == 0) {
+    mbar_init(&acc_bar[0], 1);
+    mbar_init(&acc_bar[1], 1);
+    mbar_init(&drain_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+  // the 256 bytes after the last line are read (times zero weights) by the last core matrix of
+  // the third x offset with 8-channel inputs: keep them finite
+  if (tid < 16) {
+    const uint32_t pad = sL + (uint32_t)G * kGroupBytes + (uint32_t)tid * 16;
+    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(pad), "r"(0u) : "memory");
+  }
+  const int kcw = krow / 8;
+  for (int i = tid; i < NP * kcw; i += kConvThreads) {
+    const int n = i / kcw, q = i - n * kcw;
+    cp_async16(sB + (uint32_t)(n >> 3) * sbo_b + (uint32_t)q * 128 + (uint32_t)(n & 7) * 16,
+               a.w + (size_t)n * krow + (size_t)q * 8, 16);
+  }
+  cp_async_commit();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  auto line_addr = [&](int cg, int dzi, int yy) -> uint32_t {
+    return sL + (uint32_t)cg * kGroupBytes + (uint32_t)(dzi * 4 + (yy & 3)) * kLineBytes;
+  };
+  // the three z lines of row yy into ring slot yy & 3
+  auto load_row = [&](int z, int yy) {
+    int yw = yy;
+    bool yok = true;
+    if (yw < 0 || yw >= ny) {
+      if (a.d.py) yw = yw < 0 ? yw + ny : yw - ny;
+      else yok = false;
+    }
+    for (int dzi = 0; dzi < 3; ++dzi) {
+      int zz = z + dzi - 1;
+      bool ok = yok;
+      if (zz < 0 || zz >= nz) {
+        if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
+        else ok = false;
+      }
+      const size_t row0 = ((size_t)zz * ny + yw) * kRowW;
+      for (int cg = 0; cg < G; ++cg) {
+        const uint32_t dst = line_addr(cg, dzi, yy);
+        for (int pos = tid; pos < kRowPos; pos += kConvThreads) {
+          int x = pos - 1;
+          bool okx = ok;
+          if (x < 0 || x >= kRowW) {
+            if (a.d.px) x = x < 0 ? x + kRowW : x - kRowW;
+            else okx = false;
+          }
+          cp_async16(dst + (uint32_t)pos * 16, okx ? (const void*)(a.x + (row0 + x) * a.ldx + cg * 8) : (const void*)a.x,
+                     okx ? 16u : 0u);
+        }
+      }
+    }
+  };
+
+  int fail = 0;
+  int tcount = 0;  // tiles (rows) this CTA has issued: selects the accumulator and barrier phase
+  auto epilogue = [&](int e, int z, int y) {
+    const int b = e & 1;
+    if (!mbar_wait(&acc_bar[b], (uint32_t)(e >> 1) & 1u)) fail = 1;
+    tc_fence_after();
+    const int v = (z * ny + y) * kRowW + tid;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NP);
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+      float acc[16];
+      tmem_ld16(taddr + (uint32_t)c0, acc);
+      if (fail) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cb = c0 + 8 * h;
+        if (cb >= a.cout) continue;
+        float o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float val = acc[8 * h + i];
+          if (a.bias) val += __ldg(a.bias + cb + i);
+          if (a.relu) val = fmaxf(val, 0.0f);
+          o[i] = val;
+        }
+        if (a.mask) {
+          const uint4 mq = *reinterpret_cast<const uint4*>(a.mask + (size_t)v * a.ldm + cb);
+          const bf16* mv = reinterpret_cast<const bf16*>(&mq);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (!(__bfloat162float(mv[i]) > 0.0f)) o[i] = 0.0f;
+        }
+        uint4 q;
+        __nv_bfloat162* qp = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) qp[i] = __floats2bfloat162_rn(o[2 * i], o[2 * i + 1]);
+        *reinterpret_cast<uint4*>(a.y + (size_t)v * a.ldy + cb) = q;
+      }
+    }
+  };
+
+  for (int it = blockIdx.x; it < items && !fail; it += gridDim.x) {
+    const int z = it / chunks_y;
+    const int y0 = (it - z * chunks_y) * kRowChunk;
+    const int y1 = min(ny, y0 + kRowChunk);
+    load_row(z, y0 - 1);
+    load_row(z, y0);
+    load_row(z, y0 + 1);
+    cp_async_commit();
+    int prev_y = -1;
+    for (int y = y0; y < y1; ++y) {
+      cp_async_wait<0>();  // rows y - 1 .. y + 1 (and the weights) have landed
+      fence_proxy_async();
+      if (__syncthreads_or(fail)) break;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)((tcount & 1) * NP);
+        uint32_t kk = 0;
+        if (G == 1) {
+          for (int li = 0; li < 9; ++li) {
+            const uint32_t base = line_addr(0, li / 3, y + li % 3 - 1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h, ++kk)
+              umma_bf16(d, umma_sdesc(base + 32u * h, 16, 128), umma_sdesc(sB + kk * 256, 128, sbo_b), idesc,
+                        kk > 0 ? 1u : 0u);
+          }
+        } else {
+          for (int tap = 0; tap < 27; ++tap) {
+            const int dzi = tap / 9, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            for (int cp = 0; cp < G / 2; ++cp, ++kk)
+              umma_bf16(d, umma_sdesc(line_addr(2 * cp, dzi, y + dy) + (uint32_t)(1 + dx) * 16, kGroupBytes, 128),
+                        umma_sdesc(sB + kk * 256, 128, sbo_b), idesc, kk > 0 ? 1u : 0u);
+          }
+        }
+        umma_commit(&acc_bar[tcount & 1]);
+      }
+      // row y + 2 goes into the ring slot of row y - 2, read last by the MMAs of row y - 1
+      if (prev_y >= 0 && !mbar_wait(&acc_bar[(tcount - 1) & 1], (uint32_t)((tcount - 1) >> 1) & 1u)) fail = 1;
+      if (y + 2 <= y1 && !fail) load_row(z, y + 2);
+      cp_async_commit();
+      if (prev_y >= 0) epilogue(tcount - 1, z, prev_y);
+      prev_y = y;
+      ++tcount;
+    }
+    if (prev_y >= 0) epilogue(tcount - 1, z, prev_y);
+  }
+  cp_async_wait_all();
   if (tid == 0) {
     umma_commit(&drain_bar);
     if (!mbar_wait(&drain_bar, 0)) fail = 1;
@@ -315,52 +525,71 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
   }
   if (warp == 0) tmem_alloc(&tmem_slot, kCols);
 
+  // this thread's A row groups (grp = tid / 32 + 4 r): gather (tap offsets, ci0), the ones
+  // row, or zeros; fixed for the CTA's m tile, so decoded once
+  constexpr int kAG = (kWS * 16) / kConvThreads;  // A groups per thread per stage (4)
+  int gcode[kAG];
+#pragma unroll
+  for (int r = 0; r < kAG; ++r) {
+    const int m = mt * 128 + (tid / kWS + r * (kConvThreads / kWS)) * 8;
+    if (m < a.rows) {
+      const int tap = m / a.cin;
+      gcode[r] = (tap % 3) | ((tap / 3) % 3) << 2 | (tap / 9) << 4 | (m - tap * a.cin) << 8;
+    } else {
+      gcode[r] = m == a.rows ? -1 : -2;  // -1: the ones row, -2: zeros
+    }
+  }
+  const int kcell = tid % kWS;  // the cell column of every copy this thread makes
+
   auto load_stage = [&](int j) {
     const int slot = j % kStages;
     const uint32_t a_base = sA + (uint32_t)slot * kWAStage;
     const uint32_t b_base = sB + (uint32_t)slot * kWBStage;
+    const int v = v0 + j * kWS + kcell;
+    const bool valid = v < v1;
+    int x = 0, y = 0, z = 0;
+    if (valid) {
+      const int r = v / a.d.nx;
+      x = v - r * a.d.nx;
+      z = r / a.d.ny;
+      y = r - z * a.d.ny;
+    }
     // A: 32 cells x 16 groups of 8 rows
 #pragma unroll
-    for (int r = 0; r < (kWS * 16) / kConvThreads; ++r) {
-      const int i = tid + r * kConvThreads;
-      const int k = i % kWS, grp = i / kWS;
-      const int v = v0 + j * kWS + k;
-      const int m = mt * 128 + grp * 8;
-      const uint32_t dst = a_base + (uint32_t)(k >> 3) * kLboWA + (uint32_t)grp * 128 + (uint32_t)(k & 7) * 16;
-      if (m == a.rows) {  // the ones row (bias gradient), then zeros
+    for (int r = 0; r < kAG; ++r) {
+      const int grp = tid / kWS + r * (kConvThreads / kWS);
+      const uint32_t dst = a_base + (uint32_t)(kcell >> 3) * kLboWA + (uint32_t)grp * 128 + (uint32_t)(kcell & 7) * 16;
+      const int e = gcode[r];
+      if (e < 0) {
         uint4 q = make_uint4(0, 0, 0, 0);
-        if (v < v1) q.x = 0x3F80u;  // BF16 1.0 in the low half
+        if (e == -1 && valid) q.x = 0x3F80u;  // BF16 1.0 in the low half: the bias row
         asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(q.x), "r"(q.y), "r"(q.z), "r"(q.w)
                      : "memory");
         continue;
       }
       const bf16* src = a.x;
       uint32_t bytes = 0;
-      if (m < a.rows && v < v1) {
-        const int tap = m / a.cin;
-        const int ci0 = m - tap * a.cin;
-        int dx, dy, dz;
-        tap_offsets(tap, dx, dy, dz);
-        const int x = v % a.d.nx, rr = v / a.d.nx;
-        const int nb = neighbour(a.d, x, rr % a.d.ny, rr / a.d.ny, dx, dy, dz);
+      if (valid) {
+        const int nb = neighbour(a.d, x, y, z, (e & 3) - 1, ((e >> 2) & 3) - 1, ((e >> 4) & 3) - 1);
         if (nb >= 0) {
-          src = a.x + (size_t)nb * a.ldx + ci0;
+          src = a.x + (size_t)nb * a.ldx + (e >> 8);
           bytes = 16;
         }
       }
       cp_async16(dst, src, bytes);
     }
     // B: 32 cells x NP / 8 groups
-    for (int i = tid; i < kWS * (NP / 8); i += kConvThreads) {
-      const int k = i % kWS, grp = i / kWS;
-      const int v = v0 + j * kWS + k;
-      const uint32_t dst = b_base + (uint32_t)(k >> 3) * kLboWB + (uint32_t)grp * 128 + (uint32_t)(k & 7) * 16;
-      const bool ok = v < v1 && grp * 8 < a.cout;
+#pragma unroll
+    for (int r = 0; r < (kWS * (NP / 8) + kConvThreads - 1) / kConvThreads; ++r) {
+      const int grp = tid / kWS + r * (kConvThreads / kWS);
+      if (grp >= NP / 8) break;
+      const uint32_t dst = b_base + (uint32_t)(kcell >> 3) * kLboWB + (uint32_t)grp * 128 + (uint32_t)(kcell & 7) * 16;
+      const bool ok = valid && grp * 8 < a.cout;
       cp_async16(dst, ok ? (const void*)(a.g + (size_t)v * a.ldg + grp * 8) : (const void*)a.g, ok ? 16u : 0u);
     }
   };
 
-  for (int j = 0; j < kStages - 1; ++j) {
+  for (int j = 0; j < kAhead; ++j) {
     if (j < T) load_stage(j);
     cp_async_commit();
   }
@@ -370,7 +599,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
   const uint32_t tmem = tmem_slot;
   int fail = 0;
   for (int j = 0; j < T; ++j) {
-    cp_async_wait<kStages - 2>();
+    cp_async_wait<kAhead - 1>();
     fence_proxy_async();
     if (__syncthreads_or(fail)) break;
     if (tid == 0) {
@@ -384,9 +613,10 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
       }
       umma_commit(&slot_bar[slot]);
     }
-    const int jn = j + kStages - 1;
+    const int jn = j + kAhead;
     if (jn < T) {
-      if (j >= 1 && !mbar_wait(&slot_bar[(j - 1) % kStages], (uint32_t)((j - 1) / kStages) & 1u)) fail = 1;
+      const int jo = jn - kStages;
+      if (jo >= 0 && !mbar_wait(&slot_bar[jo % kStages], (uint32_t)(jo / kStages) & 1u)) fail = 1;
       if (!fail) load_stage(jn);
     }
     cp_async_commit();
@@ -423,10 +653,14 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, int splits, int m
                                int cout, float* __restrict__ gw, float* __restrict__ gb) {
   const int rows = 27 * cin_pad;
   const int total = (rows + 1) * cout;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < total; i += warps) {
     const int m = i / cout, n = i - m * cout;
     float s = 0.0f;
-    for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * mpad + m) * np + n];
+    for (int sp = lane; sp < splits; sp += 32) s += part[((size_t)sp * mpad + m) * np + n];
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane != 0) continue;
     if (m == rows) {
       gb[n] += s;
     } else {
@@ -459,13 +693,21 @@ __device__ void block_sum_store(double (&v)[NQ], double* __restrict__ part) {
   }
 }
 
-// out[q] = scale * sum over blocks (fixed order); one block
-__global__ void k_finish(const double* __restrict__ part, int nblk, int nq, double* __restrict__ out, double scale) {
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * nq + q];
-    out[q] = scale * s;
+// out[q] = scale * sum over blocks; one block of 256 threads per quantity q (grid nq), each
+// thread a fixed strided subset, then a fixed-shape tree: the same order on every run.
+__global__ void __launch_bounds__(256) k_finish(const double* __restrict__ part, int nblk, int nq,
+                                                double* __restrict__ out, double scale) {
+  __shared__ double sh[256];
+  const int q = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 256) s += part[(size_t)b * nq + q];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w >= 1; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) out[q] = scale * sh[0];
 }
 
 // sums of b^2 and p1^2 (for the scales s_b, s_p)
@@ -669,12 +911,16 @@ __global__ void __launch_bounds__(256) k_up_dw(const bf16* __restrict__ x, int l
   }
 }
 
-// gw[i] += sum over blocks part[b][i] for the transposed convolution's (co, o, ci) + bias layout
+// dst[i] += sum over blocks part[b][i] for the transposed convolution's (co, o, ci) + bias
+// layout; one warp per output, lanes over the blocks, a fixed shuffle tree
 __global__ void k_sum_parts(const float* __restrict__ part, int nblk, int n, float* __restrict__ dst) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
     float s = 0.0f;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * n + i];
-    dst[i] += s;
+    for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * n + i];
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) dst[i] += s;
   }
 }
 
@@ -835,6 +1081,38 @@ __global__ void k_pack_conv3(const float* __restrict__ W, int cin, int cin_pad, 
   }
 }
 
+// BF16 weights of a 3x3x3 convolution in the row kernel's K order, [np][row_k(C)] for an input
+// of C channels: with C = 8 the K cores per (dz, dy) line are x offsets -1, 0, +1 and a zero
+// core; otherwise K = tap * C + c.  Forward (dgrad = 0): rows n = output channel < cout,
+// c = input channel < cin.  Input gradient: rows n = input channel < cin, c = output channel,
+// taps flipped.
+__global__ void k_pack_row(const float* __restrict__ W, int cin, int cout, int dgrad, int C, int np,
+                           bf16* __restrict__ dst) {
+  const int kr = row_k(C);
+  const int nrows = dgrad ? cin : cout;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np * kr; i += gridDim.x * blockDim.x) {
+    const int n = i / kr, K = i - n * kr;
+    int tap, c;
+    if (C == 8) {
+      const int core = K >> 3, r = core & 3;
+      c = K & 7;
+      tap = r < 3 ? (core >> 2) * 3 + r : -1;
+    } else {
+      tap = K / C;
+      c = K - tap * C;
+    }
+    float v = 0.0f;
+    if (tap >= 0 && n < nrows) {
+      if (!dgrad) {
+        if (c < cin) v = W[((size_t)n * 27 + tap) * cin + c];
+      } else if (c < cout) {
+        v = W[((size_t)c * 27 + (26 - tap)) * cin + n];
+      }
+    }
+    dst[i] = __float2bfloat16(v);
+  }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ a, int n, bf16* __restrict__ out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = __float2bfloat16(a[i]);
 }
@@ -889,6 +1167,8 @@ struct Layer {
   int np = 0, kpad = 0, npd = 0, kpadd = 0, mpad = 0;  // conv3 packing
   bf16* wf = nullptr;
   bf16* wd = nullptr;
+  bf16* wf_row = nullptr;  // row-kernel layouts (level-0 rows of 128 cells), or null
+  bf16* wd_row = nullptr;
   bf16* wu = nullptr;  // up: BF16 [cout][8][cin]
 };
 
@@ -1002,22 +1282,47 @@ int guess_sm_count() {
   return sms;
 }
 
+// CTAs of `kernel` that one SM holds at once: the tightest of threads, registers, shared
+// memory (dynamic + static + the per-block reserve) and tensor memory (512 columns per SM).
+int blocks_per_sm(const void* kernel, size_t dyn_smem, int threads, uint32_t tmem_cols) {
+  cudaFuncAttributes fa{};
+  int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0, resv = 0;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  int n = std::min(blk_sm, thr_sm / threads);
+  const int regs = std::max(1, fa.numRegs) * threads;
+  n = std::min(n, regs_sm / regs);
+  const size_t per_block = dyn_smem + fa.sharedSizeBytes + (size_t)resv;
+  n = std::min<int>(n, (int)(smem_sm / std::max<size_t>(per_block, 1)));
+  n = std::min<int>(n, (int)(512 / tmem_cols));
+  return std::max(1, n);
+}
+
 size_t conv_smem(int np, int kpad) { return (size_t)np * kpad * 2 + (size_t)kStages * kAStage; }
 
 template <int NP>
 rb_status launch_conv3_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
   auto* kern = &k_conv3_mma<NP>;
-  static size_t opted = 0;
+  static size_t opted = 48 * 1024;  // largest dynamic shared memory requested so far
   if (smem > opted) {
-    RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxConvSmem));
-    opted = kMaxConvSmem;
+    RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    opted = smem;
   }
   const int n_tiles = (a.n_vox + 127) / 128;
-  // TMEM: 512 columns per SM, so at most 512 / cols of these CTAs may hold an allocation at once
-  const int per_sm_tmem = (int)(512 / tmem_cols_for(2 * NP));
-  const int cap = std::min(resident_blocks(reinterpret_cast<const void*>(kern), smem, kConvThreads),
-                           per_sm_tmem * guess_sm_count());
-  const int grid = std::max(1, std::min(n_tiles, cap));
+  static int per_sm = 0;
+  static size_t per_sm_smem = 0;
+  if (per_sm == 0 || per_sm_smem != smem) {
+    per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kConvThreads, tmem_cols_for(2 * NP));
+    per_sm_smem = smem;
+  }
+  const int grid = std::max(1, std::min(n_tiles, per_sm * guess_sm_count()));
   kern<<<grid, kConvThreads, smem, s>>>(a);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
@@ -1034,8 +1339,48 @@ int enc_idx(int l, int s) { return 2 * l + s; }
 int dec_base(const rb_guess* g, int l) { return 2 * g->L + 3 * (g->L - 2 - l); }
 int head_idx(const rb_guess* g) { return 2 * g->L + 3 * (g->L - 1); }
 
+template <int NP>
+rb_status launch_row_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
+  auto* kern = &k_conv3_row<NP>;
+  static size_t opted = 48 * 1024;
+  if (smem > opted) {
+    RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    opted = smem;
+  }
+  static int per_sm = 0;
+  static size_t per_sm_smem = 0;
+  if (per_sm == 0 || per_sm_smem != smem) {
+    per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kConvThreads, tmem_cols_for(2 * NP));
+    per_sm_smem = smem;
+  }
+  const int items = a.d.nz * ((a.d.ny + kRowChunk - 1) / kRowChunk);
+  const int grid = std::max(1, std::min(items, per_sm * guess_sm_count()));
+  kern<<<grid, kConvThreads, smem, s>>>(a);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+// the row kernel takes grids whose rows are 128 cells and inputs of 8 or an even number of
+// 8-channel groups
+bool row_kernel_fits(const Dims& d, int cin, int np) {
+  return d.nx == kRowW && (cin == 8 || (cin % 16 == 0)) && np <= 64 && row_smem(np, cin) <= kMaxConvSmem;
+}
+
+rb_status row_launch(const Conv3Args& a, int np, cudaStream_t s) {
+  const size_t smem = row_smem(np, a.cin);
+  switch (np) {
+    case 16: return launch_row_np<16>(a, smem, s);
+    case 32: return launch_row_np<32>(a, smem, s);
+    case 48: return launch_row_np<48>(a, smem, s);
+    case 64: return launch_row_np<64>(a, smem, s);
+  }
+  set_error("rb_guess: no row convolution kernel for %d output channels", np);
+  return RB_EUNSUPPORTED;
+}
+
 rb_status conv3_launch(const Conv3Args& a, int np, cudaStream_t s) {
   const size_t smem = conv_smem(np, a.kpad);
+  RB_REQUIRE(a.kpad / 8 <= kMaxChunks, "rb_guess: convolution with %d input channels too wide", a.cin);
   RB_REQUIRE(smem <= kMaxConvSmem, "rb_guess: convolution weights (%d x %d) exceed shared memory", np, a.kpad);
   switch (np) {
     case 16: return launch_conv3_np<16>(a, smem, s);
@@ -1065,6 +1410,10 @@ rb_status conv3_fwd(rb_guess* g, const Layer& ly, const bf16* x, int ldx, bf16* 
   a.ldy = ldy;
   a.cout = ly.cout;
   a.err = g->err;
+  if (ly.wf_row) {
+    a.w = ly.wf_row;
+    return row_launch(a, ly.np, s);
+  }
   return conv3_launch(a, ly.np, s);
 }
 
@@ -1085,6 +1434,10 @@ rb_status conv3_dgrad(rb_guess* g, const Layer& ly, const bf16* gpre, int ldg, c
   a.ldy = ldgi;
   a.cout = ly.cin_pad;
   a.err = g->err;
+  if (ly.wd_row) {
+    a.w = ly.wd_row;
+    return row_launch(a, ly.npd, s);
+  }
   return conv3_launch(a, ly.npd, s);
 }
 
@@ -1104,6 +1457,11 @@ WgradPlan wgrad_plan(const Layer& ly, int n) {
 template <int NP>
 rb_status launch_wgrad_np(const WgradArgs& a, const WgradPlan& p, cudaStream_t s) {
   const size_t smem = (size_t)kStages * (kWAStage + NP * kWS * 2);
+  static bool opted = false;
+  if (!opted && smem > 48 * 1024) {
+    RB_CUDA(cudaFuncSetAttribute(&k_wgrad_mma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    opted = true;
+  }
   k_wgrad_mma<NP><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
@@ -1138,7 +1496,7 @@ rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, cons
   }
   RB_TRY(st);
   const int total = (a.rows + 1) * ly.cout;
-  k_wgrad_reduce<<<std::min(1024, (total + 255) / 256), 256, 0, s>>>(g->wpart, p.splits, ly.mpad, ly.np, ly.cin_pad,
+  k_wgrad_reduce<<<std::min(4096, (total + 7) / 8), 256, 0, s>>>(g->wpart, p.splits, ly.mpad, ly.np, ly.cin_pad,
                                                                       ly.cin, ly.cout, g->grad + ly.w_off,
                                                                       g->grad + ly.b_off);
   RB_CUDA(cudaGetLastError());
@@ -1170,6 +1528,16 @@ rb_status refresh_weights(rb_guess* g, cudaStream_t s) {
       const int total = ly.np * ly.kpad + ly.npd * ly.kpadd;
       k_pack_conv3<<<std::min(1024, (total + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cin_pad, ly.cout,
                                                                        ly.wf, ly.np, ly.kpad, ly.wd, ly.npd, ly.kpadd);
+      if (ly.wf_row) {
+        const int t = ly.np * row_k(ly.cin_pad);
+        k_pack_row<<<std::min(1024, (t + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cout, 0, ly.cin_pad,
+                                                                   ly.np, ly.wf_row);
+      }
+      if (ly.wd_row) {
+        const int t = ly.npd * row_k(ly.cout);
+        k_pack_row<<<std::min(1024, (t + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cout, 1, ly.cout,
+                                                                   ly.npd, ly.wd_row);
+      }
     } else if (ly.kind == kUp) {
       const int total = 8 * ly.cin * ly.cout;
       k_to_bf16<<<std::min(1024, (total + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, total, ly.wu);
@@ -1185,7 +1553,7 @@ rb_status forward(rb_guess* g, const double* b, const double* p1, const double* 
   const int L = g->L;
   const int n0 = g->dims[0].n();
   k_sumsq2<<<kRedGrid, kRedThreads, 0, s>>>(b, p1, n0, g->red);
-  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 2, g->scal + 2, 1.0 / n0);
+  k_finish<<<2, 256, 0, s>>>(g->red, kRedGrid, 2, g->scal + 2, 1.0 / n0);
   k_make_input<<<grid_for(n0), 256, 0, s>>>(b, p1, p2, n0, g->scal + 2, g->scal, g->x0);
   RB_CUDA(cudaGetLastError());
   for (int l = 0; l < L; ++l) {
@@ -1216,7 +1584,7 @@ rb_status forward(rb_guess* g, const double* b, const double* p1, const double* 
   const Layer& hd = g->layers[head_idx(g)];
   k_head<<<kRedGrid, kRedThreads, 0, s>>>(g->dec_b[0], g->ch[0], g->ch[0], g->theta + hd.w_off, g->theta + hd.b_off, n0,
                                           g->y, g->red);
-  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 2, 1.0 / n0);  // scal[2] = mean y
+  k_finish<<<1, 256, 0, s>>>(g->red, kRedGrid, 1, g->scal + 2, 1.0 / n0);  // scal[2] = mean y
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
@@ -1227,7 +1595,7 @@ rb_status head_bwd_c(rb_guess* g, cudaStream_t s) {
   const int n0 = g->dims[0].n();
   k_head_bwd<C><<<kRedGrid, kRedThreads, 0, s>>>(g->dec_b[0], C, g->theta + hd.w_off, g->gy, n0, g->g_b[0], C, g->red);
   // parameter gradient: head W (C sums) and b, added into grad
-  k_finish<<<1, 64, 0, s>>>(g->red, kRedGrid, C + 1, g->scal + 8, 1.0);
+  k_finish<<<C + 1, 256, 0, s>>>(g->red, kRedGrid, C + 1, g->scal + 8, 1.0);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
@@ -1272,7 +1640,7 @@ rb_status backward(rb_guess* g, cudaStream_t s) {
     const size_t smw = (size_t)kUpChunk * (cc + 8 * c) * 4;
     k_up_dw<<<ug, 256, smw, s>>>(upin, cc, cc, g->g_cat[l], 2 * c, c, g->dims[l], g->wpart);
     const int n_out = 8 * cc * c + c;
-    k_sum_parts<<<grid_for(n_out), 256, 0, s>>>(g->wpart, ug, n_out, g->grad + up.w_off);  // W then b, contiguous
+    k_sum_parts<<<std::min(4096, (n_out + 7) / 8), 256, 0, s>>>(g->wpart, ug, n_out, g->grad + up.w_off);  // W then b, contiguous
     RB_CUDA(cudaGetLastError());
   }
   // encoder, bottom first
@@ -1424,6 +1792,9 @@ extern "C" rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out) {
     if (ly.kind == kConv3) {
       A(&ly.wf, (size_t)ly.np * ly.kpad);
       A(&ly.wd, (size_t)ly.npd * ly.kpadd);
+      const Dims& d = g->dims[ly.level];
+      if (row_kernel_fits(d, ly.cin_pad, ly.np)) A(&ly.wf_row, (size_t)ly.np * row_k(ly.cin_pad));
+      if (ly.cin == ly.cin_pad && row_kernel_fits(d, ly.cout, ly.npd)) A(&ly.wd_row, (size_t)ly.npd * row_k(ly.cout));
     } else if (ly.kind == kUp) {
       A(&ly.wu, (size_t)8 * ly.cin * ly.cout);
     }
@@ -1501,7 +1872,7 @@ extern "C" rb_status rb_guess_predict(rb_guess_t g, const double* b, const doubl
   const int n0 = g->dims[0].n();
   RB_TRY(forward(g, b, p1, p2, s));
   k_sum1<<<kRedGrid, kRedThreads, 0, s>>>(p1, n0, g->red);
-  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 3, 1.0 / n0);  // scal[3] = mean p1
+  k_finish<<<1, 256, 0, s>>>(g->red, kRedGrid, 1, g->scal + 3, 1.0 / n0);  // scal[3] = mean p1
   k_guess_out<<<grid_for(n0), 256, 0, s>>>(p1, g->y, n0, g->scal, g->scal + 2, p_out);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
@@ -1518,10 +1889,10 @@ extern "C" rb_status rb_guess_loss_grad(rb_guess_t g, const double* b, const dou
   if (!accumulate) RB_CUDA(cudaMemsetAsync(g->grad, 0, g->n_params * sizeof(float), s));
   RB_TRY(forward(g, b, p1, p2, s));
   k_sum_diff<<<kRedGrid, kRedThreads, 0, s>>>(p, p1, n0, g->red);
-  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 4, 1.0 / n0);  // scal[4] = mean (p - p1)
+  k_finish<<<1, 256, 0, s>>>(g->red, kRedGrid, 1, g->scal + 4, 1.0 / n0);  // scal[4] = mean (p - p1)
   // k_loss reads means[0] = mean y (scal[2]) and means[2] = mean (p - p1) (scal[4])
   k_loss<<<kRedGrid, kRedThreads, 0, s>>>(p, p1, g->y, n0, g->scal, g->scal + 2, g->gy, g->red);
-  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 1, g->scal + 6, 1.0 / n0);  // scal[6] = loss
+  k_finish<<<1, 256, 0, s>>>(g->red, kRedGrid, 1, g->scal + 6, 1.0 / n0);  // scal[6] = loss
   RB_CUDA(cudaGetLastError());
   if (loss) {
     k_add_loss<<<1, 1, 0, s>>>(g->scal + 6, loss);
@@ -1623,7 +1994,7 @@ extern "C" rb_status rb_guess_select(rb_guess_t g, rb_op_t A, const double* b, c
     }
   }
   k_resid2<<<kRedGrid, kRedThreads, 0, s>>>(b, ax, ax + n0, n0, g->red);
-  k_finish<<<1, 32, 0, s>>>(g->red, kRedGrid, 3, g->scal + 16, 1.0);
+  k_finish<<<3, 256, 0, s>>>(g->red, kRedGrid, 3, g->scal + 16, 1.0);
   k_pick<<<grid_for(n0), 256, 0, s>>>(xs, xs + n0, n0, g->scal + 16, res, choice, x0);
   RB_CUDA(cudaGetLastError());
   return RB_OK;

@@ -41,12 +41,16 @@ def _layer_out(g, i, level_shape, c):
     return a.reshape(level_shape + (c,)).transpose(3, 0, 1, 2)
 
 
-CASES = [((16, 16, 8), (8, 16, 32, 48)), ((10, 6, 6), (8, 16)), ((8, 8, 8), (8, 16, 24))]
+# grids of 128-cell rows run the level-0 convolutions on the row kernel (x wrapped or walled)
+CASES = [((16, 16, 8), (8, 16, 32, 48), (1, 1, 0)), ((10, 6, 6), (8, 16), (1, 1, 0)),
+         ((8, 8, 8), (8, 16, 24), (1, 1, 0)), ((128, 4, 4), (8, 16), (1, 1, 0)),
+         ((128, 8, 4), (8, 16, 32), (0, 1, 1))]
+IDS = ["16x16x8-4lvl", "ragged-10x6x6", "8cube-3lvl", "rows128-periodic-x", "rows128-walled-x"]
 
 
-@pytest.mark.parametrize("shape,channels", CASES, ids=["16x16x8-4lvl", "ragged-10x6x6", "8cube-3lvl"])
-def test_forward_matches_oracle(rb, shape, channels):
-    g, spec, pref, _, (b, p1, p2, _), zyx = _setup(rb, shape, channels, 1100)
+@pytest.mark.parametrize("shape,channels,periodic", CASES, ids=IDS)
+def test_forward_matches_oracle(rb, shape, channels, periodic):
+    g, spec, pref, _, (b, p1, p2, _), zyx = _setup(rb, shape, channels, 1100, periodic)
     out = g.predict(to_dev(b), to_dev(p1), to_dev(p2)).cpu().numpy()
     x0, sb, sp = U.net_input(b, p1, p2, zyx, bf=True)
     y, cache = U.forward(spec, pref, x0, bf=True)
@@ -77,9 +81,9 @@ def test_forward_matches_oracle(rb, shape, channels):
     assert abs(out.mean()) < 1e-9 * np.abs(out).max()
 
 
-@pytest.mark.parametrize("shape,channels", CASES, ids=["16x16x8-4lvl", "ragged-10x6x6", "8cube-3lvl"])
-def test_gradient_matches_oracle(rb, shape, channels):
-    g, spec, pref, _, (b, p1, p2, t), zyx = _setup(rb, shape, channels, 1200)
+@pytest.mark.parametrize("shape,channels,periodic", CASES, ids=IDS)
+def test_gradient_matches_oracle(rb, shape, channels, periodic):
+    g, spec, pref, _, (b, p1, p2, t), zyx = _setup(rb, shape, channels, 1200, periodic)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     g.loss_grad(to_dev(b), to_dev(p1), to_dev(p2), to_dev(t), accumulate=False, loss=loss)
     lref, gref = U.loss_and_grad(spec, pref, b, p1, p2, t, zyx, bf=True)
