@@ -211,6 +211,12 @@ def run_ours(args, rank, world, local):
                      "frac_hbm": by / ms / 1e6 / hbm, "bytes": by, "flops": fl,
                      "fp64_frac": (fl / ms / 1e9 / FP64_PEAK_TFLOPS) if dt == "f64" else None,
                      "schedule": op.schedule(X, Y)})
+    # the ceiling a kernel of this size can reach: a device copy moving the same bytes
+    for r in kern:
+        src = torch.empty(r["bytes"] // 8, dtype=torch.float32, device=dev)
+        dst = torch.empty_like(src)
+        r["copy_frac"] = graph_ms(torch, lambda: dst.copy_(src)) / r["ms"]
+        del src, dst
     dom = max(kern, key=lambda r: r["ms"])
     if dom["kernel"].split("-")[1] == "f64" and dom["flops"] / (FP64_PEAK_TFLOPS * 1e12) > dom["bytes"] / (hbm * 1e9):
         roof = {"bound": "alu", "achieved": dom["gflops"] / 1e3, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -266,23 +272,50 @@ def operator_build(torch, rb, g, dev):
     return res
 
 
+def graph_ms(torch, fn, calls=20, reps=10):
+    """Device time per call of `fn`, from replays of a CUDA graph of `calls` calls (launch
+    latency amortised: what the kernels themselves take back to back)."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(calls):
+            fn()
+    ms = time_events(torch, g.replay, reps)
+    return ms / calls
+
+
 def blas1(torch, rb, dev, n, hbm):
-    """dot, axpy, axty on n x 3 blocks (FP64 and FP32): algorithmic GB/s."""
+    """dot, axpy, axty on n x 3 blocks (FP64 and FP32): algorithmic GB/s per call, timed as
+    back-to-back kernels (graph replays) and as single eager calls (launch latency included);
+    `copy_frac` compares with a device copy moving the same bytes (the ceiling at this size).
+    n is raised to four channel grids (9.4 M rows) so that every operand exceeds L2 even when
+    the replays run back to back."""
+    n = 4 * n
     res = []
     for dt in (torch.float64, torch.float32):
         k = 3
         X = torch.randn((n, k), dtype=dt, device=dev)
         Y = torch.randn((n, k), dtype=dt, device=dev)
+        ones = torch.ones((n, k), dtype=dt, device=dev)
         alpha = torch.full((k,), 1e-3, dtype=torch.float64, device=dev)
         out = torch.empty(k, dtype=torch.float64, device=dev)
         work = torch.empty(rb.lib().rb_dot_workspace_bytes(n, k), dtype=torch.uint8, device=dev)
         s = X.element_size()
         for name, fn, by in (("dot", lambda: rb.dot(X, Y, out=out, work=work), 2 * n * k * s),
                              ("axpy", lambda: rb.axpy(alpha, X, Y), 3 * n * k * s),
-                             ("axty", lambda: rb.axty(1.0, X, Y), 3 * n * k * s)):
-            ms = time_events(torch, fn, 10)
+                             ("axty", lambda: rb.axty(1.0, ones, Y), 3 * n * k * s)):
+            ms = graph_ms(torch, fn)
+            ms_call = time_events(torch, fn, 10)
+            src = torch.empty(by // 8, dtype=torch.float32, device=dev)
+            dst = torch.empty_like(src)
+            ms_copy = graph_ms(torch, lambda: dst.copy_(src))
             res.append({"op": name, "dtype": "f64" if s == 8 else "f32", "k": k, "ms": ms, "gbs": by / ms / 1e6,
-                        "frac_hbm": by / ms / 1e6 / hbm})
+                        "frac_hbm": by / ms / 1e6 / hbm, "copy_frac": ms_copy / ms, "ms_eager_call": ms_call})
+            del src, dst
     return res
 
 

@@ -97,6 +97,164 @@ __global__ void __launch_bounds__(kThreads) k_axty(int64_t n, int k, int kp, T a
 }
 
 
+// Flat streaming of a contiguous block (ld == k, 16-byte aligned): the n k entries as one
+// array of 16-byte vectors, entry f in column f % k.  The grid is a multiple of the odd part of
+// k, so that the stride (grid x threads x V entries) is a multiple of k: every vector a thread
+// touches starts in the same column, the column of each lane position e is fixed per thread,
+// and the inner loop is pure streaming (one accumulator or one alpha per position).
+constexpr int kFlatMaxK = 8;
+
+inline int odd_part(int k) {
+  while (k % 2 == 0) k /= 2;
+  return k;
+}
+
+template <typename T>
+__device__ __forceinline__ void flat_cols(int64_t first_entry, int k, int (&cole)[16 / sizeof(T)]) {
+  const int c0 = (int)(first_entry % k);
+#pragma unroll
+  for (int e = 0; e < (int)(16 / sizeof(T)); ++e) cole[e] = (c0 + e) % k;
+}
+
+// dot over units of lcm(V, K) entries (whole vectors that start and end on a row boundary):
+// the column of every entry of a unit is a compile-time constant, so the loop keeps just K
+// accumulators.  FP32 products are summed four units at a time in FP32, the groups in FP64.
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) k_dot_flat(int64_t total, const T* __restrict__ X,
+                                                       const T* __restrict__ Y, double* __restrict__ partials) {
+  constexpr int V = 16 / sizeof(T);
+  constexpr int L = V / gcd_c(V, K) * K;  // entries per unit
+  constexpr int NV = L / V;               // vectors per unit
+  __shared__ double sh[kThreads / 32][K];
+  const int64_t nunits = total / L;
+  const int64_t tid = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  double acc[K];
+  T facc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j] = 0.0, facc[j] = T(0);
+  int pending = 0;
+  for (int64_t u = tid; u < nunits; u += stride) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const Vec<T, V> x = ldv<T, V>(X + u * L + i * V);
+      const Vec<T, V> y = ldv<T, V>(Y + u * L + i * V);
+#pragma unroll
+      for (int e = 0; e < V; ++e) facc[(i * V + e) % K] = fma(x.v[e], y.v[e], facc[(i * V + e) % K]);
+    }
+    if (sizeof(T) == 8 || ++pending == 4) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc[j] += (double)facc[j], facc[j] = T(0);
+      pending = 0;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j] += (double)facc[j];
+  // tail entries past the last whole unit: entry nunits L + tid is in column tid % K
+  const int64_t f = nunits * L + tid;
+  if (f < total) {
+    const int cf = (int)(tid % K);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (cf == j) acc[j] += (double)X[f] * (double)Y[f];
+  }
+  const int w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    double v = acc[j];
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[w][j] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < K) {
+    double v = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) v += sh[i][threadIdx.x];
+    partials[(size_t)blockIdx.x * K + threadIdx.x] = v;
+  }
+}
+
+template <typename T>
+rb_status launch_dot_flat(int64_t total, int k, const T* X, const T* Y, double* partials, int& grid, cudaStream_t s) {
+  auto go = [&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    constexpr int V = 16 / sizeof(T);
+    constexpr int L = V / gcd_c(V, K) * K;
+    const int64_t blocks = std::max<int64_t>(1, (total / L + kThreads - 1) / kThreads);
+    grid = std::min(kBlasGrid, wave_grid(&k_dot_flat<T, K>, blocks));
+    k_dot_flat<T, K><<<grid, kThreads, 0, s>>>(total, X, Y, partials);
+  };
+  switch (k) {
+    case 1: go(std::integral_constant<int, 1>{}); break;
+    case 2: go(std::integral_constant<int, 2>{}); break;
+    case 3: go(std::integral_constant<int, 3>{}); break;
+    case 4: go(std::integral_constant<int, 4>{}); break;
+    case 5: go(std::integral_constant<int, 5>{}); break;
+    case 6: go(std::integral_constant<int, 6>{}); break;
+    case 7: go(std::integral_constant<int, 7>{}); break;
+    case 8: go(std::integral_constant<int, 8>{}); break;
+    default: set_error("rb_dot: flat kernel takes k <= 8"); return RB_EUNSUPPORTED;
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_axpy_flat(int64_t total, int k, const double* __restrict__ alpha,
+                                                        const T* __restrict__ X, T* __restrict__ Y) {
+  constexpr int V = 16 / sizeof(T);
+  const int64_t nvec = total / V;
+  const int64_t tid = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int cole[V];
+  flat_cols<T>(tid * V, k, cole);
+  T a[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) a[e] = (T)alpha[cole[e]];
+  for (int64_t c = tid; c < nvec; c += stride) {
+    const Vec<T, V> x = ldv<T, V>(X + c * V);
+    Vec<T, V> y = ldv_rw<T, V>(Y + c * V);
+#pragma unroll
+    for (int e = 0; e < V; ++e) y.v[e] = fma(a[e], x.v[e], y.v[e]);
+    stv<T, V>(Y + c * V, y);
+  }
+  const int64_t f = nvec * V + tid;
+  if (f < total) Y[f] = fma((T)alpha[f % k], X[f], Y[f]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_axty_flat(int64_t total, T alpha, const T* __restrict__ X,
+                                                        T* __restrict__ Y) {
+  constexpr int V = 16 / sizeof(T);
+  const int64_t nvec = total / V;
+  const int64_t tid = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t c = tid; c < nvec; c += stride) {
+    const Vec<T, V> x = ldv<T, V>(X + c * V);
+    Vec<T, V> y = ldv_rw<T, V>(Y + c * V);
+#pragma unroll
+    for (int e = 0; e < V; ++e) y.v[e] = alpha * x.v[e] * y.v[e];
+    stv<T, V>(Y + c * V, y);
+  }
+  const int64_t f = nvec * V + tid;
+  if (f < total) Y[f] = alpha * X[f] * Y[f];
+}
+
+bool flat_ok(int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
+  return ldx == k && ldy == k && ((uintptr_t)X % 16) == 0 && ((uintptr_t)Y % 16) == 0;
+}
+
+// grid of a flat kernel: one resident wave, a multiple of the odd part of k
+template <typename K>
+int flat_grid(K* kernel, int64_t total, int eb, int k) {
+  const int64_t vec_blocks = (total / (16 / eb) + kThreads - 1) / kThreads;
+  int g = wave_grid(kernel, std::max<int64_t>(vec_blocks, 1));
+  const int o = odd_part(k);
+  g = std::max(o, g / o * o);
+  return g;
+}
+
 rb_status check_block(const char* fn, int64_t n, int k, rb_dtype dtype, const void* X, int64_t ldx, const void* Y,
                       int64_t ldy) {
   RB_REQUIRE(n >= 0, "%s: negative n", fn);
@@ -166,7 +324,11 @@ extern "C" rb_status rb_dot(int64_t n, int32_t k, rb_dtype dtype, const void* X,
   const int64_t blocks = std::max<int64_t>(1, (n + kThreads / kp - 1) / (kThreads / kp));
   int grid = 1;
   double* partials = static_cast<double*>(work);
-  if (dtype == RB_F64) {
+  if (k <= kFlatMaxK && flat_ok(k, ldx, ldy, X, Y)) {
+    const int64_t total = n * k;
+    if (dtype == RB_F64) RB_TRY(launch_dot_flat<double>(total, k, (const double*)X, (const double*)Y, partials, grid, s));
+    else RB_TRY(launch_dot_flat<float>(total, k, (const float*)X, (const float*)Y, partials, grid, s));
+  } else if (dtype == RB_F64) {
     RB_DISPATCH_VEC(double, vec, grid = wave_grid(&k_dot_partial<double, V>, blocks);
                     k_dot_partial<double, V><<<grid, kThreads, 0, s>>>(n, k, kp, (const double*)X, ldx,
                                                                        (const double*)Y, ldy, partials));
@@ -192,7 +354,15 @@ extern "C" rb_status rb_axpy(int64_t n, int32_t k, rb_dtype dtype, const double*
   vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
   RB_REQUIRE(kp <= 32, "rb_axpy: k = %d needs 16-byte aligned rows", k);
   const int64_t blocks = (n + kThreads / kp - 1) / (kThreads / kp);
-  if (dtype == RB_F64) {
+  if (flat_ok(k, ldx, ldy, X, Y)) {
+    const int64_t total = n * k;
+    if (dtype == RB_F64)
+      k_axpy_flat<double><<<flat_grid(&k_axpy_flat<double>, total, 8, k), kThreads, 0, s>>>(
+          total, k, alpha, (const double*)X, (double*)Y);
+    else
+      k_axpy_flat<float><<<flat_grid(&k_axpy_flat<float>, total, 4, k), kThreads, 0, s>>>(
+          total, k, alpha, (const float*)X, (float*)Y);
+  } else if (dtype == RB_F64) {
     RB_DISPATCH_VEC(double, vec,
                     k_axpy<double, V><<<wave_grid(&k_axpy<double, V>, blocks), kThreads, 0, s>>>(
                         n, k, kp, alpha, (const double*)X, ldx, (double*)Y, ldy));
@@ -216,7 +386,15 @@ extern "C" rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha,
   vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
   RB_REQUIRE(kp <= 32, "rb_axty: k = %d needs 16-byte aligned rows", k);
   const int64_t blocks = (n + kThreads / kp - 1) / (kThreads / kp);
-  if (dtype == RB_F64) {
+  if (flat_ok(k, ldx, ldy, X, Y)) {
+    const int64_t total = n * k;
+    if (dtype == RB_F64)
+      k_axty_flat<double><<<flat_grid(&k_axty_flat<double>, total, 8, 1), kThreads, 0, s>>>(
+          total, alpha, (const double*)X, (double*)Y);
+    else
+      k_axty_flat<float><<<flat_grid(&k_axty_flat<float>, total, 4, 1), kThreads, 0, s>>>(
+          total, (float)alpha, (const float*)X, (float*)Y);
+  } else if (dtype == RB_F64) {
     RB_DISPATCH_VEC(double, vec,
                     k_axty<double, V><<<wave_grid(&k_axty<double, V>, blocks), kThreads, 0, s>>>(
                         n, k, kp, alpha, (const double*)X, ldx, (double*)Y, ldy));

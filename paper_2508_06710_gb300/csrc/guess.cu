@@ -323,12 +323,12 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a) {
     fence_barrier_init();
   }
   if (warp == 0) tmem_alloc(&tmem_slot, kCols);
-  // the 256 bytes after the last line are read (times zero weights) by the last core matrix of
-  // the third x offset with 8-channel inputs: keep them finite
-  if (tid < 16) {
-    const uint32_t pad = sL + (uint32_t)G * kGroupBytes + (uint32_t)tid * 16;
-    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(pad), "r"(0u) : "memory");
-  }
+  // With 8-channel inputs the third x offset of a line is paired with a zero-weight core that
+  // reads 16 bytes into the next line of the ring (or the pad after the last): those bytes must
+  // be finite (0 x NaN = NaN), so the whole ring and the pad start as zeros; every line
+  // written later holds finite activations.
+  for (uint32_t off = (uint32_t)tid * 16; off < (uint32_t)G * kGroupBytes + 256; off += kConvThreads * 16)
+    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(sL + off), "r"(0u) : "memory");
   const int kcw = krow / 8;
   for (int i = tid; i < NP * kcw; i += kConvThreads) {
     const int n = i / kcw, q = i - n * kcw;

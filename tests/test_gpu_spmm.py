@@ -263,9 +263,10 @@ def test_extruded_airfoil_full_size(rb):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("k", [1, 3, 4, 8, 64])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 7, 8, 64])
 @pytest.mark.parametrize("n", [1, 1000, 300_001])
 def test_dot_axpy_axty(rb, dtype, k, n):
+    """Contiguous blocks (the flat 16-byte streaming kernels for k <= 8, all k for axpy/axty)."""
     npdt = np.float64 if dtype == "f64" else np.float32
     X = W.normal((n, k), 1).astype(npdt)
     Y = W.normal((n, k), 2).astype(npdt)
@@ -288,3 +289,29 @@ def test_dot_axpy_axty(rb, dtype, k, n):
     tref = blas.axty(0.5, X, Y)
     tol3 = 1e-15 if dtype == "f64" else 2e-7
     assert np.all(np.abs(Yd2.cpu().numpy() - tref) <= tol3 * np.abs(tref) + 1e-300)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_dot_axpy_axty_strided(rb, dtype, k):
+    """Rows wider than k (ld = k + 3): the row-and-chunk kernels; padding left untouched."""
+    npdt = np.float64 if dtype == "f64" else np.float32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    n = 12_345
+    X = W.normal((n, k), 11).astype(npdt)
+    Y = W.normal((n, k), 12).astype(npdt)
+    alpha = W.normal(k, 13)
+    Xw = torch.full((n, k + 3), float("nan"), dtype=tdt, device="cuda")
+    Yw = torch.full((n, k + 3), float("nan"), dtype=tdt, device="cuda")
+    Xw[:, :k] = to_dev(X)
+    Yw[:, :k] = to_dev(Y)
+    d = rb.dot(Xw[:, :k], Yw[:, :k]).cpu().numpy()
+    scale = blas.dot(np.abs(X), np.abs(Y))
+    tol = 1e-13 if dtype == "f64" else 1e-6
+    assert np.all(np.abs(d - blas.dot(X, Y)) <= tol * scale + 1e-300)
+    rb.axpy(to_dev(alpha), Xw[:, :k], Yw[:, :k])
+    aref = blas.axpy(alpha if dtype == "f64" else alpha.astype(np.float32), X, Y)
+    got = Yw[:, :k].cpu().numpy().astype(np.float64)
+    tol2 = 1e-15 if dtype == "f64" else 2e-7
+    assert np.all(np.abs(got - aref) <= tol2 * (np.abs(X * alpha[None, :]) + np.abs(Y)) + 1e-300)
+    assert torch.isnan(Yw[:, k:]).all()
