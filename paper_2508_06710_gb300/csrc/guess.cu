@@ -647,6 +647,179 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// Weight gradient on 128-cell rows: the same product as k_wgrad_mma with K = the cells of
+// one grid row at a time, its A operand (MN-major, rows m = tap * c_in + ci, the ones row, zero
+// rows) copied from the shared-memory line ring of the row kernel instead of gathered from
+// global memory: each input line is read from L2 for three rows, and the copies need no
+// neighbour arithmetic (the ring holds the wrapped or zero halo).  The ones row and the zero
+// rows are written once.  One accumulator; the A tile of a row is rebuilt once the MMAs of the
+// previous row are done, the B tile (the masked output gradient of the row) is double-buffered.
+constexpr uint32_t kRowLboA = 16 * 128;  // A: core matrices adjacent along K (8 cells)
+
+template <int NP>
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int items_per_split) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  constexpr uint32_t kCols = tmem_cols_for(NP);
+  constexpr uint32_t kLboB = (NP / 8) * 128;
+  constexpr uint32_t kBBytes = (uint32_t)NP * kRowW * 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = a.cin / 8;
+  const uint32_t sA = smem_u32(smem);
+  const uint32_t sB = sA + 16 * kRowLboA;          // two B buffers
+  const uint32_t sL = sB + 2 * kBBytes;            // the line ring
+  const int mt = blockIdx.x, split = blockIdx.y;
+  const int ny = a.d.ny, nz = a.d.nz;
+  const int chunks_y = (ny + kRowChunk - 1) / kRowChunk;
+  const int items = nz * chunks_y;
+  const int it0 = split * items_per_split;
+  const int it1 = min(items, it0 + items_per_split);
+  const uint32_t idesc = umma_idesc_bf16(128, NP, true, true);
+
+  if (tid == 0) {
+    mbar_init(&mma_bar, 1);
+    mbar_init(&done_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+  // the 16 row groups of the m tile: gather (tap offsets, ci0), the ones row, or zeros; the
+  // constant groups are written now, for all 128 cells (this thread's cell = tid)
+  int gcode[16];
+#pragma unroll
+  for (int g8 = 0; g8 < 16; ++g8) {
+    const int m = mt * 128 + g8 * 8;
+    const uint32_t dst = sA + (uint32_t)(tid >> 3) * kRowLboA + (uint32_t)g8 * 128 + (uint32_t)(tid & 7) * 16;
+    if (m < a.rows) {
+      const int tap = m / a.cin;
+      gcode[g8] = (tap % 3) | ((tap / 3) % 3) << 2 | (tap / 9) << 4 | ((m - tap * a.cin) >> 3) << 8;
+    } else {
+      gcode[g8] = -1;
+      const uint32_t one = m == a.rows ? 0x3F80u : 0u;  // BF16 1.0 in the low half: the bias row
+      asm volatile("st.shared.v4.b32 [%0], {%1, %2, %2, %2};" ::"r"(dst), "r"(one), "r"(0u) : "memory");
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  auto line_addr = [&](int cg, int dzi, int yy) -> uint32_t {
+    return sL + (uint32_t)cg * kGroupBytes + (uint32_t)(dzi * 4 + (yy & 3)) * kLineBytes;
+  };
+  auto load_row = [&](int z, int yy) {  // three z lines of row yy (as in k_conv3_row)
+    int yw = yy;
+    bool yok = true;
+    if (yw < 0 || yw >= ny) {
+      if (a.d.py) yw = yw < 0 ? yw + ny : yw - ny;
+      else yok = false;
+    }
+    for (int dzi = 0; dzi < 3; ++dzi) {
+      int zz = z + dzi - 1;
+      bool ok = yok;
+      if (zz < 0 || zz >= nz) {
+        if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
+        else ok = false;
+      }
+      const size_t row0 = ((size_t)zz * ny + yw) * kRowW;
+      for (int cg = 0; cg < G; ++cg) {
+        const uint32_t dst = line_addr(cg, dzi, yy);
+        for (int pos = tid; pos < kRowPos; pos += kConvThreads) {
+          int x = pos - 1;
+          bool okx = ok;
+          if (x < 0 || x >= kRowW) {
+            if (a.d.px) x = x < 0 ? x + kRowW : x - kRowW;
+            else okx = false;
+          }
+          cp_async16(dst + (uint32_t)pos * 16, okx ? (const void*)(a.x + (row0 + x) * a.ldx + cg * 8) : (const void*)a.x,
+                     okx ? 16u : 0u);
+        }
+      }
+    }
+  };
+  auto load_b = [&](int z, int y, int buf) {  // the row's output gradient, this thread's cell
+    const size_t v = ((size_t)z * ny + y) * kRowW + tid;
+    const uint32_t base = sB + (uint32_t)buf * kBBytes + (uint32_t)(tid >> 3) * kLboB + (uint32_t)(tid & 7) * 16;
+#pragma unroll
+    for (int nb = 0; nb < NP / 8; ++nb) {
+      const bool ok = nb * 8 < a.cout;
+      cp_async16(base + (uint32_t)nb * 128, ok ? (const void*)(a.g + v * a.ldg + nb * 8) : (const void*)a.g, ok ? 16u : 0u);
+    }
+  };
+
+  int fail = 0;
+  int rows_done = 0;  // rows whose MMAs were issued (mma_bar phase count)
+  for (int it = it0; it < it1 && !fail; ++it) {
+    const int z = it / chunks_y;
+    const int y0 = (it - z * chunks_y) * kRowChunk;
+    const int y1 = min(ny, y0 + kRowChunk);
+    load_row(z, y0 - 1);
+    load_row(z, y0);
+    load_row(z, y0 + 1);
+    load_b(z, y0, rows_done & 1);
+    cp_async_commit();
+    for (int y = y0; y < y1; ++y) {
+      cp_async_wait<0>();  // lines y - 1 .. y + 1 and B(y) have landed
+      if (__syncthreads_or(fail)) break;
+      // the A tile is rebuilt once the previous row's MMAs have read it
+      if (rows_done > 0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
+#pragma unroll
+      for (int g8 = 0; g8 < 16; ++g8) {
+        const int e = gcode[g8];
+        if (e < 0) continue;
+        const uint32_t src = line_addr(e >> 8, (e >> 4) & 3, y + ((e >> 2) & 3) - 1) + (uint32_t)(tid + (e & 3)) * 16;
+        const uint32_t dst = sA + (uint32_t)(tid >> 3) * kRowLboA + (uint32_t)g8 * 128 + (uint32_t)(tid & 7) * 16;
+        uint32_t q0, q1, q2, q3;
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(src));
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(q0), "r"(q1), "r"(q2), "r"(q3)
+                     : "memory");
+      }
+      fence_proxy_async();
+      if (__syncthreads_or(fail)) break;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t bbuf = sB + (uint32_t)(rows_done & 1) * kBBytes;
+#pragma unroll
+        for (int kk = 0; kk < kRowW / 16; ++kk)
+          umma_bf16(tmem, umma_sdesc(sA + (uint32_t)kk * 2 * kRowLboA, kRowLboA, 128),
+                    umma_sdesc(bbuf + (uint32_t)kk * 2 * kLboB, kLboB, 128), idesc, (rows_done > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&mma_bar);
+      }
+      ++rows_done;
+      // next: the lines of row y + 2 (into the slot of row y - 2, read last by row y - 1's copies)
+      // and B of row y + 1 (into the buffer row y - 1's MMAs read: done, waited above)
+      if (y + 2 <= y1) load_row(z, y + 2);
+      if (y + 1 < y1) load_b(z, y + 1, rows_done & 1);
+      cp_async_commit();
+    }
+  }
+  cp_async_wait_all();
+  if (tid == 0) {
+    umma_commit(&done_bar);
+    if (!mbar_wait(&done_bar, 0)) fail = 1;
+  }
+  fail = __syncthreads_or(fail);
+  tc_fence_after();
+  const int m = warp * 32 + lane;
+  float* dst = a.part + ((size_t)split * a.mpad + (size_t)mt * 128 + m) * NP;
+#pragma unroll
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float acc[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      float4 q = (rows_done > 0 && !fail) ? make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3])
+                                          : make_float4(0, 0, 0, 0);
+      *reinterpret_cast<float4*>(dst + c0 + i) = q;
+    }
+  }
+  if (fail && a.err) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
 // Sums the splits of a weight-gradient partial and adds it into the parameter gradient in
 // the [c_out][tap][c_in] layout (+ biases).  cin_pad: channels of the GEMM input (>= cin).
 __global__ void k_wgrad_reduce(const float* __restrict__ part, int splits, int mpad, int np, int cin_pad, int cin,
@@ -1467,8 +1640,76 @@ rb_status launch_wgrad_np(const WgradArgs& a, const WgradPlan& p, cudaStream_t s
   return RB_OK;
 }
 
+struct RowWPlan {
+  int m_tiles = 0, splits = 0, per_split = 0;
+};
+
+RowWPlan wgrad_row_plan(const Layer& ly, const Dims& d) {
+  RowWPlan p;
+  p.m_tiles = ly.mpad / 128;
+  const int items = d.nz * ((d.ny + kRowChunk - 1) / kRowChunk);
+  const int target = std::max(1, (4 * guess_sm_count()) / p.m_tiles);
+  p.per_split = std::max(1, (items + target - 1) / target);
+  p.splits = (items + p.per_split - 1) / p.per_split;
+  return p;
+}
+
+size_t wgrad_row_smem(int np, int cin) {
+  return 16 * (size_t)kRowLboA + 2 * (size_t)np * kRowW * 2 + (size_t)(cin / 8) * kGroupBytes + 256;
+}
+
+bool wgrad_row_fits(const Layer& ly, const Dims& d) {
+  return d.nx == kRowW && ly.cin_pad % 8 == 0 && wgrad_row_smem(ly.np, ly.cin_pad) <= kMaxConvSmem;
+}
+
+template <int NP>
+rb_status launch_wgrad_row_np(const WgradArgs& a, const RowWPlan& p, cudaStream_t s) {
+  const size_t smem = wgrad_row_smem(NP, a.cin);
+  static size_t opted = 48 * 1024;
+  if (smem > opted) {
+    RB_CUDA(cudaFuncSetAttribute(&k_wgrad_row<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    opted = smem;
+  }
+  k_wgrad_row<NP><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a, p.per_split);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
 rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, const bf16* gpre, int ldg, cudaStream_t s) {
   const Dims d = g->dims[ly.level];
+  if (wgrad_row_fits(ly, d)) {
+    const RowWPlan rp = wgrad_row_plan(ly, d);
+    WgradArgs a;
+    a.x = x;
+    a.ldx = ldx;
+    a.cin = ly.cin_pad;
+    a.g = gpre;
+    a.ldg = ldg;
+    a.cout = ly.cout;
+    a.d = d;
+    a.n_vox = d.n();
+    a.rows = 27 * ly.cin_pad;
+    a.mpad = ly.mpad;
+    a.part = g->wpart;
+    a.err = g->err;
+    rb_status st;
+    switch (ly.np) {
+      case 16: st = launch_wgrad_row_np<16>(a, rp, s); break;
+      case 32: st = launch_wgrad_row_np<32>(a, rp, s); break;
+      case 48: st = launch_wgrad_row_np<48>(a, rp, s); break;
+      case 64: st = launch_wgrad_row_np<64>(a, rp, s); break;
+      default:
+        set_error("rb_guess: no row weight-gradient kernel for %d output channels", ly.np);
+        return RB_EUNSUPPORTED;
+    }
+    RB_TRY(st);
+    const int total = (a.rows + 1) * ly.cout;
+    k_wgrad_reduce<<<std::min(4096, (total + 7) / 8), 256, 0, s>>>(g->wpart, rp.splits, ly.mpad, ly.np, ly.cin_pad,
+                                                                   ly.cin, ly.cout, g->grad + ly.w_off,
+                                                                   g->grad + ly.b_off);
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+  }
   const WgradPlan p = wgrad_plan(ly, d.n());
   WgradArgs a;
   a.x = x;
@@ -1515,6 +1756,8 @@ size_t wpart_need(const rb_guess* g) {
     if (ly.kind == kConv3) {
       const WgradPlan p = wgrad_plan(ly, g->dims[ly.level].n());
       need = std::max(need, (size_t)p.splits * ly.mpad * ly.np);
+      if (wgrad_row_fits(ly, g->dims[ly.level]))
+        need = std::max(need, (size_t)wgrad_row_plan(ly, g->dims[ly.level]).splits * ly.mpad * ly.np);
     } else if (ly.kind == kUp) {
       need = std::max(need, (size_t)up_dw_grid(g, ly) * (8 * ly.cin * ly.cout + ly.cout));
     }
