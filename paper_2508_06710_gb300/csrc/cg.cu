@@ -951,7 +951,7 @@ struct PSys {
 struct PBatch {
   PSys sys[kMaxSys];
   int n_sys, total_cols;
-  double* partials;  // [gridDim.x][2][K]
+  double* partials;  // [gridDim.x][3][K]: p.q, r.D^-1 r, r.r per block and batch column
   unsigned* bar;     // [0] arrivals, [1] generation (zeroed before every launch)
   int* err;          // 0, or the code of the first wait that gave up
   int max_iter;      // iteration cap of this launch
@@ -1061,18 +1061,18 @@ __device__ void pphase_q(const PBatch& b, const PSys& S, double* red, double* ou
     }
   }
   pblock_reduce<1, VEC>(acc2, S.kp, S.k, red, out);
-  if ((int)threadIdx.x < S.k) b.partials[((size_t)blockIdx.x * 2 + 0) * K + S.col0 + threadIdx.x] = out[threadIdx.x];
+  if ((int)threadIdx.x < S.k) b.partials[((size_t)blockIdx.x * 3 + 0) * K + S.col0 + threadIdx.x] = out[threadIdx.x];
 }
 
 // phase B: d += alpha p, r -= alpha q; r.D^-1 r and r.r per column into partials
 template <int VEC>
-__device__ void pphase_update(const PBatch& b, const PSys& S, double* red, double* out) {
+__device__ void pphase_update(const PBatch& b, const PSys& S, const double* alpha, double* red, double* out) {
   const int R = kPThreads / S.kp;
   const int chunk = threadIdx.x % S.kp;
   const bool col_ok = chunk * VEC < S.k;
   float al[VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) al[e] = col_ok ? (float)__ldcg(&S.sc->alpha[chunk * VEC + e]) : 0.f;
+  for (int e = 0; e < VEC; ++e) al[e] = col_ok ? (float)alpha[chunk * VEC + e] : 0.f;
   float acc[2][VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) acc[0][e] = acc[1][e] = 0.f;
@@ -1099,13 +1099,13 @@ __device__ void pphase_update(const PBatch& b, const PSys& S, double* red, doubl
   pblock_reduce<2, VEC>(acc, S.kp, S.k, red, out);
   if ((int)threadIdx.x < 2 * S.k) {
     const int q = threadIdx.x / S.k, j = threadIdx.x % S.k;
-    b.partials[((size_t)blockIdx.x * 2 + q) * K + S.col0 + j] = out[threadIdx.x];
+    b.partials[((size_t)blockIdx.x * 3 + 1 + q) * K + S.col0 + j] = out[threadIdx.x];
   }
 }
 
 // phase C: p = D^-1 r + beta p on active columns
 template <int VEC>
-__device__ void pphase_p(const PSys& S) {
+__device__ void pphase_p(const PSys& S, const double* beta, const int* state) {
   const int R = kPThreads / S.kp;
   const int chunk = threadIdx.x % S.kp;
   if (chunk * VEC >= S.k) return;
@@ -1113,8 +1113,8 @@ __device__ void pphase_p(const PSys& S) {
   bool on[VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) {
-    be[e] = (float)__ldcg(&S.sc->beta[chunk * VEC + e]);
-    on[e] = __ldcg(&S.sc->state[chunk * VEC + e]) == ST_ACTIVE;
+    be[e] = (float)beta[chunk * VEC + e];
+    on[e] = state[chunk * VEC + e] == ST_ACTIVE;
   }
   for (int64_t row = (int64_t)(blockIdx.x - S.blk0) * R + threadIdx.x / S.kp; row < S.n;
        row += (int64_t)S.nblk * R) {
@@ -1128,25 +1128,20 @@ __device__ void pphase_p(const PSys& S) {
   }
 }
 
-// total over the blocks of system S of partial (quantity q, batch column c); whole block calls
-__device__ double preduce_column(const PBatch& b, const PSys& S, int q, int c, double* red) {
-  double s = 0.0;
-  for (int bb = threadIdx.x; bb < S.nblk; bb += kPThreads) s += __ldcg(&b.partials[((size_t)(S.blk0 + bb) * 2 + q) * K + c]);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = kPThreads / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+// Totals over the blocks of system S of nq partial quantities (slots q0 .. q0 + nq/k - 1 of its
+// k columns): warp w < nq sums quantity w over the system's blocks in a fixed order (lanes
+// strided, then a shuffle tree); every block of S computes the same totals, so the per-column
+// scalars need no broadcast.  Results land in out[w]; whole block calls.
+__device__ void psys_totals(const PBatch& b, const PSys& S, int q0, int nq, double* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < nq) {
+    const int q = q0 + w / S.k, c = S.col0 + w % S.k;
+    double s = 0.0;
+    for (int bb = lane; bb < S.nblk; bb += 32) s += __ldcg(&b.partials[((size_t)(S.blk0 + bb) * 3 + q) * K + c]);
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[w] = s;
   }
-  const double tot = red[0];
   __syncthreads();
-  return tot;
-}
-
-__device__ __forceinline__ int psys_of_column(const PBatch& b, int c) {
-  int s = 0;
-  while (s + 1 < b.n_sys && b.sys[s + 1].col0 <= c) ++s;
-  return s;
 }
 
 __device__ __forceinline__ bool pany_active(const PBatch& b) {
@@ -1156,20 +1151,41 @@ __device__ __forceinline__ bool pany_active(const PBatch& b) {
   return false;
 }
 
+// Three grid barriers per iteration: after q = A p (every block then reduces p.q of its own
+// system and forms alpha), after the x, r update (every block reduces r.D^-1 r, r.r and forms
+// the convergence test and beta), after the p update.  Every block keeps its system's column
+// scalars (state, r.D^-1 r, iterations) in shared memory, computed identically in all of the
+// system's blocks; the system's first block writes them back for the host and the next kernel.
 __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
   __shared__ double red[kPWarps * 2 * 64];
   __shared__ double out[2 * K];
-  __shared__ int go;
+  __shared__ double tot[2 * K];
+  __shared__ double l_rz[K], l_alpha[K], l_beta[K];
+  __shared__ int l_state[K], l_iters[K];
+  __shared__ int go, mine;
   int my = -1;
   for (int s = 0; s < b.n_sys; ++s)
     if ((int)blockIdx.x >= b.sys[s].blk0 && (int)blockIdx.x < b.sys[s].blk0 + b.sys[s].nblk) my = s;
+  const bool lead = my >= 0 && (int)blockIdx.x == b.sys[my].blk0;
+  if (my >= 0 && (int)threadIdx.x < b.sys[my].k) {
+    const CgScal* sc = b.sys[my].sc;
+    l_state[threadIdx.x] = __ldcg(&sc->state[threadIdx.x]);
+    l_rz[threadIdx.x] = __ldcg(&sc->rz[threadIdx.x]);
+    l_iters[threadIdx.x] = __ldcg(&sc->iters[threadIdx.x]);
+  }
   for (int it = 0; it < b.max_iter; ++it) {
-    if (threadIdx.x == 0) go = pany_active(b) ? 1 : 0;
+    if (threadIdx.x == 0) {
+      go = pany_active(b) ? 1 : 0;
+      int m = 0;
+      if (my >= 0)
+        for (int j = 0; j < b.sys[my].k; ++j) m |= l_state[j] == ST_ACTIVE;
+      mine = m;
+    }
     __syncthreads();
     if (!go) break;
     if (blockIdx.x == 0 && threadIdx.x == 0) b.bar[3] = (unsigned)(it + 1);  // iterations run so far
-    // ---- phase A
-    if (my >= 0 && __ldcg(&b.sys[my].sc->n_active) > 0) {
+    // ---- phase A: q = A p, p.q
+    if (mine) {
       const PSys& S = b.sys[my];
       switch (S.vec) {
         case 1: pphase_q<1>(b, S, red, out); break;
@@ -1179,76 +1195,71 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
       }
     }
     if (!grid_barrier(b)) return;
-    // ---- reduce p.q: alpha
-    if ((int)blockIdx.x < b.total_cols) {
-      const int c = blockIdx.x, s = psys_of_column(b, c), j = c - b.sys[s].col0;
-      const PSys& S = b.sys[s];
-      if (__ldcg(&S.sc->n_active) > 0) {
-        const double pq = preduce_column(b, S, 0, c, red);
-        if (threadIdx.x == 0) {
-          CgScal* sc = S.sc;
-          sc->pq[j] = pq;
-          double al = 0.0;
-          if (sc->state[j] == ST_ACTIVE) {
-            if (!(pq > 0.0) || !isfinite(pq)) sc->state[j] = ST_DONE;
-            else al = sc->rz[j] / pq;
-          }
-          sc->alpha[j] = al;
+    // ---- phase B: alpha from the system's p.q, then x, r and the new dot products
+    if (mine) {
+      const PSys& S = b.sys[my];
+      psys_totals(b, S, 0, S.k, tot);
+      const int j = threadIdx.x;
+      if (j < S.k) {
+        const double pq = tot[j];
+        double al = 0.0;
+        if (l_state[j] == ST_ACTIVE) {
+          if (!(pq > 0.0) || !isfinite(pq)) l_state[j] = ST_DONE;
+          else al = l_rz[j] / pq;
+        }
+        l_alpha[j] = al;
+        if (lead) {
+          S.sc->pq[j] = pq;
+          S.sc->alpha[j] = al;
         }
       }
-    }
-    if (!grid_barrier(b)) return;
-    // ---- phase B
-    if (my >= 0 && __ldcg(&b.sys[my].sc->n_active) > 0) {
-      const PSys& S = b.sys[my];
+      __syncthreads();
       switch (S.vec) {
-        case 1: pphase_update<1>(b, S, red, out); break;
-        case 2: pphase_update<2>(b, S, red, out); break;
-        case 3: pphase_update<3>(b, S, red, out); break;
-        case 4: pphase_update<4>(b, S, red, out); break;
+        case 1: pphase_update<1>(b, S, l_alpha, red, out); break;
+        case 2: pphase_update<2>(b, S, l_alpha, red, out); break;
+        case 3: pphase_update<3>(b, S, l_alpha, red, out); break;
+        case 4: pphase_update<4>(b, S, l_alpha, red, out); break;
       }
     }
     if (!grid_barrier(b)) return;
-    // ---- reduce r.z, r.r: convergence, beta
-    if ((int)blockIdx.x < b.total_cols) {
-      const int c = blockIdx.x, s = psys_of_column(b, c), j = c - b.sys[s].col0;
-      const PSys& S = b.sys[s];
-      if (__ldcg(&S.sc->n_active) > 0) {
-        const double rz_new = preduce_column(b, S, 0, c, red);
-        const double rr_new = preduce_column(b, S, 1, c, red);
-        if (threadIdx.x == 0) {
-          CgScal* sc = S.sc;
-          double be = 0.0;
-          if (sc->state[j] == ST_ACTIVE) {
-            sc->iters[j] += 1;
-            sc->rr[j] = rr_new;
-            if (!isfinite(rr_new) || !isfinite(rz_new) || rr_new <= sc->tol2[j]) {
-              sc->state[j] = ST_DONE;
-            } else {
-              be = rz_new / sc->rz[j];
-              sc->rz[j] = rz_new;
-            }
+    // ---- phase C: convergence and beta from r.D^-1 r and r.r, then p
+    if (mine) {
+      const PSys& S = b.sys[my];
+      psys_totals(b, S, 1, 2 * S.k, tot);
+      const int j = threadIdx.x;
+      if (j < S.k) {
+        const double rz_new = tot[j], rr_new = tot[S.k + j];
+        double be = 0.0;
+        if (l_state[j] == ST_ACTIVE) {
+          l_iters[j] += 1;
+          if (!isfinite(rr_new) || !isfinite(rz_new) || rr_new <= S.sc->tol2[j]) {
+            l_state[j] = ST_DONE;
+          } else {
+            be = rz_new / l_rz[j];
+            l_rz[j] = rz_new;
           }
-          sc->beta[j] = be;
+          if (lead) S.sc->rr[j] = rr_new;
+        }
+        l_beta[j] = be;
+        if (lead) {
+          S.sc->iters[j] = l_iters[j];
+          S.sc->state[j] = l_state[j];
+          S.sc->rz[j] = l_rz[j];
+          S.sc->beta[j] = be;
         }
       }
-    }
-    if (!grid_barrier(b)) return;
-    // ---- phase C
-    if (my >= 0 && __ldcg(&b.sys[my].sc->n_active) > 0) {
-      const PSys& S = b.sys[my];
+      __syncthreads();
       switch (S.vec) {
-        case 1: pphase_p<1>(S); break;
-        case 2: pphase_p<2>(S); break;
-        case 3: pphase_p<3>(S); break;
-        case 4: pphase_p<4>(S); break;
+        case 1: pphase_p<1>(S, l_beta, l_state); break;
+        case 2: pphase_p<2>(S, l_beta, l_state); break;
+        case 3: pphase_p<3>(S, l_beta, l_state); break;
+        case 4: pphase_p<4>(S, l_beta, l_state); break;
       }
+      if (lead && threadIdx.x == 0) recount(S.sc, S.k);
     }
-    // n_active of each system follows its states (block 0, before the barrier publishes it)
-    if (blockIdx.x == 0 && threadIdx.x < (unsigned)b.n_sys) recount(b.sys[threadIdx.x].sc, b.sys[threadIdx.x].k);
     if (!grid_barrier(b)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x < (unsigned)b.n_sys) recount(b.sys[threadIdx.x].sc, b.sys[threadIdx.x].k);
+  if (lead && threadIdx.x == 0) recount(b.sys[my].sc, b.sys[my].k);
 }
 
 // ------------------------------------------------------------------ host side of the batch
@@ -1466,7 +1477,7 @@ rb_status persistent_inner(Solver& S_, const rb_cg_params& prm, const Layout& L,
   pb.n_sys = 1;
   pb.sys[0] = make_psys(S_, L, base, prm.precond != 0);
   pb.total_cols = S_.k;
-  pb.partials = S_.partials;  // the workspace's partials hold kGridMax x 3 x K >= kPGridMax x 2 x K
+  pb.partials = S_.partials;  // the workspace's partials hold kGridMax x 3 x K >= kPGridMax x 3 x K
   pb.bar = S_.sc->pbar;
   pb.err = reinterpret_cast<int*>(&S_.sc->pbar[2]);
   pb.max_iter = prm.max_iter;
@@ -1622,7 +1633,7 @@ extern "C" rb_status rb_batch_create(int32_t n_sys, const rb_op_t* ops, const rb
       return cuda_fail(e, "cudaMalloc (batch workspace)", __FILE__, __LINE__);
     }
   }
-  cudaError_t e = cudaMalloc(&bt->partials, (size_t)kPGridMax * 2 * K * sizeof(double));
+  cudaError_t e = cudaMalloc(&bt->partials, (size_t)kPGridMax * 3 * K * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&bt->bar, 4 * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(bt->bar, 0, 4 * sizeof(unsigned));
   if (e != cudaSuccess) {
