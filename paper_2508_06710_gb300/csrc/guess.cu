@@ -277,29 +277,38 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
 
 // ------------------------------------------------ 3x3x3 convolution on 128-cell rows (MMA)
 //
-// When a grid row holds exactly 128 cells (the MMA's M), the 27 taps need no gathered copy:
-// each CTA keeps the three input lines (z - 1, z, z + 1) of four consecutive y rows in a
-// shared-memory ring, one line = 130 cells (the row plus its x neighbours, wrapped or zero)
+// When a grid row holds exactly W = 128 or 64 cells (the MMA's M), the 27 taps need no
+// gathered copy: each CTA keeps the three input lines (z - 1, z, z + 1) of four consecutive y
+// rows in a shared-memory ring, one line = W + 2 cells (the row and its x neighbours, wrapped or zero)
 // of 8 channels (16 bytes) per channel group, and the A operand of tap (dz, dy, dx) is a
 // descriptor into line (z + dz, y + dy) starting at cell dx + 1: core matrices of 8 cells are
 // 128 bytes apart (SBO), and the second K core of an MMA is the next channel group (LBO =
 // the group stride) or, with 8 channels, the next x offset (LBO = 16 bytes; the third x
 // offset of a line pairs with zero weights).  Each input line is loaded for three y rows
-// instead of being gathered for 27 taps.  A CTA walks kRowChunk consecutive rows of one z
+// instead of being gathered for 27 taps.  A CTA walks `chunk` consecutive rows of one z
 // plane; the loads of row y + 2 overlap the MMAs of row y and the epilogue of row y - 1.
-constexpr int kRowW = 128;
-constexpr int kRowPos = kRowW + 2;
-constexpr int kRowChunk = 16;
-constexpr uint32_t kLineBytes = kRowPos * 16;
-constexpr uint32_t kGroupBytes = 12 * kLineBytes;  // 3 z lines x 4 ring slots
+// Row widths W: 128 cells (MMA M = 128, accumulator row m in TMEM lane m) and 64 cells
+// (M = 64: row m in lane 32 (m / 16) + m % 16, the first 16 lanes of each warp's quarter).
+// rows per work item: long runs reuse the ring (2 halo rows per run), short runs give more
+// items; the launch picks the longest run that still yields enough items to fill the GPU
+inline int row_chunk(int ny, int nz, int want_items) {
+  int c = 16;
+  while (c > 2 && nz * ((ny + c - 1) / c) < want_items) c /= 2;
+  return c;
+}
+__host__ __device__ constexpr int row_pos(int W) { return W + 2; }
+__host__ __device__ constexpr uint32_t line_bytes(int W) { return (uint32_t)(W + 2) * 16; }
+__host__ __device__ constexpr uint32_t group_bytes(int W) { return 12 * line_bytes(W); }  // 3 z lines x 4 slots
 
 __host__ __device__ inline int row_k(int cin) { return cin == 8 ? 9 * 4 * 8 : 27 * cin; }
-inline size_t row_smem(int np, int cin) {
-  return (size_t)np * row_k(cin) * 2 + (size_t)(cin / 8) * kGroupBytes + 256;
+inline size_t row_smem(int np, int cin, int W) {
+  return (size_t)np * row_k(cin) * 2 + (size_t)(cin / 8) * group_bytes(W) + 256;
 }
 
-template <int NP>
-__global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a) {
+template <int NP, int W>
+__global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chunk) {
+  constexpr uint32_t kLineBytes = line_bytes(W), kGroupBytes = group_bytes(W);
+  constexpr int kRowPos = row_pos(W);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t acc_bar[2];
   __shared__ __align__(8) uint64_t drain_bar;
@@ -312,9 +321,9 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a) {
   const uint32_t sL = sB + (uint32_t)(NP * krow * 2);
   const uint32_t sbo_b = (uint32_t)(krow / 8) * 128;
   const int ny = a.d.ny, nz = a.d.nz;
-  const int chunks_y = (ny + kRowChunk - 1) / kRowChunk;
+  const int chunks_y = (ny + chunk - 1) / chunk;
   const int items = nz * chunks_y;
-  const uint32_t idesc = umma_idesc_bf16(128, NP, false, false);
+  const uint32_t idesc = umma_idesc_bf16(W, NP, false, false);
 
   if (tid == 0) {
     mbar_init(&acc_bar[0], 1);
@@ -359,14 +368,14 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a) {
         if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
         else ok = false;
       }
-      const size_t row0 = ((size_t)zz * ny + yw) * kRowW;
+      const size_t row0 = ((size_t)zz * ny + yw) * W;
       for (int cg = 0; cg < G; ++cg) {
         const uint32_t dst = line_addr(cg, dzi, yy);
         for (int pos = tid; pos < kRowPos; pos += kConvThreads) {
           int x = pos - 1;
           bool okx = ok;
-          if (x < 0 || x >= kRowW) {
-            if (a.d.px) x = x < 0 ? x + kRowW : x - kRowW;
+          if (x < 0 || x >= W) {
+            if (a.d.px) x = x < 0 ? x + W : x - W;
             else okx = false;
           }
           cp_async16(dst + (uint32_t)pos * 16, okx ? (const void*)(a.x + (row0 + x) * a.ldx + cg * 8) : (const void*)a.x,
@@ -382,13 +391,16 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a) {
     const int b = e & 1;
     if (!mbar_wait(&acc_bar[b], (uint32_t)(e >> 1) & 1u)) fail = 1;
     tc_fence_after();
-    const int v = (z * ny + y) * kRowW + tid;
+    // this thread's cell of the row: the accumulator row in its TMEM lane (see above)
+    const int lane = tid & 31;
+    const int xc = W == 128 ? tid : (lane < 16 ? warp * 16 + lane : -1);
+    const int v = (z * ny + y) * W + xc;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NP);
 #pragma unroll
     for (int c0 = 0; c0 < NP; c0 += 16) {
       float acc[16];
       tmem_ld16(taddr + (uint32_t)c0, acc);
-      if (fail) continue;
+      if (fail || xc < 0) continue;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int cb = c0 + 8 * h;
@@ -419,8 +431,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a) {
 
   for (int it = blockIdx.x; it < items && !fail; it += gridDim.x) {
     const int z = it / chunks_y;
-    const int y0 = (it - z * chunks_y) * kRowChunk;
-    const int y1 = min(ny, y0 + kRowChunk);
+    const int y0 = (it - z * chunks_y) * chunk;
+    const int y1 = min(ny, y0 + chunk);
     load_row(z, y0 - 1);
     load_row(z, y0);
     load_row(z, y0 + 1);
@@ -647,7 +659,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
-// Weight gradient on 128-cell rows: the same product as k_wgrad_mma with K = the cells of
+// Weight gradient on rows of W = 128 or 64 cells: the same product as k_wgrad_mma with K = the cells of
 // one grid row at a time, its A operand (MN-major, rows m = tap * c_in + ci, the ones row, zero
 // rows) copied from the shared-memory line ring of the row kernel instead of gathered from
 // global memory: each input line is read from L2 for three rows, and the copies need no
@@ -656,23 +668,25 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
 // previous row are done, the B tile (the masked output gradient of the row) is double-buffered.
 constexpr uint32_t kRowLboA = 16 * 128;  // A: core matrices adjacent along K (8 cells)
 
-template <int NP>
-__global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int items_per_split) {
+template <int NP, int W>
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int items_per_split, int chunk) {
+  constexpr uint32_t kLineBytes = line_bytes(W), kGroupBytes = group_bytes(W);
+  constexpr int kRowPos = row_pos(W);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   constexpr uint32_t kCols = tmem_cols_for(NP);
   constexpr uint32_t kLboB = (NP / 8) * 128;
-  constexpr uint32_t kBBytes = (uint32_t)NP * kRowW * 2;
+  constexpr uint32_t kBBytes = (uint32_t)NP * W * 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = a.cin / 8;
   const uint32_t sA = smem_u32(smem);
-  const uint32_t sB = sA + 16 * kRowLboA;          // two B buffers
+  const uint32_t sB = sA + (W / 8) * kRowLboA;     // two B buffers
   const uint32_t sL = sB + 2 * kBBytes;            // the line ring
   const int mt = blockIdx.x, split = blockIdx.y;
   const int ny = a.d.ny, nz = a.d.nz;
-  const int chunks_y = (ny + kRowChunk - 1) / kRowChunk;
+  const int chunks_y = (ny + chunk - 1) / chunk;
   const int items = nz * chunks_y;
   const int it0 = split * items_per_split;
   const int it1 = min(items, it0 + items_per_split);
@@ -697,7 +711,8 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
     } else {
       gcode[g8] = -1;
       const uint32_t one = m == a.rows ? 0x3F80u : 0u;  // BF16 1.0 in the low half: the bias row
-      asm volatile("st.shared.v4.b32 [%0], {%1, %2, %2, %2};" ::"r"(dst), "r"(one), "r"(0u) : "memory");
+      if (tid < W)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %2, %2};" ::"r"(dst), "r"(one), "r"(0u) : "memory");
     }
   }
   tc_fence_before();
@@ -722,14 +737,14 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
         if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
         else ok = false;
       }
-      const size_t row0 = ((size_t)zz * ny + yw) * kRowW;
+      const size_t row0 = ((size_t)zz * ny + yw) * W;
       for (int cg = 0; cg < G; ++cg) {
         const uint32_t dst = line_addr(cg, dzi, yy);
         for (int pos = tid; pos < kRowPos; pos += kConvThreads) {
           int x = pos - 1;
           bool okx = ok;
-          if (x < 0 || x >= kRowW) {
-            if (a.d.px) x = x < 0 ? x + kRowW : x - kRowW;
+          if (x < 0 || x >= W) {
+            if (a.d.px) x = x < 0 ? x + W : x - W;
             else okx = false;
           }
           cp_async16(dst + (uint32_t)pos * 16, okx ? (const void*)(a.x + (row0 + x) * a.ldx + cg * 8) : (const void*)a.x,
@@ -739,7 +754,8 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
     }
   };
   auto load_b = [&](int z, int y, int buf) {  // the row's output gradient, this thread's cell
-    const size_t v = ((size_t)z * ny + y) * kRowW + tid;
+    if (tid >= W) return;
+    const size_t v = ((size_t)z * ny + y) * W + tid;
     const uint32_t base = sB + (uint32_t)buf * kBBytes + (uint32_t)(tid >> 3) * kLboB + (uint32_t)(tid & 7) * 16;
 #pragma unroll
     for (int nb = 0; nb < NP / 8; ++nb) {
@@ -752,8 +768,8 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
   int rows_done = 0;  // rows whose MMAs were issued (mma_bar phase count)
   for (int it = it0; it < it1 && !fail; ++it) {
     const int z = it / chunks_y;
-    const int y0 = (it - z * chunks_y) * kRowChunk;
-    const int y1 = min(ny, y0 + kRowChunk);
+    const int y0 = (it - z * chunks_y) * chunk;
+    const int y1 = min(ny, y0 + chunk);
     load_row(z, y0 - 1);
     load_row(z, y0);
     load_row(z, y0 + 1);
@@ -767,7 +783,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
 #pragma unroll
       for (int g8 = 0; g8 < 16; ++g8) {
         const int e = gcode[g8];
-        if (e < 0) continue;
+        if (e < 0 || tid >= W) continue;
         const uint32_t src = line_addr(e >> 8, (e >> 4) & 3, y + ((e >> 2) & 3) - 1) + (uint32_t)(tid + (e & 3)) * 16;
         const uint32_t dst = sA + (uint32_t)(tid >> 3) * kRowLboA + (uint32_t)g8 * 128 + (uint32_t)(tid & 7) * 16;
         uint32_t q0, q1, q2, q3;
@@ -781,7 +797,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
         tc_fence_after();
         const uint32_t bbuf = sB + (uint32_t)(rows_done & 1) * kBBytes;
 #pragma unroll
-        for (int kk = 0; kk < kRowW / 16; ++kk)
+        for (int kk = 0; kk < W / 16; ++kk)
           umma_bf16(tmem, umma_sdesc(sA + (uint32_t)kk * 2 * kRowLboA, kRowLboA, 128),
                     umma_sdesc(bbuf + (uint32_t)kk * 2 * kLboB, kLboB, 128), idesc, (rows_done > 0 || kk > 0) ? 1u : 0u);
         umma_commit(&mma_bar);
@@ -1512,9 +1528,9 @@ int enc_idx(int l, int s) { return 2 * l + s; }
 int dec_base(const rb_guess* g, int l) { return 2 * g->L + 3 * (g->L - 2 - l); }
 int head_idx(const rb_guess* g) { return 2 * g->L + 3 * (g->L - 1); }
 
-template <int NP>
+template <int NP, int W>
 rb_status launch_row_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
-  auto* kern = &k_conv3_row<NP>;
+  auto* kern = &k_conv3_row<NP, W>;
   static size_t opted = 48 * 1024;
   if (smem > opted) {
     RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1526,26 +1542,29 @@ rb_status launch_row_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
     per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kConvThreads, tmem_cols_for(2 * NP));
     per_sm_smem = smem;
   }
-  const int items = a.d.nz * ((a.d.ny + kRowChunk - 1) / kRowChunk);
+  const int chunk = row_chunk(a.d.ny, a.d.nz, 2 * per_sm * guess_sm_count());
+  const int items = a.d.nz * ((a.d.ny + chunk - 1) / chunk);
   const int grid = std::max(1, std::min(items, per_sm * guess_sm_count()));
-  kern<<<grid, kConvThreads, smem, s>>>(a);
+  kern<<<grid, kConvThreads, smem, s>>>(a, chunk);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
 
-// the row kernel takes grids whose rows are 128 cells and inputs of 8 or an even number of
-// 8-channel groups
+// the row kernel takes grids whose rows are 128 or 64 cells and inputs of 8 or an even number
+// of 8-channel groups
 bool row_kernel_fits(const Dims& d, int cin, int np) {
-  return d.nx == kRowW && (cin == 8 || (cin % 16 == 0)) && np <= 64 && row_smem(np, cin) <= kMaxConvSmem;
+  return (d.nx == 128 || d.nx == 64) && (cin == 8 || (cin % 16 == 0)) && np <= 64 &&
+         row_smem(np, cin, d.nx) <= kMaxConvSmem;
 }
 
 rb_status row_launch(const Conv3Args& a, int np, cudaStream_t s) {
-  const size_t smem = row_smem(np, a.cin);
+  const size_t smem = row_smem(np, a.cin, a.d.nx);
+  const bool w128 = a.d.nx == 128;
   switch (np) {
-    case 16: return launch_row_np<16>(a, smem, s);
-    case 32: return launch_row_np<32>(a, smem, s);
-    case 48: return launch_row_np<48>(a, smem, s);
-    case 64: return launch_row_np<64>(a, smem, s);
+    case 16: return w128 ? launch_row_np<16, 128>(a, smem, s) : launch_row_np<16, 64>(a, smem, s);
+    case 32: return w128 ? launch_row_np<32, 128>(a, smem, s) : launch_row_np<32, 64>(a, smem, s);
+    case 48: return w128 ? launch_row_np<48, 128>(a, smem, s) : launch_row_np<48, 64>(a, smem, s);
+    case 64: return w128 ? launch_row_np<64, 128>(a, smem, s) : launch_row_np<64, 64>(a, smem, s);
   }
   set_error("rb_guess: no row convolution kernel for %d output channels", np);
   return RB_EUNSUPPORTED;
@@ -1641,36 +1660,37 @@ rb_status launch_wgrad_np(const WgradArgs& a, const WgradPlan& p, cudaStream_t s
 }
 
 struct RowWPlan {
-  int m_tiles = 0, splits = 0, per_split = 0;
+  int m_tiles = 0, splits = 0, per_split = 0, chunk = 0;
 };
 
 RowWPlan wgrad_row_plan(const Layer& ly, const Dims& d) {
   RowWPlan p;
   p.m_tiles = ly.mpad / 128;
-  const int items = d.nz * ((d.ny + kRowChunk - 1) / kRowChunk);
   const int target = std::max(1, (4 * guess_sm_count()) / p.m_tiles);
+  p.chunk = row_chunk(d.ny, d.nz, target);
+  const int items = d.nz * ((d.ny + p.chunk - 1) / p.chunk);
   p.per_split = std::max(1, (items + target - 1) / target);
   p.splits = (items + p.per_split - 1) / p.per_split;
   return p;
 }
 
-size_t wgrad_row_smem(int np, int cin) {
-  return 16 * (size_t)kRowLboA + 2 * (size_t)np * kRowW * 2 + (size_t)(cin / 8) * kGroupBytes + 256;
+size_t wgrad_row_smem(int np, int cin, int W) {
+  return (size_t)(W / 8) * kRowLboA + 2 * (size_t)np * W * 2 + (size_t)(cin / 8) * group_bytes(W) + 256;
 }
 
 bool wgrad_row_fits(const Layer& ly, const Dims& d) {
-  return d.nx == kRowW && ly.cin_pad % 8 == 0 && wgrad_row_smem(ly.np, ly.cin_pad) <= kMaxConvSmem;
+  return (d.nx == 128 || d.nx == 64) && ly.cin_pad % 8 == 0 && wgrad_row_smem(ly.np, ly.cin_pad, d.nx) <= kMaxConvSmem;
 }
 
-template <int NP>
+template <int NP, int W>
 rb_status launch_wgrad_row_np(const WgradArgs& a, const RowWPlan& p, cudaStream_t s) {
-  const size_t smem = wgrad_row_smem(NP, a.cin);
+  const size_t smem = wgrad_row_smem(NP, a.cin, W);
   static size_t opted = 48 * 1024;
   if (smem > opted) {
-    RB_CUDA(cudaFuncSetAttribute(&k_wgrad_row<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RB_CUDA(cudaFuncSetAttribute(&k_wgrad_row<NP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     opted = smem;
   }
-  k_wgrad_row<NP><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a, p.per_split);
+  k_wgrad_row<NP, W><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a, p.per_split, p.chunk);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
@@ -1693,11 +1713,12 @@ rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, cons
     a.part = g->wpart;
     a.err = g->err;
     rb_status st;
+    const bool w128 = d.nx == 128;
     switch (ly.np) {
-      case 16: st = launch_wgrad_row_np<16>(a, rp, s); break;
-      case 32: st = launch_wgrad_row_np<32>(a, rp, s); break;
-      case 48: st = launch_wgrad_row_np<48>(a, rp, s); break;
-      case 64: st = launch_wgrad_row_np<64>(a, rp, s); break;
+      case 16: st = w128 ? launch_wgrad_row_np<16, 128>(a, rp, s) : launch_wgrad_row_np<16, 64>(a, rp, s); break;
+      case 32: st = w128 ? launch_wgrad_row_np<32, 128>(a, rp, s) : launch_wgrad_row_np<32, 64>(a, rp, s); break;
+      case 48: st = w128 ? launch_wgrad_row_np<48, 128>(a, rp, s) : launch_wgrad_row_np<48, 64>(a, rp, s); break;
+      case 64: st = w128 ? launch_wgrad_row_np<64, 128>(a, rp, s) : launch_wgrad_row_np<64, 64>(a, rp, s); break;
       default:
         set_error("rb_guess: no row weight-gradient kernel for %d output channels", ly.np);
         return RB_EUNSUPPORTED;
