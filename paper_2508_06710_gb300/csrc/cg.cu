@@ -2,13 +2,14 @@
 // (the pressure solve of the projection method, Sec. 4; k flow states or parameters, Sec. 3),
 // and FP32-inner CG inside FP64 iterative refinement.
 //
-// One CG iteration is three kernels, each streaming the k interleaved columns once:
+// One FP64 CG iteration is three kernels, each streaming the k interleaved columns once:
 //   q  = A p            (SpMM, Algorithm 1)   fused with  pq_j = p_j . q_j
 //   x += a p, r -= a q, z = D^-1 r            fused with  rz_j = r_j . z_j,  rr_j = r_j . r_j
 //   p  = z + b p        (z recomputed from r; never stored)
-// The per-column scalars (alpha = rz/pq, beta = rz_new/rz) are formed on the device by the
-// last block of the reducing kernel, so the host only reads the per-column state every
-// check_every iterations.  A column whose recurrence residual passes the tolerance is
+// (the inner FP32 solve of the refinement runs a two-kernel form of the same recurrence,
+// described at k_cg_q2).  The per-column scalars (alpha = rz/pq, beta = rz_new/rz) are formed
+// on the device by the last block of the reducing kernel, so the host only reads the
+// per-column state every check_every iterations.  A column whose recurrence residual passes the tolerance is
 // checked against its true residual b - A x in FP64; if that fails it restarts from the
 // true residual (residual replacement).  Converged columns stop changing.
 //
@@ -56,6 +57,7 @@ struct CgScal {
   int n_active, n_check, n_oactive, n_orun;  // n_orun: outer columns not finished (incl. first sweep)
   unsigned counter[8];   // last-block tickets, one per reducing kernel
   unsigned pbar[4];      // persistent solve: barrier arrivals, generation, error word
+  int pact[2];           // persistent solve: system still active after iteration it (slot it & 1)
 };
 
 struct CgCtl {
@@ -251,6 +253,147 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(CgCtl ctl, const T* __restric
   }
 }
 
+// --------------------------------------------- two-kernel iteration of the inner FP32 solve
+//
+// The inner solve folds the p update into the x, r update by forming beta before r is
+// updated.  With z = D^-1 r and p = z + beta_old p_old (p_old A-conjugate to p, so
+// (A p, z) = p . q), the next preconditioned residual product is
+//   r_new . z_new = (r - alpha q) . D^-1 (r - alpha q) = alpha^2 q . D^-1 q - r . z,
+// so beta = r_new . z_new / r . z = (r . z)(q . D^-1 q) / (p . q)^2 - 1 follows from the two
+// sums the q = A p kernel can form.  Per iteration:
+//   q = A p                                 fused with  pq_j = p_j . q_j, qdq_j = q_j . D^-1 q_j
+//   x += a p, r -= a q, p = D^-1 r + b p    fused with  rz_j = r_j . D^-1 r_j, rr_j = r_j . r_j
+// alpha uses the exact r . z of the previous update; only beta uses the identity (the
+// single-reduction recurrence of pipelined CG on GPUs, e.g. Rupp et al.'s fused CG).
+
+template <typename T, int VEC, int LPR>
+__global__ void __launch_bounds__(kThreads) k_cg_q2(CsrArgs<T> a, CgCtl ctl, const T* __restrict__ dinv,
+                                                     CgScal* __restrict__ sc, double* __restrict__ partials) {
+  if (sc->n_active == 0) return;
+  __shared__ RedSmem<2> red;
+  const int R = kThreads / (a.kp * LPR);
+  const int t = threadIdx.x;
+  const int sub = t % LPR, rc = t / LPR, chunk = rc % a.kp, rloc = rc / a.kp;
+  DotAccN<T, 2 * VEC> dacc;  // [0, VEC): p . q, [VEC, 2 VEC): q . D^-1 q
+  const int64_t stride = (int64_t)gridDim.x * R;
+  for (int64_t base = (int64_t)blockIdx.x * R; base < a.n_rows; base += stride) {
+    const int64_t row = base + rloc;
+    const bool active = row < a.n_rows && chunk * VEC < a.k;
+    T acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+    row_accumulate_direct<T, VEC, LPR>(a, row, chunk, sub, active, acc);
+    if (active && sub == 0) {
+      const Vec<T, VEC> p = ldv<T, VEC>(a.X + row * a.ldx + chunk * VEC);
+      const T d = dinv ? dinv[row] : T(1);
+      Vec<T, VEC> q;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        q.v[e] = acc[e];
+        dacc.add(e, p.v[e], acc[e]);
+        dacc.add(VEC + e, acc[e], d * acc[e]);
+      }
+      stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, q);
+    }
+  }
+  T part[2][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    part[0][e] = (sub == 0) ? dacc.get(e) : T(0);
+    part[1][e] = (sub == 0) ? dacc.get(VEC + e) : T(0);
+  }
+  const double v = block_reduce<2, VEC>(part, a.kp, LPR, a.k, red);
+  if (!publish_partials<2>(v, 2 * a.k, partials, &sc->counter[6], red)) return;
+  const double tot = final_sum<2>(partials, 2 * a.k, gridDim.x, red);
+  __shared__ double totals[2 * K];
+  if ((int)threadIdx.x < 2 * a.k) totals[threadIdx.x] = tot;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < a.k) {
+    const double pq = totals[j], qdq = totals[a.k + j];
+    sc->pq[j] = pq;
+    double al = 0.0, be = 0.0;
+    if (sc->state[j] == ST_ACTIVE) {
+      if (!(pq > 0.0) || !isfinite(pq) || !isfinite(qdq)) {
+        sc->state[j] = ctl.inner ? ST_DONE : ST_BREAKDOWN;
+      } else {
+        al = sc->rz[j] / pq;
+        const double b = sc->rz[j] * qdq / (pq * pq) - 1.0;
+        be = (b > 0.0 && isfinite(b)) ? b : 0.0;
+      }
+    }
+    sc->alpha[j] = al;
+    sc->beta[j] = be;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, a.k);
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_cg_xrp(CgCtl ctl, T* __restrict__ x, int64_t ldx, T* __restrict__ r,
+                                                      T* __restrict__ p, const T* __restrict__ q,
+                                                      const T* __restrict__ dinv, CgScal* __restrict__ sc,
+                                                      double* __restrict__ partials) {
+  if (sc->n_active == 0) return;
+  __shared__ RedSmem<2> red;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  const bool col_ok = chunk * VEC < k;
+  T al[VEC], be[VEC];
+  bool on[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    const int j = chunk * VEC + e;
+    on[e] = col_ok && sc->state[j] == ST_ACTIVE;
+    al[e] = on[e] ? (T)sc->alpha[j] : T(0);
+    be[e] = on[e] ? (T)sc->beta[j] : T(0);
+  }
+  DotAccN<T, 2 * VEC> dots;  // [0, VEC): r . D^-1 r, [VEC, 2 VEC): r . r
+  if (col_ok) {
+    for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < ctl.n; row += (int64_t)gridDim.x * R) {
+      const int64_t o = row * k + chunk * VEC;
+      Vec<T, VEC> pv = ldv_rw<T, VEC>(p + o);
+      const Vec<T, VEC> qv = ldv_rw<T, VEC>(q + o);
+      Vec<T, VEC> rv = ldv_rw<T, VEC>(r + o);
+      Vec<T, VEC> xv = ldv_rw<T, VEC>(x + row * ldx + chunk * VEC);
+      const T d = dinv ? dinv[row] : T(1);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        xv.v[e] = fma(al[e], pv.v[e], xv.v[e]);
+        rv.v[e] = fma(-al[e], qv.v[e], rv.v[e]);
+        const T z = d * rv.v[e];
+        pv.v[e] = on[e] ? fma(be[e], pv.v[e], z) : pv.v[e];
+        dots.add(e, rv.v[e], z);
+        dots.add(VEC + e, rv.v[e], rv.v[e]);
+      }
+      stv<T, VEC>(x + row * ldx + chunk * VEC, xv);
+      stv<T, VEC>(r + o, rv);
+      stv<T, VEC>(p + o, pv);
+    }
+  }
+  T part[2][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) part[0][e] = dots.get(e), part[1][e] = dots.get(VEC + e);
+  const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
+  if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[7], red)) return;
+  const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
+  __shared__ double totals[2 * K];
+  if ((int)threadIdx.x < 2 * k) totals[threadIdx.x] = tot;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < k && sc->state[j] == ST_ACTIVE) {
+    const double rz_new = totals[j], rr_new = totals[k + j];
+    sc->iters[j] += 1;
+    sc->rr[j] = rr_new;
+    sc->rz[j] = rz_new;
+    if (!isfinite(rr_new) || !isfinite(rz_new)) sc->state[j] = ctl.inner ? ST_DONE : ST_BREAKDOWN;
+    else if (rr_new <= sc->tol2[j]) sc->state[j] = ctl.inner ? ST_DONE : ST_CHECK;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, k);
+}
+
 // ------------------------------------------------ true residual r = b - A x (FP64 operator)
 
 template <int VEC, int LPR>
@@ -427,10 +570,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_restart(CgCtl ctl, T* __restric
 // ---------------------------------- refinement: inner right-hand side and solution update
 
 // r32 = (r64 - mean) / scale and d32 = 0 on outer-active columns (zero elsewhere).  A column
-// that starts its recurrence here gets p32 = D^-1 r32; with reliable updates a column that
-// already has a direction keeps p32, and the last block sets beta so that the following
-// p-update kernel forms p32 = D^-1 r32 + beta p32 with beta = rz_new / (rz_old ratio) and
-// ratio = s_prev / s, which continues the previous direction in the new normalisation.
+// that starts its recurrence here gets p32 = D^-1 r32.  With reliable updates a column that
+// already has a direction continues it: the previous sweep's last update left
+// p_old = D^-1 r_old + beta p_prev (old normalisation), and the continued direction is
+// p = D^-1 r32 + ratio (p_old - D^-1 r_old) with ratio = s_prev / s, i.e. the recurrence
+// residual's share replaced by the new true residual (a reliable update) in the new scale.
 template <int VEC>
 __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* __restrict__ r64,
                                                        float* __restrict__ r32, float* __restrict__ p32,
@@ -444,6 +588,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
   bool on[VEC], fresh[VEC];
   bool any_kept = false;
   double mu[VEC], inv[VEC];
+  float ratio[VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) {
     const int j = chunk * VEC + e;
@@ -452,6 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
     any_kept |= !fresh[e];
     mu[e] = on[e] ? sc->omean[j] : 0.0;
     inv[e] = on[e] ? 1.0 / sc->oscale[j] : 0.0;
+    ratio[e] = fresh[e] ? 0.0f : (float)(sc->oprev[j] / sc->oscale[j]);
   }
   DotAccN<float, 2 * VEC> dots;
   if (col_ok) {
@@ -459,18 +605,20 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
       const int64_t o = row * k + chunk * VEC;
       const Vec<double, VEC> rv = ldv_rw<double, VEC>(r64 + o);
       const float d = dinv ? dinv[row] : 1.0f;
-      Vec<float, VEC> r, p, z;
-      if (any_kept) p = ldv_rw<float, VEC>(p32 + o);
+      Vec<float, VEC> r, p, z, rold;
+      if (any_kept) {
+        p = ldv_rw<float, VEC>(p32 + o);
+        rold = ldv_rw<float, VEC>(r32 + o);
+      }
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         r.v[e] = on[e] ? (float)((rv.v[e] - mu[e]) * inv[e]) : 0.0f;
         const float zz = d * r.v[e];
-        if (fresh[e]) p.v[e] = zz;
+        p.v[e] = fresh[e] ? zz : fmaf(ratio[e], fmaf(-d, rold.v[e], p.v[e]), zz);
         z.v[e] = 0.0f;
         dots.add(e, r.v[e], zz);
         dots.add(VEC + e, r.v[e], r.v[e]);
       }
-      dots.step();
       stv<float, VEC>(r32 + o, r);
       stv<float, VEC>(p32 + o, p);
       stv<float, VEC>(d32 + o, z);
@@ -488,15 +636,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
   const int j = threadIdx.x;
   if (j < k) {
     if (sc->ostate[j] == ST_ACTIVE && totals[k + j] > 0.0) {
-      const double rz_new = totals[j];
-      double be = 0.0;
-      if (ctl.reliable && sc->oprev[j] > 0.0) {
-        const double ratio = sc->oprev[j] / sc->oscale[j];
-        const double den = sc->rz[j] * ratio;
-        be = (den > 0.0 && isfinite(den)) ? rz_new / den : 0.0;
-      }
-      sc->beta[j] = be;
-      sc->rz[j] = rz_new;
+      sc->rz[j] = totals[j];
       sc->rr[j] = totals[k + j];
       sc->tol2[j] = ctl.inner_rtol2 * totals[k + j];
       sc->state[j] = ST_ACTIVE;
@@ -682,6 +822,22 @@ struct Solver {
     }
   }
 
+  template <typename T, int VEC, int LPR>
+  void launch_q2(const rb_op* op, const SpmmSched& ss, const T* p, T* q, const T* dinv, CgCtl c) const {
+    CsrArgs<T> a = args<T>(op, ss, p, k, q, k);
+    k_cg_q2<T, VEC, LPR><<<spmm_grid(&k_cg_q2<T, VEC, LPR>, ss), kThreads, 0, s>>>(a, c, dinv, sc, partials);
+  }
+
+  template <typename T, int VEC>
+  void launch_q2_lpr(const rb_op* op, const SpmmSched& ss, const T* p, T* q, const T* dinv, CgCtl c) const {
+    switch (ss.lpr) {
+      case 2: launch_q2<T, VEC, 2>(op, ss, p, q, dinv, c); break;
+      case 4: launch_q2<T, VEC, 4>(op, ss, p, q, dinv, c); break;
+      case 8: launch_q2<T, VEC, 8>(op, ss, p, q, dinv, c); break;
+      default: launch_q2<T, VEC, 1>(op, ss, p, q, dinv, c); break;
+    }
+  }
+
   template <int VEC, int LPR>
   void launch_resid_t(int mode, const double* B, int64_t ldb, const double* X, int64_t ldx, double* r) const {
     CsrArgs<double> a = args<double>(A, sched64, X, ldx, nullptr, 0);
@@ -710,6 +866,13 @@ struct Iter {
     k_cg_update<T, VEC><<<S_.vg(&k_cg_update<T, VEC>), kThreads, 0, S_.s>>>(c, x, ldx, r, p, q, dinv, S_.sc,
                                                                             S_.partials);
     k_cg_p<T, VEC><<<S_.vg(&k_cg_p<T, VEC>), kThreads, 0, S_.s>>>(c, r, p, dinv, S_.sc);
+  }
+  // one iteration of the two-kernel recurrence (beta from the q = A p kernel's sums)
+  template <typename T>
+  static void step2(const Solver& S_, const rb_op* op, const SpmmSched& ss, CgCtl c, T* x, int64_t ldx, T* r, T* p,
+                    T* q, const T* dinv) {
+    S_.launch_q2_lpr<T, VEC>(op, ss, p, q, dinv, c);
+    k_cg_xrp<T, VEC><<<S_.vg(&k_cg_xrp<T, VEC>), kThreads, 0, S_.s>>>(c, x, ldx, r, p, q, dinv, S_.sc, S_.partials);
   }
 };
 
@@ -852,8 +1015,6 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
         break;
       }
       k_ir_init<VEC><<<S_.vg(&k_ir_init<VEC>), kThreads, 0, S_.s>>>(c, r64, r32, p32, d32, dinv32, S_.sc, S_.partials);
-      if (c.reliable)  // continue the kept directions: p32 = D^-1 r32 + beta p32
-        k_cg_p<float, VEC><<<S_.vg(&k_cg_p<float, VEC>), kThreads, 0, S_.s>>>(c, r32, p32, dinv32, S_.sc);
       RB_CUDA(cudaGetLastError());
       int it = 0;
       if (prm.persistent) {
@@ -880,7 +1041,7 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
         if (h.n_active == 0 || total_inner + it >= prm.max_iter) break;
         const int chunk = std::min(prm.check_every, prm.max_iter - total_inner - it);
         RB_TRY(run_chunk(S_, graph, chunk, prm.check_every, uses, [&] {
-          Iter<VEC>::template step<float>(S_, S_.A32, S_.sched32, c, d32, k, r32, p32, q32, dinv32);
+          Iter<VEC>::template step2<float>(S_, S_.A32, S_.sched32, c, d32, k, r32, p32, q32, dinv32);
         }));
         it += chunk;
         spmms += chunk;
@@ -922,9 +1083,9 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
 // ===================================================================================
 // Persistent batched inner solve: every inner FP32 CG iteration of every system of a batch
 // in ONE cooperative launch.  Blocks are partitioned among the systems in proportion to
-// their work; each iteration runs the three phases of the three-kernel loop (q = A p with
-// p.q; x, r update with r.D^-1 r and r.r; p update) separated by grid-wide barriers, and
-// the per-column scalars are reduced by one block per batch column between phases.  The
+// their work; each iteration runs the two phases of the two-kernel inner loop (q = A p with
+// p.q and q.D^-1 q; x, r, p update with r.D^-1 r and r.r) separated by grid-wide barriers,
+// and every block of a system reduces the system's per-column sums after each barrier.  The
 // barrier waits are bounded (globaltimer): past the limit a block records an error and
 // every block leaves.
 // ===================================================================================
@@ -951,7 +1112,7 @@ struct PSys {
 struct PBatch {
   PSys sys[kMaxSys];
   int n_sys, total_cols;
-  double* partials;  // [gridDim.x][3][K]: p.q, r.D^-1 r, r.r per block and batch column
+  double* partials;  // [gridDim.x][4][K]: p.q, q.D^-1 q, r.D^-1 r, r.r per block and batch column
   unsigned* bar;     // [0] arrivals, [1] generation (zeroed before every launch)
   int* err;          // 0, or the code of the first wait that gave up
   int max_iter;      // iteration cap of this launch
@@ -1025,7 +1186,8 @@ __device__ __forceinline__ void pblock_reduce(float (&acc)[NQ][VEC], int kp, int
   __syncthreads();
 }
 
-// phase A: q = A p on the block's system, p . q per column into partials
+// phase A: q = A p on the block's system; p . q and q . D^-1 q per column into partial slots
+// 0 and 1
 template <int VEC>
 __device__ void pphase_q(const PBatch& b, const PSys& S, double* red, double* out) {
   const int R = kPThreads / S.kp;
@@ -1039,9 +1201,9 @@ __device__ void pphase_q(const PBatch& b, const PSys& S, double* red, double* ou
   a.ldx = S.k;
   a.k = S.k;
   a.kp = S.kp;
-  float acc2[1][VEC];
+  float acc2[2][VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) acc2[0][e] = 0.f;
+  for (int e = 0; e < VEC; ++e) acc2[0][e] = acc2[1][e] = 0.f;
   for (int64_t base = (int64_t)(blockIdx.x - S.blk0) * R; base < S.n; base += (int64_t)S.nblk * R) {
     const int64_t row = base + rloc;
     const bool active = row < S.n && chunk * VEC < S.k;
@@ -1051,28 +1213,41 @@ __device__ void pphase_q(const PBatch& b, const PSys& S, double* red, double* ou
     row_accumulate_direct<float, VEC, 1, true>(a, row, chunk, 0, active, acc);
     if (active) {
       const Vec<float, VEC> p = ldv_cg<float, VEC>(S.p + row * S.k + chunk * VEC);
+      const float dg = S.dinv ? S.dinv[row] : 1.f;
       Vec<float, VEC> qv;
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         qv.v[e] = acc[e];
         acc2[0][e] = fmaf(p.v[e], acc[e], acc2[0][e]);
+        acc2[1][e] = fmaf(acc[e], dg * acc[e], acc2[1][e]);
       }
       stv<float, VEC>(S.q + row * S.k + chunk * VEC, qv);
     }
   }
-  pblock_reduce<1, VEC>(acc2, S.kp, S.k, red, out);
-  if ((int)threadIdx.x < S.k) b.partials[((size_t)blockIdx.x * 3 + 0) * K + S.col0 + threadIdx.x] = out[threadIdx.x];
+  pblock_reduce<2, VEC>(acc2, S.kp, S.k, red, out);
+  if ((int)threadIdx.x < 2 * S.k) {
+    const int q = threadIdx.x / S.k, j = threadIdx.x % S.k;
+    b.partials[((size_t)blockIdx.x * 4 + q) * K + S.col0 + j] = out[threadIdx.x];
+  }
 }
 
-// phase B: d += alpha p, r -= alpha q; r.D^-1 r and r.r per column into partials
+// phase B: d += alpha p, r -= alpha q, p = D^-1 r + beta p on active columns; r . D^-1 r and
+// r . r per column into partial slots 2 and 3 (slots apart from phase A's, which slower blocks
+// may still be reading)
 template <int VEC>
-__device__ void pphase_update(const PBatch& b, const PSys& S, const double* alpha, double* red, double* out) {
+__device__ void pphase_xrp(const PBatch& b, const PSys& S, const double* alpha, const double* beta,
+                           const int* state, double* red, double* out) {
   const int R = kPThreads / S.kp;
   const int chunk = threadIdx.x % S.kp;
   const bool col_ok = chunk * VEC < S.k;
-  float al[VEC];
+  float al[VEC], be[VEC];
+  bool on[VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) al[e] = col_ok ? (float)alpha[chunk * VEC + e] : 0.f;
+  for (int e = 0; e < VEC; ++e) {
+    on[e] = col_ok && state[chunk * VEC + e] == ST_ACTIVE;
+    al[e] = on[e] ? (float)alpha[chunk * VEC + e] : 0.f;
+    be[e] = on[e] ? (float)beta[chunk * VEC + e] : 0.f;
+  }
   float acc[2][VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) acc[0][e] = acc[1][e] = 0.f;
@@ -1080,7 +1255,7 @@ __device__ void pphase_update(const PBatch& b, const PSys& S, const double* alph
     for (int64_t row = (int64_t)(blockIdx.x - S.blk0) * R + threadIdx.x / S.kp; row < S.n;
          row += (int64_t)S.nblk * R) {
       const int64_t o = row * S.k + chunk * VEC;
-      const Vec<float, VEC> pv = ldv_cg<float, VEC>(S.p + o);
+      Vec<float, VEC> pv = ldv_cg<float, VEC>(S.p + o);
       const Vec<float, VEC> qv = ldv_cg<float, VEC>(S.q + o);
       Vec<float, VEC> rv = ldv_cg<float, VEC>(S.r + o);
       Vec<float, VEC> xv = ldv_cg<float, VEC>(S.d + o);
@@ -1089,42 +1264,20 @@ __device__ void pphase_update(const PBatch& b, const PSys& S, const double* alph
       for (int e = 0; e < VEC; ++e) {
         xv.v[e] = fmaf(al[e], pv.v[e], xv.v[e]);
         rv.v[e] = fmaf(-al[e], qv.v[e], rv.v[e]);
-        acc[0][e] = fmaf(rv.v[e], dg * rv.v[e], acc[0][e]);
+        const float z = dg * rv.v[e];
+        pv.v[e] = on[e] ? fmaf(be[e], pv.v[e], z) : pv.v[e];
+        acc[0][e] = fmaf(rv.v[e], z, acc[0][e]);
         acc[1][e] = fmaf(rv.v[e], rv.v[e], acc[1][e]);
       }
       stv<float, VEC>(S.d + o, xv);
       stv<float, VEC>(S.r + o, rv);
+      stv<float, VEC>(S.p + o, pv);
     }
   }
   pblock_reduce<2, VEC>(acc, S.kp, S.k, red, out);
   if ((int)threadIdx.x < 2 * S.k) {
     const int q = threadIdx.x / S.k, j = threadIdx.x % S.k;
-    b.partials[((size_t)blockIdx.x * 3 + 1 + q) * K + S.col0 + j] = out[threadIdx.x];
-  }
-}
-
-// phase C: p = D^-1 r + beta p on active columns
-template <int VEC>
-__device__ void pphase_p(const PSys& S, const double* beta, const int* state) {
-  const int R = kPThreads / S.kp;
-  const int chunk = threadIdx.x % S.kp;
-  if (chunk * VEC >= S.k) return;
-  float be[VEC];
-  bool on[VEC];
-#pragma unroll
-  for (int e = 0; e < VEC; ++e) {
-    be[e] = (float)beta[chunk * VEC + e];
-    on[e] = state[chunk * VEC + e] == ST_ACTIVE;
-  }
-  for (int64_t row = (int64_t)(blockIdx.x - S.blk0) * R + threadIdx.x / S.kp; row < S.n;
-       row += (int64_t)S.nblk * R) {
-    const int64_t o = row * S.k + chunk * VEC;
-    const Vec<float, VEC> rv = ldv_cg<float, VEC>(S.r + o);
-    Vec<float, VEC> pv = ldv_cg<float, VEC>(S.p + o);
-    const float dg = S.dinv ? S.dinv[row] : 1.f;
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) pv.v[e] = on[e] ? fmaf(be[e], pv.v[e], dg * rv.v[e]) : pv.v[e];
-    stv<float, VEC>(S.p + o, pv);
+    b.partials[((size_t)blockIdx.x * 4 + 2 + q) * K + S.col0 + j] = out[threadIdx.x];
   }
 }
 
@@ -1137,7 +1290,7 @@ __device__ void psys_totals(const PBatch& b, const PSys& S, int q0, int nq, doub
   if (w < nq) {
     const int q = q0 + w / S.k, c = S.col0 + w % S.k;
     double s = 0.0;
-    for (int bb = lane; bb < S.nblk; bb += 32) s += __ldcg(&b.partials[((size_t)(S.blk0 + bb) * 3 + q) * K + c]);
+    for (int bb = lane; bb < S.nblk; bb += 32) s += __ldcg(&b.partials[((size_t)(S.blk0 + bb) * 4 + q) * K + c]);
     for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[w] = s;
   }
@@ -1151,11 +1304,12 @@ __device__ __forceinline__ bool pany_active(const PBatch& b) {
   return false;
 }
 
-// Three grid barriers per iteration: after q = A p (every block then reduces p.q of its own
-// system and forms alpha), after the x, r update (every block reduces r.D^-1 r, r.r and forms
-// the convergence test and beta), after the p update.  Every block keeps its system's column
-// scalars (state, r.D^-1 r, iterations) in shared memory, computed identically in all of the
-// system's blocks; the system's first block writes them back for the host and the next kernel.
+// Two grid barriers per iteration (the two-kernel recurrence above): after q = A p every block
+// reduces its own system's p.q and q.D^-1 q and forms alpha and beta; after the x, r, p update
+// every block reduces r.D^-1 r and r.r and forms the convergence test.  Every block keeps its
+// system's column scalars (state, r.D^-1 r, iterations) in shared memory, computed
+// identically in all of the system's blocks; the system's first block writes them back for
+// the host and the next kernel.
 __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
   __shared__ double red[kPWarps * 2 * 64];
   __shared__ double out[2 * K];
@@ -1173,9 +1327,21 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
     l_rz[threadIdx.x] = __ldcg(&sc->rz[threadIdx.x]);
     l_iters[threadIdx.x] = __ldcg(&sc->iters[threadIdx.x]);
   }
+  // Every block must leave the loop in the same iteration.  The states at entry are the same
+  // for all blocks; later, the leads publish after each iteration whether their system is
+  // still active (pact[it & 1]), and the decision at the top of iteration it reads what was
+  // published after iteration it - 2, which the barriers of iteration it - 1 made visible to
+  // every block (iteration it - 1's flags may still be in flight).  So the loop runs up to two
+  // iterations of bare barriers past the last active column.
+  const int entry_go = pany_active(b) ? 1 : 0;
   for (int it = 0; it < b.max_iter; ++it) {
     if (threadIdx.x == 0) {
-      go = pany_active(b) ? 1 : 0;
+      int g = entry_go;
+      if (it >= 2) {
+        g = 0;
+        for (int s = 0; s < b.n_sys; ++s) g |= __ldcg(&b.sys[s].sc->pact[it & 1]);
+      }
+      go = g;
       int m = 0;
       if (my >= 0)
         for (int j = 0; j < b.sys[my].k; ++j) m |= l_state[j] == ST_ACTIVE;
@@ -1183,8 +1349,8 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
     }
     __syncthreads();
     if (!go) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) b.bar[3] = (unsigned)(it + 1);  // iterations run so far
-    // ---- phase A: q = A p, p.q
+    if (lead && mine && threadIdx.x == 0) atomicMax(b.bar + 3, (unsigned)(it + 1));  // iterations with work
+    // ---- phase A: q = A p, p.q, q.D^-1 q
     if (mine) {
       const PSys& S = b.sys[my];
       switch (S.vec) {
@@ -1195,69 +1361,68 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
       }
     }
     if (!grid_barrier(b)) return;
-    // ---- phase B: alpha from the system's p.q, then x, r and the new dot products
+    // ---- phase B: alpha and beta from the system's sums, then x, r, p and the new products
     if (mine) {
       const PSys& S = b.sys[my];
-      psys_totals(b, S, 0, S.k, tot);
+      psys_totals(b, S, 0, 2 * S.k, tot);
       const int j = threadIdx.x;
       if (j < S.k) {
-        const double pq = tot[j];
-        double al = 0.0;
+        const double pq = tot[j], qdq = tot[S.k + j];
+        double al = 0.0, be = 0.0;
         if (l_state[j] == ST_ACTIVE) {
-          if (!(pq > 0.0) || !isfinite(pq)) l_state[j] = ST_DONE;
-          else al = l_rz[j] / pq;
+          if (!(pq > 0.0) || !isfinite(pq) || !isfinite(qdq)) {
+            l_state[j] = ST_DONE;
+          } else {
+            al = l_rz[j] / pq;
+            const double bb = l_rz[j] * qdq / (pq * pq) - 1.0;
+            be = (bb > 0.0 && isfinite(bb)) ? bb : 0.0;
+          }
         }
         l_alpha[j] = al;
+        l_beta[j] = be;
         if (lead) {
           S.sc->pq[j] = pq;
           S.sc->alpha[j] = al;
-        }
-      }
-      __syncthreads();
-      switch (S.vec) {
-        case 1: pphase_update<1>(b, S, l_alpha, red, out); break;
-        case 2: pphase_update<2>(b, S, l_alpha, red, out); break;
-        case 3: pphase_update<3>(b, S, l_alpha, red, out); break;
-        case 4: pphase_update<4>(b, S, l_alpha, red, out); break;
-      }
-    }
-    if (!grid_barrier(b)) return;
-    // ---- phase C: convergence and beta from r.D^-1 r and r.r, then p
-    if (mine) {
-      const PSys& S = b.sys[my];
-      psys_totals(b, S, 1, 2 * S.k, tot);
-      const int j = threadIdx.x;
-      if (j < S.k) {
-        const double rz_new = tot[j], rr_new = tot[S.k + j];
-        double be = 0.0;
-        if (l_state[j] == ST_ACTIVE) {
-          l_iters[j] += 1;
-          if (!isfinite(rr_new) || !isfinite(rz_new) || rr_new <= S.sc->tol2[j]) {
-            l_state[j] = ST_DONE;
-          } else {
-            be = rz_new / l_rz[j];
-            l_rz[j] = rz_new;
-          }
-          if (lead) S.sc->rr[j] = rr_new;
-        }
-        l_beta[j] = be;
-        if (lead) {
-          S.sc->iters[j] = l_iters[j];
-          S.sc->state[j] = l_state[j];
-          S.sc->rz[j] = l_rz[j];
           S.sc->beta[j] = be;
         }
       }
       __syncthreads();
       switch (S.vec) {
-        case 1: pphase_p<1>(S, l_beta, l_state); break;
-        case 2: pphase_p<2>(S, l_beta, l_state); break;
-        case 3: pphase_p<3>(S, l_beta, l_state); break;
-        case 4: pphase_p<4>(S, l_beta, l_state); break;
+        case 1: pphase_xrp<1>(b, S, l_alpha, l_beta, l_state, red, out); break;
+        case 2: pphase_xrp<2>(b, S, l_alpha, l_beta, l_state, red, out); break;
+        case 3: pphase_xrp<3>(b, S, l_alpha, l_beta, l_state, red, out); break;
+        case 4: pphase_xrp<4>(b, S, l_alpha, l_beta, l_state, red, out); break;
       }
-      if (lead && threadIdx.x == 0) recount(S.sc, S.k);
     }
     if (!grid_barrier(b)) return;
+    // ---- convergence from r.D^-1 r and r.r (every block of the system, identically)
+    if (mine) {
+      const PSys& S = b.sys[my];
+      psys_totals(b, S, 2, 2 * S.k, tot);
+      const int j = threadIdx.x;
+      if (j < S.k) {
+        const double rz_new = tot[j], rr_new = tot[S.k + j];
+        if (l_state[j] == ST_ACTIVE) {
+          l_iters[j] += 1;
+          l_rz[j] = rz_new;
+          if (!isfinite(rr_new) || !isfinite(rz_new) || rr_new <= S.sc->tol2[j]) l_state[j] = ST_DONE;
+          if (lead) S.sc->rr[j] = rr_new;
+        }
+        if (lead) {
+          S.sc->iters[j] = l_iters[j];
+          S.sc->state[j] = l_state[j];
+          S.sc->rz[j] = l_rz[j];
+        }
+      }
+      __syncthreads();
+      if (lead && threadIdx.x == 0) recount(S.sc, S.k);
+    }
+    if (lead && threadIdx.x == 0) {
+      int m = 0;
+      for (int j = 0; j < b.sys[my].k; ++j) m |= l_state[j] == ST_ACTIVE;
+      b.sys[my].sc->pact[it & 1] = m;
+      __threadfence();
+    }
   }
   if (lead && threadIdx.x == 0) recount(b.sys[my].sc, b.sys[my].k);
 }
@@ -1444,7 +1609,6 @@ void sweep_head(Solver& S_, const rb_cg_params& prm, const double* B, int64_t ld
   c.inner = 1;
   S_.launch_resid_v<VEC>(RM_OUTER, B, ldb, X, ldx, r64);
   k_ir_init<VEC><<<S_.vg(&k_ir_init<VEC>), kThreads, 0, S_.s>>>(c, r64, r32, p32, d32, dinv32, S_.sc, S_.partials);
-  if (c.reliable) k_cg_p<float, VEC><<<S_.vg(&k_cg_p<float, VEC>), kThreads, 0, S_.s>>>(c, r32, p32, dinv32, S_.sc);
 }
 
 template <int VEC>
@@ -1477,7 +1641,7 @@ rb_status persistent_inner(Solver& S_, const rb_cg_params& prm, const Layout& L,
   pb.n_sys = 1;
   pb.sys[0] = make_psys(S_, L, base, prm.precond != 0);
   pb.total_cols = S_.k;
-  pb.partials = S_.partials;  // the workspace's partials hold kGridMax x 3 x K >= kPGridMax x 3 x K
+  pb.partials = S_.partials;  // the workspace's partials hold kGridMax x 3 x K >= kPGridMax x 4 x K
   pb.bar = S_.sc->pbar;
   pb.err = reinterpret_cast<int*>(&S_.sc->pbar[2]);
   pb.max_iter = prm.max_iter;
@@ -1633,7 +1797,7 @@ extern "C" rb_status rb_batch_create(int32_t n_sys, const rb_op_t* ops, const rb
       return cuda_fail(e, "cudaMalloc (batch workspace)", __FILE__, __LINE__);
     }
   }
-  cudaError_t e = cudaMalloc(&bt->partials, (size_t)kPGridMax * 3 * K * sizeof(double));
+  cudaError_t e = cudaMalloc(&bt->partials, (size_t)kPGridMax * 4 * K * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&bt->bar, 4 * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(bt->bar, 0, 4 * sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -1685,7 +1849,7 @@ extern "C" rb_status rb_batch_solve(rb_batch_t bt, const double* const* B, const
     }
     // warm the launch-shape caches outside the capture
     for (int i = 0; i < bt->n_sys; ++i) {
-#define RB_WARM(V) (void)SV[i].vg(&k_ir_init<V>), (void)SV[i].vg(&k_cg_p<float, V>), (void)SV[i].vg(&k_ir_update<V>), \
+#define RB_WARM(V) (void)SV[i].vg(&k_ir_init<V>), (void)SV[i].vg(&k_ir_update<V>), \
                    (void)SV[i].vg(&k_colsum<V>), (void)SV[i].vg(&k_submean<V>)
       RB_VEC_SWITCH(SV[i].vec, RB_WARM)
 #undef RB_WARM
