@@ -125,7 +125,9 @@ typedef struct {
  * planes: L3D = dz (I_Nz (x) A~) + T_z (x) diag(z_weight), T_z the periodic [1 -2 1]
  * across planes; rb_spmm then takes k == extruded_nz columns (one per plane) and applies
  * the whole L3D.  z_weight: n_rows weights (a_i / dz for a dual area a_i), device or
- * host as the CSR's on_device says; NULL when extruded_nz == 0. */
+ * host as the CSR's on_device says; NULL when extruded_nz == 0.  Every row of an extruded
+ * operator must store its diagonal entry (it may be zero; RB_EINVAL otherwise): the library's
+ * copy holds dz a_ij with the -2 w_i of T_z folded into the diagonal. */
 typedef struct {
   int32_t k_max;
   int32_t extruded_nz;

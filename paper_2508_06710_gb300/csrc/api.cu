@@ -234,6 +234,24 @@ extern "C" rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_d
                (long long)p, ci[p], csr->n_cols);
     RB_REQUIRE(std::isfinite(va[p]), "rb_operator_create: vals[%lld] is not finite", (long long)p);
   }
+  // Extruded operator: the spanwise weights are checked, and dz and the -2 w_i of the periodic
+  // second difference are folded into the library's copy of the values (dz a_ij off the
+  // diagonal, dz a_ii - 2 w_i on it), so that the kernels add only w_i (x_{z-1} + x_{z+1}).
+  std::vector<double> w;
+  if (ext_nz > 0) {
+    RB_TRY(fetch(w, block->z_weight, (size_t)csr->n_rows, dev));
+    for (size_t i = 0; i < w.size(); ++i)
+      RB_REQUIRE(std::isfinite(w[i]), "rb_operator_create: z_weight[%zu] is not finite", i);
+    for (int i = 0; i < csr->n_rows; ++i) {
+      int diag = -1;
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        va[p] *= block->dz;
+        if (ci[p] == i) diag = p;
+      }
+      RB_REQUIRE(diag >= 0, "rb_operator_create: row %d of an extruded operator stores no diagonal entry", i);
+      va[diag] -= 2.0 * w[i];
+    }
+  }
   rb_op* op = new rb_op();
   op->n_rows = csr->n_rows;
   op->n_cols = csr->n_cols;
@@ -273,18 +291,8 @@ extern "C" rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_d
       if ((st = upload(op->dinv32, d32.data(), d32.size(), s)) != RB_OK) break;
     }
     if (ext_nz > 0) {
-      std::vector<double> w;
-      if ((st = fetch(w, block->z_weight, (size_t)op->n_rows, dev)) != RB_OK) break;
       std::vector<float> w32(w.size());
-      for (size_t i = 0; i < w.size(); ++i) {
-        if (!std::isfinite(w[i])) {
-          set_error("rb_operator_create: z_weight[%zu] is not finite", i);
-          st = RB_EINVAL;
-          break;
-        }
-        w32[i] = (float)w[i];
-      }
-      if (st != RB_OK) break;
+      for (size_t i = 0; i < w.size(); ++i) w32[i] = (float)w[i];
       op->ext_nz = ext_nz;
       op->dz = block->dz;
       if ((st = dalloc(op, &op->zw64, w.size())) != RB_OK) break;

@@ -62,6 +62,16 @@ def test_host_side_validation_without_gpu(lib):
         g.periodic[d] = 1  # a periodic axis needs >= 3 cells
     nr, nc, nnz = C.c_int32(), C.c_int32(), C.c_int64()
     assert lib.rb_fvm_csr_size(C.byref(g), 0, C.byref(nr), C.byref(nc), C.byref(nnz)) == rb.RB_EINVAL
+    # an extruded operator whose row 1 stores no diagonal entry (host arrays; refused before
+    # any device work, since the spanwise -2 w_i is folded into the stored diagonal)
+    rp = (C.c_int32 * 3)(0, 2, 3)
+    ci = (C.c_int32 * 3)(0, 1, 0)
+    va = (C.c_double * 3)(2.0, -1.0, -1.0)
+    zw = (C.c_double * 2)(0.5, 0.5)
+    csr = rb.CsrDesc(2, 2, 3, C.addressof(rp), C.addressof(ci), C.addressof(va), 0)
+    blk = rb.BlockDesc(3, 3, C.addressof(zw), 0.1)
+    assert lib.rb_operator_create(C.byref(csr), C.byref(blk), rb.RB_F64, rb.RB_CSR, None, C.byref(h)) == rb.RB_EINVAL
+    assert b"diagonal" in lib.rb_last_error()
 
 
 def test_fvm_sizes_match_oracle(lib):
