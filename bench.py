@@ -521,7 +521,7 @@ def k_sweep(torch, rb, ops, dev, hbm):
                 base = ms
             res.append({"dtype": dt, "format": fmt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6,
                         "frac_hbm": by / ms / 1e6 / hbm, "ai_flop_per_byte": 2 * op.nnz * k / by,
-                        "speedup_vs_k_spmv": k * base / ms})
+                        "speedup_vs_k_spmv": k * base / ms, "schedule": op.schedule(X, Y)})
             del X, Y
     return res
 
@@ -780,6 +780,22 @@ def profile_run(args):
             torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile": args.profile, "ok": True}))
         return
+    if args.profile == "spmm":
+        g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+        nodes, per = rb.grid_nodes(g, dev)
+        rp, ci, va, nc = rb.fvm_assemble(nodes, per, rb.RB_FVM_LAPLACIAN)
+        k, dt = args.profile_k, args.profile_dtype
+        op = rb.Operator(rp, ci, va, nc, dtype=dt, k_max=k)
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        X = torch.ones((op.n_cols, k), dtype=tdt, device=dev)
+        Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
+        if args.profile_sched:
+            op.set_schedule(k, *(int(v) for v in args.profile_sched.split(",")))
+        for _ in range(3):
+            op.spmm(X, Y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "ok": True, "schedule": op.schedule(X, Y)}))
+        return
     g, ops = build_ops(rb, torch, dev)
     if args.profile == "step":
         for name in ("L", "G", "M"):
@@ -822,10 +838,15 @@ def main():
                     help="NVTX ranges around the timed region ('timed_step') and each SpMM (its label), for ncu filters")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel, if captured for this build")
-    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess"],
+    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess", "spmm"],
                     help="short run for an ncu capture: 'step' = the timed step only, 'cg' = a 20-iteration "
                          "FP64 and FP32-refinement Poisson solve (k = 1 and 3), 'guess' = one forward and one "
-                         "training pass of the learned-guess network at 128^3 (NVTX 'predict', 'loss_grad')")
+                         "training pass of the learned-guess network at 128^3 (NVTX 'predict', 'loss_grad'), "
+                         "'spmm' = three channel-Laplacian SpMMs with --profile-k columns in --profile-dtype "
+                         "on the schedule --profile-sched (vec,lpr,stage,grid_cap; default: the untuned one)")
+    ap.add_argument("--profile-k", type=int, default=32)
+    ap.add_argument("--profile-dtype", default="f32", choices=["f64", "f32"])
+    ap.add_argument("--profile-sched", default=None)
     args = ap.parse_args()
     if args.profile:
         return profile_run(args)

@@ -163,9 +163,13 @@ __device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64
     re = __ldg(a.rp + row + 1);
   }
   const T* Xc = a.X + chunk * VEC;
-  // Unrolled by two only: with four, rows of 2 or 6 nonzeros (gradient, divergence) run a
-  // remainder whose predicated-off FMAs still take FP64-pipe issue slots (+50% on G, k = 3).
-#pragma unroll 2
+  // FP64: unrolled by two only: with four, rows of 2 or 6 nonzeros (gradient, divergence) run
+  // a remainder whose predicated-off FMAs still take FP64-pipe issue slots (+50% on G, k = 3).
+  // FP32 with up to three columns per lane: four gathers in flight per lane hide more of
+  // their latency (L f32 k = 3 40.7 -> 39.7 us, M f32 k = 1 35.0 -> 33.3 us); with 16-byte
+  // gathers (VEC = 4) four deep was slower (k = 4 and 8, the extruded k = 64).
+  constexpr int kUnroll = (sizeof(T) == 4 && VEC < 4) ? 4 : 2;
+#pragma unroll kUnroll
   for (int p = rs + sub; p < re; p += LPR) {
     const int c = __ldg(a.ci + p);
     const T v = __ldg(a.va + p);

@@ -183,8 +183,10 @@ def test_spmm_channel_full_size_k3(rb, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("nz", [3, 8, 16, 64])
-def test_extruded_spmm(rb, dtype, nz):
+@pytest.mark.parametrize("nz,sched", [(3, None), (8, None), (16, None), (64, None), (16, (4, 1, 1, 0)),
+                                      (16, (2, 1, 2, 0)), (64, (4, 2, 0, -1)), (64, (4, 1, 2, 0))])
+def test_extruded_spmm(rb, dtype, nz, sched):
+    """The spanwise epilogue in every kernel: direct (lanes per row 1 and 2), block-staged, TMA."""
     m = W.random_trimesh(300, nz)
     L, _ = mesh.cot_laplacian(m)
     a = mesh.dual_areas(m)
@@ -193,6 +195,8 @@ def test_extruded_spmm(rb, dtype, nz):
     X = W.normal((L.shape[0], nz), 500 + nz)
     npdt = np.float64 if dtype == "f64" else np.float32
     op = rb.Operator.from_scipy(L, dtype=dtype, k_max=nz, extruded_nz=nz, z_weight=torch.as_tensor(w), dz=dz)
+    if sched:
+        op.set_schedule(nz, *sched)
     Y = op.spmm(to_dev(X.astype(npdt))).cpu().numpy()
     if dtype == "f64":
         Lr, wr, dzr, Xr = L, w, dz, X
