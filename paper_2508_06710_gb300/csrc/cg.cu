@@ -781,7 +781,10 @@ struct Solver {
   double* partials;
   cudaStream_t s;
   SpmmSched sched64, sched32;
-  // one resident wave of `kern`, never more blocks than there are row blocks
+  // One resident wave of `kern`, never more blocks than there are row blocks.  Also when the
+  // plain SpMM's tuned schedule launches one block per row block: for these reducing kernels
+  // the last block's sum over ~9000 block partials costs more than the wave's grid stride
+  // (channel Poisson solve, k = 3: FP64 CG 253 -> 341 ms, refinement 129 -> 218 ms).
   template <typename K_>
   int spmm_grid(K_* kern, const SpmmSched& sc) const {
     const int R = sc.rows_per_block();
@@ -825,7 +828,8 @@ struct Solver {
   template <typename T, int VEC, int LPR>
   void launch_q2(const rb_op* op, const SpmmSched& ss, const T* p, T* q, const T* dinv, CgCtl c) const {
     CsrArgs<T> a = args<T>(op, ss, p, k, q, k);
-    k_cg_q2<T, VEC, LPR><<<spmm_grid(&k_cg_q2<T, VEC, LPR>, ss), kThreads, 0, s>>>(a, c, dinv, sc, partials);
+    k_cg_q2<T, VEC, LPR><<<spmm_grid(&k_cg_q2<T, VEC, LPR>, ss), kThreads, 0, s>>>(a, c, dinv, sc,
+                                                                                          partials);
   }
 
   template <typename T, int VEC>
@@ -841,8 +845,8 @@ struct Solver {
   template <int VEC, int LPR>
   void launch_resid_t(int mode, const double* B, int64_t ldb, const double* X, int64_t ldx, double* r) const {
     CsrArgs<double> a = args<double>(A, sched64, X, ldx, nullptr, 0);
-    k_cg_resid<VEC, LPR><<<spmm_grid(&k_cg_resid<VEC, LPR>, sched64), kThreads, 0, s>>>(a, ctl, mode, B, ldb, r, sc,
-                                                                                       partials);
+    k_cg_resid<VEC, LPR><<<spmm_grid(&k_cg_resid<VEC, LPR>, sched64), kThreads, 0, s>>>(a, ctl, mode, B, ldb,
+                                                                                              r, sc, partials);
   }
 
   template <int VEC>

@@ -83,6 +83,8 @@ __device__ __forceinline__ double final_sum(const double* partials, int m, int n
   const int o = t % mp, g = t / mp;
   double s = 0.0;
   if (o < m && g < groups) {
+    // unrolled so that the loads are in flight together; the additions keep their order
+#pragma unroll 8
     for (int b = g; b < nblocks; b += groups) s += __ldcg(partials + (size_t)b * m + o);
   }
   // fold the groups: within a warp when mp <= 32, then across warps through shared memory
