@@ -138,7 +138,8 @@ def ir_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_rtol=1e-4
 
     Outer loop: r = b - A x in FP64; stop when ||r|| <= rtol ||b||; otherwise solve
     A32 d = r / ||r|| in FP32 (values and vectors rounded to nearest even) with FP64 dot
-    accumulation to ``inner_rtol``, then x += ||r|| d in FP64.
+    accumulation to ``inner_rtol`` (relaxed to half of what the outer tolerance still needs,
+    0.5 rtol ||b|| / ||r||, when that is larger), then x += ||r|| d in FP64.
     """
     A32 = A.astype(np.float32)
     b = np.asarray(b, dtype=np.float64)
@@ -155,7 +156,8 @@ def ir_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_rtol=1e-4
             return x, ColumnInfo(total_inner, np.linalg.norm(b - A @ x) / nb, OK), sweep
         if sweep == max_sweeps:
             break
-        d32, it = pcg_fp32(A32, (r / nr).astype(np.float32), inner_rtol, inner_max_iter, jacobi)
+        tol = max(inner_rtol, 0.5 * rtol * nb / nr)
+        d32, it = pcg_fp32(A32, (r / nr).astype(np.float32), tol, inner_max_iter, jacobi)
         total_inner += it
         x = x + nr * d32.astype(np.float64)
     x = _project(x, project_mean)
@@ -171,7 +173,8 @@ def ir_reliable_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_
     next direction built from the replaced residual and the previous direction, both in the
     new normalisation: z = D^-1 r32, beta = (r32 . z) / (rz_prev (s_prev / s)^2),
     p32 <- z + beta p32 s_prev / s (the first sweep starts from p32 = z), and runs until
-    its residual falls by ``inner_rtol``; then x += s d32 in FP64.  Replacing only the
+    its residual falls by ``inner_rtol`` (or only to half of what the outer tolerance still
+    needs, 0.5 rtol ||b|| / s, when that is larger); then x += s d32 in FP64.  Replacing only the
     residual, not the direction, keeps the Krylov progress, so the iteration count stays
     close to plain FP64 CG.
     """
@@ -217,7 +220,7 @@ def ir_reliable_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_
             d = d + alpha * p
             r32 = r32 - alpha * q
             total += 1
-            if d64(r32, r32) <= inner_rtol**2 * rr0:
+            if d64(r32, r32) <= max(inner_rtol**2 * rr0, 0.25 * (rtol * nb / s) ** 2):
                 break
             z = dinv * r32
             rz_new = d64(r32, z)

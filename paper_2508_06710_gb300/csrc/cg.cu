@@ -638,7 +638,11 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
     if (sc->ostate[j] == ST_ACTIVE && totals[k + j] > 0.0) {
       sc->rz[j] = totals[j];
       sc->rr[j] = totals[k + j];
-      sc->tol2[j] = ctl.inner_rtol2 * totals[k + j];
+      // inner target: inner_rtol of the sweep's residual, but never past what the outer
+      // tolerance still needs (half of it, in the inner scale r / s), so that the last sweep
+      // does not overshoot
+      const double s2 = sc->oscale[j] * sc->oscale[j];
+      sc->tol2[j] = fmax(ctl.inner_rtol2 * totals[k + j], 0.25 * sc->otol2[j] / s2);
       sc->state[j] = ST_ACTIVE;
     } else {
       sc->state[j] = ST_IDLE;
