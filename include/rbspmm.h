@@ -237,9 +237,11 @@ typedef struct {
                             updates: the inner recurrence keeps its search direction across
                             sweeps (rescaled) and only its residual is replaced by the FP64
                             one, which keeps the iteration count near that of FP64 CG */
-  double inner_rtol;     /* mixed: the residual reduction of each sweep (e.g. 3e-3 for mixed = 2,
+  double inner_rtol;     /* mixed: the residual reduction of each sweep (e.g. 5e-2 for mixed = 2,
                             1e-4 for mixed = 1); a sweep stops earlier when half of what the
-                            outer tolerance still needs is a smaller reduction */
+                            outer tolerance still needs is a smaller reduction.  The k columns
+                            of a sweep iterate together: one that met its target keeps
+                            iterating until all have (its share of the SpMM is paid anyway) */
   int32_t max_sweeps;    /* mixed: refinement sweeps */
   int32_t project_mean;  /* 1: singular periodic/Neumann operator; remove the column mean of
                             every true residual and of the final x (zero-mean solution) */

@@ -166,70 +166,109 @@ def ir_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_rtol=1e-4
 
 def ir_reliable_pcg(A: sp.csr_matrix, b: np.ndarray, x0=None, rtol=1e-10, inner_rtol=1e-4, max_sweeps=50,
                     max_iter=20000, jacobi=True, project_mean=False):
-    """FP32-inner refinement that keeps the search direction across sweeps (reliable updates).
+    """FP32-inner refinement with reliable updates for one right-hand side: the k = 1 case of
+    ``ir_reliable_pcg_block`` (same arguments, b a vector; returns x, its ColumnInfo and the
+    number of sweeps)."""
+    B = np.asarray(b, dtype=np.float64)[:, None]
+    X0 = None if x0 is None else np.asarray(x0, dtype=np.float64)[:, None]
+    X, infos, sweeps = ir_reliable_pcg_block(A, B, X0, rtol, inner_rtol, max_sweeps, max_iter, jacobi, project_mean)
+    return X[:, 0], infos[0], sweeps
 
-    Each sweep: r = b - A x in FP64 (stop if ||r|| <= rtol ||b||), s = ||r||, r32 = r / s; the
-    FP32 recurrence (FP32 matrix and vectors, FP64 dot accumulation) then continues with the
-    next direction built from the replaced residual and the previous direction, both in the
-    new normalisation: z = D^-1 r32, beta = (r32 . z) / (rz_prev (s_prev / s)^2),
-    p32 <- z + beta p32 s_prev / s (the first sweep starts from p32 = z), and runs until
-    its residual falls by ``inner_rtol`` (or only to half of what the outer tolerance still
-    needs, 0.5 rtol ||b|| / s, when that is larger); then x += s d32 in FP64.  Replacing only the
-    residual, not the direction, keeps the Krylov progress, so the iteration count stays
-    close to plain FP64 CG.
+
+def ir_reliable_pcg_block(A: sp.csr_matrix, B: np.ndarray, X0=None, rtol=1e-10, inner_rtol=1e-4, max_sweeps=50,
+                          max_iter=20000, jacobi=True, project_mean=False):
+    """FP32-inner refinement that keeps the search direction across sweeps (reliable updates),
+    for the k columns of B solved together.
+
+    Each sweep, per column not yet converged: r = b - A x in FP64 (the column is done once
+    ||r|| <= rtol ||b||), s = ||r||, r32 = r / s; the FP32 recurrence (FP32 matrix and vectors,
+    FP64 dot accumulation) then continues with the next direction built from the replaced
+    residual and the previous direction, both in the new normalisation: z = D^-1 r32,
+    beta = (r32 . z) / (rz_prev (s_prev / s)^2), p32 <- z + beta p32 s_prev / s (the first
+    sweep starts from p32 = z).  A column's target for the sweep is a fall of its residual by
+    ``inner_rtol``, or only to half of what the outer tolerance still needs
+    (0.5 rtol ||b|| / s) when that is larger.  The columns iterate together: one that has met
+    its target keeps iterating until every column of the sweep has (the shared operator pass
+    costs the same for all of them), and a column whose p . q <= 0 stops.  Then x += s d32 in
+    FP64.  Replacing only the residual, not the direction, keeps the Krylov progress, so the
+    iteration count stays close to plain FP64 CG.  ``iters`` counts, per column, the inner
+    iterations it took part in.
     """
     f32 = np.float32
     A32 = A.astype(f32)
-    b = np.asarray(b, dtype=np.float64)
-    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
-    nb = np.linalg.norm(b)
-    if nb == 0.0:
-        return np.zeros_like(b), ColumnInfo(0, 0.0, OK), 0
-    dinv = (1.0 / A32.diagonal().astype(np.float64)).astype(f32) if jacobi else np.ones(b.shape[0], dtype=f32)
+    B = np.asarray(B, dtype=np.float64)
+    n, k = B.shape
+    X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64)
+    nb = np.linalg.norm(B, axis=0)
+    dinv = (1.0 / A32.diagonal().astype(np.float64)).astype(f32) if jacobi else np.ones(n, dtype=f32)
     d64 = lambda u, v: float(np.dot(u.astype(np.float64), v.astype(np.float64)))
-    p = None
-    s_prev = 0.0
-    rz = 0.0
-    total = 0
+    P = [None] * k
+    s_prev = np.zeros(k)
+    rz = np.zeros(k)
+    iters = [0] * k
+    done = [bool(nb[j] == 0.0) for j in range(k)]
+    for j in range(k):
+        if done[j]:
+            X[:, j] = 0.0
+    sweeps = 0
     for sweep in range(max_sweeps + 1):
-        r = _project(b - A @ x, project_mean)
-        s = np.linalg.norm(r)
-        if s <= rtol * nb:
-            x = _project(x, project_mean)
-            return x, ColumnInfo(total, np.linalg.norm(b - A @ x) / nb, OK), sweep
-        if sweep == max_sweeps or total >= max_iter:
-            break
-        r32 = (r / s).astype(f32)
-        z = dinv * r32
-        rz_new = d64(r32, z)
-        if p is None:
-            p = z.copy()
-        else:
-            ratio = s_prev / s
-            beta = rz_new / (rz * ratio * ratio)
-            p = z + f32(beta) * (p * f32(ratio)).astype(f32)
-        rz = rz_new
-        rr0 = d64(r32, r32)
-        d = np.zeros_like(r32)
-        while total < max_iter:
-            q = (A32 @ p).astype(f32)
-            pq = d64(p, q)
-            if not np.isfinite(pq) or pq <= 0.0:
-                break
-            alpha = f32(rz / pq)
-            d = d + alpha * p
-            r32 = r32 - alpha * q
-            total += 1
-            if d64(r32, r32) <= max(inner_rtol**2 * rr0, 0.25 * (rtol * nb / s) ** 2):
-                break
+        sweeps = sweep
+        R32, S, target, active = {}, {}, {}, []
+        for j in range(k):
+            if done[j]:
+                continue
+            r = _project(B[:, j] - A @ X[:, j], project_mean)
+            s = np.linalg.norm(r)
+            if s <= rtol * nb[j]:
+                done[j] = True
+                continue
+            active.append(j)
+            r32 = (r / s).astype(f32)
             z = dinv * r32
             rz_new = d64(r32, z)
-            p = z + f32(rz_new / rz) * p
-            rz = rz_new
-        x = x + s * d.astype(np.float64)
-        s_prev = s
-    x = _project(x, project_mean)
-    return x, ColumnInfo(total, np.linalg.norm(b - A @ x) / nb, NOCONV), max_sweeps
+            if P[j] is None:
+                P[j] = z.copy()
+            else:
+                ratio = s_prev[j] / s
+                beta = rz_new / (rz[j] * ratio * ratio)
+                P[j] = z + f32(beta) * (P[j] * f32(ratio)).astype(f32)
+            rz[j] = rz_new
+            R32[j], S[j] = r32, s
+            target[j] = max(inner_rtol**2 * d64(r32, r32), 0.25 * (rtol * nb[j] / s) ** 2)
+        if not active or sweep == max_sweeps or max(iters) >= max_iter:
+            break
+        D = {j: np.zeros(n, dtype=f32) for j in active}
+        running = list(active)
+        met = {j: False for j in active}
+        while running and max(iters) < max_iter:
+            for j in list(running):
+                q = (A32 @ P[j]).astype(f32)
+                pq = d64(P[j], q)
+                if not np.isfinite(pq) or pq <= 0.0:
+                    running.remove(j)
+                    continue
+                alpha = f32(rz[j] / pq)
+                D[j] = D[j] + alpha * P[j]
+                R32[j] = R32[j] - alpha * q
+                iters[j] += 1
+                if d64(R32[j], R32[j]) <= target[j]:
+                    met[j] = True
+            if all(met[j] for j in running):
+                break  # the sweep ends; the next one continues from each column's last direction
+            for j in running:
+                z = dinv * R32[j]
+                rz_new = d64(R32[j], z)
+                P[j] = z + f32(rz_new / rz[j]) * P[j]
+                rz[j] = rz_new
+        for j in active:
+            X[:, j] = X[:, j] + S[j] * D[j].astype(np.float64)
+            s_prev[j] = S[j]
+    infos = []
+    for j in range(k):
+        X[:, j] = _project(X[:, j], project_mean)
+        rel = np.linalg.norm(B[:, j] - A @ X[:, j]) / nb[j] if nb[j] > 0 else 0.0
+        infos.append(ColumnInfo(iters[j], rel, OK if done[j] else NOCONV))
+    return X, infos, sweeps
 
 
 def batch_solve(systems, **kw):

@@ -58,6 +58,7 @@ struct CgScal {
   unsigned counter[8];   // last-block tickets, one per reducing kernel
   unsigned pbar[4];      // persistent solve: barrier arrivals, generation, error word
   int pact[2];           // persistent solve: system still active after iteration it (slot it & 1)
+  int met[K];            // inner solve: the column has reached its sweep's target
 };
 
 struct CgCtl {
@@ -388,10 +389,24 @@ __global__ void __launch_bounds__(kThreads) k_cg_xrp(CgCtl ctl, T* __restrict__ 
     sc->rr[j] = rr_new;
     sc->rz[j] = rz_new;
     if (!isfinite(rr_new) || !isfinite(rz_new)) sc->state[j] = ctl.inner ? ST_DONE : ST_BREAKDOWN;
-    else if (rr_new <= sc->tol2[j]) sc->state[j] = ctl.inner ? ST_DONE : ST_CHECK;
+    else if (rr_new <= sc->tol2[j]) {
+      if (ctl.inner) sc->met[j] = 1;
+      else sc->state[j] = ST_CHECK;
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) recount(sc, k);
+  if (threadIdx.x == 0) {
+    // inner solve: a column that has met its target keeps iterating (its share of the SpMM
+    // is paid anyway) until every active column has; then the sweep ends for all of them
+    if (ctl.inner) {
+      bool all = true;
+      for (int c = 0; c < k; ++c) all &= sc->state[c] != ST_ACTIVE || sc->met[c] != 0;
+      if (all)
+        for (int c = 0; c < k; ++c)
+          if (sc->state[c] == ST_ACTIVE) sc->state[c] = ST_DONE;
+    }
+    recount(sc, k);
+  }
 }
 
 // ------------------------------------------------ true residual r = b - A x (FP64 operator)
@@ -635,6 +650,7 @@ __global__ void __launch_bounds__(kThreads) k_ir_init(CgCtl ctl, const double* _
   __syncthreads();
   const int j = threadIdx.x;
   if (j < k) {
+    sc->met[j] = 0;
     if (sc->ostate[j] == ST_ACTIVE && totals[k + j] > 0.0) {
       sc->rz[j] = totals[j];
       sc->rr[j] = totals[k + j];
@@ -1323,7 +1339,7 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
   __shared__ double out[2 * K];
   __shared__ double tot[2 * K];
   __shared__ double l_rz[K], l_alpha[K], l_beta[K];
-  __shared__ int l_state[K], l_iters[K];
+  __shared__ int l_state[K], l_iters[K], l_met[K];
   __shared__ int go, mine;
   int my = -1;
   for (int s = 0; s < b.n_sys; ++s)
@@ -1334,6 +1350,7 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
     l_state[threadIdx.x] = __ldcg(&sc->state[threadIdx.x]);
     l_rz[threadIdx.x] = __ldcg(&sc->rz[threadIdx.x]);
     l_iters[threadIdx.x] = __ldcg(&sc->iters[threadIdx.x]);
+    l_met[threadIdx.x] = 0;
   }
   // Every block must leave the loop in the same iteration.  The states at entry are the same
   // for all blocks; later, the leads publish after each iteration whether their system is
@@ -1413,14 +1430,26 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
         if (l_state[j] == ST_ACTIVE) {
           l_iters[j] += 1;
           l_rz[j] = rz_new;
-          if (!isfinite(rr_new) || !isfinite(rz_new) || rr_new <= S.sc->tol2[j]) l_state[j] = ST_DONE;
+          if (!isfinite(rr_new) || !isfinite(rz_new)) l_state[j] = ST_DONE;
+          else if (rr_new <= S.sc->tol2[j]) l_met[j] = 1;
           if (lead) S.sc->rr[j] = rr_new;
         }
-        if (lead) {
-          S.sc->iters[j] = l_iters[j];
-          S.sc->state[j] = l_state[j];
-          S.sc->rz[j] = l_rz[j];
-        }
+      }
+      __syncthreads();
+      // as in the two-kernel loop: columns that met their target keep iterating until every
+      // active column of the system has
+      if (threadIdx.x == 0) {
+        bool all = true;
+        for (int c = 0; c < S.k; ++c) all &= l_state[c] != ST_ACTIVE || l_met[c] != 0;
+        if (all)
+          for (int c = 0; c < S.k; ++c)
+            if (l_state[c] == ST_ACTIVE) l_state[c] = ST_DONE;
+      }
+      __syncthreads();
+      if (lead && j < S.k) {
+        S.sc->iters[j] = l_iters[j];
+        S.sc->state[j] = l_state[j];
+        S.sc->rz[j] = l_rz[j];
       }
       __syncthreads();
       if (lead && threadIdx.x == 0) recount(S.sc, S.k);
@@ -1666,9 +1695,13 @@ void fill_report(const CgScal& hs, int k, int mixed, rb_cg_report& rep, rb_statu
     rep.iters[j] = hs.iters[j];
     rep.true_rel_res[j] = hs.bb[j] > 0 ? sqrt(hs.rr_true[j] / hs.bb[j]) : 0.0;
     const int st = mixed ? hs.ostate[j] : hs.state[j];
+    // the recorded batch sequence ends after its last sweep without another outer check: a
+    // column whose final true residual (just computed in FP64) meets the tolerance has converged
+    const double tol2 = mixed ? hs.otol2[j] : hs.tol2[j];
+    const bool met = hs.bb[j] > 0 && hs.rr_true[j] <= tol2;
     rb_status cs = RB_OK;
     if (st == ST_BREAKDOWN) cs = RB_EBREAKDOWN;
-    else if (st == ST_NOCONV || st == ST_ACTIVE || st == ST_RESTART) cs = RB_ENOCONV;
+    else if ((st == ST_NOCONV || st == ST_ACTIVE || st == ST_RESTART) && !met) cs = RB_ENOCONV;
     rep.status[j] = cs;
     if (cs == RB_EBREAKDOWN || (cs == RB_ENOCONV && worst == RB_OK)) worst = cs;
   }

@@ -113,6 +113,29 @@ def test_reliable_ir_matches_fp64_and_keeps_iterations():
     assert 3 <= sweeps <= 8
 
 
+def test_reliable_ir_block_columns_in_lockstep():
+    """The k-column reliable refinement: every column reaches the FP64 solution within
+    kappa * 1e-10; columns that are not done share each sweep's iterations (a column that met
+    its target keeps iterating), so their counts agree until they finish; k = 1 is the
+    single-column solve; the total stays near FP64 CG's."""
+    g = W.channel_grid(16, 12, 10)
+    A = (-fvm.laplacian(g)).tocsr()
+    B = W.zero_mean(W.normal((A.shape[0], 3), 13))
+    B[:, 2] *= 1e-3  # a different scale: the same relative tolerance
+    X, infos, sweeps = cg.ir_reliable_pcg_block(A, B, rtol=1e-10, inner_rtol=5e-2, project_mean=True)
+    Ad = A.toarray()
+    kappa = np.linalg.cond(Ad + np.ones_like(Ad))
+    for j in range(3):
+        x64, i64 = cg.pcg(A, B[:, j], rtol=1e-10, project_mean=True)
+        assert infos[j].status == cg.OK and infos[j].rel_res <= 1e-10
+        assert np.linalg.norm(X[:, j] - x64) <= kappa * 2e-10 * np.linalg.norm(x64)
+        assert infos[j].iters <= 1.3 * i64.iters
+    assert max(i.iters for i in infos) - min(i.iters for i in infos) <= max(i.iters for i in infos) // 4
+    x1, i1, s1 = cg.ir_reliable_pcg(A, B[:, 0], rtol=1e-10, inner_rtol=5e-2, project_mean=True)
+    X1, I1, S1 = cg.ir_reliable_pcg_block(A, B[:, :1], rtol=1e-10, inner_rtol=5e-2, project_mean=True)
+    assert np.array_equal(x1, X1[:, 0]) and i1.iters == I1[0].iters and s1 == S1
+
+
 def test_batch_equals_individual_solves():
     systems = []
     for s, k in ((W.unit_periodic_grid(6), 2), (W.channel_grid(6, 5, 4), 1)):
