@@ -291,6 +291,15 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_mma(Conv3Args a) {
 // (M = 64: row m in lane 32 (m / 16) + m % 16, the first 16 lanes of each warp's quarter).
 // rows per work item: long runs reuse the ring (2 halo rows per run), short runs give more
 // items; the launch picks the longest run that still yields enough items to fill the GPU
+// Forward and input-gradient launches: the rows of each z plane are cut into the most equal
+// runs that still give one run per resident CTA (resident / nz runs per plane, at least one),
+// so that no CTA waits for a second run while others idle.  (Runs of 16 rows over 1024
+// items and 912 resident CTAs at 128^3 left 112 CTAs a second run: the launch took 32
+// row-steps for an average of 18.)
+inline int row_chunk_fill(int ny, int nz, int resident) {
+  const int parts = std::max(1, std::min(ny, resident / std::max(nz, 1)));
+  return (ny + parts - 1) / parts;
+}
 inline int row_chunk(int ny, int nz, int want_items) {
   int c = 16;
   while (c > 2 && nz * ((ny + c - 1) / c) < want_items) c /= 2;
@@ -349,6 +358,10 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chu
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // base descriptors (start address sL or sB); see the MMA issue below
+  const uint64_t adesc_g1 = umma_sdesc(sL, 16, 128);
+  const uint64_t adesc_gn = umma_sdesc(sL, kGroupBytes, 128);
+  const uint64_t bdesc0 = umma_sdesc(sB, 128, sbo_b);
 
   auto line_addr = [&](int cg, int dzi, int yy) -> uint32_t {
     return sL + (uint32_t)cg * kGroupBytes + (uint32_t)(dzi * 4 + (yy & 3)) * kLineBytes;
@@ -445,21 +458,24 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chu
       if (tid == 0) {
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)((tcount & 1) * NP);
+        // Descriptors differ only in their start address (bits 0-13, in 16-byte units), and
+        // every shared address here is below 256 KB: each MMA's descriptor is a base
+        // descriptor plus its byte offset / 16, with no carry out of the field.
+        uint64_t bdesc = bdesc0;
         uint32_t kk = 0;
         if (G == 1) {
           for (int li = 0; li < 9; ++li) {
-            const uint32_t base = line_addr(0, li / 3, y + li % 3 - 1);
+            const uint64_t a = adesc_g1 + ((line_addr(0, li / 3, y + li % 3 - 1) - sL) >> 4);
 #pragma unroll
-            for (int h = 0; h < 2; ++h, ++kk)
-              umma_bf16(d, umma_sdesc(base + 32u * h, 16, 128), umma_sdesc(sB + kk * 256, 128, sbo_b), idesc,
-                        kk > 0 ? 1u : 0u);
+            for (int h = 0; h < 2; ++h, ++kk, bdesc += 16)
+              umma_bf16(d, a + 2u * h, bdesc, idesc, kk > 0 ? 1u : 0u);
           }
         } else {
           for (int tap = 0; tap < 27; ++tap) {
             const int dzi = tap / 9, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-            for (int cp = 0; cp < G / 2; ++cp, ++kk)
-              umma_bf16(d, umma_sdesc(line_addr(2 * cp, dzi, y + dy) + (uint32_t)(1 + dx) * 16, kGroupBytes, 128),
-                        umma_sdesc(sB + kk * 256, 128, sbo_b), idesc, kk > 0 ? 1u : 0u);
+            const uint64_t a = adesc_gn + ((line_addr(0, dzi, y + dy) - sL + (uint32_t)(1 + dx) * 16) >> 4);
+            for (int cp = 0; cp < G / 2; ++cp, ++kk, bdesc += 16)
+              umma_bf16(d, a + (uint64_t)((2u * cp * kGroupBytes) >> 4), bdesc, idesc, kk > 0 ? 1u : 0u);
           }
         }
         umma_commit(&acc_bar[tcount & 1]);
@@ -1542,7 +1558,7 @@ rb_status launch_row_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
     per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kConvThreads, tmem_cols_for(2 * NP));
     per_sm_smem = smem;
   }
-  const int chunk = row_chunk(a.d.ny, a.d.nz, 2 * per_sm * guess_sm_count());
+  const int chunk = row_chunk_fill(a.d.ny, a.d.nz, per_sm * guess_sm_count());
   const int items = a.d.nz * ((a.d.ny + chunk - 1) / chunk);
   const int grid = std::max(1, std::min(items, per_sm * guess_sm_count()));
   kern<<<grid, kConvThreads, smem, s>>>(a, chunk);
