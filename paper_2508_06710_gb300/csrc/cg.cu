@@ -1306,17 +1306,18 @@ __device__ void pphase_xrp(const PBatch& b, const PSys& S, const double* alpha, 
 }
 
 // Totals over the blocks of system S of nq partial quantities (slots q0 .. q0 + nq/k - 1 of its
-// k columns): warp w < nq sums quantity w over the system's blocks in a fixed order (lanes
-// strided, then a shuffle tree); every block of S computes the same totals, so the per-column
-// scalars need no broadcast.  Results land in out[w]; whole block calls.
+// k columns): warp w sums quantities w, w + 16, ... over the system's blocks in a fixed order
+// (lanes strided, then a shuffle tree); every block of S computes the same totals, so the
+// per-column scalars need no broadcast.  Results land in out[i] for i < nq (nq <= 2 K);
+// whole block calls.
 __device__ void psys_totals(const PBatch& b, const PSys& S, int q0, int nq, double* out) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w < nq) {
-    const int q = q0 + w / S.k, c = S.col0 + w % S.k;
+  for (int i = w; i < nq; i += kPWarps) {
+    const int q = q0 + i / S.k, c = S.col0 + i % S.k;
     double s = 0.0;
     for (int bb = lane; bb < S.nblk; bb += 32) s += __ldcg(&b.partials[((size_t)(S.blk0 + bb) * 4 + q) * K + c]);
     for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[w] = s;
+    if (lane == 0) out[i] = s;
   }
   __syncthreads();
 }

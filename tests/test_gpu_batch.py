@@ -38,7 +38,7 @@ def _make(rb, systems, mixed=2):
         Bs.append(B)
         ops.append(rb.Operator.from_scipy(A, k_max=k))
         ops32.append(rb.Operator.from_scipy(A, dtype="f32", k_max=k))
-    prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, max_sweeps=8)
+    prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, max_sweeps=16)
     batch = rb.Batch(ops, ops32, [s[1] for s in systems], prm)
     return batch, As, Bs
 
@@ -83,10 +83,27 @@ def test_batch_equals_single_solves(rb):
         op32 = rb.Operator.from_scipy(A, dtype="f32", k_max=k)
         x1 = torch.zeros_like(X)
         r1 = rb.cg_solve(op, to_dev(B), x1, A_inner=op32,
-                         params=rb.cg_params(rtol=1e-10, mixed=2, project_mean=True, max_sweeps=8))
+                         params=rb.cg_params(rtol=1e-10, mixed=2, project_mean=True, max_sweeps=16))
         assert r1.status == rb.RB_OK
         assert torch.allclose(X, x1, rtol=1e-6, atol=1e-9 * float(x1.abs().max()))
         assert all(abs(a - b) <= max(3, b // 20) for a, b in zip(r.iters, r1.iters)), (r.iters, r1.iters)
+
+
+def test_batch_at_the_column_limit(rb):
+    """64 columns in total (the limit) over systems with 32, 24 and 8 columns: the persistent
+    kernel's partial slots for every batch column and its wide-block reductions."""
+    systems = [(W.unit_periodic_grid(10), 32, 21), (W.channel_grid(12, 10, 8, gamma=1.5), 24, 22),
+               (W.unit_periodic_grid(8), 8, 23)]
+    batch, As, Bs = _make(rb, systems, 2)
+    Bd = [to_dev(B) for B in Bs]
+    Xd = [torch.zeros_like(b) for b in Bd]
+    res = batch.solve(Bd, Xd)
+    for A, B, X, r in zip(As, Bs, Xd, res):
+        assert r.status == rb.RB_OK, r
+        Xh = X.cpu().numpy()
+        assert np.all(_true_res(A, B, Xh) <= 1e-10)
+        Xr, _ = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True)
+        assert np.all(np.linalg.norm(Xh - Xr, axis=0) <= 1e-6 * np.linalg.norm(Xr, axis=0))
 
 
 @pytest.mark.parametrize("k", [1, 3, 8])

@@ -84,6 +84,23 @@ def test_cg_channel_stretched(rb, mixed):
             assert res.iters[j] <= 1.3 * infos[j].iters
 
 
+@pytest.mark.parametrize("k", [33, 64])
+@pytest.mark.parametrize("mixed", [0, 2])
+def test_cg_wide_blocks(rb, k, mixed):
+    """The widest blocks: k = 64 (the column limit; four columns per lane, 16 lanes per row)
+    and k = 33 (three per lane, 11 of 16 lanes busy): every column to the true 1e-10 residual
+    and to the oracle's solution; columns scaled over six decades share one relative tolerance."""
+    g = W.unit_periodic_grid(12)
+    A = _poisson(g)
+    B = W.zero_mean(W.normal((A.shape[0], k), W.seed_for(7, k)))
+    B *= np.logspace(-3, 3, k)[None, :]
+    res, X = _solve(rb, A, B, mixed=mixed)
+    assert res.status == rb.RB_OK, res
+    assert np.all(_true_res(A, B, X) <= 1e-10)
+    Xr, _ = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True)
+    assert np.all(np.linalg.norm(X - Xr, axis=0) <= 1e-7 * np.linalg.norm(Xr, axis=0))
+
+
 def test_cg_initial_guess_and_already_converged(rb):
     g = W.unit_periodic_grid(16)
     A = _poisson(g)
