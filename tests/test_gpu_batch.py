@@ -106,7 +106,7 @@ def test_batch_at_the_column_limit(rb):
         assert np.all(np.linalg.norm(Xh - Xr, axis=0) <= 1e-6 * np.linalg.norm(Xr, axis=0))
 
 
-@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("k", [1, 3, 8, 16])
 def test_persistent_single_system(rb, k):
     g = W.channel_grid(40, 32, 24, gamma=1.5)
     A, B = _system(g, k, 40 + k)

@@ -171,6 +171,15 @@ def test_spmm_edge_cases(rb):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_spmm_no_nonzeros(rb, dtype, k):
+    """Rows but no nonzeros: Y = 0 (not NaN, not stale) on every schedule the tuner tries."""
+    A = sp.csr_matrix((50, 30))
+    op = _run(rb, A, W.normal((30, k), 2), dtype, tune=True)
+    assert op.nnz == 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_spmm_channel_full_size_k3(rb, dtype):
     """192 x 128 x 96 channel Laplacian, k = 3, in the bench's launch configuration."""
     g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
