@@ -33,6 +33,49 @@ __device__ __forceinline__ double centre_dist(const GridDev& g, int d, int t) {
   return 0.5 * (width(g, d, lo) + width(g, d, t));
 }
 
+// Cell widths and reciprocal centre distances along each axis, as the row kernels read them:
+// either computed where needed (GeomDirect) or from tables that each block builds once in
+// shared memory (GeomTab: 2 (nx + ny + nz) doubles), which takes the FP64 divisions (a few
+// dozen FP64-pipe instructions each, six per Laplacian row) out of the per-row work.  A face
+// coefficient is A_f * (1 / d_f) in both (one rounding more than A_f / d_f; both neighbours of
+// a face compute it from the same operands, so L stays exactly symmetric).
+struct GeomDirect {
+  const GridDev* g;
+  double s;  // scale of icd: the operator's scale for L and G (folded in), 1 for M
+  __device__ double w(int d, int t) const { return width(*g, d, t); }
+  __device__ double icd(int d, int t) const { return s / centre_dist(*g, d, t); }
+};
+struct GeomTab {
+  const double* wt[3];
+  const double* it[3];
+  __device__ double w(int d, int t) const { return wt[d][t]; }
+  __device__ double icd(int d, int t) const { return it[d][t]; }
+};
+
+inline size_t geom_tab_bytes(const GridDev& g) { return 16 * (size_t)(g.n[0] + g.n[1] + g.n[2]); }
+constexpr size_t kGeomTabMax = 48 * 1024;
+
+// whole block: the tables in shared memory (icd scaled by s)
+__device__ GeomTab build_geom_tab(const GridDev& g, double* smem, double s) {
+  GeomTab t;
+  double* p = smem;
+  for (int d = 0; d < 3; ++d) {
+    t.wt[d] = p;
+    p += g.n[d];
+  }
+  for (int d = 0; d < 3; ++d) {
+    t.it[d] = p;
+    p += g.n[d];
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int i = threadIdx.x; i < g.n[d]; i += blockDim.x) {
+      const_cast<double*>(t.wt[d])[i] = width(g, d, i);
+      const_cast<double*>(t.it[d])[i] = s / centre_dist(g, d, i);
+    }
+  __syncthreads();
+  return t;
+}
+
 // number of (cell, wall face) incidences over the cells before `id` (lexicographic, x fastest)
 __device__ __forceinline__ int64_t walls_before(const GridDev& g, int i, int j, int k) {
   const int64_t Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
@@ -61,141 +104,216 @@ __device__ __forceinline__ int64_t face_index(const GridDev& g, int dir, const i
   return face_offset(g, dir) + f[0] + (int64_t)face_dim(g, dir, 0) * (f[1] + (int64_t)face_dim(g, dir, 1) * f[2]);
 }
 
-__device__ __forceinline__ double face_area(const GridDev& g, int dir, const int c[3]) {
-  // product of the two transverse widths, in increasing axis order
+// product of the two transverse widths, in increasing axis order
+template <class Geom>
+__device__ __forceinline__ double face_area(const Geom& G, int dir, const int c[3]) {
   const int a = dir == 0 ? 1 : 0;
   const int b = dir == 2 ? 1 : 2;
-  return width(g, a, c[a]) * width(g, b, c[b]);
+  return G.w(a, c[a]) * G.w(b, c[b]);
 }
 
+// Sorts a row's (column, value) pairs by column with a fixed compare-exchange network
+// (every index known at compile time, so the arrays stay in registers); absent entries carry
+// the column INT64_MAX and sort to the end.  Odd-even transposition: N rounds.
 template <int N>
-__device__ __forceinline__ void sort_pairs(int64_t (&col)[N], double (&val)[N], int cnt) {
-  for (int a = 1; a < cnt; ++a) {
-    const int64_t kc = col[a];
-    const double kv = val[a];
-    int b = a - 1;
-    while (b >= 0 && col[b] > kc) {
-      col[b + 1] = col[b];
-      val[b + 1] = val[b];
-      --b;
+__device__ __forceinline__ void sort_pairs(int64_t (&col)[N], double (&val)[N]) {
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+#pragma unroll
+    for (int a = r & 1; a + 1 < N; a += 2) {
+      const bool sw = col[a] > col[a + 1];
+      const int64_t c0 = sw ? col[a + 1] : col[a], c1 = sw ? col[a] : col[a + 1];
+      const double v0 = sw ? val[a + 1] : val[a], v1 = sw ? val[a] : val[a + 1];
+      col[a] = c0, col[a + 1] = c1, val[a] = v0, val[a + 1] = v1;
     }
-    col[b + 1] = kc;
-    val[b + 1] = kv;
   }
 }
 
-__global__ void k_laplacian(GridDev g, double scale, int32_t* __restrict__ rp, int32_t* __restrict__ ci,
-                            double* __restrict__ va, int64_t n, int64_t nnz) {
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id == 0) rp[n] = (int32_t)nnz;
-  if (id >= n) return;
-  const int i = (int)(id % g.n[0]);
-  const int j = (int)((id / g.n[0]) % g.n[1]);
-  const int k = (int)(id / ((int64_t)g.n[0] * g.n[1]));
-  const int c[3] = {i, j, k};
-  const int64_t start = 7 * id - walls_before(g, i, j, k);
+// cell coordinates of row id (n < 2^31: 32-bit division)
+__device__ __forceinline__ void cell_of(const GridDev& g, int64_t id, int (&c)[3]) {
+  const unsigned u = (unsigned)id, nx = (unsigned)g.n[0], ny = (unsigned)g.n[1];
+  const unsigned q = u / nx;
+  c[0] = (int)(u - q * nx);
+  c[1] = (int)(q % ny);
+  c[2] = (int)(q / ny);
+}
+
+// The row writers store the row's entries at ci[start - obase ..], va[start - obase ..]: the
+// global arrays (obase 0) or a block's staging buffer in shared memory (obase = the first
+// entry of the block's rows).
+template <class Geom>
+__device__ __forceinline__ void laplacian_row(const GridDev& g, const Geom& G, double scale, int32_t* __restrict__ rp,
+                                              int32_t* __restrict__ ci, double* __restrict__ va, int64_t id,
+                                              int64_t obase = 0) {
+  int c[3];
+  cell_of(g, id, c);
+  const int64_t start = 7 * id - walls_before(g, c[0], c[1], c[2]);
   int64_t col[7];
   double val[7];
-  int cnt = 0;
+  int cnt = 1;
   double diag = 0.0;
   const int64_t stride[3] = {1, g.n[0], (int64_t)g.n[0] * g.n[1]};
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double A = face_area(g, d, c);
+    const double A = face_area(G, d, c);
     const int t = c[d];
-    // minus neighbour across the face at position t
-    if (g.per[d] || t > 0) {
-      const int tn = (t == 0) ? g.n[d] - 1 : t - 1;
-      const double cf = A / centre_dist(g, d, t);
-      col[cnt] = id + (int64_t)(tn - t) * stride[d];
-      val[cnt++] = cf;
-      diag += cf;
-    }
-    // plus neighbour across the face at position t + 1
-    if (g.per[d] || t < g.n[d] - 1) {
-      const int tp = (t == g.n[d] - 1) ? 0 : t + 1;
-      const double cf = A / centre_dist(g, d, tp);
-      col[cnt] = id + (int64_t)(tp - t) * stride[d];
-      val[cnt++] = cf;
-      diag += cf;
-    }
+    // minus neighbour across the face at position t (slot 2d), plus neighbour across the face
+    // at position t + 1 (slot 2d + 1); a wall leaves its slot absent
+    const bool has_m = g.per[d] || t > 0, has_p = g.per[d] || t < g.n[d] - 1;
+    const int tn = (t == 0) ? g.n[d] - 1 : t - 1;
+    const int tp = (t == g.n[d] - 1) ? 0 : t + 1;
+    const double cm = has_m ? A * G.icd(d, t) : 0.0;
+    const double cp = has_p ? A * G.icd(d, tp) : 0.0;
+    col[2 * d] = has_m ? id + (int64_t)(tn - t) * stride[d] : INT64_MAX;
+    val[2 * d] = cm;
+    col[2 * d + 1] = has_p ? id + (int64_t)(tp - t) * stride[d] : INT64_MAX;
+    val[2 * d + 1] = cp;
+    diag += cm;
+    diag += cp;
+    cnt += (int)has_m + (int)has_p;
   }
-  col[cnt] = id;
-  val[cnt++] = -diag;
-  sort_pairs<7>(col, val, cnt);
+  col[6] = id;
+  val[6] = -diag;
+  sort_pairs<7>(col, val);
   rp[id] = (int32_t)start;
-  for (int e = 0; e < cnt; ++e) {
-    ci[start + e] = (int32_t)col[e];
-    va[start + e] = scale * val[e];
-  }
+#pragma unroll
+  for (int e = 0; e < 7; ++e)
+    if (e < cnt) {
+      ci[start - obase + e] = (int32_t)col[e];
+      va[start - obase + e] = val[e];  // the scale is in G.icd
+    }
 }
 
-__global__ void k_divergence(GridDev g, double scale, int32_t* __restrict__ rp, int32_t* __restrict__ ci,
-                             double* __restrict__ va, int64_t n, int64_t nnz) {
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id == 0) rp[n] = (int32_t)nnz;
-  if (id >= n) return;
-  const int i = (int)(id % g.n[0]);
-  const int j = (int)((id / g.n[0]) % g.n[1]);
-  const int k = (int)(id / ((int64_t)g.n[0] * g.n[1]));
-  const int c[3] = {i, j, k};
-  const int64_t start = 6 * id - walls_before(g, i, j, k);
+template <class Geom>
+__device__ __forceinline__ void divergence_row(const GridDev& g, const Geom& G, double scale, int32_t* __restrict__ rp,
+                                               int32_t* __restrict__ ci, double* __restrict__ va, int64_t id,
+                                               int64_t obase = 0) {
+  int c[3];
+  cell_of(g, id, c);
+  const int64_t start = 6 * id - walls_before(g, c[0], c[1], c[2]);
   int64_t col[6];
   double val[6];
   int cnt = 0;
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double A = face_area(g, d, c);
+    const double A = face_area(G, d, c);
     const int t = c[d];
-    if (g.per[d] || t > 0) {  // minus face: this cell lies above it
-      col[cnt] = face_index(g, d, c, t);
-      val[cnt++] = -A;
-    }
-    if (g.per[d] || t < g.n[d] - 1) {  // plus face: this cell lies below it
-      const int tp = (t == g.n[d] - 1) ? 0 : t + 1;
-      col[cnt] = face_index(g, d, c, tp);
-      val[cnt++] = A;
-    }
+    // minus face (this cell lies above it) in slot 2d, plus face (below it) in slot 2d + 1
+    const bool has_m = g.per[d] || t > 0, has_p = g.per[d] || t < g.n[d] - 1;
+    const int tp = (t == g.n[d] - 1) ? 0 : t + 1;
+    col[2 * d] = has_m ? face_index(g, d, c, t) : INT64_MAX;
+    val[2 * d] = -A;
+    col[2 * d + 1] = has_p ? face_index(g, d, c, tp) : INT64_MAX;
+    val[2 * d + 1] = A;
+    cnt += (int)has_m + (int)has_p;
   }
-  sort_pairs<6>(col, val, cnt);
+  sort_pairs<6>(col, val);
   rp[id] = (int32_t)start;
-  for (int e = 0; e < cnt; ++e) {
-    ci[start + e] = (int32_t)col[e];
-    va[start + e] = scale * val[e];
-  }
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+    if (e < cnt) {
+      ci[start - obase + e] = (int32_t)col[e];
+      va[start - obase + e] = scale * val[e];
+    }
 }
 
-__global__ void k_gradient(GridDev g, double scale, int32_t* __restrict__ rp, int32_t* __restrict__ ci,
-                           double* __restrict__ va, int64_t nf) {
-  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f == 0) rp[nf] = (int32_t)(2 * nf);
-  if (f >= nf) return;
-  int dir = 0;
-  int64_t local = f;
-  for (; dir < 2; ++dir) {
-    const int64_t cnt = (int64_t)face_dim(g, dir, 0) * face_dim(g, dir, 1) * face_dim(g, dir, 2);
-    if (local < cnt) break;
-    local -= cnt;
-  }
-  const int fx = face_dim(g, dir, 0), fy = face_dim(g, dir, 1);
+// the face's two cells for a compile-time direction (every index a constant: no local arrays)
+template <int DIR, class Geom>
+__device__ __forceinline__ void gradient_face(const GridDev& g, const Geom& G, double scale, int32_t* __restrict__ rp,
+                                              int32_t* __restrict__ ci, double* __restrict__ va, int64_t f,
+                                              int64_t local) {
+  const unsigned fx = (unsigned)face_dim(g, DIR, 0), fy = (unsigned)face_dim(g, DIR, 1);
+  const unsigned u = (unsigned)local, q = u / fx;
   int c[3];
-  c[0] = (int)(local % fx);
-  c[1] = (int)((local / fx) % fy);
-  c[2] = (int)(local / ((int64_t)fx * fy));
-  const int p = g.per[dir] ? c[dir] : c[dir] + 1;  // face position along dir
-  const int lo = (p == 0) ? g.n[dir] - 1 : p - 1;
-  int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
-  cm[dir] = lo;
-  cp[dir] = p;
-  const int64_t idm = cm[0] + (int64_t)g.n[0] * (cm[1] + (int64_t)g.n[1] * cm[2]);
-  const int64_t idp = cp[0] + (int64_t)g.n[0] * (cp[1] + (int64_t)g.n[1] * cp[2]);
-  const double inv = 1.0 / centre_dist(g, dir, p);
+  c[0] = (int)(u - q * fx);
+  c[1] = (int)(q % fy);
+  c[2] = (int)(q / fy);
+  const int p = g.per[DIR] ? c[DIR] : c[DIR] + 1;  // face position along DIR
+  const int lo = (p == 0) ? g.n[DIR] - 1 : p - 1;
+  const int64_t sx = 1, sy = g.n[0], sz = (int64_t)g.n[0] * g.n[1];
+  const int64_t base = c[0] * sx + c[1] * sy + c[2] * sz - (int64_t)c[DIR] * (DIR == 0 ? sx : DIR == 1 ? sy : sz);
+  const int64_t sd = DIR == 0 ? sx : DIR == 1 ? sy : sz;
+  const int64_t idm = base + lo * sd, idp = base + p * sd;
+  const double inv = G.icd(DIR, p);  // scale / d_f
   const int64_t s = 2 * f;
   rp[f] = (int32_t)s;
   if (idm < idp) {
-    ci[s] = (int32_t)idm, va[s] = -scale * inv;
-    ci[s + 1] = (int32_t)idp, va[s + 1] = scale * inv;
+    ci[s] = (int32_t)idm, va[s] = -inv;
+    ci[s + 1] = (int32_t)idp, va[s + 1] = inv;
   } else {
-    ci[s] = (int32_t)idp, va[s] = scale * inv;
-    ci[s + 1] = (int32_t)idm, va[s + 1] = -scale * inv;
+    ci[s] = (int32_t)idp, va[s] = inv;
+    ci[s + 1] = (int32_t)idm, va[s + 1] = -inv;
+  }
+}
+
+template <class Geom>
+__device__ __forceinline__ void gradient_row(const GridDev& g, const Geom& G, double scale, int32_t* __restrict__ rp,
+                                             int32_t* __restrict__ ci, double* __restrict__ va, int64_t f) {
+  const int64_t n0 = (int64_t)face_dim(g, 0, 0) * face_dim(g, 0, 1) * face_dim(g, 0, 2);
+  const int64_t n1 = (int64_t)face_dim(g, 1, 0) * face_dim(g, 1, 1) * face_dim(g, 1, 2);
+  if (f < n0) gradient_face<0>(g, G, scale, rp, ci, va, f, f);
+  else if (f < n0 + n1) gradient_face<1>(g, G, scale, rp, ci, va, f, f - n0);
+  else gradient_face<2>(g, G, scale, rp, ci, va, f, f - n0 - n1);
+}
+
+enum FvmKernelKind { FK_LAP = 0, FK_DIV = 1, FK_GRAD = 2 };
+
+constexpr int kFvmThreads = 256;
+
+// first CSR entry of row r < rows of the Laplacian (7 per cell) or the divergence (6 per cell)
+template <int KIND>
+__device__ __forceinline__ int64_t row_start(const GridDev& g, int64_t r) {
+  constexpr int per = KIND == FK_LAP ? 7 : 6;
+  int c[3];
+  cell_of(g, r, c);
+  return per * r - walls_before(g, c[0], c[1], c[2]);
+}
+
+// One thread per row, grid-stride over tiles of 256 rows.  With TAB the block first builds
+// the axis tables; for the Laplacian and the divergence it also stages each tile's entries
+// (one contiguous range of the CSR arrays) in shared memory and writes them out coalesced,
+// instead of each thread storing its row's 6-7 entries with a stride across the warp.
+template <int KIND, bool TAB>
+__global__ void __launch_bounds__(kFvmThreads) k_fvm(GridDev g, double scale, int32_t* __restrict__ rp,
+                                                     int32_t* __restrict__ ci, double* __restrict__ va, int64_t rows,
+                                                     int64_t nnz) {
+  extern __shared__ double geom_smem[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) rp[rows] = (int32_t)nnz;
+  constexpr bool kStage = TAB && KIND != FK_GRAD;
+  constexpr int kPer = KIND == FK_LAP ? 7 : 6;
+  auto body = [&](const auto& G, double* s_va, int32_t* s_ci) {
+    for (int64_t r0 = (int64_t)blockIdx.x * kFvmThreads; r0 < rows; r0 += (int64_t)gridDim.x * kFvmThreads) {
+      const int64_t id = r0 + threadIdx.x;
+      if constexpr (kStage) {
+        const int64_t base = row_start<KIND>(g, r0);
+        const int64_t end = r0 + kFvmThreads >= rows ? nnz : row_start<KIND>(g, r0 + kFvmThreads);
+        if (id < rows) {
+          if constexpr (KIND == FK_LAP) laplacian_row(g, G, scale, rp, s_ci, s_va, id, base);
+          else divergence_row(g, G, scale, rp, s_ci, s_va, id, base);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < (int)(end - base); e += kFvmThreads) {
+          ci[base + e] = s_ci[e];
+          va[base + e] = s_va[e];
+        }
+        __syncthreads();
+      } else if (id < rows) {
+        if constexpr (KIND == FK_LAP) laplacian_row(g, G, scale, rp, ci, va, id);
+        else if constexpr (KIND == FK_DIV) divergence_row(g, G, scale, rp, ci, va, id);
+        else gradient_row(g, G, scale, rp, ci, va, id);
+      }
+    }
+  };
+  // L and G take the scale into their reciprocal distances; M multiplies its areas by it
+  const double icd_scale = KIND == FK_DIV ? 1.0 : scale;
+  if constexpr (TAB) {
+    const GeomTab G = build_geom_tab(g, geom_smem, icd_scale);
+    double* s_va = geom_smem + 2 * (g.n[0] + g.n[1] + g.n[2]);
+    int32_t* s_ci = reinterpret_cast<int32_t*>(s_va + kPer * kFvmThreads);
+    body(G, s_va, s_ci);
+  } else {
+    GeomDirect G{&g, icd_scale};
+    body(G, nullptr, nullptr);
   }
 }
 
@@ -300,6 +418,27 @@ void sizes(const GridDev& g, int64_t& n, int64_t& nf, int64_t& walls) {
   }
 }
 
+// Tables in shared memory when the three axes fit (2 (nx + ny + nz) doubles within 48 KB),
+// then a grid of a few resident waves, each block building its tables once; else the direct
+// form, one block per 256 rows.
+template <int KIND>
+rb_status launch_fvm(const GridDev& g, double scale, int32_t* rp, int32_t* ci, double* va, int64_t rows, int64_t nnz,
+                     cudaStream_t s) {
+  const int bs = kFvmThreads;
+  const int64_t blocks = (rows + bs - 1) / bs;
+  const size_t stage = KIND == FK_GRAD ? 0 : (size_t)(KIND == FK_LAP ? 7 : 6) * bs * (8 + 4);
+  const size_t smem = geom_tab_bytes(g) + stage;
+  if (smem <= kGeomTabMax) {
+    auto* kern = &k_fvm<KIND, true>;
+    const int grid = wave_grid(kern, blocks, smem, bs);
+    kern<<<grid, bs, smem, s>>>(g, scale, rp, ci, va, rows, nnz);
+  } else {
+    k_fvm<KIND, false><<<(unsigned)std::max<int64_t>(1, blocks), bs, 0, s>>>(g, scale, rp, ci, va, rows, nnz);
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
 }  // namespace
 }  // namespace rb
 
@@ -332,21 +471,12 @@ extern "C" rb_status rb_fvm_assemble(const rb_grid_desc* grid, rb_fvm_kind kind,
   int64_t n, nf, walls;
   sizes(g, n, nf, walls);
   cudaStream_t s = S(stream);
-  const int bs = 256;
   switch (kind) {
-    case RB_FVM_LAPLACIAN:
-      k_laplacian<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(g, scale, row_ptr, col_idx, vals, n, 7 * n - walls);
-      break;
-    case RB_FVM_DIVERGENCE:
-      k_divergence<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(g, scale, row_ptr, col_idx, vals, n, 6 * n - walls);
-      break;
-    case RB_FVM_GRADIENT:
-      k_gradient<<<(unsigned)((nf + bs - 1) / bs), bs, 0, s>>>(g, scale, row_ptr, col_idx, vals, nf);
-      break;
+    case RB_FVM_LAPLACIAN: return launch_fvm<FK_LAP>(g, scale, row_ptr, col_idx, vals, n, 7 * n - walls, s);
+    case RB_FVM_DIVERGENCE: return launch_fvm<FK_DIV>(g, scale, row_ptr, col_idx, vals, n, 6 * n - walls, s);
+    case RB_FVM_GRADIENT: return launch_fvm<FK_GRAD>(g, scale, row_ptr, col_idx, vals, nf, 2 * nf, s);
     default: set_error("rb_fvm_assemble: unknown kind %d", (int)kind); return RB_EINVAL;
   }
-  RB_CUDA(cudaGetLastError());
-  return RB_OK;
 }
 
 extern "C" rb_status rb_mesh_cot_laplacian(int32_t n_vert, const double* points, int32_t n_tri,
