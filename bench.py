@@ -478,17 +478,34 @@ def extruded_bench(torch, rb, dev, hbm):
 
 def e2e(args, torch, step_items, stream, dev, flops_step):
     """The same step through the public API from pinned host buffers: H2D of every input,
-    the six SpMMs, D2H of every result, all inside the timed region."""
+    the six SpMMs, D2H of every result, all inside the timed region.  Uploads, SpMMs and
+    downloads run on three streams ordered by events, so that the download of one result
+    overlaps the uploads of the next inputs (the host link is full duplex)."""
     hx = [torch.empty(X.shape, dtype=X.dtype, pin_memory=True).copy_(X.cpu()) for (_, _, X, _, _, _) in step_items]
     hy = [torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True) for (_, _, _, Y, _, _) in step_items]
     h2d = sum(t.numel() * t.element_size() for t in hx)
     d2h = sum(t.numel() * t.element_size() for t in hy)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
     def one():
-        for (_, op, X, Y, _, _), a, b in zip(step_items, hx, hy):
-            X.copy_(a, non_blocking=True)
-            op.spmm(X, Y)
-            b.copy_(Y, non_blocking=True)
+        done_in, done_op = [], []
+        with torch.cuda.stream(s_in):
+            for (_, op, X, Y, _, _), a in zip(step_items, hx):
+                s_in.wait_stream(stream)  # X's previous readers (last step's SpMM) are done
+                X.copy_(a, non_blocking=True)
+                done_in.append(torch.cuda.Event())
+                done_in[-1].record(s_in)
+        for (_, op, X, Y, _, _), ev in zip(step_items, done_in):
+            stream.wait_event(ev)
+            stream.wait_stream(s_out)  # Y's previous download is done
+            op.spmm(X, Y, stream=stream)
+            done_op.append(torch.cuda.Event())
+            done_op[-1].record(stream)
+        with torch.cuda.stream(s_out):
+            for (_, op, X, Y, _, _), b, ev in zip(step_items, hy, done_op):
+                s_out.wait_event(ev)
+                b.copy_(Y, non_blocking=True)
+        s_out.synchronize()
         stream.synchronize()
 
     for _ in range(2):
