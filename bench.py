@@ -387,7 +387,7 @@ def batch_bench(torch, rb, dev):
         A32 = rb.Operator(rp, ci, va, nc, dtype="f32", k_max=k)
         B = torch.as_tensor(W.zero_mean(W.normal((g.n_cells, k), W.seed_for(4, k, salt=len(systems)))), device=dev)
         systems.append((g, k, A64, A32, B))
-    prm = rb.cg_params(rtol=1e-10, mixed=2, project_mean=True, max_sweeps=8)
+    prm = rb.cg_params(rtol=1e-10, mixed=2, project_mean=True, max_sweeps=16)
     batch = rb.Batch([s[2] for s in systems], [s[3] for s in systems], [s[1] for s in systems], prm)
     Bs = [s[4] for s in systems]
     Xs = [torch.zeros_like(b) for b in Bs]

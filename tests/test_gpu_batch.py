@@ -89,6 +89,30 @@ def test_batch_equals_single_solves(rb):
         assert all(abs(a - b) <= max(3, b // 20) for a, b in zip(r.iters, r1.iters)), (r.iters, r1.iters)
 
 
+def test_batch_bench_configuration(rb):
+    """The bench's batch at full size in its launch configuration (64^3 k = 8, 128^3 k = 1,
+    three 96 x 64 x 48 channels k = 3, same seeds, one persistent launch per sweep under the
+    recorded graph): every column reaches the true 1e-10 residual, recomputed on the CPU with
+    the oracle's operators (a property that holds at any size)."""
+    systems, As, Bs = [], [], []
+    for i, (g, k) in enumerate(zip(W.batch_grids(), W.BATCH_K_DEFAULT)):
+        A = (-fvm.laplacian(g)).tocsr()
+        B = W.zero_mean(W.normal((g.n_cells, k), W.seed_for(4, k, salt=i)))
+        As.append(A)
+        Bs.append(B)
+        systems.append((rb.Operator.from_scipy(A, k_max=k), rb.Operator.from_scipy(A, dtype="f32", k_max=k), k))
+    prm = rb.cg_params(rtol=1e-10, mixed=2, project_mean=True, max_sweeps=16)
+    batch = rb.Batch([s[0] for s in systems], [s[1] for s in systems], [s[2] for s in systems], prm)
+    Bd = [to_dev(B) for B in Bs]
+    Xd = [torch.zeros_like(b) for b in Bd]
+    res = batch.solve(Bd, Xd)
+    for A, B, X, r in zip(As, Bs, Xd, res):
+        assert r.status == rb.RB_OK, r
+        tr = _true_res(A, B, X.cpu().numpy())
+        assert np.all(tr <= 1e-10), tr
+        assert np.allclose(r.true_rel_res, tr, rtol=1e-3, atol=1e-14)
+
+
 def test_batch_at_the_column_limit(rb):
     """64 columns in total (the limit) over systems with 32, 24 and 8 columns: the persistent
     kernel's partial slots for every batch column and its wide-block reductions."""

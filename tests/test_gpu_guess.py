@@ -197,3 +197,32 @@ def test_select_smoothing_matches_a_restatement(rb):
     want = int(ref[1] < ref[0])
     assert choice.item() == want
     assert np.allclose(x0.cpu().numpy(), xs[want], rtol=1e-12, atol=1e-12)
+
+
+def test_full_size_shift_equivariance_and_zero_network(rb):
+    """The 128^3 network of the bench (channels 8, 16, 32, 48; periodic x, y, walls in z), in
+    the bench's launch configuration, checked through properties that hold at any size: a
+    periodic shift of the inputs by 8 cells in x (a multiple of the three poolings) shifts the
+    prediction by 8 cells (up to the rounding of the global input and output scalings), and
+    the zero network returns the previous pressure."""
+    from paper_2508_06710_gb300 import guess_pipeline as gp
+
+    grid = W.rbc_grid(W.GUESS_N, 1.4)
+    net = gp.network(grid)
+    net.init_params(torch.as_tensor(W.normal(net.n_params, 1800).astype(np.float32), device="cuda"), head_scale=1.0)
+    n = net.n
+    N = W.GUESS_N
+    b, p1, p2 = (torch.as_tensor(W.normal(n, 1801 + i), device="cuda") for i in range(3))
+    out = net.predict(b, p1, p2).clone()
+
+    def roll(v):
+        return torch.roll(v.view(N, N, N), shifts=8, dims=2).reshape(-1).contiguous()
+
+    out_s = net.predict(roll(b), roll(p1), roll(p2))
+    contribution = (out - (p1 - p1.mean())).norm()
+    assert float((out_s - roll(out)).norm()) <= 1e-3 * float(contribution)
+    assert float(contribution) > 1e-3 * float(p1.norm())  # the network does contribute
+    net.set_params(torch.zeros(net.n_params, dtype=torch.float32, device="cuda"))
+    out0 = net.predict(b, p1, p2)
+    assert torch.allclose(out0, p1 - p1.mean(), rtol=0, atol=1e-12 * float(p1.abs().max()))
+
