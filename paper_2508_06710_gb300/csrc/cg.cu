@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_q(CsrArgs<T> a, CgCtl ctl, CgSc
     T acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = T(0);
-    row_accumulate_direct<T, VEC, LPR>(a, row, chunk, sub, active, acc);
+    row_accumulate_direct<T, VEC, LPR, false, true>(a, row, chunk, sub, active, acc);
     if (active && sub == 0) {
       const Vec<T, VEC> p = ldv<T, VEC>(a.X + row * a.ldx + chunk * VEC);
       Vec<T, VEC> q;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_q2(CsrArgs<T> a, CgCtl ctl, con
     T acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = T(0);
-    row_accumulate_direct<T, VEC, LPR>(a, row, chunk, sub, active, acc);
+    row_accumulate_direct<T, VEC, LPR, false, true>(a, row, chunk, sub, active, acc);
     if (active && sub == 0) {
       const Vec<T, VEC> p = ldv<T, VEC>(a.X + row * a.ldx + chunk * VEC);
       const T d = dinv ? dinv[row] : T(1);

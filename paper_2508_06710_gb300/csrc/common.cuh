@@ -176,6 +176,45 @@ __device__ __forceinline__ Vec<T, VEC> ldv_cg(const T* p) {
   return r;
 }
 
+// An L2 eviction policy that keeps lines longer (evict_last), for data re-read across a
+// kernel (the SpMM's gathered X) while the matrix and the outputs stream past.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ double ld_keep(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_keep(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// ldv with the evict_last L2 policy (read-only data)
+template <typename T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> ldv_keep(const T* p, uint64_t pol) {
+  Vec<T, VEC> r;
+  if constexpr (sizeof(T) == 8 && VEC == 2) {
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p), "l"(pol));
+  } else if constexpr (sizeof(T) == 4 && VEC == 4) {
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(p), "l"(pol));
+  } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(r.v[0]), "=f"(r.v[1]) : "l"(p), "l"(pol));
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) r.v[e] = ld_keep(p + e, pol);
+  }
+  return r;
+}
+
 template <typename T, int VEC>
 __device__ __forceinline__ void stv(T* p, const Vec<T, VEC>& r) {
   if constexpr (sizeof(T) * VEC == 16) {

@@ -154,7 +154,7 @@ __device__ __forceinline__ void extruded_epilogue(const CsrArgs<T>& a, int64_t r
 // index and value loads are issued by all KP * LPR lanes of the row and served as one
 // broadcast.  Must be called by every lane of the warp when LPR > 1.
 // COHERENT: gather X through L2 only (X written by other blocks of the same launch).
-template <typename T, int VEC, int LPR, bool COHERENT = false>
+template <typename T, int VEC, int LPR, bool COHERENT = false, bool KEEP = false>
 __device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64_t row, int chunk, int sub,
                                                       bool active, T (&acc)[VEC]) {
   int rs = 0, re = 0;
@@ -169,11 +169,19 @@ __device__ __forceinline__ void row_accumulate_direct(const CsrArgs<T>& a, int64
   // their latency (L f32 k = 3 40.7 -> 39.7 us, M f32 k = 1 35.0 -> 33.3 us); with 16-byte
   // gathers (VEC = 4) four deep was slower (k = 4 and 8, the extruded k = 64).
   constexpr int kUnroll = (sizeof(T) == 4 && VEC < 4) ? 4 : 2;
+  // KEEP (the CG's q = A p): the gathered p lines get the evict_last L2 policy, so that the
+  // next kernel of the iteration, which reads p again, finds them in L2 (the plain SpMM, whose
+  // X is not read again, runs faster without it)
+  uint64_t keep = 0;
+  if constexpr (KEEP) keep = l2_keep_policy();
 #pragma unroll kUnroll
   for (int p = rs + sub; p < re; p += LPR) {
     const int c = __ldg(a.ci + p);
     const T v = __ldg(a.va + p);
-    const Vec<T, VEC> x = COHERENT ? ldv_cg<T, VEC>(Xc + (int64_t)c * a.ldx) : ldv<T, VEC>(Xc + (int64_t)c * a.ldx);
+    Vec<T, VEC> x;
+    if constexpr (COHERENT) x = ldv_cg<T, VEC>(Xc + (int64_t)c * a.ldx);
+    else if constexpr (KEEP) x = ldv_keep<T, VEC>(Xc + (int64_t)c * a.ldx, keep);
+    else x = ldv<T, VEC>(Xc + (int64_t)c * a.ldx);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = fma(v, x.v[e], acc[e]);
   }
