@@ -1957,7 +1957,7 @@ extern "C" rb_status rb_batch_tune(rb_batch_t bt, const double* const* B, const 
   RB_REQUIRE(bt && B && ldb && X && ldx, "rb_batch_tune: null argument");
   cudaStream_t s = S(stream);
   const int cap = pcg_blocks_per_sm();
-  const double rtols[] = {1e-1, 3e-2, 1e-2};
+  const double rtols[] = {1e-1, 5e-2, 3e-2, 1e-2};
   double best = 1e30;
   int best_bps = 0;
   double best_rtol = bt->prm.inner_rtol;
