@@ -1331,11 +1331,29 @@ __global__ void k_bf16_to_f32(const bf16* __restrict__ a, int lda, int n, int c,
 }
 
 // guess selection: r = b - A c for two candidates (A c already in ac0 / ac1), sums of r^2, b^2
-__global__ void k_resid2(const double* __restrict__ b, const double* __restrict__ ac0, const double* __restrict__ ac1,
-                         int n, double* part) {
+// The judge's two candidates are kept interleaved, [n][2] (cell i: candidate 0 then 1), so that
+// each smoothing sweep applies A to both in one k = 2 SpMM (the matrix read once for the two).
+__global__ void k_pack2(const double* __restrict__ c0, const double* __restrict__ c1, int n, double* __restrict__ xs) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    xs[2 * i] = c0[i];
+    xs[2 * i + 1] = c1[i];
+  }
+}
+
+// damped Jacobi on both candidates: x += omega D^-1 (b - A x)
+__global__ void k_jacobi2(const double* __restrict__ b, const double* __restrict__ ax, const double* __restrict__ dinv,
+                          double omega, int n, double* __restrict__ xs) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double w = omega * dinv[i];
+    xs[2 * i] += w * (b[i] - ax[2 * i]);
+    xs[2 * i + 1] += w * (b[i] - ax[2 * i + 1]);
+  }
+}
+
+__global__ void k_resid2(const double* __restrict__ b, const double* __restrict__ ax, int n, double* part) {
   double v[3] = {0.0, 0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double bi = b[i], r0 = bi - ac0[i], r1 = bi - ac1[i];
+    const double bi = b[i], r0 = bi - ax[2 * i], r1 = bi - ax[2 * i + 1];
     v[0] += r0 * r0;
     v[1] += r1 * r1;
     v[2] += bi * bi;
@@ -1343,9 +1361,8 @@ __global__ void k_resid2(const double* __restrict__ b, const double* __restrict_
   block_sum_store<3>(v, part);
 }
 
-__global__ void k_pick(const double* __restrict__ c0, const double* __restrict__ c1, int n,
-                       const double* __restrict__ sums, double* __restrict__ res, int* __restrict__ choice,
-                       double* __restrict__ x0) {
+__global__ void k_pick(const double* __restrict__ xs, int n, const double* __restrict__ sums, double* __restrict__ res,
+                       int* __restrict__ choice, double* __restrict__ x0) {
   const double bb = sums[2] > 0.0 ? sums[2] : 1.0;
   const int pick = sums[1] < sums[0] ? 1 : 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1353,8 +1370,7 @@ __global__ void k_pick(const double* __restrict__ c0, const double* __restrict__
     res[1] = sqrt(sums[1] / bb);
     *choice = pick;
   }
-  const double* src = pick ? c1 : c0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x0[i] = src[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x0[i] = xs[2 * i + pick];
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -2241,15 +2257,6 @@ extern "C" rb_status rb_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int
                              rb_stream_t stream);
 
 // damped Jacobi sweep on two vectors: x_i += omega dinv (b - (A x)_i)
-__global__ void k_jacobi2(const double* __restrict__ b, const double* __restrict__ ax, const double* __restrict__ dinv,
-                          double omega, int n, double* __restrict__ x) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double w = omega * dinv[i];
-    x[i] += w * (b[i] - ax[i]);
-    x[n + i] += w * (b[i] - ax[n + i]);
-  }
-}
-
 extern "C" rb_status rb_guess_select(rb_guess_t g, rb_op_t A, const double* b, const double* cand0,
                                      const double* cand1, int32_t sweeps, double omega, double* x0, double* res,
                                      int32_t* choice, rb_stream_t stream) {
@@ -2261,21 +2268,20 @@ extern "C" rb_status rb_guess_select(rb_guess_t g, rb_op_t A, const double* b, c
   RB_REQUIRE(sweeps >= 0 && sweeps <= 1000, "rb_guess_select: sweeps = %d outside [0, 1000]", sweeps);
   RB_REQUIRE(sweeps == 0 || (A->has_diag && A->dinv64), "rb_guess_select: smoothing needs A's diagonal");
   cudaStream_t s = S(stream);
-  double* ax = g->sel;             // [2][n]: A x_0, A x_1
-  double* xs = g->sel + 2 * (size_t)n0;  // [2][n]: the (smoothed) candidates
-  RB_CUDA(cudaMemcpyAsync(xs, cand0, (size_t)n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  RB_CUDA(cudaMemcpyAsync(xs + n0, cand1, (size_t)n0 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double* ax = g->sel;                   // [n][2]: A x_0, A x_1, interleaved
+  double* xs = g->sel + 2 * (size_t)n0;  // [n][2]: the (smoothed) candidates, interleaved
+  k_pack2<<<grid_for(n0), 256, 0, s>>>(cand0, cand1, n0, xs);
+  RB_CUDA(cudaGetLastError());
   for (int it = 0; it <= sweeps; ++it) {
-    RB_TRY(rb_spmm(A, xs, 1, ax, 1, 1, nullptr, stream));
-    RB_TRY(rb_spmm(A, xs + n0, 1, ax + n0, 1, 1, nullptr, stream));
+    RB_TRY(rb_spmm(A, xs, 2, ax, 2, 2, nullptr, stream));  // both candidates, one pass over A
     if (it < sweeps) {
       k_jacobi2<<<grid_for(n0), 256, 0, s>>>(b, ax, A->dinv64, omega, n0, xs);
       RB_CUDA(cudaGetLastError());
     }
   }
-  k_resid2<<<kRedGrid, kRedThreads, 0, s>>>(b, ax, ax + n0, n0, g->red);
+  k_resid2<<<kRedGrid, kRedThreads, 0, s>>>(b, ax, n0, g->red);
   k_finish<<<3, 256, 0, s>>>(g->red, kRedGrid, 3, g->scal + 16, 1.0);
-  k_pick<<<grid_for(n0), 256, 0, s>>>(xs, xs + n0, n0, g->scal + 16, res, choice, x0);
+  k_pick<<<grid_for(n0), 256, 0, s>>>(xs, n0, g->scal + 16, res, choice, x0);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
