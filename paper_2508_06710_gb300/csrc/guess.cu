@@ -1695,10 +1695,28 @@ struct RowWPlan {
   int m_tiles = 0, splits = 0, per_split = 0, chunk = 0;
 };
 
+size_t wgrad_row_smem(int np, int cin, int W);
+
+// CTAs of the row weight-gradient kernel resident on the GPU at once (its registers, shared
+// memory and TMEM), for a launch of one wave
+int wgrad_row_resident(int np, int W, size_t smem) {
+  const void* k = nullptr;
+  switch (np) {
+    case 16: k = W == 128 ? (const void*)&k_wgrad_row<16, 128> : (const void*)&k_wgrad_row<16, 64>; break;
+    case 32: k = W == 128 ? (const void*)&k_wgrad_row<32, 128> : (const void*)&k_wgrad_row<32, 64>; break;
+    case 48: k = W == 128 ? (const void*)&k_wgrad_row<48, 128> : (const void*)&k_wgrad_row<48, 64>; break;
+    default: k = W == 128 ? (const void*)&k_wgrad_row<64, 128> : (const void*)&k_wgrad_row<64, 64>; break;
+  }
+  return blocks_per_sm(k, smem, kConvThreads, tmem_cols_for(np)) * guess_sm_count();
+}
+
+// m_tiles x splits CTAs, no more than are resident at once (one wave: a partial second wave
+// would cost a whole CTA's run), each taking per_split runs of `chunk` rows
 RowWPlan wgrad_row_plan(const Layer& ly, const Dims& d) {
   RowWPlan p;
   p.m_tiles = ly.mpad / 128;
-  const int target = std::max(1, (4 * guess_sm_count()) / p.m_tiles);
+  const int resident = wgrad_row_resident(ly.np, d.nx, wgrad_row_smem(ly.np, ly.cin_pad, d.nx));
+  const int target = std::max(1, resident / p.m_tiles);
   p.chunk = row_chunk(d.ny, d.nz, target);
   const int items = d.nz * ((d.ny + p.chunk - 1) / p.chunk);
   p.per_split = std::max(1, (items + target - 1) / target);
