@@ -133,8 +133,13 @@ __global__ void __launch_bounds__(kThreads) k_dot_flat(int64_t total, const T* _
   const int64_t stride = (int64_t)gridDim.x * kThreads;
   double acc[K];
   T facc[K];
+  // FP64: one accumulator per position of the unit (L independent FMA chains instead of K
+  // chains of L / K, for the FP64 pipe's latency), folded into the columns at the end
+  double pacc[sizeof(T) == 8 ? L : 1];
 #pragma unroll
   for (int j = 0; j < K; ++j) acc[j] = 0.0, facc[j] = T(0);
+#pragma unroll
+  for (int q = 0; q < (sizeof(T) == 8 ? L : 1); ++q) pacc[q] = 0.0;
   int pending = 0;
   for (int64_t u = tid; u < nunits; u += stride) {
 #pragma unroll
@@ -142,16 +147,29 @@ __global__ void __launch_bounds__(kThreads) k_dot_flat(int64_t total, const T* _
       const Vec<T, V> x = ldv<T, V>(X + u * L + i * V);
       const Vec<T, V> y = ldv<T, V>(Y + u * L + i * V);
 #pragma unroll
-      for (int e = 0; e < V; ++e) facc[(i * V + e) % K] = fma(x.v[e], y.v[e], facc[(i * V + e) % K]);
+      for (int e = 0; e < V; ++e) {
+        if constexpr (sizeof(T) == 8) pacc[i * V + e] = fma((double)x.v[e], (double)y.v[e], pacc[i * V + e]);
+        else facc[(i * V + e) % K] = fma(x.v[e], y.v[e], facc[(i * V + e) % K]);
+      }
     }
-    if (sizeof(T) == 8 || ++pending == 4) {
+    // FP32 products are summed four units at a time in FP32, the groups in FP64 (FP64
+    // products accumulate in place: a flush per unit would add a DADD per column and unit on
+    // the FP64 pipe, which bounds this kernel)
+    if constexpr (sizeof(T) == 4) {
+      if (++pending == 4) {
 #pragma unroll
-      for (int j = 0; j < K; ++j) acc[j] += (double)facc[j], facc[j] = T(0);
-      pending = 0;
+        for (int j = 0; j < K; ++j) acc[j] += (double)facc[j], facc[j] = T(0);
+        pending = 0;
+      }
     }
   }
+  if constexpr (sizeof(T) == 8) {
 #pragma unroll
-  for (int j = 0; j < K; ++j) acc[j] += (double)facc[j];
+    for (int q = 0; q < L; ++q) acc[q % K] += pacc[q];
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc[j] += (double)facc[j];
+  }
   // tail entries past the last whole unit: entry nunits L + tid is in column tid % K
   const int64_t f = nunits * L + tid;
   if (f < total) {
