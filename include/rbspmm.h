@@ -22,6 +22,10 @@
  *     whose size a *_workspace_bytes query returns.
  *   - Invalid arguments (null pointers, negative sizes, ld < k, k > RB_MAX_K, dtype
  *     mismatch) return RB_EINVAL before any work is queued.
+ *   - Host threads: calls on different handles may run concurrently from different
+ *     threads (the library's launch caches are per thread); calls on the same operator,
+ *     batch or guess handle must not overlap (rb_tune_spmm and the solvers update the
+ *     handle's state).
  */
 #ifndef RBSPMM_H
 #define RBSPMM_H

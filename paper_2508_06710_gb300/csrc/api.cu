@@ -26,7 +26,7 @@ void clear_error() { g_err.clear(); }
 int resident_blocks(const void* kernel, size_t smem, int threads) {
   static std::mutex mu;
   static std::map<std::pair<const void*, size_t>, int> cache;
-  static int sms = 0;
+  thread_local int sms = 0;
   std::lock_guard<std::mutex> lock(mu);
   auto key = std::make_pair(kernel, smem * 4096 + (size_t)threads);
   auto it = cache.find(key);

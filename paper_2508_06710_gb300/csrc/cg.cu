@@ -1468,7 +1468,7 @@ __global__ void __launch_bounds__(kPThreads) k_pcg_batch(PBatch b) {
 // ------------------------------------------------------------------ host side of the batch
 
 int sm_count() {
-  static int sms = 0;
+  thread_local int sms = 0;
   if (!sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
@@ -1479,7 +1479,7 @@ int sm_count() {
 
 // Resident blocks of k_pcg_batch per multiprocessor (the cooperative-launch limit).
 int pcg_blocks_per_sm() {
-  static int per_sm = 0;
+  thread_local int per_sm = 0;
   if (!per_sm) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, kPThreads, 0) != cudaSuccess ||
         per_sm < 1) {

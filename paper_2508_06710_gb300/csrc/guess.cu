@@ -1494,7 +1494,7 @@ void build_layers(const rb_guess_cfg& c, std::vector<Layer>& out, int64_t& n) {
 }
 
 int guess_sm_count() {
-  static int sms = 0;
+  thread_local int sms = 0;
   if (!sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1531,14 +1531,14 @@ size_t conv_smem(int np, int kpad) { return (size_t)np * kpad * 2 + (size_t)kSta
 template <int NP>
 rb_status launch_conv3_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
   auto* kern = &k_conv3_mma<NP>;
-  static size_t opted = 48 * 1024;  // largest dynamic shared memory requested so far
+  thread_local size_t opted = 48 * 1024;  // largest dynamic shared memory requested so far
   if (smem > opted) {
     RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     opted = smem;
   }
   const int n_tiles = (a.n_vox + 127) / 128;
-  static int per_sm = 0;
-  static size_t per_sm_smem = 0;
+  thread_local int per_sm = 0;
+  thread_local size_t per_sm_smem = 0;
   if (per_sm == 0 || per_sm_smem != smem) {
     per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kConvThreads, tmem_cols_for(2 * NP));
     per_sm_smem = smem;
@@ -1563,13 +1563,13 @@ int head_idx(const rb_guess* g) { return 2 * g->L + 3 * (g->L - 1); }
 template <int NP, int W>
 rb_status launch_row_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
   auto* kern = &k_conv3_row<NP, W>;
-  static size_t opted = 48 * 1024;
+  thread_local size_t opted = 48 * 1024;
   if (smem > opted) {
     RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     opted = smem;
   }
-  static int per_sm = 0;
-  static size_t per_sm_smem = 0;
+  thread_local int per_sm = 0;
+  thread_local size_t per_sm_smem = 0;
   if (per_sm == 0 || per_sm_smem != smem) {
     per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kConvThreads, tmem_cols_for(2 * NP));
     per_sm_smem = smem;
@@ -1681,7 +1681,7 @@ WgradPlan wgrad_plan(const Layer& ly, int n) {
 template <int NP>
 rb_status launch_wgrad_np(const WgradArgs& a, const WgradPlan& p, cudaStream_t s) {
   const size_t smem = (size_t)kStages * (kWAStage + NP * kWS * 2);
-  static bool opted = false;
+  thread_local bool opted = false;
   if (!opted && smem > 48 * 1024) {
     RB_CUDA(cudaFuncSetAttribute(&k_wgrad_mma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     opted = true;
@@ -1735,7 +1735,7 @@ bool wgrad_row_fits(const Layer& ly, const Dims& d) {
 template <int NP, int W>
 rb_status launch_wgrad_row_np(const WgradArgs& a, const RowWPlan& p, cudaStream_t s) {
   const size_t smem = wgrad_row_smem(NP, a.cin, W);
-  static size_t opted = 48 * 1024;
+  thread_local size_t opted = 48 * 1024;
   if (smem > opted) {
     RB_CUDA(cudaFuncSetAttribute(&k_wgrad_row<NP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     opted = smem;

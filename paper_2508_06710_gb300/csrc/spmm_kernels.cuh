@@ -88,7 +88,7 @@ rb_status launch_csr(const rb_op* op, const SpmmSched& sc, const T* X, int64_t l
       auto* kern = &k_spmm_tma<T, VEC, EPI>;
       const int cap = tma_capacity<T>(op, R, kTmaSmemLimit);
       const size_t smem = tma_layout<T>(R, cap).total;
-      static size_t opted = 0;  // largest dynamic shared memory requested so far (per instantiation)
+      thread_local size_t opted = 0;  // largest dynamic shared memory requested so far (per instantiation)
       if (smem > 48 * 1024 && smem > opted) {
         RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemLimit));
         opted = kTmaSmemLimit;
