@@ -998,11 +998,16 @@ __global__ void k_up(const bf16* __restrict__ in, int ldi, int cin, const bf16* 
     for (int ci = 0; ci < cin; ci += 8) {
       const uint4 q = *reinterpret_cast<const uint4*>(xin + ci);
       const bf16* h = reinterpret_cast<const bf16*>(&q);
+      float xv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float xv = __bfloat162float(h[u]);
+      for (int u = 0; u < 8; ++u) xv[u] = __bfloat162float(h[u]);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(sw[((gq * 8 + e) * 8 + o) * cin + ci + u]) * xv;
+      for (int e = 0; e < 8; ++e) {
+        // the 8 weights W[gq 8 + e][o][ci .. ci + 7]: one 16-byte shared-memory load
+        const uint4 wq = *reinterpret_cast<const uint4*>(sw + ((gq * 8 + e) * 8 + o) * cin + ci);
+        const bf16* wh = reinterpret_cast<const bf16*>(&wq);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[e] += __bfloat162float(wh[u]) * xv[u];
       }
     }
     uint4 q;
@@ -1036,7 +1041,9 @@ __global__ void k_up_dx(const bf16* __restrict__ gu, int ldg, int cout, const bf
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const float gv = __bfloat162float(h[u]);
-          const bf16* wr = sw + ((co + u) * 8 + o) * cin + gq * 8;
+          // W[co + u][o][gq 8 .. gq 8 + 7]: one 16-byte shared-memory load
+          const uint4 wq = *reinterpret_cast<const uint4*>(sw + ((co + u) * 8 + o) * cin + gq * 8);
+          const bf16* wr = reinterpret_cast<const bf16*>(&wq);
 #pragma unroll
           for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(wr[e]) * gv;
         }
