@@ -60,6 +60,13 @@ const char* rb_last_error(void);
 /* Library version, e.g. "0.1.0". */
 const char* rb_version(void);
 
+/* Measured FMA throughput of the current GPU in TFLOP/s (2 flops per FMA) for RB_F64 or
+ * RB_F32: eight independent FMA chains per thread on a full-occupancy grid, best of five
+ * launches timed with CUDA events.  The arithmetic roof against which the FP64 SpMM and CG
+ * kernels are measured (on GB300 they reach the FP64 rate before HBM bandwidth).
+ * Synchronises `stream`; allocates nothing; a measurement utility, not part of the method. */
+rb_status rb_fma_peak(rb_dtype dtype, double* tflops, rb_stream_t stream);
+
 /* ------------------------------------------------------------------------------------
  * Operator build: staggered symmetry-preserving FVM operators on Cartesian grids
  * (Sec. 3, semi-discrete equations (ns); Sec. 4, symmetry-preserving discretisation).

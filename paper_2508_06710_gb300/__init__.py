@@ -26,7 +26,7 @@ RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT = 0, 1, 2
 RB_MAX_K = 64
 
 # exported C symbols, in the order include/rbspmm.h declares them
-SYMBOLS = ["rb_last_error", "rb_version", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_mesh_cot_laplacian",
+SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_mesh_cot_laplacian",
            "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
@@ -102,6 +102,7 @@ def lib():
     sig = {
         "rb_last_error": (C.c_char_p, []),
         "rb_version": (C.c_char_p, []),
+        "rb_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_void_p]),
         "rb_fvm_csr_size": (C.c_int, [C.POINTER(GridDesc), C.c_int, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "rb_fvm_assemble": (C.c_int, [C.POINTER(GridDesc), C.c_int, dbl, vp, vp, vp, vp]),
         "rb_mesh_cot_laplacian": (C.c_int, [i32, vp, i32, vp, vp, vp, i64, vp, vp, vp, vp]),
@@ -158,6 +159,13 @@ def _check(status: int, what: str):
 
 def version() -> str:
     return lib().rb_version().decode()
+
+
+def fma_peak(dtype="f64", stream=None) -> float:
+    """Measured FMA throughput of the GPU in TFLOP/s (rb_fma_peak)."""
+    v = C.c_double()
+    _check(lib().rb_fma_peak({"f64": RB_F64, "f32": RB_F32}[dtype], C.byref(v), _stream(stream)), "rb_fma_peak")
+    return v.value
 
 
 # ----------------------------------------------------------------------------- tensor helpers

@@ -328,3 +328,12 @@ def test_dot_axpy_axty_strided(rb, dtype, k):
     tol2 = 1e-15 if dtype == "f64" else 2e-7
     assert np.all(np.abs(got - aref) <= tol2 * (np.abs(X * alpha[None, :]) + np.abs(Y)) + 1e-300)
     assert torch.isnan(Yw[:, k:]).all()
+
+
+def test_fma_peak_is_plausible(rb):
+    """The measured FMA roofs: FP64 within GB300's nominal rate (152 SMs x 2 FMAs per clock x 2
+    flops at up to 2.07 GHz, 1.26 TFLOP/s) and above half of it; FP32 far above FP64."""
+    f64 = rb.fma_peak("f64")
+    f32 = rb.fma_peak("f32")
+    assert 0.5 * 1.26 < f64 <= 1.05 * 1.26, f64
+    assert f32 > 20 * f64, (f32, f64)
