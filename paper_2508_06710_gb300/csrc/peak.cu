@@ -1,7 +1,9 @@
 // Measured FMA throughput of the GPU (FP64 and FP32): the arithmetic roof of the FP64 SpMM
 // and CG kernels, which GB300's FP64 rate bounds before HBM does.  Every thread runs eight
-// independent FMA chains on values the compiler cannot fold (they come from the arguments),
-// a full-occupancy grid keeps every pipe busy, and CUDA events time the launch.
+// independent FMA chains on values the compiler cannot fold, a full-occupancy grid keeps every
+// pipe busy, and CUDA events time the launch.  The multiplier and addend are per-thread
+// register values: taken straight from the kernel's parameters (constant-bank operands), the
+// FP64 FMAs of GB300 issue at about 0.81 of their rate with register operands.
 #include "common.cuh"
 
 namespace rb {
@@ -18,7 +20,8 @@ __device__ __forceinline__ void fma_sink(double v) { g_fma_sink64 = v; }
 __device__ __forceinline__ void fma_sink(float v) { g_fma_sink32 = v; }
 
 template <typename T>
-__global__ void __launch_bounds__(kPeakThreads) k_fma_peak(int iters, T a, T b) {
+__global__ void __launch_bounds__(kPeakThreads) k_fma_peak(int iters, T a0, T b0) {
+  const T a = a0 + (T)threadIdx.x * (T)1e-15, b = b0 + (T)threadIdx.x * (T)1e-17;  // in registers
   T v[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) v[c] = a + (T)(threadIdx.x + c);
