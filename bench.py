@@ -321,6 +321,8 @@ def graph_ms(torch, fn, calls=20, reps=10):
 def blas1(torch, rb, dev, n, hbm):
     """dot, axpy, axty on n x 3 blocks (FP64 and FP32): algorithmic GB/s per call, timed as
     back-to-back kernels (graph replays) and as single eager calls (launch latency included);
+    axty with alpha = 1 (the Jacobi product, one multiply per entry) and with another alpha
+    (two multiplies per entry, which the FP64 multiply rate bounds before HBM does);
     `copy_frac` compares with a device copy moving the same bytes (the ceiling at this size).
     n is raised to four channel grids (9.4 M rows) so that every operand exceeds L2 even when
     the replays run back to back."""
@@ -337,7 +339,8 @@ def blas1(torch, rb, dev, n, hbm):
         s = X.element_size()
         for name, fn, by in (("dot", lambda: rb.dot(X, Y, out=out, work=work), 2 * n * k * s),
                              ("axpy", lambda: rb.axpy(alpha, X, Y), 3 * n * k * s),
-                             ("axty", lambda: rb.axty(1.0, ones, Y), 3 * n * k * s)):
+                             ("axty", lambda: rb.axty(1.0, ones, Y), 3 * n * k * s),
+                             ("axty_scaled", lambda: rb.axty(1.0 + 2.0 ** -20, ones, Y), 3 * n * k * s)):
             ms = graph_ms(torch, fn)
             ms_call = time_events(torch, fn, 10)
             src = torch.empty(by // 8, dtype=torch.float32, device=dev)

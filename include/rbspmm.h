@@ -231,7 +231,9 @@ rb_status rb_dot_noalloc(int64_t n, int32_t k, rb_dtype dtype, const void* X, in
 /* Y[:, j] += alpha[j] X[:, j]; alpha: k float64 DEVICE values. */
 rb_status rb_axpy(int64_t n, int32_t k, rb_dtype dtype, const double* alpha, const void* X, int64_t ldx, void* Y,
                   int64_t ldy, rb_stream_t stream);
-/* Y[i, j] = alpha X[i, j] Y[i, j]  (the element-wise product of Sec. 1 and Sec. 3.1). */
+/* Y[i, j] = alpha X[i, j] Y[i, j]  (the element-wise product of Sec. 1 and Sec. 3.1), each
+ * entry rounded as (alpha x) y; alpha == 1 (after conversion to the block's type) computes the
+ * single product x y, which is the same value. */
 rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha, const void* X, int64_t ldx, void* Y,
                   int64_t ldy, rb_stream_t stream);
 

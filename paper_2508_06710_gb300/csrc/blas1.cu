@@ -81,7 +81,16 @@ __global__ void __launch_bounds__(kThreads) k_axpy(int64_t n, int k, int kp, con
   }
 }
 
-template <typename T, int VEC>
+// alpha x y with alpha == 1 taken as the one product x y: the same value (1 x is x exactly), and
+// half the FP64 multiplies, which GB300 issues at 2 per clock per SM: two multiplies per entry
+// bound the FP64 kernel near 90 µs on 28 M entries, more than its HBM time.
+template <bool UNIT, typename T>
+__device__ __forceinline__ T axty_elem(T alpha, T x, T y) {
+  if constexpr (UNIT) return x * y;
+  else return alpha * x * y;
+}
+
+template <typename T, int VEC, bool UNIT>
 __global__ void __launch_bounds__(kThreads) k_axty(int64_t n, int k, int kp, T alpha, const T* __restrict__ X,
                                                    int64_t ldx, T* __restrict__ Y, int64_t ldy) {
   const int R = kThreads / kp;
@@ -91,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_axty(int64_t n, int k, int kp, T a
     const Vec<T, VEC> x = ldv<T, VEC>(X + row * ldx + chunk * VEC);
     Vec<T, VEC> y = ldv_rw<T, VEC>(Y + row * ldy + chunk * VEC);
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) y.v[e] = alpha * x.v[e] * y.v[e];
+    for (int e = 0; e < VEC; ++e) y.v[e] = axty_elem<UNIT>(alpha, x.v[e], y.v[e]);
     stv<T, VEC>(Y + row * ldy + chunk * VEC, y);
   }
 }
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_axpy_flat(int64_t total, int k, co
   if (f < total) Y[f] = fma((T)alpha[f % k], X[f], Y[f]);
 }
 
-template <typename T>
+template <typename T, bool UNIT>
 __global__ void __launch_bounds__(kThreads) k_axty_flat(int64_t total, T alpha, const T* __restrict__ X,
                                                         T* __restrict__ Y) {
   constexpr int V = 16 / sizeof(T);
@@ -252,11 +261,11 @@ __global__ void __launch_bounds__(kThreads) k_axty_flat(int64_t total, T alpha, 
     const Vec<T, V> x = ldv<T, V>(X + c * V);
     Vec<T, V> y = ldv_rw<T, V>(Y + c * V);
 #pragma unroll
-    for (int e = 0; e < V; ++e) y.v[e] = alpha * x.v[e] * y.v[e];
+    for (int e = 0; e < V; ++e) y.v[e] = axty_elem<UNIT>(alpha, x.v[e], y.v[e]);
     stv<T, V>(Y + c * V, y);
   }
   const int64_t f = nvec * V + tid;
-  if (f < total) Y[f] = alpha * X[f] * Y[f];
+  if (f < total) Y[f] = axty_elem<UNIT>(alpha, X[f], Y[f]);
 }
 
 bool flat_ok(int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
@@ -393,6 +402,23 @@ extern "C" rb_status rb_axpy(int64_t n, int32_t k, rb_dtype dtype, const double*
   return RB_OK;
 }
 
+template <typename T, bool UNIT>
+rb_status launch_axty(int64_t n, int k, int vec, int kp, T alpha, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                      cudaStream_t s) {
+  if (flat_ok(k, ldx, ldy, X, Y)) {
+    const int64_t total = n * k;
+    k_axty_flat<T, UNIT><<<flat_grid(&k_axty_flat<T, UNIT>, total, (int)sizeof(T), 1), kThreads, 0, s>>>(
+        total, alpha, (const T*)X, (T*)Y);
+  } else {
+    const int64_t blocks = (n + kThreads / kp - 1) / (kThreads / kp);
+    RB_DISPATCH_VEC(T, vec,
+                    k_axty<T, V, UNIT><<<wave_grid(&k_axty<T, V, UNIT>, blocks), kThreads, 0, s>>>(
+                        n, k, kp, alpha, (const T*)X, ldx, (T*)Y, ldy));
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
 extern "C" rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha, const void* X, int64_t ldx, void* Y,
                              int64_t ldy, rb_stream_t stream) {
   clear_error();
@@ -403,26 +429,12 @@ extern "C" rb_status rb_axty(int64_t n, int32_t k, rb_dtype dtype, double alpha,
   int vec, kp;
   vec_kp(eb, k, ldx, ldy, X, Y, vec, kp);
   RB_REQUIRE(kp <= 32, "rb_axty: k = %d needs 16-byte aligned rows", k);
-  const int64_t blocks = (n + kThreads / kp - 1) / (kThreads / kp);
-  if (flat_ok(k, ldx, ldy, X, Y)) {
-    const int64_t total = n * k;
-    if (dtype == RB_F64)
-      k_axty_flat<double><<<flat_grid(&k_axty_flat<double>, total, 8, 1), kThreads, 0, s>>>(
-          total, alpha, (const double*)X, (double*)Y);
-    else
-      k_axty_flat<float><<<flat_grid(&k_axty_flat<float>, total, 4, 1), kThreads, 0, s>>>(
-          total, (float)alpha, (const float*)X, (float*)Y);
-  } else if (dtype == RB_F64) {
-    RB_DISPATCH_VEC(double, vec,
-                    k_axty<double, V><<<wave_grid(&k_axty<double, V>, blocks), kThreads, 0, s>>>(
-                        n, k, kp, alpha, (const double*)X, ldx, (double*)Y, ldy));
-  } else {
-    RB_DISPATCH_VEC(float, vec,
-                    k_axty<float, V><<<wave_grid(&k_axty<float, V>, blocks), kThreads, 0, s>>>(
-                        n, k, kp, (float)alpha, (const float*)X, ldx, (float*)Y, ldy));
+  if (dtype == RB_F64) {
+    if (alpha == 1.0) return launch_axty<double, true>(n, k, vec, kp, 1.0, X, ldx, Y, ldy, s);
+    return launch_axty<double, false>(n, k, vec, kp, alpha, X, ldx, Y, ldy, s);
   }
-  RB_CUDA(cudaGetLastError());
-  return RB_OK;
+  if ((float)alpha == 1.0f) return launch_axty<float, true>(n, k, vec, kp, 1.0f, X, ldx, Y, ldy, s);
+  return launch_axty<float, false>(n, k, vec, kp, (float)alpha, X, ldx, Y, ldy, s);
 }
 
 // ---------------------------------------------------------------------------------------

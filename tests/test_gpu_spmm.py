@@ -302,6 +302,11 @@ def test_dot_axpy_axty(rb, dtype, k, n):
     tref = blas.axty(0.5, X, Y)
     tol3 = 1e-15 if dtype == "f64" else 2e-7
     assert np.all(np.abs(Yd2.cpu().numpy() - tref) <= tol3 * np.abs(tref) + 1e-300)
+    # alpha = 1 (the Jacobi product, one multiply per entry): the correctly rounded x y, bit for
+    # bit (the FP64 product of two FP32 values is exact, so rounding it once gives the FP32 one)
+    Yd3 = to_dev(Y)
+    rb.axty(1.0, Xd, Yd3)
+    assert np.array_equal(Yd3.cpu().numpy(), blas.axty(1.0, X, Y).astype(npdt))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -328,6 +333,16 @@ def test_dot_axpy_axty_strided(rb, dtype, k):
     tol2 = 1e-15 if dtype == "f64" else 2e-7
     assert np.all(np.abs(got - aref) <= tol2 * (np.abs(X * alpha[None, :]) + np.abs(Y)) + 1e-300)
     assert torch.isnan(Yw[:, k:]).all()
+    for a in (0.5, 1.0):  # both axty kernels: the scaled product and the unit one
+        Yw[:, :k] = to_dev(Y)
+        rb.axty(a, Xw[:, :k], Yw[:, :k])
+        tref = blas.axty(a, X, Y)
+        got = Yw[:, :k].cpu().numpy()
+        if a == 1.0:
+            assert np.array_equal(got, tref.astype(npdt))
+        else:
+            assert np.all(np.abs(got - tref) <= (1e-15 if dtype == "f64" else 2e-7) * np.abs(tref) + 1e-300)
+        assert torch.isnan(Yw[:, k:]).all()
 
 
 def test_fma_peak_is_plausible(rb):
