@@ -269,6 +269,7 @@ def run_ours(args, rank, world, local):
         out["poisson"] = poisson(torch, rb, ops, g, dev)
         out["operator_build"] = operator_build(torch, rb, g, dev)
         out["blas1"] = blas1(torch, rb, dev, g.n_cells, hbm)
+        out["stencils"] = stencils(torch, rb, dev, hbm)
         del ops, step_items
         torch.cuda.empty_cache()
         out["batch"] = batch_bench(torch, rb, dev)
@@ -303,6 +304,57 @@ def operator_build(torch, rb, g, dev):
 
         ms = time_events(torch, run, 5)
         res[name] = {"ms": ms, "nnz": nnz, "gbs_written": (nnz * 12 + 4 * (nr + 1)) / ms / 1e6}
+    return res
+
+
+STENCIL_N = 160  # the fine mesh on which Sec. 4.1 compares the 7p, 13p and 27p patterns
+
+
+def stencils(torch, rb, dev, hbm):
+    """SpMM on the 7p (FVM), 13p and 27p Laplacians of the uniform periodic 160^3 grid (Sec. 4.1's
+    denser patterns), FP64 and FP32, k = 1, 2, 4, 8 (tuned; events, median of 10): GFLOP/s,
+    algorithmic GB/s and the speed-up over k SpMVs, k t_1 / t_k; and the device assembly of
+    each 13p / 27p CSR (events, median of 5)."""
+    import ctypes as C
+
+    n, h = STENCIL_N, 1.0 / STENCIL_N
+    cells = n ** 3
+    res = {"grid": f"periodic {n}^3", "n": cells, "spmm": [], "assembly": {}}
+    for name in ("7p", "13p", "27p"):
+        if name == "7p":
+            nodes, per = rb.grid_nodes(W.unit_periodic_grid(n), dev)
+            rp, ci, va, _ = rb.fvm_assemble(nodes, per, rb.RB_FVM_LAPLACIAN)
+        else:
+            kind = rb.RB_STENCIL_13P if name == "13p" else rb.RB_STENCIL_27P
+            rp, ci, va, _ = rb.stencil_assemble((n, n, n), (h, h, h), kind, device=dev)
+            narr, harr = (C.c_int32 * 3)(n, n, n), (C.c_double * 3)(h, h, h)
+
+            def run():
+                rb._check(rb.lib().rb_stencil_assemble(narr, harr, kind, 1.0, rb._ptr(rp), rb._ptr(ci), rb._ptr(va),
+                                                       rb._stream()), "rb_stencil_assemble")
+
+            ms = time_events(torch, run, 5)
+            res["assembly"][name] = {"ms": ms, "nnz": ci.numel(), "gbs_written": (ci.numel() * 12 + 4 * (cells + 1)) / ms / 1e6}
+        for dt in ("f64", "f32"):
+            op = rb.Operator(rp, ci, va, cells, dtype=dt, k_max=8)
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            s_b = 8 if dt == "f64" else 4
+            base = None
+            for k in (1, 2, 4, 8):
+                X = torch.randn((cells, k), dtype=tdt, device=dev)
+                Y = torch.empty((cells, k), dtype=tdt, device=dev)
+                op.tune(X, Y)
+                ms = time_events(torch, lambda: op.spmm(X, Y), 10)
+                by = spmm_bytes(op.nnz, cells, cells, k, s_b)
+                base = ms if k == 1 else base
+                res["spmm"].append({"stencil": name, "dtype": dt, "k": k, "nnz": op.nnz, "ms": ms,
+                                    "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6, "frac_hbm": by / ms / 1e6 / hbm,
+                                    "ai_flop_per_byte": 2 * op.nnz * k / by, "speedup_vs_k_spmv": k * base / ms,
+                                    "schedule": op.schedule(X, Y)})
+                del X, Y
+            del op
+        del rp, ci, va
+        torch.cuda.empty_cache()
     return res
 
 

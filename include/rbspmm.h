@@ -104,6 +104,27 @@ rb_status rb_fvm_csr_size(const rb_grid_desc* grid, rb_fvm_kind kind, int32_t* n
 rb_status rb_fvm_assemble(const rb_grid_desc* grid, rb_fvm_kind kind, double scale, int32_t* row_ptr,
                           int32_t* col_idx, double* vals, rb_stream_t stream);
 
+/* Wider Laplacian stencils on a uniform periodic Cartesian grid (Sec. 4.1: the denser 13p and
+ * 27p sparsity patterns measured beside the first-neighbour 7p of RB_FVM_LAPLACIAN).  The paper
+ * fixes only the patterns; the values are volume-integrated like the FVM Laplacian (cell
+ * volume V = h[0] h[1] h[2] times a pointwise Laplacian), so -L is symmetric positive
+ * semi-definite with the constants as null space:
+ *   RB_STENCIL_13P  the first and second neighbours along each axis: along axis d the
+ *                   fourth-order difference (-u[-2] + 16 u[-1] - 30 u[0] + 16 u[+1] - u[+2])
+ *                   / (12 h[d]^2), summed over the axes; needs n[d] >= 5.
+ *   RB_STENCIL_27P  the 3 x 3 x 3 block on cubic cells (h[0] == h[1] == h[2] = h): weights
+ *                   -128, 14, 3, 1 over 30 h^2 for the centre and the face, edge and corner
+ *                   neighbours (leading error isotropic); needs n[d] >= 3.
+ * Cells are numbered id = i + n[0] (j + n[1] k).  n and h are HOST arrays.  Writes the CSR
+ * times `scale` into caller-allocated DEVICE arrays: row_ptr[N + 1], col_idx[kind N],
+ * vals[kind N] (float64), N = n[0] n[1] n[2]; every row has exactly `kind` entries, columns
+ * sorted.  RB_EINVAL (nothing launched) for an unknown kind, too few cells, a non-positive or
+ * non-finite spacing, unequal spacings for 27p, kind N above 2^31 - 1, or a null output.
+ * Asynchronous on `stream`. */
+typedef enum { RB_STENCIL_13P = 13, RB_STENCIL_27P = 27 } rb_stencil_kind;
+rb_status rb_stencil_assemble(const int32_t n[3], const double h[3], rb_stencil_kind kind, double scale,
+                              int32_t* row_ptr, int32_t* col_idx, double* vals, rb_stream_t stream);
+
 /* Cotangent-weight Laplacian of a triangle mesh (vertex-centred, per unit depth), the
  * unstructured operator of the extruded-airfoil case (Sec. 4.3).  The caller passes the
  * mesh (DEVICE: points[2 n_vert] as x,y pairs, triangles[3 n_tri] counter-clockwise) and

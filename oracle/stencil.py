@@ -52,12 +52,10 @@ def _from_offsets(shape, offsets) -> sp.csr_matrix:
     return A
 
 
-def laplacian_13p(shape, h) -> sp.csr_matrix:
-    """13p: V times the sum over the axes of the fourth-order second difference (Sec. 4.1)."""
-    shape = tuple(int(s) for s in shape)
+def offsets_13p(h):
+    """(offset, value) pairs of a 13p row: V times the fourth-order second difference along
+    each axis, summed (Sec. 4.1)."""
     h = tuple(float(x) for x in h)
-    if min(shape) < 5:
-        raise ValueError("13p needs at least 5 cells along every axis")
     vol = h[0] * h[1] * h[2]
     offsets = []
     centre = 0.0
@@ -68,22 +66,46 @@ def laplacian_13p(shape, h) -> sp.csr_matrix:
             offsets.append((tuple(e), vol * c / (12.0 * h[d] * h[d])))
         centre += vol * (-30.0) / (12.0 * h[d] * h[d])
     offsets.append(((0, 0, 0), centre))
-    return _from_offsets(shape, offsets)
+    return offsets
 
 
-def laplacian_27p(shape, h) -> sp.csr_matrix:
-    """27p on cubic cells of width h: V / (30 h^2) times -128 (centre), 14 (faces), 3 (edges),
-    1 (corners) (Sec. 4.1)."""
-    shape = tuple(int(s) for s in shape)
+def offsets_27p(h):
+    """(offset, value) pairs of a 27p row on cubic cells of width h: V / (30 h^2) times -128
+    (centre), 14 (faces), 3 (edges), 1 (corners) (Sec. 4.1)."""
     h = float(h)
-    if min(shape) < 3:
-        raise ValueError("27p needs at least 3 cells along every axis")
     scale = h ** 3 / (30.0 * h * h)
     weight = {0: -128.0, 1: 14.0, 2: 3.0, 3: 1.0}  # by the number of nonzero offset components
     offsets = []
     for o in itertools.product((-1, 0, 1), repeat=3):
         offsets.append((o, scale * weight[sum(1 for c in o if c != 0)]))
-    return _from_offsets(shape, offsets)
+    return offsets
+
+
+def laplacian_13p(shape, h) -> sp.csr_matrix:
+    """13p on the periodic grid of `shape` cells with spacings h (Sec. 4.1)."""
+    shape = tuple(int(s) for s in shape)
+    if min(shape) < 5:
+        raise ValueError("13p needs at least 5 cells along every axis")
+    return _from_offsets(shape, offsets_13p(h))
+
+
+def laplacian_27p(shape, h) -> sp.csr_matrix:
+    """27p on the periodic grid of `shape` cubic cells of width h (Sec. 4.1)."""
+    shape = tuple(int(s) for s in shape)
+    if min(shape) < 3:
+        raise ValueError("27p needs at least 3 cells along every axis")
+    return _from_offsets(shape, offsets_27p(h))
+
+
+def row(shape, offsets, r):
+    """Columns (sorted) and values of row r alone: the sampled rows of a grid too large to
+    assemble here."""
+    nx, ny, nz = (int(s) for s in shape)
+    i, j, k = r % nx, (r // nx) % ny, r // (nx * ny)
+    cols = [int(_cell_index((nx, ny, nz), (i + dx) % nx, (j + dy) % ny, (k + dz) % nz)) for (dx, dy, dz), _ in offsets]
+    vals = [w for _, w in offsets]
+    order = np.argsort(cols, kind="stable")
+    return np.asarray(cols)[order], np.asarray(vals)[order]
 
 
 def cell_coordinates(shape, h) -> np.ndarray:

@@ -23,10 +23,12 @@ STATUS_NAMES = ["RB_OK", "RB_EINVAL", "RB_ENOMEM", "RB_ECUDA", "RB_ENOCONV", "RB
 RB_F64, RB_F32 = 0, 1
 RB_CSR, RB_SELL, RB_AUTO = 0, 1, 2
 RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT = 0, 1, 2
+RB_STENCIL_13P, RB_STENCIL_27P = 13, 27
 RB_MAX_K = 64
 
 # exported C symbols, in the order include/rbspmm.h declares them
-SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_mesh_cot_laplacian",
+SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_stencil_assemble",
+           "rb_mesh_cot_laplacian",
            "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
@@ -105,6 +107,7 @@ def lib():
         "rb_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_void_p]),
         "rb_fvm_csr_size": (C.c_int, [C.POINTER(GridDesc), C.c_int, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "rb_fvm_assemble": (C.c_int, [C.POINTER(GridDesc), C.c_int, dbl, vp, vp, vp, vp]),
+        "rb_stencil_assemble": (C.c_int, [C.POINTER(i32), C.POINTER(dbl), C.c_int, dbl, vp, vp, vp, vp]),
         "rb_mesh_cot_laplacian": (C.c_int, [i32, vp, i32, vp, vp, vp, i64, vp, vp, vp, vp]),
         "rb_operator_create": (C.c_int, [C.POINTER(CsrDesc), C.POINTER(BlockDesc), C.c_int, C.c_int, vp,
                                          C.POINTER(vp)]),
@@ -236,6 +239,21 @@ def fvm_assemble(nodes, periodic, kind, scale=1.0, stream=None):
     _check(lib().rb_fvm_assemble(C.byref(g), kind, float(scale), _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)),
            "rb_fvm_assemble")
     return rp, ci, va, nc
+
+
+def stencil_assemble(shape, h, kind, scale=1.0, device="cuda", stream=None):
+    """CSR (row_ptr, col_idx, vals, n) of the 13p or 27p Laplacian (``RB_STENCIL_13P`` /
+    ``RB_STENCIL_27P``) on the uniform periodic grid of ``shape`` cells with spacings ``h``."""
+    torch = _torch()
+    n_arr = (C.c_int32 * 3)(*[int(v) for v in shape])
+    h_arr = (C.c_double * 3)(*[float(v) for v in h])
+    rows = int(shape[0]) * int(shape[1]) * int(shape[2])
+    rp = torch.empty(rows + 1, dtype=torch.int32, device=device)
+    ci = torch.empty(int(kind) * rows, dtype=torch.int32, device=device)
+    va = torch.empty(int(kind) * rows, dtype=torch.float64, device=device)
+    _check(lib().rb_stencil_assemble(n_arr, h_arr, int(kind), float(scale), _ptr(rp), _ptr(ci), _ptr(va),
+                                     _stream(stream)), "rb_stencil_assemble")
+    return rp, ci, va, rows
 
 
 def grid_nodes(grid, device="cuda"):

@@ -74,6 +74,24 @@ def test_host_side_validation_without_gpu(lib):
     assert b"diagonal" in lib.rb_last_error()
 
 
+def test_stencil_validation_without_gpu(lib):
+    """rb_stencil_assemble refuses bad grids before any device work (null outputs here)."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+
+    def call(n, h, kind):
+        return lib.rb_stencil_assemble((C.c_int32 * 3)(*n), (C.c_double * 3)(*h), kind, 1.0, None, None, None, None)
+
+    for n, h, kind, msg in (((4, 6, 6), (1, 1, 1), 13, b">= 5 cells"), ((5, 5, 2), (1, 1, 1), 27, b">= 3 cells"),
+                            ((5, 5, 5), (1, 1, 2), 27, b"cubic"), ((5, 5, 5), (1, 0, 1), 13, b"positive"),
+                            ((5, 5, 5), (1, float("nan"), 1), 13, b"positive"), ((5, 5, 5), (1, 1, 1), 7, b"unknown kind"),
+                            ((1000, 1000, 100), (1, 1, 1), 27, b"32-bit"), ((5, 5, 5), (1, 1, 1), 13, b"null output")):
+        assert call(n, h, kind) == rb.RB_EINVAL
+        assert msg in lib.rb_last_error(), (n, h, kind, lib.rb_last_error())
+    assert lib.rb_stencil_assemble(None, None, 13, 1.0, None, None, None, None) == rb.RB_EINVAL
+
+
 def test_fvm_sizes_match_oracle(lib):
     """Row, column and nonzero counts of the device builder equal the oracle's (no GPU work)."""
     import ctypes as C
