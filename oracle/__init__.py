@@ -11,6 +11,8 @@ Contents, each function citing the passage of the paper it follows:
   * ``cg``      Jacobi-preconditioned CG per column, FP32-inner iterative refinement,
                 batched uneven systems (Poisson solve of the projection method, Sec. 4)
   * ``stencil`` 13p and 27p Laplacians on uniform periodic grids (the denser patterns of Sec. 4.1)
+  * ``refine``  coarse-to-fine prolongation and volume-weighted restriction of cell fields
+                (inline mesh refinement, Sec. 3.3)
   * ``mesh``    cotangent-weight Laplacian of a triangle mesh and its periodic extrusion
                 (repeated geometries, Sec. 2; airfoil case, Sec. 4.3)
   * ``bounds``  arithmetic-intensity and speed-up models (Eqs. (ai), (pmspmm), (poipm), (pmite),
