@@ -270,6 +270,7 @@ def run_ours(args, rank, world, local):
         out["operator_build"] = operator_build(torch, rb, g, dev)
         out["blas1"] = blas1(torch, rb, dev, g.n_cells, hbm)
         out["stencils"] = stencils(torch, rb, dev, hbm)
+        out["refine"] = refine_maps(torch, rb, dev, hbm)
         del ops, step_items
         torch.cuda.empty_cache()
         out["batch"] = batch_bench(torch, rb, dev)
@@ -355,6 +356,46 @@ def stencils(torch, rb, dev, hbm):
             del op
         del rp, ci, va
         torch.cuda.empty_cache()
+    return res
+
+
+def refine_maps(torch, rb, dev, hbm):
+    """Inline mesh refinement (Sec. 3.3): the k states of the 96 x 64 x 48 channel mapped onto
+    192 x 128 x 96 by the prolongation P (8 entries per fine row) and back by the restriction R,
+    FP64 and FP32, k = 1, 3, 4, 8 (tuned; events, median of 10); and the device assembly of P
+    and R (events, median of 5)."""
+    import ctypes as C
+
+    g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+    nodes, per = rb.grid_nodes(g, dev)
+    res = {"fine": "channel 192x128x96", "coarse": "channel 96x64x48", "spmm": [], "assembly": {}}
+    for name, kind in (("prolong", rb.RB_REFINE_PROLONG), ("restrict", rb.RB_REFINE_RESTRICT)):
+        rp, ci, va, nc = rb.refine_assemble(nodes, per, kind)
+        gd = rb._grid_desc(nodes, per)
+
+        def run():
+            rb._check(rb.lib().rb_refine_assemble(C.byref(gd), kind, rb._ptr(rp), rb._ptr(ci), rb._ptr(va), rb._stream()),
+                      "rb_refine_assemble")
+
+        ms = time_events(torch, run, 5)
+        nr = rp.numel() - 1
+        res["assembly"][name] = {"ms": ms, "nnz": ci.numel(), "gbs_written": (ci.numel() * 12 + 4 * (nr + 1)) / ms / 1e6}
+        for dt in ("f64", "f32"):
+            op = rb.Operator(rp, ci, va, nc, dtype=dt, k_max=8)
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            s_b = 8 if dt == "f64" else 4
+            for k in (1, 3, 4, 8):
+                X = torch.randn((nc, k), dtype=tdt, device=dev)
+                Y = torch.empty((nr, k), dtype=tdt, device=dev)
+                op.tune(X, Y)
+                ms = time_events(torch, lambda: op.spmm(X, Y), 10)
+                by = spmm_bytes(op.nnz, nr, nc, k, s_b)
+                res["spmm"].append({"map": name, "dtype": dt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6,
+                                    "gbs": by / ms / 1e6, "frac_hbm": by / ms / 1e6 / hbm, "schedule": op.schedule(X, Y)})
+                del X, Y
+            del op
+        del rp, ci, va
+    torch.cuda.empty_cache()
     return res
 
 

@@ -125,6 +125,27 @@ typedef enum { RB_STENCIL_13P = 13, RB_STENCIL_27P = 27 } rb_stencil_kind;
 rb_status rb_stencil_assemble(const int32_t n[3], const double h[3], rb_stencil_kind kind, double scale,
                               int32_t* row_ptr, int32_t* col_idx, double* vals, rb_stream_t stream);
 
+/* Coarse-to-fine maps of cell fields for inline mesh refinement (Sec. 3.3: the flow states
+ * are developed on a coarser mesh and then mapped onto the target mesh, all k states at once
+ * as one rectangular SpMM).  `fine` is a grid as above with an even number n[d] >= 4 of cells
+ * along every axis; its coarse grid keeps every other node (coarse cell I = fine cells 2I and
+ * 2I + 1 along each axis), so N_c = N / 8 cells, numbered the same way.  The paper does not
+ * give the map; the reading here:
+ *   RB_REFINE_PROLONG   P (N x N_c): along each axis, linear interpolation in the cell-centre
+ *                       coordinate between the two coarse centres nearest to the fine centre
+ *                       (across a periodic seam with the period added; next to a wall the two
+ *                       coarse cells at the wall, extrapolating); the product of the three
+ *                       axis weights, 8 entries per row; reproduces trilinear fields exactly.
+ *   RB_REFINE_RESTRICT  R (N_c x N): the volume-weighted mean of the 8 children of each coarse
+ *                       cell (keeps the integral of the field).
+ * Writes into caller-allocated DEVICE arrays row_ptr[rows + 1], col_idx[8 rows],
+ * vals[8 rows] (float64), rows = N (P) or N_c (R); columns sorted.  RB_EINVAL (nothing
+ * launched) for an unknown kind, an odd or too small axis, a null array, or 8 N > 2^31 - 1.
+ * Asynchronous on `stream`. */
+typedef enum { RB_REFINE_PROLONG = 0, RB_REFINE_RESTRICT = 1 } rb_refine_kind;
+rb_status rb_refine_assemble(const rb_grid_desc* fine, rb_refine_kind kind, int32_t* row_ptr, int32_t* col_idx,
+                             double* vals, rb_stream_t stream);
+
 /* Cotangent-weight Laplacian of a triangle mesh (vertex-centred, per unit depth), the
  * unstructured operator of the extruded-airfoil case (Sec. 4.3).  The caller passes the
  * mesh (DEVICE: points[2 n_vert] as x,y pairs, triangles[3 n_tri] counter-clockwise) and

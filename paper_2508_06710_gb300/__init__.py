@@ -24,11 +24,12 @@ RB_F64, RB_F32 = 0, 1
 RB_CSR, RB_SELL, RB_AUTO = 0, 1, 2
 RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT = 0, 1, 2
 RB_STENCIL_13P, RB_STENCIL_27P = 13, 27
+RB_REFINE_PROLONG, RB_REFINE_RESTRICT = 0, 1
 RB_MAX_K = 64
 
 # exported C symbols, in the order include/rbspmm.h declares them
 SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_stencil_assemble",
-           "rb_mesh_cot_laplacian",
+           "rb_refine_assemble", "rb_mesh_cot_laplacian",
            "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
@@ -108,6 +109,7 @@ def lib():
         "rb_fvm_csr_size": (C.c_int, [C.POINTER(GridDesc), C.c_int, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "rb_fvm_assemble": (C.c_int, [C.POINTER(GridDesc), C.c_int, dbl, vp, vp, vp, vp]),
         "rb_stencil_assemble": (C.c_int, [C.POINTER(i32), C.POINTER(dbl), C.c_int, dbl, vp, vp, vp, vp]),
+        "rb_refine_assemble": (C.c_int, [C.POINTER(GridDesc), C.c_int, vp, vp, vp, vp]),
         "rb_mesh_cot_laplacian": (C.c_int, [i32, vp, i32, vp, vp, vp, i64, vp, vp, vp, vp]),
         "rb_operator_create": (C.c_int, [C.POINTER(CsrDesc), C.POINTER(BlockDesc), C.c_int, C.c_int, vp,
                                          C.POINTER(vp)]),
@@ -254,6 +256,26 @@ def stencil_assemble(shape, h, kind, scale=1.0, device="cuda", stream=None):
     _check(lib().rb_stencil_assemble(n_arr, h_arr, int(kind), float(scale), _ptr(rp), _ptr(ci), _ptr(va),
                                      _stream(stream)), "rb_stencil_assemble")
     return rp, ci, va, rows
+
+
+def refine_assemble(nodes, periodic, kind, stream=None):
+    """CSR (row_ptr, col_idx, vals, n_cols) of the prolongation (``RB_REFINE_PROLONG``, fine x
+    coarse) or restriction (``RB_REFINE_RESTRICT``, coarse x fine) between the grid whose
+    axis node coordinates are the float64 CUDA tensors ``nodes`` and its 2:1 coarsening."""
+    torch = _torch()
+    nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
+    n_fine = 1
+    for n in nodes:
+        n_fine *= int(n.numel() - 1)
+    rows, cols = (n_fine, n_fine // 8) if kind == RB_REFINE_PROLONG else (n_fine // 8, n_fine)
+    dev = nodes[0].device
+    rp = torch.empty(rows + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(8 * rows, dtype=torch.int32, device=dev)
+    va = torch.empty(8 * rows, dtype=torch.float64, device=dev)
+    g = _grid_desc(nodes, periodic)
+    _check(lib().rb_refine_assemble(C.byref(g), int(kind), _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)),
+           "rb_refine_assemble")
+    return rp, ci, va, cols
 
 
 def grid_nodes(grid, device="cuda"):

@@ -12,6 +12,9 @@
 //     each angle to the weight of the opposite edge (at most two contributions per edge,
 //     whose sum does not depend on their order), then one thread per row clamps negative
 //     weights and forms the diagonal.
+// (3) The coarse-to-fine maps of inline mesh refinement (Sec. 3.3): prolongation P (fine cells
+//     x coarse cells) and restriction R (coarse x fine) between a grid and its 2:1 coarsening
+//     (every other node), 8 entries per row in both, so again no scan.
 #include <algorithm>
 
 #include "common.cuh"
@@ -439,6 +442,150 @@ rb_status launch_fvm(const GridDev& g, double scale, int32_t* rp, int32_t* ci, d
   return RB_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Inline mesh refinement maps.  The coarse grid is the fine one with every other node, so
+// coarse cell I along an axis is fine cells 2I and 2I + 1 and its centre is the midpoint of
+// fine nodes 2I and 2I + 2.
+// ------------------------------------------------------------------------------------------
+constexpr int kMapThreads = 128;
+
+// Along axis d: the two coarse cells whose centres interpolate fine cell t (left child: the
+// parent and its left neighbour; right child: the parent and its right neighbour; across a
+// periodic seam the neighbour's centre shifted by the period; at a wall the two cells next to
+// it, extrapolating), returned sorted by index with their linear weights.
+__device__ __forceinline__ void prolong_axis(const GridDev& g, int d, int t, int (&c)[2], double (&w)[2]) {
+  const double* x = g.nodes[d];
+  const int nf = g.n[d], nc = nf / 2, parent = t >> 1;
+  int lo = (t & 1) ? parent : parent - 1;
+  int hi = lo + 1;
+  const double period = x[nf] - x[0];
+  double shift_lo = 0.0, shift_hi = 0.0;
+  if (lo < 0) {
+    if (g.per[d]) lo = nc - 1, shift_lo = -period;
+    else lo = 0, hi = 1;
+  }
+  if (hi >= nc) {
+    if (g.per[d]) hi = 0, shift_hi = period;
+    else lo = nc - 2, hi = nc - 1;
+  }
+  double x_lo = 0.5 * (x[2 * lo] + x[2 * lo + 2]);
+  double x_hi = 0.5 * (x[2 * hi] + x[2 * hi + 2]);
+  if (shift_lo != 0.0) x_lo = x_lo + shift_lo;
+  if (shift_hi != 0.0) x_hi = x_hi + shift_hi;
+  const double xf = 0.5 * (x[t] + x[t + 1]);
+  const double w_hi = (xf - x_lo) / (x_hi - x_lo);
+  const double w_lo = (x_hi - xf) / (x_hi - x_lo);
+  const bool sw = lo > hi;  // the seam puts the neighbour's index on the other side
+  c[0] = sw ? hi : lo, c[1] = sw ? lo : hi;
+  w[0] = sw ? w_hi : w_lo, w[1] = sw ? w_lo : w_hi;
+}
+
+// The two coarse cells and weights of one axis position: P's (fine position t) or R's (coarse
+// position p: the children 2p, 2p + 1 and their widths over the parent's).
+struct AxisMap {
+  int c[2];
+  double w[2];
+};
+
+template <bool RESTRICT>
+__device__ __forceinline__ AxisMap axis_map(const GridDev& g, int d, int t) {
+  AxisMap m;
+  if constexpr (RESTRICT) {
+    const double* x = g.nodes[d];
+    const double wc = x[2 * t + 2] - x[2 * t];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      m.c[a] = 2 * t + a;
+      m.w[a] = (x[2 * t + a + 1] - x[2 * t + a]) / wc;
+    }
+  } else {
+    prolong_axis(g, d, t, m.c, m.w);
+  }
+  return m;
+}
+
+// Axis positions per row: P's rows run over fine positions, R's over coarse ones.
+template <bool RESTRICT>
+__host__ __device__ inline int map_len(const GridDev& g, int d) { return RESTRICT ? g.n[d] / 2 : g.n[d]; }
+
+// Per-axis tables (AxisMap for every position of the three axes) in shared memory, 24 bytes
+// per position, when they fit in this budget; the weights then cost each block its share of
+// (nx + ny + nz) divisions pairs instead of six FP64 divisions per row.
+constexpr size_t kMapTabMax = 32 * 1024;
+
+// RESTRICT = false: P's rows (one per fine cell); true: R's rows (one per coarse cell, the
+// children in index order).  TAB: a persistent grid whose blocks build the axis tables once
+// and stride over 128-row tiles; else one tile per block with the weights computed per row.
+// Each tile is staged in shared memory and written out by consecutive threads.
+template <bool RESTRICT, bool TAB>
+__global__ void __launch_bounds__(kMapThreads) k_refine_map(GridDev g, int32_t* __restrict__ rp,
+                                                            int32_t* __restrict__ ci, double* __restrict__ va) {
+  __shared__ double s_val[kMapThreads * 8];
+  __shared__ int32_t s_col[kMapThreads * 8];
+  extern __shared__ AxisMap s_tab[];
+  const int l0 = map_len<RESTRICT>(g, 0), l1 = map_len<RESTRICT>(g, 1), l2 = map_len<RESTRICT>(g, 2);
+  if constexpr (TAB) {
+    for (int t = threadIdx.x; t < l0 + l1 + l2; t += kMapThreads) {
+      const int d = t < l0 ? 0 : (t < l0 + l1 ? 1 : 2);
+      const int q = t - (d == 0 ? 0 : (d == 1 ? l0 : l0 + l1));
+      // the axis as a compile-time index, so that the grid stays in registers
+      s_tab[t] = d == 0 ? axis_map<RESTRICT>(g, 0, q) : (d == 1 ? axis_map<RESTRICT>(g, 1, q) : axis_map<RESTRICT>(g, 2, q));
+    }
+    __syncthreads();
+  }
+  const int ncx = g.n[0] / 2, ncy = g.n[1] / 2;
+  const int rows = l0 * l1 * l2;
+  const int sx = RESTRICT ? g.n[0] : ncx, sy = RESTRICT ? g.n[1] : ncy;  // column grid
+  const int stride = TAB ? gridDim.x * kMapThreads : rows;
+  for (int r0 = blockIdx.x * kMapThreads; r0 < rows; r0 += stride) {
+    const int nr = min(kMapThreads, rows - r0);
+    const int r = r0 + threadIdx.x;
+    if (threadIdx.x < nr) {
+      const int i = r % l0, q = r / l0, j = q % l1, k = q / l1;
+      AxisMap m[3];
+      if constexpr (TAB) {
+        m[0] = s_tab[i], m[1] = s_tab[l0 + j], m[2] = s_tab[l0 + l1 + k];
+      } else {
+        m[0] = axis_map<RESTRICT>(g, 0, i), m[1] = axis_map<RESTRICT>(g, 1, j), m[2] = axis_map<RESTRICT>(g, 2, k);
+      }
+      int e = threadIdx.x * 8;
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc, ++e) {
+            s_col[e] = m[0].c[cc] + sx * (m[1].c[b] + sy * m[2].c[a]);
+            s_val[e] = m[2].w[a] * (m[1].w[b] * m[0].w[cc]);
+          }
+      rp[r] = 8 * r;
+      if (r == rows - 1) rp[rows] = 8 * rows;
+    }
+    __syncthreads();
+    const int64_t base = 8 * (int64_t)r0;
+    for (int e = threadIdx.x; e < nr * 8; e += kMapThreads) {
+      ci[base + e] = s_col[e];
+      va[base + e] = s_val[e];
+    }
+    __syncthreads();  // the staging buffers are refilled by the next tile
+  }
+}
+
+template <bool RESTRICT>
+rb_status launch_refine_map(const GridDev& g, int32_t* rp, int32_t* ci, double* va, cudaStream_t s) {
+  const int64_t rows = (int64_t)map_len<RESTRICT>(g, 0) * map_len<RESTRICT>(g, 1) * map_len<RESTRICT>(g, 2);
+  const int64_t tiles = (rows + kMapThreads - 1) / kMapThreads;
+  const size_t tab = sizeof(AxisMap) * (size_t)(map_len<RESTRICT>(g, 0) + map_len<RESTRICT>(g, 1) + map_len<RESTRICT>(g, 2));
+  if (tab <= kMapTabMax) {
+    auto* kern = &k_refine_map<RESTRICT, true>;
+    kern<<<wave_grid(kern, tiles, tab, kMapThreads), kMapThreads, tab, s>>>(g, rp, ci, va);
+  } else {
+    k_refine_map<RESTRICT, false><<<(unsigned)tiles, kMapThreads, 0, s>>>(g, rp, ci, va);
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
 }  // namespace
 }  // namespace rb
 
@@ -501,4 +648,26 @@ extern "C" rb_status rb_mesh_cot_laplacian(int32_t n_vert, const double* points,
   k_cot_rows<<<(n_vert + 255) / 256, 256, 0, s>>>(n_vert, row_ptr, col_idx, vals, cl, bad);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
+}
+
+extern "C" rb_status rb_refine_assemble(const rb_grid_desc* fine, rb_refine_kind kind, int32_t* row_ptr,
+                                        int32_t* col_idx, double* vals, rb_stream_t stream) {
+  clear_error();
+  RB_REQUIRE(fine != nullptr, "rb_refine_assemble: null grid");
+  RB_REQUIRE(kind == RB_REFINE_PROLONG || kind == RB_REFINE_RESTRICT, "rb_refine_assemble: unknown kind %d", (int)kind);
+  GridDev g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = fine->n[d];
+    g.per[d] = fine->periodic[d] ? 1 : 0;
+    g.nodes[d] = fine->nodes[d];
+    RB_REQUIRE(g.n[d] >= 4 && g.n[d] % 2 == 0, "rb_refine_assemble: axis %d has %d cells (need an even number >= 4)",
+               d, g.n[d]);
+    RB_REQUIRE(g.nodes[d] != nullptr, "rb_refine_assemble: null nodes[%d]", d);
+  }
+  const int64_t n_fine = (int64_t)g.n[0] * g.n[1] * g.n[2];
+  RB_REQUIRE(8 * n_fine <= INT32_MAX, "rb_refine_assemble: grid too large for int32 CSR indexing");
+  RB_REQUIRE(row_ptr && col_idx && vals, "rb_refine_assemble: null output array");
+  cudaStream_t s = S(stream);
+  if (kind == RB_REFINE_PROLONG) return launch_refine_map<false>(g, row_ptr, col_idx, vals, s);
+  return launch_refine_map<true>(g, row_ptr, col_idx, vals, s);
 }

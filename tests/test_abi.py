@@ -92,6 +92,29 @@ def test_stencil_validation_without_gpu(lib):
     assert lib.rb_stencil_assemble(None, None, 13, 1.0, None, None, None, None) == rb.RB_EINVAL
 
 
+def test_refine_validation_without_gpu(lib):
+    """rb_refine_assemble refuses odd or small axes, null node arrays and unknown kinds first."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+
+    nodes = (C.c_double * 9)(*range(9))
+    for n, kind, msg in (((8, 7, 8), 0, b"even number"), ((8, 2, 8), 1, b"even number"), ((8, 8, 8), 2, b"unknown kind"),
+                         ((8, 8, 8), 0, b"null output")):
+        g = rb.GridDesc()
+        for d in range(3):
+            g.n[d] = n[d]
+            g.periodic[d] = 1
+            g.nodes[d] = C.addressof(nodes)
+        assert lib.rb_refine_assemble(C.byref(g), kind, None, None, None, None) == rb.RB_EINVAL
+        assert msg in lib.rb_last_error(), (n, kind, lib.rb_last_error())
+    g = rb.GridDesc()
+    for d in range(3):
+        g.n[d] = 8
+    assert lib.rb_refine_assemble(C.byref(g), 0, None, None, None, None) == rb.RB_EINVAL
+    assert b"null nodes" in lib.rb_last_error()
+
+
 def test_fvm_sizes_match_oracle(lib):
     """Row, column and nonzero counts of the device builder equal the oracle's (no GPU work)."""
     import ctypes as C
