@@ -6,13 +6,15 @@ path; the only module both sides use is ``workloads`` (seeded inputs, no arithme
 the method).
 
 Contents, each function citing the passage of the paper it follows:
-  * ``fvm``     staggered symmetry-preserving FVM operators M, G, L (Sec. 3, Eq. (ns); Sec. 4)
+  * ``fvm``     staggered symmetry-preserving FVM operators M, G, L and the cell-to-face
+                interpolator (Sec. 3, Eq. (ns); Sec. 4)
   * ``spmm``    SpMM over k right-hand sides (Sec. 2, Eq. (1) and Algorithm 1)
   * ``cg``      Jacobi-preconditioned CG per column, FP32-inner iterative refinement,
                 batched uneven systems (Poisson solve of the projection method, Sec. 4)
   * ``stencil`` 13p and 27p Laplacians on uniform periodic grids (the denser patterns of Sec. 4.1)
   * ``refine``  coarse-to-fine prolongation and volume-weighted restriction of cell fields
                 (inline mesh refinement, Sec. 3.3)
+  * ``flow``    one Heun RK3 projection step of Eq. (ns) on m stacked flow states (Secs. 3, 4)
   * ``mesh``    cotangent-weight Laplacian of a triangle mesh and its periodic extrusion
                 (repeated geometries, Sec. 2; airfoil case, Sec. 4.3)
   * ``bounds``  arithmetic-intensity and speed-up models (Eqs. (ai), (pmspmm), (poipm), (pmite),

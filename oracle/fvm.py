@@ -99,6 +99,30 @@ def divergence(grid) -> sp.csr_matrix:
     return M
 
 
+def interpolation(grid) -> sp.csr_matrix:
+    """Gamma_{c->s} (faces x cells): the mean of the two cells of each face, the cell-to-face
+    interpolator of Eq. (ns) (u_s = Gamma u_c) and of the convective operator C = M U_s Gamma."""
+    mi, pl, _, _ = faces(grid)
+    nf = mi.shape[0]
+    f = np.arange(nf)
+    I = sp.csr_matrix((np.full(2 * nf, 0.5), (np.concatenate([f, f]), np.concatenate([mi, pl]))),
+                      shape=(nf, grid.n_cells))
+    I.sort_indices()
+    return I
+
+
+def face_blocks(grid):
+    """(first face, count) of the x, y and z faces in the face numbering."""
+    out, start = [], 0
+    for d, a in enumerate(grid.axes):
+        nd = 1
+        for e, b in enumerate(grid.axes):
+            nd *= (b.n if (e != d or b.periodic) else b.n - 1)
+        out.append((start, nd))
+        start += nd
+    return out
+
+
 def staggered_volumes(grid) -> np.ndarray:
     """Omega_s: the face control volumes A_f d_f."""
     _, _, A, d = faces(grid)
