@@ -271,6 +271,7 @@ def run_ours(args, rank, world, local):
         out["blas1"] = blas1(torch, rb, dev, g.n_cells, hbm)
         out["stencils"] = stencils(torch, rb, dev, hbm)
         out["refine"] = refine_maps(torch, rb, dev, hbm)
+        out["projection"] = projection(torch, rb, dev)
         del ops, step_items
         torch.cuda.empty_cache()
         out["batch"] = batch_bench(torch, rb, dev)
@@ -396,6 +397,55 @@ def refine_maps(torch, rb, dev, hbm):
             del op
         del rp, ci, va
     torch.cuda.empty_cache()
+    return res
+
+
+FLOW_N = 128  # the periodic 128^3 box of the batched systems, here in 2 pi units
+
+
+def projection(torch, rb, dev):
+    """Heun RK3 projection steps of Eq. (ns) on m = 1, 2, 4, 8 stacked flow states (the
+    paper's ensemble of Sec. 3.1) in the periodic 2 pi box of 128^3 cells: Taylor-Green
+    vortices of amplitude 1 + 0.1 s plus seeded noise of 0.01, nu = 0.01, dt = 0.01, the
+    Poisson solves by the FP32-inner refinement to 1e-10 from the previous step's pressure.
+    One warm-up step, then three timed (host clock around synchronised steps: every solve
+    synchronises to read its report).  Reports ms per step, the Poisson share and the speed-up
+    of one m-state step over m single-state steps (the iteration speed-up of Eq. (pmite))."""
+    import math
+
+    from paper_2508_06710_gb300.flow_step import ProjectionStep
+
+    n, nu, dt = FLOW_N, 0.01, 0.01
+    L = 2 * math.pi
+    nodes = [torch.linspace(0.0, L, n + 1, dtype=torch.float64, device=dev) for _ in range(3)]
+    cells = n ** 3
+    h = L / n
+    c = (torch.arange(n, dtype=torch.float64, device=dev) + 0.5) * h
+    z, y, x = torch.meshgrid(c, c, c, indexing="ij")
+    su, sv = (torch.sin(x) * torch.cos(y)).reshape(-1), (-torch.cos(x) * torch.sin(y)).reshape(-1)
+    res = {"grid": f"periodic {n}^3, 2 pi", "nu": nu, "dt": dt, "steps": 3, "states": []}
+    base = None
+    for m in (1, 2, 4, 8):
+        stepper = ProjectionStep(torch, nodes, m, nu, dt, mixed=2)
+        u = torch.as_tensor(0.01 * W.normal((cells, 3 * m), 1900 + m), device=dev)
+        for s in range(m):
+            u[:, s] += (1 + 0.1 * s) * su
+            u[:, m + s] += (1 + 0.1 * s) * sv
+        us = torch.zeros((3 * cells, m), dtype=torch.float64, device=dev)
+        stepper.step(u, us)
+        torch.cuda.synchronize()
+        stepper.poisson_ms, stepper.iters = 0.0, []
+        t0 = time.perf_counter()
+        for _ in range(3):
+            stepper.step(u, us)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / 3
+        base = ms if m == 1 else base
+        res["states"].append({"m": m, "ms_per_step": ms, "ms_per_state_step": ms / m,
+                              "poisson_share": stepper.poisson_ms / 3 / ms, "solve_iters": stepper.iters,
+                              "speedup_vs_m_single": m * base / ms})
+        del stepper, u, us
+        torch.cuda.empty_cache()
     return res
 
 

@@ -86,7 +86,15 @@ rb_status rb_fma_peak(rb_dtype dtype, double* tflops, rb_stream_t stream);
  *                      minus their sum on the diagonal (symmetric, zero row sums).
  * Requirements: n[d] >= 3 on a periodic axis, n[d] >= 2 between walls.
  * ------------------------------------------------------------------------------------ */
-typedef enum { RB_FVM_LAPLACIAN = 0, RB_FVM_DIVERGENCE = 1, RB_FVM_GRADIENT = 2 } rb_fvm_kind;
+typedef enum {
+  RB_FVM_LAPLACIAN = 0,
+  RB_FVM_DIVERGENCE = 1,
+  RB_FVM_GRADIENT = 2,
+  RB_FVM_INTERP_C2S = 3, /* Gamma_{c->s} (faces x cells): 1/2 on the two cells of each face, the
+                            cell-to-face interpolator of Eq. (ns) and of C = M U_s Gamma */
+  RB_FVM_INTERP_S2C = 4  /* Gamma_{c->s}^T (cells x faces): 1/2 on each face of a cell; the
+                            face-to-cell interpolator on grids with equal cell and face volumes */
+} rb_fvm_kind;
 
 typedef struct {
   int32_t n[3];

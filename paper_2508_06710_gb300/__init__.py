@@ -22,7 +22,7 @@ STATUS_NAMES = ["RB_OK", "RB_EINVAL", "RB_ENOMEM", "RB_ECUDA", "RB_ENOCONV", "RB
                 "RB_EUNSUPPORTED"]
 RB_F64, RB_F32 = 0, 1
 RB_CSR, RB_SELL, RB_AUTO = 0, 1, 2
-RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT = 0, 1, 2
+RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT, RB_FVM_INTERP_C2S, RB_FVM_INTERP_S2C = 0, 1, 2, 3, 4
 RB_STENCIL_13P, RB_STENCIL_27P = 13, 27
 RB_REFINE_PROLONG, RB_REFINE_RESTRICT = 0, 1
 RB_MAX_K = 64

@@ -16,6 +16,7 @@
 //     x coarse cells) and restriction R (coarse x fine) between a grid and its 2:1 coarsening
 //     (every other node), 8 entries per row in both, so again no scan.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -187,7 +188,8 @@ __device__ __forceinline__ void laplacian_row(const GridDev& g, const Geom& G, d
     }
 }
 
-template <class Geom>
+// HALF: the face-to-cell interpolator (1/2 on each face of the cell) instead of +-A_f
+template <class Geom, bool HALF = false>
 __device__ __forceinline__ void divergence_row(const GridDev& g, const Geom& G, double scale, int32_t* __restrict__ rp,
                                                int32_t* __restrict__ ci, double* __restrict__ va, int64_t id,
                                                int64_t obase = 0) {
@@ -205,9 +207,9 @@ __device__ __forceinline__ void divergence_row(const GridDev& g, const Geom& G, 
     const bool has_m = g.per[d] || t > 0, has_p = g.per[d] || t < g.n[d] - 1;
     const int tp = (t == g.n[d] - 1) ? 0 : t + 1;
     col[2 * d] = has_m ? face_index(g, d, c, t) : INT64_MAX;
-    val[2 * d] = -A;
+    val[2 * d] = HALF ? 0.5 : -A;
     col[2 * d + 1] = has_p ? face_index(g, d, c, tp) : INT64_MAX;
-    val[2 * d + 1] = A;
+    val[2 * d + 1] = HALF ? 0.5 : A;
     cnt += (int)has_m + (int)has_p;
   }
   sort_pairs<6>(col, val);
@@ -220,8 +222,9 @@ __device__ __forceinline__ void divergence_row(const GridDev& g, const Geom& G, 
     }
 }
 
-// the face's two cells for a compile-time direction (every index a constant: no local arrays)
-template <int DIR, class Geom>
+// the face's two cells for a compile-time direction (every index a constant: no local arrays);
+// HALF: the cell-to-face interpolator (1/2 on both cells) instead of -+1/d_f
+template <int DIR, bool HALF, class Geom>
 __device__ __forceinline__ void gradient_face(const GridDev& g, const Geom& G, double scale, int32_t* __restrict__ rp,
                                               int32_t* __restrict__ ci, double* __restrict__ va, int64_t f,
                                               int64_t local) {
@@ -237,29 +240,31 @@ __device__ __forceinline__ void gradient_face(const GridDev& g, const Geom& G, d
   const int64_t base = c[0] * sx + c[1] * sy + c[2] * sz - (int64_t)c[DIR] * (DIR == 0 ? sx : DIR == 1 ? sy : sz);
   const int64_t sd = DIR == 0 ? sx : DIR == 1 ? sy : sz;
   const int64_t idm = base + lo * sd, idp = base + p * sd;
-  const double inv = G.icd(DIR, p);  // scale / d_f
+  const double inv = HALF ? 0.5 * scale : G.icd(DIR, p);  // scale / d_f
+  const double vm = HALF ? inv : -inv;
   const int64_t s = 2 * f;
   rp[f] = (int32_t)s;
   if (idm < idp) {
-    ci[s] = (int32_t)idm, va[s] = -inv;
+    ci[s] = (int32_t)idm, va[s] = vm;
     ci[s + 1] = (int32_t)idp, va[s + 1] = inv;
   } else {
     ci[s] = (int32_t)idp, va[s] = inv;
-    ci[s + 1] = (int32_t)idm, va[s + 1] = -inv;
+    ci[s + 1] = (int32_t)idm, va[s + 1] = vm;
   }
 }
 
-template <class Geom>
+template <class Geom, bool HALF = false>
 __device__ __forceinline__ void gradient_row(const GridDev& g, const Geom& G, double scale, int32_t* __restrict__ rp,
                                              int32_t* __restrict__ ci, double* __restrict__ va, int64_t f) {
   const int64_t n0 = (int64_t)face_dim(g, 0, 0) * face_dim(g, 0, 1) * face_dim(g, 0, 2);
   const int64_t n1 = (int64_t)face_dim(g, 1, 0) * face_dim(g, 1, 1) * face_dim(g, 1, 2);
-  if (f < n0) gradient_face<0>(g, G, scale, rp, ci, va, f, f);
-  else if (f < n0 + n1) gradient_face<1>(g, G, scale, rp, ci, va, f, f - n0);
-  else gradient_face<2>(g, G, scale, rp, ci, va, f, f - n0 - n1);
+  if (f < n0) gradient_face<0, HALF>(g, G, scale, rp, ci, va, f, f);
+  else if (f < n0 + n1) gradient_face<1, HALF>(g, G, scale, rp, ci, va, f, f - n0);
+  else gradient_face<2, HALF>(g, G, scale, rp, ci, va, f, f - n0 - n1);
 }
 
-enum FvmKernelKind { FK_LAP = 0, FK_DIV = 1, FK_GRAD = 2 };
+// FK_C2S has the gradient's pattern and FK_S2C the divergence's, with 1/2 for every entry
+enum FvmKernelKind { FK_LAP = 0, FK_DIV = 1, FK_GRAD = 2, FK_C2S = 3, FK_S2C = 4 };
 
 constexpr int kFvmThreads = 256;
 
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(kFvmThreads) k_fvm(GridDev g, double scale, in
                                                      int64_t nnz) {
   extern __shared__ double geom_smem[];
   if (blockIdx.x == 0 && threadIdx.x == 0) rp[rows] = (int32_t)nnz;
-  constexpr bool kStage = TAB && KIND != FK_GRAD;
+  constexpr bool kStage = TAB && KIND != FK_GRAD && KIND != FK_C2S;
   constexpr int kPer = KIND == FK_LAP ? 7 : 6;
   auto body = [&](const auto& G, double* s_va, int32_t* s_ci) {
     for (int64_t r0 = (int64_t)blockIdx.x * kFvmThreads; r0 < rows; r0 += (int64_t)gridDim.x * kFvmThreads) {
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(kFvmThreads) k_fvm(GridDev g, double scale, in
         const int64_t end = r0 + kFvmThreads >= rows ? nnz : row_start<KIND>(g, r0 + kFvmThreads);
         if (id < rows) {
           if constexpr (KIND == FK_LAP) laplacian_row(g, G, scale, rp, s_ci, s_va, id, base);
-          else divergence_row(g, G, scale, rp, s_ci, s_va, id, base);
+          else divergence_row<std::decay_t<decltype(G)>, KIND == FK_S2C>(g, G, scale, rp, s_ci, s_va, id, base);
         }
         __syncthreads();
         for (int e = threadIdx.x; e < (int)(end - base); e += kFvmThreads) {
@@ -302,13 +307,15 @@ __global__ void __launch_bounds__(kFvmThreads) k_fvm(GridDev g, double scale, in
         __syncthreads();
       } else if (id < rows) {
         if constexpr (KIND == FK_LAP) laplacian_row(g, G, scale, rp, ci, va, id);
-        else if constexpr (KIND == FK_DIV) divergence_row(g, G, scale, rp, ci, va, id);
-        else gradient_row(g, G, scale, rp, ci, va, id);
+        else if constexpr (KIND == FK_DIV || KIND == FK_S2C)
+          divergence_row<std::decay_t<decltype(G)>, KIND == FK_S2C>(g, G, scale, rp, ci, va, id);
+        else gradient_row<std::decay_t<decltype(G)>, KIND == FK_C2S>(g, G, scale, rp, ci, va, id);
       }
     }
   };
-  // L and G take the scale into their reciprocal distances; M multiplies its areas by it
-  const double icd_scale = KIND == FK_DIV ? 1.0 : scale;
+  // L and G take the scale into their reciprocal distances; M and the interpolators multiply
+  // their entries by it
+  const double icd_scale = (KIND == FK_LAP || KIND == FK_GRAD) ? scale : 1.0;
   if constexpr (TAB) {
     const GeomTab G = build_geom_tab(g, geom_smem, icd_scale);
     double* s_va = geom_smem + 2 * (g.n[0] + g.n[1] + g.n[2]);
@@ -429,7 +436,7 @@ rb_status launch_fvm(const GridDev& g, double scale, int32_t* rp, int32_t* ci, d
                      cudaStream_t s) {
   const int bs = kFvmThreads;
   const int64_t blocks = (rows + bs - 1) / bs;
-  const size_t stage = KIND == FK_GRAD ? 0 : (size_t)(KIND == FK_LAP ? 7 : 6) * bs * (8 + 4);
+  const size_t stage = (KIND == FK_GRAD || KIND == FK_C2S) ? 0 : (size_t)(KIND == FK_LAP ? 7 : 6) * bs * (8 + 4);
   const size_t smem = geom_tab_bytes(g) + stage;
   if (smem <= kGeomTabMax) {
     auto* kern = &k_fvm<KIND, true>;
@@ -603,6 +610,8 @@ extern "C" rb_status rb_fvm_csr_size(const rb_grid_desc* grid, rb_fvm_kind kind,
     case RB_FVM_LAPLACIAN: *n_rows = (int32_t)n, *n_cols = (int32_t)n, *nnz = 7 * n - walls; break;
     case RB_FVM_DIVERGENCE: *n_rows = (int32_t)n, *n_cols = (int32_t)nf, *nnz = 6 * n - walls; break;
     case RB_FVM_GRADIENT: *n_rows = (int32_t)nf, *n_cols = (int32_t)n, *nnz = 2 * nf; break;
+    case RB_FVM_INTERP_C2S: *n_rows = (int32_t)nf, *n_cols = (int32_t)n, *nnz = 2 * nf; break;
+    case RB_FVM_INTERP_S2C: *n_rows = (int32_t)n, *n_cols = (int32_t)nf, *nnz = 6 * n - walls; break;
     default: set_error("rb_fvm_csr_size: unknown kind %d", (int)kind); return RB_EINVAL;
   }
   return RB_OK;
@@ -622,6 +631,8 @@ extern "C" rb_status rb_fvm_assemble(const rb_grid_desc* grid, rb_fvm_kind kind,
     case RB_FVM_LAPLACIAN: return launch_fvm<FK_LAP>(g, scale, row_ptr, col_idx, vals, n, 7 * n - walls, s);
     case RB_FVM_DIVERGENCE: return launch_fvm<FK_DIV>(g, scale, row_ptr, col_idx, vals, n, 6 * n - walls, s);
     case RB_FVM_GRADIENT: return launch_fvm<FK_GRAD>(g, scale, row_ptr, col_idx, vals, nf, 2 * nf, s);
+    case RB_FVM_INTERP_C2S: return launch_fvm<FK_C2S>(g, scale, row_ptr, col_idx, vals, nf, 2 * nf, s);
+    case RB_FVM_INTERP_S2C: return launch_fvm<FK_S2C>(g, scale, row_ptr, col_idx, vals, n, 6 * n - walls, s);
     default: set_error("rb_fvm_assemble: unknown kind %d", (int)kind); return RB_EINVAL;
   }
 }
