@@ -144,6 +144,10 @@ class ProjectionStep:
 
     def step(self, u_c, u_s):
         """One Heun RK3 step; u_c (n, 3 m) and u_s (n_faces, m) are updated in place."""
+        f64 = self.torch.float64
+        for name, t, shape in (("u_c", u_c, (self.n, 3 * self.m)), ("u_s", u_s, (self.nf, self.m))):
+            if tuple(t.shape) != shape or t.dtype != f64 or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous float64 tensor of shape {shape}")
         self.derivative(u_c, u_s, self.F[0])
         for i in (1, 2):
             self._combine(u_c, HEUN3_A[i])

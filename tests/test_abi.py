@@ -128,7 +128,8 @@ def test_fvm_sizes_match_oracle(lib):
         for d in range(3):
             gd.n[d] = g.axes[d].n
             gd.periodic[d] = 1 if g.axes[d].periodic else 0
-        for kind, ref in ((0, fvm.laplacian(g)), (1, fvm.divergence(g)), (2, fvm.gradient(g))):
+        I = fvm.interpolation(g)
+        for kind, ref in ((0, fvm.laplacian(g)), (1, fvm.divergence(g)), (2, fvm.gradient(g)), (3, I), (4, I.T.tocsr())):
             nr, nc, nnz = C.c_int32(), C.c_int32(), C.c_int64()
             assert lib.rb_fvm_csr_size(C.byref(gd), kind, C.byref(nr), C.byref(nc), C.byref(nnz)) == 0
             assert (nr.value, nc.value, nnz.value) == (ref.shape[0], ref.shape[1], ref.nnz)
