@@ -7,7 +7,10 @@
  * builds a batched Jacobi-preconditioned CG Poisson solve on top of spmm, dot, axpy and
  * axty (the four basic operations of Sec. 1).  The k columns are the flow states of an
  * ensemble, the parameters of a multiple-parameter run (Sec. 3), or the identical planes
- * of a mesh extruded along a periodic direction (Sec. 2, repeated geometries).
+ * of a mesh extruded along a periodic direction (Sec. 2, repeated geometries).  The same
+ * build also assembles on the device the operators those solves and steps need: the FVM
+ * operators and their cell/face interpolators, the denser 13p / 27p Laplacians of Sec. 4.1,
+ * and the coarse-to-fine maps of inline mesh refinement (Sec. 3.3).
  *
  * Conventions shared by every call
  *   - Dense blocks are row-major with the k columns of one row next to each other (the
