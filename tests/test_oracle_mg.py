@@ -1,0 +1,51 @@
+"""Pins of the geometric-multigrid-preconditioned CG oracle (the multigrid hierarchy of Sec. 4
+and Appendix A, built geometrically): the V-cycle is a symmetric positive semi-definite
+operator (so CG may use it), its iteration count does not grow with the grid while plain
+CG's does, and it reaches the plain CG solution."""
+import numpy as np
+
+import workloads as W
+from oracle import cg as ocg
+from oracle import mg
+
+
+def test_vcycle_is_symmetric_positive():
+    g = W.Grid((W.uniform_axis(8, 1.0), W.uniform_axis(8, 2.0), W.uniform_axis(8, 1.5)))
+    lv = mg.hierarchy(g)
+    assert len(lv) == 2
+    n = g.n_cells
+    Pi = np.eye(n) - 1.0 / n
+    B = np.column_stack([mg.vcycle(lv, Pi[:, i]) for i in range(n)])
+    assert np.abs(B - B.T).max() <= 1e-9 * np.abs(B).max()
+    w = np.linalg.eigvalsh(0.5 * (B + B.T))
+    assert w.min() >= -1e-9 * w.max()
+    assert np.sum(w > 1e-9 * w.max()) == n - 1  # only the constants in the null space
+
+
+def test_iterations_do_not_grow_with_the_grid():
+    mg_its, cg_its = [], []
+    for n in (8, 16, 32):
+        g = W.unit_periodic_grid(n)
+        lv = mg.hierarchy(g)
+        b = W.zero_mean(W.normal((g.n_cells, 1), 20 + n))[:, 0]
+        x, it = mg.mg_pcg(lv, b)
+        xr, info = ocg.pcg(lv[0].A, b, rtol=1e-10, project_mean=True)
+        assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+        r = b - lv[0].A @ x
+        assert np.linalg.norm(r - r.mean()) <= 1e-10 * np.linalg.norm(b)
+        mg_its.append(it)
+        cg_its.append(info.iters)
+    assert max(mg_its) <= 15 and max(mg_its) - min(mg_its) <= 2, mg_its
+    assert cg_its[2] >= 3 * cg_its[0], cg_its  # plain CG grows like 1/h
+
+
+def test_walled_stretched_grid():
+    """The channel shape (walls and tanh stretching in y): fewer iterations than plain CG."""
+    g = W.channel_grid(32, 16, 24)
+    lv = mg.hierarchy(g)
+    assert len(lv) == 3
+    b = W.zero_mean(W.normal((g.n_cells, 1), 33))[:, 0]
+    x, it = mg.mg_pcg(lv, b)
+    xr, info = ocg.pcg(lv[0].A, b, rtol=1e-10, project_mean=True)
+    assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+    assert it * 4 <= info.iters, (it, info.iters)
