@@ -163,6 +163,7 @@ def run_ours(args, rank, world, local):
     rbbuild.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    torch.manual_seed(2508_06710 + rank)  # the sweeps' N(0,1) blocks (torch.randn) are seeded too
     stream = torch.cuda.current_stream()
     g, ops = build_ops(rb, torch, dev)
     hbm, hbm_src = peaks()
