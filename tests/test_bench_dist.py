@@ -51,3 +51,17 @@ def test_reference_slices_cover_the_operator():
     sl = bench.reference_slices([(A, 3)], 7)[0]
     assert len(sl) == 7 and sum(s.shape[0] for s, _ in sl) == 103
     assert sum(s.nnz for s, _ in sl) == A.nnz
+
+
+def test_reference_arm_line():
+    """The reference arm's JSON fields on one step (rank 0, N = 1): the oracle on host cores."""
+    out = bench.run_reference(type("A", (), {"steps": 1, "warmup": 0})(), 0, 1)
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "config", "cpu_baseline", "e2e"):
+        assert key in out, key
+    assert out["impl"] == "reference" and out["metric"] == bench.METRIC and out["value"] > 0
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == out["value"]
+    e2e = out["e2e"]
+    assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
