@@ -16,7 +16,8 @@ Contents, each function citing the passage of the paper it follows:
                 (inline mesh refinement, Sec. 3.3)
   * ``flow``    one Heun RK3 projection step of Eq. (ns) on m stacked flow states (Secs. 3, 4)
   * ``mg``      geometric-multigrid-preconditioned CG (V-cycle over 2:1 coarsenings; the
-                multigrid preconditioning of Sec. 4 and Appendix A, built geometrically)
+                multigrid preconditioning of Sec. 4 and Appendix A, built geometrically) and
+                block CG over the k columns (Sec. 5.1)
   * ``mesh``    cotangent-weight Laplacian of a triangle mesh and its periodic extrusion
                 (repeated geometries, Sec. 2; airfoil case, Sec. 4.3)
   * ``bounds``  arithmetic-intensity and speed-up models (Eqs. (ai), (pmspmm), (poipm), (pmite),

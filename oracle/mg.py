@@ -1,4 +1,5 @@
-"""Geometric-multigrid-preconditioned CG for the Poisson matrix A = -L (FP64).
+"""Stronger Poisson solvers for A = -L (FP64): geometric-multigrid-preconditioned CG, and block
+CG over the k columns.
 
 The paper solves its Poisson equations with CG preconditioned by an algebraic multigrid
 (Sec. 4, Chronos' aAMG) and reports, in Appendix A, the SpMMs of every level of that
@@ -17,6 +18,11 @@ hierarchy here is geometric, built from the same pieces as the rest of the metho
   * the preconditioner z = B r is one V-cycle from a zero guess; the outer iteration is
     Saad's preconditioned CG (Algorithm 9.1) with the zero-mean projection of singular
     (periodic or all-Neumann) problems.
+
+Block CG (Sec. 5.1 names block-Krylov methods as the way to share more than the matrix across
+the k columns): O'Leary's block conjugate gradient, one search block of k directions per
+iteration, the k x k systems solved by a pseudo-inverse so that converged or dependent
+directions do no harm.
 
 Test infrastructure only; see the package docstring.
 """
@@ -97,3 +103,31 @@ def mg_pcg(levels, b: np.ndarray, rtol: float = 1e-10, max_iter: int = 500, proj
         p = z + (rz_new / rz) * p
         rz = rz_new
     return _project(x, project_mean), max_iter
+
+
+def block_cg(A, B: np.ndarray, rtol: float = 1e-10, max_iter: int = 1000, project_mean: bool = False):
+    """O'Leary's block CG on A X = B (no preconditioner): X, iterations.  Stops when every
+    column's true residual is below rtol times its right-hand side."""
+    B = np.asarray(B, dtype=np.float64)
+    if project_mean:
+        B = B - B.mean(axis=0, keepdims=True)
+    nb = np.linalg.norm(B, axis=0)
+    X = np.zeros_like(B)
+    R = B.copy()
+    P = R.copy()
+    RR = R.T @ R
+    for it in range(1, max_iter + 1):
+        Q = A @ P
+        alpha = np.linalg.pinv(P.T @ Q) @ RR
+        X = X + P @ alpha
+        R = R - Q @ alpha
+        T = B - A @ X
+        if project_mean:
+            T = T - T.mean(axis=0, keepdims=True)
+        if np.all(np.linalg.norm(T, axis=0) <= rtol * np.where(nb > 0, nb, 1.0)):
+            return X, it
+        RR_new = R.T @ R
+        beta = np.linalg.pinv(RR) @ RR_new
+        P = R + P @ beta
+        RR = RR_new
+    return X, max_iter

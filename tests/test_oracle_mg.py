@@ -49,3 +49,34 @@ def test_walled_stretched_grid():
     xr, info = ocg.pcg(lv[0].A, b, rtol=1e-10, project_mean=True)
     assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
     assert it * 4 <= info.iters, (it, info.iters)
+
+
+def test_block_cg_terminates_in_ceil_n_over_k():
+    """With n distinct eigenvalues and k random right-hand sides the block Krylov space (k new
+    directions per iteration) fills after ceil(n / k) iterations: block CG stops there,
+    single-column CG after n.  (With eigenvalues of multiplicity >= k the invariant subspace
+    holding B has dimension k per eigenvalue and there is no such gain.)"""
+    import scipy.sparse as sp
+
+    n = 24
+    lam = 1.0 + np.arange(n) ** 1.5
+    Q, _ = np.linalg.qr(W.normal((n, n), 40))
+    A = sp.csr_matrix(Q @ np.diag(lam) @ Q.T)
+    for k in (1, 3, 4, 6):
+        B = W.normal((n, k), 41 + k)
+        X, it = mg.block_cg(A, B, rtol=1e-9)
+        assert it <= -(-n // k), (k, it)
+        assert np.allclose(A @ X, B, atol=1e-8 * np.abs(B).max())
+
+
+def test_block_cg_matches_columnwise_cg_on_poisson():
+    """Same solutions as k separate CG solves, in no more iterations (the periodic Laplacian's
+    eigenvalues are highly repeated, so there the block brings no finite-termination gain)."""
+    g = W.unit_periodic_grid(8)
+    A = (-mg.fvm.laplacian(g)).tocsr()
+    B = W.zero_mean(W.normal((g.n_cells, 4), 42))
+    X, it = mg.block_cg(A, B, rtol=1e-10, project_mean=True)
+    Xr, infos = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True, jacobi=False)
+    X = X - X.mean(axis=0, keepdims=True)
+    assert np.all(np.linalg.norm(X - Xr, axis=0) <= 1e-8 * np.linalg.norm(Xr, axis=0))
+    assert it <= max(i.iters for i in infos)
