@@ -61,9 +61,9 @@ FP64_PEAK_TFLOPS = 1.25
 
 
 # DRAM traffic (read + write) per launch of the dominant kernel, from one ncu capture of the
-# step (profiles/spmm_step_channel192x128x96_launches.md), valid only for the SpMM sources it was
-# taken with: the fingerprint of those sources is checked at run time, and traffic is null
-# (not measured for this build) when they have changed.
+# timed step, valid only for the SpMM sources it was taken with: the fingerprint of those
+# sources is checked at run time, and traffic is null (not measured for this build) when they
+# have changed.
 SPMM_SOURCES = ['spmm_impl.cuh', 'spmm_kernels.cuh', 'spmm_f64.cu', 'spmm_f32.cu', 'spmm_tma.cuh', 'common.cuh', 'tma.cuh', 'spmm.cu']
 TRAFFIC = {"L-f64-k3": (264_989_952 + 42_116_608, "e7f84975ace965f4")}
 
@@ -147,9 +147,10 @@ def build_ops(rb, torch, dev):
         for dt in ("f64", "f32"):
             ops[(name, dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, k_max=32), k)
             ops[(name + "-sell", dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, fmt="sell", k_max=32), k)
-        if name == "L":
-            ops[("A", "f64")] = (rb.Operator(rp, ci, -va, nc, dtype="f64", k_max=3), 3)
-            ops[("A", "f32")] = (rb.Operator(rp, ci, -va, nc, dtype="f32", k_max=3), 3)
+        if name == "L":  # the Poisson matrix A = -L, assembled with scale -1
+            rp, ci, va, nc = rb.fvm_assemble(nodes, per, kind, scale=-1.0)
+            ops[("A", "f64")] = (rb.Operator(rp, ci, va, nc, dtype="f64", k_max=3), 3)
+            ops[("A", "f32")] = (rb.Operator(rp, ci, va, nc, dtype="f32", k_max=3), 3)
     torch.cuda.synchronize()
     return g, ops
 
@@ -758,8 +759,7 @@ def poisson(torch, rb, ops, g, dev):
     Mop, _ = ops[("M", "f64")]
     U = torch.as_tensor(W.face_field(Mop.n_cols, k, 2002), device=dev)
     B = torch.empty((Mop.n_rows, k), dtype=torch.float64, device=dev)
-    Mop.spmm(U, B)
-    B.neg_()
+    Mop.spmm(U, B, c=torch.full((k,), -1.0, dtype=torch.float64, device=dev))  # b = -M u
     out = {"k": k, "rtol": 1e-10}
     for name, mixed, pers in (("fp64_cg", 0, False), ("ir_fp32_inner", 2, False),
                               ("ir_fp32_inner_persistent", 2, True), ("ir_fp32_inner_restarted", 1, False)):
@@ -947,6 +947,68 @@ def run_reference(args, rank, world, budget_s=120.0):
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                 "vs_baseline", "dtype", "data", "config", "gpu_launches", "clocks")
+
+
+def _pick(d, keys):
+    return {k: d[k] for k in keys if d is not None and k in d}
+
+
+def _round(v, digits=4):
+    """Floats of a nested summary to `digits` significant digits (keeps the line short)."""
+    if isinstance(v, float):
+        return float(f"{v:.{digits}g}")
+    if isinstance(v, dict):
+        return {k: _round(x, digits) for k, x in v.items()}
+    if isinstance(v, list):
+        return [_round(x, digits) for x in v]
+    return v
+
+
+def headline(out, detail_path):
+    """The one short JSON line that ends stdout: the headline metric with its roofline, e2e,
+    cpu_baseline and clocks, plus a few figures of the secondary sections; every section in
+    full goes to `detail_path`."""
+    h = _pick(out, HEADLINE_KEYS)
+    if "roofline" in out:
+        h["roofline"] = _pick(out["roofline"], ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                                "peak_source", "peak_measured", "frac_of_measured", "hbm_frac_of_measured"))
+    if "e2e" in out:
+        h["e2e"] = _pick(out["e2e"], ("value", "unit", "ms_per_step", "h2d_bytes_per_step", "d2h_bytes_per_step"))
+    if "cpu_baseline" in out:
+        cb = out["cpu_baseline"]
+        h["cpu_baseline"] = _pick(cb, ("value", "unit", "cores", "kind", "sample"))
+        if "all_cores" in cb:
+            h["cpu_baseline"]["all_cores"] = _pick(cb["all_cores"], ("value", "cores"))
+    s = {}
+    if "kernels" in out:
+        s["kernel_ms"] = {r["kernel"]: round(r["ms"] * 1e3, 2) for r in out["kernels"]}
+        s["kernel_ms_unit"] = "us"
+    if "overlapped_step" in out:
+        s["overlapped_step_gflops"] = out["overlapped_step"].get("value")
+    p = out.get("poisson")
+    if p:
+        s["poisson_ms"] = {k: v["ms"] for k, v in p.items() if isinstance(v, dict) and "ms" in v}
+    mg = out.get("multigrid")
+    if mg:
+        s["multigrid_ms"] = {r["case"]: r["ms"] for r in mg.get("runs", []) if "case" in r and "ms" in r}
+    b = out.get("batch")
+    if b:
+        s["batch_graph_ms"] = b.get("batch_graph_ms")
+        s["batch_sequential_fp64_cg_ms"] = b.get("sequential_fp64_cg_ms")
+    lg = out.get("learned_guess")
+    if lg and "eval" in lg:
+        s["learned_guess_ms_per_system"] = {k: v.get("ms_per_system") for k, v in lg["eval"].items()
+                                            if isinstance(v, dict) and "ms_per_system" in v}
+    ks = out.get("ksweep")
+    if ks:
+        s["ksweep_frac_hbm_csr"] = {f"{r['dtype']}-k{r['k']}": round(r["frac_hbm"], 3) for r in ks if r["format"] == "csr"}
+    h["summary"] = _round(s)
+    h["detail"] = os.path.relpath(detail_path, ROOT) if os.path.isabs(detail_path) else detail_path
+    return h
+
+
 def max_over_ranks(torch, value, world, dev=None):
     """The largest `value` over all ranks (the timing rule of a replicated run)."""
     if world <= 1:
@@ -1021,7 +1083,7 @@ def profile_run(args):
         Mop, _ = ops[("M", "f64")]
         for k in (1, 3):
             U = torch.as_tensor(W.face_field(Mop.n_cols, k, 2002), device=dev)
-            B = Mop.spmm(U).neg_()
+            B = Mop.spmm(U, c=torch.full((k,), -1.0, dtype=torch.float64, device=dev))
             for mixed in (False, True):
                 prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, max_iter=20, check_every=10)
                 X = torch.zeros((Mop.n_rows, k), dtype=torch.float64, device=dev)
@@ -1053,6 +1115,8 @@ def main():
                          "training pass of the learned-guess network at 128^3 (NVTX 'predict', 'loss_grad'), "
                          "'spmm' = three channel-Laplacian SpMMs with --profile-k columns in --profile-dtype "
                          "on the schedule --profile-sched (vec,lpr,stage,grid_cap; default: the untuned one)")
+    ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
+                    help="file receiving the full result (every section); stdout ends with the headline line only")
     ap.add_argument("--profile-k", type=int, default=32)
     ap.add_argument("--profile-dtype", default="f32", choices=["f64", "f32"])
     ap.add_argument("--profile-sched", default=None)
@@ -1074,7 +1138,12 @@ def main():
     else:
         out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:
-        print(json.dumps(out))
+        if args.impl == "reference":
+            print(json.dumps(out))
+        else:
+            with open(args.detail, "w") as f:
+                json.dump(out, f, indent=1)
+            print(json.dumps(headline(out, args.detail)))
     if world > 1:
         import torch
 

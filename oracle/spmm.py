@@ -35,21 +35,6 @@ def spmm(A: sp.csr_matrix, X: np.ndarray, c: np.ndarray | None = None) -> np.nda
     return Y
 
 
-def spmm_loops(row_ptr, col_idx, vals, X, c=None) -> np.ndarray:
-    """Algorithm 1 written out with plain loops over rows, nonzeros and columns (tiny inputs only)."""
-    n_r = len(row_ptr) - 1
-    k = X.shape[1]
-    Y = np.zeros((n_r, k), dtype=np.float64)
-    for i in range(n_r):
-        s = [0.0] * k
-        for p in range(row_ptr[i], row_ptr[i + 1]):
-            for j in range(k):
-                s[j] += float(vals[p]) * float(X[col_idx[p], j])
-        for j in range(k):
-            Y[i, j] = (1.0 if c is None else float(c[j])) * s[j]
-    return Y
-
-
 def kron_spmv(A: sp.csr_matrix, X: np.ndarray) -> np.ndarray:
     """(I_k (x) A~) applied to the column-stacked vector (x_1; ...; x_k), Eq. (1)'s left-hand side."""
     k = X.shape[1]

@@ -25,16 +25,20 @@ void clear_error() { g_err.clear(); }
 
 int resident_blocks(const void* kernel, size_t smem, int threads) {
   static std::mutex mu;
-  static std::map<std::pair<const void*, size_t>, int> cache;
-  thread_local int sms = 0;
+  static std::map<std::pair<int, std::pair<const void*, size_t>>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
   std::lock_guard<std::mutex> lock(mu);
-  auto key = std::make_pair(kernel, smem * 4096 + (size_t)threads);
+  auto key = std::make_pair(dev, std::make_pair(kernel, smem * 4096 + (size_t)threads));
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 152;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
   }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
@@ -44,6 +48,21 @@ int resident_blocks(const void* kernel, size_t smem, int threads) {
   const int v = std::min(kPersistentGrid, std::max(1, per_sm * sms));
   cache[key] = v;
   return v;
+}
+
+rb_status opt_in_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return RB_OK;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> opted;
+  int dev = 0;
+  RB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = opted[std::make_pair(dev, kernel)];
+  if (bytes > cur) {
+    RB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+  }
+  return RB_OK;
 }
 
 rb_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {

@@ -1046,12 +1046,11 @@ rb_status solve_vec(Solver& S_, const rb_cg_params& prm, const double* B, int64_
         rb_cg_params p2 = prm;
         p2.max_iter = prm.max_iter - total_inner;
         RB_TRY(persistent_inner(S_, p2, L, base));
-        unsigned done = 0;
-        RB_CUDA(cudaMemcpyAsync(&done, &S_.sc->pbar[3], sizeof(unsigned), cudaMemcpyDeviceToHost, S_.s));
+        unsigned pb[2] = {0, 0};  // pbar[2]: barrier error word, pbar[3]: iterations done
+        RB_CUDA(cudaMemcpyAsync(pb, &S_.sc->pbar[2], 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, S_.s));
         RB_CUDA(cudaStreamSynchronize(S_.s));
         ++syncs;
-        unsigned err = 0;
-        RB_CUDA(cudaMemcpy(&err, &S_.sc->pbar[2], sizeof(unsigned), cudaMemcpyDeviceToHost));
+        const unsigned err = pb[0], done = pb[1];
         if (err) {
           set_error("rb_cg_solve: a grid barrier wait of the persistent inner solve gave up");
           return RB_ETIMEOUT;

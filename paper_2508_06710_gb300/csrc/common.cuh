@@ -73,6 +73,11 @@ constexpr int kPersistentGrid = 152 * 8;  // 8 resident blocks of 256 threads on
 // register count, and never more than kPersistentGrid.
 int resident_blocks(const void* kernel, size_t smem, int threads = kThreads);
 
+// Raises `kernel`'s dynamic shared memory limit to at least `bytes` on the current device.
+// The attribute belongs to the device, so the largest value set is remembered per (device,
+// kernel); a host thread that moves to another device sets it again there.
+rb_status opt_in_smem(const void* kernel, size_t bytes);
+
 template <typename K>
 inline int wave_grid(K* kernel, int64_t work_blocks, size_t smem = 0, int threads = kThreads) {
   const int cap = resident_blocks(reinterpret_cast<const void*>(kernel), smem, threads);

@@ -1538,11 +1538,7 @@ size_t conv_smem(int np, int kpad) { return (size_t)np * kpad * 2 + (size_t)kSta
 template <int NP>
 rb_status launch_conv3_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
   auto* kern = &k_conv3_mma<NP>;
-  thread_local size_t opted = 48 * 1024;  // largest dynamic shared memory requested so far
-  if (smem > opted) {
-    RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    opted = smem;
-  }
+  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(kern), smem));
   const int n_tiles = (a.n_vox + 127) / 128;
   thread_local int per_sm = 0;
   thread_local size_t per_sm_smem = 0;
@@ -1570,11 +1566,7 @@ int head_idx(const rb_guess* g) { return 2 * g->L + 3 * (g->L - 1); }
 template <int NP, int W>
 rb_status launch_row_np(const Conv3Args& a, size_t smem, cudaStream_t s) {
   auto* kern = &k_conv3_row<NP, W>;
-  thread_local size_t opted = 48 * 1024;
-  if (smem > opted) {
-    RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    opted = smem;
-  }
+  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(kern), smem));
   thread_local int per_sm = 0;
   thread_local size_t per_sm_smem = 0;
   if (per_sm == 0 || per_sm_smem != smem) {
@@ -1688,11 +1680,7 @@ WgradPlan wgrad_plan(const Layer& ly, int n) {
 template <int NP>
 rb_status launch_wgrad_np(const WgradArgs& a, const WgradPlan& p, cudaStream_t s) {
   const size_t smem = (size_t)kStages * (kWAStage + NP * kWS * 2);
-  thread_local bool opted = false;
-  if (!opted && smem > 48 * 1024) {
-    RB_CUDA(cudaFuncSetAttribute(&k_wgrad_mma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    opted = true;
-  }
+  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(&k_wgrad_mma<NP>), smem));
   k_wgrad_mma<NP><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
@@ -1742,11 +1730,7 @@ bool wgrad_row_fits(const Layer& ly, const Dims& d) {
 template <int NP, int W>
 rb_status launch_wgrad_row_np(const WgradArgs& a, const RowWPlan& p, cudaStream_t s) {
   const size_t smem = wgrad_row_smem(NP, a.cin, W);
-  thread_local size_t opted = 48 * 1024;
-  if (smem > opted) {
-    RB_CUDA(cudaFuncSetAttribute(&k_wgrad_row<NP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    opted = smem;
-  }
+  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(&k_wgrad_row<NP, W>), smem));
   k_wgrad_row<NP, W><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a, p.per_split, p.chunk);
   RB_CUDA(cudaGetLastError());
   return RB_OK;

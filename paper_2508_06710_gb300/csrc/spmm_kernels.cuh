@@ -88,12 +88,9 @@ rb_status launch_csr(const rb_op* op, const SpmmSched& sc, const T* X, int64_t l
       auto* kern = &k_spmm_tma<T, VEC, EPI>;
       const int cap = tma_capacity<T>(op, R, kTmaSmemLimit);
       const size_t smem = tma_layout<T>(R, cap).total;
-      thread_local size_t opted = 0;  // largest dynamic shared memory requested so far (per instantiation)
-      if (smem > 48 * 1024 && smem > opted) {
-        RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemLimit));
-        opted = kTmaSmemLimit;
-      }
+      RB_TRY(opt_in_smem(reinterpret_cast<const void*>(kern), smem));
       grid = wave_grid(kern, grid, smem, kTmaThreads);
+      if (sc.grid_cap > 0) grid = std::min<int64_t>(grid, sc.grid_cap);  // fewer blocks, more tiles each
       kern<<<(unsigned)grid, kTmaThreads, smem, s>>>(a, R, cap, op->err);
       RB_CUDA(cudaGetLastError());
       return RB_OK;

@@ -54,12 +54,12 @@ def generate(torch, prob, spectra, face_fields, dev="cuda"):
     prm = cg_params(rtol=1e-10, mixed=2, project_mean=True, check_every=50)
     work = torch.empty(cg_workspace_bytes(prob["A64"], chains, prm), dtype=torch.uint8, device=dev)
     iters = []
+    neg = torch.full((chains,), -1.0, dtype=torch.float64, device=dev)  # b = -M u through the SpMM's scale
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for t in range(steps):
         U = face_fields(spectra[t], g.shape, torch, dev)
-        prob["M"].spmm(U, B)
-        B.neg_()
+        prob["M"].spmm(U, B, c=neg)
         r = cg_solve(prob["A64"], B, X, A_inner=prob["A32"], params=prm, work=work)
         iters.append(max(r.iters))
         Bs[t].copy_(B.t())

@@ -142,6 +142,52 @@ def test_spmm_tma_pipeline_channel(rb, dtype, k):
     assert ok, worst
 
 
+def _ragged_long_rows(nr, nc, seed, every=4999, long_len=3000):
+    """Random rows of ~7 nonzeros, some empty, and every `every`-th row longer than a TMA stage
+    holds, so that staged and unstaged tiles alternate along one block's walk."""
+    g = np.random.default_rng(seed)
+    lens = g.poisson(7, nr)
+    lens[::13] = 0
+    lens[every // 2::every] = long_len
+    lens = np.minimum(lens, nc)
+    ci = np.concatenate([np.sort(g.choice(nc, size=l, replace=False)) for l in lens]).astype(np.int32)
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    return sp.csr_matrix((g.standard_normal(rp[-1]), ci, rp), shape=(nr, nc))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 4, 32])
+@pytest.mark.parametrize("grid_cap", [1, 3, 7])
+def test_spmm_tma_steady_state(rb, dtype, k, grid_cap):
+    """The TMA pipeline past its first round: with the grid capped at 1, 3 or 7 blocks every
+    block walks tens to hundreds of tiles, so the 3-stage ring wraps over many phases (the
+    empty-barrier waits of the later rounds), the producer reloads the boundaries of its next
+    32 tiles many times, and staged and unstaged tiles (rows longer than a stage) alternate."""
+    nr = 90_000 if k <= 4 else 9_000
+    A = _ragged_long_rows(nr, 7_001, seed=500 + k)
+    X = W.normal((7_001, k), 510 + k)
+    c = W.normal(k, 520 + k)
+    npdt = np.float64 if dtype == "f64" else np.float32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    op = rb.Operator.from_scipy(A, dtype=dtype, k_max=k)
+    vec = 3 if k == 3 else min(k, 16 // (8 if dtype == "f64" else 4))
+    op.set_schedule(k, vec, 1, 2, grid_cap)
+    R = 256 // (1 << int(np.ceil(np.log2(k // vec))))  # rows per tile
+    tiles = -(-nr // R)
+    assert tiles // grid_cap >= 40, "each block must walk many tiles"
+    Xd = to_dev(X.astype(npdt))
+    for rep in range(2):  # the second call starts from barriers re-initialised by a new launch
+        Yd = torch.full((nr, k), float("nan"), dtype=tdt, device="cuda")
+        op.spmm(Xd, Yd, c=to_dev(c))
+        op.check()
+        Aref = A if dtype == "f64" else spmm.round_f32(A)
+        Xref = X.astype(npdt).astype(np.float64)
+        cref = c if dtype == "f64" else c.astype(np.float32).astype(np.float64)
+        ok, worst = componentwise_ok(Yd.cpu().numpy(), spmm.spmm(Aref, Xref, cref), spmm.abs_bound(Aref, Xref, cref),
+                                     TOL[dtype])
+        assert ok, (rep, worst)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_spmm_fvm_operators(rb, dtype):
     """L (k = 3, velocity components), G (k = 3) and M (k = 1) of a channel grid."""
@@ -186,6 +232,30 @@ def test_spmm_channel_full_size_k3(rb, dtype):
     A = fvm.laplacian_direct(g)
     X = W.normal((A.shape[1], 3), 2003)
     _run(rb, A, X, dtype)
+
+
+@pytest.mark.parametrize("name,k", [("G", 3), ("L", 32)])
+@pytest.mark.parametrize("sched", ["tuned", "tma"])
+def test_spmm_channel_full_size_fp32_timed_schedules(rb, name, k, sched):
+    """The FP32 SpMMs whose tuned schedule the bench times on the full 192 x 128 x 96 channel
+    (the gradient with k = 3, the Laplacian with k = 32), on the tuner's pick and forced onto
+    the TMA pipeline with one resident wave (tens of tiles per block), against the oracle."""
+    g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+    A = fvm.gradient(g) if name == "G" else fvm.laplacian_direct(g)
+    X = W.normal((A.shape[1], k), 2100 + k).astype(np.float32)
+    op = rb.Operator.from_scipy(A, dtype="f32", k_max=k)
+    Xd = to_dev(X)
+    Yd = torch.full((A.shape[0], k), float("nan"), dtype=torch.float32, device="cuda")
+    if sched == "tuned":
+        op.tune(Xd, Yd)
+    else:
+        op.set_schedule(k, 3 if k == 3 else 4, 1, 2, -1)
+    op.spmm(Xd, Yd)
+    op.check()
+    Aref = spmm.round_f32(A)
+    Xref = X.astype(np.float64)
+    ok, worst = componentwise_ok(Yd.cpu().numpy(), spmm.spmm(Aref, Xref), spmm.abs_bound(Aref, Xref), TOL["f32"])
+    assert ok, (op.schedule(Xd, Yd), worst)
 
 
 # ------------------------------------------------------------------------------- extruded

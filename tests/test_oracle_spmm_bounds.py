@@ -18,20 +18,23 @@ def _rand_csr(nr, nc, density, seed):
 
 @pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
 def test_spmm_equals_k_spmvs_and_kron(k):
-    """P4: SpMM = k SpMVs = (I_k (x) A~) x, bit for bit with the same summation order."""
+    """P4: SpMM = k SpMVs = (I_k (x) A~) x = the dense product A X diag(c), on tiny inputs."""
     A = _rand_csr(37, 29, 0.2, k)
     X = W.normal((29, k), 10 + k)
     c = W.normal(k, 20 + k)
     Y = spmm.spmm(A, X)
-    Yl = spmm.spmm_loops(A.indptr, A.indices, A.data, X)
+    Yd = A.toarray() @ X  # dense matrix product: no sparse code involved
     Yk = spmm.kron_spmv(A, X)
-    assert np.abs(Y - Yl).max() <= 1e-14 * np.abs(Yl).max()
-    assert np.abs(Y - Yk).max() <= 1e-14 * np.abs(Yl).max()
+    assert np.abs(Y - Yd).max() <= 1e-14 * np.abs(Yd).max()
+    assert np.abs(Y - Yk).max() <= 1e-14 * np.abs(Yd).max()
     Yc = spmm.spmm(A, X, c)
-    Ycl = spmm.spmm_loops(A.indptr, A.indices, A.data, X, c)
-    assert np.abs(Yc - Ycl).max() <= 1e-14 * np.abs(Ycl).max()
-    for j in range(k):  # one column at a time against a dense product
-        assert np.allclose(Yc[:, j], c[j] * (A.toarray() @ X[:, j]), rtol=1e-13, atol=1e-13)
+    assert np.abs(Yc - Yd * c[None, :]).max() <= 1e-14 * np.abs(Yd * c[None, :]).max()
+    # integer entries: every partial sum is exact, so any summation order gives the same bits
+    Ai = A.copy()
+    Ai.data = np.round(4 * Ai.data)
+    Xi = np.round(8 * X)
+    assert np.array_equal(spmm.spmm(Ai, Xi), Ai.toarray() @ Xi)
+    assert np.array_equal(spmm.kron_spmv(Ai, Xi), Ai.toarray() @ Xi)
 
 
 def test_spmm_rectangular_operators():
