@@ -149,11 +149,15 @@ rb_status rb_stencil_assemble(const int32_t n[3], const double h[3], rb_stencil_
  *                       axis weights, 8 entries per row; reproduces trilinear fields exactly.
  *   RB_REFINE_RESTRICT  R (N_c x N): the volume-weighted mean of the 8 children of each coarse
  *                       cell (keeps the integral of the field).
- * Writes into caller-allocated DEVICE arrays row_ptr[rows + 1], col_idx[8 rows],
- * vals[8 rows] (float64), rows = N (P) or N_c (R); columns sorted.  RB_EINVAL (nothing
- * launched) for an unknown kind, an odd or too small axis, a null array, or 8 N > 2^31 - 1.
- * Asynchronous on `stream`. */
-typedef enum { RB_REFINE_PROLONG = 0, RB_REFINE_RESTRICT = 1 } rb_refine_kind;
+ *   RB_REFINE_PROLONG_T P^T (N_c x N): the transpose of P, entry for entry (the same values,
+ *                       bit for bit); the restriction of residuals in the multigrid cycle of
+ *                       the Poisson solve (Sec. 4, Appendix A).  Row lengths vary (8 to 125);
+ *                       the total is the same 8 N entries.
+ * Writes into caller-allocated DEVICE arrays row_ptr[rows + 1], col_idx[8 N], vals[8 N]
+ * (float64), rows = N (P) or N_c (R, P^T); columns sorted.  RB_EINVAL (nothing launched) for
+ * an unknown kind, an odd or too small axis, a null array, 8 N > 2^31 - 1, or (P^T) more
+ * than 1900 coarse positions summed over the three axes.  Asynchronous on `stream`. */
+typedef enum { RB_REFINE_PROLONG = 0, RB_REFINE_RESTRICT = 1, RB_REFINE_PROLONG_T = 2 } rb_refine_kind;
 rb_status rb_refine_assemble(const rb_grid_desc* fine, rb_refine_kind kind, int32_t* row_ptr, int32_t* col_idx,
                              double* vals, rb_stream_t stream);
 

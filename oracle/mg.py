@@ -79,8 +79,15 @@ def vcycle(levels, r: np.ndarray, level: int = 0, nu: int = 2, omega: float = 2.
     return _project(e, project_mean)
 
 
-def mg_pcg(levels, b: np.ndarray, rtol: float = 1e-10, max_iter: int = 500, project_mean: bool = True, **kw):
-    """CG on A_0 x = b preconditioned by one V-cycle per iteration (Saad Algorithm 9.1)."""
+def mg_pcg(levels, b: np.ndarray, rtol: float = 1e-10, max_iter: int = 500, project_mean: bool = True,
+           flexible: bool = False, **kw):
+    """CG on A_0 x = b preconditioned by one V-cycle per iteration (Saad Algorithm 9.1).
+
+    flexible: take beta in the Polak-Ribiere form z_new . (r_new - r_old) / (z_old . r_old)
+    (Notay's flexible CG), which tolerates a preconditioner that is not exactly the same
+    symmetric operator at every iteration, e.g. a V-cycle run in lower precision.  With a
+    fixed symmetric preconditioner z_new . r_old = 0 in exact arithmetic, so both forms give
+    the same iterates."""
     A = levels[0].A
     b = _project(np.asarray(b, dtype=np.float64), project_mean)
     nb = np.linalg.norm(b)
@@ -98,9 +105,11 @@ def mg_pcg(levels, b: np.ndarray, rtol: float = 1e-10, max_iter: int = 500, proj
         r = r - alpha * q
         if np.linalg.norm(_project(b - A @ x, project_mean)) <= rtol * nb:
             return _project(x, project_mean), it
+        r_old = r + alpha * q
         z = vcycle(levels, r, project_mean=project_mean, **kw)
         rz_new = r @ z
-        p = z + (rz_new / rz) * p
+        beta = (z @ (r - r_old)) / rz if flexible else rz_new / rz
+        p = z + beta * p
         rz = rz_new
     return _project(x, project_mean), max_iter
 

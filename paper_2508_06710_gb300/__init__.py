@@ -24,7 +24,7 @@ RB_F64, RB_F32 = 0, 1
 RB_CSR, RB_SELL, RB_AUTO = 0, 1, 2
 RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT, RB_FVM_INTERP_C2S, RB_FVM_INTERP_S2C = 0, 1, 2, 3, 4
 RB_STENCIL_13P, RB_STENCIL_27P = 13, 27
-RB_REFINE_PROLONG, RB_REFINE_RESTRICT = 0, 1
+RB_REFINE_PROLONG, RB_REFINE_RESTRICT, RB_REFINE_PROLONG_T = 0, 1, 2
 RB_MAX_K = 64
 
 # exported C symbols, in the order include/rbspmm.h declares them
@@ -260,8 +260,9 @@ def stencil_assemble(shape, h, kind, scale=1.0, device="cuda", stream=None):
 
 def refine_assemble(nodes, periodic, kind, stream=None):
     """CSR (row_ptr, col_idx, vals, n_cols) of the prolongation (``RB_REFINE_PROLONG``, fine x
-    coarse) or restriction (``RB_REFINE_RESTRICT``, coarse x fine) between the grid whose
-    axis node coordinates are the float64 CUDA tensors ``nodes`` and its 2:1 coarsening."""
+    coarse), the restriction (``RB_REFINE_RESTRICT``, coarse x fine) or the transposed
+    prolongation (``RB_REFINE_PROLONG_T``, coarse x fine) between the grid whose axis node
+    coordinates are the float64 CUDA tensors ``nodes`` and its 2:1 coarsening."""
     torch = _torch()
     nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
     n_fine = 1
@@ -270,8 +271,8 @@ def refine_assemble(nodes, periodic, kind, stream=None):
     rows, cols = (n_fine, n_fine // 8) if kind == RB_REFINE_PROLONG else (n_fine // 8, n_fine)
     dev = nodes[0].device
     rp = torch.empty(rows + 1, dtype=torch.int32, device=dev)
-    ci = torch.empty(8 * rows, dtype=torch.int32, device=dev)
-    va = torch.empty(8 * rows, dtype=torch.float64, device=dev)
+    ci = torch.empty(8 * n_fine if kind == RB_REFINE_PROLONG_T else 8 * rows, dtype=torch.int32, device=dev)
+    va = torch.empty(ci.numel(), dtype=torch.float64, device=dev)
     g = _grid_desc(nodes, periodic)
     _check(lib().rb_refine_assemble(C.byref(g), int(kind), _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)),
            "rb_refine_assemble")

@@ -593,6 +593,100 @@ rb_status launch_refine_map(const GridDev& g, int32_t* rp, int32_t* ci, double* 
   return RB_OK;
 }
 
+// P^T (N_c x N), the restriction of the multigrid cycle: row I of the 1-D transpose along an
+// axis lists the fine positions t whose interpolation uses coarse cell I (two to five of them:
+// 2I - 1 .. 2I + 2 inside, wrapped at a periodic seam, one more next to a wall where P
+// extrapolates), sorted, with P's weights.  P = P_z (x) P_y (x) P_x, so P^T's row (I, J, K) is
+// the product of the three 1-D rows: cx[I] cy[J] cz[K] entries, columns sorted when z runs
+// outermost, and its offset has a closed form in the per-axis prefix sums of the counts.
+struct TAxis {
+  int cnt, pre;  // entries of this 1-D row, entries of the rows before it on the axis
+  int t[8];
+  double w[8];
+};
+
+__device__ void prolong_t_axis(const GridDev& g, int d, int I, TAxis& r) {
+  const int nf = g.n[d];
+  r.cnt = 0;
+  for (int o = -3; o <= 4; ++o) {
+    int t = 2 * I + o;
+    if (g.per[d]) t = ((t % nf) + nf) % nf;
+    else if (t < 0 || t >= nf) continue;
+    bool seen = false;
+    for (int q = 0; q < r.cnt; ++q) seen |= r.t[q] == t;
+    if (seen) continue;
+    int c[2];
+    double w[2];
+    prolong_axis(g, d, t, c, w);
+    if (c[0] == I || c[1] == I) {
+      r.t[r.cnt] = t;
+      r.w[r.cnt] = c[0] == I ? w[0] : w[1];
+      ++r.cnt;
+    }
+  }
+  for (int q = 1; q < r.cnt; ++q)  // insertion sort by fine position
+    for (int u = q; u > 0 && r.t[u - 1] > r.t[u]; --u) {
+      const int tt = r.t[u];
+      r.t[u] = r.t[u - 1], r.t[u - 1] = tt;
+      const double ww = r.w[u];
+      r.w[u] = r.w[u - 1], r.w[u - 1] = ww;
+    }
+}
+
+constexpr size_t kProlongTTabMax = 200 * 1024;
+
+__global__ void __launch_bounds__(kMapThreads) k_prolong_t(GridDev g, int32_t* __restrict__ rp,
+                                                           int32_t* __restrict__ ci, double* __restrict__ va) {
+  extern __shared__ TAxis s_ax[];
+  const int ncx = g.n[0] / 2, ncy = g.n[1] / 2, ncz = g.n[2] / 2;
+  for (int p = threadIdx.x; p < ncx + ncy + ncz; p += kMapThreads) {
+    const int d = p < ncx ? 0 : (p < ncx + ncy ? 1 : 2);
+    prolong_t_axis(g, d, p - (d == 0 ? 0 : (d == 1 ? ncx : ncx + ncy)), s_ax[p]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {  // exclusive prefix of the counts along each axis
+    const int d = threadIdx.x;
+    const int b = d == 0 ? 0 : (d == 1 ? ncx : ncx + ncy), len = d == 0 ? ncx : (d == 1 ? ncy : ncz);
+    int acc = 0;
+    for (int q = 0; q < len; ++q) {
+      s_ax[b + q].pre = acc;
+      acc += s_ax[b + q].cnt;
+    }
+  }
+  __syncthreads();
+  const TAxis* ax = s_ax;
+  const TAxis* ay = s_ax + ncx;
+  const TAxis* az = s_ax + ncx + ncy;
+  const int64_t sx = 2 * (int64_t)g.n[0], sy = 2 * (int64_t)g.n[1];  // entries per axis (each t in two rows)
+  const int64_t rows = (int64_t)ncx * ncy * ncz;
+  const int nfx = g.n[0], nfy = g.n[1];
+  for (int64_t r = (int64_t)blockIdx.x * kMapThreads + threadIdx.x; r < rows; r += (int64_t)gridDim.x * kMapThreads) {
+    const int I = (int)(r % ncx), J = (int)((r / ncx) % ncy), Kz = (int)(r / ((int64_t)ncx * ncy));
+    const TAxis &X = ax[I], &Y = ay[J], &Z = az[Kz];
+    int64_t e = (int64_t)Z.pre * sy * sx + (int64_t)Z.cnt * ((int64_t)Y.pre * sx + (int64_t)Y.cnt * X.pre);
+    rp[r] = (int32_t)e;
+    if (r == rows - 1) rp[rows] = (int32_t)(e + (int64_t)X.cnt * Y.cnt * Z.cnt);
+    for (int a = 0; a < Z.cnt; ++a)
+      for (int b = 0; b < Y.cnt; ++b)
+        for (int c = 0; c < X.cnt; ++c, ++e) {
+          ci[e] = X.t[c] + nfx * (Y.t[b] + nfy * Z.t[a]);
+          va[e] = Z.w[a] * (Y.w[b] * X.w[c]);  // the product in P's order: bit-identical entries
+        }
+  }
+}
+
+rb_status launch_prolong_t(const GridDev& g, int32_t* rp, int32_t* ci, double* va, cudaStream_t s) {
+  const size_t tab = sizeof(TAxis) * (size_t)(g.n[0] / 2 + g.n[1] / 2 + g.n[2] / 2);
+  RB_REQUIRE(tab <= kProlongTTabMax, "rb_refine_assemble: P^T needs %zu bytes of axis tables (limit %zu)", tab,
+             kProlongTTabMax);
+  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(&k_prolong_t), tab));
+  const int64_t rows = (int64_t)(g.n[0] / 2) * (g.n[1] / 2) * (g.n[2] / 2);
+  const int64_t tiles = (rows + kMapThreads - 1) / kMapThreads;
+  k_prolong_t<<<wave_grid(&k_prolong_t, tiles, tab, kMapThreads), kMapThreads, tab, s>>>(g, rp, ci, va);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
 }  // namespace
 }  // namespace rb
 
@@ -665,7 +759,8 @@ extern "C" rb_status rb_refine_assemble(const rb_grid_desc* fine, rb_refine_kind
                                         int32_t* col_idx, double* vals, rb_stream_t stream) {
   clear_error();
   RB_REQUIRE(fine != nullptr, "rb_refine_assemble: null grid");
-  RB_REQUIRE(kind == RB_REFINE_PROLONG || kind == RB_REFINE_RESTRICT, "rb_refine_assemble: unknown kind %d", (int)kind);
+  RB_REQUIRE(kind == RB_REFINE_PROLONG || kind == RB_REFINE_RESTRICT || kind == RB_REFINE_PROLONG_T,
+             "rb_refine_assemble: unknown kind %d", (int)kind);
   GridDev g;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = fine->n[d];
@@ -680,5 +775,6 @@ extern "C" rb_status rb_refine_assemble(const rb_grid_desc* fine, rb_refine_kind
   RB_REQUIRE(row_ptr && col_idx && vals, "rb_refine_assemble: null output array");
   cudaStream_t s = S(stream);
   if (kind == RB_REFINE_PROLONG) return launch_refine_map<false>(g, row_ptr, col_idx, vals, s);
+  if (kind == RB_REFINE_PROLONG_T) return launch_prolong_t(g, row_ptr, col_idx, vals, s);
   return launch_refine_map<true>(g, row_ptr, col_idx, vals, s);
 }

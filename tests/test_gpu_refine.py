@@ -49,6 +49,25 @@ def _check_csr(rp, ci, va, A):
 
 
 @pytest.mark.parametrize("name", list(GRIDS))
+def test_prolong_transpose_matches_oracle(rb, name):
+    """P^T (the multigrid restriction of residuals): the structure of the oracle's P transposed
+    bit for bit, and the values the same bits as the device's own P entries."""
+    g = GRIDS[name]()
+    rp, ci, va, nc = _device_map(rb, g, rb.RB_REFINE_PROLONG_T)
+    P = refine.prolongation(g)
+    PT = P.T.tocsr()
+    PT.sort_indices()
+    assert nc == g.n_cells and rp.numel() - 1 == g.n_cells // 8
+    _check_csr(rp, ci, va, PT)
+    prp, pci, pva, _ = _device_map(rb, g, rb.RB_REFINE_PROLONG)
+    import scipy.sparse as sp
+
+    Pd = sp.csr_matrix((pva.cpu().numpy(), pci.cpu().numpy(), prp.cpu().numpy()), shape=P.shape).T.tocsr()
+    Pd.sort_indices()
+    assert np.array_equal(va.cpu().numpy(), Pd.data)
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
 @pytest.mark.parametrize("kind", ["prolong", "restrict"])
 def test_refine_map_matches_oracle(rb, name, kind):
     g = GRIDS[name]()

@@ -80,3 +80,39 @@ def test_block_cg_matches_columnwise_cg_on_poisson():
     X = X - X.mean(axis=0, keepdims=True)
     assert np.all(np.linalg.norm(X - Xr, axis=0) <= 1e-8 * np.linalg.norm(Xr, axis=0))
     assert it <= max(i.iters for i in infos)
+
+
+def test_flexible_beta_equals_standard_with_a_fixed_preconditioner():
+    """With the same symmetric V-cycle every iteration, the Polak-Ribiere beta equals the
+    Fletcher-Reeves one in exact arithmetic: same iteration count and the same solution."""
+    g = W.channel_grid(16, 16, 8)
+    lv = mg.hierarchy(g)
+    b = W.zero_mean(W.normal((g.n_cells, 1), 44))[:, 0]
+    x0, it0 = mg.mg_pcg(lv, b)
+    x1, it1 = mg.mg_pcg(lv, b, flexible=True)
+    assert abs(it0 - it1) <= 1, (it0, it1)
+    assert np.linalg.norm(x1 - x0) <= 1e-9 * np.linalg.norm(x0)
+
+
+def test_flexible_beta_survives_a_perturbed_preconditioner():
+    """A V-cycle whose output is perturbed at the 1e-6 level each iteration (as an FP32 cycle
+    is): the flexible form still reaches 1e-10 in about the same number of iterations."""
+    g = W.unit_periodic_grid(16)
+    lv = mg.hierarchy(g)
+    b = W.zero_mean(W.normal((g.n_cells, 1), 45))[:, 0]
+    rng = np.random.default_rng(46)
+    clean = mg.vcycle
+
+    def noisy(levels, r, level=0, *args, **kw):
+        z = clean(levels, r, level, *args, **kw)
+        return z * (1.0 + 1e-6 * rng.standard_normal(z.shape)) if level == 0 else z
+
+    mg.vcycle = noisy
+    try:
+        x, it = mg.mg_pcg(lv, b, flexible=True)
+    finally:
+        mg.vcycle = clean
+    _, it_ref = mg.mg_pcg(lv, b)
+    r = b - lv[0].A @ x
+    assert np.linalg.norm(r - r.mean()) <= 1e-10 * np.linalg.norm(b)
+    assert it <= it_ref + 3, (it, it_ref)
