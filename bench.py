@@ -269,11 +269,13 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e(args, torch, step_items, stream, dev, flops_step)
         out["ksweep"] = k_sweep(torch, rb, ops, dev, hbm)
         out["poisson"] = poisson(torch, rb, ops, g, dev)
+        out["multigrid"] = multigrid(torch, rb, g, dev, out["poisson"])
         out["operator_build"] = operator_build(torch, rb, g, dev)
         out["blas1"] = blas1(torch, rb, dev, g.n_cells, hbm)
         out["stencils"] = stencils(torch, rb, dev, hbm)
         out["refine"] = refine_maps(torch, rb, dev, hbm)
         out["projection"] = projection(torch, rb, dev)
+        out["refinement_run"] = refinement_run(torch, rb, dev)
         del ops, step_items
         torch.cuda.empty_cache()
         out["batch"] = batch_bench(torch, rb, dev)
@@ -412,7 +414,8 @@ def projection(torch, rb, dev):
     Poisson solves by the FP32-inner refinement to 1e-10 from the previous step's pressure.
     One warm-up step, then three timed (host clock around synchronised steps: every solve
     synchronises to read its report).  Reports ms per step, the Poisson share and the speed-up
-    of one m-state step over m single-state steps (the iteration speed-up of Eq. (pmite))."""
+    of one m-state step over m single-state steps (the iteration speed-up of Eq. (pmite)), with
+    the pressure solved by the multigrid CG and by the Jacobi-preconditioned CG."""
     import math
 
     from paper_2508_06710_gb300.flow_step import ProjectionStep
@@ -426,9 +429,17 @@ def projection(torch, rb, dev):
     z, y, x = torch.meshgrid(c, c, c, indexing="ij")
     su, sv = (torch.sin(x) * torch.cos(y)).reshape(-1), (-torch.cos(x) * torch.sin(y)).reshape(-1)
     res = {"grid": f"periodic {n}^3, 2 pi", "nu": nu, "dt": dt, "steps": 3, "states": []}
+    for solver in ("mg", "jacobi"):
+        _projection_runs(torch, res, nodes, n, cells, nu, dt, su, sv, solver, dev)
+    return res
+
+
+def _projection_runs(torch, res, nodes, n, cells, nu, dt, su, sv, solver, dev):
+    from paper_2508_06710_gb300.flow_step import ProjectionStep
+
     base = None
     for m in (1, 2, 4, 8):
-        stepper = ProjectionStep(torch, nodes, m, nu, dt, mixed=2)
+        stepper = ProjectionStep(torch, nodes, m, nu, dt, mixed=2, solver=solver)
         u = torch.as_tensor(0.01 * W.normal((cells, 3 * m), 1900 + m), device=dev)
         for s in range(m):
             u[:, s] += (1 + 0.1 * s) * su
@@ -443,10 +454,70 @@ def projection(torch, rb, dev):
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t0) * 1e3 / 3
         base = ms if m == 1 else base
-        res["states"].append({"m": m, "ms_per_step": ms, "ms_per_state_step": ms / m,
+        res["states"].append({"solver": solver, "m": m, "ms_per_step": ms, "ms_per_state_step": ms / m,
                               "poisson_share": stepper.poisson_ms / 3 / ms, "solve_iters": stepper.iters,
                               "speedup_vs_m_single": m * base / ms})
         del stepper, u, us
+        torch.cuda.empty_cache()
+
+
+def refinement_run(torch, rb, dev, steps=3):
+    """Inline mesh refinement (Sec. 3.3) over a time-step sequence: m = 1, 2, 4, 8 stacked flow
+    states developed on the 64^3 periodic 2 pi box (dt = 0.02), mapped onto 128^3 (trilinear P
+    over the 3 m columns, then a projection) and continued there (dt = 0.01); Taylor-Green
+    vortices of amplitude 1 + 0.1 s plus seeded noise of 0.01, nu = 0.01; pressure solves by
+    the multigrid CG (FP32 cycle inside FP64 refinement) to 1e-10 from the previous pressure.
+    Per m: ms per coarse step and per fine step (host clock around synchronised steps, after
+    one untimed step on each grid), the mapping's ms, the mesh pace ratio delta_m = f^C / f^F
+    with f = (ms per step) / dt (Sec. 3.3's simulation pace), the fine grid's iteration
+    speed-up m t_1 / t_m, and the whole-simulation speed-up of Eq. (speedup1) at the paper's
+    beta = 10, gamma = 15 beside the single-mesh one (gamma = 0)."""
+    import math
+
+    from paper_2508_06710_gb300.flow_step import RefinedEnsemble
+
+    nf, nu, dtf = 2 * 64, 0.01, 0.01
+    L = 2 * math.pi
+    nodes = [torch.linspace(0.0, L, nf + 1, dtype=torch.float64, device=dev) for _ in range(3)]
+    nc = nf // 2
+    h = L / nc
+    c = (torch.arange(nc, dtype=torch.float64, device=dev) + 0.5) * h
+    z, y, x = torch.meshgrid(c, c, c, indexing="ij")
+    su, sv = (torch.sin(x) * torch.cos(y)).reshape(-1), (-torch.cos(x) * torch.sin(y)).reshape(-1)
+    res = {"coarse": f"periodic {nc}^3", "fine": f"periodic {nf}^3", "dt_coarse": 2 * dtf, "dt_fine": dtf, "nu": nu,
+           "steps": steps, "states": []}
+    base = None
+    for m in (1, 2, 4, 8):
+        run = RefinedEnsemble(torch, nodes, m, nu, dtf, mixed=2, solver="mg")
+        u = torch.as_tensor(0.01 * W.normal((nc ** 3, 3 * m), 2900 + m), device=dev)
+        for s in range(m):
+            u[:, s] += (1 + 0.1 * s) * su
+            u[:, m + s] += (1 + 0.1 * s) * sv
+        us = torch.zeros((3 * nc ** 3, m), dtype=torch.float64, device=dev)
+        run.coarse.step(u, us)  # untimed: records the solver's graphs
+        uf, usf, t = run.run(u, us, steps, 0)
+        run.fine.step(uf, usf)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            run.fine.step(uf, usf)
+        torch.cuda.synchronize()
+        ms_f = (time.perf_counter() - t0) * 1e3 / steps
+        ms_c = t["coarse_ms"] / steps
+        f_c, f_f = ms_c / (2 * dtf), ms_f / dtf
+        rec = {"m": m, "ms_per_coarse_step": ms_c, "ms_per_fine_step": ms_f, "map_ms": t["map_ms"],
+               "delta_m": f_c / f_f, "Pi_m": f_f / f_c, "fine_solve_iters": run.fine.iters[-3:]}
+        if m == 1:
+            base = rec
+        rec["fine_iteration_speedup"] = m * base["ms_per_fine_step"] / ms_f
+        beta, gamma = 10.0, 15.0
+        d1, dm = base["delta_m"], rec["delta_m"]
+        # Eq. (speedup1): (1 + d1 g + (1 + g) b) / (m (dm g + 1) + (1 + g) b) * m f_1^F / f_m^F
+        rec["simulation_speedup_refined"] = ((1 + d1 * gamma + (1 + gamma) * beta) / (m * (dm * gamma + 1) + (1 + gamma) * beta)
+                                             * rec["fine_iteration_speedup"])
+        rec["simulation_speedup_single_mesh"] = (1 + beta) / (m + beta) * rec["fine_iteration_speedup"]
+        res["states"].append(rec)
+        del run, u, us, uf, usf
         torch.cuda.empty_cache()
     return res
 
@@ -780,6 +851,71 @@ def poisson(torch, rb, ops, g, dev):
         else:  # the mixed-precision solution against the FP64 one, per column (both zero-mean)
             out[name]["rel_err_vs_fp64_cg"] = ((X - X64).norm(dim=0) / X64.norm(dim=0)).tolist()
     out["speedup_ir_vs_fp64"] = out["fp64_cg"]["ms"] / out["ir_fp32_inner"]["ms"]
+    return out
+
+
+def multigrid(torch, rb, g, dev, poisson_res=None):
+    """Multigrid-preconditioned CG (Sec. 4; Appendix A's level, restriction and prolongation
+    SpMMs) to a 1e-10 true relative residual: the channel (k = 3, b = -M u) and the periodic
+    128^3 box (k = 8, zero-mean N(0,1)), with the FP64 cycle and with the FP32 cycle inside
+    FP64 refinement; beside the Jacobi solvers on the same systems.  Host clock around
+    synchronised solves (each solve synchronises to read its report); best of two after one
+    untimed solve (which records the CUDA graphs)."""
+    out = {"runs": []}
+    cases = [("channel-k3", g, 3), ("periodic128-k8", W.unit_periodic_grid(128), 8)]
+    for case, grid, k in cases:
+        nodes, per = rb.grid_nodes(grid, dev)
+        t0 = time.perf_counter()
+        m = rb.Multigrid(nodes, per, k_max=k)
+        torch.cuda.synchronize()
+        t_build = (time.perf_counter() - t0) * 1e3
+        if case.startswith("channel"):
+            rpm, cim, vam, ncm = rb.fvm_assemble(nodes, per, rb.RB_FVM_DIVERGENCE)
+            Mop = rb.Operator(rpm, cim, vam, ncm, dtype="f64", k_max=k)
+            U = torch.as_tensor(W.face_field(Mop.n_cols, k, 2002), device=dev)
+            B = Mop.spmm(U, c=torch.full((k,), -1.0, dtype=torch.float64, device=dev))
+            del Mop, U
+        else:
+            B = torch.as_tensor(W.zero_mean(W.normal((grid.n_cells, k), W.seed_for(4, k, salt=99))), device=dev)
+        for mixed in (False, True):
+            prm = rb.mg_params(mixed=mixed)
+            X = torch.zeros_like(B)
+            m.solve(B, X, prm)
+            best = None
+            for _ in range(2):
+                X.zero_()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                r = m.solve(B, X, prm)
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t) * 1e3
+                best = (ms, r) if best is None or ms < best[0] else best
+            ms, r = best
+            out["runs"].append({"case": f"{case}-{'fp32cycle-ir' if mixed else 'fp64'}", "grid": grid.name, "k": k,
+                                "levels": m.shapes, "ms": ms, "iters": r.iters, "sweeps": r.sweeps,
+                                "true_rel_res": r.true_rel_res, "status": r.status, "build_ms": t_build,
+                                "device_gb": m.info().device_bytes / 1e9})
+        if case.startswith("periodic"):  # the Jacobi refinement on the same system
+            rp, ci, va, nc = rb.fvm_assemble(nodes, per, rb.RB_FVM_LAPLACIAN, scale=-1.0)
+            A64 = rb.Operator(rp, ci, va, nc, dtype="f64", k_max=k)
+            A32 = rb.Operator(rp, ci, va, nc, dtype="f32", k_max=k)
+            for name, mixed in (("jacobi-fp64-cg", 0), ("jacobi-ir", 2)):
+                p = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, check_every=50)
+                w = torch.empty(rb.cg_workspace_bytes(A64, k, p), dtype=torch.uint8, device=dev)
+                X = torch.zeros_like(B)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                r = rb.cg_solve(A64, B, X, A_inner=A32 if mixed else None, params=p, work=w)
+                torch.cuda.synchronize()
+                out["runs"].append({"case": f"{case}-{name}", "k": k, "ms": (time.perf_counter() - t) * 1e3,
+                                    "iters": r.iters, "true_rel_res": r.true_rel_res})
+            del A64, A32
+        del m, B
+        torch.cuda.empty_cache()
+    if poisson_res:
+        ch = {r["case"]: r["ms"] for r in out["runs"]}
+        out["channel_speedup_vs_jacobi_fp64_cg"] = poisson_res["fp64_cg"]["ms"] / ch["channel-k3-fp32cycle-ir"]
+        out["channel_speedup_vs_jacobi_ir"] = poisson_res["ir_fp32_inner"]["ms"] / ch["channel-k3-fp32cycle-ir"]
     return out
 
 

@@ -383,6 +383,79 @@ rb_status rb_batch_tune(rb_batch_t batch, const double* const* B, const int64_t*
 rb_status rb_batch_set_barrier(rb_batch_t batch, double timeout_ms, int32_t extra_arrivals);
 
 /* ------------------------------------------------------------------------------------------
+ * Multigrid-preconditioned CG for the Poisson matrix A = -L of a Cartesian FVM grid
+ * (Sec. 4: the paper solves the pressure equation by CG with a multigrid preconditioner;
+ * Appendix A, Table 9: the SpMMs of its levels, restrictions and prolongations).
+ *
+ * The paper's hierarchy is algebraic and comes from a closed library; this one is geometric,
+ * built on the device from the library's own assemblies: level l + 1 keeps every other node
+ * of level l (an axis is halved while its cell count is even and its half is >= min_cells),
+ * A_l = -L rediscretised on each level (rb_fvm_assemble), the trilinear prolongation P_l and
+ * its transpose as the restriction (rb_refine_assemble: RB_REFINE_PROLONG, _PROLONG_T), and
+ * the coarsest level (at most 4096 cells) solved exactly through a dense inverse of
+ * A_L + s 1 1^T (s > 0), formed on the device when the hierarchy is built; on the zero-mean
+ * right-hand sides of the singular periodic / Neumann operator it gives the zero-mean
+ * solution.  The preconditioner z = B r is one V(nu, nu) cycle from a zero guess with damped
+ * Jacobi smoothing (weight omega): nu sweeps, residual, restriction, the next level's cycle,
+ * prolongation-add, nu sweeps.  All k columns go through each kernel together.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct rb_mg* rb_mg_t;
+
+typedef struct {
+  int32_t nu;         /* Jacobi sweeps before and after the coarse correction (1..16; 2) */
+  double omega;       /* Jacobi damping weight in (0, 1] (2/3) */
+  int32_t min_cells;  /* an axis is halved only if its half keeps >= min_cells cells (>= 2; 4) */
+  int32_t flexible;   /* 1: flexible CG beta = -alpha (q . z_new) / (r . z)_old (Notay), robust
+                         to an FP32 cycle; 0: beta = (r . z)_new / (r . z)_old (1) */
+} rb_mg_params;
+
+#define RB_MG_MAX_LEVELS 16
+typedef struct {
+  int32_t levels;
+  int32_t n[RB_MG_MAX_LEVELS][3];  /* cells along x, y, z, level by level (fine first) */
+  int64_t nnz_A[RB_MG_MAX_LEVELS]; /* nonzeros of -L on the level */
+  int64_t nnz_P[RB_MG_MAX_LEVELS]; /* nonzeros of P from the next level (0 on the coarsest) */
+  int64_t device_bytes;            /* device memory the hierarchy holds */
+} rb_mg_info_t;
+
+/* Builds the hierarchy of `grid` (as for rb_fvm_assemble; nodes are DEVICE float64) for up to
+ * k_max columns, every level in FP64 and FP32, with level and solve vectors for k_max
+ * columns.  params NULL = the defaults above.  Allocates (the library owns the memory until
+ * rb_mg_destroy); synchronises `stream`.  RB_EINVAL for invalid parameters, an axis too small
+ * for rb_fvm_assemble, or a grid beyond int32 indexing; RB_EINVAL also when the coarsest
+ * level would keep more than 4096 cells (the grid does not halve often enough). */
+rb_status rb_mg_create(const rb_grid_desc* grid, int32_t k_max, const rb_mg_params* params, rb_stream_t stream,
+                       rb_mg_t* out);
+rb_status rb_mg_destroy(rb_mg_t mg);
+rb_status rb_mg_info(rb_mg_t mg, rb_mg_info_t* info);
+
+/* One V-cycle z = B_l r on level `level` (its cells, numbered as on the grid), in `dtype`
+ * arithmetic (RB_F64, or RB_F32: operators and vectors in FP32).  R (in), Z (out): float64
+ * DEVICE n_l x k blocks (ldr, ldz >= k), k <= k_max.  level = L - 1 applies the coarsest
+ * level's dense inverse.  Calls on one hierarchy must not overlap (it holds the level
+ * vectors).  Asynchronous on `stream`; allocates nothing. */
+rb_status rb_mg_vcycle(rb_mg_t mg, int32_t level, rb_dtype dtype, const double* R, int64_t ldr, double* Z,
+                       int64_t ldz, int32_t k, rb_stream_t stream);
+
+/* Solves A x_j = b_j for k <= k_max columns by PCG (Saad, Alg. 9.1) preconditioned by one
+ * V-cycle per iteration.  params: rtol (true relative residual ||b - A x|| / ||b||, the mean
+ * removed from both when project_mean), max_iter, check_every (iterations between host
+ * reads of the per-column state), project_mean, and
+ *   mixed = 0: FP64 CG and cycle; the true residual is checked every check_every iterations
+ *              (columns stop at the first check that meets rtol);
+ *   mixed != 0: FP64 iterative refinement around the same PCG run in FP32 (operators,
+ *              vectors and cycle; dot products summed in FP64 across threads): each sweep
+ *              solves A d = r / ||r|| to inner_rtol (or to half of what rtol still needs,
+ *              when that is looser) and updates x += ||r|| d in FP64; at most max_sweeps.
+ * precond and persistent are ignored.  B (ldb), X (ldx; in: initial guess, out: solution,
+ * zero-mean with project_mean): float64 DEVICE.  Synchronises `stream`; allocates nothing
+ * (the hierarchy holds the vectors and CUDA graphs of the iterations, recorded on first use
+ * for each k).  Returns the worst column status; report (may be NULL) as for rb_cg_solve
+ * (iters: CG iterations, over all sweeps when mixed; spmm_calls: FP64 residuals). */
+rb_status rb_mg_solve(rb_mg_t mg, const rb_cg_params* params, const double* B, int64_t ldb, double* X, int64_t ldx,
+                      int32_t k, rb_cg_report* report, rb_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * Learned initial guess for the pressure Poisson solve.
  *
  * The paper's projection step (Sec. 3; the Poisson solve that dominates Sec. 4) solves

@@ -35,7 +35,8 @@ SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
            "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier", "rb_guess_param_count", "rb_guess_create",
            "rb_guess_destroy", "rb_guess_init_params", "rb_guess_set_params", "rb_guess_get_params", "rb_guess_get_grad", "rb_guess_predict",
-           "rb_guess_loss_grad", "rb_guess_adam_step", "rb_guess_read_activation", "rb_guess_select"]
+           "rb_guess_loss_grad", "rb_guess_adam_step", "rb_guess_read_activation", "rb_guess_select",
+           "rb_mg_create", "rb_mg_destroy", "rb_mg_info", "rb_mg_vcycle", "rb_mg_solve"]
 
 
 class RbError(RuntimeError):
@@ -67,6 +68,19 @@ class OpInfo(C.Structure):
 
 class SpmmSchedule(C.Structure):
     _fields_ = [("vec", C.c_int32), ("lpr", C.c_int32), ("stage", C.c_int32), ("grid_cap", C.c_int32)]
+
+
+class MgParams(C.Structure):
+    _fields_ = [("nu", C.c_int32), ("omega", C.c_double), ("min_cells", C.c_int32), ("flexible", C.c_int32)]
+
+
+RB_MG_MAX_LEVELS = 16
+
+
+class MgInfo(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("n", (C.c_int32 * 3) * RB_MG_MAX_LEVELS),
+                ("nnz_A", C.c_int64 * RB_MG_MAX_LEVELS), ("nnz_P", C.c_int64 * RB_MG_MAX_LEVELS),
+                ("device_bytes", C.c_int64)]
 
 
 class GuessCfg(C.Structure):
@@ -148,6 +162,11 @@ def lib():
         "rb_guess_adam_step": (C.c_int, [vp, C.POINTER(AdamParams), dbl, vp]),
         "rb_guess_read_activation": (C.c_int, [vp, i32, vp, C.POINTER(i64), vp]),
         "rb_guess_select": (C.c_int, [vp, vp, vp, vp, vp, i32, dbl, vp, vp, vp, vp]),
+        "rb_mg_create": (C.c_int, [C.POINTER(GridDesc), i32, C.POINTER(MgParams), vp, C.POINTER(vp)]),
+        "rb_mg_destroy": (C.c_int, [vp]),
+        "rb_mg_info": (C.c_int, [vp, C.POINTER(MgInfo)]),
+        "rb_mg_vcycle": (C.c_int, [vp, i32, C.c_int, vp, i64, vp, i64, i32, vp]),
+        "rb_mg_solve": (C.c_int, [vp, C.POINTER(CgParams), vp, i64, vp, i64, i32, C.POINTER(CgReport), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -526,6 +545,79 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Multigrid:
+    """Geometric multigrid hierarchy of -L on a Cartesian grid (rb_mg_create): the V-cycle
+    preconditioner and the multigrid-preconditioned CG solve of the pressure equation."""
+
+    def __init__(self, nodes, periodic, k_max=1, nu=2, omega=2.0 / 3.0, min_cells=4, flexible=True, stream=None):
+        torch = _torch()
+        self._nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
+        g = _grid_desc(self._nodes, periodic)
+        prm = MgParams(int(nu), float(omega), int(min_cells), 1 if flexible else 0)
+        h = C.c_void_p()
+        _check(lib().rb_mg_create(C.byref(g), int(k_max), C.byref(prm), _stream(stream), C.byref(h)), "rb_mg_create")
+        self.handle = h
+        self.k_max = int(k_max)
+        inf = self.info()
+        self.levels = inf.levels
+        self.shapes = [tuple(inf.n[l][d] for d in range(3)) for l in range(inf.levels)]
+        self.n = self.shapes[0][0] * self.shapes[0][1] * self.shapes[0][2]
+
+    def info(self) -> MgInfo:
+        inf = MgInfo()
+        _check(lib().rb_mg_info(self.handle, C.byref(inf)), "rb_mg_info")
+        return inf
+
+    def vcycle(self, R, Z=None, level=0, dtype="f64", stream=None):
+        """Z = B_level R (one V-cycle on that level); R, Z float64 (n_level, k) CUDA blocks."""
+        torch = _torch()
+        R, n, k, ldr = _block(R, "R")
+        sh = self.shapes[level] if 0 <= level < self.levels else None
+        if sh is None or n != sh[0] * sh[1] * sh[2]:
+            raise ValueError(f"R must have one row per cell of level {level} ({sh})")
+        if Z is None:
+            Z = torch.empty((n, k), dtype=torch.float64, device=R.device)
+        Z, nz, _, ldz = _block(Z, "Z")
+        if nz != n or Z.shape[1] != k:
+            raise ValueError("Z must have the shape of R")
+        _check(lib().rb_mg_vcycle(self.handle, int(level), {"f64": RB_F64, "f32": RB_F32}[dtype], _ptr(R), ldr,
+                                  _ptr(Z), ldz, k, _stream(stream)), "rb_mg_vcycle")
+        return Z
+
+    def solve(self, B, X, params: CgParams | None = None, stream=None, raise_on_fail=False) -> CgResult:
+        """Solves -L X[:, j] = B[:, j] (X holds the initial guess on entry)."""
+        params = params or mg_params()
+        B, n, k, ldb = _block(B, "B")
+        X, nx, kx, ldx = _block(X, "X")
+        if n != self.n or nx != self.n or kx != k:
+            raise ValueError(f"B and X must be ({self.n}, k) blocks of the same k")
+        rep = CgReport()
+        st = lib().rb_mg_solve(self.handle, C.byref(params), _ptr(B), ldb, _ptr(X), ldx, k, C.byref(rep),
+                               _stream(stream))
+        if st not in (RB_OK, RB_ENOCONV, RB_EBREAKDOWN) or (raise_on_fail and st != RB_OK):
+            _check(st, "rb_mg_solve")
+        return CgResult(st, list(rep.iters[:k]), list(rep.true_rel_res[:k]), list(rep.status[:k]), rep.spmm_calls,
+                        rep.sweeps, rep.host_syncs, rep.ms)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().rb_mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_params(rtol=1e-10, max_iter=500, mixed=True, inner_rtol=1e-4, max_sweeps=30, project_mean=True,
+              check_every=4) -> CgParams:
+    """Parameters of Multigrid.solve: mixed = FP32 cycle and CG inside FP64 refinement."""
+    return CgParams(rtol, max_iter, 1, 1 if mixed else 0, inner_rtol, max_sweeps, 1 if project_mean else 0,
+                    check_every, 0)
 
 
 def guess_cfg(nx, ny, nz, channels=(8, 16, 32, 48), periodic=(1, 1, 0)) -> GuessCfg:

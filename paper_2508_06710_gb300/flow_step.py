@@ -9,7 +9,8 @@ velocities with the face-interpolated cell velocities.  Sec. 4 integrates in tim
 Heun's third-order Runge-Kutta scheme, with a projection at every stage.
 
 Every arithmetic step runs in the library's kernels (SpMM with per-column scales, axpy,
-axty, the Jacobi-PCG Poisson solve); this module allocates the buffers, zero-fills and copies
+axty, the Poisson solve by Jacobi- or multigrid-preconditioned CG); this module allocates the
+buffers, zero-fills and copies
 them, and takes row and column views (the face blocks of each direction, the columns of each
 velocity component).  Layout: u_c is (n, 3 m) with column i m + s for component i of state
 s; u_s is (n_faces, m), x faces first, then y, then z.
@@ -27,8 +28,9 @@ import time
 
 import numpy as np
 
-from . import (Operator, RbError, axpy, axty, cg_params, cg_solve, cg_workspace_bytes, fvm_assemble, RB_FVM_DIVERGENCE,
-               RB_FVM_GRADIENT, RB_FVM_INTERP_C2S, RB_FVM_INTERP_S2C, RB_FVM_LAPLACIAN, RB_OK)
+from . import (Multigrid, Operator, RbError, axpy, axty, cg_params, cg_solve, cg_workspace_bytes, fvm_assemble,
+               mg_params, refine_assemble, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT, RB_FVM_INTERP_C2S, RB_FVM_INTERP_S2C,
+               RB_FVM_LAPLACIAN, RB_OK, RB_REFINE_PROLONG)
 
 HEUN3_C = (0.0, 1.0 / 3.0, 2.0 / 3.0)
 HEUN3_A = ((), (1.0 / 3.0,), (0.0, 2.0 / 3.0))
@@ -38,9 +40,12 @@ HEUN3_B = (0.25, 0.0, 0.75)
 class ProjectionStep:
     """Heun RK3 projection steps of m flow states on a uniform periodic grid.
 
-    nodes: the grid's three float64 CUDA node tensors (uniform spacing, periodic axes)."""
+    nodes: the grid's three float64 CUDA node tensors (uniform spacing, periodic axes).
+    solver: "jacobi" (rb_cg_solve: Jacobi-PCG, FP64 or FP32-inner refinement by `mixed`) or
+    "mg" (rb_mg_solve: multigrid-preconditioned CG, FP64 or FP32 cycle inside FP64 refinement
+    by `mixed`) for the pressure equation."""
 
-    def __init__(self, torch, nodes, m, nu, dt, rtol=1e-10, mixed=0):
+    def __init__(self, torch, nodes, m, nu, dt, rtol=1e-10, mixed=0, solver="jacobi"):
         self.torch = torch
         nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
         host = [n.cpu().numpy() for n in nodes]
@@ -65,15 +70,23 @@ class ProjectionStep:
         self.G = op(RB_FVM_GRADIENT, self.m)    # cell-to-face gradient of the pressure
         self.L = op(RB_FVM_LAPLACIAN, m3)       # diffusion
         self.A = op(RB_FVM_LAPLACIAN, self.m, scale=-1.0)  # Poisson matrix -L
-        self.A32 = op(RB_FVM_LAPLACIAN, self.m, scale=-1.0, dtype="f32") if mixed else None
+        self.A32 = op(RB_FVM_LAPLACIAN, self.m, scale=-1.0, dtype="f32") if mixed and solver == "jacobi" else None
         self.I = op(RB_FVM_INTERP_C2S, m3)      # Gamma_{c->s}
         self.IT = op(RB_FVM_INTERP_S2C, m3)     # Gamma_{s->c} = Gamma_{c->s}^T
         self.nf = self.I.n_rows
         # faces of each direction: periodic axes have n faces per direction
         self.blocks = [(d * self.n, self.n) for d in range(3)]
-        self.prm = cg_params(rtol=rtol, mixed=mixed, project_mean=True, check_every=50)
         f64 = dict(dtype=torch.float64, device=dev)
-        self.work = torch.empty(cg_workspace_bytes(self.A, self.m, self.prm), dtype=torch.uint8, device=dev)
+        if solver == "mg":
+            self.mg = Multigrid(nodes, per, k_max=self.m)
+            self.prm = mg_params(rtol=rtol, mixed=bool(mixed))
+            self.work = None
+        elif solver == "jacobi":
+            self.mg = None
+            self.prm = cg_params(rtol=rtol, mixed=mixed, project_mean=True, check_every=50)
+            self.work = torch.empty(cg_workspace_bytes(self.A, self.m, self.prm), dtype=torch.uint8, device=dev)
+        else:
+            raise ValueError(f"unknown solver {solver!r}")
         self.Y = torch.empty((self.nf, m3), **f64)      # Gamma u, then u_s * Gamma u
         self.Gm = torch.empty((self.nf, m3), **f64)     # G p on each direction's faces, by component
         self.ut_s = torch.empty((self.nf, self.m), **f64)
@@ -121,7 +134,10 @@ class ProjectionStep:
             axpy(self.one_m, self._cols(self.Y, d)[f0:f0 + nd], self.ut_s[f0:f0 + nd])
         self.M.spmm(self.ut_s, self.B, c=self._alpha(-1.0 / cdt, self.m))
         t0 = time.perf_counter()
-        res = cg_solve(self.A, self.B, self.P[slot], A_inner=self.A32, params=self.prm, work=self.work)
+        if self.mg is not None:
+            res = self.mg.solve(self.B, self.P[slot], self.prm)
+        else:
+            res = cg_solve(self.A, self.B, self.P[slot], A_inner=self.A32, params=self.prm, work=self.work)
         self.poisson_ms += (time.perf_counter() - t0) * 1e3
         if res.status != RB_OK:
             raise RbError(res.status, f"projection solve: {res}")
@@ -158,3 +174,56 @@ class ProjectionStep:
         us = self.project(self.ut, self.dt, 2)
         u_c.copy_(self.ut)
         u_s.copy_(us)
+
+
+class RefinedEnsemble:
+    """Inline mesh refinement (Sec. 3.3) of m stacked flow states: the states develop on the
+    2:1 coarser grid (every other node of `fine_nodes`, larger time step), are mapped onto the
+    fine grid, and continue there.  The mapping interpolates every component of the coarse
+    cell velocities with the trilinear prolongation P (one rectangular SpMM over the 3 m
+    columns) and projects the result on the fine grid, so that the fine states start from
+    divergence-free face velocities and the matching cell velocities.
+
+    Both grids are uniform and periodic (ProjectionStep's requirement); each keeps its own
+    operators and Poisson solver."""
+
+    def __init__(self, torch, fine_nodes, m, nu, dt_fine, dt_coarse=None, rtol=1e-10, mixed=2, solver="mg"):
+        self.torch = torch
+        fine_nodes = [n.to(dtype=torch.float64).contiguous() for n in fine_nodes]
+        coarse_nodes = [n[::2].contiguous() for n in fine_nodes]  # every other node
+        self.m = int(m)
+        self.coarse = ProjectionStep(torch, coarse_nodes, m, nu, 2.0 * dt_fine if dt_coarse is None else dt_coarse,
+                                     rtol=rtol, mixed=mixed, solver=solver)
+        self.fine = ProjectionStep(torch, fine_nodes, m, nu, dt_fine, rtol=rtol, mixed=mixed, solver=solver)
+        rp, ci, va, nc = refine_assemble(fine_nodes, [True, True, True], RB_REFINE_PROLONG)
+        self.P = Operator(rp, ci, va, nc, k_max=3 * self.m)
+
+    def map_to_fine(self, u_c_coarse):
+        """(u_c, u_s) on the fine grid from the coarse cell velocities (n_coarse, 3 m)."""
+        torch = self.torch
+        u = torch.empty((self.fine.n, 3 * self.m), dtype=torch.float64, device=self.fine.dev)
+        self.P.spmm(u_c_coarse, u)
+        us = self.fine.project(u, self.fine.dt, 2)
+        return u, us.clone()
+
+    def run(self, u_c, u_s, steps_coarse, steps_fine):
+        """`steps_coarse` steps of the coarse states (u_c, u_s given on the coarse grid, updated
+        in place), the mapping, `steps_fine` steps on the fine grid; returns the fine (u_c, u_s)
+        and the wall time of each phase in ms (synchronised)."""
+        torch = self.torch
+        t = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps_coarse):
+            self.coarse.step(u_c, u_s)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        uf, usf = self.map_to_fine(u_c)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for _ in range(steps_fine):
+            self.fine.step(uf, usf)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        t["coarse_ms"], t["map_ms"], t["fine_ms"] = (t1 - t0) * 1e3, (t2 - t1) * 1e3, (t3 - t2) * 1e3
+        return uf, usf, t

@@ -99,8 +99,8 @@ def test_refine_validation_without_gpu(lib):
     import paper_2508_06710_gb300 as rb
 
     nodes = (C.c_double * 9)(*range(9))
-    for n, kind, msg in (((8, 7, 8), 0, b"even number"), ((8, 2, 8), 1, b"even number"), ((8, 8, 8), 2, b"unknown kind"),
-                         ((8, 8, 8), 0, b"null output")):
+    for n, kind, msg in (((8, 7, 8), 0, b"even number"), ((8, 2, 8), 1, b"even number"), ((8, 8, 8), 3, b"unknown kind"),
+                         ((8, 8, 8), 0, b"null output"), ((8, 8, 8), 2, b"null output"), ((8, 5, 8), 2, b"even number")):
         g = rb.GridDesc()
         for d in range(3):
             g.n[d] = n[d]
@@ -133,3 +133,29 @@ def test_fvm_sizes_match_oracle(lib):
             nr, nc, nnz = C.c_int32(), C.c_int32(), C.c_int64()
             assert lib.rb_fvm_csr_size(C.byref(gd), kind, C.byref(nr), C.byref(nc), C.byref(nnz)) == 0
             assert (nr.value, nc.value, nnz.value) == (ref.shape[0], ref.shape[1], ref.nnz)
+
+
+def test_multigrid_validation_without_gpu(lib):
+    """rb_mg_create / rb_mg_solve / rb_mg_vcycle refuse bad parameters before any device work."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+
+    nodes = (C.c_double * 9)(*range(9))
+    g = rb.GridDesc()
+    for d in range(3):
+        g.n[d] = 8
+        g.periodic[d] = 1
+        g.nodes[d] = C.addressof(nodes)
+    h = C.c_void_p()
+    for k_max, prm, msg in ((0, None, b"k_max"), (65, None, b"k_max"), (3, rb.MgParams(0, 0.5, 4, 1), b"nu"),
+                            (3, rb.MgParams(2, 1.5, 4, 1), b"omega"), (3, rb.MgParams(2, 0.5, 1, 1), b"min_cells")):
+        st = lib.rb_mg_create(C.byref(g), k_max, None if prm is None else C.byref(prm), None, C.byref(h))
+        assert st == rb.RB_EINVAL and msg in lib.rb_last_error(), (k_max, lib.rb_last_error())
+        assert not h.value
+    g.nodes[1] = None
+    assert lib.rb_mg_create(C.byref(g), 1, None, None, C.byref(h)) == rb.RB_EINVAL
+    assert b"null nodes" in lib.rb_last_error()
+    rep = rb.CgReport()
+    assert lib.rb_mg_solve(None, C.byref(rb.mg_params()), None, 1, None, 1, 1, C.byref(rep), None) == rb.RB_EINVAL
+    assert lib.rb_mg_vcycle(None, 0, 0, None, 1, None, 1, 1, None) == rb.RB_EINVAL

@@ -40,8 +40,8 @@ def _box(shape, lengths):
     return W.Grid(tuple(W.uniform_axis(n, L) for n, L in zip(shape, lengths)))
 
 
-@pytest.mark.parametrize("mixed", [0, 2])
-def test_projection_step_matches_oracle(rb, mixed):
+@pytest.mark.parametrize("mixed,solver", [(0, "jacobi"), (2, "jacobi"), (0, "mg"), (2, "mg")])
+def test_projection_step_matches_oracle(rb, mixed, solver):
     from paper_2508_06710_gb300.flow_step import ProjectionStep
 
     g = _box((10, 12, 8), (2 * math.pi, 3.0, 2.5))
@@ -50,7 +50,7 @@ def test_projection_step_matches_oracle(rb, mixed):
     u = 0.5 * W.normal((g.n_cells, 3 * m), 1700) + flow.taylor_green(g, m, amp=[1.0, 0.7])
     us = W.normal((fvm.n_faces(g), m), 1701)
     nodes, _ = rb.grid_nodes(g)
-    stepper = ProjectionStep(torch, nodes, m, nu, dt, mixed=mixed)
+    stepper = ProjectionStep(torch, nodes, m, nu, dt, mixed=mixed, solver=solver)
     ud, usd = to_dev(u), to_dev(us)
     scale = np.abs(u).max()
     for s in range(4):
@@ -96,3 +96,35 @@ def test_projection_step_full_size(rb):
     decay = math.exp(-2 * nu * 2 * dt)
     err = (ud - to_dev(tg) * decay).abs().max().item()
     assert err <= 0.05, err
+
+
+@pytest.mark.parametrize("mixed", [0, 2])
+def test_refined_run_matches_oracle(rb, mixed):
+    """Inline mesh refinement (Sec. 3.3): two steps of two states on the 8^3 box, the mapping
+    (trilinear P, then a projection) onto 16^3, two steps there; against the oracle's run.
+    Bar as for the step (the solves stop at 1e-10 on the device, 1e-12 in the oracle)."""
+    from paper_2508_06710_gb300.flow_step import RefinedEnsemble
+
+    fine = _box((16, 16, 16), (2 * math.pi,) * 3)
+    coarse = _box((8, 8, 8), (2 * math.pi,) * 3)
+    m, nu, dtf = 2, 0.05, 0.02
+    u = flow.taylor_green(coarse, m, amp=[1.0, 0.6]) + 0.2 * W.normal((coarse.n_cells, 3 * m), 1900)
+    ops_c = flow.operators(coarse)
+    u, us, _ = flow.project(ops_c, u, 1.0)
+    nodes, _ = rb.grid_nodes(fine)
+    run = RefinedEnsemble(torch, nodes, m, nu, dtf, mixed=mixed)
+    ud, usd = to_dev(u), to_dev(us)
+    uf, usf, t = run.run(ud, usd, 2, 2)
+    ur, usr = flow.refined_run(fine, u, us, nu, 2 * dtf, dtf, 2, 2)
+    scale = np.abs(u).max()
+    assert np.abs(uf.cpu().numpy() - ur).max() <= 1e-7 * scale
+    assert np.abs(usf.cpu().numpy() - usr).max() <= 1e-7 * scale
+    ops_f = flow.operators(fine)
+    U = usf.cpu().numpy()
+    assert np.abs(ops_f.M @ U).max() <= 1e-8 * (abs(ops_f.M) @ np.abs(U)).max()
+    assert set(t) == {"coarse_ms", "map_ms", "fine_ms"}
+    # the mapping alone: P (one SpMM over the 3 m columns) and the fine projection
+    uc_map, us_map = run.map_to_fine(to_dev(u))
+    ur_map, usr_map = flow.map_to_fine(fine, u, dtf)
+    assert np.abs(uc_map.cpu().numpy() - ur_map).max() <= 1e-8 * scale
+    assert np.abs(us_map.cpu().numpy() - usr_map).max() <= 1e-8 * scale
