@@ -1187,6 +1187,55 @@ def profile_run(args):
             torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile": args.profile, "ok": True}))
         return
+    if args.profile == "mg":
+        # one multigrid solve (FP32 cycle inside FP64 refinement) on the channel, k = 3, after
+        # an untimed one that records the CUDA graphs; NVTX range "mg_solve"
+        g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+        nodes, per = rb.grid_nodes(g, dev)
+        m = rb.Multigrid(nodes, per, k_max=3)
+        B = torch.as_tensor(W.zero_mean(W.normal((g.n_cells, 3), 2004)), device=dev)
+        X = torch.zeros_like(B)
+        m.solve(B, X, rb.mg_params(mixed=True))
+        X.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("mg_solve")
+        r = m.solve(B, X, rb.mg_params(mixed=True))
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile": args.profile, "ok": True, "iters": r.iters, "res": r.true_rel_res}))
+        return
+    if args.profile == "assembly":
+        # the device builds of the 27p Laplacian (96^3 periodic), and of P, R and P^T on the channel
+        n = 96
+        rb.stencil_assemble((n, n, n), (1.0 / n,) * 3, rb.RB_STENCIL_27P, device=dev)
+        rb.stencil_assemble((n, n, n), (1.0 / n,) * 3, rb.RB_STENCIL_13P, device=dev)
+        g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+        nodes, per = rb.grid_nodes(g, dev)
+        for kind in (rb.RB_REFINE_PROLONG, rb.RB_REFINE_RESTRICT, rb.RB_REFINE_PROLONG_T):
+            rb.refine_assemble(nodes, per, kind)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "ok": True}))
+        return
+    if args.profile == "projection":
+        # two Heun RK3 projection steps of m = 2 states on the periodic 128^3 box (multigrid
+        # pressure solves); NVTX range "projection_step" around the second
+        import math
+
+        from paper_2508_06710_gb300.flow_step import ProjectionStep
+
+        n = 128
+        nodes = [torch.linspace(0.0, 2 * math.pi, n + 1, dtype=torch.float64, device=dev) for _ in range(3)]
+        st = ProjectionStep(torch, nodes, 2, 0.01, 0.01, mixed=2, solver="mg")
+        u = torch.as_tensor(W.normal((n ** 3, 6), 2005), device=dev)
+        us = torch.zeros((3 * n ** 3, 2), dtype=torch.float64, device=dev)
+        st.step(u, us)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("projection_step")
+        st.step(u, us)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile": args.profile, "ok": True, "iters": st.iters}))
+        return
     if args.profile == "spmm":
         g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
         nodes, per = rb.grid_nodes(g, dev)
@@ -1245,12 +1294,15 @@ def main():
                     help="NVTX ranges around the timed region ('timed_step') and each SpMM (its label), for ncu filters")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel, if captured for this build")
-    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess", "spmm"],
+    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess", "spmm", "mg", "assembly", "projection"],
                     help="short run for an ncu capture: 'step' = the timed step only, 'cg' = a 20-iteration "
                          "FP64 and FP32-refinement Poisson solve (k = 1 and 3), 'guess' = one forward and one "
                          "training pass of the learned-guess network at 128^3 (NVTX 'predict', 'loss_grad'), "
                          "'spmm' = three channel-Laplacian SpMMs with --profile-k columns in --profile-dtype "
-                         "on the schedule --profile-sched (vec,lpr,stage,grid_cap; default: the untuned one)")
+                         "on the schedule --profile-sched (vec,lpr,stage,grid_cap; default: the untuned one), "
+                         "'mg' = one multigrid solve on the channel (k = 3, NVTX 'mg_solve'), 'assembly' = the 13p / "
+                         "27p builds at 96^3 and P, R, P^T on the channel, 'projection' = two projection steps of "
+                         "two states at 128^3 (NVTX 'projection_step' around the second)")
     ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
                     help="file receiving the full result (every section); stdout ends with the headline line only")
     ap.add_argument("--profile-k", type=int, default=32)

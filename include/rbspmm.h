@@ -56,7 +56,7 @@ typedef enum {
 } rb_status;
 
 typedef enum { RB_F64 = 0, RB_F32 = 1 } rb_dtype;
-typedef enum { RB_CSR = 0, RB_SELL = 1, RB_AUTO = 2 } rb_format;
+typedef enum { RB_CSR = 0, RB_SELL = 1, RB_AUTO = 2, RB_STENCIL = 3 } rb_format;
 
 /* Message of the calling thread's last failed call ("" if none). Owned by the library. */
 const char* rb_last_error(void);
@@ -224,6 +224,19 @@ typedef struct {
  * synchronises `stream`. */
 rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_desc* block, rb_dtype dtype, rb_format format,
                              rb_stream_t stream, rb_op_t* out);
+/* The Laplacian of rb_fvm_assemble (RB_FVM_LAPLACIAN, times `scale`) as a matrix-free operator
+ * (format RB_STENCIL): the repeated-block reuse of Sec. 2 taken to the structure of a Cartesian
+ * grid, where every coefficient A_f / d_f is a product of per-axis quantities (two cell widths
+ * and one inverse centre distance), so the operator is held as 2 (n_x + n_y + n_z) + 3 numbers
+ * and an SpMM reads only X and writes only Y.  The coefficients are formed in `dtype`
+ * arithmetic from the tables (FP32: the tables rounded to nearest, so entries can differ from
+ * RNE(FP64 entries) by a few ulp).  The handle works with rb_spmm, rb_tune_spmm,
+ * rb_operator_info/check/destroy and every call built on rb_spmm (e.g. rb_galerkin_guess); the
+ * CG solves take CSR operators only.  grid as for rb_fvm_assemble (DEVICE nodes).  Allocates;
+ * synchronises `stream`. */
+rb_status rb_fvm_stencil_create(const rb_grid_desc* grid, double scale, rb_dtype dtype, int32_t k_max,
+                                rb_stream_t stream, rb_op_t* out);
+
 rb_status rb_operator_destroy(rb_op_t op);
 rb_status rb_operator_info(rb_op_t op, rb_op_info* info);
 /* Synchronises `stream` and reports whether a kernel applying `op` since the last check gave
@@ -407,6 +420,9 @@ typedef struct {
   int32_t min_cells;  /* an axis is halved only if its half keeps >= min_cells cells (>= 2; 4) */
   int32_t flexible;   /* 1: flexible CG beta = -alpha (q . z_new) / (r . z)_old (Notay), robust
                          to an FP32 cycle; 0: beta = (r . z)_new / (r . z)_old (1) */
+  int32_t matrix_free; /* 1: the FP32 cycle and the FP32 CG apply -L and the transfers from
+                          per-axis tables (rb_fvm_stencil_create; no matrix bytes); 0: the CSR
+                          operators (1) */
 } rb_mg_params;
 
 #define RB_MG_MAX_LEVELS 16
@@ -454,6 +470,35 @@ rb_status rb_mg_vcycle(rb_mg_t mg, int32_t level, rb_dtype dtype, const double* 
  * (iters: CG iterations, over all sweeps when mixed; spmm_calls: FP64 residuals). */
 rb_status rb_mg_solve(rb_mg_t mg, const rb_cg_params* params, const double* B, int64_t ldb, double* X, int64_t ldx,
                       int32_t k, rb_cg_report* report, rb_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Galerkin initial guess: the best combination of candidate starting vectors.
+ *
+ * Not from the paper, whose solver starts each step from the previous pressure.  For k
+ * systems A x_j = b_j sharing A (SPD, or semi-definite with compatible b_j) and n_cand <= 3
+ * candidate blocks V_a (say the previous two pressures and the learned guess), column j gets
+ * x0_j = sum_a c_aj V_a[:, j] with (V_j^T A V_j) c_j = V_j^T b_j: the Ritz-Galerkin projection
+ * (Saad, Iterative Methods, Sec. 5.1), which minimises the A-norm of the error over the span
+ * of the candidates, so x0 is never worse than any one of them.  Dependent candidates get
+ * coefficient 0 (a Cholesky that skips pivots below 1e-12 of their diagonal); if rounding
+ * leaves the combination's energy x^T A x / 2 - b^T x above the best single candidate's, that
+ * candidate is taken instead.  One SpMM per candidate, one fused reduction, one
+ * elementwise pass.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Workspace bytes for n rows, k columns and n_cand candidates (0 for invalid sizes). */
+size_t rb_galerkin_workspace_bytes(int64_t n, int32_t k, int32_t n_cand);
+
+/* A: square FP64 operator (n x n).  cand: HOST array of n_cand DEVICE pointers to n x k
+ * float64 blocks with leading dimensions ldc[a] (host array); B (ldb), X0 (ldx): float64
+ * DEVICE n x k blocks; X0 may be one of the candidates.  coef: DEVICE k x n_cand doubles
+ * (column j's coefficients at j * n_cand), or NULL.  work: DEVICE, 256-byte aligned,
+ * rb_galerkin_workspace_bytes bytes.  Asynchronous on `stream`; allocates nothing.
+ * RB_EINVAL for null pointers, k outside [1, 64], n_cand outside [1, 3], ld < k, a non-square
+ * or FP32 operator, or a small workspace. */
+rb_status rb_galerkin_guess(rb_op_t A, int32_t k, int32_t n_cand, const double* const* cand, const int64_t* ldc,
+                            const double* B, int64_t ldb, double* X0, int64_t ldx, double* coef, void* work,
+                            size_t work_bytes, rb_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
  * Learned initial guess for the pressure Poisson solve.

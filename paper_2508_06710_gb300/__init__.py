@@ -21,7 +21,7 @@ RB_OK, RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ENOCONV, RB_EBREAKDOWN, RB_ETIMEOUT, R
 STATUS_NAMES = ["RB_OK", "RB_EINVAL", "RB_ENOMEM", "RB_ECUDA", "RB_ENOCONV", "RB_EBREAKDOWN", "RB_ETIMEOUT",
                 "RB_EUNSUPPORTED"]
 RB_F64, RB_F32 = 0, 1
-RB_CSR, RB_SELL, RB_AUTO = 0, 1, 2
+RB_CSR, RB_SELL, RB_AUTO, RB_STENCIL = 0, 1, 2, 3
 RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT, RB_FVM_INTERP_C2S, RB_FVM_INTERP_S2C = 0, 1, 2, 3, 4
 RB_STENCIL_13P, RB_STENCIL_27P = 13, 27
 RB_REFINE_PROLONG, RB_REFINE_RESTRICT, RB_REFINE_PROLONG_T = 0, 1, 2
@@ -29,14 +29,15 @@ RB_MAX_K = 64
 
 # exported C symbols, in the order include/rbspmm.h declares them
 SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_stencil_assemble",
-           "rb_refine_assemble", "rb_mesh_cot_laplacian",
+           "rb_refine_assemble", "rb_mesh_cot_laplacian", "rb_fvm_stencil_create",
            "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
            "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier", "rb_guess_param_count", "rb_guess_create",
            "rb_guess_destroy", "rb_guess_init_params", "rb_guess_set_params", "rb_guess_get_params", "rb_guess_get_grad", "rb_guess_predict",
            "rb_guess_loss_grad", "rb_guess_adam_step", "rb_guess_read_activation", "rb_guess_select",
-           "rb_mg_create", "rb_mg_destroy", "rb_mg_info", "rb_mg_vcycle", "rb_mg_solve"]
+           "rb_mg_create", "rb_mg_destroy", "rb_mg_info", "rb_mg_vcycle", "rb_mg_solve",
+           "rb_galerkin_workspace_bytes", "rb_galerkin_guess"]
 
 
 class RbError(RuntimeError):
@@ -71,7 +72,8 @@ class SpmmSchedule(C.Structure):
 
 
 class MgParams(C.Structure):
-    _fields_ = [("nu", C.c_int32), ("omega", C.c_double), ("min_cells", C.c_int32), ("flexible", C.c_int32)]
+    _fields_ = [("nu", C.c_int32), ("omega", C.c_double), ("min_cells", C.c_int32), ("flexible", C.c_int32),
+                ("matrix_free", C.c_int32)]
 
 
 RB_MG_MAX_LEVELS = 16
@@ -127,6 +129,7 @@ def lib():
         "rb_mesh_cot_laplacian": (C.c_int, [i32, vp, i32, vp, vp, vp, i64, vp, vp, vp, vp]),
         "rb_operator_create": (C.c_int, [C.POINTER(CsrDesc), C.POINTER(BlockDesc), C.c_int, C.c_int, vp,
                                          C.POINTER(vp)]),
+        "rb_fvm_stencil_create": (C.c_int, [C.POINTER(GridDesc), dbl, C.c_int, i32, vp, C.POINTER(vp)]),
         "rb_operator_destroy": (C.c_int, [vp]),
         "rb_operator_info": (C.c_int, [vp, C.POINTER(OpInfo)]),
         "rb_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp, vp]),
@@ -167,6 +170,8 @@ def lib():
         "rb_mg_info": (C.c_int, [vp, C.POINTER(MgInfo)]),
         "rb_mg_vcycle": (C.c_int, [vp, i32, C.c_int, vp, i64, vp, i64, i32, vp]),
         "rb_mg_solve": (C.c_int, [vp, C.POINTER(CgParams), vp, i64, vp, i64, i32, C.POINTER(CgReport), vp]),
+        "rb_galerkin_workspace_bytes": (sz, [i64, i32, i32]),
+        "rb_galerkin_guess": (C.c_int, [vp, i32, i32, C.POINTER(vp), C.POINTER(i64), vp, i64, vp, i64, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -349,6 +354,25 @@ class Operator:
         self.extruded_nz = inf.extruded_nz
 
     @classmethod
+    def stencil(cls, nodes, periodic, scale=1.0, dtype="f64", k_max=1, stream=None):
+        """The FVM Laplacian of the grid times `scale` as a matrix-free operator (rb_fvm_stencil_create):
+        per-axis tables instead of stored entries."""
+        torch = _torch()
+        nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
+        g = _grid_desc(nodes, periodic)
+        h = C.c_void_p()
+        _check(lib().rb_fvm_stencil_create(C.byref(g), float(scale), {"f64": RB_F64, "f32": RB_F32}[dtype],
+                                           int(k_max), _stream(stream), C.byref(h)), "rb_fvm_stencil_create")
+        self = cls.__new__(cls)
+        self.handle = h
+        self.dtype = dtype
+        self._keep = None
+        inf = self.info()
+        self.n_rows, self.n_cols, self.nnz = inf.n_rows, inf.n_cols, inf.nnz
+        self.extruded_nz = 0
+        return self
+
+    @classmethod
     def from_scipy(cls, A, **kw):
         torch = _torch()
         A = A.tocsr()
@@ -440,6 +464,32 @@ def axty(alpha, X, Y, stream=None):
     _check(lib().rb_axty(n, k, _dtype_code(X), float(alpha), _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)),
            "rb_axty")
     return Y
+
+
+def galerkin_guess(A: "Operator", B, cands, X0=None, coef=None, work=None, stream=None):
+    """X0 = the combination of the candidate blocks (each (n, k), float64, CUDA) with the
+    smallest energy-norm error for A X = B, column by column (rb_galerkin_guess).  X0 may be
+    one of the candidates; coef (k x len(cands) float64, CUDA) receives the coefficients."""
+    torch = _torch()
+    B, n, k, ldb = _block(B, "B")
+    cs = [_block(c, "candidate") for c in cands]
+    for c in cs:
+        if c[1] != n or c[2] != k:
+            raise ValueError("every candidate must have the shape of B")
+    if X0 is None:
+        X0 = torch.empty((n, k), dtype=torch.float64, device=B.device)
+    X0, nx, kx, ldx = _block(X0, "X0")
+    if nx != n or kx != k:
+        raise ValueError("X0 must have the shape of B")
+    nc = len(cs)
+    wb = lib().rb_galerkin_workspace_bytes(n, k, nc)
+    if work is None:
+        work = torch.empty(wb, dtype=torch.uint8, device=B.device)
+    ptrs = (C.c_void_p * nc)(*[c[0].data_ptr() for c in cs])
+    lds = (C.c_int64 * nc)(*[c[3] for c in cs])
+    _check(lib().rb_galerkin_guess(A.handle, k, nc, ptrs, lds, _ptr(B), ldb, _ptr(X0), ldx, _ptr(coef), _ptr(work),
+                                   work.numel(), _stream(stream)), "rb_galerkin_guess")
+    return X0
 
 
 # ----------------------------------------------------------------------------- Poisson solve
@@ -551,11 +601,12 @@ class Multigrid:
     """Geometric multigrid hierarchy of -L on a Cartesian grid (rb_mg_create): the V-cycle
     preconditioner and the multigrid-preconditioned CG solve of the pressure equation."""
 
-    def __init__(self, nodes, periodic, k_max=1, nu=2, omega=2.0 / 3.0, min_cells=4, flexible=True, stream=None):
+    def __init__(self, nodes, periodic, k_max=1, nu=2, omega=2.0 / 3.0, min_cells=4, flexible=True, matrix_free=True,
+                 stream=None):
         torch = _torch()
         self._nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
         g = _grid_desc(self._nodes, periodic)
-        prm = MgParams(int(nu), float(omega), int(min_cells), 1 if flexible else 0)
+        prm = MgParams(int(nu), float(omega), int(min_cells), 1 if flexible else 0, 1 if matrix_free else 0)
         h = C.c_void_p()
         _check(lib().rb_mg_create(C.byref(g), int(k_max), C.byref(prm), _stream(stream), C.byref(h)), "rb_mg_create")
         self.handle = h

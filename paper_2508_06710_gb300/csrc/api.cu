@@ -93,7 +93,8 @@ rb_status dalloc(rb_op* op, T** p, size_t count) {
 void free_op(rb_op* op) {
   if (!op) return;
   void* ptrs[] = {op->row_ptr, op->col_idx, op->vals,    op->sell_ptr, op->sell_width, op->sell_row,
-                  op->sell_col, op->sell_val, op->dinv64, op->dinv32,  op->zw64,       op->zw32, op->err};
+                  op->sell_col, op->sell_val, op->dinv64, op->dinv32,  op->zw64,       op->zw32, op->err,
+                  op->st_w[0],  op->st_w[1],  op->st_w[2],  op->st_ic[0], op->st_ic[1],  op->st_ic[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete op;

@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "stencil7.cuh"
 
 namespace rb {
 namespace {
@@ -687,6 +688,86 @@ rb_status launch_prolong_t(const GridDev& g, int32_t* rp, int32_t* ci, double* v
   return RB_OK;
 }
 
+// Per-axis tables of the matrix-free operators (stencil7.cuh): cell widths and inverse centre
+// distances of each axis (the Laplacian), and the 1-D prolongation and its transpose (the
+// transfers), in FP64 and rounded to FP32.
+__global__ void k_stencil7_axis(GridDev g, int d, double* __restrict__ w64, double* __restrict__ ic64,
+                                float* __restrict__ w32, float* __restrict__ ic32) {
+  const int n = g.n[d];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= n; t += gridDim.x * blockDim.x) {
+    if (t < n) {
+      const double w = width(g, d, t);
+      w64[t] = w;
+      w32[t] = (float)w;
+    }
+    double ic = 0.0;
+    if (g.per[d]) ic = 1.0 / centre_dist(g, d, t == n ? 0 : t);
+    else if (t > 0 && t < n) ic = 1.0 / centre_dist(g, d, t);
+    ic64[t] = ic;
+    ic32[t] = (float)ic;
+  }
+}
+
+__global__ void k_transfer_axis(GridDev g, int d, PAxis<double>* __restrict__ pa64, TAxisTab<double>* __restrict__ ta64,
+                                PAxis<float>* __restrict__ pa32, TAxisTab<float>* __restrict__ ta32) {
+  const int nf = g.n[d], nc = nf / 2;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf + nc; t += gridDim.x * blockDim.x) {
+    if (t < nf) {
+      int c[2];
+      double w[2];
+      prolong_axis(g, d, t, c, w);
+      pa64[t] = PAxis<double>{c[0], c[1], w[0], w[1]};
+      pa32[t] = PAxis<float>{c[0], c[1], (float)w[0], (float)w[1]};
+    } else {
+      const int I = t - nf;
+      TAxis r;
+      prolong_t_axis(g, d, I, r);
+      TAxisTab<double> a{};
+      TAxisTab<float> b{};
+      a.cnt = b.cnt = r.cnt;
+      for (int q = 0; q < r.cnt; ++q) {
+        a.t[q] = b.t[q] = r.t[q];
+        a.w[q] = r.w[q];
+        b.w[q] = (float)r.w[q];
+      }
+      ta64[I] = a;
+      ta32[I] = b;
+    }
+  }
+}
+
+}  // namespace
+
+rb_status stencil7_tables(const rb_grid_desc* grid, double* w64[3], double* ic64[3], float* w32[3], float* ic32[3],
+                          cudaStream_t s) {
+  GridDev g;
+  RB_TRY(grid_from_desc(grid, g));
+  for (int d = 0; d < 3; ++d) {
+    k_stencil7_axis<<<(g.n[d] + 1 + 127) / 128, 128, 0, s>>>(g, d, w64[d], ic64[d], w32[d], ic32[d]);
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+rb_status transfer_tables(const rb_grid_desc* fine, PAxis<double>* pa64[3], TAxisTab<double>* ta64[3],
+                          PAxis<float>* pa32[3], TAxisTab<float>* ta32[3], cudaStream_t s) {
+  GridDev g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = fine->n[d];
+    g.per[d] = fine->periodic[d] ? 1 : 0;
+    g.nodes[d] = fine->nodes[d];
+    RB_REQUIRE(g.n[d] >= 4 && g.n[d] % 2 == 0, "transfer tables: axis %d has %d cells (need an even number >= 4)", d,
+               g.n[d]);
+  }
+  for (int d = 0; d < 3; ++d) {
+    const int m = g.n[d] + g.n[d] / 2;
+    k_transfer_axis<<<(m + 127) / 128, 128, 0, s>>>(g, d, pa64[d], ta64[d], pa32[d], ta32[d]);
+  }
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+namespace {
 }  // namespace
 }  // namespace rb
 

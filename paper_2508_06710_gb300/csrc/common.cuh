@@ -116,6 +116,12 @@ struct rb_op {
   double* zw64 = nullptr;
   float* zw32 = nullptr;
   int64_t device_bytes = 0;
+  // matrix-free 7-point Laplacian of a Cartesian grid (format RB_STENCIL): per-axis cell
+  // widths and inverse centre distances in the operator's type, and the scale
+  int32_t st_n[3] = {0, 0, 0}, st_per[3] = {0, 0, 0};
+  void* st_w[3] = {nullptr, nullptr, nullptr};
+  void* st_ic[3] = {nullptr, nullptr, nullptr};
+  double st_scale = 1.0;
   int* err = nullptr;  // device status word: nonzero after a bounded wait in a kernel gave up
   std::map<int, rb::SpmmSched> tuned;  // k -> schedule chosen by rb_tune_spmm
 };

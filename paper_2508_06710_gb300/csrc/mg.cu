@@ -42,6 +42,7 @@
 #include "common.cuh"
 #include "reduce.cuh"
 #include "spmm_impl.cuh"
+#include "stencil7.cuh"
 
 namespace rb {
 
@@ -125,8 +126,8 @@ enum SweepMode : int { SW_JACOBI = 0, SW_RESID = 1 };
 // One product-shaped pass over level l: with e the iterate (a.X) and r the level's right-hand
 // side, writes out = e + omega D^-1 (r - A e) (SW_JACOBI) or out = r - A e (SW_RESID).  With
 // DOTS (the last sweep of the outer cycle), also r . out and q . out per column.
-template <typename T, int VEC, int MODE, bool DOTS>
-__global__ void __launch_bounds__(kThreads) k_mg_sweep(CsrArgs<T> a, const T* __restrict__ r,
+template <typename T, int VEC, int MODE, bool DOTS, bool ST>
+__global__ void __launch_bounds__(kThreads) k_mg_sweep(CsrArgs<T> a, Stencil7<T> st, const T* __restrict__ r,
                                                         const T* __restrict__ dinv, T omega, T* __restrict__ out,
                                                         MgDots dd, const int* __restrict__ gate) {
   if (gate && *gate == 0) return;
@@ -145,7 +146,12 @@ __global__ void __launch_bounds__(kThreads) k_mg_sweep(CsrArgs<T> a, const T* __
     T acc[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] = T(0);
-    row_accumulate_direct<T, VEC, 1>(a, row, chunk, 0, active, acc);
+    if constexpr (ST) {
+      T unused;
+      if (active) stencil7_apply<T, VEC>(st, a.X, a.ldx, row, chunk * VEC, acc, unused);
+    } else {
+      row_accumulate_direct<T, VEC, 1>(a, row, chunk, 0, active, acc);
+    }
     if (active) {
       const int64_t o = row * a.k + chunk * VEC;
       const Vec<T, VEC> rv = ldv<T, VEC>(r + o);
@@ -227,6 +233,45 @@ __global__ void __launch_bounds__(kThreads) k_mg_prolong_add(CsrArgs<T> a, const
   }
 }
 
+// Matrix-free transfers (stencil7.cuh): e += P e_c over the fine rows, r_c = P^T r over the
+// coarse rows
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_mg_prolong_st(Transfer3<T> tr, int64_t n, int k, int kp,
+                                                             const T* __restrict__ ec, T* __restrict__ e,
+                                                             const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  if (chunk * VEC >= k) return;
+  for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < n; row += (int64_t)gridDim.x * R) {
+    T acc[VEC];
+    prolong_apply<T, VEC>(tr, ec, k, row, chunk * VEC, acc);
+    const int64_t o = row * k + chunk * VEC;
+    Vec<T, VEC> y = ldv_rw<T, VEC>(e + o);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) y.v[q] += acc[q];
+    stv<T, VEC>(e + o, y);
+  }
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_mg_restrict_st(Transfer3<T> tr, int64_t nc, int k, int kp,
+                                                              const T* __restrict__ rf, T* __restrict__ rc,
+                                                              const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  if (chunk * VEC >= k) return;
+  for (int64_t row = (int64_t)blockIdx.x * R + threadIdx.x / kp; row < nc; row += (int64_t)gridDim.x * R) {
+    T acc[VEC];
+    restrict_apply<T, VEC>(tr, rf, k, row, chunk * VEC, acc);
+    Vec<T, VEC> y;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) y.v[q] = acc[q];
+    stv<T, VEC>(rc + row * k + chunk * VEC, y);
+  }
+}
+
 // z = Ainv r on the coarsest level (Ainv dense FP64, nc x nc): one block per row, lanes over
 // (m, column), the m lanes folded through shared memory in a fixed order
 template <typename T>
@@ -253,8 +298,8 @@ __global__ void __launch_bounds__(kThreads) k_mg_coarse(int nc, int k, const dou
 // ---------------------------------------------------------------------- CG kernels
 
 // q = A p, p . q; the last block forms alpha = (r . z) / (p . q) per column
-template <typename T, int VEC>
-__global__ void __launch_bounds__(kThreads) k_mgcg_q(CsrArgs<T> a, MgScal* __restrict__ sc,
+template <typename T, int VEC, bool ST>
+__global__ void __launch_bounds__(kThreads) k_mgcg_q(CsrArgs<T> a, Stencil7<T> st, MgScal* __restrict__ sc,
                                                       double* __restrict__ partials) {
   if (sc->n_active == 0) return;
   __shared__ RedSmem<1> red;
@@ -271,7 +316,12 @@ __global__ void __launch_bounds__(kThreads) k_mgcg_q(CsrArgs<T> a, MgScal* __res
     T acc[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] = T(0);
-    row_accumulate_direct<T, VEC, 1, false, true>(a, row, chunk, 0, active, acc);
+    if constexpr (ST) {
+      T unused;
+      if (active) stencil7_apply<T, VEC>(st, a.X, a.ldx, row, chunk * VEC, acc, unused);
+    } else {
+      row_accumulate_direct<T, VEC, 1, false, true>(a, row, chunk, 0, active, acc);
+    }
     if (active) {
       const int64_t o = row * a.k + chunk * VEC;
       const Vec<T, VEC> pv = ldv<T, VEC>(a.X + o);
@@ -650,6 +700,11 @@ struct rb_mg_level {
   rb_op* A[2] = {nullptr, nullptr};   // -L: [0] FP64, [1] FP32
   rb_op* P[2] = {nullptr, nullptr};   // prolongation from the next level (this level's rows)
   rb_op* PT[2] = {nullptr, nullptr};  // its transpose (the next level's rows)
+  rb_op* S32 = nullptr;               // -L matrix-free in FP32 (the FP32 cycle's operator)
+  // matrix-free transfers to the next level: per-axis 1-D maps (FP32)
+  rb::PAxis<float>* pa32[3] = {nullptr, nullptr, nullptr};
+  rb::TAxisTab<float>* ta32[3] = {nullptr, nullptr, nullptr};
+  void* tab_mem = nullptr;  // one allocation holding the transfer tables (both precisions)
   // level vectors, n x k_max doubles each (used as FP32 by the FP32 cycle)
   void *rhs = nullptr, *ea = nullptr, *eb = nullptr, *res = nullptr, *out = nullptr;
 };
@@ -701,7 +756,8 @@ void mg_free(rb_mg* g) {
       if (l.P[d]) rb_operator_destroy(l.P[d]);
       if (l.PT[d]) rb_operator_destroy(l.PT[d]);
     }
-    for (void* p : {l.rhs, l.ea, l.eb, l.res, l.out})
+    if (l.S32) rb_operator_destroy(l.S32);
+    for (void* p : {l.rhs, l.ea, l.eb, l.res, l.out, l.tab_mem})
       if (p) cudaFree(p);
   }
   for (void* p : {(void*)g->ainv, (void*)g->x64, (void*)g->rt, g->x, g->r, g->p, g->q, g->z, (void*)g->sc,
@@ -763,6 +819,7 @@ rb_status build_hierarchy(rb_mg* g, const rb_grid_desc* grid, cudaStream_t s) {
       RB_TRY(rb_fvm_assemble(&cur, RB_FVM_LAPLACIAN, -1.0, t.rp, t.ci, t.va, reinterpret_cast<rb_stream_t>(s)));
       RB_TRY(make_ops(nr, ncol, nnz, t.rp, t.ci, t.va, g->k_max, s, lv.A));
     }
+    RB_TRY(rb_fvm_stencil_create(&cur, -1.0, RB_F32, g->k_max, reinterpret_cast<rb_stream_t>(s), &lv.S32));
     bool coarsen = l + 1 < kMgMaxLevels;
     for (int d = 0; d < 3; ++d) coarsen = coarsen && cur.n[d] % 2 == 0 && cur.n[d] / 2 >= mc;
     if (coarsen) {
@@ -773,6 +830,27 @@ rb_status build_hierarchy(rb_mg* g, const rb_grid_desc* grid, cudaStream_t s) {
       RB_TRY(make_ops((int)nf, (int)ncoarse, 8 * nf, t.rp, t.ci, t.va, g->k_max, s, lv.P));
       RB_TRY(rb_refine_assemble(&cur, RB_REFINE_PROLONG_T, t.rp, t.ci, t.va, reinterpret_cast<rb_stream_t>(s)));
       RB_TRY(make_ops((int)ncoarse, (int)nf, 8 * nf, t.rp, t.ci, t.va, g->k_max, s, lv.PT));
+      // per-axis transfer tables, FP64 and FP32, in one allocation
+      size_t bytes = 0;
+      for (int d = 0; d < 3; ++d)
+        bytes += (sizeof(PAxis<double>) + sizeof(PAxis<float>)) * cur.n[d] +
+                 (sizeof(TAxisTab<double>) + sizeof(TAxisTab<float>)) * (cur.n[d] / 2) + 64;
+      RB_TRY(mg_alloc(g, reinterpret_cast<char**>(&lv.tab_mem), bytes));
+      char* q = static_cast<char*>(lv.tab_mem);
+      PAxis<double>* pa64[3];
+      TAxisTab<double>* ta64[3];
+      auto carve = [&q](size_t b) {
+        char* r = q;
+        q += (b + 15) & ~(size_t)15;
+        return r;
+      };
+      for (int d = 0; d < 3; ++d) {
+        pa64[d] = reinterpret_cast<PAxis<double>*>(carve(sizeof(PAxis<double>) * cur.n[d]));
+        ta64[d] = reinterpret_cast<TAxisTab<double>*>(carve(sizeof(TAxisTab<double>) * (cur.n[d] / 2)));
+        lv.pa32[d] = reinterpret_cast<PAxis<float>*>(carve(sizeof(PAxis<float>) * cur.n[d]));
+        lv.ta32[d] = reinterpret_cast<TAxisTab<float>*>(carve(sizeof(TAxisTab<float>) * (cur.n[d] / 2)));
+      }
+      RB_TRY(transfer_tables(&cur, pa64, ta64, lv.pa32, lv.ta32, s));
     }
     // level vectors (the finest level's right-hand side and output are the solve's r and z)
     const size_t cnt = (size_t)lv.cells * g->k_max;
@@ -858,6 +936,50 @@ struct Cycle {
     return wave_grid(kern, (rows + kThreads / kp - 1) / (kThreads / kp));
   }
 
+  // the FP32 cycle runs matrix-free (stencil7.cuh) unless the hierarchy was built otherwise
+  bool mf() const { return sizeof(T) == 4 && g->prm.matrix_free; }
+
+  static Stencil7<T> st_view(const rb_op* op) {
+    Stencil7<T> v{};
+    if (op) {
+      for (int d = 0; d < 3; ++d) {
+        v.n[d] = op->st_n[d];
+        v.per[d] = op->st_per[d];
+        v.w[d] = static_cast<const T*>(op->st_w[d]);
+        v.ic[d] = static_cast<const T*>(op->st_ic[d]);
+      }
+      v.scale = (T)op->st_scale;
+    }
+    return v;
+  }
+
+  Transfer3<T> tr_view(const rb_mg_level& lv) const {
+    Transfer3<T> t{};
+    if constexpr (sizeof(T) == 4) {
+      for (int d = 0; d < 3; ++d) {
+        t.nf[d] = lv.n[d];
+        t.pa[d] = lv.pa32[d];
+        t.ta[d] = lv.ta32[d];
+      }
+    }
+    return t;
+  }
+
+  // one product-shaped pass over a level (CSR or matrix-free)
+  template <int MODE, bool DOTS>
+  void sweep(const rb_mg_level& lv, const T* e, const T* r, const T* dinv, T* out, const MgDots& dd) const {
+    const T omega = (T)g->prm.omega;
+    if (mf()) {
+      auto* kern = &k_mg_sweep<T, VEC, MODE, DOTS, true>;
+      kern<<<grid(kern, lv.cells), kThreads, 0, s>>>(csr_args<T>(lv.S32, e, nullptr, k, kp), st_view(lv.S32), r, dinv,
+                                                     omega, out, dd, gate);
+    } else {
+      auto* kern = &k_mg_sweep<T, VEC, MODE, DOTS, false>;
+      kern<<<grid(kern, lv.cells), kThreads, 0, s>>>(csr_args<T>(lv.A[ti()], e, nullptr, k, kp), st_view(nullptr), r,
+                                                     dinv, omega, out, dd, gate);
+    }
+  }
+
   // z = B r on level l (r, z: n_l x k blocks of T, ld = k); dd: dots of the last sweep
   rb_status run(int l, const T* r, T* z, const MgDots* dd) const {
     const rb_mg_level& lv = g->lv[l];
@@ -869,41 +991,37 @@ struct Cycle {
       RB_REQUIRE(dd == nullptr, "rb_mg: a one-level hierarchy cannot precondition CG (the grid does not coarsen)");
       return RB_OK;
     }
-    const rb_op* A = lv.A[ti()];
-    const T* dinv = dinv_of<T>(A);
+    const T* dinv = dinv_of<T>(mf() ? lv.S32 : lv.A[ti()]);
     T* bufs[2] = {static_cast<T*>(lv.ea), static_cast<T*>(lv.eb)};
     int c = 0;
     k_mg_smooth0<T, VEC><<<grid(&k_mg_smooth0<T, VEC>, lv.cells), kThreads, 0, s>>>(lv.cells, k, kp, r, dinv, omega,
                                                                                      bufs[0], gate);
     MgDots none;
-    for (int it = 1; it < nu; ++it, c ^= 1) {
-      auto* kern = &k_mg_sweep<T, VEC, SW_JACOBI, false>;
-      kern<<<grid(kern, lv.cells), kThreads, 0, s>>>(csr_args<T>(A, bufs[c], nullptr, k, kp), r, dinv, omega,
-                                                     bufs[c ^ 1], none, gate);
-    }
-    {  // residual, restriction
-      auto* kern = &k_mg_sweep<T, VEC, SW_RESID, false>;
-      kern<<<grid(kern, lv.cells), kThreads, 0, s>>>(csr_args<T>(A, bufs[c], nullptr, k, kp), r, dinv, omega,
-                                                     static_cast<T*>(lv.res), none, gate);
+    for (int it = 1; it < nu; ++it, c ^= 1) sweep<SW_JACOBI, false>(lv, bufs[c], r, dinv, bufs[c ^ 1], none);
+    // residual, restriction, the next level, prolongation-add
+    sweep<SW_RESID, false>(lv, bufs[c], r, dinv, static_cast<T*>(lv.res), none);
+    const rb_mg_level& nx = g->lv[l + 1];
+    if (mf()) {
+      auto* rk = &k_mg_restrict_st<T, VEC>;
+      rk<<<grid(rk, nx.cells), kThreads, 0, s>>>(tr_view(lv), nx.cells, k, kp, static_cast<const T*>(lv.res),
+                                                static_cast<T*>(nx.rhs), gate);
+    } else {
       const rb_op* PT = lv.PT[ti()];
-      const rb_mg_level& nx = g->lv[l + 1];
       RB_TRY(spmm_launch(PT, pick_sched(PT, k, k, k, lv.res, nx.rhs), lv.res, k, nx.rhs, k, k, nullptr, s));
-      RB_TRY(run(l + 1, static_cast<const T*>(nx.rhs), static_cast<T*>(nx.out), nullptr));
-      const rb_op* P = lv.P[ti()];
+    }
+    RB_TRY(run(l + 1, static_cast<const T*>(nx.rhs), static_cast<T*>(nx.out), nullptr));
+    if (mf()) {
+      auto* pk = &k_mg_prolong_st<T, VEC>;
+      pk<<<grid(pk, lv.cells), kThreads, 0, s>>>(tr_view(lv), lv.cells, k, kp, static_cast<const T*>(nx.out), bufs[c],
+                                                gate);
+    } else {
       auto* pk = &k_mg_prolong_add<T, VEC>;
-      pk<<<grid(pk, lv.cells), kThreads, 0, s>>>(csr_args<T>(P, nx.out, bufs[c], k, kp), gate);
+      pk<<<grid(pk, lv.cells), kThreads, 0, s>>>(csr_args<T>(lv.P[ti()], nx.out, bufs[c], k, kp), gate);
     }
     for (int it = 1; it <= nu; ++it, c ^= 1) {
       T* dst = (it == nu) ? z : bufs[c ^ 1];
-      if (it == nu && dd) {
-        auto* kern = &k_mg_sweep<T, VEC, SW_JACOBI, true>;
-        kern<<<grid(kern, lv.cells), kThreads, 0, s>>>(csr_args<T>(A, bufs[c], nullptr, k, kp), r, dinv, omega, dst,
-                                                       *dd, gate);
-      } else {
-        auto* kern = &k_mg_sweep<T, VEC, SW_JACOBI, false>;
-        kern<<<grid(kern, lv.cells), kThreads, 0, s>>>(csr_args<T>(A, bufs[c], nullptr, k, kp), r, dinv, omega, dst,
-                                                       none, gate);
-      }
+      if (it == nu && dd) sweep<SW_JACOBI, true>(lv, bufs[c], r, dinv, dst, *dd);
+      else sweep<SW_JACOBI, false>(lv, bufs[c], r, dinv, dst, none);
     }
     RB_CUDA(cudaGetLastError());
     return RB_OK;
@@ -923,8 +1041,15 @@ rb_status cg_iteration(const rb_mg* g, const Cycle<T, VEC>& cy, bool inner, int 
   T* q = static_cast<T*>(g->q);
   T* z = static_cast<T*>(g->z);
   cudaStream_t s = cy.s;
-  auto* kq = &k_mgcg_q<T, VEC>;
-  kq<<<cy.grid(kq, n), kThreads, 0, s>>>(csr_args<T>(A, p, q, k, kp), g->sc, g->partials);
+  if (cy.mf()) {
+    auto* kq = &k_mgcg_q<T, VEC, true>;
+    kq<<<cy.grid(kq, n), kThreads, 0, s>>>(csr_args<T>(l0.S32, p, q, k, kp), Cycle<T, VEC>::st_view(l0.S32), g->sc,
+                                           g->partials);
+  } else {
+    auto* kq = &k_mgcg_q<T, VEC, false>;
+    kq<<<cy.grid(kq, n), kThreads, 0, s>>>(csr_args<T>(A, p, q, k, kp), Cycle<T, VEC>::st_view(nullptr), g->sc,
+                                           g->partials);
+  }
   if (inner) {
     auto* kx = &k_mgcg_xr<T, VEC, true>;
     kx<<<cy.grid(kx, n), kThreads, 0, s>>>(n, k, kp, x, r, p, q, g->sc, g->partials);
@@ -1176,7 +1301,7 @@ extern "C" rb_status rb_mg_create(const rb_grid_desc* grid, int32_t k_max, const
   RB_REQUIRE(grid && out, "rb_mg_create: null argument");
   *out = nullptr;
   RB_REQUIRE(k_max >= 1 && k_max <= RB_MAX_K, "rb_mg_create: k_max %d outside [1, %d]", k_max, RB_MAX_K);
-  rb_mg_params prm{2, 2.0 / 3.0, 4, 1};
+  rb_mg_params prm{2, 2.0 / 3.0, 4, 1, 1};
   if (params) prm = *params;
   RB_REQUIRE(prm.nu >= 1 && prm.nu <= 16, "rb_mg_create: nu = %d outside [1, 16]", prm.nu);
   RB_REQUIRE(prm.omega > 0.0 && prm.omega <= 1.0, "rb_mg_create: omega = %g outside (0, 1]", prm.omega);

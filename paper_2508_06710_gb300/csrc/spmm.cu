@@ -22,6 +22,8 @@ rb_status spmm_launch_f64(const rb_op* op, const SpmmSched& sc, const void* X, i
                           int k, const double* cs, cudaStream_t s);
 rb_status spmm_launch_f32(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy,
                           int k, const double* cs, cudaStream_t s);
+rb_status stencil_spmm_launch(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                              int k, const double* cs, cudaStream_t s);
 
 namespace {
 
@@ -31,7 +33,7 @@ bool sched_valid(const rb_op* op, const SpmmSched& sc, int k, int64_t ldx, int64
   if (sc.vec < 1 || sc.vec > 4 || !vec_ok(eb, sc.vec, k, ldx, ldy, X, Y)) return false;
   if (sc.kp != next_pow2(k / sc.vec) || sc.kp > 32) return false;
   if (sc.kp * sc.lpr > 32) return false;
-  if (op->format == RB_SELL && (sc.lpr != 1 || sc.stage)) return false;
+  if ((op->format == RB_SELL || op->format == RB_STENCIL) && (sc.lpr != 1 || sc.stage)) return false;
   if (sc.stage == 2 && sc.lpr != 1) return false;
   if (op->ext_nz > 0 && sc.vec == 3) return false;  // the spanwise epilogue takes widths dividing Nz only
   if (op->ext_nz > 0 && (op->ext_nz % sc.vec)) return false;
@@ -80,6 +82,7 @@ SpmmSched default_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const 
 
 rb_status spmm_launch(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy, int k,
                       const double* cs, cudaStream_t s) {
+  if (op->format == RB_STENCIL) return stencil_spmm_launch(op, sc, X, ldx, Y, ldy, k, cs, s);
   if (op->dtype == RB_F64) return spmm_launch_f64(op, sc, X, ldx, Y, ldy, k, cs, s);
   return spmm_launch_f32(op, sc, X, ldx, Y, ldy, k, cs, s);
 }
@@ -208,6 +211,8 @@ extern "C" rb_status rb_set_spmm_schedule(rb_op_t A, int32_t k, const rb_spmm_sc
   RB_REQUIRE(sc.stage >= 0 && sc.stage <= 2, "rb_set_spmm_schedule: stage must be 0, 1 or 2");
   RB_REQUIRE(sc.kp * sc.lpr <= 32, "rb_set_spmm_schedule: (k / vec) * lpr exceeds a warp");
   RB_REQUIRE(!(A->format == RB_SELL && (sc.lpr != 1 || sc.stage)), "rb_set_spmm_schedule: sliced ELL takes lpr 1, stage 0");
+  RB_REQUIRE(!(A->format == RB_STENCIL && (sc.lpr != 1 || sc.stage)),
+             "rb_set_spmm_schedule: a stencil operator takes lpr 1, stage 0");
   RB_REQUIRE(!(sc.stage == 2 && sc.lpr != 1), "rb_set_spmm_schedule: the TMA pipeline takes lpr 1");
   RB_REQUIRE(!(A->ext_nz > 0 && (sc.vec == 3 || A->ext_nz % sc.vec)), "rb_set_spmm_schedule: vec must divide Nz");
   A->tuned[k] = sc;

@@ -1,0 +1,194 @@
+// Matrix-free operators of Cartesian FVM grids: the 7-point Laplacian and the refinement
+// transfers applied from per-axis tables instead of stored entries.
+//
+// The repeated-block structure of Sec. 2 reads each matrix entry once for all k columns; on a
+// Cartesian grid the entries themselves repeat: every coefficient of the symmetry-preserving
+// Laplacian (Sec. 3, Eq. (ns); L = M G) is a product of one-dimensional quantities,
+//   across the x face between cells (i-1, j, k) and (i, j, k):  w_y[j] w_z[k] / d_x[i],
+// w the cell widths and d the distances between neighbouring cell centres (wrapped on a
+// periodic axis), and likewise for y and z; the diagonal is minus the sum of the six.  So the
+// operator is the grid's 2 (n_x + n_y + n_z) + 3 numbers, and an SpMM with it reads only X
+// and writes only Y (the "stencil descriptor" form: no index or value streams at all).  The
+// trilinear prolongation P of the refinement maps and its transpose are products of per-axis
+// 1-D maps in the same way.
+//
+// Tables (device arrays, in the operator's type T):
+//   w[d][t]   width of cell t along axis d, t < n[d]
+//   ic[d][f]  1 / d_f for face f = 0 .. n[d] of axis d (face f between cells f - 1 and f),
+//             0 on the wall faces f = 0 and f = n[d] of a bounded axis (excluded faces: the
+//             homogeneous Neumann condition); on a periodic axis face n[d] is face 0
+#pragma once
+
+#include "common.cuh"
+
+namespace rb {
+
+template <typename T>
+struct Stencil7 {
+  int n[3];
+  int per[3];
+  const T* w[3];
+  const T* ic[3];
+  T scale;  // the operator is scale * L
+};
+
+// The row's cell (i, j, k), its six face coefficients of L and the diagonal -sum of them
+template <typename T>
+struct Coef7 {
+  int i, j, k;
+  T cxm, cxp, cym, cyp, czm, czp, diag;
+};
+
+template <typename T>
+__device__ __forceinline__ Coef7<T> stencil7_coef(const Stencil7<T>& s, int64_t row) {
+  Coef7<T> c;
+  const int nx = s.n[0], ny = s.n[1];
+  const int64_t plane = (int64_t)nx * ny;
+  c.k = (int)(row / plane);
+  const int64_t rem = row - (int64_t)c.k * plane;
+  c.j = (int)(rem / nx);
+  c.i = (int)(rem - (int64_t)c.j * nx);
+  const T wx = __ldg(s.w[0] + c.i), wy = __ldg(s.w[1] + c.j), wz = __ldg(s.w[2] + c.k);
+  const T ayz = wy * wz, axz = wx * wz, axy = wx * wy;
+  c.cxm = ayz * __ldg(s.ic[0] + c.i), c.cxp = ayz * __ldg(s.ic[0] + c.i + 1);
+  c.cym = axz * __ldg(s.ic[1] + c.j), c.cyp = axz * __ldg(s.ic[1] + c.j + 1);
+  c.czm = axy * __ldg(s.ic[2] + c.k), c.czp = axy * __ldg(s.ic[2] + c.k + 1);
+  c.diag = -(((c.cxm + c.cxp) + (c.cym + c.cyp)) + (c.czm + c.czp));
+  return c;
+}
+
+// (A X)[row, col0 .. col0 + VEC) into acc, and the inverse diagonal of A into dinv.
+template <typename T, int VEC>
+__device__ __forceinline__ void stencil7_apply(const Stencil7<T>& s, const T* __restrict__ X, int64_t ldx, int64_t row,
+                                               int col0, T (&acc)[VEC], T& dinv) {
+  const Coef7<T> cf = stencil7_coef(s, row);
+  const int i = cf.i, j = cf.j, k = cf.k;
+  const int nx = s.n[0], ny = s.n[1];
+  const int64_t plane = (int64_t)nx * ny;
+  const T cxm = cf.cxm, cxp = cf.cxp, cym = cf.cym, cyp = cf.cyp, czm = cf.czm, czp = cf.czp, diag = cf.diag;
+  dinv = T(1) / (s.scale * diag);
+  // neighbour rows (a wall neighbour has coefficient 0: any valid row will do, take this one)
+  const int im = i > 0 ? i - 1 : (s.per[0] ? nx - 1 : i), ip = i + 1 < nx ? i + 1 : (s.per[0] ? 0 : i);
+  const int jm = j > 0 ? j - 1 : (s.per[1] ? ny - 1 : j), jp = j + 1 < ny ? j + 1 : (s.per[1] ? 0 : j);
+  const int nz = s.n[2];
+  const int km = k > 0 ? k - 1 : (s.per[2] ? nz - 1 : k), kp = k + 1 < nz ? k + 1 : (s.per[2] ? 0 : k);
+  const T* xc = X + col0;
+  const Vec<T, VEC> x0 = ldv<T, VEC>(xc + row * ldx);
+  const Vec<T, VEC> a = ldv<T, VEC>(xc + (row - i + im) * ldx);
+  const Vec<T, VEC> b = ldv<T, VEC>(xc + (row - i + ip) * ldx);
+  const Vec<T, VEC> c = ldv<T, VEC>(xc + (row + (int64_t)(jm - j) * nx) * ldx);
+  const Vec<T, VEC> d = ldv<T, VEC>(xc + (row + (int64_t)(jp - j) * nx) * ldx);
+  const Vec<T, VEC> e = ldv<T, VEC>(xc + (row + (int64_t)(km - k) * plane) * ldx);
+  const Vec<T, VEC> f = ldv<T, VEC>(xc + (row + (int64_t)(kp - k) * plane) * ldx);
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) {
+    T y = diag * x0.v[q];
+    y = fma(cxm, a.v[q], y);
+    y = fma(cxp, b.v[q], y);
+    y = fma(cym, c.v[q], y);
+    y = fma(cyp, d.v[q], y);
+    y = fma(czm, e.v[q], y);
+    y = fma(czp, f.v[q], y);
+    acc[q] = s.scale * y;
+  }
+}
+
+// ----------------------------------------------------------------------------- transfers
+
+// The 1-D prolongation of one fine position: the two coarse positions and their weights
+template <typename T>
+struct PAxis {
+  int c0, c1;
+  T w0, w1;
+};
+
+// The 1-D transpose of one coarse position: the fine positions that use it (at most 8) and
+// their weights, sorted by position
+template <typename T>
+struct TAxisTab {
+  int cnt;
+  int t[8];
+  T w[8];
+};
+
+template <typename T>
+struct Transfer3 {
+  int nf[3];               // fine cells per axis (coarse: nf / 2)
+  const PAxis<T>* pa[3];   // per fine position
+  const TAxisTab<T>* ta[3];  // per coarse position
+};
+
+// (P E_c)[fine row, col0 .. col0 + VEC): trilinear interpolation from the coarse block
+template <typename T, int VEC>
+__device__ __forceinline__ void prolong_apply(const Transfer3<T>& tr, const T* __restrict__ Ec, int k, int64_t row,
+                                              int col0, T (&acc)[VEC]) {
+  const int nx = tr.nf[0], ny = tr.nf[1];
+  const int64_t plane = (int64_t)nx * ny;
+  const int kk = (int)(row / plane);
+  const int64_t rem = row - (int64_t)kk * plane;
+  const int j = (int)(rem / nx);
+  const int i = (int)(rem - (int64_t)j * nx);
+  const PAxis<T> px = tr.pa[0][i], py = tr.pa[1][j], pz = tr.pa[2][kk];
+  const int cnx = nx / 2, cny = ny / 2;
+  const int cx[2] = {px.c0, px.c1}, cy[2] = {py.c0, py.c1}, cz[2] = {pz.c0, pz.c1};
+  const T wx[2] = {px.w0, px.w1}, wy[2] = {py.w0, py.w1}, wz[2] = {pz.w0, pz.w1};
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) acc[q] = T(0);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const T wab = wz[a] * wy[b];
+      const int64_t base = (int64_t)cnx * (cy[b] + (int64_t)cny * cz[a]);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T wt = wab * wx[c];
+        const Vec<T, VEC> v = ldv<T, VEC>(Ec + (base + cx[c]) * k + col0);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = fma(wt, v.v[q], acc[q]);
+      }
+    }
+}
+
+// (P^T R_f)[coarse row, col0 .. col0 + VEC): the weighted sum over the fine cells whose
+// interpolation uses this coarse cell
+template <typename T, int VEC>
+__device__ __forceinline__ void restrict_apply(const Transfer3<T>& tr, const T* __restrict__ Rf, int k, int64_t row,
+                                               int col0, T (&acc)[VEC]) {
+  const int cnx = tr.nf[0] / 2, cny = tr.nf[1] / 2;
+  const int64_t plane = (int64_t)cnx * cny;
+  const int K3 = (int)(row / plane);
+  const int64_t rem = row - (int64_t)K3 * plane;
+  const int J = (int)(rem / cnx);
+  const int I = (int)(rem - (int64_t)J * cnx);
+  const TAxisTab<T>& tx = tr.ta[0][I];
+  const TAxisTab<T>& ty = tr.ta[1][J];
+  const TAxisTab<T>& tz = tr.ta[2][K3];
+  const int nx = tr.nf[0], ny = tr.nf[1];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) acc[q] = T(0);
+  const int ncx = tx.cnt, ncy = ty.cnt, ncz = tz.cnt;
+  for (int a = 0; a < ncz; ++a) {
+    const T wa = tz.w[a];
+    const int64_t za = (int64_t)ny * tz.t[a];
+    for (int b = 0; b < ncy; ++b) {
+      const T wab = wa * ty.w[b];
+      const int64_t base = (int64_t)nx * (ty.t[b] + za);
+      for (int c = 0; c < ncx; ++c) {
+        const T wt = wab * tx.w[c];
+        const Vec<T, VEC> v = ldv<T, VEC>(Rf + (base + tx.t[c]) * k + col0);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = fma(wt, v.v[q], acc[q]);
+      }
+    }
+  }
+}
+
+// Device tables of a Laplacian stencil (both precisions) and of the transfers between a
+// grid and its 2:1 coarsening, built from the grid's device node coordinates.
+rb_status stencil7_tables(const rb_grid_desc* g, double* w64[3], double* ic64[3], float* w32[3], float* ic32[3],
+                          cudaStream_t s);
+rb_status transfer_tables(const rb_grid_desc* fine, PAxis<double>* pa64[3], TAxisTab<double>* ta64[3],
+                          PAxis<float>* pa32[3], TAxisTab<float>* ta32[3], cudaStream_t s);
+
+}  // namespace rb

@@ -148,8 +148,8 @@ def test_multigrid_validation_without_gpu(lib):
         g.periodic[d] = 1
         g.nodes[d] = C.addressof(nodes)
     h = C.c_void_p()
-    for k_max, prm, msg in ((0, None, b"k_max"), (65, None, b"k_max"), (3, rb.MgParams(0, 0.5, 4, 1), b"nu"),
-                            (3, rb.MgParams(2, 1.5, 4, 1), b"omega"), (3, rb.MgParams(2, 0.5, 1, 1), b"min_cells")):
+    for k_max, prm, msg in ((0, None, b"k_max"), (65, None, b"k_max"), (3, rb.MgParams(0, 0.5, 4, 1, 1), b"nu"),
+                            (3, rb.MgParams(2, 1.5, 4, 1, 1), b"omega"), (3, rb.MgParams(2, 0.5, 1, 1, 1), b"min_cells")):
         st = lib.rb_mg_create(C.byref(g), k_max, None if prm is None else C.byref(prm), None, C.byref(h))
         assert st == rb.RB_EINVAL and msg in lib.rb_last_error(), (k_max, lib.rb_last_error())
         assert not h.value
@@ -159,3 +159,17 @@ def test_multigrid_validation_without_gpu(lib):
     rep = rb.CgReport()
     assert lib.rb_mg_solve(None, C.byref(rb.mg_params()), None, 1, None, 1, 1, C.byref(rep), None) == rb.RB_EINVAL
     assert lib.rb_mg_vcycle(None, 0, 0, None, 1, None, 1, 1, None) == rb.RB_EINVAL
+
+
+def test_galerkin_validation_without_gpu(lib):
+    """rb_galerkin_guess refuses bad sizes and null arguments before any device work."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+
+    assert lib.rb_galerkin_workspace_bytes(100, 3, 3) > 0
+    assert lib.rb_galerkin_workspace_bytes(100, 3, 4) == 0 and lib.rb_galerkin_workspace_bytes(100, 65, 1) == 0
+    ptrs = (C.c_void_p * 1)(None)
+    lds = (C.c_int64 * 1)(3)
+    assert lib.rb_galerkin_guess(None, 3, 1, ptrs, lds, None, 3, None, 3, None, None, 0, None) == rb.RB_EINVAL
+    assert b"null operator" in lib.rb_last_error()

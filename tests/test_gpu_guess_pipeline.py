@@ -1,5 +1,6 @@
 """The learned-guess pipeline end to end on a small Rayleigh-Benard-shaped grid: solver-made
-training pairs, training with the library's kernels, and CG from the judged guess.
+training pairs, training with the library's kernels, and CG (Jacobi and multigrid) from the
+judged guess and from the Galerkin combination of the candidates.
 
 The trained network's predictions are a heuristic (parity unpinned); what is checked is that
 every solve reaches the same 1e-10 true residual from any guess, that training lowers the
@@ -34,4 +35,8 @@ def test_pipeline_small_rbc(rb):
     assert gs["median_rel_res_selected"] <= gs["median_rel_res_prev_smoothed"], gs
     # and CG from it reaches the same 1e-10 (asserted inside evaluate) in about as many
     # iterations: at this tolerance the iteration count barely depends on the guess
-    assert ev["learned_ir"]["median_iters"] <= 1.05 * ev["prev_ir"]["median_iters"], ev
+    assert ev["learned_judged_ir"]["median_iters"] <= 1.05 * ev["prev_ir"]["median_iters"], ev
+    # the Galerkin combination of p_{t-1}, p_{t-2} and the network's guess is closer than the
+    # previous pressure, and the multigrid solve from it takes no more iterations
+    assert gs["median_rel_err_galerkin_learned"] < gs["median_rel_err_prev"], gs
+    assert ev["galerkin_learned_mg"]["median_iters"] <= ev["prev_mg"]["median_iters"], ev
