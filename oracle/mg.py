@@ -14,7 +14,12 @@ hierarchy here is geometric, built from the same pieces as the rest of the metho
     restriction of residuals (residuals of the volume-integrated equations are integrals, so
     P^T, not the cell average, carries them), which keeps the cycle symmetric;
   * smoothing: damped Jacobi, nu1 sweeps before and nu2 = nu1 after the coarse correction with
-    the same weight, the coarsest level solved by CG to a tight tolerance;
+    the same weight, the coarsest level solved by CG to a tight tolerance; on grids stretched
+    along one axis (a wall-refined channel) the point smoother leaves error that is smooth
+    along that axis but rough across it, which no coarse grid of the full coarsening sees, so
+    the line variant relaxes whole grid lines along the strongly coupled axis at once (block
+    Jacobi with exact tridiagonal blocks: the classical remedy for anisotropy, e.g. Trottenberg,
+    Oosterlee and Schueller, Multigrid, Sec. 5.1);
   * the preconditioner z = B r is one V-cycle from a zero guess; the outer iteration is
     Saad's preconditioned CG (Algorithm 9.1) with the zero-mean projection of singular
     (periodic or all-Neumann) problems.
@@ -42,20 +47,66 @@ class Level:
     A: sp.csr_matrix       # -L on this level
     dinv: np.ndarray       # 1 / diag(A)
     P: sp.csr_matrix | None  # prolongation from the next coarser level (None on the coarsest)
+    T: object = None       # line smoothing: a factorisation of the line-block part of A (None: point Jacobi)
 
 
-def hierarchy(grid, min_cells: int = 4) -> list:
-    """Levels from fine to coarse."""
+def line_axis(grid, ratio: float = 4.0):
+    """The wall-bounded axis along which the couplings of the Laplacian are strongest, if they
+    exceed the others' by `ratio` somewhere: a coupling across a face along axis d scales as
+    (transverse area) / (centre distance) ~ 1 / w_d^2 relative to the cell volume, so the
+    axis with the smallest cell width against the largest of the other axes' widths.  Only
+    walled axes qualify (their lines are plain tridiagonal blocks; grids are refined towards
+    walls).  None when the grid is isotropic enough for point smoothing."""
+    mins = [float(np.diff(a.nodes).min()) for a in grid.axes]
+    best, worst = None, 1.0
+    for d in range(3):
+        if grid.axes[d].periodic:
+            continue
+        other = max(float(np.diff(grid.axes[e].nodes).max()) for e in range(3) if e != d)
+        r = (other / mins[d]) ** 2
+        if r > worst:
+            best, worst = d, r
+    return best if worst >= ratio else None
+
+
+def line_block(grid, A: sp.csr_matrix, axis: int) -> sp.csr_matrix:
+    """The part of A coupling cells along `axis` only (the diagonal and the two neighbours along
+    the axis, wrapped on a periodic axis): block diagonal with one tridiagonal (periodic:
+    cyclic) block per grid line."""
+    n = [a.n for a in grid.axes]
+    stride = [1, n[0], n[0] * n[1]][axis]
+    A = A.tocoo()
+    idx = np.arange(A.shape[0])
+    pos = (idx // stride) % n[axis]
+    # same line: the two cells differ only in their position along the axis
+    same = (A.row - pos[A.row] * stride) == (A.col - pos[A.col] * stride)
+    return sp.csr_matrix((A.data[same], (A.row[same], A.col[same])), shape=A.shape)
+
+
+def hierarchy(grid, min_cells: int = 4, smoother: str = "jacobi") -> list:
+    """Levels from fine to coarse.  smoother: "jacobi" (point) or "line" (block Jacobi over the
+    grid lines of the strongest-coupling axis of the finest grid, when it has one; the coarse
+    grids keep the fine grid's aspect ratios, so every level uses the same axis)."""
+    import scipy.sparse.linalg as sla
+
     levels = []
     g = grid
+    axis = line_axis(grid) if smoother == "line" else None
     while True:
         A = (-fvm.laplacian(g)).tocsr()
         can_coarsen = all(a.n % 2 == 0 and a.n // 2 >= min_cells for a in g.axes)
         P = refine.prolongation(g) if can_coarsen else None
-        levels.append(Level(A, 1.0 / A.diagonal(), P))
+        T = sla.splu(line_block(g, A, axis).tocsc()) if axis is not None else None
+        levels.append(Level(A, 1.0 / A.diagonal(), P, T))
         if not can_coarsen:
             return levels
         g = refine.coarse_grid(g)
+
+
+def _smooth(lv: Level, e: np.ndarray, r: np.ndarray, omega: float) -> np.ndarray:
+    """One damped sweep: e + omega B^{-1} (r - A e), B = diag(A) or the line blocks of A."""
+    s = r - lv.A @ e
+    return e + omega * (lv.T.solve(s) if lv.T is not None else lv.dinv * s)
 
 
 def _project(x, on):
@@ -71,11 +122,11 @@ def vcycle(levels, r: np.ndarray, level: int = 0, nu: int = 2, omega: float = 2.
         return e
     e = np.zeros_like(r)
     for _ in range(nu):
-        e = e + omega * lv.dinv * (r - lv.A @ e)
+        e = _smooth(lv, e, r, omega)
     rc = lv.P.T @ (r - lv.A @ e)
     e = e + lv.P @ vcycle(levels, _project(rc, project_mean), level + 1, nu, omega, project_mean)
     for _ in range(nu):
-        e = e + omega * lv.dinv * (r - lv.A @ e)
+        e = _smooth(lv, e, r, omega)
     return _project(e, project_mean)
 
 

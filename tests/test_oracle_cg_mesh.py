@@ -252,3 +252,38 @@ def test_airfoil_mesh_shape():
     assert not inside.any()
     m2 = W.airfoil_mesh(n_points=4000, seed=1)
     assert np.array_equal(m.triangles, m2.triangles)
+
+
+def _reliable_problem(k, seed):
+    g = W.channel_grid(24, 16, 12)
+    A = (-fvm.laplacian(g)).tocsr()
+    B = W.zero_mean(W.normal((g.n_cells, k), seed))
+    return A, B
+
+
+def test_reliable_updates_keep_krylov_progress():
+    """The reason for keeping the search direction across sweeps: with a loose inner target
+    (many sweeps) the reliable-update refinement needs about as many inner iterations as plain
+    FP64 PCG, while restarting each sweep from scratch needs far more.  A wrong rescaling of
+    the kept direction (the s_prev / s factors) or a dropped direction loses this."""
+    A, B = _reliable_problem(1, 81)
+    b = B[:, 0]
+    _, info64 = cg.pcg(A, b, rtol=1e-10, project_mean=True)
+    for inner in (0.3, 0.1):
+        x, info, sweeps = cg.ir_reliable_pcg(A, b, rtol=1e-10, inner_rtol=inner, project_mean=True)
+        _, info_r, sweeps_r = cg.ir_pcg(A, b, rtol=1e-10, inner_rtol=inner, project_mean=True)
+        assert info.status == cg.OK and sweeps >= 8
+        assert info.iters <= 1.15 * info64.iters, (inner, info.iters, info64.iters)
+        assert info_r.iters >= 1.5 * info.iters, (inner, info_r.iters, info.iters)
+
+
+def test_reliable_block_symmetry_and_degenerate_columns():
+    """Equal columns give equal results (the lockstep treats them alike); a zero column is done
+    at once with x = 0; every other column reaches the tolerance."""
+    A, B = _reliable_problem(3, 82)
+    B[:, 1] = B[:, 0]
+    B[:, 2] = 0.0
+    X, infos, _ = cg.ir_reliable_pcg_block(A, B, rtol=1e-10, inner_rtol=5e-2, project_mean=True)
+    assert np.array_equal(X[:, 0], X[:, 1]) and infos[0].iters == infos[1].iters
+    assert np.all(X[:, 2] == 0.0) and infos[2].iters == 0
+    assert infos[0].status == cg.OK and infos[0].rel_res <= 1e-10

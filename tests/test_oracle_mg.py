@@ -116,3 +116,48 @@ def test_flexible_beta_survives_a_perturbed_preconditioner():
     r = b - lv[0].A @ x
     assert np.linalg.norm(r - r.mean()) <= 1e-10 * np.linalg.norm(b)
     assert it <= it_ref + 3, (it, it_ref)
+
+
+def test_line_axis_and_blocks():
+    """The stretched wall-normal axis of a channel is found, an isotropic box has none; the
+    line block holds exactly the diagonal and the along-axis couplings of A."""
+    g = W.channel_grid(16, 16, 8)
+    assert mg.line_axis(g) == 1
+    assert mg.line_axis(W.unit_periodic_grid(8)) is None
+    # a thin periodic axis does not qualify (its lines would be cyclic)
+    assert mg.line_axis(W.Grid((W.uniform_axis(32, 0.1), W.uniform_axis(8), W.uniform_axis(8)))) is None
+    A = (-mg.fvm.laplacian(g)).tocsr()
+    T = mg.line_block(g, A, 1)
+    D = A - T
+    assert np.allclose(T.diagonal(), A.diagonal())
+    nx = 16
+    r, c = D.nonzero()
+    assert np.all(np.abs(r - c) != nx)  # no y coupling left outside the blocks ...
+    r, c = T.nonzero()
+    assert np.all((r == c) | (np.abs(r - c) == nx))  # ... and nothing else inside them
+    assert abs(T - T.T).max() == 0.0
+
+
+def test_line_vcycle_is_symmetric_positive():
+    g = W.Grid((W.uniform_axis(8, 1.0), W.tanh_axis(8, 2.0, 0.0, 1.0), W.uniform_axis(8, 1.5)))
+    lv = mg.hierarchy(g, smoother="line")
+    assert lv[0].T is not None
+    n = g.n_cells
+    Pi = np.eye(n) - 1.0 / n
+    B = np.column_stack([mg.vcycle(lv, Pi[:, i]) for i in range(n)])
+    assert np.abs(B - B.T).max() <= 1e-9 * np.abs(B).max()
+    w = np.linalg.eigvalsh(0.5 * (B + B.T))
+    assert w.min() >= -1e-9 * w.max() and np.sum(w > 1e-9 * w.max()) == n - 1
+
+
+def test_line_smoothing_on_the_stretched_channel():
+    """The walled tanh channel: line smoothing along y needs at most half the iterations of
+    point smoothing, and reaches the same solution."""
+    g = W.channel_grid(32, 32, 16)
+    b = W.zero_mean(W.normal((g.n_cells, 1), 47))[:, 0]
+    lp = mg.hierarchy(g)
+    ll = mg.hierarchy(g, smoother="line")
+    xp, itp = mg.mg_pcg(lp, b)
+    xl, itl = mg.mg_pcg(ll, b)
+    assert itl * 2 <= itp, (itl, itp)
+    assert np.linalg.norm(xl - xp) <= 1e-8 * np.linalg.norm(xp)
