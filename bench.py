@@ -268,6 +268,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.quick:
         out["e2e"] = e2e(args, torch, step_items, stream, dev, flops_step)
         out["ksweep"] = k_sweep(torch, rb, ops, dev, hbm)
+        out["ksweep_stencil"] = k_sweep_stencil(torch, rb, g, dev, hbm)
         out["poisson"] = poisson(torch, rb, ops, g, dev)
         out["multigrid"] = multigrid(torch, rb, g, dev, out["poisson"])
         out["operator_build"] = operator_build(torch, rb, g, dev)
@@ -807,6 +808,30 @@ def k_sweep(torch, rb, ops, dev, hbm):
     return res
 
 
+def k_sweep_stencil(torch, rb, g, dev, hbm):
+    """The channel Laplacian as a matrix-free operator (rb_fvm_stencil_create: entries formed
+    from per-axis tables), k = 1 .. 32, FP64 and FP32 (events, median of 10 after tuning):
+    algorithmic bytes are X read once and Y written, s k (n_r + n_c), the tables (a few KB)
+    aside; beside each, the CSR kernel's time at the same k from `ksweep`."""
+    nodes, per = rb.grid_nodes(g, dev)
+    res = []
+    for dt in ("f32", "f64"):
+        op = rb.Operator.stencil(nodes, per, dtype=dt, k_max=32)
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        s_b = 8 if dt == "f64" else 4
+        for k in W.ks_sweep():
+            X = torch.randn((op.n_cols, k), dtype=tdt, device=dev)
+            Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
+            op.tune(X, Y)
+            ms = time_events(torch, lambda: op.spmm(X, Y), 10)
+            by = s_b * k * (op.n_rows + op.n_cols)
+            res.append({"dtype": dt, "format": "stencil", "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6,
+                        "gbs": by / ms / 1e6, "frac_hbm": by / ms / 1e6 / hbm, "schedule": op.schedule(X, Y)})
+            del X, Y
+        op.close()
+    return res
+
+
 def time_events(torch, fn, reps):
     s = torch.cuda.current_stream()
     ts = []
@@ -1140,6 +1165,9 @@ def headline(out, detail_path):
     ks = out.get("ksweep")
     if ks:
         s["ksweep_frac_hbm_csr"] = {f"{r['dtype']}-k{r['k']}": round(r["frac_hbm"], 3) for r in ks if r["format"] == "csr"}
+    kst = out.get("ksweep_stencil")
+    if kst:
+        s["ksweep_stencil_gflops"] = {f"{r['dtype']}-k{r['k']}": r["gflops"] for r in kst}
     h["summary"] = _round(s)
     h["detail"] = os.path.relpath(detail_path, ROOT) if os.path.isabs(detail_path) else detail_path
     return h
@@ -1203,6 +1231,20 @@ def profile_run(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile": args.profile, "ok": True, "iters": r.iters, "res": r.true_rel_res}))
+        return
+    if args.profile == "stencil":
+        # the matrix-free channel Laplacian (rb_fvm_stencil_create), FP32, k = 1 then k = 3,
+        # three SpMMs each on seeded blocks
+        g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+        nodes, per = rb.grid_nodes(g, dev)
+        op = rb.Operator.stencil(nodes, per, dtype="f32", k_max=3)
+        for k in (1, 3):
+            X = torch.as_tensor(W.normal((g.n_cells, k), 2006).astype(np.float32), device=dev)
+            Y = torch.empty_like(X)
+            for _ in range(3):
+                op.spmm(X, Y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "ok": True}))
         return
     if args.profile == "assembly":
         # the device builds of the 27p Laplacian (96^3 periodic), and of P, R and P^T on the channel
@@ -1294,7 +1336,7 @@ def main():
                     help="NVTX ranges around the timed region ('timed_step') and each SpMM (its label), for ncu filters")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel, if captured for this build")
-    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess", "spmm", "mg", "assembly", "projection"],
+    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess", "spmm", "mg", "assembly", "projection", "stencil"],
                     help="short run for an ncu capture: 'step' = the timed step only, 'cg' = a 20-iteration "
                          "FP64 and FP32-refinement Poisson solve (k = 1 and 3), 'guess' = one forward and one "
                          "training pass of the learned-guess network at 128^3 (NVTX 'predict', 'loss_grad'), "
@@ -1302,7 +1344,8 @@ def main():
                          "on the schedule --profile-sched (vec,lpr,stage,grid_cap; default: the untuned one), "
                          "'mg' = one multigrid solve on the channel (k = 3, NVTX 'mg_solve'), 'assembly' = the 13p / "
                          "27p builds at 96^3 and P, R, P^T on the channel, 'projection' = two projection steps of "
-                         "two states at 128^3 (NVTX 'projection_step' around the second)")
+                         "two states at 128^3 (NVTX 'projection_step' around the second), 'stencil' = the "
+                         "matrix-free channel Laplacian in FP32, three SpMMs with k = 1 then k = 3")
     ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
                     help="file receiving the full result (every section); stdout ends with the headline line only")
     ap.add_argument("--profile-k", type=int, default=32)

@@ -423,6 +423,11 @@ typedef struct {
   int32_t matrix_free; /* 1: the FP32 cycle and the FP32 CG apply -L and the transfers from
                           per-axis tables (rb_fvm_stencil_create; no matrix bytes); 0: the CSR
                           operators (1) */
+  int32_t smoother;    /* 0: point Jacobi; 1: line Jacobi along the wall-bounded axis whose
+                          couplings exceed the others' by a factor >= 4 somewhere (a grid refined
+                          towards its walls: point smoothing stalls there), each grid line along
+                          it relaxed at once by a tridiagonal solve; point Jacobi when there is
+                          no such axis (1) */
 } rb_mg_params;
 
 #define RB_MG_MAX_LEVELS 16
@@ -432,6 +437,7 @@ typedef struct {
   int64_t nnz_A[RB_MG_MAX_LEVELS]; /* nonzeros of -L on the level */
   int64_t nnz_P[RB_MG_MAX_LEVELS]; /* nonzeros of P from the next level (0 on the coarsest) */
   int64_t device_bytes;            /* device memory the hierarchy holds */
+  int32_t line_axis;               /* the line smoother's axis, -1 for point Jacobi */
 } rb_mg_info_t;
 
 /* Builds the hierarchy of `grid` (as for rb_fvm_assemble; nodes are DEVICE float64) for up to

@@ -73,7 +73,7 @@ class SpmmSchedule(C.Structure):
 
 class MgParams(C.Structure):
     _fields_ = [("nu", C.c_int32), ("omega", C.c_double), ("min_cells", C.c_int32), ("flexible", C.c_int32),
-                ("matrix_free", C.c_int32)]
+                ("matrix_free", C.c_int32), ("smoother", C.c_int32)]
 
 
 RB_MG_MAX_LEVELS = 16
@@ -82,7 +82,7 @@ RB_MG_MAX_LEVELS = 16
 class MgInfo(C.Structure):
     _fields_ = [("levels", C.c_int32), ("n", (C.c_int32 * 3) * RB_MG_MAX_LEVELS),
                 ("nnz_A", C.c_int64 * RB_MG_MAX_LEVELS), ("nnz_P", C.c_int64 * RB_MG_MAX_LEVELS),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("line_axis", C.c_int32)]
 
 
 class GuessCfg(C.Structure):
@@ -602,17 +602,19 @@ class Multigrid:
     preconditioner and the multigrid-preconditioned CG solve of the pressure equation."""
 
     def __init__(self, nodes, periodic, k_max=1, nu=2, omega=2.0 / 3.0, min_cells=4, flexible=True, matrix_free=True,
-                 stream=None):
+                 smoother="line", stream=None):
         torch = _torch()
         self._nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
         g = _grid_desc(self._nodes, periodic)
-        prm = MgParams(int(nu), float(omega), int(min_cells), 1 if flexible else 0, 1 if matrix_free else 0)
+        prm = MgParams(int(nu), float(omega), int(min_cells), 1 if flexible else 0, 1 if matrix_free else 0,
+                       {"jacobi": 0, "line": 1}[smoother])
         h = C.c_void_p()
         _check(lib().rb_mg_create(C.byref(g), int(k_max), C.byref(prm), _stream(stream), C.byref(h)), "rb_mg_create")
         self.handle = h
         self.k_max = int(k_max)
         inf = self.info()
         self.levels = inf.levels
+        self.line_axis = inf.line_axis
         self.shapes = [tuple(inf.n[l][d] for d in range(3)) for l in range(inf.levels)]
         self.n = self.shapes[0][0] * self.shapes[0][1] * self.shapes[0][2]
 

@@ -272,6 +272,231 @@ __global__ void __launch_bounds__(kThreads) k_mg_restrict_st(Transfer3<T> tr, in
   }
 }
 
+// ------------------------------------------------------------------- line smoothing
+// Block Jacobi over the grid lines along one wall-bounded axis (the strongly coupled one of a
+// wall-refined grid): the block of a line is the tridiagonal part of A along it (A's diagonal
+// and its two couplings along the axis).  Thomas' algorithm: with l_j, u_j the couplings to
+// positions j - 1 and j + 1 and b_j the diagonal, den_0 = b_0, den_j = b_j - l_j c_{j-1},
+// c_j = u_j / den_j (the factors, fixed with the operator, computed once per level), then per
+// right-hand side s: d_j = (s_j - l_j d_{j-1}) / den_j forward and x_j = d_j - c_j x_{j+1}
+// backward.
+
+struct LineGeom {
+  int axis, len, stride;  // the axis, its cell count, the row stride along it
+  int nlines;             // lines (rows / len)
+  FastDiv div_inner;      // lines are numbered (inner, outer): inner < stride
+  int inner;              // = stride (rows before the line axis in the numbering)
+};
+
+// first row of line t: inner part below the axis, outer part above it
+__device__ __forceinline__ int64_t line_base(const LineGeom& lg, int t) {
+  if (lg.stride == 1) return (int64_t)t * lg.len;
+  const uint32_t o = lg.div_inner.div((uint32_t)t);
+  const uint32_t i = (uint32_t)t - o * (uint32_t)lg.inner;
+  return (int64_t)o * lg.len * lg.inner + i;
+}
+
+template <typename T>
+__device__ __forceinline__ void along(const Coef7<T>& c, int axis, T& lo, T& up) {
+  lo = axis == 0 ? c.cxm : (axis == 1 ? c.cym : c.czm);
+  up = axis == 0 ? c.cxp : (axis == 1 ? c.cyp : c.czp);
+}
+
+// the factors c_j and 1 / den_j of every line, from the FP64 tables, in both precisions
+__global__ void k_line_factors(Stencil7<double> st, LineGeom lg, double* __restrict__ c64,
+                               double* __restrict__ id64, double* __restrict__ a64, float* __restrict__ c32,
+                               float* __restrict__ id32, float* __restrict__ a32) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < lg.nlines; t += gridDim.x * blockDim.x) {
+    const int64_t b0 = line_base(lg, t);
+    double cprev = 0.0;
+    for (int j = 0; j < lg.len; ++j) {
+      const int64_t row = b0 + (int64_t)j * lg.stride;
+      const Coef7<double> cf = stencil7_coef(st, row);
+      double lo, up;
+      along(cf, lg.axis, lo, up);
+      lo *= st.scale, up *= st.scale;
+      const double den = st.scale * cf.diag - lo * cprev;
+      const double c = up / den;
+      c64[row] = c, id64[row] = 1.0 / den, a64[row] = -lo / den;
+      c32[row] = (float)c, id32[row] = (float)(1.0 / den), a32[row] = (float)(-lo / den);
+      cprev = c;
+    }
+  }
+}
+
+enum LineMode : int { LN_ZERO = 0, LN_JACOBI = 1 };
+
+constexpr int kSeg = kThreads / 32;  // segments per line: one warp each
+
+// out = e + omega T^-1 (r - A e) over each line (LN_ZERO: e = 0, out = omega T^-1 r); with DOTS
+// the last sweep of the outer cycle, also r . out and q . out per column.
+//
+// Partition method: Thomas' two recurrences are first order, d_j = a_j d_{j-1} + b_j with
+// a_j = -l_j / den_j, b_j = s_j / den_j, and x_j = d_j - c_j x_{j+1}; a segment of a line
+// composes its cells' maps into one affine map, the segments' maps are joined in shared
+// memory, and each segment then finishes its cells from its entry value.  A block holds
+// 32 / KP lines (the lanes of a warp: KP column chunks of each line in adjacent lanes, lines
+// next to each other, so that loads along the other axes are coalesced) and kSeg segments (the
+// warps).  Passes: (1) residual, b_j kept in `out`, forward composition; (2) d_j into `out`,
+// with the backward composition accumulated forward (x_j0 = sum_j P_j d_j + P x_j1, P the
+// running product of -c); (3) backward substitution and the damped update.
+template <typename T, int VEC, int MODE, bool DOTS>
+__global__ void __launch_bounds__(kThreads) k_mg_line(Stencil7<T> st, LineGeom lg, int k, int kp,
+                                                       const T* __restrict__ e, const T* __restrict__ r,
+                                                       const T* __restrict__ cfac, const T* __restrict__ idn,
+                                                       const T* __restrict__ aco, T omega, T* __restrict__ out,
+                                                       MgDots dd, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  __shared__ RedSmem<2> red;
+  __shared__ T sA[kSeg][32][VEC], sB[kSeg][32][VEC];
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int chunk = lane % kp, ll = lane / kp, LW = 32 / kp;
+  const bool col_ok = chunk * VEC < k;
+  const int j0 = (seg * lg.len) / kSeg, j1 = ((seg + 1) * lg.len) / kSeg;
+  T d0[VEC], d1[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) d0[q] = d1[q] = T(0);
+  const T* qv_base = static_cast<const T*>(dd.q);
+  for (int line0 = blockIdx.x * LW; line0 < lg.nlines; line0 += gridDim.x * LW) {  // uniform over the block
+    const int t = line0 + ll;
+    const bool on = col_ok && t < lg.nlines;
+    const int64_t b0 = on ? line_base(lg, t) : 0;
+    // pass 1: b_j = s_j / den_j into out; forward map of the segment: d_out = A d_in + B
+    T A[VEC], B[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) A[q] = T(1), B[q] = T(0);
+    if (on) {
+      for (int j = j0; j < j1; ++j) {
+        const int64_t row = b0 + (int64_t)j * lg.stride;
+        const int64_t o = row * k + chunk * VEC;
+        const Vec<T, VEC> rv = ldv<T, VEC>(r + o);
+        T sv[VEC];
+        if constexpr (MODE == LN_ZERO) {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) sv[q] = rv.v[q];
+        } else {
+          T ae[VEC], unused;
+          stencil7_apply<T, VEC>(st, e, k, row, chunk * VEC, ae, unused);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) sv[q] = rv.v[q] - ae[q];
+        }
+        const T id = __ldg(idn + row), a = __ldg(aco + row);
+        Vec<T, VEC> bv;
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          bv.v[q] = sv[q] * id;
+          A[q] = a * A[q];
+          B[q] = fma(a, B[q], bv.v[q]);
+        }
+        stv<T, VEC>(out + o, bv);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) sA[seg][lane][q] = A[q], sB[seg][lane][q] = B[q];
+    __syncthreads();
+    T din[VEC];  // d just before the segment: the earlier segments' maps applied to d = 0
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) din[q] = T(0);
+    for (int s2 = 0; s2 < seg; ++s2)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) din[q] = fma(sA[s2][lane][q], din[q], sB[s2][lane][q]);
+    __syncthreads();  // sA / sB are reused below
+    // pass 2: d_j into out; backward map of the segment accumulated forward: x_j0 = S + P x_j1
+    T P[VEC], S[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) P[q] = T(1), S[q] = T(0);
+    if (on) {
+      for (int j = j0; j < j1; ++j) {
+        const int64_t row = b0 + (int64_t)j * lg.stride;
+        const int64_t o = row * k + chunk * VEC;
+        const T a = __ldg(aco + row), c = __ldg(cfac + row);
+        Vec<T, VEC> dv = ldv_rw<T, VEC>(out + o);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          din[q] = fma(a, din[q], dv.v[q]);
+          dv.v[q] = din[q];
+          S[q] = fma(P[q], din[q], S[q]);
+          P[q] = -c * P[q];
+        }
+        stv<T, VEC>(out + o, dv);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) sA[seg][lane][q] = P[q], sB[seg][lane][q] = S[q];
+    __syncthreads();
+    T xin[VEC];  // x just after the segment: the later segments' maps from x_len = 0
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) xin[q] = T(0);
+    for (int s2 = kSeg - 1; s2 > seg; --s2)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) xin[q] = fma(sA[s2][lane][q], xin[q], sB[s2][lane][q]);
+    __syncthreads();
+    // pass 3: backward substitution, damped update (and the dot products)
+    if (on) {
+      for (int j = j1 - 1; j >= j0; --j) {
+        const int64_t row = b0 + (int64_t)j * lg.stride;
+        const int64_t o = row * k + chunk * VEC;
+        const T c = __ldg(cfac + row);
+        const Vec<T, VEC> dv = ldv_rw<T, VEC>(out + o);
+        Vec<T, VEC> y;
+        if constexpr (MODE == LN_ZERO) {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) {
+            xin[q] = dv.v[q] - c * xin[q];
+            y.v[q] = omega * xin[q];
+          }
+        } else {
+          const Vec<T, VEC> ev = ldv<T, VEC>(e + o);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) {
+            xin[q] = dv.v[q] - c * xin[q];
+            y.v[q] = fma(omega, xin[q], ev.v[q]);
+          }
+        }
+        if constexpr (DOTS) {
+          const Vec<T, VEC> rv = ldv<T, VEC>(r + o);
+          if (dd.init) {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) d0[q] = fma(rv.v[q], y.v[q], d0[q]);
+          } else {
+            const Vec<T, VEC> qv = ldv<T, VEC>(qv_base + o);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+              d0[q] = fma(rv.v[q], y.v[q], d0[q]);
+              d1[q] = fma(qv.v[q], y.v[q], d1[q]);
+            }
+          }
+        }
+        stv<T, VEC>(out + o, y);
+      }
+    }
+  }
+  if constexpr (DOTS) {
+    T part[2][VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) part[0][q] = d0[q], part[1][q] = d1[q];
+    const double v = block_reduce<2, VEC>(part, kp, 1, k, red);
+    MgScal* sc = dd.sc;
+    if (!publish_partials<2>(v, 2 * k, dd.partials, &sc->counter[2], red)) return;
+    const double tot = final_sum<2>(dd.partials, 2 * k, gridDim.x, red);
+    __shared__ double s_tot[2 * K];
+    if ((int)threadIdx.x < 2 * k) s_tot[threadIdx.x] = tot;
+    __syncthreads();
+    const int jj = threadIdx.x;
+    if (jj < k) {
+      const double rz_new = s_tot[jj], qz = s_tot[k + jj];
+      double beta = 0.0;
+      if (!dd.init && sc->state[jj] == MG_ACTIVE) {
+        const double rz_old = sc->rz[jj];
+        beta = dd.flexible ? -sc->alpha[jj] * qz / rz_old : rz_new / rz_old;
+        if (!isfinite(beta)) beta = 0.0;
+      }
+      sc->beta[jj] = beta;
+      sc->rz[jj] = rz_new;
+    }
+  }
+}
+
 // z = Ainv r on the coarsest level (Ainv dense FP64, nc x nc): one block per row, lanes over
 // (m, column), the m lanes folded through shared memory in a fixed order
 template <typename T>
@@ -701,6 +926,10 @@ struct rb_mg_level {
   rb_op* P[2] = {nullptr, nullptr};   // prolongation from the next level (this level's rows)
   rb_op* PT[2] = {nullptr, nullptr};  // its transpose (the next level's rows)
   rb_op* S32 = nullptr;               // -L matrix-free in FP32 (the FP32 cycle's operator)
+  rb_op* S64 = nullptr;               // -L matrix-free in FP64 (line smoothing of the FP64 cycle)
+  void* line_mem = nullptr;           // line smoothing: c_j and 1 / den_j per cell, FP64 then FP32
+  double *lc64 = nullptr, *lid64 = nullptr, *la64 = nullptr;
+  float *lc32 = nullptr, *lid32 = nullptr, *la32 = nullptr;
   // matrix-free transfers to the next level: per-axis 1-D maps (FP32)
   rb::PAxis<float>* pa32[3] = {nullptr, nullptr, nullptr};
   rb::TAxisTab<float>* ta32[3] = {nullptr, nullptr, nullptr};
@@ -711,6 +940,7 @@ struct rb_mg_level {
 
 struct rb_mg {
   int L = 0, k_max = 1;
+  int line_axis = -1;  // axis of the line smoother, -1: point Jacobi
   rb_mg_params prm{};
   std::vector<rb_mg_level> lv;
   int nc = 0;              // coarsest cells
@@ -757,7 +987,8 @@ void mg_free(rb_mg* g) {
       if (l.PT[d]) rb_operator_destroy(l.PT[d]);
     }
     if (l.S32) rb_operator_destroy(l.S32);
-    for (void* p : {l.rhs, l.ea, l.eb, l.res, l.out, l.tab_mem})
+    if (l.S64) rb_operator_destroy(l.S64);
+    for (void* p : {l.rhs, l.ea, l.eb, l.res, l.out, l.tab_mem, l.line_mem})
       if (p) cudaFree(p);
   }
   for (void* p : {(void*)g->ainv, (void*)g->x64, (void*)g->rt, g->x, g->r, g->p, g->q, g->z, (void*)g->sc,
@@ -795,6 +1026,60 @@ struct DevCsr {
   }
 };
 
+LineGeom line_geom(const rb_mg_level& lv, int axis) {
+  LineGeom lg{};
+  lg.axis = axis;
+  lg.len = lv.n[axis];
+  lg.stride = axis == 0 ? 1 : (axis == 1 ? lv.n[0] : lv.n[0] * lv.n[1]);
+  lg.inner = lg.stride;
+  lg.nlines = (int)(lv.cells / lg.len);
+  lg.div_inner.init((uint32_t)lg.stride);
+  return lg;
+}
+
+Stencil7<double> stencil_view64(const rb_op* op) {
+  Stencil7<double> v{};
+  for (int d = 0; d < 3; ++d) {
+    v.n[d] = op->st_n[d];
+    v.per[d] = op->st_per[d];
+    v.w[d] = static_cast<const double*>(op->st_w[d]);
+    v.ic[d] = static_cast<const double*>(op->st_ic[d]);
+  }
+  v.scale = op->st_scale;
+  v.init_div();
+  return v;
+}
+
+// The line smoother's axis: the wall-bounded axis whose couplings exceed the others' most,
+// if by a factor >= 4 somewhere (coupling across a face ~ 1 / width^2 relative to the cell:
+// (largest width of the other axes / smallest width of this one)^2); -1 for none
+int choose_line_axis(const rb_grid_desc* grid) {
+  double mn[3], mx[3];
+  for (int d = 0; d < 3; ++d) {
+    std::vector<double> h(grid->n[d] + 1);
+    if (cudaMemcpy(h.data(), grid->nodes[d], sizeof(double) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    mn[d] = 1e300, mx[d] = 0.0;
+    for (int t = 0; t < grid->n[d]; ++t) {
+      const double w = h[t + 1] - h[t];
+      mn[d] = std::min(mn[d], w), mx[d] = std::max(mx[d], w);
+    }
+  }
+  int best = -1;
+  double worst = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    if (grid->periodic[d]) continue;
+    double other = 0.0;
+    for (int e = 0; e < 3; ++e)
+      if (e != d) other = std::max(other, mx[e]);
+    const double r = (other / mn[d]) * (other / mn[d]);
+    if (r > worst) best = d, worst = r;
+  }
+  return worst >= 4.0 ? best : -1;
+}
+
 rb_status build_hierarchy(rb_mg* g, const rb_grid_desc* grid, cudaStream_t s) {
   std::vector<std::vector<double*>> nodes;  // per level, per axis (level 0: the caller's)
   struct NodeGuard {
@@ -820,6 +1105,23 @@ rb_status build_hierarchy(rb_mg* g, const rb_grid_desc* grid, cudaStream_t s) {
       RB_TRY(make_ops(nr, ncol, nnz, t.rp, t.ci, t.va, g->k_max, s, lv.A));
     }
     RB_TRY(rb_fvm_stencil_create(&cur, -1.0, RB_F32, g->k_max, reinterpret_cast<rb_stream_t>(s), &lv.S32));
+    if (g->line_axis >= 0) {  // the line smoother's factors (every level but a one-cell line)
+      RB_TRY(rb_fvm_stencil_create(&cur, -1.0, RB_F64, g->k_max, reinterpret_cast<rb_stream_t>(s), &lv.S64));
+      const size_t cells = (size_t)lv.cells;
+      RB_TRY(mg_alloc(g, reinterpret_cast<char**>(&lv.line_mem), cells * 36 + 256));
+      char* q = static_cast<char*>(lv.line_mem);
+      lv.lc64 = reinterpret_cast<double*>(q);
+      lv.lid64 = lv.lc64 + cells;
+      lv.la64 = lv.lid64 + cells;
+      lv.lc32 = reinterpret_cast<float*>(lv.la64 + cells);
+      lv.lid32 = lv.lc32 + cells;
+      lv.la32 = lv.lid32 + cells;
+      const LineGeom lg = line_geom(lv, g->line_axis);
+      Stencil7<double> v = stencil_view64(lv.S64);
+      k_line_factors<<<std::max(1, std::min((lg.nlines + 127) / 128, kMaxGrid)), 128, 0, s>>>(
+          v, lg, lv.lc64, lv.lid64, lv.la64, lv.lc32, lv.lid32, lv.la32);
+      RB_CUDA(cudaGetLastError());
+    }
     bool coarsen = l + 1 < kMgMaxLevels;
     for (int d = 0; d < 3; ++d) coarsen = coarsen && cur.n[d] % 2 == 0 && cur.n[d] / 2 >= mc;
     if (coarsen) {
@@ -949,6 +1251,7 @@ struct Cycle {
         v.ic[d] = static_cast<const T*>(op->st_ic[d]);
       }
       v.scale = (T)op->st_scale;
+      v.init_div();
     }
     return v;
   }
@@ -961,6 +1264,7 @@ struct Cycle {
         t.pa[d] = lv.pa32[d];
         t.ta[d] = lv.ta32[d];
       }
+      t.init_div();
     }
     return t;
   }
@@ -980,6 +1284,22 @@ struct Cycle {
     }
   }
 
+  // one line sweep over a level (the FP32 or FP64 tables of its operator)
+  template <int MODE, bool DOTS>
+  void line(const rb_mg_level& lv, const T* e, const T* r, T* out, const MgDots& dd) const {
+    const LineGeom lg = line_geom(lv, g->line_axis);
+    const T* cf;
+    const T* id;
+    const T* ac;
+    const rb_op* op;
+    if constexpr (sizeof(T) == 4) cf = lv.lc32, id = lv.lid32, ac = lv.la32, op = lv.S32;
+    else cf = lv.lc64, id = lv.lid64, ac = lv.la64, op = lv.S64;
+    auto* kern = &k_mg_line<T, VEC, MODE, DOTS>;
+    const int lines_per_block = 32 / kp;
+    const int blocks = wave_grid(kern, (lg.nlines + lines_per_block - 1) / lines_per_block);
+    kern<<<blocks, kThreads, 0, s>>>(st_view(op), lg, k, kp, e, r, cf, id, ac, (T)g->prm.omega, out, dd, gate);
+  }
+
   // z = B r on level l (r, z: n_l x k blocks of T, ld = k); dd: dots of the last sweep
   rb_status run(int l, const T* r, T* z, const MgDots* dd) const {
     const rb_mg_level& lv = g->lv[l];
@@ -994,10 +1314,15 @@ struct Cycle {
     const T* dinv = dinv_of<T>(mf() ? lv.S32 : lv.A[ti()]);
     T* bufs[2] = {static_cast<T*>(lv.ea), static_cast<T*>(lv.eb)};
     int c = 0;
-    k_mg_smooth0<T, VEC><<<grid(&k_mg_smooth0<T, VEC>, lv.cells), kThreads, 0, s>>>(lv.cells, k, kp, r, dinv, omega,
-                                                                                     bufs[0], gate);
     MgDots none;
-    for (int it = 1; it < nu; ++it, c ^= 1) sweep<SW_JACOBI, false>(lv, bufs[c], r, dinv, bufs[c ^ 1], none);
+    if (g->line_axis >= 0) {
+      line<LN_ZERO, false>(lv, nullptr, r, bufs[0], none);
+      for (int it = 1; it < nu; ++it, c ^= 1) line<LN_JACOBI, false>(lv, bufs[c], r, bufs[c ^ 1], none);
+    } else {
+      k_mg_smooth0<T, VEC><<<grid(&k_mg_smooth0<T, VEC>, lv.cells), kThreads, 0, s>>>(lv.cells, k, kp, r, dinv, omega,
+                                                                                       bufs[0], gate);
+      for (int it = 1; it < nu; ++it, c ^= 1) sweep<SW_JACOBI, false>(lv, bufs[c], r, dinv, bufs[c ^ 1], none);
+    }
     // residual, restriction, the next level, prolongation-add
     sweep<SW_RESID, false>(lv, bufs[c], r, dinv, static_cast<T*>(lv.res), none);
     const rb_mg_level& nx = g->lv[l + 1];
@@ -1020,8 +1345,13 @@ struct Cycle {
     }
     for (int it = 1; it <= nu; ++it, c ^= 1) {
       T* dst = (it == nu) ? z : bufs[c ^ 1];
-      if (it == nu && dd) sweep<SW_JACOBI, true>(lv, bufs[c], r, dinv, dst, *dd);
-      else sweep<SW_JACOBI, false>(lv, bufs[c], r, dinv, dst, none);
+      if (g->line_axis >= 0) {
+        if (it == nu && dd) line<LN_JACOBI, true>(lv, bufs[c], r, dst, *dd);
+        else line<LN_JACOBI, false>(lv, bufs[c], r, dst, none);
+      } else {
+        if (it == nu && dd) sweep<SW_JACOBI, true>(lv, bufs[c], r, dinv, dst, *dd);
+        else sweep<SW_JACOBI, false>(lv, bufs[c], r, dinv, dst, none);
+      }
     }
     RB_CUDA(cudaGetLastError());
     return RB_OK;
@@ -1301,11 +1631,12 @@ extern "C" rb_status rb_mg_create(const rb_grid_desc* grid, int32_t k_max, const
   RB_REQUIRE(grid && out, "rb_mg_create: null argument");
   *out = nullptr;
   RB_REQUIRE(k_max >= 1 && k_max <= RB_MAX_K, "rb_mg_create: k_max %d outside [1, %d]", k_max, RB_MAX_K);
-  rb_mg_params prm{2, 2.0 / 3.0, 4, 1, 1};
+  rb_mg_params prm{2, 2.0 / 3.0, 4, 1, 1, 1};
   if (params) prm = *params;
   RB_REQUIRE(prm.nu >= 1 && prm.nu <= 16, "rb_mg_create: nu = %d outside [1, 16]", prm.nu);
   RB_REQUIRE(prm.omega > 0.0 && prm.omega <= 1.0, "rb_mg_create: omega = %g outside (0, 1]", prm.omega);
   RB_REQUIRE(prm.min_cells >= 2, "rb_mg_create: min_cells = %d (at least 2)", prm.min_cells);
+  RB_REQUIRE(prm.smoother == 0 || prm.smoother == 1, "rb_mg_create: smoother = %d (0 or 1)", prm.smoother);
   for (int d = 0; d < 3; ++d) {
     RB_REQUIRE(grid->nodes[d] != nullptr, "rb_mg_create: null nodes[%d]", d);
     RB_REQUIRE(grid->n[d] >= (grid->periodic[d] ? 3 : 2), "rb_mg_create: axis %d has %d cells", d, grid->n[d]);
@@ -1316,6 +1647,7 @@ extern "C" rb_status rb_mg_create(const rb_grid_desc* grid, int32_t k_max, const
   g->k_max = k_max;
   g->prm = prm;
   cudaStream_t s = S(stream);
+  g->line_axis = prm.smoother ? choose_line_axis(grid) : -1;
   rb_status st = build_hierarchy(g, grid, s);
   if (st == RB_OK) {
     const size_t cnt = (size_t)n0 * k_max;
@@ -1359,6 +1691,7 @@ extern "C" rb_status rb_mg_info(rb_mg_t mg, rb_mg_info_t* info) {
     info->nnz_P[l] = mg->lv[l].P[0] ? mg->lv[l].P[0]->nnz : 0;
   }
   info->device_bytes = mg->device_bytes;
+  info->line_axis = mg->line_axis;
   return RB_OK;
 }
 

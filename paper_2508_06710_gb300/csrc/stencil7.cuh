@@ -23,13 +23,40 @@
 
 namespace rb {
 
+// Unsigned 32-bit division by a divisor fixed for a whole launch, as one multiply-high, an add
+// and two shifts: Granlund and Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994), the round-up method for N = 32: with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0),
+// t = floor(m n / 2^32).  Exact for every n < 2^32 and 1 <= d < 2^31.  The rows of the grids
+// here are below 2^31, so (i, j, k) come from two of these instead of 64-bit divisions.
+struct FastDiv {
+  uint32_t m = 0;
+  int s1 = 0, s2 = 0;
+  __host__ void init(uint32_t d) {
+    int l = 0;
+    while ((uint64_t)1 << l < d) ++l;
+    m = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 1 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
 template <typename T>
 struct Stencil7 {
   int n[3];
   int per[3];
   const T* w[3];
   const T* ic[3];
-  T scale;  // the operator is scale * L
+  T scale;          // the operator is scale * L
+  FastDiv dx, dxy;  // division by n[0] and by n[0] n[1]
+  __host__ void init_div() {
+    dx.init((uint32_t)n[0]);
+    dxy.init((uint32_t)n[0] * (uint32_t)n[1]);
+  }
 };
 
 // The row's cell (i, j, k), its six face coefficients of L and the diagonal -sum of them
@@ -42,12 +69,11 @@ struct Coef7 {
 template <typename T>
 __device__ __forceinline__ Coef7<T> stencil7_coef(const Stencil7<T>& s, int64_t row) {
   Coef7<T> c;
-  const int nx = s.n[0], ny = s.n[1];
-  const int64_t plane = (int64_t)nx * ny;
-  c.k = (int)(row / plane);
-  const int64_t rem = row - (int64_t)c.k * plane;
-  c.j = (int)(rem / nx);
-  c.i = (int)(rem - (int64_t)c.j * nx);
+  const uint32_t r32 = (uint32_t)row;
+  c.k = (int)s.dxy.div(r32);
+  const uint32_t rem = r32 - (uint32_t)c.k * (uint32_t)(s.n[0] * s.n[1]);
+  c.j = (int)s.dx.div(rem);
+  c.i = (int)(rem - (uint32_t)c.j * (uint32_t)s.n[0]);
   const T wx = __ldg(s.w[0] + c.i), wy = __ldg(s.w[1] + c.j), wz = __ldg(s.w[2] + c.k);
   const T ayz = wy * wz, axz = wx * wz, axy = wx * wy;
   c.cxm = ayz * __ldg(s.ic[0] + c.i), c.cxp = ayz * __ldg(s.ic[0] + c.i + 1);
@@ -116,6 +142,13 @@ struct Transfer3 {
   int nf[3];               // fine cells per axis (coarse: nf / 2)
   const PAxis<T>* pa[3];   // per fine position
   const TAxisTab<T>* ta[3];  // per coarse position
+  FastDiv fx, fxy, cx, cxy;  // division by the fine and the coarse row lengths and planes
+  __host__ void init_div() {
+    fx.init((uint32_t)nf[0]);
+    fxy.init((uint32_t)nf[0] * (uint32_t)nf[1]);
+    cx.init((uint32_t)(nf[0] / 2));
+    cxy.init((uint32_t)(nf[0] / 2) * (uint32_t)(nf[1] / 2));
+  }
 };
 
 // (P E_c)[fine row, col0 .. col0 + VEC): trilinear interpolation from the coarse block
@@ -123,11 +156,11 @@ template <typename T, int VEC>
 __device__ __forceinline__ void prolong_apply(const Transfer3<T>& tr, const T* __restrict__ Ec, int k, int64_t row,
                                               int col0, T (&acc)[VEC]) {
   const int nx = tr.nf[0], ny = tr.nf[1];
-  const int64_t plane = (int64_t)nx * ny;
-  const int kk = (int)(row / plane);
-  const int64_t rem = row - (int64_t)kk * plane;
-  const int j = (int)(rem / nx);
-  const int i = (int)(rem - (int64_t)j * nx);
+  const uint32_t r32 = (uint32_t)row;
+  const int kk = (int)tr.fxy.div(r32);
+  const uint32_t rem = r32 - (uint32_t)kk * (uint32_t)(nx * ny);
+  const int j = (int)tr.fx.div(rem);
+  const int i = (int)(rem - (uint32_t)j * (uint32_t)nx);
   const PAxis<T> px = tr.pa[0][i], py = tr.pa[1][j], pz = tr.pa[2][kk];
   const int cnx = nx / 2, cny = ny / 2;
   const int cx[2] = {px.c0, px.c1}, cy[2] = {py.c0, py.c1}, cz[2] = {pz.c0, pz.c1};
@@ -156,29 +189,40 @@ template <typename T, int VEC>
 __device__ __forceinline__ void restrict_apply(const Transfer3<T>& tr, const T* __restrict__ Rf, int k, int64_t row,
                                                int col0, T (&acc)[VEC]) {
   const int cnx = tr.nf[0] / 2, cny = tr.nf[1] / 2;
-  const int64_t plane = (int64_t)cnx * cny;
-  const int K3 = (int)(row / plane);
-  const int64_t rem = row - (int64_t)K3 * plane;
-  const int J = (int)(rem / cnx);
-  const int I = (int)(rem - (int64_t)J * cnx);
+  const uint32_t r32 = (uint32_t)row;
+  const int K3 = (int)tr.cxy.div(r32);
+  const uint32_t rem = r32 - (uint32_t)K3 * (uint32_t)(cnx * cny);
+  const int J = (int)tr.cx.div(rem);
+  const int I = (int)(rem - (uint32_t)J * (uint32_t)cnx);
   const TAxisTab<T>& tx = tr.ta[0][I];
   const TAxisTab<T>& ty = tr.ta[1][J];
   const TAxisTab<T>& tz = tr.ta[2][K3];
   const int nx = tr.nf[0], ny = tr.nf[1];
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[q] = T(0);
+  // the x list in registers (fixed bound, guarded), y and z lists from the cached table
   const int ncx = tx.cnt, ncy = ty.cnt, ncz = tz.cnt;
+  int xt[8];
+  T xw[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    xt[c] = c < ncx ? tx.t[c] : 0;
+    xw[c] = c < ncx ? tx.w[c] : T(0);
+  }
   for (int a = 0; a < ncz; ++a) {
     const T wa = tz.w[a];
     const int64_t za = (int64_t)ny * tz.t[a];
     for (int b = 0; b < ncy; ++b) {
       const T wab = wa * ty.w[b];
-      const int64_t base = (int64_t)nx * (ty.t[b] + za);
-      for (int c = 0; c < ncx; ++c) {
-        const T wt = wab * tx.w[c];
-        const Vec<T, VEC> v = ldv<T, VEC>(Rf + (base + tx.t[c]) * k + col0);
+      const T* base = Rf + (int64_t)nx * (ty.t[b] + za) * k + col0;
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) acc[q] = fma(wt, v.v[q], acc[q]);
+      for (int c = 0; c < 8; ++c) {
+        if (c < ncx) {
+          const Vec<T, VEC> v = ldv<T, VEC>(base + (int64_t)xt[c] * k);
+          const T wt = wab * xw[c];
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[q] = fma(wt, v.v[q], acc[q]);
+        }
       }
     }
   }

@@ -54,6 +54,7 @@ Stencil7<T> view(const rb_op* op) {
     s.ic[d] = static_cast<const T*>(op->st_ic[d]);
   }
   s.scale = (T)op->st_scale;
+  s.init_div();
   return s;
 }
 
@@ -148,6 +149,7 @@ extern "C" rb_status rb_fvm_stencil_create(const rb_grid_desc* grid, double scal
     Stencil7<double> v;
     for (int d = 0; d < 3; ++d) v.n[d] = op->st_n[d], v.per[d] = op->st_per[d], v.w[d] = w64[d], v.ic[d] = ic64[d];
     v.scale = scale;
+    v.init_div();
     const int grid_blocks = (int)std::min<int64_t>(((int64_t)nr + 255) / 256, kMaxGrid);
     k_stencil7_dinv<<<grid_blocks, 256, 0, s>>>(v, nr, op->dinv64, op->dinv32);
     cudaError_t e = cudaGetLastError();

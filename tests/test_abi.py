@@ -148,8 +148,8 @@ def test_multigrid_validation_without_gpu(lib):
         g.periodic[d] = 1
         g.nodes[d] = C.addressof(nodes)
     h = C.c_void_p()
-    for k_max, prm, msg in ((0, None, b"k_max"), (65, None, b"k_max"), (3, rb.MgParams(0, 0.5, 4, 1, 1), b"nu"),
-                            (3, rb.MgParams(2, 1.5, 4, 1, 1), b"omega"), (3, rb.MgParams(2, 0.5, 1, 1, 1), b"min_cells")):
+    for k_max, prm, msg in ((0, None, b"k_max"), (65, None, b"k_max"), (3, rb.MgParams(0, 0.5, 4, 1, 1, 1), b"nu"),
+                            (3, rb.MgParams(2, 1.5, 4, 1, 1, 1), b"omega"), (3, rb.MgParams(2, 0.5, 1, 1, 1, 1), b"min_cells")):
         st = lib.rb_mg_create(C.byref(g), k_max, None if prm is None else C.byref(prm), None, C.byref(h))
         assert st == rb.RB_EINVAL and msg in lib.rb_last_error(), (k_max, lib.rb_last_error())
         assert not h.value
