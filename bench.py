@@ -137,6 +137,20 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def face_starts(g):
+    """First rows of the x-, y- and z-face blocks of the gradient of grid g (faces numbered by
+    direction; a bounded axis has n - 1 interior faces, a periodic one n)."""
+    n = [a.n for a in g.axes]
+    counts = []
+    for d in range(3):
+        c = n[d] if g.axes[d].periodic else n[d] - 1
+        for e in range(3):
+            if e != d:
+                c *= n[e]
+        counts.append(c)
+    return [0, counts[0], counts[0] + counts[1]]
+
+
 def build_ops(rb, torch, dev):
     """Operators of the channel workload, assembled on the device by the library."""
     g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
@@ -147,6 +161,8 @@ def build_ops(rb, torch, dev):
         for dt in ("f64", "f32"):
             ops[(name, dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, k_max=32), k)
             ops[(name + "-sell", dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, fmt="sell", k_max=32), k)
+            if name == "G":  # its x-, y- and z-face rows each sweep all cells: take their tiles in turn
+                ops[(name, dt)][0].set_row_blocks(face_starts(g))
         if name == "L":  # the Poisson matrix A = -L, assembled with scale -1
             rp, ci, va, nc = rb.fvm_assemble(nodes, per, kind, scale=-1.0)
             ops[("A", "f64")] = (rb.Operator(rp, ci, va, nc, dtype="f64", k_max=3), 3)
@@ -351,8 +367,8 @@ def stencils(torch, rb, dev, hbm):
                 X = torch.randn((cells, k), dtype=tdt, device=dev)
                 Y = torch.empty((cells, k), dtype=tdt, device=dev)
                 op.tune(X, Y)
-                ms = time_events(torch, lambda: op.spmm(X, Y), 10)
                 by = spmm_bytes(op.nnz, cells, cells, k, s_b)
+                ms = spmm_ms(torch, op, X, Y, by)
                 base = ms if k == 1 else base
                 res["spmm"].append({"stencil": name, "dtype": dt, "k": k, "nnz": op.nnz, "ms": ms,
                                     "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6, "frac_hbm": by / ms / 1e6 / hbm,
@@ -394,8 +410,8 @@ def refine_maps(torch, rb, dev, hbm):
                 X = torch.randn((nc, k), dtype=tdt, device=dev)
                 Y = torch.empty((nr, k), dtype=tdt, device=dev)
                 op.tune(X, Y)
-                ms = time_events(torch, lambda: op.spmm(X, Y), 10)
                 by = spmm_bytes(op.nnz, nr, nc, k, s_b)
+                ms = spmm_ms(torch, op, X, Y, by)
                 res["spmm"].append({"map": name, "dtype": dt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6,
                                     "gbs": by / ms / 1e6, "frac_hbm": by / ms / 1e6 / hbm, "schedule": op.schedule(X, Y)})
                 del X, Y
@@ -560,6 +576,22 @@ def overlapped_step(torch, args, step_items, stream, flops_step, ms_serial, worl
             "vs_single_stream": ms_serial / ms, "gpu_launches": len(step_items) * args.steps}
 
 
+L2_BYTES = 126 * 2 ** 20  # GB300's L2
+
+
+def spmm_ms(torch, op, X, Y, bytes_per_call, calls=24, reps=5):
+    """Device time of one op.spmm on blocks shaped like X, Y, measured without host launch
+    latency: a CUDA graph of `calls` SpMMs cycling over enough (X, Y) copies that the blocks of
+    consecutive calls exceed twice the L2 (so no call finds its inputs in L2 from the one
+    before), replayed `reps` times; the median replay divided by `calls`."""
+    copies = max(1, min(calls, -(-2 * L2_BYTES // max(int(bytes_per_call), 1))))
+    xs = [X] + [X.clone() for _ in range(copies - 1)]
+    ys = [Y] + [torch.empty_like(Y) for _ in range(copies - 1)]
+    ms = graph_ms(torch, lambda: [op.spmm(xs[i % copies], ys[i % copies]) for i in range(calls)], calls=1, reps=reps)
+    del xs, ys
+    return ms / calls
+
+
 def graph_ms(torch, fn, calls=20, reps=10):
     """Device time per call of `fn`, from replays of a CUDA graph of `calls` calls (launch
     latency amortised: what the kernels themselves take back to back)."""
@@ -623,8 +655,8 @@ def rbc_spmm(torch, rb, dev, hbm):
             X = torch.randn((op.n_cols, k), dtype=tdt, device=dev)
             Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
             op.tune(X, Y)
-            ms = time_events(torch, lambda: op.spmm(X, Y), 10)
             by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, 8 if dt == "f64" else 4)
+            ms = spmm_ms(torch, op, X, Y, by)
             res.append({"dtype": dt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6,
                         "frac_hbm": by / ms / 1e6 / hbm})
         op.close()
@@ -725,15 +757,15 @@ def extruded_bench(torch, rb, dev, hbm):
         X = torch.randn((n2, nz), dtype=tdt, device=dev)
         Y = torch.empty_like(X)
         op.tune(X, Y)
-        ms = time_events(torch, lambda: op.spmm(X, Y), 10)
         by = int(ci.shape[0]) * (s + 4) + 4 * (n2 + 1) + s * n2 + 2 * s * n2 * nz
+        ms = spmm_ms(torch, op, X, Y, by)
         fl = 2 * int(ci.shape[0]) * nz + 4 * n2 * nz
         op3 = rb.Operator.from_scipy(L3, dtype=dt, k_max=1)
         x1 = torch.randn((L3.shape[0], 1), dtype=tdt, device=dev)
         y1 = torch.empty_like(x1)
         op3.tune(x1, y1)
-        ms3 = time_events(torch, lambda: op3.spmm(x1, y1), 10)
         by3 = L3.nnz * (s + 4) + 4 * (L3.shape[0] + 1) + 2 * s * L3.shape[0]
+        ms3 = spmm_ms(torch, op3, x1, y1, by3)
         res["runs"].append({"dtype": dt, "spmm_k64_ms": ms, "gflops": fl / ms / 1e6, "gbs": by / ms / 1e6,
                             "frac_hbm": by / ms / 1e6 / hbm, "spmv_3d_ms": ms3, "spmv_3d_gbs": by3 / ms3 / 1e6,
                             "speedup_vs_3d_spmv": ms3 / ms, "schedule": op.schedule(X, Y)})
@@ -786,7 +818,8 @@ def e2e(args, torch, step_items, stream, dev, flops_step):
 
 
 def k_sweep(torch, rb, ops, dev, hbm):
-    """Laplacian SpMM for k = 1 .. 32 in FP64 and FP32 (events, median of 10 after tuning)."""
+    """Laplacian SpMM for k = 1 .. 32 in FP64 and FP32, CSR and SELL (tuned; spmm_ms: graph replays,
+    inputs cycled past the L2)."""
     res = []
     for dt, fmt in (("f64", "csr"), ("f32", "csr"), ("f64", "sell"), ("f32", "sell")):
         op, _ = ops[("L" if fmt == "csr" else "L-sell", dt)]
@@ -796,9 +829,9 @@ def k_sweep(torch, rb, ops, dev, hbm):
             X = torch.randn((op.n_cols, k), dtype=tdt, device=dev)
             Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
             op.tune(X, Y)
-            ms = time_events(torch, lambda: op.spmm(X, Y), 10)
             s_b = 8 if dt == "f64" else 4
             by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, s_b)
+            ms = spmm_ms(torch, op, X, Y, by)
             if k == 1:
                 base = ms
             res.append({"dtype": dt, "format": fmt, "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6, "gbs": by / ms / 1e6,
@@ -810,7 +843,8 @@ def k_sweep(torch, rb, ops, dev, hbm):
 
 def k_sweep_stencil(torch, rb, g, dev, hbm):
     """The channel Laplacian as a matrix-free operator (rb_fvm_stencil_create: entries formed
-    from per-axis tables), k = 1 .. 32, FP64 and FP32 (events, median of 10 after tuning):
+    from per-axis tables), k = 1 .. 32, FP64 and FP32 (tuned; spmm_ms: graph replays, inputs cycled past
+    the L2):
     algorithmic bytes are X read once and Y written, s k (n_r + n_c), the tables (a few KB)
     aside; beside each, the CSR kernel's time at the same k from `ksweep`."""
     nodes, per = rb.grid_nodes(g, dev)
@@ -823,8 +857,8 @@ def k_sweep_stencil(torch, rb, g, dev, hbm):
             X = torch.randn((op.n_cols, k), dtype=tdt, device=dev)
             Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
             op.tune(X, Y)
-            ms = time_events(torch, lambda: op.spmm(X, Y), 10)
             by = s_b * k * (op.n_rows + op.n_cols)
+            ms = spmm_ms(torch, op, X, Y, by)
             res.append({"dtype": dt, "format": "stencil", "k": k, "ms": ms, "gflops": 2 * op.nnz * k / ms / 1e6,
                         "gbs": by / ms / 1e6, "frac_hbm": by / ms / 1e6 / hbm, "schedule": op.schedule(X, Y)})
             del X, Y
@@ -945,17 +979,20 @@ def multigrid(torch, rb, g, dev, poisson_res=None):
 
 
 def learned_guess(torch, rb, dev, args):
-    """Learned initial guess on the Rayleigh-Benard-shaped 128^3 grid: solver-generated pairs
-    (8 forcing sequences solved together, k = 8), training with the library's tcgen05 kernels,
-    then CG to 1e-10 on held-out steps from zero (FP64 CG), from p_{t-1} (FP64 CG and
-    FP32-inner refinement) and from the judged learned guess (refinement)."""
+    """Learned initial guess on the Rayleigh-Benard-shaped 128^3 grid (walls in z, tanh 1.4):
+    solver-generated pairs (8 forcing sequences solved together, k = 8, by the multigrid CG),
+    training with the library's tcgen05 kernels, then CG to 1e-10 on held-out steps from each
+    guess (zero, p_{t-1}, the judged network guess, the Galerkin combinations) with the Jacobi
+    solvers and the multigrid CG (guess_pipeline.evaluate).  Full configuration by default:
+    8 x 252 steps, 1800 training and 200 held-out pairs, 6 epochs."""
     from paper_2508_06710_gb300 import guess_pipeline as gp
 
     n = W.GUESS_N
     chains = W.GUESS_CHAINS
-    steps = W.GUESS_STEPS if args.guess_full else 40
-    holdout = W.GUESS_HOLDOUT if args.guess_full else 4
-    epochs = args.guess_epochs if args.guess_epochs else (6 if args.guess_full else 3)
+    full = not args.guess_quick
+    steps = W.GUESS_STEPS if full else 40
+    holdout = W.GUESS_HOLDOUT if full else 4
+    epochs = args.guess_epochs if args.guess_epochs else (6 if full else 3)
     grid = W.rbc_grid(n, 1.4)
     prob = gp.make_problem(torch, grid, chains, dev)
     spectra = W.forcing_spectra(steps, chains, seed=5000)
@@ -977,7 +1014,7 @@ def learned_guess(torch, rb, dev, args):
             lvl = int(name[3])
             conv_flops += 2 * 27 * ci * co * (prob["n"] >> (3 * lvl))
     return {"grid": f"rbc {n}^3 tanh 1.4", "params": net.n_params, "chains": chains, "steps": steps,
-            "holdout": holdout, "full_config": bool(args.guess_full), "generate": gen,
+            "holdout": holdout, "full_config": full, "generate": gen,
             "predict_ms": t_pred, "train_sample_ms": t_lg,
             "forward_conv_tflops": conv_flops / (t_pred * 1e-3) / 1e12,
             "train": {k: v for k, v in tr.items()}, "eval": ev}
@@ -1328,9 +1365,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="timed step only (no e2e, sweeps, solves, CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-guess", action="store_true", help="skip the learned-guess section")
-    ap.add_argument("--guess-full", action="store_true",
-                    help="learned guess on the full data set: 8 sequences x 252 steps (1800 training, 200 test "
-                         "pairs); the default uses 8 x 40 steps to keep the run within minutes")
+    ap.add_argument("--guess-quick", action="store_true",
+                    help="learned guess on a reduced data set (8 sequences x 40 steps, 3 epochs); the default is "
+                         "the full Rayleigh-Benard configuration: 8 sequences x 252 steps (1800 training, 200 test "
+                         "pairs), 6 epochs")
     ap.add_argument("--guess-epochs", type=int, default=None)
     ap.add_argument("--nvtx", action="store_true",
                     help="NVTX ranges around the timed region ('timed_step') and each SpMM (its label), for ncu filters")

@@ -238,6 +238,15 @@ rb_status rb_fvm_stencil_create(const rb_grid_desc* grid, double scale, rb_dtype
                                 rb_stream_t stream, rb_op_t* out);
 
 rb_status rb_operator_destroy(rb_op_t op);
+
+/* Scheduling hint for a CSR operator whose rows form n_blocks (<= 3) consecutive blocks that
+ * address the same columns in the same order: the x-, y- and z-face rows of the gradient G, each
+ * block sweeping all cells.  The SpMM without staging then takes row tiles from the blocks in
+ * turn, so that the tiles gathering one region of X run together and X is read from HBM about
+ * once instead of once per block.  starts: HOST array of the blocks' first rows (starts[0] = 0,
+ * increasing, < n_rows).  n_blocks = 1 removes the hint.  Results do not change (each row's
+ * sum is the same); RB_EINVAL for invalid starts or a non-CSR operator. */
+rb_status rb_operator_set_row_blocks(rb_op_t op, int32_t n_blocks, const int32_t* starts);
 rb_status rb_operator_info(rb_op_t op, rb_op_info* info);
 /* Synchronises `stream` and reports whether a kernel applying `op` since the last check gave
  * up a bounded wait on its shared-memory pipeline (RB_ETIMEOUT; the affected outputs are

@@ -30,7 +30,8 @@ RB_MAX_K = 64
 # exported C symbols, in the order include/rbspmm.h declares them
 SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_stencil_assemble",
            "rb_refine_assemble", "rb_mesh_cot_laplacian", "rb_fvm_stencil_create",
-           "rb_operator_create", "rb_operator_destroy", "rb_operator_info", "rb_operator_check", "rb_spmm",
+           "rb_operator_create", "rb_operator_destroy", "rb_operator_set_row_blocks", "rb_operator_info",
+           "rb_operator_check", "rb_spmm",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
            "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier", "rb_guess_param_count", "rb_guess_create",
@@ -131,6 +132,7 @@ def lib():
                                          C.POINTER(vp)]),
         "rb_fvm_stencil_create": (C.c_int, [C.POINTER(GridDesc), dbl, C.c_int, i32, vp, C.POINTER(vp)]),
         "rb_operator_destroy": (C.c_int, [vp]),
+        "rb_operator_set_row_blocks": (C.c_int, [vp, i32, C.POINTER(i32)]),
         "rb_operator_info": (C.c_int, [vp, C.POINTER(OpInfo)]),
         "rb_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp, vp]),
         "rb_tune_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp]),
@@ -409,6 +411,13 @@ class Operator:
         _check(lib().rb_get_spmm_schedule(self.handle, k, ldx, ldy, _ptr(X), _ptr(Y), C.byref(s)),
                "rb_get_spmm_schedule")
         return {"vec": s.vec, "lpr": s.lpr, "stage": s.stage, "grid_cap": s.grid_cap}
+
+    def set_row_blocks(self, starts):
+        """Rows in len(starts) blocks starting at these rows that address the same columns in order
+        (rb_operator_set_row_blocks); [] or [0] removes the hint."""
+        starts = [int(v) for v in starts] or [0]
+        _check(lib().rb_operator_set_row_blocks(self.handle, len(starts), (C.c_int32 * len(starts))(*starts)),
+               "rb_operator_set_row_blocks")
 
     def check(self, stream=None):
         """Raises RbError(RB_ETIMEOUT) if a pipelined SpMM kernel gave up a bounded wait."""

@@ -359,6 +359,24 @@ extern "C" rb_status rb_operator_check(rb_op_t op, rb_stream_t stream) {
   return RB_OK;
 }
 
+extern "C" rb_status rb_operator_set_row_blocks(rb_op_t op, int32_t n_blocks, const int32_t* starts) {
+  clear_error();
+  RB_REQUIRE(op != nullptr, "rb_operator_set_row_blocks: null operator");
+  RB_REQUIRE(n_blocks >= 1 && n_blocks <= 3, "rb_operator_set_row_blocks: n_blocks = %d outside [1, 3]", n_blocks);
+  RB_REQUIRE(op->format == RB_CSR, "rb_operator_set_row_blocks: CSR operators only");
+  RB_REQUIRE(n_blocks == 1 || starts != nullptr, "rb_operator_set_row_blocks: null starts");
+  if (n_blocks > 1) {
+    RB_REQUIRE(starts[0] == 0, "rb_operator_set_row_blocks: the first block must start at row 0");
+    for (int b = 1; b < n_blocks; ++b)
+      RB_REQUIRE(starts[b] > starts[b - 1] && starts[b] < op->n_rows,
+                 "rb_operator_set_row_blocks: block starts must increase within [0, n_rows)");
+  }
+  op->n_rblk = n_blocks;
+  for (int b = 0; b < n_blocks; ++b) op->rblk_off[b] = n_blocks > 1 ? starts[b] : 0;
+  op->rblk_off[n_blocks] = op->n_rows;
+  return RB_OK;
+}
+
 extern "C" rb_status rb_operator_info(rb_op_t op, rb_op_info* info) {
   clear_error();
   RB_REQUIRE(op && info, "rb_operator_info: null argument");

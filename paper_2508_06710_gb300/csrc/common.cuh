@@ -122,6 +122,8 @@ struct rb_op {
   void* st_w[3] = {nullptr, nullptr, nullptr};
   void* st_ic[3] = {nullptr, nullptr, nullptr};
   double st_scale = 1.0;
+  int32_t n_rblk = 1;                     // row blocks addressing the same columns in order
+  int32_t rblk_off[4] = {0, 0, 0, 0};      // their starts and the end (rb_operator_set_row_blocks)
   int* err = nullptr;  // device status word: nonzero after a bounded wait in a kernel gave up
   std::map<int, rb::SpmmSched> tuned;  // k -> schedule chosen by rb_tune_spmm
 };

@@ -24,6 +24,10 @@ struct CsrArgs {
   // extruded operator: Y = A' X + w_i (x_{z-1} + x_{z+1}) across the k periodic columns, A'
   // the stored values (dz A~ with -2 w_i folded into the diagonal)
   const T* __restrict__ zw = nullptr;
+  // row blocks that address the same columns in the same order (the x, y, z faces of a
+  // gradient): the direct kernel takes tiles from the blocks in turn (nblk > 1)
+  int nblk = 1;
+  int blk_off[4] = {0, 0, 0, 0};  // block starts and the end (nblk + 1 entries)
 };
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
@@ -55,6 +59,9 @@ inline void fill_csr_args(const rb_op* op, const SpmmSched& sc, CsrArgs<T>& a, s
   a.kp = sc.kp;
   a.stage_cap = stage_capacity<T>(op, sc.rows_per_block(), sc.stage, smem_limit);
   a.zw = (sizeof(T) == 8) ? reinterpret_cast<const T*>(op->zw64) : reinterpret_cast<const T*>(op->zw32);
+  a.nblk = op->n_rblk > 1 ? op->n_rblk : 1;
+  for (int b = 0; b <= a.nblk && b < 4; ++b) a.blk_off[b] = op->rblk_off[b];
+  if (a.nblk == 1) a.blk_off[0] = 0, a.blk_off[1] = op->n_rows;
 }
 
 struct TileInfo {
@@ -213,6 +220,32 @@ __device__ __forceinline__ void store_row(const CsrArgs<T>& a, int64_t row, int 
 
 // SpMM without staging: a persistent grid strides over blocks of R = 256 / (KP LPR) rows;
 // no block-wide barrier anywhere, so every warp keeps its gathers in flight independently.
+// The same kernel for an operator whose rows come in blocks addressing the same columns in the
+// same order (its row-block hint): tile q of block b is work item q * nblk + b, so that the
+// tiles at one position of every block, which gather the same region of X, run at about the
+// same time and find X in L2.  A separate kernel, so that the plain one's code is unaffected.
+template <typename T, int VEC, int LPR, int EPI>
+__global__ void __launch_bounds__(kThreads) k_spmm_direct_blk(CsrArgs<T> a) {
+  const int R = kThreads / (a.kp * LPR);
+  const int t = threadIdx.x;
+  const int sub = t % LPR;
+  const int rc = t / LPR;
+  const int chunk = rc % a.kp;
+  const int rloc = rc / a.kp;
+  int64_t tiles = 0;
+  for (int b = 0; b < a.nblk; ++b) tiles = max(tiles, (int64_t)(a.blk_off[b + 1] - a.blk_off[b] + R - 1) / R);
+  for (int64_t w = blockIdx.x; w < tiles * a.nblk; w += gridDim.x) {
+    const int b = (int)(w % a.nblk);
+    const int64_t row = a.blk_off[b] + (w / a.nblk) * R + rloc;
+    const bool active = row < a.blk_off[b + 1] && chunk * VEC < a.k;
+    T acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = T(0);
+    row_accumulate_direct<T, VEC, LPR>(a, row, chunk, sub, active, acc);
+    if (active && sub == 0) store_row<T, VEC, EPI>(a, row, chunk, acc);
+  }
+}
+
 template <typename T, int VEC, int LPR, int EPI>
 __global__ void __launch_bounds__(kThreads) k_spmm_direct(CsrArgs<T> a) {
   const int R = kThreads / (a.kp * LPR);

@@ -102,7 +102,7 @@ rb_status launch_csr(const rb_op* op, const SpmmSched& sc, const T* X, int64_t l
     const size_t smem = csr_smem_bytes<T>(R, a.stage_cap);
     k_spmm_csr<T, VEC, LPR, EPI><<<(unsigned)std::min<int64_t>(grid, INT32_MAX), kThreads, smem, s>>>(a);
   } else {
-    auto* kern = &k_spmm_direct<T, VEC, LPR, EPI>;
+    auto* kern = a.nblk > 1 ? &k_spmm_direct_blk<T, VEC, LPR, EPI> : &k_spmm_direct<T, VEC, LPR, EPI>;
     if (sc.grid_cap < 0) grid = wave_grid(kern, grid);  // one resident wave, grid-stride
     else if (sc.grid_cap > 0) grid = std::min<int64_t>(grid, sc.grid_cap);
     kern<<<(unsigned)std::min<int64_t>(grid, INT32_MAX), kThreads, 0, s>>>(a);

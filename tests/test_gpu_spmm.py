@@ -234,6 +234,48 @@ def test_spmm_channel_full_size_k3(rb, dtype):
     _run(rb, A, X, dtype)
 
 
+def _face_starts(g):
+    """First rows of the x-, y- and z-face blocks of the gradient of grid g."""
+    n = [a.n for a in g.axes]
+    counts = []
+    for d in range(3):
+        c = n[d] if g.axes[d].periodic else n[d] - 1
+        for e in range(3):
+            if e != d:
+                c *= n[e]
+        counts.append(c)
+    return [0, counts[0], counts[0] + counts[1]]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 4])
+@pytest.mark.parametrize("lpr", [1, 2])
+def test_spmm_row_blocks_interleaved(rb, dtype, k, lpr):
+    """The row-block hint (the gradient's x, y, z face blocks, of unequal lengths on a walled
+    grid; and three arbitrary blocks of a random matrix): the direct kernel takes tiles from
+    the blocks in turn; every row's result is unchanged."""
+    g = W.channel_grid(40, 31, 23)
+    G = fvm.gradient(g)
+    starts = _face_starts(g)
+    assert starts[2] < G.shape[0]
+    for A, st in ((G, starts), (_rand_csr(7001, 3001, 5, seed=95), [0, 1000, 4500])):
+        X = W.normal((A.shape[1], k), 96 + k)
+        npdt = np.float64 if dtype == "f64" else np.float32
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        op = rb.Operator.from_scipy(A, dtype=dtype, k_max=k)
+        op.set_row_blocks(st)
+        vec = 3 if k == 3 else min(k, 16 // (8 if dtype == "f64" else 4))
+        op.set_schedule(k, vec, lpr, 0, -1)
+        Yd = torch.full((A.shape[0], k), float("nan"), dtype=tdt, device="cuda")
+        op.spmm(to_dev(X.astype(npdt)), Yd)
+        Aref = A if dtype == "f64" else spmm.round_f32(A)
+        Xref = X.astype(npdt).astype(np.float64)
+        ok, worst = componentwise_ok(Yd.cpu().numpy(), spmm.spmm(Aref, Xref), spmm.abs_bound(Aref, Xref), TOL[dtype])
+        assert ok, worst
+    with pytest.raises(rb.RbError):
+        op.set_row_blocks([0, 5000, 3000])  # not increasing
+
+
 @pytest.mark.parametrize("name,k", [("G", 3), ("L", 32)])
 @pytest.mark.parametrize("sched", ["tuned", "tma"])
 def test_spmm_channel_full_size_fp32_timed_schedules(rb, name, k, sched):
