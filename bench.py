@@ -161,8 +161,7 @@ def build_ops(rb, torch, dev):
         for dt in ("f64", "f32"):
             ops[(name, dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, k_max=32), k)
             ops[(name + "-sell", dt)] = (rb.Operator(rp, ci, va, nc, dtype=dt, fmt="sell", k_max=32), k)
-            if name == "G":  # its x-, y- and z-face rows each sweep all cells: take their tiles in turn
-                ops[(name, dt)][0].set_row_blocks(face_starts(g))
+        ops[(name, "df64")] = (rb.Operator(rp, ci, va, nc, dtype="df64", k_max=32), k)
         if name == "L":  # the Poisson matrix A = -L, assembled with scale -1
             rp, ci, va, nc = rb.fvm_assemble(nodes, per, kind, scale=-1.0)
             ops[("A", "f64")] = (rb.Operator(rp, ci, va, nc, dtype="f64", k_max=3), 3)
@@ -285,6 +284,7 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e(args, torch, step_items, stream, dev, flops_step)
         out["ksweep"] = k_sweep(torch, rb, ops, dev, hbm)
         out["ksweep_stencil"] = k_sweep_stencil(torch, rb, g, dev, hbm)
+        out["step_variants"] = step_variants(torch, rb, ops, g, dev, hbm)
         out["poisson"] = poisson(torch, rb, ops, g, dev)
         out["multigrid"] = multigrid(torch, rb, g, dev, out["poisson"])
         out["operator_build"] = operator_build(torch, rb, g, dev)
@@ -817,19 +817,28 @@ def e2e(args, torch, step_items, stream, dev, flops_step):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+def _blocks_for(torch, rb, op, dt, k, dev):
+    """Seeded N(0,1) X and an empty Y for op in its type (double-float: split from FP64)."""
+    if dt == "df64":
+        X = rb.df_split(torch.randn((op.n_cols, k), dtype=torch.float64, device=dev))
+        return X, torch.empty((op.n_rows, k, 2), dtype=torch.float32, device=dev)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    return (torch.randn((op.n_cols, k), dtype=tdt, device=dev),
+            torch.empty((op.n_rows, k), dtype=tdt, device=dev))
+
+
 def k_sweep(torch, rb, ops, dev, hbm):
-    """Laplacian SpMM for k = 1 .. 32 in FP64 and FP32, CSR and SELL (tuned; spmm_ms: graph replays,
-    inputs cycled past the L2)."""
+    """Laplacian SpMM for k = 1 .. 32 in FP64, FP32 and double-float, CSR and SELL (tuned;
+    spmm_ms: graph replays, inputs cycled past the L2).  The double-float column moves FP64's
+    bytes (8-byte pairs) and does its arithmetic on the FP32 pipe."""
     res = []
-    for dt, fmt in (("f64", "csr"), ("f32", "csr"), ("f64", "sell"), ("f32", "sell")):
+    for dt, fmt in (("f64", "csr"), ("f32", "csr"), ("df64", "csr"), ("f64", "sell"), ("f32", "sell")):
         op, _ = ops[("L" if fmt == "csr" else "L-sell", dt)]
-        tdt = torch.float64 if dt == "f64" else torch.float32
         base = None
         for k in W.ks_sweep():
-            X = torch.randn((op.n_cols, k), dtype=tdt, device=dev)
-            Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
+            X, Y = _blocks_for(torch, rb, op, dt, k, dev)
             op.tune(X, Y)
-            s_b = 8 if dt == "f64" else 4
+            s_b = 4 if dt == "f32" else 8
             by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, s_b)
             ms = spmm_ms(torch, op, X, Y, by)
             if k == 1:
@@ -839,6 +848,62 @@ def k_sweep(torch, rb, ops, dev, hbm):
                         "speedup_vs_k_spmv": k * base / ms, "schedule": op.schedule(X, Y)})
             del X, Y
     return res
+
+
+def step_variants(torch, rb, ops, g, dev, hbm):
+    """Two variants of the timed step's kernels, each beside the plain one (spmm_ms: graph
+    replays, inputs cycled past the L2): the FP64 SpMMs in double-float arithmetic (the same
+    bytes, the multiply-adds on the FP32 pipe), and the gradient with its row-block hint (the
+    x-, y- and z-face row blocks taking tiles in turn)."""
+    out = {"df64_vs_f64": [], "row_block_hint": []}
+    for name in ("L", "G", "M"):
+        op64, k = ops[(name, "f64")]
+        opdf, _ = ops[(name, "df64")]
+        by = spmm_bytes(op64.nnz, op64.n_rows, op64.n_cols, k, 8)
+        r = {"op": f"{name}-k{k}"}
+        for dt, op in (("f64", op64), ("df64", opdf)):
+            X, Y = _blocks_for(torch, rb, op, dt, k, dev)
+            op.tune(X, Y)
+            ms = spmm_ms(torch, op, X, Y, by)
+            r[dt + "_us"] = ms * 1e3
+            r[dt + "_frac_hbm"] = by / ms / 1e6 / hbm
+            r[dt + "_schedule"] = op.schedule(X, Y)
+            del X, Y
+        r["speedup"] = r["f64_us"] / r["df64_us"]
+        out["df64_vs_f64"].append(r)
+    for dt in ("f64", "f32"):
+        op, k = ops[("G", dt)]
+        X, Y = _blocks_for(torch, rb, op, dt, k, dev)
+        by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, 8 if dt == "f64" else 4)
+        sched = op.schedule(X, Y)
+        op.set_schedule(k, sched["vec"], sched["lpr"], 0, -1)  # the direct kernel, with and without the hint
+        plain = spmm_ms(torch, op, X, Y, by)
+        op.set_row_blocks(face_starts(g))
+        hinted = spmm_ms(torch, op, X, Y, by)
+        op.set_row_blocks([0])
+        op.tune(X, Y)  # back to the tuned schedule for later sections
+        out["row_block_hint"].append({"op": f"G-{dt}-k{k}", "plain_us": plain * 1e3, "hint_us": hinted * 1e3})
+        del X, Y
+    # the three kernel families on every operator of the step, at the tuned vector width with one
+    # lane per row: direct (indices and values read by the row's lanes), staged (a block's
+    # nonzeros copied to shared memory by its threads first), TMA (a producer warp streaming
+    # tiles into a 3-stage shared-memory ring)
+    out["schedule_families"] = []
+    for name in ("L", "G", "M"):
+        for dt in ("f64", "f32"):
+            op, k = ops[(name, dt)]
+            X, Y = _blocks_for(torch, rb, op, dt, k, dev)
+            by = spmm_bytes(op.nnz, op.n_rows, op.n_cols, k, 8 if dt == "f64" else 4)
+            op.tune(X, Y)
+            tuned = op.schedule(X, Y)
+            r = {"op": f"{name}-{dt}-k{k}", "tuned": tuned}
+            for fam, stage, gc in (("direct", 0, -1), ("staged", 1, 0), ("tma", 2, 0)):
+                op.set_schedule(k, tuned["vec"], 1, stage, gc)
+                r[fam + "_us"] = spmm_ms(torch, op, X, Y, by) * 1e3
+            op.tune(X, Y)
+            out["schedule_families"].append(r)
+            del X, Y
+    return out
 
 
 def k_sweep_stencil(torch, rb, g, dev, hbm):
@@ -1202,6 +1267,10 @@ def headline(out, detail_path):
     ks = out.get("ksweep")
     if ks:
         s["ksweep_frac_hbm_csr"] = {f"{r['dtype']}-k{r['k']}": round(r["frac_hbm"], 3) for r in ks if r["format"] == "csr"}
+    sv = out.get("step_variants")
+    if sv:
+        s["df64_vs_f64_us"] = {r["op"]: [r["f64_us"], r["df64_us"]] for r in sv["df64_vs_f64"]}
+        s["families_us"] = {r["op"]: [r["direct_us"], r["staged_us"], r["tma_us"]] for r in sv["schedule_families"]}
     kst = out.get("ksweep_stencil")
     if kst:
         s["ksweep_stencil_gflops"] = {f"{r['dtype']}-k{r['k']}": r["gflops"] for r in kst}

@@ -55,7 +55,15 @@ typedef enum {
   RB_EUNSUPPORTED = 7   /* a valid request this build does not implement */
 } rb_status;
 
-typedef enum { RB_F64 = 0, RB_F32 = 1 } rb_dtype;
+/* RB_DF64 ("double-float"): an FP64 number carried as the unevaluated sum hi + lo of two FP32
+ * numbers (Dekker 1971), stored as an 8-byte pair {float hi; float lo;} with hi at the lower
+ * address, hi = RN32(x), lo = RN32(x - hi).  About 48 significant bits; FP32's exponent range
+ * (|x| above ~3.4e38 becomes infinite, |x| below ~1e-30 keeps fewer low bits).  Operators
+ * (CSR only) and rb_spmm take it: the FP64 rate of GB300 is 1/64 of its FP32 rate, and the
+ * error-free FP32 transformations of a double-float multiply-add take about twelve FP32
+ * instructions, so the SpMM's k multiply-adds per entry run at FP32-pipe speed while moving
+ * FP64's bytes.  rb_df64_split / rb_df64_join convert FP64 blocks. */
+typedef enum { RB_F64 = 0, RB_F32 = 1, RB_DF64 = 2 } rb_dtype;
 typedef enum { RB_CSR = 0, RB_SELL = 1, RB_AUTO = 2, RB_STENCIL = 3 } rb_format;
 
 /* Message of the calling thread's last failed call ("" if none). Owned by the library. */
@@ -217,7 +225,8 @@ typedef struct {
 } rb_op_info;
 
 /* Copies and validates the CSR (monotone row_ptr, col_idx in range, finite values;
- * RB_EINVAL otherwise), converts values to `dtype` (RB_F32: round to nearest even), and
+ * RB_EINVAL otherwise), converts values to `dtype` (RB_F32: round to nearest even; RB_DF64:
+ * the pairs of rb_df64_split, CSR layout only, not extruded, values within FP32's range), and
  * lays it out in `format` (RB_SELL: sliced ELL with C = 32 rows per slice and rows sorted
  * by length within windows of sigma = 256 rows; RB_AUTO picks CSR).  Also stores the
  * inverse diagonal for Jacobi preconditioning when the operator is square.  Allocates;
@@ -254,13 +263,22 @@ rb_status rb_operator_info(rb_op_t op, rb_op_info* info);
 rb_status rb_operator_check(rb_op_t op, rb_stream_t stream);
 
 /* Y = A~ X with a per-column scale:  Y[i, j] = c[j] * sum_p val[p] X[idx[p], j]  (Algorithm 1).
- * X: n_cols x k (ldx), Y: n_rows x k (ldy), both of the operator's dtype; c: k float64
+ * X: n_cols x k (ldx), Y: n_rows x k (ldy), both of the operator's dtype (RB_DF64: pairs,
+ * the CSR kernel without staging, each row's sum formed with TwoProd/TwoSum and within about
+ * 2^-46 sum_p |val[p] X[idx[p], j]| of the exact value); c: k float64
  * DEVICE values or NULL (= 1).  For an extruded operator k must equal extruded_nz and
  * the full L3D is applied (c is then applied to the whole row).  X and Y must not
  * overlap.  Vector width, rows per block and lanes per row are chosen per (operator, k)
  * from the tuning table (rb_tune_spmm). */
 rb_status rb_spmm(rb_op_t A, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t k, const double* c,
                   rb_stream_t stream);
+
+/* FP64 block <-> double-float block (RB_DF64 pairs), n x k, leading dimensions in elements
+ * (pairs count as one element):  rb_df64_split: D[i, j] = (RN32(x), RN32(x - RN32(x))) for
+ * x = X[i, j] (|x| above FP32's range gives infinite pairs);  rb_df64_join: X[i, j] =
+ * RN64(hi + lo).  DEVICE blocks, 8-byte aligned, not overlapping; RB_EINVAL otherwise. */
+rb_status rb_df64_split(int64_t n, int32_t k, const double* X, int64_t ldx, void* D, int64_t ldd, rb_stream_t stream);
+rb_status rb_df64_join(int64_t n, int32_t k, const void* D, int64_t ldd, double* X, int64_t ldx, rb_stream_t stream);
 
 /* Times the candidate SpMM schedules for (A, k) on scratch copies of X/Y shapes and
  * stores the fastest in A's tuning table (synchronises; X, Y as for rb_spmm, their

@@ -6,7 +6,9 @@ computation runs in the library's CUDA kernels; there is no Python or CPU fallba
 librbspmm.so is missing the calls raise.
 
 Layout: a block of k right-hand sides is a 2-D tensor (n, k) whose rows are contiguous
-(stride (ld, 1), ld >= k): the k columns of one row are interleaved, as in Algorithm 1.
+(stride (ld, 1), ld >= k): the k columns of one row are interleaved, as in Algorithm 1.  A
+double-float block (dtype "df64": FP64 values as pairs hi + lo of FP32 numbers) is a float32
+tensor (n, k, 2) with strides (2 ld, 2, 1): the same bytes as an (n, k) float64 block.
 """
 from __future__ import annotations
 
@@ -20,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "librbspmm.so")
 RB_OK, RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ENOCONV, RB_EBREAKDOWN, RB_ETIMEOUT, RB_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["RB_OK", "RB_EINVAL", "RB_ENOMEM", "RB_ECUDA", "RB_ENOCONV", "RB_EBREAKDOWN", "RB_ETIMEOUT",
                 "RB_EUNSUPPORTED"]
-RB_F64, RB_F32 = 0, 1
+RB_F64, RB_F32, RB_DF64 = 0, 1, 2
 RB_CSR, RB_SELL, RB_AUTO, RB_STENCIL = 0, 1, 2, 3
 RB_FVM_LAPLACIAN, RB_FVM_DIVERGENCE, RB_FVM_GRADIENT, RB_FVM_INTERP_C2S, RB_FVM_INTERP_S2C = 0, 1, 2, 3, 4
 RB_STENCIL_13P, RB_STENCIL_27P = 13, 27
@@ -31,7 +33,7 @@ RB_MAX_K = 64
 SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_fvm_assemble", "rb_stencil_assemble",
            "rb_refine_assemble", "rb_mesh_cot_laplacian", "rb_fvm_stencil_create",
            "rb_operator_create", "rb_operator_destroy", "rb_operator_set_row_blocks", "rb_operator_info",
-           "rb_operator_check", "rb_spmm",
+           "rb_operator_check", "rb_spmm", "rb_df64_split", "rb_df64_join",
            "rb_tune_spmm", "rb_set_spmm_schedule", "rb_get_spmm_schedule", "rb_dot_workspace_bytes", "rb_dot",
            "rb_dot_noalloc", "rb_axpy", "rb_axty", "rb_cg_workspace_bytes", "rb_cg_solve", "rb_batch_create", "rb_batch_destroy",
            "rb_batch_solve", "rb_batch_tune", "rb_batch_set_barrier", "rb_guess_param_count", "rb_guess_create",
@@ -135,6 +137,8 @@ def lib():
         "rb_operator_set_row_blocks": (C.c_int, [vp, i32, C.POINTER(i32)]),
         "rb_operator_info": (C.c_int, [vp, C.POINTER(OpInfo)]),
         "rb_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp, vp]),
+        "rb_df64_split": (C.c_int, [i64, i32, vp, i64, vp, i64, vp]),
+        "rb_df64_join": (C.c_int, [i64, i32, vp, i64, vp, i64, vp]),
         "rb_tune_spmm": (C.c_int, [vp, vp, i64, vp, i64, i32, vp]),
         "rb_set_spmm_schedule": (C.c_int, [vp, i32, C.POINTER(SpmmSchedule)]),
         "rb_get_spmm_schedule": (C.c_int, [vp, i32, i64, i64, vp, vp, C.POINTER(SpmmSchedule)]),
@@ -216,8 +220,18 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
-def _block(t, name):
-    """(pointer, n, k, ld) of a row-major 2-D block whose rows are contiguous."""
+def _block(t, name, pairs=False):
+    """(tensor, n, k, ld) of a row-major 2-D block whose rows are contiguous, or (pairs) of a
+    double-float block (float32, (n, k, 2), strides (2 ld, 2, 1)); ld in elements (pairs)."""
+    if pairs:
+        torch = _torch()
+        if t.dim() != 3 or t.dtype != torch.float32 or t.shape[2] != 2 or t.stride(2) != 1 or t.stride(1) != 2 or t.stride(0) % 2:
+            raise ValueError(f"{name}: a double-float block is float32 (n, k, 2) with strides (2 ld, 2, 1)")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        return t, t.shape[0], t.shape[1], max(t.stride(0) // 2, t.shape[1])
+    if t.dim() == 3:
+        raise ValueError(f"{name}: a double-float block goes only to a df64 operator or df_join")
     if t.dim() == 1:
         t = t.view(-1, 1)
     if t.dim() != 2 or t.stride(1) != 1:
@@ -330,7 +344,8 @@ def mesh_cot_laplacian(points, triangles, row_ptr, col_idx, stream=None):
 
 # ----------------------------------------------------------------------------- operators
 class Operator:
-    """A = I_k (x) A~ stored once on the device (CSR or sliced ELL, FP64 or FP32)."""
+    """A = I_k (x) A~ stored once on the device (CSR or sliced ELL, FP64 or FP32; CSR as
+    double-float pairs with dtype "df64")."""
 
     def __init__(self, row_ptr, col_idx, vals, n_cols, dtype="f64", fmt="csr", k_max=1, extruded_nz=0,
                  z_weight=None, dz=0.0, stream=None):
@@ -344,7 +359,7 @@ class Operator:
                     va.data_ptr() if va.numel() else None, 1 if on_dev else 0)
         b = BlockDesc(int(k_max), int(extruded_nz), None if zw is None else zw.data_ptr(), float(dz))
         h = C.c_void_p()
-        dt = {"f64": RB_F64, "f32": RB_F32}[dtype]
+        dt = {"f64": RB_F64, "f32": RB_F32, "df64": RB_DF64}[dtype]
         fm = {"csr": RB_CSR, "sell": RB_SELL, "auto": RB_AUTO}[fmt]
         _check(lib().rb_operator_create(C.byref(d), C.byref(b), dt, fm, _stream(stream) if on_dev else None,
                                         C.byref(h)), "rb_operator_create")
@@ -386,18 +401,29 @@ class Operator:
         _check(lib().rb_operator_info(self.handle, C.byref(inf)), "rb_operator_info")
         return inf
 
+    def _blocks(self, X, Y):
+        """Checks that X and Y hold the operator's type: float64 (f64), float32 (f32) or
+        double-float pairs (df64)."""
+        torch = _torch()
+        pairs = self.dtype == "df64"
+        want = torch.float32 if self.dtype in ("f32", "df64") else torch.float64
+        X, _, k, ldx = _block(X, "X", pairs)
+        Y, _, _, ldy = _block(Y, "Y", pairs)
+        if X.dtype != want or Y.dtype != want:
+            raise ValueError(f"X and Y must be {want} blocks for a {self.dtype} operator")
+        return X, k, ldx, Y, ldy
+
     def spmm(self, X, Y=None, c=None, stream=None):
         torch = _torch()
-        X, _, k, ldx = _block(X, "X")
         if Y is None:
-            Y = torch.empty((self.n_rows, k), dtype=X.dtype, device=X.device)
-        Y, _, _, ldy = _block(Y, "Y")
+            shape = (self.n_rows, X.shape[1], 2) if self.dtype == "df64" else (self.n_rows, X.shape[1] if X.dim() > 1 else 1)
+            Y = torch.empty(shape, dtype=X.dtype, device=X.device)
+        X, k, ldx, Y, ldy = self._blocks(X, Y)
         _check(lib().rb_spmm(self.handle, _ptr(X), ldx, _ptr(Y), ldy, k, _ptr(c), _stream(stream)), "rb_spmm")
         return Y
 
     def tune(self, X, Y, stream=None):
-        X, _, k, ldx = _block(X, "X")
-        Y, _, _, ldy = _block(Y, "Y")
+        X, k, ldx, Y, ldy = self._blocks(X, Y)
         _check(lib().rb_tune_spmm(self.handle, _ptr(X), ldx, _ptr(Y), ldy, k, _stream(stream)), "rb_tune_spmm")
 
     def set_schedule(self, k, vec, lpr=1, stage=0, grid_cap=-1):
@@ -405,8 +431,7 @@ class Operator:
         _check(lib().rb_set_spmm_schedule(self.handle, k, C.byref(s)), "rb_set_spmm_schedule")
 
     def schedule(self, X, Y):
-        X, _, k, ldx = _block(X, "X")
-        Y, _, _, ldy = _block(Y, "Y")
+        X, k, ldx, Y, ldy = self._blocks(X, Y)
         s = SpmmSchedule()
         _check(lib().rb_get_spmm_schedule(self.handle, k, ldx, ldy, _ptr(X), _ptr(Y), C.byref(s)),
                "rb_get_spmm_schedule")
@@ -433,6 +458,35 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- double-float blocks
+def df_split(X, out=None, stream=None):
+    """The double-float block (float32 (n, k, 2)) of the float64 block X (rb_df64_split)."""
+    torch = _torch()
+    X, n, k, ldx = _block(X, "X")
+    if X.dtype != torch.float64:
+        raise ValueError("X must be a float64 block")
+    if out is None:
+        out = torch.empty((n, k, 2), dtype=torch.float32, device=X.device)
+    out, nd, kd, ldd = _block(out, "out", pairs=True)
+    if nd != n or kd != k:
+        raise ValueError("out must be a double-float block of X's shape")
+    _check(lib().rb_df64_split(n, k, _ptr(X), ldx, _ptr(out), ldd, _stream(stream)), "rb_df64_split")
+    return out
+
+
+def df_join(D, out=None, stream=None):
+    """The float64 block hi + lo of the double-float block D (rb_df64_join)."""
+    torch = _torch()
+    D, n, k, ldd = _block(D, "D", pairs=True)
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.float64, device=D.device)
+    out, no, ko, ldx = _block(out, "out")
+    if out.dtype != torch.float64 or no != n or ko != k:
+        raise ValueError("out must be a float64 block of D's shape")
+    _check(lib().rb_df64_join(n, k, _ptr(D), ldd, _ptr(out), ldx, _stream(stream)), "rb_df64_join")
+    return out
 
 
 # ----------------------------------------------------------------------------- basic operations

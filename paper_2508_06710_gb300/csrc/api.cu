@@ -126,6 +126,19 @@ rb_status upload_values(rb_op* op, void** dst, const std::vector<double>& v, cud
     RB_TRY(upload(p, v.data(), v.size(), s));
     RB_CUDA(cudaStreamSynchronize(s));
     *dst = p;
+  } else if (op->dtype == RB_DF64) {
+    // pairs (hi, lo) = (RN32(v), RN32(v - hi)); v - hi is exact in FP64
+    std::vector<float> f(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float hi = (float)v[i];
+      f[2 * i] = hi;
+      f[2 * i + 1] = (float)(v[i] - (double)hi);
+    }
+    float* p = nullptr;
+    RB_TRY(dalloc(op, &p, f.size()));
+    RB_TRY(upload(p, f.data(), f.size(), s));
+    RB_CUDA(cudaStreamSynchronize(s));
+    *dst = p;
   } else {
     std::vector<float> f(v.size());
     for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];  // round to nearest even
@@ -215,7 +228,11 @@ extern "C" rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_d
   clear_error();
   RB_REQUIRE(csr && out, "rb_operator_create: null descriptor or output");
   *out = nullptr;
-  RB_REQUIRE(dtype == RB_F64 || dtype == RB_F32, "rb_operator_create: unknown dtype %d", (int)dtype);
+  RB_REQUIRE(dtype == RB_F64 || dtype == RB_F32 || dtype == RB_DF64, "rb_operator_create: unknown dtype %d",
+             (int)dtype);
+  RB_REQUIRE(dtype != RB_DF64 || format != RB_SELL, "rb_operator_create: RB_DF64 takes the CSR layout only");
+  RB_REQUIRE(dtype != RB_DF64 || !block || block->extruded_nz == 0,
+             "rb_operator_create: RB_DF64 operators cannot be extruded");
   RB_REQUIRE(format == RB_CSR || format == RB_SELL || format == RB_AUTO, "rb_operator_create: unknown format %d",
              (int)format);
   RB_REQUIRE(csr->n_rows >= 0 && csr->n_cols >= 0 && csr->nnz >= 0, "rb_operator_create: negative size");
@@ -253,6 +270,8 @@ extern "C" rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_d
     RB_REQUIRE(ci[p] >= 0 && ci[p] < csr->n_cols, "rb_operator_create: col_idx[%lld] = %d outside [0, %d)",
                (long long)p, ci[p], csr->n_cols);
     RB_REQUIRE(std::isfinite(va[p]), "rb_operator_create: vals[%lld] is not finite", (long long)p);
+    RB_REQUIRE(dtype != RB_DF64 || std::fabs(va[p]) <= 3.4028234663852886e38,
+               "rb_operator_create: vals[%lld] = %g outside the FP32 range of RB_DF64 pairs", (long long)p, va[p]);
   }
   // Extruded operator: the spanwise weights are checked, and dz and the -2 w_i of the periodic
   // second difference are folded into the library's copy of the values (dz a_ij off the

@@ -24,17 +24,20 @@ rb_status spmm_launch_f32(const rb_op* op, const SpmmSched& sc, const void* X, i
                           int k, const double* cs, cudaStream_t s);
 rb_status stencil_spmm_launch(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy,
                               int k, const double* cs, cudaStream_t s);
+rb_status spmm_launch_df(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                         int k, const double* cs, cudaStream_t s);
 
 namespace {
 
 bool sched_valid(const rb_op* op, const SpmmSched& sc, int k, int64_t ldx, int64_t ldy, const void* X,
                  const void* Y) {
-  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  const int eb = op->dtype == RB_F32 ? 4 : 8;
   if (sc.vec < 1 || sc.vec > 4 || !vec_ok(eb, sc.vec, k, ldx, ldy, X, Y)) return false;
   if (sc.kp != next_pow2(k / sc.vec) || sc.kp > 32) return false;
   if (sc.kp * sc.lpr > 32) return false;
   if ((op->format == RB_SELL || op->format == RB_STENCIL) && (sc.lpr != 1 || sc.stage)) return false;
   if (sc.stage == 2 && sc.lpr != 1) return false;
+  if (op->dtype == RB_DF64 && sc.stage) return false;  // double-float: the direct kernel only
   if (op->ext_nz > 0 && sc.vec == 3) return false;  // the spanwise epilogue takes widths dividing Nz only
   if (op->ext_nz > 0 && (op->ext_nz % sc.vec)) return false;
   return true;
@@ -53,7 +56,7 @@ std::vector<int> vec_candidates(int eb, int k) {
 }  // namespace
 
 SpmmSched default_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
-  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  const int eb = op->dtype == RB_F32 ? 4 : 8;
   SpmmSched sc;
   sc.lpr = 1;
   sc.stage = 0;
@@ -84,6 +87,7 @@ rb_status spmm_launch(const rb_op* op, const SpmmSched& sc, const void* X, int64
                       const double* cs, cudaStream_t s) {
   if (op->format == RB_STENCIL) return stencil_spmm_launch(op, sc, X, ldx, Y, ldy, k, cs, s);
   if (op->dtype == RB_F64) return spmm_launch_f64(op, sc, X, ldx, Y, ldy, k, cs, s);
+  if (op->dtype == RB_DF64) return spmm_launch_df(op, sc, X, ldx, Y, ldy, k, cs, s);
   return spmm_launch_f32(op, sc, X, ldx, Y, ldy, k, cs, s);
 }
 
@@ -95,7 +99,7 @@ rb_status spmm_validate(const rb_op* op, const void* X, int64_t ldx, const void*
   RB_REQUIRE((op->n_cols == 0 || X) && (op->n_rows == 0 || Y), "spmm: null X or Y");
   RB_REQUIRE(op->ext_nz == 0 || k == op->ext_nz, "spmm: extruded operator needs k == extruded_nz (%d), got %d",
              op->ext_nz, k);
-  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  const int eb = op->dtype == RB_F32 ? 4 : 8;
   RB_REQUIRE((uintptr_t)X % eb == 0 && (uintptr_t)Y % eb == 0, "spmm: X or Y not aligned to the element size");
   const SpmmSched sc = default_sched(op, k, ldx, ldy, X, Y);
   if (!sched_valid(op, sc, k, ldx, ldy, X, Y)) {
@@ -119,7 +123,7 @@ SpmmSched pick_sched(const rb_op* op, int k, int64_t ldx, int64_t ldy, const voi
 std::vector<SpmmSched> tune_candidates(const rb_op* op, int k, int64_t ldx, int64_t ldy, const void* X,
                                        const void* Y) {
   std::vector<SpmmSched> cands;
-  const int eb = op->dtype == RB_F64 ? 8 : 4;
+  const int eb = op->dtype == RB_F32 ? 4 : 8;
   for (int vec : vec_candidates(eb, k)) {
     for (int lpr = 1; lpr <= 8; lpr <<= 1) {
       if (lpr > 1 && op->avg_row_len < 2.0 * lpr) continue;  // lanes would idle on short rows
@@ -214,6 +218,7 @@ extern "C" rb_status rb_set_spmm_schedule(rb_op_t A, int32_t k, const rb_spmm_sc
   RB_REQUIRE(!(A->format == RB_STENCIL && (sc.lpr != 1 || sc.stage)),
              "rb_set_spmm_schedule: a stencil operator takes lpr 1, stage 0");
   RB_REQUIRE(!(sc.stage == 2 && sc.lpr != 1), "rb_set_spmm_schedule: the TMA pipeline takes lpr 1");
+  RB_REQUIRE(!(A->dtype == RB_DF64 && sc.stage), "rb_set_spmm_schedule: a double-float operator takes stage 0");
   RB_REQUIRE(!(A->ext_nz > 0 && (sc.vec == 3 || A->ext_nz % sc.vec)), "rb_set_spmm_schedule: vec must divide Nz");
   A->tuned[k] = sc;
   return RB_OK;

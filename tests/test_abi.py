@@ -173,3 +173,35 @@ def test_galerkin_validation_without_gpu(lib):
     lds = (C.c_int64 * 1)(3)
     assert lib.rb_galerkin_guess(None, 3, 1, ptrs, lds, None, 3, None, 3, None, None, 0, None) == rb.RB_EINVAL
     assert b"null operator" in lib.rb_last_error()
+
+
+def test_double_float_validation_without_gpu(lib):
+    """RB_DF64 operators: CSR only, not extruded, values inside FP32's range; the split and join
+    calls check their blocks (host arrays: every refusal comes before device work)."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+
+    h = C.c_void_p()
+    rp = (C.c_int32 * 3)(0, 2, 3)
+    ci = (C.c_int32 * 3)(0, 1, 0)
+    va = (C.c_double * 3)(2.0, -1.0, 1e39)
+    csr = rb.CsrDesc(2, 2, 3, C.addressof(rp), C.addressof(ci), C.addressof(va), 0)
+    assert lib.rb_operator_create(C.byref(csr), None, rb.RB_DF64, rb.RB_SELL, None, C.byref(h)) == rb.RB_EINVAL
+    assert b"CSR" in lib.rb_last_error()
+    zw = (C.c_double * 2)(0.5, 0.5)
+    blk = rb.BlockDesc(3, 3, C.addressof(zw), 0.1)
+    assert lib.rb_operator_create(C.byref(csr), C.byref(blk), rb.RB_DF64, rb.RB_CSR, None, C.byref(h)) == rb.RB_EINVAL
+    assert b"extruded" in lib.rb_last_error()
+    assert lib.rb_operator_create(C.byref(csr), None, rb.RB_DF64, rb.RB_CSR, None, C.byref(h)) == rb.RB_EINVAL
+    assert b"FP32 range" in lib.rb_last_error()
+    assert lib.rb_operator_create(C.byref(csr), None, 3, rb.RB_CSR, None, C.byref(h)) == rb.RB_EINVAL
+    buf = (C.c_double * 64)()
+    a = C.addressof(buf)
+    assert lib.rb_df64_split(4, 0, a, 1, a + 256, 1, None) == rb.RB_EINVAL  # k = 0
+    assert lib.rb_df64_split(4, 2, a, 1, a + 256, 2, None) == rb.RB_EINVAL  # ldx < k
+    assert lib.rb_df64_split(4, 2, a, 2, a + 8, 2, None) == rb.RB_EINVAL  # overlapping blocks
+    assert b"overlap" in lib.rb_last_error()
+    assert lib.rb_df64_join(4, 2, a + 4, 2, a + 256, 2, None) == rb.RB_EINVAL  # misaligned
+    assert lib.rb_df64_join(4, 2, None, 2, a, 2, None) == rb.RB_EINVAL
+    assert lib.rb_df64_split(0, 2, None, 2, None, 2, None) == rb.RB_OK  # nothing to do
