@@ -814,7 +814,42 @@ def e2e(args, torch, step_items, stream, dev, flops_step):
         ts.append(time.perf_counter() - t)
     ms = statistics.median(ts) * 1e3
     return {"value": flops_step / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "host_link": host_link(torch, dev)}
+
+
+def host_link(torch, dev, mb=256):
+    """The host link's copy rates with pinned buffers of `mb` MB: H2D alone, D2H alone, and both
+    at once on two streams (the ceiling of the end-to-end step, whose copies are of this kind)."""
+    n = mb * 2 ** 20 // 8
+    h_in = torch.empty(n, dtype=torch.float64, pin_memory=True).fill_(1.0)
+    h_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    d_in = torch.empty(n, dtype=torch.float64, device=dev)
+    d_out = torch.ones(n, dtype=torch.float64, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+        return statistics.median(ts)
+
+    def both():
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+
+    by = n * 8
+    t_h2d = timed(lambda: d_in.copy_(h_in, non_blocking=True))
+    t_d2h = timed(lambda: h_out.copy_(d_out, non_blocking=True))
+    t_both = timed(both)
+    return {"bytes": by, "h2d_gbs": by / t_h2d / 1e9, "d2h_gbs": by / t_d2h / 1e9,
+            "both_gbs": 2 * by / t_both / 1e9}
 
 
 def _blocks_for(torch, rb, op, dt, k, dev):
@@ -1267,6 +1302,9 @@ def headline(out, detail_path):
     ks = out.get("ksweep")
     if ks:
         s["ksweep_frac_hbm_csr"] = {f"{r['dtype']}-k{r['k']}": round(r["frac_hbm"], 3) for r in ks if r["format"] == "csr"}
+    hl = (out.get("e2e") or {}).get("host_link")
+    if hl:
+        s["host_link_gbs"] = {"h2d": hl["h2d_gbs"], "d2h": hl["d2h_gbs"], "both": hl["both_gbs"]}
     sv = out.get("step_variants")
     if sv:
         s["df64_vs_f64_us"] = {r["op"]: [r["f64_us"], r["df64_us"]] for r in sv["df64_vs_f64"]}

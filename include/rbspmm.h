@@ -505,6 +505,61 @@ rb_status rb_mg_solve(rb_mg_t mg, const rb_cg_params* params, const double* B, i
                       int32_t k, rb_cg_report* report, rb_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * The projection step on m stacked flow states (Sec. 3, Eq. (ns) and Eq. (ns-nrhs): every
+ * operator acts as I_m (x) A, one SpMM over the states' columns; Sec. 4: Heun's third-order
+ * Runge-Kutta scheme, c = (0, 1/3, 2/3), a_21 = 1/3, a_32 = 2/3, b = (1/4, 0, 3/4), with a
+ * projection at every stage), sequenced in the library on rb_spmm, rb_axpy, rb_axty and the
+ * Poisson solvers.  With cell velocities u_c, face velocities u_s, cell volume V:
+ *   derivative  F = (nu L u_c - M (u_s * Gamma u_c)) / V, Gamma the cell-to-face
+ *               interpolator (RB_FVM_INTERP_C2S), * the element-wise product (rb_axty);
+ *   projection  u~_s = the face-normal component of Gamma u~ on each face, -L p =
+ *               -M u~_s / (c dt) solved to zero mean (the previous solve of the same stage is
+ *               the initial guess), u_s = u~_s - c dt G p, u_c = u~ - c dt G_c p with G_c p's
+ *               component d = Gamma^T (G p on the faces of direction d).
+ * Layout (DEVICE float64): u_c n x 3 m (ldu >= 3 m), column i m + s = component i of state
+ * s; u_s n_faces x m (lds >= m), n_faces = 3 n, numbered as for rb_fvm_assemble (the x faces
+ * first, then y, then z; on a periodic axis n faces per direction).  The grid must be uniform
+ * and periodic along every axis (one cell volume; Gamma^T the face-to-cell interpolator).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct rb_projection* rb_projection_t;
+typedef enum { RB_PROJ_JACOBI = 0, RB_PROJ_MG = 1 } rb_proj_solver;
+
+typedef struct {
+  int32_t m;          /* stacked states, 3 m <= RB_MAX_K */
+  double nu;          /* kinematic viscosity (>= 0) */
+  double dt;          /* time step (> 0) */
+  int32_t solver;     /* RB_PROJ_JACOBI: rb_cg_solve (mixed 0, 1 or 2); RB_PROJ_MG: rb_mg_solve
+                         on the grid's multigrid hierarchy (mixed 0 or nonzero) */
+  rb_cg_params cg;    /* the pressure solves' parameters; project_mean must be 1 */
+} rb_projection_params;
+
+typedef struct {
+  int32_t iters[3];   /* the stages' pressure solves: CG iterations, the largest over the states */
+  int32_t status;     /* the worst solve status (RB_OK, RB_ENOCONV, RB_EBREAKDOWN) */
+  double poisson_ms;  /* wall time of the solves */
+} rb_projection_report;
+
+/* Builds the step's operators (M, G, L, Gamma, Gamma^T, the Poisson matrix -L in FP64 and, for
+ * the Jacobi refinement, FP32; or the multigrid hierarchy), work vectors and column scales
+ * for `grid` (as for rb_fvm_assemble, DEVICE nodes).  Allocates (the library owns the memory
+ * until rb_projection_destroy); synchronises `stream`.  RB_EINVAL for a non-uniform or
+ * non-periodic grid, axes below 3 cells, invalid parameters. */
+rb_status rb_projection_create(const rb_grid_desc* grid, const rb_projection_params* params, rb_stream_t stream,
+                               rb_projection_t* out);
+rb_status rb_projection_destroy(rb_projection_t p);
+/* One Heun RK3 step of the m states; u_c and u_s are updated in place.  Synchronises `stream`
+ * (the solves read their convergence on the host).  Returns the worst solve status; report
+ * may be NULL.  Calls on one handle must not overlap. */
+rb_status rb_projection_step(rb_projection_t p, double* u_c, int64_t ldu, double* u_s, int64_t lds,
+                             rb_projection_report* report, rb_stream_t stream);
+/* One projection with time cdt (> 0): u_c becomes divergence-free-consistent cell velocities
+ * in place and u_s receives the projected face velocities (the mapping of inline mesh
+ * refinement, Sec. 3.3, projects the prolonged velocities this way).  Uses the third stage's
+ * pressure as the initial guess; report->iters[0] holds the solve's iterations. */
+rb_status rb_projection_project(rb_projection_t p, double cdt, double* u_c, int64_t ldu, double* u_s, int64_t lds,
+                                rb_projection_report* report, rb_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * Galerkin initial guess: the best combination of candidate starting vectors.
  *
  * Not from the paper, whose solver starts each step from the previous pressure.  For k

@@ -40,6 +40,7 @@ SYMBOLS = ["rb_last_error", "rb_version", "rb_fma_peak", "rb_fvm_csr_size", "rb_
            "rb_guess_destroy", "rb_guess_init_params", "rb_guess_set_params", "rb_guess_get_params", "rb_guess_get_grad", "rb_guess_predict",
            "rb_guess_loss_grad", "rb_guess_adam_step", "rb_guess_read_activation", "rb_guess_select",
            "rb_mg_create", "rb_mg_destroy", "rb_mg_info", "rb_mg_vcycle", "rb_mg_solve",
+           "rb_projection_create", "rb_projection_destroy", "rb_projection_step", "rb_projection_project",
            "rb_galerkin_workspace_bytes", "rb_galerkin_guess"]
 
 
@@ -109,6 +110,17 @@ class CgReport(C.Structure):
                 ("host_syncs", C.c_int32), ("ms", C.c_double)]
 
 
+RB_PROJ_JACOBI, RB_PROJ_MG = 0, 1
+
+
+class ProjectionParams(C.Structure):
+    _fields_ = [("m", C.c_int32), ("nu", C.c_double), ("dt", C.c_double), ("solver", C.c_int32), ("cg", CgParams)]
+
+
+class ProjectionReport(C.Structure):
+    _fields_ = [("iters", C.c_int32 * 3), ("status", C.c_int32), ("poisson_ms", C.c_double)]
+
+
 _lib = None
 
 
@@ -176,6 +188,10 @@ def lib():
         "rb_mg_info": (C.c_int, [vp, C.POINTER(MgInfo)]),
         "rb_mg_vcycle": (C.c_int, [vp, i32, C.c_int, vp, i64, vp, i64, i32, vp]),
         "rb_mg_solve": (C.c_int, [vp, C.POINTER(CgParams), vp, i64, vp, i64, i32, C.POINTER(CgReport), vp]),
+        "rb_projection_create": (C.c_int, [C.POINTER(GridDesc), C.POINTER(ProjectionParams), vp, C.POINTER(vp)]),
+        "rb_projection_destroy": (C.c_int, [vp]),
+        "rb_projection_step": (C.c_int, [vp, vp, i64, vp, i64, C.POINTER(ProjectionReport), vp]),
+        "rb_projection_project": (C.c_int, [vp, C.c_double, vp, i64, vp, i64, C.POINTER(ProjectionReport), vp]),
         "rb_galerkin_workspace_bytes": (sz, [i64, i32, i32]),
         "rb_galerkin_guess": (C.c_int, [vp, i32, i32, C.POINTER(vp), C.POINTER(i64), vp, i64, vp, i64, vp, vp, sz, vp]),
     }

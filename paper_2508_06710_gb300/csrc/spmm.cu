@@ -107,9 +107,9 @@ rb_status spmm_validate(const rb_op* op, const void* X, int64_t ldx, const void*
               "8- or 16-byte aligned rows)", k);
     return RB_EUNSUPPORTED;
   }
-  // X and Y must not overlap
-  const uintptr_t xb = (uintptr_t)X, xe = xb + (uintptr_t)((int64_t)op->n_cols * ldx * eb);
-  const uintptr_t yb = (uintptr_t)Y, ye = yb + (uintptr_t)((int64_t)op->n_rows * ldy * eb);
+  // X and Y must not overlap (the bytes each spans: its last row ends after k columns)
+  const uintptr_t xb = (uintptr_t)X, xe = xb + (uintptr_t)(((int64_t)(op->n_cols - 1) * ldx + k) * eb);
+  const uintptr_t yb = (uintptr_t)Y, ye = yb + (uintptr_t)(((int64_t)(op->n_rows - 1) * ldy + k) * eb);
   RB_REQUIRE(op->n_rows == 0 || op->n_cols == 0 || xe <= yb || ye <= xb, "spmm: X and Y overlap");
   return RB_OK;
 }

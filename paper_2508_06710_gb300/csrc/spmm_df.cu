@@ -222,8 +222,8 @@ rb_status check_pair_block(const char* fn, int64_t n, int k, const void* A, int6
   RB_REQUIRE(lda >= k && ldb >= k, "%s: leading dimensions smaller than k", fn);
   RB_REQUIRE(n == 0 || (A && B), "%s: null block", fn);
   RB_REQUIRE((uintptr_t)A % 8 == 0 && (uintptr_t)B % 8 == 0, "%s: blocks not 8-byte aligned", fn);
-  const uintptr_t ab = (uintptr_t)A, ae = ab + (uintptr_t)(n * lda * 8);
-  const uintptr_t bb = (uintptr_t)B, be = bb + (uintptr_t)(n * ldb * 8);
+  const uintptr_t ab = (uintptr_t)A, ae = ab + (uintptr_t)(((n - 1) * lda + k) * 8);
+  const uintptr_t bb = (uintptr_t)B, be = bb + (uintptr_t)(((n - 1) * ldb + k) * 8);
   RB_REQUIRE(n == 0 || ae <= bb || be <= ab, "%s: the blocks overlap", fn);
   return RB_OK;
 }

@@ -205,3 +205,37 @@ def test_double_float_validation_without_gpu(lib):
     assert lib.rb_df64_join(4, 2, a + 4, 2, a + 256, 2, None) == rb.RB_EINVAL  # misaligned
     assert lib.rb_df64_join(4, 2, None, 2, a, 2, None) == rb.RB_EINVAL
     assert lib.rb_df64_split(0, 2, None, 2, None, 2, None) == rb.RB_OK  # nothing to do
+
+
+def test_projection_validation_without_gpu(lib):
+    """rb_projection_create and rb_projection_step refuse bad arguments before device work."""
+    import ctypes as C
+
+    import paper_2508_06710_gb300 as rb
+
+    g = rb.GridDesc()
+    for d in range(3):
+        g.n[d] = 8
+        g.periodic[d] = 1
+    h = C.c_void_p()
+    good = rb.ProjectionParams(2, 0.01, 0.01, rb.RB_PROJ_MG, rb.mg_params())
+
+    def create(prm, grid=g):
+        return lib.rb_projection_create(C.byref(grid), C.byref(prm), None, C.byref(h))
+
+    for bad in (rb.ProjectionParams(0, 0.01, 0.01, 0, rb.mg_params()),     # m < 1
+                rb.ProjectionParams(22, 0.01, 0.01, 0, rb.mg_params()),    # 3 m > RB_MAX_K
+                rb.ProjectionParams(2, 0.01, 0.0, 0, rb.mg_params()),      # dt = 0
+                rb.ProjectionParams(2, -1.0, 0.01, 0, rb.mg_params()),     # nu < 0
+                rb.ProjectionParams(2, 0.01, 0.01, 7, rb.mg_params()),     # unknown solver
+                rb.ProjectionParams(2, 0.01, 0.01, 0, rb.mg_params(project_mean=False))):
+        assert create(bad) == rb.RB_EINVAL
+    walled = rb.GridDesc()
+    for d in range(3):
+        walled.n[d] = 8
+        walled.periodic[d] = 1 if d < 2 else 0
+    assert create(good, walled) == rb.RB_EINVAL and b"periodic" in lib.rb_last_error()
+    assert lib.rb_projection_create(None, C.byref(good), None, C.byref(h)) == rb.RB_EINVAL
+    rep = rb.ProjectionReport()
+    assert lib.rb_projection_step(None, None, 6, None, 2, C.byref(rep), None) == rb.RB_EINVAL
+    assert lib.rb_projection_destroy(None) == rb.RB_OK

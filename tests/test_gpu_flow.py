@@ -78,13 +78,17 @@ def test_projection_step_full_size(rb):
     stepper = ProjectionStep(torch, nodes, 2, nu, dt, mixed=2)
     ud = to_dev(u0)
     usd = torch.zeros((3 * g.n_cells, 2), dtype=torch.float64, device="cuda")
+    per = [True, True, True]
+    I = rb.Operator(*rb.fvm_assemble(nodes, per, rb.RB_FVM_INTERP_C2S), k_max=6)
+    M = rb.Operator(*rb.fvm_assemble(nodes, per, rb.RB_FVM_DIVERGENCE), k_max=2)
     # divergence of the face-normal interpolation of u0, before any projection
-    stepper.I.spmm(ud, stepper.Y)
-    us0 = torch.cat([stepper.Y[d * g.n_cells:(d + 1) * g.n_cells, 2 * d:2 * d + 2] for d in range(3)])
-    d0 = stepper.M.spmm(us0.contiguous()).abs().max().item()
+    Y = I.spmm(ud)
+    us0 = torch.cat([Y[d * g.n_cells:(d + 1) * g.n_cells, 2 * d:2 * d + 2] for d in range(3)])
+    d0 = M.spmm(us0.contiguous()).abs().max().item()
     stepper.step(ud, usd)
     stepper.step(ud, usd)
-    div = stepper.M.spmm(usd).abs().max().item()
+    assert len(stepper.iters) == 6 and stepper.poisson_ms > 0.0
+    div = M.spmm(usd).abs().max().item()
     assert div <= 1e-6 * d0, (div, d0)  # ||r||_2 <= 1e-10 ||b||_2 bounds the max-norm by ~1.5e-7 ||b||_max
     single = ProjectionStep(torch, nodes, 1, nu, dt, mixed=2)
     u1 = to_dev(u0[:, [1, 3, 5]])
@@ -128,3 +132,43 @@ def test_refined_run_matches_oracle(rb, mixed):
     ur_map, usr_map = flow.map_to_fine(fine, u, dtf)
     assert np.abs(uc_map.cpu().numpy() - ur_map).max() <= 1e-8 * scale
     assert np.abs(us_map.cpu().numpy() - usr_map).max() <= 1e-8 * scale
+
+
+def test_projection_abi_strided_and_refusals(rb):
+    """rb_projection_step on u_c and u_s held inside wider blocks (ld > 3 m, ld > m) gives the
+    contiguous call's result and leaves the other columns alone; a non-uniform or walled grid,
+    a wrong shape and overlapping blocks are refused."""
+    from paper_2508_06710_gb300.flow_step import ProjectionStep
+
+    g = _box((8, 8, 16), (2 * math.pi, 2.0, 3.0))
+    nodes, _ = rb.grid_nodes(g)
+    m = 2
+    with pytest.raises(rb.RbError) as e:  # 6 and 10 cells do not halve: no multigrid hierarchy
+        ProjectionStep(torch, rb.grid_nodes(_box((8, 6, 10), (1.0, 1.0, 1.0)))[0], m, 0.02, 0.01, solver="mg")
+    assert e.value.status == rb.RB_EINVAL and "coarsen" in str(e.value)
+    u = flow.taylor_green(g, m, amp=[1.0, 0.5]) + 0.1 * W.normal((g.n_cells, 3 * m), 1950)
+    us = W.normal((fvm.n_faces(g), m), 1951)
+    a = ProjectionStep(torch, nodes, m, 0.02, 0.01, mixed=2, solver="mg")
+    b = ProjectionStep(torch, nodes, m, 0.02, 0.01, mixed=2, solver="mg")
+    ud, usd = to_dev(u), to_dev(us)
+    uw = torch.full((g.n_cells, 3 * m + 3), 9.0, dtype=torch.float64, device="cuda")
+    usw = torch.full((fvm.n_faces(g), m + 1), 9.0, dtype=torch.float64, device="cuda")
+    uw[:, 1:1 + 3 * m] = ud
+    usw[:, :m] = usd
+    a.step(ud, usd)
+    b.step(uw[:, 1:1 + 3 * m], usw[:, :m])
+    assert torch.equal(uw[:, 1:1 + 3 * m], ud) and torch.equal(usw[:, :m], usd)
+    assert bool((uw[:, 0] == 9.0).all()) and bool((uw[:, 1 + 3 * m:] == 9.0).all()) and bool((usw[:, m] == 9.0).all())
+    with pytest.raises(ValueError):
+        a.step(ud[:, :3], usd)
+    walled = W.channel_grid(8, 8, 16)
+    wn, _ = rb.grid_nodes(walled)
+    with pytest.raises(rb.RbError) as e:
+        ProjectionStep(torch, wn, m, 0.02, 0.01)
+    assert e.value.status == rb.RB_EINVAL
+    import ctypes as C
+
+    rep = rb.ProjectionReport()
+    st = rb.lib().rb_projection_step(a.handle, C.c_void_p(ud.data_ptr()), 3 * m, C.c_void_p(ud.data_ptr() + 8), m,
+                                     C.byref(rep), None)
+    assert st == rb.RB_EINVAL and b"overlap" in rb.lib().rb_last_error()
