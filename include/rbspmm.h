@@ -443,7 +443,8 @@ typedef struct rb_mg* rb_mg_t;
 
 typedef struct {
   int32_t nu;         /* Jacobi sweeps before and after the coarse correction (1..16; 2) */
-  double omega;       /* Jacobi damping weight in (0, 1] (2/3) */
+  double omega;       /* Jacobi damping weight in (0, 1] (0.8: the smoothing analysis of damped
+                         Jacobi for the 2-D and 3-D Poisson stencils gives 4/5 and 6/7) */
   int32_t min_cells;  /* an axis is halved only if its half keeps >= min_cells cells (>= 2; 4) */
   int32_t flexible;   /* 1: flexible CG beta = -alpha (q . z_new) / (r . z)_old (Notay), robust
                          to an FP32 cycle; 0: beta = (r . z)_new / (r . z)_old (1) */

@@ -680,7 +680,7 @@ class Multigrid:
     """Geometric multigrid hierarchy of -L on a Cartesian grid (rb_mg_create): the V-cycle
     preconditioner and the multigrid-preconditioned CG solve of the pressure equation."""
 
-    def __init__(self, nodes, periodic, k_max=1, nu=2, omega=2.0 / 3.0, min_cells=4, flexible=True, matrix_free=True,
+    def __init__(self, nodes, periodic, k_max=1, nu=2, omega=0.8, min_cells=4, flexible=True, matrix_free=True,
                  smoother="line", stream=None):
         torch = _torch()
         self._nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]

@@ -1631,7 +1631,7 @@ extern "C" rb_status rb_mg_create(const rb_grid_desc* grid, int32_t k_max, const
   RB_REQUIRE(grid && out, "rb_mg_create: null argument");
   *out = nullptr;
   RB_REQUIRE(k_max >= 1 && k_max <= RB_MAX_K, "rb_mg_create: k_max %d outside [1, %d]", k_max, RB_MAX_K);
-  rb_mg_params prm{2, 2.0 / 3.0, 4, 1, 1, 1};
+  rb_mg_params prm{2, 0.8, 4, 1, 1, 1};
   if (params) prm = *params;
   RB_REQUIRE(prm.nu >= 1 && prm.nu <= 16, "rb_mg_create: nu = %d outside [1, 16]", prm.nu);
   RB_REQUIRE(prm.omega > 0.0 && prm.omega <= 1.0, "rb_mg_create: omega = %g outside (0, 1]", prm.omega);
