@@ -209,19 +209,27 @@ __device__ __forceinline__ void restrict_apply(const Transfer3<T>& tr, const T* 
     xt[c] = c < ncx ? tx.t[c] : 0;
     xw[c] = c < ncx ? tx.w[c] : T(0);
   }
+  // y positions four at a time (a coarse cell has at most 4 of them away from a wall): the
+  // gathers of four fine rows are in flight together, not one row's after another's
   for (int a = 0; a < ncz; ++a) {
     const T wa = tz.w[a];
     const int64_t za = (int64_t)ny * tz.t[a];
-    for (int b = 0; b < ncy; ++b) {
-      const T wab = wa * ty.w[b];
-      const T* base = Rf + (int64_t)nx * (ty.t[b] + za) * k + col0;
+    for (int b0 = 0; b0 < ncy; b0 += 4) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (c < ncx) {
-          const Vec<T, VEC> v = ldv<T, VEC>(base + (int64_t)xt[c] * k);
-          const T wt = wab * xw[c];
+      for (int bb = 0; bb < 4; ++bb) {
+        const int b = b0 + bb;
+        if (b < ncy) {
+          const T wab = wa * ty.w[b];
+          const T* base = Rf + (int64_t)nx * (ty.t[b] + za) * k + col0;
 #pragma unroll
-          for (int q = 0; q < VEC; ++q) acc[q] = fma(wt, v.v[q], acc[q]);
+          for (int c = 0; c < 8; ++c) {
+            if (c < ncx) {
+              const Vec<T, VEC> v = ldv<T, VEC>(base + (int64_t)xt[c] * k);
+              const T wt = wab * xw[c];
+#pragma unroll
+              for (int q = 0; q < VEC; ++q) acc[q] = fma(wt, v.v[q], acc[q]);
+            }
+          }
         }
       }
     }
