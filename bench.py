@@ -943,19 +943,17 @@ def step_variants(torch, rb, ops, g, dev, hbm):
 
 def k_sweep_stencil(torch, rb, g, dev, hbm):
     """The channel Laplacian as a matrix-free operator (rb_fvm_stencil_create: entries formed
-    from per-axis tables), k = 1 .. 32, FP64 and FP32 (tuned; spmm_ms: graph replays, inputs cycled past
-    the L2):
+    from per-axis tables), k = 1 .. 32, FP32, FP64 and double-float (tuned; spmm_ms: graph
+    replays, inputs cycled past the L2):
     algorithmic bytes are X read once and Y written, s k (n_r + n_c), the tables (a few KB)
     aside; beside each, the CSR kernel's time at the same k from `ksweep`."""
     nodes, per = rb.grid_nodes(g, dev)
     res = []
-    for dt in ("f32", "f64"):
+    for dt in ("f32", "f64", "df64"):
         op = rb.Operator.stencil(nodes, per, dtype=dt, k_max=32)
-        tdt = torch.float64 if dt == "f64" else torch.float32
-        s_b = 8 if dt == "f64" else 4
+        s_b = 4 if dt == "f32" else 8
         for k in W.ks_sweep():
-            X = torch.randn((op.n_cols, k), dtype=tdt, device=dev)
-            Y = torch.empty((op.n_rows, k), dtype=tdt, device=dev)
+            X, Y = _blocks_for(torch, rb, op, dt, k, dev)
             op.tune(X, Y)
             by = s_b * k * (op.n_rows + op.n_cols)
             ms = spmm_ms(torch, op, X, Y, by)

@@ -239,7 +239,9 @@ rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_desc* block,
  * and one inverse centre distance), so the operator is held as 2 (n_x + n_y + n_z) + 3 numbers
  * and an SpMM reads only X and writes only Y.  The coefficients are formed in `dtype`
  * arithmetic from the tables (FP32: the tables rounded to nearest, so entries can differ from
- * RNE(FP64 entries) by a few ulp).  The handle works with rb_spmm, rb_tune_spmm,
+ * RNE(FP64 entries) by a few ulp; RB_DF64: blocks of pairs, the entries factorised as
+ * V_ijk c_nb with V = w_x w_y w_z and per-axis tables c = ic / w formed in FP64 and split, the
+ * products and sums in double-float arithmetic).  The handle works with rb_spmm, rb_tune_spmm,
  * rb_operator_info/check/destroy and every call built on rb_spmm (e.g. rb_galerkin_guess); the
  * CG solves take CSR operators only.  grid as for rb_fvm_assemble (DEVICE nodes).  Allocates;
  * synchronises `stream`. */

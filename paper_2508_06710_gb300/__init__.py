@@ -394,7 +394,7 @@ class Operator:
         nodes = [n.to(dtype=torch.float64).contiguous() for n in nodes]
         g = _grid_desc(nodes, periodic)
         h = C.c_void_p()
-        _check(lib().rb_fvm_stencil_create(C.byref(g), float(scale), {"f64": RB_F64, "f32": RB_F32}[dtype],
+        _check(lib().rb_fvm_stencil_create(C.byref(g), float(scale), {"f64": RB_F64, "f32": RB_F32, "df64": RB_DF64}[dtype],
                                            int(k_max), _stream(stream), C.byref(h)), "rb_fvm_stencil_create")
         self = cls.__new__(cls)
         self.handle = h

@@ -225,8 +225,14 @@ rb_status launch_t(const rb_op* op, const SpmmSched& sc, const void* X, int64_t 
 
 }  // namespace
 
+rb_status stencil_df_launch(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                            int k, const double* cs, cudaStream_t s);
+rb_status stencil_df_tables(const rb_grid_desc* grid, double scale, double* const w64[3], double* const ic64[3],
+                            void* tab[3], int64_t* bytes, cudaStream_t s);
+
 rb_status stencil_spmm_launch(const rb_op* op, const SpmmSched& sc, const void* X, int64_t ldx, void* Y, int64_t ldy,
                               int k, const double* cs, cudaStream_t s) {
+  if (op->dtype == RB_DF64) return stencil_df_launch(op, sc, X, ldx, Y, ldy, k, cs, s);
   if (op->dtype == RB_F64) return launch_t<double>(op, sc, X, ldx, Y, ldy, k, cs, s);
   return launch_t<float>(op, sc, X, ldx, Y, ldy, k, cs, s);
 }
@@ -240,7 +246,8 @@ extern "C" rb_status rb_fvm_stencil_create(const rb_grid_desc* grid, double scal
   clear_error();
   RB_REQUIRE(grid && out, "rb_fvm_stencil_create: null argument");
   *out = nullptr;
-  RB_REQUIRE(dtype == RB_F64 || dtype == RB_F32, "rb_fvm_stencil_create: unknown dtype %d", (int)dtype);
+  RB_REQUIRE(dtype == RB_F64 || dtype == RB_F32 || dtype == RB_DF64, "rb_fvm_stencil_create: unknown dtype %d",
+             (int)dtype);
   RB_REQUIRE(k_max >= 1 && k_max <= RB_MAX_K, "rb_fvm_stencil_create: k_max %d outside [1, %d]", k_max, RB_MAX_K);
   RB_REQUIRE(std::isfinite(scale), "rb_fvm_stencil_create: scale is not finite");
   for (int d = 0; d < 3; ++d) RB_REQUIRE(grid->nodes[d] != nullptr, "rb_fvm_stencil_create: null nodes[%d]", d);
@@ -291,9 +298,17 @@ extern "C" rb_status rb_fvm_stencil_create(const rb_grid_desc* grid, double scal
     if (e != cudaSuccess) st = cuda_fail(e, "stencil operator tables", __FILE__, __LINE__);
     op->has_diag = 1;
   }
-  // keep the tables of the operator's type
+  // keep the tables of the operator's type (double-float: the factorised pair tables)
+  if (st == RB_OK && dtype == RB_DF64) {
+    void* tab[3] = {nullptr, nullptr, nullptr};
+    st = stencil_df_tables(grid, scale, w64, ic64, tab, &op->device_bytes, s);
+    for (int d = 0; d < 3; ++d) op->st_w[d] = tab[d];
+  }
   for (int d = 0; d < 3; ++d) {
-    if (dtype == RB_F64) {
+    if (dtype == RB_DF64) {
+      for (void* q : {(void*)w64[d], (void*)ic64[d], (void*)w32[d], (void*)ic32[d]})
+        if (q) cudaFree(q);
+    } else if (dtype == RB_F64) {
       op->st_w[d] = w64[d], op->st_ic[d] = ic64[d];
       if (w32[d]) cudaFree(w32[d]);
       if (ic32[d]) cudaFree(ic32[d]);

@@ -220,3 +220,67 @@ def test_refusals(rb):
     op64 = rb.Operator.from_scipy(A, dtype="f64", k_max=2)
     with pytest.raises(ValueError):  # nor the other way round
         op64.spmm(_df_block(rb, np.ones((100, 2))))
+
+
+def _stencil_df(rb, g, k, scale=1.0):
+    nodes, per = rb.grid_nodes(g)
+    return rb.Operator.stencil(nodes, per, scale=scale, dtype="df64", k_max=k)
+
+
+@pytest.mark.parametrize("name", ["channel-24x16x12", "periodic-10", "rbc-8x8x16", "channel-13x6x5"])
+@pytest.mark.parametrize("k", [1, 3, 4, 8])
+def test_stencil_df_at_fp64_bar(rb, name, k):
+    """The matrix-free Laplacian in double-float arithmetic (factorised entries V c): within
+    1e-12 (|L||X|) of the oracle's assembled FP64 Laplacian, scale -1 included (A = -L); odd
+    and even axes, walls and periodic axes."""
+    g = {"channel-24x16x12": W.channel_grid(24, 16, 12, gamma=1.5), "periodic-10": W.unit_periodic_grid(10),
+         "rbc-8x8x16": W.Grid((W.uniform_axis(8), W.uniform_axis(8), W.tanh_axis(16, 1.4, 0.0, 1.0))),
+         "channel-13x6x5": W.channel_grid(13, 6, 5, gamma=2.0)}[name]
+    L = fvm.laplacian_direct(g).tocsr()
+    X = W.normal((g.n_cells, k), 800 + k)
+    for scale in (1.0, -1.0):
+        op = _stencil_df(rb, g, k, scale)
+        Yd = op.spmm(_df_block(rb, X))
+        Y = rb.df_join(Yd).cpu().numpy()
+        _check((scale * L).tocsr(), X, Y, tol=1e-12)
+
+
+def test_stencil_df_scaled_strided(rb):
+    g = W.channel_grid(16, 12, 8, gamma=1.5)
+    L = fvm.laplacian_direct(g).tocsr()
+    k = 3
+    X = W.normal((g.n_cells, k), 830)
+    c = np.array([0.5, -1.0 / 3.0, 2.5])
+    op = _stencil_df(rb, g, k)
+    Xd = _df_block(rb, X, ld_pad=2)
+    Yw = torch.full((g.n_cells, k + 1, 2), float("nan"), dtype=torch.float32, device="cuda")
+    op.spmm(Xd, Yw[:, :k], c=to_dev(c))
+    assert torch.isnan(Yw[:, k]).all()
+    Y = rb.df_join(Yw[:, :k]).cpu().numpy()
+    _check(L, X, Y, c=c, tol=1e-12)
+
+
+def test_stencil_df_channel_full_size_k3(rb):
+    """The 192 x 128 x 96 channel, k = 3: the whole product against the native FP64 CSR SpMM
+    within 2e-12 (|L||X|) and sampled rows against the oracle within 1e-12."""
+    g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+    nodes, per = rb.grid_nodes(g)
+    rp, ci, va, nc = rb.fvm_assemble(nodes, per, rb.RB_FVM_LAPLACIAN)
+    k = 3
+    X = W.normal((nc, k), 2026)
+    Xd64 = to_dev(X)
+    op = rb.Operator.stencil(nodes, per, dtype="df64", k_max=k)
+    Xdf = rb.df_split(Xd64)
+    Ydf = torch.empty((op.n_rows, k, 2), dtype=torch.float32, device="cuda")
+    op.tune(Xdf, Ydf)
+    op.spmm(Xdf, Ydf)
+    Y = rb.df_join(Ydf)
+    op64 = rb.Operator(rp, ci, va, nc, dtype="f64", k_max=k)
+    Y64 = op64.spmm(Xd64)
+    bound = rb.Operator(rp, ci, va.abs(), nc, dtype="f64", k_max=k).spmm(Xd64.abs())
+    rel = ((Y - Y64).abs() / bound.clamp_min(1e-300)).max().item()
+    assert rel <= 2e-12, rel
+    Lc = fvm.laplacian_direct(g).tocsr()
+    rows = np.random.default_rng(6).choice(Lc.shape[0], 4000, replace=False)
+    Ls = Lc[rows]
+    assert np.all(np.abs(Y.cpu().numpy()[rows] - Ls @ X) <= 1e-12 * (abs(Ls) @ np.abs(X)))
