@@ -1306,10 +1306,9 @@ def headline(out, detail_path):
     sv = out.get("step_variants")
     if sv:
         s["df64_vs_f64_us"] = {r["op"]: [r["f64_us"], r["df64_us"]] for r in sv["df64_vs_f64"]}
-        s["families_us"] = {r["op"]: [r["direct_us"], r["staged_us"], r["tma_us"]] for r in sv["schedule_families"]}
     kst = out.get("ksweep_stencil")
-    if kst:
-        s["ksweep_stencil_gflops"] = {f"{r['dtype']}-k{r['k']}": r["gflops"] for r in kst}
+    if kst:  # the matrix-free sweep at k = 1, 3 and 32
+        s["ksweep_stencil_gflops"] = {f"{r['dtype']}-k{r['k']}": round(r["gflops"]) for r in kst if r["k"] in (1, 3, 32)}
     h["summary"] = _round(s)
     h["detail"] = os.path.relpath(detail_path, ROOT) if os.path.isabs(detail_path) else detail_path
     return h
