@@ -1387,6 +1387,20 @@ def profile_run(args):
         torch.cuda.synchronize()
         print(json.dumps({"profile": args.profile, "ok": True}))
         return
+    if args.profile == "df":
+        # the channel Laplacian in double-float arithmetic, k = 3: three CSR SpMMs, then three
+        # matrix-free ones, on seeded blocks
+        g = W.channel_grid(*W.CHANNEL_SHAPE, gamma=1.5)
+        nodes, per = rb.grid_nodes(g, dev)
+        rp, ci, va, nc = rb.fvm_assemble(nodes, per, rb.RB_FVM_LAPLACIAN)
+        X = rb.df_split(torch.as_tensor(W.normal((g.n_cells, 3), 2007), device=dev))
+        Y = torch.empty_like(X)
+        for op in (rb.Operator(rp, ci, va, nc, dtype="df64", k_max=3), rb.Operator.stencil(nodes, per, dtype="df64", k_max=3)):
+            for _ in range(3):
+                op.spmm(X, Y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "ok": True}))
+        return
     if args.profile == "assembly":
         # the device builds of the 27p Laplacian (96^3 periodic), and of P, R and P^T on the channel
         n = 96
@@ -1478,7 +1492,7 @@ def main():
                     help="NVTX ranges around the timed region ('timed_step') and each SpMM (its label), for ncu filters")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per launch of the dominant kernel, if captured for this build")
-    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess", "spmm", "mg", "assembly", "projection", "stencil"],
+    ap.add_argument("--profile", default=None, choices=["step", "cg", "guess", "spmm", "mg", "assembly", "projection", "stencil", "df"],
                     help="short run for an ncu capture: 'step' = the timed step only, 'cg' = a 20-iteration "
                          "FP64 and FP32-refinement Poisson solve (k = 1 and 3), 'guess' = one forward and one "
                          "training pass of the learned-guess network at 128^3 (NVTX 'predict', 'loss_grad'), "
@@ -1487,7 +1501,8 @@ def main():
                          "'mg' = one multigrid solve on the channel (k = 3, NVTX 'mg_solve'), 'assembly' = the 13p / "
                          "27p builds at 96^3 and P, R, P^T on the channel, 'projection' = two projection steps of "
                          "two states at 128^3 (NVTX 'projection_step' around the second), 'stencil' = the "
-                         "matrix-free channel Laplacian in FP32, three SpMMs with k = 1 then k = 3")
+                         "matrix-free channel Laplacian in FP32, three SpMMs with k = 1 then k = 3, 'df' = the channel "
+                         "Laplacian in double-float arithmetic, k = 3, three CSR then three matrix-free SpMMs")
     ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
                     help="file receiving the full result (every section); stdout ends with the headline line only")
     ap.add_argument("--profile-k", type=int, default=32)
