@@ -51,7 +51,7 @@ int resident_blocks(const void* kernel, size_t smem, int threads) {
 }
 
 rb_status opt_in_smem(const void* kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return RB_OK;
+  if (bytes == 0) return RB_OK;
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> opted;
   int dev = 0;
@@ -59,7 +59,11 @@ rb_status opt_in_smem(const void* kernel, size_t bytes) {
   std::lock_guard<std::mutex> lock(mu);
   size_t& cur = opted[std::make_pair(dev, kernel)];
   if (bytes > cur) {
-    RB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    // without the attribute, static and dynamic shared memory together stay within 48 KB
+    cudaFuncAttributes fa{};
+    RB_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    if (fa.sharedSizeBytes + bytes > 48 * 1024)
+      RB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     cur = bytes;
   }
   return RB_OK;

@@ -324,6 +324,61 @@ __global__ void k_line_factors(Stencil7<double> st, LineGeom lg, double* __restr
   }
 }
 
+// The 7-point operator seen from one grid line along axis d (cells t = 0 .. len - 1): the
+// face area across d is the product of the other two axes' widths, fixed on the line, and the
+// coefficient across another axis e is w_d[t] times a factor fixed on the line (the third
+// axis' width times 1 / d_f of the face across e).  A cell then costs two table reads along
+// the line, and its neighbours along d are the line's own cells, carried from cell to cell.
+template <typename T>
+struct LineSten {
+  const T* wd;   // widths along the line
+  const T* icd;  // 1 / d_f of the faces along the line
+  T area;        // face area across d
+  T f1m, f1p, f2m, f2p;        // e1 < e2 the other axes: the factors of the lower / upper face
+  int o1m, o1p, o2m, o2p;  // row offsets of those neighbours (wrapped, or 0 at a wall)
+  int wrap;                // along a periodic d: offset from cell 0 to cell len - 1 (else 0)
+};
+
+template <typename P>
+__device__ __forceinline__ P sel3(int a, P v0, P v1, P v2) {
+  return a == 0 ? v0 : (a == 1 ? v1 : v2);
+}
+
+// the line along axis d whose cell t = 0 is row b0
+template <typename T>
+__device__ __forceinline__ LineSten<T> line_sten(const Stencil7<T>& s, int d, int64_t b0) {
+  const uint32_t r32 = (uint32_t)b0;
+  const int p2 = (int)s.dxy.div(r32);
+  const uint32_t rem = r32 - (uint32_t)p2 * (uint32_t)(s.n[0] * s.n[1]);
+  const int p1 = (int)s.dx.div(rem);
+  const int p0 = (int)(rem - (uint32_t)p1 * (uint32_t)s.n[0]);
+  const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+  const int64_t plane = (int64_t)s.n[0] * s.n[1];
+  LineSten<T> L;
+  L.wd = sel3(d, s.w[0], s.w[1], s.w[2]);
+  L.icd = sel3(d, s.ic[0], s.ic[1], s.ic[2]);
+  const int pe1 = sel3(e1, p0, p1, p2), pe2 = sel3(e2, p0, p1, p2);
+  const T* w1 = sel3(e1, s.w[0], s.w[1], s.w[2]);
+  const T* w2 = sel3(e2, s.w[0], s.w[1], s.w[2]);
+  const T* ic1 = sel3(e1, s.ic[0], s.ic[1], s.ic[2]);
+  const T* ic2 = sel3(e2, s.ic[0], s.ic[1], s.ic[2]);
+  const T we1 = __ldg(w1 + pe1), we2 = __ldg(w2 + pe2);
+  L.area = we1 * we2;
+  L.f1m = we2 * __ldg(ic1 + pe1), L.f1p = we2 * __ldg(ic1 + pe1 + 1);
+  L.f2m = we1 * __ldg(ic2 + pe2), L.f2p = we1 * __ldg(ic2 + pe2 + 1);
+  auto offs = [&](int e, int pe, int& om, int& op) {  // rows < 2^31: offsets fit in 32 bits
+    const int ne = sel3(e, s.n[0], s.n[1], s.n[2]), per = sel3(e, s.per[0], s.per[1], s.per[2]);
+    const int str = sel3(e, 1, s.n[0], (int)plane);
+    const int pm = pe > 0 ? pe - 1 : (per ? ne - 1 : pe), pp = pe + 1 < ne ? pe + 1 : (per ? 0 : pe);
+    om = (pm - pe) * str, op = (pp - pe) * str;
+  };
+  offs(e1, pe1, L.o1m, L.o1p);
+  offs(e2, pe2, L.o2m, L.o2p);
+  const int nd = sel3(d, s.n[0], s.n[1], s.n[2]);
+  L.wrap = sel3(d, s.per[0], s.per[1], s.per[2]) ? (nd - 1) * sel3(d, 1, s.n[0], (int)plane) : 0;
+  return L;
+}
+
 enum LineMode : int { LN_ZERO = 0, LN_JACOBI = 1 };
 
 constexpr int kSeg = kThreads / 32;  // segments per line: one warp each
@@ -365,6 +420,24 @@ __global__ void __launch_bounds__(kThreads) k_mg_line(Stencil7<T> st, LineGeom l
     T A[VEC], B[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) A[q] = T(1), B[q] = T(0);
+    // FP64: the residual in the line's own form (e_{j-1}, e_j, e_{j+1} carried along the line,
+    // four of the six coefficients one product each), which takes most of the generic form's
+    // FP64 arithmetic off the slow FP64 pipe; FP32 keeps the generic form, whose fewer
+    // registers keep the whole grid of blocks resident
+    constexpr bool kLineForm = sizeof(T) == 8 && MODE != LN_ZERO;
+    LineSten<T> ls{};
+    Vec<T, VEC> xp{}, x0{}, xn{};
+    T icm = T(0);
+    const int64_t sk = (int64_t)lg.stride * k;
+    if constexpr (kLineForm) {
+      if (on) {
+        ls = line_sten(st, lg.axis, b0);
+        const T* ec = e + (b0 + (int64_t)j0 * lg.stride) * k + chunk * VEC;
+        x0 = ldv<T, VEC>(ec);
+        xp = j0 > 0 ? ldv<T, VEC>(ec - sk) : (ls.wrap ? ldv<T, VEC>(ec + (int64_t)ls.wrap * k) : x0);
+        icm = __ldg(ls.icd + j0);
+      }
+    }
     if (on) {
       for (int j = j0; j < j1; ++j) {
         const int64_t row = b0 + (int64_t)j * lg.stride;
@@ -374,6 +447,27 @@ __global__ void __launch_bounds__(kThreads) k_mg_line(Stencil7<T> st, LineGeom l
         if constexpr (MODE == LN_ZERO) {
 #pragma unroll
           for (int q = 0; q < VEC; ++q) sv[q] = rv.v[q];
+        } else if constexpr (kLineForm) {
+          const T* ec = e + o;
+          xn = j + 1 < lg.len ? ldv<T, VEC>(ec + sk) : (ls.wrap ? ldv<T, VEC>(ec - (int64_t)ls.wrap * k) : x0);
+          const Vec<T, VEC> a1 = ldv<T, VEC>(ec + (int64_t)ls.o1m * k), b1 = ldv<T, VEC>(ec + (int64_t)ls.o1p * k);
+          const Vec<T, VEC> a2 = ldv<T, VEC>(ec + (int64_t)ls.o2m * k), b2 = ldv<T, VEC>(ec + (int64_t)ls.o2p * k);
+          const T wt = __ldg(ls.wd + j), icp = __ldg(ls.icd + j + 1);
+          const T c1m = wt * ls.f1m, c1p = wt * ls.f1p, c2m = wt * ls.f2m, c2p = wt * ls.f2p;
+          const T cdm = ls.area * icm, cdp = ls.area * icp;
+          const T diag = -(((c1m + c1p) + (c2m + c2p)) + (cdm + cdp));
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) {
+            T y = diag * x0.v[q];
+            y = fma(c1m, a1.v[q], y);
+            y = fma(c1p, b1.v[q], y);
+            y = fma(c2m, a2.v[q], y);
+            y = fma(c2p, b2.v[q], y);
+            y = fma(cdm, xp.v[q], y);
+            y = fma(cdp, xn.v[q], y);
+            sv[q] = rv.v[q] - st.scale * y;
+          }
+          xp = x0, x0 = xn, icm = icp;
         } else {
           T ae[VEC], unused;
           stencil7_apply<T, VEC>(st, e, k, row, chunk * VEC, ae, unused);

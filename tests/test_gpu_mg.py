@@ -76,6 +76,28 @@ def test_vcycle_per_level_matches_oracle(rb, name, dtype, k, smoother):
     assert np.array_equal(Z1, Z2)  # a second call on the same hierarchy gives the same bits
 
 
+@pytest.mark.parametrize("shape", [(8, 160, 8), (12, 40, 12)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3])
+def test_line_smoother_line_lengths(rb, shape, dtype, k):
+    """Wall-normal lines of 160 cells (longer than the 128 whose segments stay in registers:
+    the kernel that parks them in the output block) and of 40 and 20 cells (segments of 5, and
+    of 2 or 3 cells: unequal splits): one V-cycle per level against the oracle's."""
+    g = W.channel_grid(*shape)
+    lv = mg.hierarchy(g, smoother="line")
+    m = _mg(rb, g, k, smoother="line")
+    assert m.line_axis == 1 and m.levels == len(lv) == 2
+    tol = 1e-9 if dtype == "f64" else 1e-4
+    for l in range(len(lv)):
+        n = lv[l].A.shape[0]
+        R = _zm(W.normal((n, k), 900 + 10 * l + k))
+        Z = m.vcycle(to_dev(R), level=l, dtype=dtype).cpu().numpy()
+        for j in range(k):
+            zr = mg.vcycle(lv, R[:, j], level=l)
+            err = np.linalg.norm(_zm(Z[:, j:j + 1])[:, 0] - (zr - zr.mean())) / np.linalg.norm(zr - zr.mean())
+            assert err <= tol, (l, j, err)
+
+
 def _true_rel_res(A, B, X):
     Rt = B - A @ X
     return np.linalg.norm(_zm(Rt), axis=0) / np.linalg.norm(_zm(B), axis=0)
