@@ -501,6 +501,184 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chu
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// ------------------------------------------- 3x3x3 convolution on slabs of short rows (MMA)
+//
+// Grids whose rows are short (W = 16, 32 or 64 cells: the network's coarser levels) take an
+// M = 128 tile as R = 128 / W whole rows of one z plane.  The three x offsets go into N instead of A:
+// B stacks the weights of dx = -1, 0, +1 as three column blocks of PW columns, so one MMA of a
+// (dz, dy) tap line and input-channel pair gives, for every cell p of the tile, in[p] W_dx for
+// all three dx at once; the epilogue forms out[x] = D[x - 1][dx = -1] + D[x][0] + D[x + 1][+1]
+// with warp shuffles along the row (across the two warps of a 64-cell row through shared
+// memory; wrapped on a periodic x; nothing past a wall).  The A
+// operand then needs no x halo: tap line (dz, dy) is R consecutive rows of the CTA's slab,
+// rows y0 - 1 .. y0 + R of the three z planes, stored per 8-channel group (core matrices of 8
+// cells 128 bytes apart; the pair's second group one group slab further, LBO).  A tile costs
+// 9 C_in / 16 MMAs of N = 3 PW, against 27 C_in / 16 of N = PW for taps one at a time, and
+// loads (R + 2) / R of its three planes' rows instead of gathering 27 copies of every cell.
+__host__ __device__ constexpr uint32_t slab_group_bytes(int W) { return (uint32_t)(128 / W + 2) * W * 16; }
+inline size_t slab_smem(int nt, int cin, int W) {
+  return (size_t)nt * 9 * cin * 2 + (size_t)3 * (cin / 8) * slab_group_bytes(W);
+}
+
+template <int NT, int W>
+__global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw) {
+  constexpr int R = 128 / W;
+  constexpr uint32_t kGS = slab_group_bytes(W);
+  constexpr uint32_t kCols = tmem_cols_for(NT);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = a.cin / 8, ktot = 9 * a.cin;
+  const uint32_t sB = smem_u32(smem);
+  const uint32_t sS = sB + (uint32_t)(NT * ktot * 2);
+  const uint32_t sbo_b = (uint32_t)(ktot / 8) * 128;
+  const int ny = a.d.ny, nz = a.d.nz;
+  const int tiles_y = ny / R, n_tiles = nz * tiles_y;
+  const uint32_t idesc = umma_idesc_bf16(128, NT, false, false);
+
+  if (tid == 0) {
+    mbar_init(&acc_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+  // weights [NT][ktot] -> K-major canonical layout: core (n / 8, q) at (n / 8) sbo_b + 128 q
+  const int kcw = ktot / 8;
+  for (int i = tid; i < NT * kcw; i += kConvThreads) {
+    const int n = i / kcw, q = i - n * kcw;
+    cp_async16(sB + (uint32_t)(n >> 3) * sbo_b + (uint32_t)q * 128 + (uint32_t)(n & 7) * 16,
+               a.w + (size_t)n * ktot + (size_t)q * 8, 16);
+  }
+  cp_async_commit();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  // this thread's cell: row r, position x of the tile, accumulator row tid (TMEM lane tid)
+  const int x = tid % W, r = tid / W;
+  const bool has_l = x > 0 || a.d.px, has_r = x < W - 1 || a.d.px;
+  // neighbours along the row within the warp (rows of W >= 32 cells span W / 32 warps: the
+  // first and last lanes of a warp trade with the adjacent warps through shared memory)
+  constexpr int WL = W < 32 ? W : 32;
+  const int seg = lane & ~(WL - 1);
+  const int src_l = seg | ((lane + WL - 1) & (WL - 1)), src_r = seg | ((lane + 1) & (WL - 1));
+  constexpr int WPR = W / 32;  // warps per row (0 for W = 16)
+  __shared__ float xl[WPR > 1 ? 4 : 1][16], xr[WPR > 1 ? 4 : 1][16];
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  int fail = 0;
+  uint32_t phase = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int z = t / tiles_y, y0 = (t - z * tiles_y) * R;
+    // slab [dz][group][row y0 - 1 + rr][cell][8 channels]; a thread's consecutive copies read
+    // consecutive 16-byte pieces of one cell
+    const int total = 3 * (R + 2) * W * G;
+    for (int i = tid; i < total; i += kConvThreads) {
+      const int cg = i % G;
+      int rest = i / G;
+      const int xx = rest % W;
+      rest /= W;
+      const int rr = rest % (R + 2), dzi = rest / (R + 2);
+      int yy = y0 - 1 + rr, zz = z + dzi - 1;
+      bool ok = true;
+      if (yy < 0 || yy >= ny) {
+        if (a.d.py) yy = yy < 0 ? yy + ny : yy - ny;
+        else ok = false;
+      }
+      if (zz < 0 || zz >= nz) {
+        if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
+        else ok = false;
+      }
+      const uint32_t dst = sS + (uint32_t)(dzi * G + cg) * kGS + (uint32_t)(rr * W + xx) * 16;
+      cp_async16(dst, ok ? (const void*)(a.x + ((size_t)(zz * ny + yy) * W + xx) * a.ldx + cg * 8) : (const void*)a.x,
+                 ok ? 16u : 0u);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();  // the slab (and, on the first tile, the weights) has landed
+    fence_proxy_async();
+    if (__syncthreads_or(fail)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      uint32_t kk = 0;
+      for (int li = 0; li < 9; ++li) {
+        const int dzi = li / 3, dyi = li % 3;
+        for (int pr = 0; pr < G / 2; ++pr, ++kk) {
+          const uint64_t ad = umma_sdesc(sS + (uint32_t)(dzi * G + 2 * pr) * kGS + (uint32_t)(dyi * W) * 16, kGS, 128);
+          const uint64_t bd = umma_sdesc(sB + kk * 256, 128, sbo_b);
+          umma_bf16(tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+        }
+      }
+      umma_commit(&acc_bar);
+    }
+    if (!mbar_wait(&acc_bar, phase)) fail = 1;
+    phase ^= 1u;
+    tc_fence_after();
+    const int v = (z * ny + y0 + r) * W + x;
+    for (int c0 = 0; c0 < pw; c0 += 16) {
+      float pm[16], pc[16], pp[16];
+      tmem_ld16(taddr + (uint32_t)c0, pm);             // dx = -1 block (whole warp)
+      tmem_ld16(taddr + (uint32_t)(pw + c0), pc);      // dx = 0
+      tmem_ld16(taddr + (uint32_t)(2 * pw + c0), pp);  // dx = +1
+      float lv[16], rv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        lv[i] = __shfl_sync(0xffffffffu, pm[i], src_l);
+        rv[i] = __shfl_sync(0xffffffffu, pp[i], src_r);
+      }
+      if constexpr (WPR > 1) {
+        const int wr = warp % WPR, w0 = warp - wr;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (lane == 31) xl[warp][i] = pm[i];
+          if (lane == 0) xr[warp][i] = pp[i];
+        }
+        __syncthreads();
+        const int wl = w0 + (wr + WPR - 1) % WPR, wn = w0 + (wr + 1) % WPR;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (lane == 0) lv[i] = xl[wl][i];
+          if (lane == 31) rv[i] = xr[wn][i];
+        }
+        __syncthreads();  // xl, xr are rewritten by the next column chunk
+      }
+      float o[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) o[i] = pc[i] + (has_l ? lv[i] : 0.0f) + (has_r ? rv[i] : 0.0f);
+      if (fail) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cb = c0 + 8 * h;
+        if (cb >= a.cout) continue;
+        float q8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float val = o[8 * h + i];
+          if (a.bias) val += __ldg(a.bias + cb + i);
+          if (a.relu) val = fmaxf(val, 0.0f);
+          q8[i] = val;
+        }
+        if (a.mask) {
+          const uint4 mq = *reinterpret_cast<const uint4*>(a.mask + (size_t)v * a.ldm + cb);
+          const bf16* mv = reinterpret_cast<const bf16*>(&mq);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (!(__bfloat162float(mv[i]) > 0.0f)) q8[i] = 0.0f;
+        }
+        uint4 q;
+        __nv_bfloat162* qp = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) qp[i] = __floats2bfloat162_rn(q8[2 * i], q8[2 * i + 1]);
+        *reinterpret_cast<uint4*>(a.y + (size_t)v * a.ldy + cb) = q;
+      }
+    }
+    tc_fence_before();  // this tile's TMEM reads precede the next tile's MMAs (next barrier)
+  }
+  cp_async_wait_all();
+  if (fail && a.err) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
 // ------------------------------------------------------- weight gradient of a 3x3x3 conv (MMA)
 //
 // D[m][n] = sum over cells v of A[m][v] B[n][v] with m = tap * c_in + ci (plus one row
@@ -1325,6 +1503,32 @@ __global__ void k_pack_row(const float* __restrict__ W, int cin, int cout, int d
   }
 }
 
+// BF16 weights of a 3x3x3 convolution for the slab kernel, [3 pw][9 C] for an input of C
+// channels: row n = (dx + 1) pw + o (o < pw, zero rows past the real channels), column
+// K = ((dz + 1) 3 + (dy + 1)) C + c.  Forward (dgrad = 0): o = output channel < cout,
+// c = input channel < cin.  Input gradient: o = input channel < cin, c = output channel,
+// taps flipped.
+__global__ void k_pack_slab(const float* __restrict__ W, int cin, int cout, int dgrad, int C, int pw,
+                            bf16* __restrict__ dst) {
+  const int ktot = 9 * C, nt = 3 * pw;
+  const int nrows = dgrad ? cin : cout;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt * ktot; i += gridDim.x * blockDim.x) {
+    const int n = i / ktot, K = i - n * ktot;
+    const int part = n / pw, o = n - part * pw;
+    const int li = K / C, c = K - li * C;
+    const int tap = li * 3 + part;  // (dz + 1) 9 + (dy + 1) 3 + (dx + 1)
+    float v = 0.0f;
+    if (o < nrows) {
+      if (!dgrad) {
+        if (c < cin) v = W[((size_t)o * 27 + tap) * cin + c];
+      } else if (c < cout) {
+        v = W[((size_t)c * 27 + (26 - tap)) * cin + o];
+      }
+    }
+    dst[i] = __float2bfloat16(v);
+  }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ a, int n, bf16* __restrict__ out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = __float2bfloat16(a[i]);
 }
@@ -1397,6 +1601,9 @@ struct Layer {
   bf16* wd = nullptr;
   bf16* wf_row = nullptr;  // row-kernel layouts (level-0 rows of 128 cells), or null
   bf16* wd_row = nullptr;
+  bf16* wf_slab = nullptr;  // slab-kernel layouts (rows of 16 or 32 cells), or null
+  bf16* wd_slab = nullptr;
+  int pw_f = 0, pw_d = 0;   // their column blocks: output channels rounded up to 16
   bf16* wu = nullptr;  // up: BF16 [cout][8][cin]
 };
 
@@ -1601,6 +1808,53 @@ rb_status row_launch(const Conv3Args& a, int np, cudaStream_t s) {
   return RB_EUNSUPPORTED;
 }
 
+template <int NT, int W>
+rb_status launch_slab_nt(const Conv3Args& a, int pw, size_t smem, cudaStream_t s) {
+  auto* kern = &k_conv3_slab<NT, W>;
+  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(kern), smem));
+  thread_local int per_sm = 0;
+  thread_local size_t per_sm_smem = 0;
+  if (per_sm == 0 || per_sm_smem != smem) {
+    per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kConvThreads, tmem_cols_for(NT));
+    per_sm_smem = smem;
+  }
+  const int n_tiles = a.d.nz * (a.d.ny / (128 / W));
+  const int grid = std::max(1, std::min(n_tiles, per_sm * guess_sm_count()));
+  kern<<<grid, kConvThreads, smem, s>>>(a, pw);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
+// the slab kernel takes rows of 16, 32 or 64 cells (whole rows per 128-cell tile), inputs of
+// an even number of 8-channel groups and at most 192 stacked output columns
+bool slab_kernel_fits(const Dims& d, int cin, int pw) {
+  return (d.nx == 16 || d.nx == 32 || d.nx == 64) && d.ny % (128 / d.nx) == 0 && cin % 16 == 0 && pw % 16 == 0 &&
+         3 * pw <= 192 && slab_smem(3 * pw, cin, d.nx) <= kMaxConvSmem;
+}
+
+template <int NT>
+rb_status slab_launch_w(const Conv3Args& a, int pw, size_t smem, cudaStream_t s) {
+  switch (a.d.nx) {
+    case 16: return launch_slab_nt<NT, 16>(a, pw, smem, s);
+    case 32: return launch_slab_nt<NT, 32>(a, pw, smem, s);
+    case 64: return launch_slab_nt<NT, 64>(a, pw, smem, s);
+  }
+  set_error("rb_guess: no slab convolution kernel for rows of %d cells", a.d.nx);
+  return RB_EUNSUPPORTED;
+}
+
+rb_status slab_launch(const Conv3Args& a, int pw, cudaStream_t s) {
+  const size_t smem = slab_smem(3 * pw, a.cin, a.d.nx);
+  switch (3 * pw) {
+    case 48: return slab_launch_w<48>(a, pw, smem, s);
+    case 96: return slab_launch_w<96>(a, pw, smem, s);
+    case 144: return slab_launch_w<144>(a, pw, smem, s);
+    case 192: return slab_launch_w<192>(a, pw, smem, s);
+  }
+  set_error("rb_guess: no slab convolution kernel for %d output channels", pw);
+  return RB_EUNSUPPORTED;
+}
+
 rb_status conv3_launch(const Conv3Args& a, int np, cudaStream_t s) {
   const size_t smem = conv_smem(np, a.kpad);
   RB_REQUIRE(a.kpad / 8 <= kMaxChunks, "rb_guess: convolution with %d input channels too wide", a.cin);
@@ -1633,6 +1887,10 @@ rb_status conv3_fwd(rb_guess* g, const Layer& ly, const bf16* x, int ldx, bf16* 
   a.ldy = ldy;
   a.cout = ly.cout;
   a.err = g->err;
+  if (ly.wf_slab) {
+    a.w = ly.wf_slab;
+    return slab_launch(a, ly.pw_f, s);
+  }
   if (ly.wf_row) {
     a.w = ly.wf_row;
     return row_launch(a, ly.np, s);
@@ -1657,6 +1915,10 @@ rb_status conv3_dgrad(rb_guess* g, const Layer& ly, const bf16* gpre, int ldg, c
   a.ldy = ldgi;
   a.cout = ly.cin_pad;
   a.err = g->err;
+  if (ly.wd_slab) {
+    a.w = ly.wd_slab;
+    return slab_launch(a, ly.pw_d, s);
+  }
   if (ly.wd_row) {
     a.w = ly.wd_row;
     return row_launch(a, ly.npd, s);
@@ -1842,6 +2104,16 @@ rb_status refresh_weights(rb_guess* g, cudaStream_t s) {
         const int t = ly.npd * row_k(ly.cout);
         k_pack_row<<<std::min(1024, (t + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cout, 1, ly.cout,
                                                                    ly.npd, ly.wd_row);
+      }
+      if (ly.wf_slab) {
+        const int t = 3 * ly.pw_f * 9 * ly.cin_pad;
+        k_pack_slab<<<std::min(1024, (t + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cout, 0, ly.cin_pad,
+                                                                    ly.pw_f, ly.wf_slab);
+      }
+      if (ly.wd_slab) {
+        const int t = 3 * ly.pw_d * 9 * ly.cout;
+        k_pack_slab<<<std::min(1024, (t + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cout, 1, ly.cout,
+                                                                    ly.pw_d, ly.wd_slab);
       }
     } else if (ly.kind == kUp) {
       const int total = 8 * ly.cin * ly.cout;
@@ -2100,6 +2372,15 @@ extern "C" rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out) {
       const Dims& d = g->dims[ly.level];
       if (row_kernel_fits(d, ly.cin_pad, ly.np)) A(&ly.wf_row, (size_t)ly.np * row_k(ly.cin_pad));
       if (ly.cin == ly.cin_pad && row_kernel_fits(d, ly.cout, ly.npd)) A(&ly.wd_row, (size_t)ly.npd * row_k(ly.cout));
+      const int pwf = round_up(ly.cout, 16), pwd = round_up(ly.cin_pad, 16);
+      if (slab_kernel_fits(d, ly.cin_pad, pwf)) {
+        ly.pw_f = pwf;
+        A(&ly.wf_slab, (size_t)3 * pwf * 9 * ly.cin_pad);
+      }
+      if (ly.cin == ly.cin_pad && slab_kernel_fits(d, ly.cout, pwd)) {
+        ly.pw_d = pwd;
+        A(&ly.wd_slab, (size_t)3 * pwd * 9 * ly.cout);
+      }
     } else if (ly.kind == kUp) {
       A(&ly.wu, (size_t)8 * ly.cin * ly.cout);
     }
