@@ -703,6 +703,7 @@ struct WgradArgs {
   int mpad = 0;
   int cells_per_split = 0;  // multiple of kWS
   float* part = nullptr;
+  int np = 0;  // columns of a partial row (output channels padded)
   int* err = nullptr;
 };
 
@@ -1028,6 +1029,206 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// Weight gradient on rows of W cells (a multiple of 16) with no operand tile built per row:
+// D[(j, ci)][(j', co)] = sum over the row's cells x of line_j[x][ci] g[x + j' - 1][co], K = the
+// cells.  A (MN-major) is the nine input lines (dy, dz) around the row, line j = 3 (dy + 1) +
+// (dz + 1) as M core j (8 channels of one line per core, cores one line apart: M = 128 holds the
+// nine and seven don't-care cores); B (MN-major) is the row's output gradient with its x halo,
+// the N cores 16 bytes apart, so that core j' reads g shifted by j' - 1 cells: dx = 1 - j'
+// (N = 32: the fourth core is don't-care).  So tap (dz, dy, dx) and channel pair come out
+// of one MMA per 16 cells for all 27 taps of an 8-channel group pair, the operands read where
+// the copies put them.  A CTA takes runs of `chunk` rows of one z plane; a run's lines are
+// stored in order [y line][dz] per 8-channel group (no slot reuse within a run), so the nine
+// lines of every row are consecutive.  The bias gradient (sum of g) is summed per thread.
+// Accumulators: one 32-column block per (input group, output group), in TMEM for the CTA's
+// runs; the partial [split][m = tap c_in + ci (+ the bias row 27 c_in)][n = co] goes to
+// k_wgrad_reduce.
+__host__ __device__ constexpr int wlin_halo(int W) { return W + 4; }  // g line: cells -1 .. W + 2
+inline size_t wgrad_lin_smem(int W, int G, int Go, int chunk) {
+  return ((size_t)G * (chunk + 2) * 3 + 7) * W * 16 + 2 * (size_t)Go * wlin_halo(W) * 16;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chunk, int runs_per_split) {
+  constexpr uint32_t kLB = W * 16;                   // one line: W cells x 8 channels
+  constexpr uint32_t kGH = wlin_halo(W) * 16;        // one g line with its halo
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float bred[4][16];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = a.cin / 8, Go = (a.cout + 7) / 8;
+  const uint32_t cols = tmem_cols_for(32 * G * Go);
+  const int nlines = G * (chunk + 2) * 3 + 7;
+  const uint32_t sL = smem_u32(smem);
+  const uint32_t sG = sL + (uint32_t)nlines * kLB;  // two g buffers of Go lines each
+  const int ny = a.d.ny, nz = a.d.nz;
+  const int runs_y = (ny + chunk - 1) / chunk, items = nz * runs_y;
+  const int it0 = blockIdx.x * runs_per_split, it1 = min(items, it0 + runs_per_split);
+  const uint32_t idesc = umma_idesc_bf16(128, 32, true, true);
+
+  if (tid == 0) {
+    mbar_init(&mma_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, cols);
+  // every byte the MMAs may read starts finite: the don't-care cores read lines past a
+  // run's window and the g halo past the row
+  const uint32_t total_bytes = (uint32_t)nlines * kLB + 2u * Go * kGH;
+  for (uint32_t off = (uint32_t)tid * 16; off < total_bytes; off += kConvThreads * 16)
+    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(sL + off), "r"(0u) : "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // line (cg, yl, dzi) of the current run: input row y0 - 1 + yl of plane z + dzi - 1
+  auto load_lines = [&](int z, int y0, int yl) {
+    int yy = y0 - 1 + yl;
+    bool yok = true;
+    if (yy < 0 || yy >= ny) {
+      if (a.d.py) yy = yy < 0 ? yy + ny : yy - ny;
+      else yok = false;
+    }
+    const int per = W * G;
+    for (int i = tid; i < 3 * per; i += kConvThreads) {
+      const int dzi = i / per, rem = i - dzi * per;
+      const int x = rem / G, cg = rem - x * G;
+      int zz = z + dzi - 1;
+      bool ok = yok;
+      if (zz < 0 || zz >= nz) {
+        if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
+        else ok = false;
+      }
+      const uint32_t dst = sL + (uint32_t)((cg * (chunk + 2) + yl) * 3 + dzi) * kLB + (uint32_t)x * 16;
+      cp_async16(dst, ok ? (const void*)(a.x + ((size_t)(zz * ny + yy) * W + x) * a.ldx + cg * 8) : (const void*)a.x,
+                 ok ? 16u : 0u);
+    }
+  };
+  // the output gradient of row (z, y) with its halo into g buffer `buf`: cell h - 1 at h
+  auto load_g = [&](int z, int y, int buf) {
+    const int nh = W + 2;  // cells -1 .. W (the two spare cells stay zero)
+    for (int i = tid; i < nh * Go; i += kConvThreads) {
+      const int h = i / Go, cgo = i - h * Go;
+      int x = h - 1;
+      bool ok = cgo * 8 < a.cout;
+      if (x < 0 || x >= W) {
+        if (a.d.px) x = x < 0 ? x + W : x - W;
+        else ok = false;
+      }
+      const uint32_t dst = sG + (uint32_t)(buf * Go + cgo) * kGH + (uint32_t)h * 16;
+      cp_async16(dst, ok ? (const void*)(a.g + ((size_t)(z * ny + y) * W + x) * a.ldg + cgo * 8) : (const void*)a.g,
+                 ok ? 16u : 0u);
+    }
+  };
+
+  float bsum[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) bsum[i] = 0.0f;
+  int fail = 0;
+  int rows_done = 0;  // rows whose MMAs were issued (mma_bar phase count)
+  for (int it = it0; it < it1; ++it) {
+    const int z = it / runs_y, y0 = (it - z * runs_y) * chunk, y1 = min(ny, y0 + chunk);
+    // the previous run's MMAs read the line buffer: all done before it is overwritten
+    if (rows_done > 0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
+    if (!fail) {
+      for (int yl = 0; yl < 3; ++yl) load_lines(z, y0, yl);
+      load_g(z, y0, rows_done & 1);
+    }
+    cp_async_commit();
+    for (int y = y0; y < y1; ++y) {
+      // row y + 1's output gradient goes into the buffer row y - 1's MMAs read
+      if (y > y0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
+      if (!fail) {
+        if (y + 2 <= y1) load_lines(z, y0, y - y0 + 3);
+        if (y + 1 < y1) load_g(z, y + 1, (rows_done + 1) & 1);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();  // row y's lines and output gradient have landed
+      fence_proxy_async();
+      if (__syncthreads_or(fail)) break;
+      const uint32_t gb = sG + (uint32_t)((rows_done & 1) * Go) * kGH;
+      if (tid < W) {
+#pragma unroll
+        for (int cgo = 0; cgo < 2; ++cgo) {
+          if (cgo >= Go) break;
+          uint32_t q[4];
+          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3])
+                       : "r"(gb + (uint32_t)cgo * kGH + (uint32_t)(tid + 1) * 16));
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q[i]));
+            bsum[cgo * 8 + 2 * i] += f.x;
+            bsum[cgo * 8 + 2 * i + 1] += f.y;
+          }
+        }
+      }
+      if (tid == 0) {
+        tc_fence_after();
+        const int yl = y - y0;
+#pragma unroll 1
+        for (int ks = 0; ks < W / 16; ++ks)
+          for (int cg = 0; cg < G; ++cg) {
+            const uint64_t ad =
+                umma_sdesc(sL + (uint32_t)((cg * (chunk + 2) + yl) * 3) * kLB + (uint32_t)ks * 256, 128, kLB);
+            for (int cgo = 0; cgo < Go; ++cgo) {
+              const uint64_t bd = umma_sdesc(gb + (uint32_t)cgo * kGH + (uint32_t)ks * 256, 128, 16);
+              umma_bf16(tmem + (uint32_t)((cg * Go + cgo) * 32), ad, bd, idesc,
+                        (rows_done > 0 || ks > 0) ? 1u : 0u);
+            }
+          }
+        umma_commit(&mma_bar);
+      }
+      ++rows_done;
+    }
+  }
+  cp_async_wait_all();
+  if (rows_done > 0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
+  fail = __syncthreads_or(fail);
+  tc_fence_after();
+  // partials: lane m = j * 8 + ci of accumulator (cg, cgo), columns j' * 8 + co
+  const int m = warp * 32 + lane, j = m >> 3, ci = m & 7;
+  const int dyi = j / 3, dzi = j - 3 * dyi;
+  float* part = a.part + (size_t)blockIdx.x * a.mpad * a.np;
+  for (int cg = 0; cg < G; ++cg)
+    for (int cgo = 0; cgo < Go; ++cgo) {
+      float a0[16], a1[16];  // columns j' = 0, 1 and j' = 2, 3
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((cg * Go + cgo) * 32);
+      tmem_ld16(ta, a0);
+      tmem_ld16(ta + 16u, a1);
+      if (j >= 9) continue;
+      const float z0 = rows_done > 0 && !fail ? 1.0f : 0.0f;  // zeros from a CTA without rows
+      float* dst = part + (size_t)(dzi * 9 + dyi * 3) * a.cin * a.np + (size_t)(cg * 8 + ci) * a.np + cgo * 8;
+      const size_t tap_stride = (size_t)a.cin * a.np;  // dx = 1 - j': tap offsets 2, 1, 0
+#pragma unroll
+      for (int i = 0; i < 8; i += 4) {
+        *reinterpret_cast<float4*>(dst + 2 * tap_stride + i) =
+            make_float4(z0 * a0[i], z0 * a0[i + 1], z0 * a0[i + 2], z0 * a0[i + 3]);
+        *reinterpret_cast<float4*>(dst + tap_stride + i) =
+            make_float4(z0 * a0[8 + i], z0 * a0[9 + i], z0 * a0[10 + i], z0 * a0[11 + i]);
+        *reinterpret_cast<float4*>(dst + i) = make_float4(z0 * a1[i], z0 * a1[i + 1], z0 * a1[i + 2], z0 * a1[i + 3]);
+      }
+    }
+  // the bias row: per channel, warps' sums in order
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    float v = bsum[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) bred[warp][i] = v;
+  }
+  __syncthreads();
+  if (tid < 8 * Go && tid < 16) {
+    const float v = ((bred[0][tid] + bred[1][tid]) + bred[2][tid]) + bred[3][tid];
+    part[(size_t)(27 * a.cin) * a.np + tid] = (rows_done > 0 && !fail) ? v : 0.0f;
+  }
+  if (fail && a.err) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, cols);
 }
 
 // Sums the splits of a weight-gradient partial and adds it into the parameter gradient in
@@ -1998,8 +2199,89 @@ rb_status launch_wgrad_row_np(const WgradArgs& a, const RowWPlan& p, cudaStream_
   return RB_OK;
 }
 
+// The line-buffer weight gradient: rows of 16 to 128 cells, at most two output groups (its
+// per-thread bias sums) and eight 32-column accumulators (256 TMEM columns)
+struct LinWPlan {
+  int chunk = 0, splits = 0, per_split = 0;
+  size_t smem = 0;
+};
+
+bool wgrad_lin_fits(const Layer& ly, const Dims& d) {
+  const int G = ly.cin_pad / 8, Go = (ly.cout + 7) / 8;
+  return (d.nx == 16 || d.nx == 32 || d.nx == 64 || d.nx == 128) && Go <= 2 && G * Go <= 8 &&
+         wgrad_lin_smem(d.nx, G, Go, 2) <= kMaxConvSmem;
+}
+
+const void* wgrad_lin_kernel(int W) {
+  switch (W) {
+    case 16: return (const void*)&k_wgrad_lin<16>;
+    case 32: return (const void*)&k_wgrad_lin<32>;
+    case 64: return (const void*)&k_wgrad_lin<64>;
+    default: return (const void*)&k_wgrad_lin<128>;
+  }
+}
+
+// runs of the longest chunk (16, 8, 4, 2 rows) whose line buffer leaves room for two CTAs per
+// SM, then one wave of CTAs with equal shares of the runs
+LinWPlan wgrad_lin_plan(const Layer& ly, const Dims& d) {
+  LinWPlan p;
+  const int G = ly.cin_pad / 8, Go = (ly.cout + 7) / 8;
+  p.chunk = 2;
+  for (int c = 16; c >= 2; c /= 2)
+    if (wgrad_lin_smem(d.nx, G, Go, c) <= 100 * 1024 || c == 2) {
+      p.chunk = std::min(c, std::max(2, d.ny));
+      break;
+    }
+  p.smem = wgrad_lin_smem(d.nx, G, Go, p.chunk);
+  const int resident = blocks_per_sm(wgrad_lin_kernel(d.nx), p.smem, kConvThreads, tmem_cols_for(32 * G * Go)) *
+                       guess_sm_count();
+  const int items = d.nz * ((d.ny + p.chunk - 1) / p.chunk);
+  p.per_split = std::max(1, (items + resident - 1) / resident);
+  p.splits = (items + p.per_split - 1) / p.per_split;
+  return p;
+}
+
+template <int W>
+rb_status launch_wgrad_lin(const WgradArgs& a, const LinWPlan& p, cudaStream_t s) {
+  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(&k_wgrad_lin<W>), p.smem));
+  k_wgrad_lin<W><<<p.splits, kConvThreads, p.smem, s>>>(a, p.chunk, p.per_split);
+  RB_CUDA(cudaGetLastError());
+  return RB_OK;
+}
+
 rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, const bf16* gpre, int ldg, cudaStream_t s) {
   const Dims d = g->dims[ly.level];
+  if (wgrad_lin_fits(ly, d)) {
+    const LinWPlan lp = wgrad_lin_plan(ly, d);
+    WgradArgs a;
+    a.x = x;
+    a.ldx = ldx;
+    a.cin = ly.cin_pad;
+    a.g = gpre;
+    a.ldg = ldg;
+    a.cout = ly.cout;
+    a.d = d;
+    a.n_vox = d.n();
+    a.rows = 27 * ly.cin_pad;
+    a.mpad = ly.mpad;
+    a.np = ly.np;
+    a.part = g->wpart;
+    a.err = g->err;
+    rb_status st;
+    switch (d.nx) {
+      case 16: st = launch_wgrad_lin<16>(a, lp, s); break;
+      case 32: st = launch_wgrad_lin<32>(a, lp, s); break;
+      case 64: st = launch_wgrad_lin<64>(a, lp, s); break;
+      default: st = launch_wgrad_lin<128>(a, lp, s); break;
+    }
+    RB_TRY(st);
+    const int total = (a.rows + 1) * ly.cout;
+    k_wgrad_reduce<<<std::min(4096, (total + 7) / 8), 256, 0, s>>>(g->wpart, lp.splits, ly.mpad, ly.np, ly.cin_pad,
+                                                                   ly.cin, ly.cout, g->grad + ly.w_off,
+                                                                   g->grad + ly.b_off);
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+  }
   if (wgrad_row_fits(ly, d)) {
     const RowWPlan rp = wgrad_row_plan(ly, d);
     WgradArgs a;
@@ -2082,6 +2364,8 @@ size_t wpart_need(const rb_guess* g) {
       need = std::max(need, (size_t)p.splits * ly.mpad * ly.np);
       if (wgrad_row_fits(ly, g->dims[ly.level]))
         need = std::max(need, (size_t)wgrad_row_plan(ly, g->dims[ly.level]).splits * ly.mpad * ly.np);
+      if (wgrad_lin_fits(ly, g->dims[ly.level]))
+        need = std::max(need, (size_t)wgrad_lin_plan(ly, g->dims[ly.level]).splits * ly.mpad * ly.np);
     } else if (ly.kind == kUp) {
       need = std::max(need, (size_t)up_dw_grid(g, ly) * (8 * ly.cin * ly.cout + ly.cout));
     }
