@@ -703,7 +703,8 @@ struct WgradArgs {
   int mpad = 0;
   int cells_per_split = 0;  // multiple of kWS
   float* part = nullptr;
-  int np = 0;  // columns of a partial row (output channels padded)
+  int np = 0;      // columns of a partial row (output channels padded)
+  int go_cta = 0;  // output groups of 8 channels per CTA (line-buffer kernel)
   int* err = nullptr;
 };
 
@@ -1043,8 +1044,8 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int ite
 // stored in order [y line][dz] per 8-channel group (no slot reuse within a run), so the nine
 // lines of every row are consecutive.  The bias gradient (sum of g) is summed per thread.
 // Accumulators: one 32-column block per (input group, output group), in TMEM for the CTA's
-// runs; the partial [split][m = tap c_in + ci (+ the bias row 27 c_in)][n = co] goes to
-// k_wgrad_reduce.
+// runs (at most two output groups per CTA: more are spread over the grid's y dimension); the
+// partial [split][m = tap c_in + ci (+ the bias row 27 c_in)][n = co] goes to k_wgrad_reduce.
 __host__ __device__ constexpr int wlin_halo(int W) { return W + 4; }  // g line: cells -1 .. W + 2
 inline size_t wgrad_lin_smem(int W, int G, int Go, int chunk) {
   return ((size_t)G * (chunk + 2) * 3 + 7) * W * 16 + 2 * (size_t)Go * wlin_halo(W) * 16;
@@ -1059,8 +1060,9 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
   __shared__ uint32_t tmem_slot;
   __shared__ float bred[4][16];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int G = a.cin / 8, Go = (a.cout + 7) / 8;
-  const uint32_t cols = tmem_cols_for(32 * G * Go);
+  // this CTA's output groups: cgo0 .. cgo0 + Go - 1 of the layer's (grid dimension y)
+  const int G = a.cin / 8, cgo0 = blockIdx.y * a.go_cta, Go = min(a.go_cta, (a.cout + 7) / 8 - cgo0);
+  const uint32_t cols = tmem_cols_for(32 * G * a.go_cta);
   const int nlines = G * (chunk + 2) * 3 + 7;
   const uint32_t sL = smem_u32(smem);
   const uint32_t sG = sL + (uint32_t)nlines * kLB;  // two g buffers of Go lines each
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
   if (warp == 0) tmem_alloc(&tmem_slot, cols);
   // every byte the MMAs may read starts finite: the don't-care cores read lines past a
   // run's window and the g halo past the row
-  const uint32_t total_bytes = (uint32_t)nlines * kLB + 2u * Go * kGH;
+  const uint32_t total_bytes = (uint32_t)nlines * kLB + 2u * a.go_cta * kGH;
   for (uint32_t off = (uint32_t)tid * 16; off < total_bytes; off += kConvThreads * 16)
     asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(sL + off), "r"(0u) : "memory");
   tc_fence_before();
@@ -1113,13 +1115,13 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
     for (int i = tid; i < nh * Go; i += kConvThreads) {
       const int h = i / Go, cgo = i - h * Go;
       int x = h - 1;
-      bool ok = cgo * 8 < a.cout;
+      bool ok = (cgo0 + cgo) * 8 < a.cout;
       if (x < 0 || x >= W) {
         if (a.d.px) x = x < 0 ? x + W : x - W;
         else ok = false;
       }
       const uint32_t dst = sG + (uint32_t)(buf * Go + cgo) * kGH + (uint32_t)h * 16;
-      cp_async16(dst, ok ? (const void*)(a.g + ((size_t)(z * ny + y) * W + x) * a.ldg + cgo * 8) : (const void*)a.g,
+      cp_async16(dst, ok ? (const void*)(a.g + ((size_t)(z * ny + y) * W + x) * a.ldg + (cgo0 + cgo) * 8) : (const void*)a.g,
                  ok ? 16u : 0u);
     }
   };
@@ -1192,7 +1194,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
   // partials: lane m = j * 8 + ci of accumulator (cg, cgo), columns j' * 8 + co
   const int m = warp * 32 + lane, j = m >> 3, ci = m & 7;
   const int dyi = j / 3, dzi = j - 3 * dyi;
-  float* part = a.part + (size_t)blockIdx.x * a.mpad * a.np;
+  float* part = a.part + (size_t)blockIdx.x * a.mpad * a.np + cgo0 * 8;
   for (int cg = 0; cg < G; ++cg)
     for (int cgo = 0; cgo < Go; ++cgo) {
       float a0[16], a1[16];  // columns j' = 0, 1 and j' = 2, 3
@@ -2202,14 +2204,20 @@ rb_status launch_wgrad_row_np(const WgradArgs& a, const RowWPlan& p, cudaStream_
 // The line-buffer weight gradient: rows of 16 to 128 cells, at most two output groups (its
 // per-thread bias sums) and eight 32-column accumulators (256 TMEM columns)
 struct LinWPlan {
-  int chunk = 0, splits = 0, per_split = 0;
+  int chunk = 0, splits = 0, per_split = 0, go_cta = 0, go_tiles = 0;
   size_t smem = 0;
 };
 
-bool wgrad_lin_fits(const Layer& ly, const Dims& d) {
+// output groups per CTA: two, or one where two would need more than eight accumulators
+int wgrad_lin_go(const Layer& ly) {
   const int G = ly.cin_pad / 8, Go = (ly.cout + 7) / 8;
-  return (d.nx == 16 || d.nx == 32 || d.nx == 64 || d.nx == 128) && Go <= 2 && G * Go <= 8 &&
-         wgrad_lin_smem(d.nx, G, Go, 2) <= kMaxConvSmem;
+  return (Go >= 2 && 2 * G <= 8) ? 2 : 1;
+}
+
+bool wgrad_lin_fits(const Layer& ly, const Dims& d) {
+  const int G = ly.cin_pad / 8, go = wgrad_lin_go(ly);
+  return (d.nx == 16 || d.nx == 32 || d.nx == 64 || d.nx == 128) && G * go <= 8 &&
+         wgrad_lin_smem(d.nx, G, go, 2) <= kMaxConvSmem;
 }
 
 const void* wgrad_lin_kernel(int W) {
@@ -2225,7 +2233,9 @@ const void* wgrad_lin_kernel(int W) {
 // SM, then one wave of CTAs with equal shares of the runs
 LinWPlan wgrad_lin_plan(const Layer& ly, const Dims& d) {
   LinWPlan p;
-  const int G = ly.cin_pad / 8, Go = (ly.cout + 7) / 8;
+  const int G = ly.cin_pad / 8, Go = wgrad_lin_go(ly);
+  p.go_cta = Go;
+  p.go_tiles = ((ly.cout + 7) / 8 + Go - 1) / Go;
   p.chunk = 2;
   for (int c = 16; c >= 2; c /= 2)
     if (wgrad_lin_smem(d.nx, G, Go, c) <= 100 * 1024 || c == 2) {
@@ -2236,7 +2246,8 @@ LinWPlan wgrad_lin_plan(const Layer& ly, const Dims& d) {
   const int resident = blocks_per_sm(wgrad_lin_kernel(d.nx), p.smem, kConvThreads, tmem_cols_for(32 * G * Go)) *
                        guess_sm_count();
   const int items = d.nz * ((d.ny + p.chunk - 1) / p.chunk);
-  p.per_split = std::max(1, (items + resident - 1) / resident);
+  const int target = std::max(1, resident / p.go_tiles);
+  p.per_split = std::max(1, (items + target - 1) / target);
   p.splits = (items + p.per_split - 1) / p.per_split;
   return p;
 }
@@ -2244,7 +2255,7 @@ LinWPlan wgrad_lin_plan(const Layer& ly, const Dims& d) {
 template <int W>
 rb_status launch_wgrad_lin(const WgradArgs& a, const LinWPlan& p, cudaStream_t s) {
   RB_TRY(opt_in_smem(reinterpret_cast<const void*>(&k_wgrad_lin<W>), p.smem));
-  k_wgrad_lin<W><<<p.splits, kConvThreads, p.smem, s>>>(a, p.chunk, p.per_split);
+  k_wgrad_lin<W><<<dim3(p.splits, p.go_tiles), kConvThreads, p.smem, s>>>(a, p.chunk, p.per_split);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
@@ -2265,6 +2276,7 @@ rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, cons
     a.rows = 27 * ly.cin_pad;
     a.mpad = ly.mpad;
     a.np = ly.np;
+    a.go_cta = lp.go_cta;
     a.part = g->wpart;
     a.err = g->err;
     rb_status st;
