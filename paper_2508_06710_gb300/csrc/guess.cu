@@ -515,9 +515,16 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chu
 // cells 128 bytes apart; the pair's second group one group slab further, LBO).  A tile costs
 // 9 C_in / 16 MMAs of N = 3 PW, against 27 C_in / 16 of N = PW for taps one at a time, and
 // loads (R + 2) / R of its three planes' rows instead of gathering 27 copies of every cell.
+// K of the stacked weights: 9 tap lines x C channels, as MMAs of two 8-channel K cores; with
+// C = 8 the cores of an MMA are two z lines of one y offset (z offsets -1, 0 and +1, zero
+// weights): 6 MMAs of 16
+__host__ __device__ constexpr int stack_k(int C) { return C == 8 ? 96 : 9 * C; }
+// dz slabs of a group: the three planes, and for 8-channel inputs a zero fourth (the partner of
+// the last plane's cores)
+__host__ __device__ constexpr int slab_planes(int cin) { return cin == 8 ? 4 : 3; }
 __host__ __device__ constexpr uint32_t slab_group_bytes(int W) { return (uint32_t)(128 / W + 2) * W * 16; }
 inline size_t slab_smem(int nt, int cin, int W) {
-  return (size_t)nt * 9 * cin * 2 + (size_t)3 * (cin / 8) * slab_group_bytes(W);
+  return (size_t)nt * stack_k(cin) * 2 + (size_t)slab_planes(cin) * (cin / 8) * slab_group_bytes(W);
 }
 
 template <int NT, int W>
@@ -529,7 +536,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
   __shared__ __align__(8) uint64_t acc_bar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int G = a.cin / 8, ktot = 9 * a.cin;
+  const int G = a.cin / 8, ktot = stack_k(a.cin);
   const uint32_t sB = smem_u32(smem);
   const uint32_t sS = sB + (uint32_t)(NT * ktot * 2);
   const uint32_t sbo_b = (uint32_t)(ktot / 8) * 128;
@@ -550,6 +557,9 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
                a.w + (size_t)n * ktot + (size_t)q * 8, 16);
   }
   cp_async_commit();
+  if (G == 1)  // the zero fourth plane (finite bytes behind zero weights)
+    for (uint32_t off = (uint32_t)tid * 16; off < kGS; off += kConvThreads * 16)
+      asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(sS + 3 * kGS + off), "r"(0u) : "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -599,12 +609,19 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
     if (tid == 0) {
       tc_fence_after();
       uint32_t kk = 0;
-      for (int li = 0; li < 9; ++li) {
-        const int dzi = li / 3, dyi = li % 3;
-        for (int pr = 0; pr < G / 2; ++pr, ++kk) {
-          const uint64_t ad = umma_sdesc(sS + (uint32_t)(dzi * G + 2 * pr) * kGS + (uint32_t)(dyi * W) * 16, kGS, 128);
-          const uint64_t bd = umma_sdesc(sB + kk * 256, 128, sbo_b);
-          umma_bf16(tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+      if (G == 1) {  // cores: planes (0, 1) and (2, zero) of each y offset
+        for (int dyi = 0; dyi < 3; ++dyi)
+          for (int pr = 0; pr < 2; ++pr, ++kk) {
+            const uint64_t ad = umma_sdesc(sS + (uint32_t)(2 * pr) * kGS + (uint32_t)(dyi * W) * 16, kGS, 128);
+            umma_bf16(tmem, ad, umma_sdesc(sB + kk * 256, 128, sbo_b), idesc, kk > 0 ? 1u : 0u);
+          }
+      } else {
+        for (int li = 0; li < 9; ++li) {
+          const int dzi = li / 3, dyi = li % 3;
+          for (int pr = 0; pr < G / 2; ++pr, ++kk) {
+            const uint64_t ad = umma_sdesc(sS + (uint32_t)(dzi * G + 2 * pr) * kGS + (uint32_t)(dyi * W) * 16, kGS, 128);
+            umma_bf16(tmem, ad, umma_sdesc(sB + kk * 256, 128, sbo_b), idesc, kk > 0 ? 1u : 0u);
+          }
         }
       }
       umma_commit(&acc_bar);
@@ -846,183 +863,6 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
 #pragma unroll
     for (int i = 0; i < 16; i += 4) {
       float4 q = (T > 0 && !fail) ? make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]) : make_float4(0, 0, 0, 0);
-      *reinterpret_cast<float4*>(dst + c0 + i) = q;
-    }
-  }
-  if (fail && a.err) atomicExch(a.err, 1);
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kCols);
-}
-
-// Weight gradient on rows of W = 128 or 64 cells: the same product as k_wgrad_mma with K = the cells of
-// one grid row at a time, its A operand (MN-major, rows m = tap * c_in + ci, the ones row, zero
-// rows) copied from the shared-memory line ring of the row kernel instead of gathered from
-// global memory: each input line is read from L2 for three rows, and the copies need no
-// neighbour arithmetic (the ring holds the wrapped or zero halo).  The ones row and the zero
-// rows are written once.  One accumulator; the A tile of a row is rebuilt once the MMAs of the
-// previous row are done, the B tile (the masked output gradient of the row) is double-buffered.
-constexpr uint32_t kRowLboA = 16 * 128;  // A: core matrices adjacent along K (8 cells)
-
-template <int NP, int W>
-__global__ void __launch_bounds__(kConvThreads) k_wgrad_row(WgradArgs a, int items_per_split, int chunk) {
-  constexpr uint32_t kLineBytes = line_bytes(W), kGroupBytes = group_bytes(W);
-  constexpr int kRowPos = row_pos(W);
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mma_bar;
-  __shared__ __align__(8) uint64_t done_bar;
-  __shared__ uint32_t tmem_slot;
-  constexpr uint32_t kCols = tmem_cols_for(NP);
-  constexpr uint32_t kLboB = (NP / 8) * 128;
-  constexpr uint32_t kBBytes = (uint32_t)NP * W * 2;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int G = a.cin / 8;
-  const uint32_t sA = smem_u32(smem);
-  const uint32_t sB = sA + (W / 8) * kRowLboA;     // two B buffers
-  const uint32_t sL = sB + 2 * kBBytes;            // the line ring
-  const int mt = blockIdx.x, split = blockIdx.y;
-  const int ny = a.d.ny, nz = a.d.nz;
-  const int chunks_y = (ny + chunk - 1) / chunk;
-  const int items = nz * chunks_y;
-  const int it0 = split * items_per_split;
-  const int it1 = min(items, it0 + items_per_split);
-  const uint32_t idesc = umma_idesc_bf16(128, NP, true, true);
-
-  if (tid == 0) {
-    mbar_init(&mma_bar, 1);
-    mbar_init(&done_bar, 1);
-    fence_barrier_init();
-  }
-  if (warp == 0) tmem_alloc(&tmem_slot, kCols);
-  // the 16 row groups of the m tile: gather (tap offsets, ci0), the ones row, or zeros; the
-  // constant groups are written now, for all 128 cells (this thread's cell = tid)
-  int gcode[16];
-#pragma unroll
-  for (int g8 = 0; g8 < 16; ++g8) {
-    const int m = mt * 128 + g8 * 8;
-    const uint32_t dst = sA + (uint32_t)(tid >> 3) * kRowLboA + (uint32_t)g8 * 128 + (uint32_t)(tid & 7) * 16;
-    if (m < a.rows) {
-      const int tap = m / a.cin;
-      gcode[g8] = (tap % 3) | ((tap / 3) % 3) << 2 | (tap / 9) << 4 | ((m - tap * a.cin) >> 3) << 8;
-    } else {
-      gcode[g8] = -1;
-      const uint32_t one = m == a.rows ? 0x3F80u : 0u;  // BF16 1.0 in the low half: the bias row
-      if (tid < W)
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %2, %2};" ::"r"(dst), "r"(one), "r"(0u) : "memory");
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-
-  auto line_addr = [&](int cg, int dzi, int yy) -> uint32_t {
-    return sL + (uint32_t)cg * kGroupBytes + (uint32_t)(dzi * 4 + (yy & 3)) * kLineBytes;
-  };
-  auto load_row = [&](int z, int yy) {  // three z lines of row yy (as in k_conv3_row)
-    int yw = yy;
-    bool yok = true;
-    if (yw < 0 || yw >= ny) {
-      if (a.d.py) yw = yw < 0 ? yw + ny : yw - ny;
-      else yok = false;
-    }
-    for (int dzi = 0; dzi < 3; ++dzi) {
-      int zz = z + dzi - 1;
-      bool ok = yok;
-      if (zz < 0 || zz >= nz) {
-        if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
-        else ok = false;
-      }
-      const size_t row0 = ((size_t)zz * ny + yw) * W;
-      for (int cg = 0; cg < G; ++cg) {
-        const uint32_t dst = line_addr(cg, dzi, yy);
-        for (int pos = tid; pos < kRowPos; pos += kConvThreads) {
-          int x = pos - 1;
-          bool okx = ok;
-          if (x < 0 || x >= W) {
-            if (a.d.px) x = x < 0 ? x + W : x - W;
-            else okx = false;
-          }
-          cp_async16(dst + (uint32_t)pos * 16, okx ? (const void*)(a.x + (row0 + x) * a.ldx + cg * 8) : (const void*)a.x,
-                     okx ? 16u : 0u);
-        }
-      }
-    }
-  };
-  auto load_b = [&](int z, int y, int buf) {  // the row's output gradient, this thread's cell
-    if (tid >= W) return;
-    const size_t v = ((size_t)z * ny + y) * W + tid;
-    const uint32_t base = sB + (uint32_t)buf * kBBytes + (uint32_t)(tid >> 3) * kLboB + (uint32_t)(tid & 7) * 16;
-#pragma unroll
-    for (int nb = 0; nb < NP / 8; ++nb) {
-      const bool ok = nb * 8 < a.cout;
-      cp_async16(base + (uint32_t)nb * 128, ok ? (const void*)(a.g + v * a.ldg + nb * 8) : (const void*)a.g, ok ? 16u : 0u);
-    }
-  };
-
-  int fail = 0;
-  int rows_done = 0;  // rows whose MMAs were issued (mma_bar phase count)
-  for (int it = it0; it < it1 && !fail; ++it) {
-    const int z = it / chunks_y;
-    const int y0 = (it - z * chunks_y) * chunk;
-    const int y1 = min(ny, y0 + chunk);
-    load_row(z, y0 - 1);
-    load_row(z, y0);
-    load_row(z, y0 + 1);
-    load_b(z, y0, rows_done & 1);
-    cp_async_commit();
-    for (int y = y0; y < y1; ++y) {
-      cp_async_wait<0>();  // lines y - 1 .. y + 1 and B(y) have landed
-      if (__syncthreads_or(fail)) break;
-      // the A tile is rebuilt once the previous row's MMAs have read it
-      if (rows_done > 0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
-#pragma unroll
-      for (int g8 = 0; g8 < 16; ++g8) {
-        const int e = gcode[g8];
-        if (e < 0 || tid >= W) continue;
-        const uint32_t src = line_addr(e >> 8, (e >> 4) & 3, y + ((e >> 2) & 3) - 1) + (uint32_t)(tid + (e & 3)) * 16;
-        const uint32_t dst = sA + (uint32_t)(tid >> 3) * kRowLboA + (uint32_t)g8 * 128 + (uint32_t)(tid & 7) * 16;
-        uint32_t q0, q1, q2, q3;
-        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(q0), "=r"(q1), "=r"(q2), "=r"(q3) : "r"(src));
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(q0), "r"(q1), "r"(q2), "r"(q3)
-                     : "memory");
-      }
-      fence_proxy_async();
-      if (__syncthreads_or(fail)) break;
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t bbuf = sB + (uint32_t)(rows_done & 1) * kBBytes;
-#pragma unroll
-        for (int kk = 0; kk < W / 16; ++kk)
-          umma_bf16(tmem, umma_sdesc(sA + (uint32_t)kk * 2 * kRowLboA, kRowLboA, 128),
-                    umma_sdesc(bbuf + (uint32_t)kk * 2 * kLboB, kLboB, 128), idesc, (rows_done > 0 || kk > 0) ? 1u : 0u);
-        umma_commit(&mma_bar);
-      }
-      ++rows_done;
-      // next: the lines of row y + 2 (into the slot of row y - 2, read last by row y - 1's copies)
-      // and B of row y + 1 (into the buffer row y - 1's MMAs read: done, waited above)
-      if (y + 2 <= y1) load_row(z, y + 2);
-      if (y + 1 < y1) load_b(z, y + 1, rows_done & 1);
-      cp_async_commit();
-    }
-  }
-  cp_async_wait_all();
-  if (tid == 0) {
-    umma_commit(&done_bar);
-    if (!mbar_wait(&done_bar, 0)) fail = 1;
-  }
-  fail = __syncthreads_or(fail);
-  tc_fence_after();
-  const int m = warp * 32 + lane;
-  float* dst = a.part + ((size_t)split * a.mpad + (size_t)mt * 128 + m) * NP;
-#pragma unroll
-  for (int c0 = 0; c0 < NP; c0 += 16) {
-    float acc[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
-#pragma unroll
-    for (int i = 0; i < 16; i += 4) {
-      float4 q = (rows_done > 0 && !fail) ? make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3])
-                                          : make_float4(0, 0, 0, 0);
       *reinterpret_cast<float4*>(dst + c0 + i) = q;
     }
   }
@@ -1706,22 +1546,30 @@ __global__ void k_pack_row(const float* __restrict__ W, int cin, int cout, int d
   }
 }
 
-// BF16 weights of a 3x3x3 convolution for the slab kernel, [3 pw][9 C] for an input of C
-// channels: row n = (dx + 1) pw + o (o < pw, zero rows past the real channels), column
-// K = ((dz + 1) 3 + (dy + 1)) C + c.  Forward (dgrad = 0): o = output channel < cout,
+// BF16 weights of a 3x3x3 convolution for the slab kernel, [3 pw][stack_k(C)] for an
+// input of C channels: row n = (dx + 1) pw + o (o < pw, zero rows past the real channels),
+// column K = ((dz + 1) 3 + (dy + 1)) C + c (C = 8: see stack_k).  Forward (dgrad = 0): o = output channel < cout,
 // c = input channel < cin.  Input gradient: o = input channel < cin, c = output channel,
 // taps flipped.
 __global__ void k_pack_slab(const float* __restrict__ W, int cin, int cout, int dgrad, int C, int pw,
                             bf16* __restrict__ dst) {
-  const int ktot = 9 * C, nt = 3 * pw;
+  const int ktot = stack_k(C), nt = 3 * pw;
   const int nrows = dgrad ? cin : cout;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt * ktot; i += gridDim.x * blockDim.x) {
     const int n = i / ktot, K = i - n * ktot;
     const int part = n / pw, o = n - part * pw;
-    const int li = K / C, c = K - li * C;
+    int li, c;
+    if (C == 8) {  // MMA m = 2 (dy + 1) + pair, core kc: plane dz + 1 = 2 pair + kc (3: zero)
+      const int m = K >> 4, kc = (K >> 3) & 1, dzi = 2 * (m & 1) + kc;
+      c = K & 7;
+      li = dzi < 3 ? dzi * 3 + (m >> 1) : -1;
+    } else {
+      li = K / C;
+      c = K - li * C;
+    }
     const int tap = li * 3 + part;  // (dz + 1) 9 + (dy + 1) 3 + (dx + 1)
     float v = 0.0f;
-    if (o < nrows) {
+    if (li >= 0 && o < nrows) {
       if (!dgrad) {
         if (c < cin) v = W[((size_t)o * 27 + tap) * cin + c];
       } else if (c < cout) {
@@ -2029,10 +1877,10 @@ rb_status launch_slab_nt(const Conv3Args& a, int pw, size_t smem, cudaStream_t s
 }
 
 // the slab kernel takes rows of 16, 32 or 64 cells (whole rows per 128-cell tile), inputs of
-// an even number of 8-channel groups and at most 192 stacked output columns
+// 8 channels or an even number of 8-channel groups and at most 192 stacked output columns
 bool slab_kernel_fits(const Dims& d, int cin, int pw) {
-  return (d.nx == 16 || d.nx == 32 || d.nx == 64) && d.ny % (128 / d.nx) == 0 && cin % 16 == 0 && pw % 16 == 0 &&
-         3 * pw <= 192 && slab_smem(3 * pw, cin, d.nx) <= kMaxConvSmem;
+  return (d.nx == 16 || d.nx == 32 || d.nx == 64) && d.ny % (128 / d.nx) == 0 && (cin == 8 || cin % 16 == 0) &&
+         pw % 16 == 0 && 3 * pw <= 192 && slab_smem(3 * pw, cin, d.nx) <= kMaxConvSmem;
 }
 
 template <int NT>
@@ -2151,56 +1999,6 @@ rb_status launch_wgrad_np(const WgradArgs& a, const WgradPlan& p, cudaStream_t s
   return RB_OK;
 }
 
-struct RowWPlan {
-  int m_tiles = 0, splits = 0, per_split = 0, chunk = 0;
-};
-
-size_t wgrad_row_smem(int np, int cin, int W);
-
-// CTAs of the row weight-gradient kernel resident on the GPU at once (its registers, shared
-// memory and TMEM), for a launch of one wave
-int wgrad_row_resident(int np, int W, size_t smem) {
-  const void* k = nullptr;
-  switch (np) {
-    case 16: k = W == 128 ? (const void*)&k_wgrad_row<16, 128> : (const void*)&k_wgrad_row<16, 64>; break;
-    case 32: k = W == 128 ? (const void*)&k_wgrad_row<32, 128> : (const void*)&k_wgrad_row<32, 64>; break;
-    case 48: k = W == 128 ? (const void*)&k_wgrad_row<48, 128> : (const void*)&k_wgrad_row<48, 64>; break;
-    default: k = W == 128 ? (const void*)&k_wgrad_row<64, 128> : (const void*)&k_wgrad_row<64, 64>; break;
-  }
-  return blocks_per_sm(k, smem, kConvThreads, tmem_cols_for(np)) * guess_sm_count();
-}
-
-// m_tiles x splits CTAs, no more than are resident at once (one wave: a partial second wave
-// would cost a whole CTA's run), each taking per_split runs of `chunk` rows
-RowWPlan wgrad_row_plan(const Layer& ly, const Dims& d) {
-  RowWPlan p;
-  p.m_tiles = ly.mpad / 128;
-  const int resident = wgrad_row_resident(ly.np, d.nx, wgrad_row_smem(ly.np, ly.cin_pad, d.nx));
-  const int target = std::max(1, resident / p.m_tiles);
-  p.chunk = row_chunk(d.ny, d.nz, target);
-  const int items = d.nz * ((d.ny + p.chunk - 1) / p.chunk);
-  p.per_split = std::max(1, (items + target - 1) / target);
-  p.splits = (items + p.per_split - 1) / p.per_split;
-  return p;
-}
-
-size_t wgrad_row_smem(int np, int cin, int W) {
-  return (size_t)(W / 8) * kRowLboA + 2 * (size_t)np * W * 2 + (size_t)(cin / 8) * group_bytes(W) + 256;
-}
-
-bool wgrad_row_fits(const Layer& ly, const Dims& d) {
-  return (d.nx == 128 || d.nx == 64) && ly.cin_pad % 8 == 0 && wgrad_row_smem(ly.np, ly.cin_pad, d.nx) <= kMaxConvSmem;
-}
-
-template <int NP, int W>
-rb_status launch_wgrad_row_np(const WgradArgs& a, const RowWPlan& p, cudaStream_t s) {
-  const size_t smem = wgrad_row_smem(NP, a.cin, W);
-  RB_TRY(opt_in_smem(reinterpret_cast<const void*>(&k_wgrad_row<NP, W>), smem));
-  k_wgrad_row<NP, W><<<dim3(p.m_tiles, p.splits), kConvThreads, smem, s>>>(a, p.per_split, p.chunk);
-  RB_CUDA(cudaGetLastError());
-  return RB_OK;
-}
-
 // The line-buffer weight gradient: rows of 16 to 128 cells, at most two output groups (its
 // per-thread bias sums) and eight 32-column accumulators (256 TMEM columns)
 struct LinWPlan {
@@ -2294,40 +2092,6 @@ rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, cons
     RB_CUDA(cudaGetLastError());
     return RB_OK;
   }
-  if (wgrad_row_fits(ly, d)) {
-    const RowWPlan rp = wgrad_row_plan(ly, d);
-    WgradArgs a;
-    a.x = x;
-    a.ldx = ldx;
-    a.cin = ly.cin_pad;
-    a.g = gpre;
-    a.ldg = ldg;
-    a.cout = ly.cout;
-    a.d = d;
-    a.n_vox = d.n();
-    a.rows = 27 * ly.cin_pad;
-    a.mpad = ly.mpad;
-    a.part = g->wpart;
-    a.err = g->err;
-    rb_status st;
-    const bool w128 = d.nx == 128;
-    switch (ly.np) {
-      case 16: st = w128 ? launch_wgrad_row_np<16, 128>(a, rp, s) : launch_wgrad_row_np<16, 64>(a, rp, s); break;
-      case 32: st = w128 ? launch_wgrad_row_np<32, 128>(a, rp, s) : launch_wgrad_row_np<32, 64>(a, rp, s); break;
-      case 48: st = w128 ? launch_wgrad_row_np<48, 128>(a, rp, s) : launch_wgrad_row_np<48, 64>(a, rp, s); break;
-      case 64: st = w128 ? launch_wgrad_row_np<64, 128>(a, rp, s) : launch_wgrad_row_np<64, 64>(a, rp, s); break;
-      default:
-        set_error("rb_guess: no row weight-gradient kernel for %d output channels", ly.np);
-        return RB_EUNSUPPORTED;
-    }
-    RB_TRY(st);
-    const int total = (a.rows + 1) * ly.cout;
-    k_wgrad_reduce<<<std::min(4096, (total + 7) / 8), 256, 0, s>>>(g->wpart, rp.splits, ly.mpad, ly.np, ly.cin_pad,
-                                                                   ly.cin, ly.cout, g->grad + ly.w_off,
-                                                                   g->grad + ly.b_off);
-    RB_CUDA(cudaGetLastError());
-    return RB_OK;
-  }
   const WgradPlan p = wgrad_plan(ly, d.n());
   WgradArgs a;
   a.x = x;
@@ -2374,8 +2138,6 @@ size_t wpart_need(const rb_guess* g) {
     if (ly.kind == kConv3) {
       const WgradPlan p = wgrad_plan(ly, g->dims[ly.level].n());
       need = std::max(need, (size_t)p.splits * ly.mpad * ly.np);
-      if (wgrad_row_fits(ly, g->dims[ly.level]))
-        need = std::max(need, (size_t)wgrad_row_plan(ly, g->dims[ly.level]).splits * ly.mpad * ly.np);
       if (wgrad_lin_fits(ly, g->dims[ly.level]))
         need = std::max(need, (size_t)wgrad_lin_plan(ly, g->dims[ly.level]).splits * ly.mpad * ly.np);
     } else if (ly.kind == kUp) {
@@ -2402,12 +2164,12 @@ rb_status refresh_weights(rb_guess* g, cudaStream_t s) {
                                                                    ly.npd, ly.wd_row);
       }
       if (ly.wf_slab) {
-        const int t = 3 * ly.pw_f * 9 * ly.cin_pad;
+        const int t = 3 * ly.pw_f * stack_k(ly.cin_pad);
         k_pack_slab<<<std::min(1024, (t + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cout, 0, ly.cin_pad,
                                                                     ly.pw_f, ly.wf_slab);
       }
       if (ly.wd_slab) {
-        const int t = 3 * ly.pw_d * 9 * ly.cout;
+        const int t = 3 * ly.pw_d * stack_k(ly.cout);
         k_pack_slab<<<std::min(1024, (t + 255) / 256), 256, 0, s>>>(g->theta + ly.w_off, ly.cin, ly.cout, 1, ly.cout,
                                                                     ly.pw_d, ly.wd_slab);
       }
@@ -2671,11 +2433,11 @@ extern "C" rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out) {
       const int pwf = round_up(ly.cout, 16), pwd = round_up(ly.cin_pad, 16);
       if (slab_kernel_fits(d, ly.cin_pad, pwf)) {
         ly.pw_f = pwf;
-        A(&ly.wf_slab, (size_t)3 * pwf * 9 * ly.cin_pad);
+        A(&ly.wf_slab, (size_t)3 * pwf * stack_k(ly.cin_pad));
       }
       if (ly.cin == ly.cin_pad && slab_kernel_fits(d, ly.cout, pwd)) {
         ly.pw_d = pwd;
-        A(&ly.wd_slab, (size_t)3 * pwd * 9 * ly.cout);
+        A(&ly.wd_slab, (size_t)3 * pwd * stack_k(ly.cout));
       }
     } else if (ly.kind == kUp) {
       A(&ly.wu, (size_t)8 * ly.cin * ly.cout);
