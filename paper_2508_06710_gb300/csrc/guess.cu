@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_mma(WgradArgs a) {
 // partial [split][m = tap c_in + ci (+ the bias row 27 c_in)][n = co] goes to k_wgrad_reduce.
 __host__ __device__ constexpr int wlin_halo(int W) { return W + 4; }  // g line: cells -1 .. W + 2
 inline size_t wgrad_lin_smem(int W, int G, int Go, int chunk) {
-  return ((size_t)G * (chunk + 2) * 3 + 7) * W * 16 + 2 * (size_t)Go * wlin_halo(W) * 16;
+  return ((size_t)G * (chunk + 2) * 3 + 7) * W * 16 + 3 * (size_t)Go * wlin_halo(W) * 16;
 }
 
 template <int W>
@@ -896,7 +896,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
   constexpr uint32_t kLB = W * 16;                   // one line: W cells x 8 channels
   constexpr uint32_t kGH = wlin_halo(W) * 16;        // one g line with its halo
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t mma_bar[2];  // rows alternate between the two
   __shared__ uint32_t tmem_slot;
   __shared__ float bred[4][16];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -905,20 +905,21 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
   const uint32_t cols = tmem_cols_for(32 * G * a.go_cta);
   const int nlines = G * (chunk + 2) * 3 + 7;
   const uint32_t sL = smem_u32(smem);
-  const uint32_t sG = sL + (uint32_t)nlines * kLB;  // two g buffers of Go lines each
+  const uint32_t sG = sL + (uint32_t)nlines * kLB;  // three g buffers of Go lines each
   const int ny = a.d.ny, nz = a.d.nz;
   const int runs_y = (ny + chunk - 1) / chunk, items = nz * runs_y;
   const int it0 = blockIdx.x * runs_per_split, it1 = min(items, it0 + runs_per_split);
   const uint32_t idesc = umma_idesc_bf16(128, 32, true, true);
 
   if (tid == 0) {
-    mbar_init(&mma_bar, 1);
+    mbar_init(&mma_bar[0], 1);
+    mbar_init(&mma_bar[1], 1);
     fence_barrier_init();
   }
   if (warp == 0) tmem_alloc(&tmem_slot, cols);
   // every byte the MMAs may read starts finite: the don't-care cores read lines past a
   // run's window and the g halo past the row
-  const uint32_t total_bytes = (uint32_t)nlines * kLB + 2u * a.go_cta * kGH;
+  const uint32_t total_bytes = (uint32_t)nlines * kLB + 3u * a.go_cta * kGH;
   for (uint32_t off = (uint32_t)tid * 16; off < total_bytes; off += kConvThreads * 16)
     asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(sL + off), "r"(0u) : "memory");
   tc_fence_before();
@@ -970,28 +971,34 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
 #pragma unroll
   for (int i = 0; i < 16; ++i) bsum[i] = 0.0f;
   int fail = 0;
-  int rows_done = 0;  // rows whose MMAs were issued (mma_bar phase count)
+  int rows_done = 0;  // rows whose MMAs were issued
+  // row r's MMAs commit to mma_bar[r & 1], as that barrier's phase r / 2
+  auto wait_row = [&](int r) {
+    if (r >= 0 && !mbar_wait(&mma_bar[r & 1], (uint32_t)(r >> 1) & 1u)) fail = 1;
+  };
   for (int it = it0; it < it1; ++it) {
     const int z = it / runs_y, y0 = (it - z * runs_y) * chunk, y1 = min(ny, y0 + chunk);
     // the previous run's MMAs read the line buffer: all done before it is overwritten
-    if (rows_done > 0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
+    wait_row(rows_done - 2);
+    wait_row(rows_done - 1);
     if (!fail) {
       for (int yl = 0; yl < 3; ++yl) load_lines(z, y0, yl);
-      load_g(z, y0, rows_done & 1);
+      load_g(z, y0, rows_done % 3);
     }
     cp_async_commit();
     for (int y = y0; y < y1; ++y) {
-      // row y + 1's output gradient goes into the buffer row y - 1's MMAs read
-      if (y > y0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
+      // row y + 1's output gradient goes into the buffer row y - 2's MMAs read (row y - 1's
+      // may still run)
+      if (y > y0) wait_row(rows_done - 2);
       if (!fail) {
         if (y + 2 <= y1) load_lines(z, y0, y - y0 + 3);
-        if (y + 1 < y1) load_g(z, y + 1, (rows_done + 1) & 1);
+        if (y + 1 < y1) load_g(z, y + 1, (rows_done + 1) % 3);
       }
       cp_async_commit();
       cp_async_wait<1>();  // row y's lines and output gradient have landed
       fence_proxy_async();
       if (__syncthreads_or(fail)) break;
-      const uint32_t gb = sG + (uint32_t)((rows_done & 1) * Go) * kGH;
+      const uint32_t gb = sG + (uint32_t)((rows_done % 3) * Go) * kGH;
       if (tid < W) {
 #pragma unroll
         for (int cgo = 0; cgo < 2; ++cgo) {
@@ -1022,13 +1029,14 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
                         (rows_done > 0 || ks > 0) ? 1u : 0u);
             }
           }
-        umma_commit(&mma_bar);
+        umma_commit(&mma_bar[rows_done & 1]);
       }
       ++rows_done;
     }
   }
   cp_async_wait_all();
-  if (rows_done > 0 && !mbar_wait(&mma_bar, (uint32_t)(rows_done - 1) & 1u)) fail = 1;
+  wait_row(rows_done - 2);
+  wait_row(rows_done - 1);
   fail = __syncthreads_or(fail);
   tc_fence_after();
   // partials: lane m = j * 8 + ci of accumulator (cg, cgo), columns j' * 8 + co
