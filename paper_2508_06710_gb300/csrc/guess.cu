@@ -927,6 +927,22 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
+  // this thread's copies of a row's lines: copy k is piece i = tid + 128 k of (dzi, x, cg), the
+  // same for every row, so its offsets are worked out once (up to kWT copies a thread)
+  constexpr int kWT = 6;
+  const int per = W * G;
+  const bool tabled = 3 * per <= kWT * kConvThreads;
+  uint32_t t_dst[kWT], t_src[kWT];
+  int t_dz[kWT];
+#pragma unroll
+  for (int k = 0; k < kWT; ++k) {
+    const int i = tid + k * kConvThreads;
+    const int dzi = i / per, rem = i - dzi * per;
+    const int x = rem / G, cg = rem - x * G;
+    t_dz[k] = i < 3 * per ? dzi : -1;
+    t_dst[k] = (uint32_t)((cg * (chunk + 2)) * 3 + dzi) * kLB + (uint32_t)x * 16;
+    t_src[k] = (uint32_t)(x * a.ldx + cg * 8);
+  }
   // line (cg, yl, dzi) of the current run: input row y0 - 1 + yl of plane z + dzi - 1
   auto load_lines = [&](int z, int y0, int yl) {
     int yy = y0 - 1 + yl;
@@ -935,7 +951,31 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
       if (a.d.py) yy = yy < 0 ? yy + ny : yy - ny;
       else yok = false;
     }
-    const int per = W * G;
+    if (tabled) {
+      // the row's start in each of the three planes (or none past a wall)
+      const bf16* pb[3];
+      bool pok[3];
+#pragma unroll
+      for (int dzi = 0; dzi < 3; ++dzi) {
+        int zz = z + dzi - 1;
+        pok[dzi] = yok;
+        if (zz < 0 || zz >= nz) {
+          if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
+          else pok[dzi] = false;
+        }
+        pb[dzi] = a.x + (size_t)(zz * ny + yy) * W * a.ldx;
+      }
+      const uint32_t yoff = sL + (uint32_t)(yl * 3) * kLB;
+#pragma unroll
+      for (int k = 0; k < kWT; ++k) {
+        if (t_dz[k] < 0) break;
+        const int dz = t_dz[k];
+        const bool ok = dz == 0 ? pok[0] : (dz == 1 ? pok[1] : pok[2]);
+        const bf16* b = dz == 0 ? pb[0] : (dz == 1 ? pb[1] : pb[2]);
+        cp_async16(yoff + t_dst[k], ok ? (const void*)(b + t_src[k]) : (const void*)a.x, ok ? 16u : 0u);
+      }
+      return;
+    }
     for (int i = tid; i < 3 * per; i += kConvThreads) {
       const int dzi = i / per, rem = i - dzi * per;
       const int x = rem / G, cg = rem - x * G;
