@@ -543,6 +543,9 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
   const int ny = a.d.ny, nz = a.d.nz;
   const int tiles_y = ny / R, n_tiles = nz * tiles_y;
   const uint32_t idesc = umma_idesc_bf16(128, NT, false, false);
+  // i / G as the high word of i * ceil(2^32 / G): exact for i < 2^32 / G (the copy indices
+  // here are below 2^16)
+  const uint32_t g_magic = G == 1 ? 0u : (uint32_t)((0x100000000ull + (uint64_t)G - 1) / (uint64_t)G);
 
   if (tid == 0) {
     mbar_init(&acc_bar, 1);
@@ -583,8 +586,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
     // consecutive 16-byte pieces of one cell
     const int total = 3 * (R + 2) * W * G;
     for (int i = tid; i < total; i += kConvThreads) {
-      const int cg = i % G;
-      int rest = i / G;
+      int rest = G == 1 ? i : (int)__umulhi((uint32_t)i, g_magic);  // i / G
+      const int cg = i - rest * G;
       const int xx = rest % W;
       rest /= W;
       const int rr = rest % (R + 2), dzi = rest / (R + 2);
