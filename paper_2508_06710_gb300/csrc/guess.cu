@@ -1352,40 +1352,69 @@ __global__ void __launch_bounds__(256) k_up_dw(const bf16* __restrict__ x, int l
   const int nc = cx * cy * cz;
   const int n_w = cout * 8 * cin;
   const int n_out = n_w + cout;
+  const int gx = cin / 8, gg = cout / 8;  // 8-channel groups (channel counts are multiples of 8)
+  // output t + 256 r of this thread: (co, o, ci) with ci fastest, stepped from r = 0 (256 =
+  // q cin + s: ci advances by s, the (co, o) index by q, carrying)
+  const int step_q = 256 / cin, step_s = 256 - step_q * cin;
   float acc[kUpOut];
 #pragma unroll
   for (int r = 0; r < kUpOut; ++r) acc[r] = 0.0f;
   for (int c0 = blockIdx.x * kUpChunk; c0 < nc; c0 += gridDim.x * kUpChunk) {
     __syncthreads();
-    for (int i = threadIdx.x; i < kUpChunk * cin; i += blockDim.x) {
-      const int k = i / cin, ci = i - k * cin;
+    // 16-byte pieces: the chunk's coarse inputs, then for each cell and child o its gradient
+    for (int i = threadIdx.x; i < kUpChunk * gx; i += blockDim.x) {
+      const int k = i / gx, q = i - k * gx;
       const int v = c0 + k;
-      sx[i] = v < nc ? __bfloat162float(x[(size_t)v * ldx + ci]) : 0.0f;
+      float* d = sx + k * cin + q * 8;
+      if (v < nc) {
+        const uint4 u = *reinterpret_cast<const uint4*>(x + (size_t)v * ldx + q * 8);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(h[e]);
+          d[2 * e] = f.x, d[2 * e + 1] = f.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) d[e] = 0.0f;
+      }
     }
-    for (int i = threadIdx.x; i < kUpChunk * 8 * cout; i += blockDim.x) {
-      const int co = i % cout, r = i / cout, o = r % 8, k = r / 8;
+    for (int i = threadIdx.x; i < kUpChunk * 8 * gg; i += blockDim.x) {
+      const int q = i % gg, r = i / gg, o = r & 7, k = r >> 3;
       const int v = c0 + k;
-      float gv = 0.0f;
+      float* d = sg + (k * 8 + o) * cout + q * 8;
       if (v < nc) {
         const int xx = v % cx, rr = v / cx;
-        gv = __bfloat162float(gu[(size_t)fine_of(fine, xx, rr % cy, rr / cy, o) * ldg + co]);
+        const uint4 u = *reinterpret_cast<const uint4*>(gu + (size_t)fine_of(fine, xx, rr % cy, rr / cy, o) * ldg + q * 8);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(h[e]);
+          d[2 * e] = f.x, d[2 * e + 1] = f.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) d[e] = 0.0f;
       }
-      sg[i] = gv;
     }
     __syncthreads();
+    int ci = (int)threadIdx.x % cin, rest = (int)threadIdx.x / cin;  // output threadIdx.x (r = 0)
 #pragma unroll 4
     for (int r = 0; r < kUpOut; ++r) {
       const int idx = threadIdx.x + r * blockDim.x;
       if (idx >= n_out) break;
       float s = 0.0f;
       if (idx < n_w) {
-        const int ci = idx % cin, rr = idx / cin, o = rr % 8, co = rr / 8;
-        for (int k = 0; k < kUpChunk; ++k) s += sx[k * cin + ci] * sg[(k * 8 + o) * cout + co];
+        const int go = (rest & 7) * cout + (rest >> 3);  // child o = rest % 8, channel co = rest / 8
+        for (int k = 0; k < kUpChunk; ++k) s += sx[k * cin + ci] * sg[k * 8 * cout + go];
       } else {
         const int co = idx - n_w;
         for (int k = 0; k < kUpChunk * 8; ++k) s += sg[k * cout + co];
       }
       acc[r] += s;
+      ci += step_s;
+      rest += step_q;
+      if (ci >= cin) ci -= cin, ++rest;
     }
   }
   for (int r = 0; r < kUpOut; ++r) {
