@@ -367,6 +367,22 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chu
     return sL + (uint32_t)cg * kGroupBytes + (uint32_t)(dzi * 4 + (yy & 3)) * kLineBytes;
   };
   // the three z lines of row yy into ring slot yy & 3
+  // this thread's line positions (pos = tid, and tid + 128 for the last halo cells): the cell
+  // each copies (wrapped, or none past a wall) is the same for every line
+  constexpr int kPos = (kRowPos + kConvThreads - 1) / kConvThreads;
+  int p_off[kPos];
+  bool p_ok[kPos];
+#pragma unroll
+  for (int k = 0; k < kPos; ++k) {
+    const int pos = tid + k * kConvThreads;
+    int x = pos - 1;
+    p_ok[k] = pos < kRowPos;
+    if (x < 0 || x >= W) {
+      if (a.d.px) x = x < 0 ? x + W : x - W;
+      else p_ok[k] = false;
+    }
+    p_off[k] = x * a.ldx;
+  }
   auto load_row = [&](int z, int yy) {
     int yw = yy;
     bool yok = true;
@@ -381,23 +397,24 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chu
         if (a.d.pz) zz = zz < 0 ? zz + nz : zz - nz;
         else ok = false;
       }
-      const size_t row0 = ((size_t)zz * ny + yw) * W;
+      const bf16* row = a.x + ((size_t)zz * ny + yw) * W * a.ldx;
       for (int cg = 0; cg < G; ++cg) {
         const uint32_t dst = line_addr(cg, dzi, yy);
-        for (int pos = tid; pos < kRowPos; pos += kConvThreads) {
-          int x = pos - 1;
-          bool okx = ok;
-          if (x < 0 || x >= W) {
-            if (a.d.px) x = x < 0 ? x + W : x - W;
-            else okx = false;
-          }
-          cp_async16(dst + (uint32_t)pos * 16, okx ? (const void*)(a.x + (row0 + x) * a.ldx + cg * 8) : (const void*)a.x,
-                     okx ? 16u : 0u);
+#pragma unroll
+        for (int k = 0; k < kPos; ++k) {
+          if (tid + k * kConvThreads >= kRowPos) break;
+          const bool okx = ok && p_ok[k];
+          cp_async16(dst + (uint32_t)(tid + k * kConvThreads) * 16,
+                     okx ? (const void*)(row + p_off[k] + cg * 8) : (const void*)a.x, okx ? 16u : 0u);
         }
       }
     }
   };
 
+  // the biases of the output channels, once (zero without biases or past cout)
+  float bias_r[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) bias_r[i] = (a.bias && i < a.cout) ? __ldg(a.bias + i) : 0.0f;
   int fail = 0;
   int tcount = 0;  // tiles (rows) this CTA has issued: selects the accumulator and barrier phase
   auto epilogue = [&](int e, int z, int y) {
@@ -421,8 +438,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_row(Conv3Args a, int chu
         float o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          float val = acc[8 * h + i];
-          if (a.bias) val += __ldg(a.bias + cb + i);
+          float val = acc[8 * h + i] + bias_r[c0 + 8 * h + i];
           if (a.relu) val = fmaxf(val, 0.0f);
           o[i] = val;
         }
