@@ -44,14 +44,16 @@ def _layer_out(g, i, level_shape, c):
 # grids of 128-cell rows run the level-0 convolutions on the row kernel (x wrapped or walled);
 # levels whose rows are 16 or 32 cells (a multiple of 128 / W rows per plane) run the slab
 # kernel: 16x16x8 (level 0, W = 16), 128x16x8 (level 2, W = 32, walled x), 128x64x8 (levels
-# 2 and 3, W = 32 and 16, with the level-2 decoder and its input gradient at N = 192)
+# 2 and 3, W = 32 and 16, with the level-2 decoder and its input gradient at N = 192; x
+# wrapped and walled)
 CASES = [((16, 16, 8), (8, 16, 32, 48), (1, 1, 0)), ((10, 6, 6), (8, 16), (1, 1, 0)),
          ((8, 8, 8), (8, 16, 24), (1, 1, 0)), ((128, 4, 4), (8, 16), (1, 1, 0)),
          ((128, 8, 4), (8, 16, 32), (0, 1, 1)), ((128, 40, 16), (8, 16, 32, 48), (1, 1, 0)),
          ((64, 8, 4), (8, 16), (1, 1, 0)), ((128, 16, 8), (8, 16, 32), (0, 1, 1)),
-         ((128, 64, 8), (8, 16, 32, 48), (1, 1, 0))]
+         ((128, 64, 8), (8, 16, 32, 48), (1, 1, 0)), ((128, 64, 8), (8, 16, 32, 48), (0, 1, 1))]
 IDS = ["16x16x8-4lvl", "ragged-10x6x6", "8cube-3lvl", "rows128-periodic-x", "rows128-walled-x",
-       "rows128-40x16-4lvl", "rows64-level0", "rows128-then-64-walled-x", "slabs32-16-4lvl"]
+       "rows128-40x16-4lvl", "rows64-level0", "rows128-then-64-walled-x", "slabs32-16-4lvl",
+       "slabs32-16-4lvl-walled-x"]
 
 
 @pytest.mark.parametrize("shape,channels,periodic", CASES, ids=IDS)
