@@ -550,6 +550,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
   constexpr uint32_t kCols = tmem_cols_for(NT);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = a.cin / 8, ktot = stack_k(a.cin);
@@ -565,6 +566,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
 
   if (tid == 0) {
     mbar_init(&acc_bar, 1);
+    mbar_init(&drain_bar, 1);
     fence_barrier_init();
   }
   if (warp == 0) tmem_alloc(&tmem_slot, kCols);
@@ -709,6 +711,11 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3_slab(Conv3Args a, int pw
     tc_fence_before();  // this tile's TMEM reads precede the next tile's MMAs (next barrier)
   }
   cp_async_wait_all();
+  // every MMA this CTA issued has completed before TMEM is released (also after a wait gave up)
+  if (tid == 0) {
+    umma_commit(&drain_bar);
+    if (!mbar_wait(&drain_bar, 0)) fail = 1;
+  }
   if (fail && a.err) atomicExch(a.err, 1);
   tc_fence_before();
   __syncthreads();
