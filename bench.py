@@ -981,7 +981,8 @@ def time_events(torch, fn, reps):
 
 
 def poisson(torch, rb, ops, g, dev):
-    """Poisson solves to a 1e-10 true relative residual on b = M u (k = 3): FP64 CG vs FP32-inner refinement."""
+    """Poisson solves to a 1e-10 true relative residual on b = M u (k = 3): FP64 CG vs FP32-inner refinement
+    (inner operator: the FP32 CSR copy, or the matrix-free Laplacian)."""
     Aop, k = ops[("A", "f64")]
     A32, _ = ops[("A", "f32")]
     Mop, _ = ops[("M", "f64")]
@@ -989,8 +990,12 @@ def poisson(torch, rb, ops, g, dev):
     B = torch.empty((Mop.n_rows, k), dtype=torch.float64, device=dev)
     Mop.spmm(U, B, c=torch.full((k,), -1.0, dtype=torch.float64, device=dev))  # b = -M u
     out = {"k": k, "rtol": 1e-10}
-    for name, mixed, pers in (("fp64_cg", 0, False), ("ir_fp32_inner", 2, False),
-                              ("ir_fp32_inner_persistent", 2, True), ("ir_fp32_inner_restarted", 1, False)):
+    nodes, per = rb.grid_nodes(g, dev)
+    A32_mf = rb.Operator.stencil(nodes, per, scale=-1.0, dtype="f32", k_max=k)  # matrix-free inner operator
+    for name, mixed, pers, inner in (("fp64_cg", 0, False, None), ("ir_fp32_inner", 2, False, A32),
+                                     ("ir_fp32_inner_persistent", 2, True, A32),
+                                     ("ir_fp32_inner_restarted", 1, False, A32),
+                                     ("ir_fp32_inner_matrix_free", 2, False, A32_mf)):
         prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, check_every=50, persistent=pers)
         work = torch.empty(rb.cg_workspace_bytes(Aop, k, prm), dtype=torch.uint8, device=dev)
         times = []
@@ -998,7 +1003,7 @@ def poisson(torch, rb, ops, g, dev):
             X = torch.zeros((Mop.n_rows, k), dtype=torch.float64, device=dev)
             torch.cuda.synchronize()
             t = time.perf_counter()
-            r = rb.cg_solve(Aop, B, X, A_inner=A32 if mixed else None, params=prm, work=work)
+            r = rb.cg_solve(Aop, B, X, A_inner=inner, params=prm, work=work)
             torch.cuda.synchronize()
             times.append((time.perf_counter() - t) * 1e3)
         out[name] = {"ms": min(times), "iters": r.iters, "true_rel_res": r.true_rel_res, "status": r.status,

@@ -24,6 +24,7 @@
 #include "common.cuh"
 #include "reduce.cuh"
 #include "spmm_impl.cuh"
+#include "stencil7.cuh"
 
 namespace rb {
 
@@ -267,6 +268,44 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(CgCtl ctl, const T* __restric
 // alpha uses the exact r . z of the previous update; only beta uses the identity (the
 // single-reduction recurrence of pipelined CG on GPUs, e.g. Rupp et al.'s fused CG).
 
+// The q = A p kernels' common end: the block's sums of p . q and q . D^-1 q per column, then,
+// in the last block, alpha and beta per column from the totals (see above)
+template <typename T, int VEC, int LPR>
+__device__ __forceinline__ void q2_tail(DotAccN<T, 2 * VEC>& dacc, bool lead, int kp, int k, const CgCtl& ctl,
+                                        CgScal* __restrict__ sc, double* __restrict__ partials, RedSmem<2>& red) {
+  T part[2][VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    part[0][e] = lead ? dacc.get(e) : T(0);
+    part[1][e] = lead ? dacc.get(VEC + e) : T(0);
+  }
+  const double v = block_reduce<2, VEC>(part, kp, LPR, k, red);
+  if (!publish_partials<2>(v, 2 * k, partials, &sc->counter[6], red)) return;
+  const double tot = final_sum<2>(partials, 2 * k, gridDim.x, red);
+  __shared__ double totals[2 * K];
+  if ((int)threadIdx.x < 2 * k) totals[threadIdx.x] = tot;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < k) {
+    const double pq = totals[j], qdq = totals[k + j];
+    sc->pq[j] = pq;
+    double al = 0.0, be = 0.0;
+    if (sc->state[j] == ST_ACTIVE) {
+      if (!(pq > 0.0) || !isfinite(pq) || !isfinite(qdq)) {
+        sc->state[j] = ctl.inner ? ST_DONE : ST_BREAKDOWN;
+      } else {
+        al = sc->rz[j] / pq;
+        const double b = sc->rz[j] * qdq / (pq * pq) - 1.0;
+        be = (b > 0.0 && isfinite(b)) ? b : 0.0;
+      }
+    }
+    sc->alpha[j] = al;
+    sc->beta[j] = be;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) recount(sc, k);
+}
+
 template <typename T, int VEC, int LPR>
 __global__ void __launch_bounds__(kThreads) k_cg_q2(CsrArgs<T> a, CgCtl ctl, const T* __restrict__ dinv,
                                                      CgScal* __restrict__ sc, double* __restrict__ partials) {
@@ -297,37 +336,40 @@ __global__ void __launch_bounds__(kThreads) k_cg_q2(CsrArgs<T> a, CgCtl ctl, con
       stv<T, VEC>(a.Y + row * a.ldy + chunk * VEC, q);
     }
   }
-  T part[2][VEC];
+  q2_tail<T, VEC, LPR>(dacc, sub == 0, a.kp, a.k, ctl, sc, partials, red);
+}
+
+// q = A p with the matrix-free FP32 Laplacian (stencil7.cuh: no index or value streams) and
+// the same sums as k_cg_q2; p and q have leading dimension k
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads) k_cg_q2_st(Stencil7<T> st, CgCtl ctl, const T* __restrict__ p,
+                                                        T* __restrict__ q, const T* __restrict__ dinv,
+                                                        CgScal* __restrict__ sc, double* __restrict__ partials) {
+  if (sc->n_active == 0) return;
+  __shared__ RedSmem<2> red;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp, rloc = threadIdx.x / kp;
+  DotAccN<T, 2 * VEC> dacc;  // [0, VEC): p . q, [VEC, 2 VEC): q . D^-1 q
+  const int64_t stride = (int64_t)gridDim.x * R;
+  for (int64_t base = (int64_t)blockIdx.x * R; base < ctl.n; base += stride) {
+    const int64_t row = base + rloc;
+    if (row < ctl.n && chunk * VEC < k) {
+      T acc[VEC], unused;
+      stencil7_apply<T, VEC>(st, p, k, row, chunk * VEC, acc, unused);
+      const Vec<T, VEC> pv = ldv<T, VEC>(p + row * k + chunk * VEC);
+      const T d = dinv ? dinv[row] : T(1);
+      Vec<T, VEC> qv;
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) {
-    part[0][e] = (sub == 0) ? dacc.get(e) : T(0);
-    part[1][e] = (sub == 0) ? dacc.get(VEC + e) : T(0);
-  }
-  const double v = block_reduce<2, VEC>(part, a.kp, LPR, a.k, red);
-  if (!publish_partials<2>(v, 2 * a.k, partials, &sc->counter[6], red)) return;
-  const double tot = final_sum<2>(partials, 2 * a.k, gridDim.x, red);
-  __shared__ double totals[2 * K];
-  if ((int)threadIdx.x < 2 * a.k) totals[threadIdx.x] = tot;
-  __syncthreads();
-  const int j = threadIdx.x;
-  if (j < a.k) {
-    const double pq = totals[j], qdq = totals[a.k + j];
-    sc->pq[j] = pq;
-    double al = 0.0, be = 0.0;
-    if (sc->state[j] == ST_ACTIVE) {
-      if (!(pq > 0.0) || !isfinite(pq) || !isfinite(qdq)) {
-        sc->state[j] = ctl.inner ? ST_DONE : ST_BREAKDOWN;
-      } else {
-        al = sc->rz[j] / pq;
-        const double b = sc->rz[j] * qdq / (pq * pq) - 1.0;
-        be = (b > 0.0 && isfinite(b)) ? b : 0.0;
+      for (int e = 0; e < VEC; ++e) {
+        qv.v[e] = acc[e];
+        dacc.add(e, pv.v[e], acc[e]);
+        dacc.add(VEC + e, acc[e], d * acc[e]);
       }
+      stv<T, VEC>(q + row * k + chunk * VEC, qv);
     }
-    sc->alpha[j] = al;
-    sc->beta[j] = be;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) recount(sc, a.k);
+  q2_tail<T, VEC, 1>(dacc, true, kp, k, ctl, sc, partials, red);
 }
 
 template <typename T, int VEC>
@@ -854,6 +896,21 @@ struct Solver {
 
   template <typename T, int VEC>
   void launch_q2_lpr(const rb_op* op, const SpmmSched& ss, const T* p, T* q, const T* dinv, CgCtl c) const {
+    if constexpr (sizeof(T) == 4) {
+      if (op->format == RB_STENCIL) {  // the matrix-free inner operator
+        Stencil7<float> st{};
+        for (int d = 0; d < 3; ++d) {
+          st.n[d] = op->st_n[d];
+          st.per[d] = op->st_per[d];
+          st.w[d] = static_cast<const float*>(op->st_w[d]);
+          st.ic[d] = static_cast<const float*>(op->st_ic[d]);
+        }
+        st.scale = (float)op->st_scale;
+        st.init_div();
+        k_cg_q2_st<T, VEC><<<vg(&k_cg_q2_st<T, VEC>), kThreads, 0, s>>>(st, c, p, q, dinv, sc, partials);
+        return;
+      }
+    }
     switch (ss.lpr) {
       case 2: launch_q2<T, VEC, 2>(op, ss, p, q, dinv, c); break;
       case 4: launch_q2<T, VEC, 4>(op, ss, p, q, dinv, c); break;
@@ -1568,7 +1625,8 @@ rb_status validate_solve(const char* fn, rb_op_t A, rb_op_t A_inner, const rb_cg
   if (prm.mixed) {
     RB_REQUIRE(A_inner && A_inner->dtype == RB_F32 && A_inner->n_rows == A->n_rows && A_inner->nnz == A->nnz,
                "%s: mixed precision needs A_inner, the same matrix stored as RB_F32", fn);
-    RB_REQUIRE(A_inner->format == RB_CSR, "%s: the inner operator must be CSR", fn);
+    RB_REQUIRE(A_inner->format == RB_CSR || (A_inner->format == RB_STENCIL && !prm.persistent),
+               "%s: the inner operator must be CSR, or matrix-free (RB_STENCIL) without persistent", fn);
     RB_REQUIRE(prm.inner_rtol > 0 && prm.inner_rtol < 1, "%s: inner_rtol must be in (0, 1)", fn);
     RB_REQUIRE(prm.max_sweeps >= 1, "%s: max_sweeps >= 1 required", fn);
   }
@@ -1821,6 +1879,7 @@ extern "C" rb_status rb_batch_create(int32_t n_sys, const rb_op_t* ops, const rb
     RB_TRY(validate_solve("rb_batch_create", ops[i], ops_inner[i], *params, reinterpret_cast<const double*>(8),
                           k[i], reinterpret_cast<const double*>(8), k[i], k[i]));
     RB_REQUIRE(ops[i]->n_rows > 0, "rb_batch_create: system %d is empty", i);
+    RB_REQUIRE(ops_inner[i]->format == RB_CSR, "rb_batch_create: system %d: the inner operator must be CSR", i);
     cols += k[i];
   }
   RB_REQUIRE(cols <= RB_MAX_K, "rb_batch_create: %d columns in total exceed %d", cols, RB_MAX_K);

@@ -84,6 +84,34 @@ def test_cg_channel_stretched(rb, mixed):
             assert res.iters[j] <= 1.3 * infos[j].iters
 
 
+@pytest.mark.parametrize("case", ["channel", "periodic"])
+@pytest.mark.parametrize("k", [1, 3])
+@pytest.mark.parametrize("mixed", [1, 2])
+def test_cg_matrix_free_inner_operator(rb, case, k, mixed):
+    """The refinement with the matrix-free FP32 Laplacian (RB_STENCIL) as the inner operator:
+    the same true 1e-10 residual and the oracle's solution; the persistent inner solve and the
+    batch, which read CSR arrays, refuse it."""
+    g = W.channel_grid(40, 32, 24, gamma=1.5) if case == "channel" else W.unit_periodic_grid(24)
+    A = _poisson(g)
+    B = W.zero_mean(W.normal((A.shape[0], k), W.seed_for(11, k)))
+    op = rb.Operator.from_scipy(A, k_max=k)
+    nodes, per = rb.grid_nodes(g)
+    opi = rb.Operator.stencil(nodes, per, scale=-1.0, dtype="f32", k_max=k)
+    X = to_dev(np.zeros_like(B))
+    res = rb.cg_solve(op, to_dev(B), X, A_inner=opi, params=rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True))
+    assert res.status == rb.RB_OK, res
+    Xh = X.cpu().numpy()
+    assert np.all(_true_res(A, B, Xh) <= 1e-10)
+    Xr, _ = ocg.pcg_columns(A, B, rtol=1e-10, project_mean=True)
+    assert np.all(np.linalg.norm(Xh - Xr, axis=0) <= 1e-6 * np.linalg.norm(Xr, axis=0))
+    # the same solve with the CSR inner operator takes about as many iterations
+    ref, _ = _solve(rb, A, B, mixed=mixed)
+    assert all(abs(a - b) <= max(5, b // 10) for a, b in zip(res.iters, ref.iters)), (res.iters, ref.iters)
+    with pytest.raises(rb.RbError) as e:
+        rb.cg_solve(op, to_dev(B), X, A_inner=opi, params=rb.cg_params(mixed=mixed, persistent=1, project_mean=True))
+    assert e.value.status == rb.RB_EINVAL
+
+
 @pytest.mark.parametrize("k", [33, 64])
 @pytest.mark.parametrize("mixed", [0, 2])
 def test_cg_wide_blocks(rb, k, mixed):
