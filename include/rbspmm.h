@@ -376,7 +376,9 @@ typedef struct {
 size_t rb_cg_workspace_bytes(rb_op_t A, int32_t k, const rb_cg_params* params);
 
 /* Solves A x_j = b_j for the k columns.  A: square FP64 operator with a diagonal.
- * A_inner: the same matrix stored as RB_F32, required when params->mixed (else NULL).
+ * A_inner: the same matrix stored as RB_F32, required when params->mixed (else NULL): a CSR
+ * copy, or the matrix-free Laplacian of the same grid (rb_fvm_stencil_create, RB_F32, the same
+ * scale), whose inner iterations read no matrix; the persistent inner solve takes CSR only.
  * B (n x k, ldb), X (n x k, ldx; in: initial guess, out: solution): float64 DEVICE.
  * work: device scratch of rb_cg_workspace_bytes bytes.  Synchronises `stream` (the host
  * reads the per-column state every check_every iterations).  Returns the worst column
