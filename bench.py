@@ -682,8 +682,9 @@ def batch_bench(torch, rb, dev):
         rp, ci, va, nc = rb.fvm_assemble(nodes, per, rb.RB_FVM_LAPLACIAN, scale=-1.0)
         A64 = rb.Operator(rp, ci, va, nc, dtype="f64", k_max=k)
         A32 = rb.Operator(rp, ci, va, nc, dtype="f32", k_max=k)
+        A32_mf = rb.Operator.stencil(nodes, per, scale=-1.0, dtype="f32", k_max=k)
         B = torch.as_tensor(W.zero_mean(W.normal((g.n_cells, k), W.seed_for(4, k, salt=len(systems)))), device=dev)
-        systems.append((g, k, A64, A32, B))
+        systems.append((g, k, A64, A32, B, A32_mf))
     prm = rb.cg_params(rtol=1e-10, mixed=2, project_mean=True, max_sweeps=16)
     batch = rb.Batch([s[2] for s in systems], [s[3] for s in systems], [s[1] for s in systems], prm)
     Bs = [s[4] for s in systems]
@@ -701,11 +702,26 @@ def batch_bench(torch, rb, dev):
 
     run_batch()
     t_batch, rep = min((run_batch() for _ in range(3)), key=lambda x: x[0])
+    # the same batch with the matrix-free inner operators (no matrix streams in the inner solve)
+    batch_mf = rb.Batch([s[2] for s in systems], [s[5] for s in systems], [s[1] for s in systems], prm)
+    batch_mf.tune(Bs, Xs)
+
+    def run_batch_mf():
+        for x in Xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = batch_mf.solve(Bs, Xs)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3, r
+
+    run_batch_mf()
+    t_batch_mf, rep_mf = min((run_batch_mf() for _ in range(3)), key=lambda x: x[0])
 
     def run_seq(mixed):
         t = 0.0
         its = []
-        for g, k, A64, A32, B in systems:
+        for g, k, A64, A32, B, _ in systems:
             X = torch.zeros_like(B)
             p = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, check_every=50)
             w = torch.empty(rb.cg_workspace_bytes(A64, k, p), dtype=torch.uint8, device=dev)
@@ -721,7 +737,9 @@ def batch_bench(torch, rb, dev):
     t_seq_ir, it_seq = min((run_seq(2) for _ in range(2)), key=lambda x: x[0])
     t_seq_64, it_64 = min((run_seq(0) for _ in range(2)), key=lambda x: x[0])
     return {"systems": [{"grid": g.name, "n": g.n_cells, "k": k} for g, k, *_ in systems],
-            "batch_graph_ms": t_batch, "tuned_ms": tuned_ms, "sequential_ir_ms": t_seq_ir,
+            "batch_graph_ms": t_batch, "tuned_ms": tuned_ms, "batch_graph_matrix_free_ms": t_batch_mf,
+            "batch_matrix_free_true_rel_res": [max(r.true_rel_res) for r in rep_mf],
+            "batch_matrix_free_status": [r.status for r in rep_mf], "sequential_ir_ms": t_seq_ir,
             "sequential_fp64_cg_ms": t_seq_64, "speedup_vs_sequential_ir": t_seq_ir / t_batch,
             "speedup_vs_fp64_cg": t_seq_64 / t_batch, "batch_iters": [r.iters for r in rep],
             "batch_true_rel_res": [max(r.true_rel_res) for r in rep], "batch_status": [r.status for r in rep],
@@ -1297,6 +1315,7 @@ def headline(out, detail_path):
     b = out.get("batch")
     if b:
         s["batch_graph_ms"] = b.get("batch_graph_ms")
+        s["batch_graph_matrix_free_ms"] = b.get("batch_graph_matrix_free_ms")
         s["batch_sequential_fp64_cg_ms"] = b.get("sequential_fp64_cg_ms")
     lg = out.get("learned_guess")
     if lg and "eval" in lg:

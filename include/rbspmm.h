@@ -378,7 +378,7 @@ size_t rb_cg_workspace_bytes(rb_op_t A, int32_t k, const rb_cg_params* params);
 /* Solves A x_j = b_j for the k columns.  A: square FP64 operator with a diagonal.
  * A_inner: the same matrix stored as RB_F32, required when params->mixed (else NULL): a CSR
  * copy, or the matrix-free Laplacian of the same grid (rb_fvm_stencil_create, RB_F32, the same
- * scale), whose inner iterations read no matrix; the persistent inner solve takes CSR only.
+ * scale), whose inner iterations read no matrix.
  * B (n x k, ldb), X (n x k, ldx; in: initial guess, out: solution): float64 DEVICE.
  * work: device scratch of rb_cg_workspace_bytes bytes.  Synchronises `stream` (the host
  * reads the per-column state every check_every iterations).  Returns the worst column
@@ -403,7 +403,8 @@ rb_status rb_cg_solve(rb_op_t A, rb_op_t A_inner, const rb_cg_params* params, co
 typedef struct rb_batch* rb_batch_t;
 
 /* Allocates the per-system workspaces and the launch state.  n_sys <= 8, sum of k <= 64,
- * every ops[s] square RB_F64 CSR with a diagonal, ops_inner[s] its RB_F32 copy. */
+ * every ops[s] square RB_F64 CSR with a diagonal, ops_inner[s] its RB_F32 copy (CSR, or the
+ * matrix-free Laplacian of the same grid as for rb_cg_solve). */
 rb_status rb_batch_create(int32_t n_sys, const rb_op_t* ops, const rb_op_t* ops_inner, const int32_t* k,
                           const rb_cg_params* params, rb_batch_t* out);
 rb_status rb_batch_destroy(rb_batch_t batch);

@@ -1175,9 +1175,11 @@ constexpr int kPThreads = 512;
 constexpr int kPWarps = kPThreads / 32;
 
 struct PSys {
-  const int32_t* rp;
+  const int32_t* rp;  // CSR inner operator, or
   const int32_t* ci;
   const float* va;
+  Stencil7<float> st;  // the matrix-free one (mf = 1)
+  int mf;
   const float* dinv;
   float* r;
   float* p;
@@ -1290,7 +1292,12 @@ __device__ void pphase_q(const PBatch& b, const PSys& S, double* red, double* ou
     float acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = 0.f;
-    row_accumulate_direct<float, VEC, 1, true>(a, row, chunk, 0, active, acc);
+    if (S.mf) {  // p is written by other blocks of this launch: coherent loads
+      float unused;
+      if (active) stencil7_apply<float, VEC, true>(S.st, S.p, S.k, row, chunk * VEC, acc, unused);
+    } else {
+      row_accumulate_direct<float, VEC, 1, true>(a, row, chunk, 0, active, acc);
+    }
     if (active) {
       const Vec<float, VEC> p = ldv_cg<float, VEC>(S.p + row * S.k + chunk * VEC);
       const float dg = S.dinv ? S.dinv[row] : 1.f;
@@ -1625,8 +1632,8 @@ rb_status validate_solve(const char* fn, rb_op_t A, rb_op_t A_inner, const rb_cg
   if (prm.mixed) {
     RB_REQUIRE(A_inner && A_inner->dtype == RB_F32 && A_inner->n_rows == A->n_rows && A_inner->nnz == A->nnz,
                "%s: mixed precision needs A_inner, the same matrix stored as RB_F32", fn);
-    RB_REQUIRE(A_inner->format == RB_CSR || (A_inner->format == RB_STENCIL && !prm.persistent),
-               "%s: the inner operator must be CSR, or matrix-free (RB_STENCIL) without persistent", fn);
+    RB_REQUIRE(A_inner->format == RB_CSR || A_inner->format == RB_STENCIL,
+               "%s: the inner operator must be CSR or matrix-free (RB_STENCIL)", fn);
     RB_REQUIRE(prm.inner_rtol > 0 && prm.inner_rtol < 1, "%s: inner_rtol must be in (0, 1)", fn);
     RB_REQUIRE(prm.max_sweeps >= 1, "%s: max_sweeps >= 1 required", fn);
   }
@@ -1671,10 +1678,21 @@ rb_status init_solver(Solver& S_, rb_op_t A, rb_op_t A_inner, const rb_cg_params
 }
 
 PSys make_psys(const Solver& S_, const Layout& L, char* base, bool precond) {
-  PSys p;
+  PSys p{};
   p.rp = S_.A32->row_ptr;
   p.ci = S_.A32->col_idx;
   p.va = static_cast<const float*>(S_.A32->vals);
+  p.mf = S_.A32->format == RB_STENCIL ? 1 : 0;
+  if (p.mf) {
+    for (int d = 0; d < 3; ++d) {
+      p.st.n[d] = S_.A32->st_n[d];
+      p.st.per[d] = S_.A32->st_per[d];
+      p.st.w[d] = static_cast<const float*>(S_.A32->st_w[d]);
+      p.st.ic[d] = static_cast<const float*>(S_.A32->st_ic[d]);
+    }
+    p.st.scale = (float)S_.A32->st_scale;
+    p.st.init_div();
+  }
   p.dinv = precond ? S_.A32->dinv32 : nullptr;
   p.r = reinterpret_cast<float*>(base + L.r32);
   p.p = reinterpret_cast<float*>(base + L.p32);
@@ -1879,7 +1897,6 @@ extern "C" rb_status rb_batch_create(int32_t n_sys, const rb_op_t* ops, const rb
     RB_TRY(validate_solve("rb_batch_create", ops[i], ops_inner[i], *params, reinterpret_cast<const double*>(8),
                           k[i], reinterpret_cast<const double*>(8), k[i], k[i]));
     RB_REQUIRE(ops[i]->n_rows > 0, "rb_batch_create: system %d is empty", i);
-    RB_REQUIRE(ops_inner[i]->format == RB_CSR, "rb_batch_create: system %d: the inner operator must be CSR", i);
     cols += k[i];
   }
   RB_REQUIRE(cols <= RB_MAX_K, "rb_batch_create: %d columns in total exceed %d", cols, RB_MAX_K);

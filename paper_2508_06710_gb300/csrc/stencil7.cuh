@@ -84,7 +84,8 @@ __device__ __forceinline__ Coef7<T> stencil7_coef(const Stencil7<T>& s, int64_t 
 }
 
 // (A X)[row, col0 .. col0 + VEC) into acc, and the inverse diagonal of A into dinv.
-template <typename T, int VEC>
+// COHERENT: X read through L2 only (X written by other blocks of the same launch).
+template <typename T, int VEC, bool COHERENT = false>
 __device__ __forceinline__ void stencil7_apply(const Stencil7<T>& s, const T* __restrict__ X, int64_t ldx, int64_t row,
                                                int col0, T (&acc)[VEC], T& dinv) {
   const Coef7<T> cf = stencil7_coef(s, row);
@@ -99,13 +100,14 @@ __device__ __forceinline__ void stencil7_apply(const Stencil7<T>& s, const T* __
   const int nz = s.n[2];
   const int km = k > 0 ? k - 1 : (s.per[2] ? nz - 1 : k), kp = k + 1 < nz ? k + 1 : (s.per[2] ? 0 : k);
   const T* xc = X + col0;
-  const Vec<T, VEC> x0 = ldv<T, VEC>(xc + row * ldx);
-  const Vec<T, VEC> a = ldv<T, VEC>(xc + (row - i + im) * ldx);
-  const Vec<T, VEC> b = ldv<T, VEC>(xc + (row - i + ip) * ldx);
-  const Vec<T, VEC> c = ldv<T, VEC>(xc + (row + (int64_t)(jm - j) * nx) * ldx);
-  const Vec<T, VEC> d = ldv<T, VEC>(xc + (row + (int64_t)(jp - j) * nx) * ldx);
-  const Vec<T, VEC> e = ldv<T, VEC>(xc + (row + (int64_t)(km - k) * plane) * ldx);
-  const Vec<T, VEC> f = ldv<T, VEC>(xc + (row + (int64_t)(kp - k) * plane) * ldx);
+  auto ld = [&](int64_t r) { return COHERENT ? ldv_cg<T, VEC>(xc + r * ldx) : ldv<T, VEC>(xc + r * ldx); };
+  const Vec<T, VEC> x0 = ld(row);
+  const Vec<T, VEC> a = ld(row - i + im);
+  const Vec<T, VEC> b = ld(row - i + ip);
+  const Vec<T, VEC> c = ld(row + (int64_t)(jm - j) * nx);
+  const Vec<T, VEC> d = ld(row + (int64_t)(jp - j) * nx);
+  const Vec<T, VEC> e = ld(row + (int64_t)(km - k) * plane);
+  const Vec<T, VEC> f = ld(row + (int64_t)(kp - k) * plane);
 #pragma unroll
   for (int q = 0; q < VEC; ++q) {
     T y = diag * x0.v[q];

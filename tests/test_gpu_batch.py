@@ -30,22 +30,27 @@ SYSTEMS = [(W.unit_periodic_grid(16), 2, 11), (W.channel_grid(20, 16, 12, gamma=
            (W.unit_periodic_grid(8), 1, 13), (W.channel_grid(12, 9, 7, gamma=1.4), 4, 14)]
 
 
-def _make(rb, systems, mixed=2):
+def _make(rb, systems, mixed=2, inner="csr"):
     ops, ops32, Bs, As = [], [], [], []
     for g, k, seed in systems:
         A, B = _system(g, k, seed)
         As.append(A)
         Bs.append(B)
         ops.append(rb.Operator.from_scipy(A, k_max=k))
-        ops32.append(rb.Operator.from_scipy(A, dtype="f32", k_max=k))
+        if inner == "csr":
+            ops32.append(rb.Operator.from_scipy(A, dtype="f32", k_max=k))
+        else:  # the matrix-free FP32 Laplacian of the same grid
+            nodes, per = rb.grid_nodes(g)
+            ops32.append(rb.Operator.stencil(nodes, per, scale=-1.0, dtype="f32", k_max=k))
     prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, max_sweeps=16)
     batch = rb.Batch(ops, ops32, [s[1] for s in systems], prm)
     return batch, As, Bs
 
 
+@pytest.mark.parametrize("inner", ["csr", "matrix_free"])
 @pytest.mark.parametrize("mixed", [1, 2])
-def test_batch_matches_oracle_and_replays(rb, mixed):
-    batch, As, Bs = _make(rb, SYSTEMS, mixed)
+def test_batch_matches_oracle_and_replays(rb, mixed, inner):
+    batch, As, Bs = _make(rb, SYSTEMS, mixed, inner)
     Bd = [to_dev(B) for B in Bs]
     Xd = [torch.zeros_like(b) for b in Bd]
     res = batch.solve(Bd, Xd)
