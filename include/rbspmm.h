@@ -243,8 +243,9 @@ rb_status rb_operator_create(const rb_csr_desc* csr, const rb_block_desc* block,
  * V_ijk c_nb with V = w_x w_y w_z and per-axis tables c = ic / w formed in FP64 and split, the
  * products and sums in double-float arithmetic).  The handle works with rb_spmm, rb_tune_spmm,
  * rb_operator_info/check/destroy and every call built on rb_spmm (e.g. rb_galerkin_guess); the
- * CG solves take CSR operators only.  grid as for rb_fvm_assemble (DEVICE nodes).  Allocates;
- * synchronises `stream`. */
+ * CG solves take it (RB_F32) as their inner operator (A_inner of rb_cg_solve, ops_inner of
+ * rb_batch_create) and their FP64 operator as CSR.  grid as for rb_fvm_assemble (DEVICE nodes).
+ * Allocates; synchronises `stream`. */
 rb_status rb_fvm_stencil_create(const rb_grid_desc* grid, double scale, rb_dtype dtype, int32_t k_max,
                                 rb_stream_t stream, rb_op_t* out);
 

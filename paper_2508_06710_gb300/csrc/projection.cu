@@ -250,7 +250,8 @@ extern "C" rb_status rb_projection_create(const rb_grid_desc* grid, const rb_pro
     }
   } else if (st == RB_OK) {
     T(make_op(grid, RB_FVM_LAPLACIAN, -1.0, RB_F64, m, s, &p->A));
-    if (st == RB_OK && p->prm.mixed) T(make_op(grid, RB_FVM_LAPLACIAN, -1.0, RB_F32, m, s, &p->A32));
+    // the inner FP32 solve on the matrix-free Laplacian (no matrix streams in its iterations)
+    if (st == RB_OK && p->prm.mixed) T(rb_fvm_stencil_create(grid, -1.0, RB_F32, m, stream, &p->A32));
     if (st == RB_OK) {
       p->work_bytes = rb_cg_workspace_bytes(p->A, m, &p->prm);
       if (p->work_bytes && cudaMalloc(&p->work, p->work_bytes) != cudaSuccess) {
