@@ -1487,13 +1487,15 @@ def profile_run(args):
         Aop, _ = ops[("A", "f64")]
         A32, _ = ops[("A", "f32")]
         Mop, _ = ops[("M", "f64")]
+        nodes, per = rb.grid_nodes(g, dev)
+        A32_mf = rb.Operator.stencil(nodes, per, scale=-1.0, dtype="f32", k_max=3)
         for k in (1, 3):
             U = torch.as_tensor(W.face_field(Mop.n_cols, k, 2002), device=dev)
             B = Mop.spmm(U, c=torch.full((k,), -1.0, dtype=torch.float64, device=dev))
-            for mixed in (False, True):
+            for mixed, inner in ((False, None), (True, A32), (True, A32_mf)):
                 prm = rb.cg_params(rtol=1e-10, mixed=mixed, project_mean=True, max_iter=20, check_every=10)
                 X = torch.zeros((Mop.n_rows, k), dtype=torch.float64, device=dev)
-                rb.cg_solve(Aop, B, X, A_inner=A32 if mixed else None, params=prm)
+                rb.cg_solve(Aop, B, X, A_inner=inner, params=prm)
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "ok": True}))
 

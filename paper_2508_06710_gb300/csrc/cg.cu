@@ -339,6 +339,39 @@ __global__ void __launch_bounds__(kThreads) k_cg_q2(CsrArgs<T> a, CgCtl ctl, con
   q2_tail<T, VEC, LPR>(dacc, sub == 0, a.kp, a.k, ctl, sc, partials, red);
 }
 
+// The same on runs of RUN consecutive cells along x (n_x a multiple of RUN; stencil7_apply_run):
+// the y and z factors once per run, the centre values of p reused for p . q.  CONTIG: p and q
+// rows hold exactly VEC columns (k = VEC), moved as 16-byte vectors.
+template <typename T, int VEC, int RUN, bool CONTIG>
+__global__ void __launch_bounds__(kThreads) k_cg_q2_run(Stencil7<T> st, FastDiv drun, FastDiv drow, int64_t n_runs,
+                                                         CgCtl ctl, const T* __restrict__ p, T* __restrict__ q,
+                                                         const T* __restrict__ dinv, CgScal* __restrict__ sc,
+                                                         double* __restrict__ partials) {
+  if (sc->n_active == 0) return;
+  __shared__ RedSmem<2> red;
+  const int k = ctl.k, kp = ctl.kp;
+  const int R = kThreads / kp;
+  const int chunk = threadIdx.x % kp;
+  DotAccN<T, 2 * VEC> dacc;  // [0, VEC): p . q, [VEC, 2 VEC): q . D^-1 q
+  if (chunk * VEC < k) {
+    for (int64_t u = (int64_t)blockIdx.x * R + threadIdx.x / kp; u < n_runs; u += (int64_t)gridDim.x * R) {
+      Vec<T, VEC> pv[RUN], qv[RUN];
+      const int64_t row0 = stencil7_apply_run<T, VEC, RUN, CONTIG>(st, drun, drow, u, p + chunk * VEC, k, pv, qv);
+#pragma unroll
+      for (int c = 0; c < RUN; ++c) {
+        const T d = dinv ? dinv[row0 + c] : T(1);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          dacc.add(e, pv[c].v[e], qv[c].v[e]);
+          dacc.add(VEC + e, qv[c].v[e], d * qv[c].v[e]);
+        }
+      }
+      store_run<T, VEC, RUN, CONTIG>(q + row0 * k + chunk * VEC, k, qv);
+    }
+  }
+  q2_tail<T, VEC, 1>(dacc, true, kp, k, ctl, sc, partials, red);
+}
+
 // q = A p with the matrix-free FP32 Laplacian (stencil7.cuh: no index or value streams) and
 // the same sums as k_cg_q2; p and q have leading dimension k
 template <typename T, int VEC>
@@ -907,6 +940,21 @@ struct Solver {
         }
         st.scale = (float)op->st_scale;
         st.init_div();
+        constexpr int RUN = 4;
+        if (op->st_n[0] % RUN == 0) {  // runs of four cells along x
+          const int64_t n_runs = n / RUN;
+          FastDiv drun, drow;
+          drun.init((uint32_t)(op->st_n[0] / RUN));
+          drow.init((uint32_t)op->st_n[1]);
+          const bool contig = kp == 1 && k == VEC && ((uintptr_t)p % 16) == 0 && ((uintptr_t)q % 16) == 0;
+          auto go = [&](auto kern) {
+            kern<<<wave_grid(kern, (n_runs + kThreads / kp - 1) / (kThreads / kp)), kThreads, 0, s>>>(
+                st, drun, drow, n_runs, c, p, q, dinv, sc, partials);
+          };
+          if (contig) go(&k_cg_q2_run<T, VEC, RUN, true>);
+          else go(&k_cg_q2_run<T, VEC, RUN, false>);
+          return;
+        }
         k_cg_q2_st<T, VEC><<<vg(&k_cg_q2_st<T, VEC>), kThreads, 0, s>>>(st, c, p, q, dinv, sc, partials);
         return;
       }

@@ -19,6 +19,8 @@
 //             homogeneous Neumann condition); on a periodic axis face n[d] is face 0
 #pragma once
 
+#include <cstring>
+
 #include "common.cuh"
 
 namespace rb {
@@ -119,6 +121,111 @@ __device__ __forceinline__ void stencil7_apply(const Stencil7<T>& s, const T* __
     y = fma(czp, f.v[q], y);
     acc[q] = s.scale * y;
   }
+}
+
+// A run of RUN consecutive cells along x (n_x a multiple of RUN): the row split, the y and z
+// factors and the neighbour base addresses are formed once per run, and the x neighbours inside
+// the run come from registers.  CONTIG: X rows hold exactly the k = VEC columns (ld = VEC,
+// 16-byte aligned bases), so a run of RUN * VEC values moves as 16-byte vectors.
+template <typename T, int VEC, int RUN, bool CONTIG>
+__device__ __forceinline__ void load_run(const T* __restrict__ p, int64_t ldx, Vec<T, VEC> (&v)[RUN]) {
+  if constexpr (CONTIG && (sizeof(T) * VEC * RUN) % 16 == 0) {
+    constexpr int NV = sizeof(T) * VEC * RUN / 16;
+    T buf[VEC * RUN];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
+      memcpy(reinterpret_cast<char*>(buf) + 16 * q, &f, 16);
+    }
+#pragma unroll
+    for (int c = 0; c < RUN; ++c)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) v[c].v[q] = buf[c * VEC + q];
+  } else {
+#pragma unroll
+    for (int c = 0; c < RUN; ++c) v[c] = ldv<T, VEC>(p + (int64_t)c * ldx);
+  }
+}
+
+template <typename T, int VEC, int RUN, bool CONTIG>
+__device__ __forceinline__ void store_run(T* __restrict__ p, int64_t ldy, const Vec<T, VEC> (&y)[RUN]) {
+  if constexpr (CONTIG && (sizeof(T) * VEC * RUN) % 16 == 0) {
+    constexpr int NV = sizeof(T) * VEC * RUN / 16;
+    T buf[VEC * RUN];
+#pragma unroll
+    for (int c = 0; c < RUN; ++c)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) buf[c * VEC + q] = y[c].v[q];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      float4 f;
+      memcpy(&f, reinterpret_cast<char*>(buf) + 16 * q, 16);
+      reinterpret_cast<float4*>(p)[q] = f;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < RUN; ++c) stv<T, VEC>(p + (int64_t)c * ldy, y[c]);
+  }
+}
+
+// (A X) for the RUN cells of run u (u = i0 / RUN + (n_x / RUN)(j + n_y k); drun divides by
+// n_x / RUN, drow by n_y), columns xc .. xc + VEC: the centre values into x0, the products into
+// y; returns the run's first row
+template <typename T, int VEC, int RUN, bool CONTIG>
+__device__ __forceinline__ int64_t stencil7_apply_run(const Stencil7<T>& st, const FastDiv& drun, const FastDiv& drow,
+                                                      int64_t u, const T* __restrict__ xc, int64_t ldx,
+                                                      Vec<T, VEC> (&x0)[RUN], Vec<T, VEC> (&y)[RUN]) {
+  const int nx = st.n[0], ny = st.n[1], nz = st.n[2];
+  const uint32_t runs_x = (uint32_t)(nx / RUN);
+  const uint32_t line = drun.div((uint32_t)u);  // j + ny k
+  const int i0 = (int)((uint32_t)u - line * runs_x) * RUN;
+  const int kz = (int)drow.div(line);
+  const int j = (int)(line - (uint32_t)kz * (uint32_t)ny);
+  const int64_t row0 = (int64_t)line * nx + i0;
+  const T wy = __ldg(st.w[1] + j), wz = __ldg(st.w[2] + kz);
+  const T ayz = wy * wz;
+  const T icym = __ldg(st.ic[1] + j), icyp = __ldg(st.ic[1] + j + 1);
+  const T iczm = __ldg(st.ic[2] + kz), iczp = __ldg(st.ic[2] + kz + 1);
+  const int jm = j > 0 ? j - 1 : (st.per[1] ? ny - 1 : j), jp = j + 1 < ny ? j + 1 : (st.per[1] ? 0 : j);
+  const int km = kz > 0 ? kz - 1 : (st.per[2] ? nz - 1 : kz), kp2 = kz + 1 < nz ? kz + 1 : (st.per[2] ? 0 : kz);
+  const int64_t plane = (int64_t)nx * ny;
+  Vec<T, VEC> ym[RUN], yp[RUN], zm[RUN], zp[RUN];
+  load_run<T, VEC, RUN, CONTIG>(xc + row0 * ldx, ldx, x0);
+  load_run<T, VEC, RUN, CONTIG>(xc + (row0 + (int64_t)(jm - j) * nx) * ldx, ldx, ym);
+  load_run<T, VEC, RUN, CONTIG>(xc + (row0 + (int64_t)(jp - j) * nx) * ldx, ldx, yp);
+  load_run<T, VEC, RUN, CONTIG>(xc + (row0 + (int64_t)(km - kz) * plane) * ldx, ldx, zm);
+  load_run<T, VEC, RUN, CONTIG>(xc + (row0 + (int64_t)(kp2 - kz) * plane) * ldx, ldx, zp);
+  // x neighbours of the run's ends (wrapped on a periodic axis; at a wall the coefficient is 0)
+  const int il = i0 > 0 ? i0 - 1 : (st.per[0] ? nx - 1 : i0);
+  const int ir = i0 + RUN < nx ? i0 + RUN : (st.per[0] ? 0 : i0 + RUN - 1);
+  const Vec<T, VEC> xl = ldv<T, VEC>(xc + (row0 - i0 + il) * ldx);
+  const Vec<T, VEC> xr = ldv<T, VEC>(xc + (row0 - i0 + ir) * ldx);
+  T icx[RUN + 1], wx[RUN];
+#pragma unroll
+  for (int c = 0; c <= RUN; ++c) icx[c] = __ldg(st.ic[0] + i0 + c);
+#pragma unroll
+  for (int c = 0; c < RUN; ++c) wx[c] = __ldg(st.w[0] + i0 + c);
+#pragma unroll
+  for (int c = 0; c < RUN; ++c) {
+    const T cxm = ayz * icx[c], cxp = ayz * icx[c + 1];
+    const T axz = wx[c] * wz, axy = wx[c] * wy;
+    const T cym = axz * icym, cyp = axz * icyp, czm = axy * iczm, czp = axy * iczp;
+    const T diag = -(((cxm + cxp) + (cym + cyp)) + (czm + czp));
+    const Vec<T, VEC>& left = c == 0 ? xl : x0[c > 0 ? c - 1 : 0];
+    const Vec<T, VEC>& right = c == RUN - 1 ? xr : x0[c < RUN - 1 ? c + 1 : 0];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      T a = diag * x0[c].v[q];
+      a = fma(cxm, left.v[q], a);
+      a = fma(cxp, right.v[q], a);
+      a = fma(cym, ym[c].v[q], a);
+      a = fma(cyp, yp[c].v[q], a);
+      a = fma(czm, zm[c].v[q], a);
+      a = fma(czp, zp[c].v[q], a);
+      y[c].v[q] = st.scale * a;
+    }
+  }
+  return row0;
 }
 
 // ----------------------------------------------------------------------------- transfers
