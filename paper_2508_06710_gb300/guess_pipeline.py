@@ -23,12 +23,12 @@ from . import RB_FVM_DIVERGENCE, RB_FVM_LAPLACIAN
 
 
 def make_problem(torch, grid, k, dev="cuda"):
-    """A = -L in FP64 and FP32, the divergence M (FP64) and the multigrid hierarchy of A of a
-    structured grid, for k columns."""
+    """A = -L in FP64 (CSR) and FP32 (matrix-free: the refinement's inner operator), the
+    divergence M (FP64) and the multigrid hierarchy of A of a structured grid, for k columns."""
     nodes, per = grid_nodes(grid, dev)
     rp, ci, va, nc = fvm_assemble(nodes, per, RB_FVM_LAPLACIAN, scale=-1.0)
     A64 = Operator(rp, ci, va, nc, dtype="f64", k_max=k)
-    A32 = Operator(rp, ci, va, nc, dtype="f32", k_max=k)
+    A32 = Operator.stencil(nodes, per, scale=-1.0, dtype="f32", k_max=k)
     rp, ci, va, nc = fvm_assemble(nodes, per, RB_FVM_DIVERGENCE)
     M = Operator(rp, ci, va, nc, dtype="f64", k_max=k)
     mg = Multigrid(nodes, per, k_max=k)
