@@ -84,14 +84,16 @@ def test_cg_channel_stretched(rb, mixed):
             assert res.iters[j] <= 1.3 * infos[j].iters
 
 
-@pytest.mark.parametrize("case", ["channel", "periodic"])
+@pytest.mark.parametrize("case", ["channel", "periodic", "channel-odd-runs"])
 @pytest.mark.parametrize("k", [1, 3])
 @pytest.mark.parametrize("mixed", [1, 2])
 def test_cg_matrix_free_inner_operator(rb, case, k, mixed):
     """The refinement with the matrix-free FP32 Laplacian (RB_STENCIL) as the inner operator,
-    kernel by kernel and as one persistent launch per sweep: the same true 1e-10 residual and
-    the oracle's solution."""
-    g = W.channel_grid(40, 32, 24, gamma=1.5) if case == "channel" else W.unit_periodic_grid(24)
+    kernel by kernel (runs of four cells along x; one cell per thread when n_x is not a multiple
+    of 4) and as one persistent launch per sweep: the same true 1e-10 residual and the oracle's
+    solution."""
+    g = {"channel": W.channel_grid(40, 32, 24, gamma=1.5), "periodic": W.unit_periodic_grid(24),
+         "channel-odd-runs": W.channel_grid(30, 32, 24, gamma=1.5)}[case]
     A = _poisson(g)
     B = W.zero_mean(W.normal((A.shape[0], k), W.seed_for(11, k)))
     op = rb.Operator.from_scipy(A, k_max=k)
