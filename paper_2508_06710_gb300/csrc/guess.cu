@@ -2130,8 +2130,10 @@ const void* wgrad_lin_kernel(int W) {
   }
 }
 
-// runs of the longest chunk (16, 8, 4, 2 rows) whose line buffer leaves room for two CTAs per
-// SM, then one wave of CTAs with equal shares of the runs
+// runs of the longest chunk (16, 8, 4, 2 rows) whose line buffer leaves room for four CTAs per
+// SM (the kernel waits on a block barrier every row: more CTAs hide it), then one wave of CTAs
+// with equal shares of the runs
+constexpr size_t kWlinSmemTarget = 56 * 1024;
 LinWPlan wgrad_lin_plan(const Layer& ly, const Dims& d) {
   LinWPlan p;
   const int G = ly.cin_pad / 8, Go = wgrad_lin_go(ly);
@@ -2139,7 +2141,7 @@ LinWPlan wgrad_lin_plan(const Layer& ly, const Dims& d) {
   p.go_tiles = ((ly.cout + 7) / 8 + Go - 1) / Go;
   p.chunk = 2;
   for (int c = 16; c >= 2; c /= 2)
-    if (wgrad_lin_smem(d.nx, G, Go, c) <= 100 * 1024 || c == 2) {
+    if (wgrad_lin_smem(d.nx, G, Go, c) <= kWlinSmemTarget || c == 2) {
       p.chunk = std::min(c, std::max(2, d.ny));
       break;
     }
