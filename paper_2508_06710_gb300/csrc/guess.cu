@@ -1266,6 +1266,15 @@ __global__ void k_pool(const bf16* __restrict__ in, int ldi, Dims fine, int c, b
   }
 }
 
+// the block's copy of a transposed convolution's weights (count a multiple of 8 BF16 values,
+// W from cudaMalloc): 16-byte pieces, then a barrier
+__device__ __forceinline__ void stage_weights(const bf16* __restrict__ W, int count, bf16* sw) {
+  const uint4* src = reinterpret_cast<const uint4*>(W);
+  uint4* dst = reinterpret_cast<uint4*>(sw);
+  for (int i = threadIdx.x; i < count / 8; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+}
+
 // fine cell index of coarse cell (x, y, z) and offset o = a * 4 + b * 2 + c (z, y, x offsets)
 __device__ __forceinline__ int fine_of(const Dims& fine, int x, int y, int z, int o) {
   return (2 * x + (o & 1)) + fine.nx * ((2 * y + ((o >> 1) & 1)) + fine.ny * (2 * z + (o >> 2)));
@@ -1277,8 +1286,7 @@ __global__ void k_up(const bf16* __restrict__ in, int ldi, int cin, const bf16* 
                      const float* __restrict__ bias, Dims fine, int cout, bf16* __restrict__ out, int ldo) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   bf16* sw = reinterpret_cast<bf16*>(sm_raw);
-  for (int i = threadIdx.x; i < cout * 8 * cin; i += blockDim.x) sw[i] = W[i];
-  __syncthreads();
+  stage_weights(W, cout * 8 * cin, sw);
   const int groups = cout / 8;
   const int total = fine.n() * groups;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -1319,8 +1327,7 @@ __global__ void k_up_dx(const bf16* __restrict__ gu, int ldg, int cout, const bf
                         const bf16* __restrict__ xin, int ldx, Dims fine, bf16* __restrict__ gin, int ldgi) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   bf16* sw = reinterpret_cast<bf16*>(sm_raw);
-  for (int i = threadIdx.x; i < cout * 8 * cin; i += blockDim.x) sw[i] = W[i];
-  __syncthreads();
+  stage_weights(W, cout * 8 * cin, sw);
   const int cx = fine.nx / 2, cy = fine.ny / 2, cz = fine.nz / 2;
   const int groups = cin / 8;
   const int total = cx * cy * cz * groups;
