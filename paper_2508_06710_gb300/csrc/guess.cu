@@ -1147,28 +1147,56 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_lin(WgradArgs a, int chu
   if (warp == 0) tmem_dealloc(tmem, cols);
 }
 
-// Sums the splits of a weight-gradient partial and adds it into the parameter gradient in
-// the [c_out][tap][c_in] layout (+ biases).  cin_pad: channels of the GEMM input (>= cin).
+// Sums over the splits of a [splits][stride] FP32 partial for the block's 32 consecutive
+// columns (lane = column f; ok: f is a real column): warp w adds splits w, w + warps, ... in
+// order, then warp 0 adds the warps' sums in warp order: a fixed order, so the result does not
+// depend on scheduling.  Each warp reads 128 contiguous bytes per split.  Valid in warp 0.
+__device__ __forceinline__ float split_column_sum(const float* __restrict__ part, int splits, size_t stride, int f,
+                                                  bool ok, float (*sh)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float s = 0.0f;
+  if (ok) {
+    const float* p = part + f;
+#pragma unroll 4
+    for (int sp = warp; sp < splits; sp += nw) s += __ldcs(p + (size_t)sp * stride);
+  }
+  sh[warp][lane] = s;
+  __syncthreads();
+  float t = 0.0f;
+  if (warp == 0) {
+    t = sh[0][lane];
+    for (int w = 1; w < nw; ++w) t += sh[w][lane];
+  }
+  __syncthreads();
+  return t;
+}
+
+// Sums the splits of a weight-gradient partial [split][m < mpad][n < np] and adds it into the
+// parameter gradient in the [c_out][tap][c_in] layout (+ biases, row m = 27 cin_pad).
+// cin_pad: channels of the GEMM input (>= cin).
 __global__ void k_wgrad_reduce(const float* __restrict__ part, int splits, int mpad, int np, int cin_pad, int cin,
                                int cout, float* __restrict__ gw, float* __restrict__ gb) {
+  __shared__ float sh[32][32];
   const int rows = 27 * cin_pad;
-  const int total = (rows + 1) * cout;
-  const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < total; i += warps) {
-    const int m = i / cout, n = i - m * cout;
-    float s = 0.0f;
-    for (int sp = lane; sp < splits; sp += 32) s += part[((size_t)sp * mpad + m) * np + n];
-    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane != 0) continue;
+  const int total = (rows + 1) * np;
+  for (int f0 = blockIdx.x * 32; f0 < total; f0 += gridDim.x * 32) {
+    const int f = f0 + (threadIdx.x & 31);
+    const float v = split_column_sum(part, splits, (size_t)mpad * np, f, f < total, sh);
+    if (threadIdx.x >= 32 || f >= total) continue;
+    const int m = f / np, n = f - m * np;
+    if (n >= cout) continue;
     if (m == rows) {
-      gb[n] += s;
+      gb[n] += v;
     } else {
       const int tap = m / cin_pad, ci = m - tap * cin_pad;
-      if (ci < cin) gw[((size_t)n * 27 + tap) * cin + ci] += s;
+      if (ci < cin) gw[((size_t)n * 27 + tap) * cin + ci] += v;
     }
   }
 }
+
+// threads per block of the split reductions: a warp per 4 splits or more, at most 32 warps
+inline int split_sum_threads(int splits) { return 32 * std::min(32, std::max(1, splits / 4)); }
+inline int split_sum_blocks(int64_t columns) { return (int)std::max<int64_t>(1, std::min<int64_t>(8192, (columns + 31) / 32)); }
 
 // ------------------------------------------------------------------------ streaming kernels
 
@@ -1455,15 +1483,13 @@ __global__ void __launch_bounds__(256) k_up_dw(const bf16* __restrict__ x, int l
 }
 
 // dst[i] += sum over blocks part[b][i] for the transposed convolution's (co, o, ci) + bias
-// layout; one warp per output, lanes over the blocks, a fixed shuffle tree
+// layout, the blocks summed in a fixed order
 __global__ void k_sum_parts(const float* __restrict__ part, int nblk, int n, float* __restrict__ dst) {
-  const int lane = threadIdx.x & 31;
-  const int warps = gridDim.x * (blockDim.x >> 5);
-  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-    float s = 0.0f;
-    for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * n + i];
-    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) dst[i] += s;
+  __shared__ float sh[32][32];
+  for (int f0 = blockIdx.x * 32; f0 < n; f0 += gridDim.x * 32) {
+    const int f = f0 + (threadIdx.x & 31);
+    const float v = split_column_sum(part, nblk, (size_t)n, f, f < n, sh);
+    if (threadIdx.x < 32 && f < n) dst[f] += v;
   }
 }
 
@@ -2197,10 +2223,8 @@ rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, cons
       default: st = launch_wgrad_lin<128>(a, lp, s); break;
     }
     RB_TRY(st);
-    const int total = (a.rows + 1) * ly.cout;
-    k_wgrad_reduce<<<std::min(4096, (total + 7) / 8), 256, 0, s>>>(g->wpart, lp.splits, ly.mpad, ly.np, ly.cin_pad,
-                                                                   ly.cin, ly.cout, g->grad + ly.w_off,
-                                                                   g->grad + ly.b_off);
+    k_wgrad_reduce<<<split_sum_blocks((int64_t)(a.rows + 1) * ly.np), split_sum_threads(lp.splits), 0, s>>>(
+        g->wpart, lp.splits, ly.mpad, ly.np, ly.cin_pad, ly.cin, ly.cout, g->grad + ly.w_off, g->grad + ly.b_off);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
   }
@@ -2230,10 +2254,8 @@ rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, cons
       return RB_EUNSUPPORTED;
   }
   RB_TRY(st);
-  const int total = (a.rows + 1) * ly.cout;
-  k_wgrad_reduce<<<std::min(4096, (total + 7) / 8), 256, 0, s>>>(g->wpart, p.splits, ly.mpad, ly.np, ly.cin_pad,
-                                                                      ly.cin, ly.cout, g->grad + ly.w_off,
-                                                                      g->grad + ly.b_off);
+  k_wgrad_reduce<<<split_sum_blocks((int64_t)(a.rows + 1) * ly.np), split_sum_threads(p.splits), 0, s>>>(
+      g->wpart, p.splits, ly.mpad, ly.np, ly.cin_pad, ly.cin, ly.cout, g->grad + ly.w_off, g->grad + ly.b_off);
   RB_CUDA(cudaGetLastError());
   return RB_OK;
 }
@@ -2387,7 +2409,8 @@ rb_status backward(rb_guess* g, cudaStream_t s) {
     const size_t smw = (size_t)kUpChunk * (cc + 8 * c) * 4;
     k_up_dw<<<ug, 256, smw, s>>>(upin, cc, cc, g->g_cat[l], 2 * c, c, g->dims[l], g->wpart);
     const int n_out = 8 * cc * c + c;
-    k_sum_parts<<<std::min(4096, (n_out + 7) / 8), 256, 0, s>>>(g->wpart, ug, n_out, g->grad + up.w_off);  // W then b, contiguous
+    k_sum_parts<<<split_sum_blocks(n_out), split_sum_threads(ug), 0, s>>>(g->wpart, ug, n_out,
+                                                                        g->grad + up.w_off);  // W then b, contiguous
     RB_CUDA(cudaGetLastError());
   }
   // encoder, bottom first
