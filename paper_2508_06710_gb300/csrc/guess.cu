@@ -1395,90 +1395,93 @@ __global__ void k_up_dx(const bf16* __restrict__ gu, int ldg, int cout, const bf
   }
 }
 
-// weight and bias gradient of the transposed convolution: per block partial sums over a
-// grid-stride share of the coarse cells, outputs (co, o, ci) and then the cout biases.
-// Thread t owns outputs t, t + 256, ... (at most kUpOut of them).
-constexpr int kUpOut = 64;
-constexpr int kUpChunk = 16;
-__global__ void __launch_bounds__(256) k_up_dw(const bf16* __restrict__ x, int ldx, int cin,
-                                               const bf16* __restrict__ gu, int ldg, int cout, Dims fine,
-                                               float* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  float* sx = reinterpret_cast<float*>(sm_raw);        // [kUpChunk][cin]
-  float* sg = sx + kUpChunk * cin;                     // [kUpChunk][8][cout]
-  const int cx = fine.nx / 2, cy = fine.ny / 2, cz = fine.nz / 2;
-  const int nc = cx * cy * cz;
-  const int n_w = cout * 8 * cin;
-  const int n_out = n_w + cout;
-  const int gx = cin / 8, gg = cout / 8;  // 8-channel groups (channel counts are multiples of 8)
-  // output t + 256 r of this thread: (co, o, ci) with ci fastest, stepped from r = 0 (256 =
-  // q cin + s: ci advances by s, the (co, o) index by q, carrying)
-  const int step_q = 256 / cin, step_s = 256 - step_q * cin;
-  float acc[kUpOut];
+// weight and bias gradient of the transposed convolution, dW[co][o][ci] = sum over coarse cells v
+// of g[fine(v, o)][co] x[v][ci] and db[co] = sum over fine cells of g[.][co]: an outer-product
+// sum per child o.  Tiles of 8 co x 8 ci for one o (tile index o fastest, then the co group,
+// then the ci group), tb tiles per block (blockIdx.y: the tile group), each tile held in
+// registers by ln lanes (ln a power of two, the lanes of a tile adjacent in a warp) that stride
+// over the block's range of cells_per_split coarse cells (blockIdx.x).  The lanes then add up
+// by a fixed xor tree, and the block writes its share of part[blockIdx.x][8 cin cout + cout]
+// (W in [co][o][ci] order, then the biases, which the tiles of the first ci group sum over o).
+constexpr int kUpDwThreads = 256;
+__global__ void __launch_bounds__(kUpDwThreads, 2)
+    k_up_dw(const bf16* __restrict__ x, int ldx, int cin, const bf16* __restrict__ gu, int ldg, int cout, Dims fine,
+            int tb, int ln, int cells_per_split, float* __restrict__ part) {
+  __shared__ float sb[64][8];  // tb <= 64: each tile's bias sums
+  const int tile = threadIdx.x / ln, j = threadIdx.x & (ln - 1);
+  const int gco = cout / 8;
+  const int n_tiles = gco * cin;  // 8 (cout / 8) (cin / 8)
+  const int tg = blockIdx.y * tb + tile;
+  const bool valid = tile < tb && tg < n_tiles;
+  const int o = tg & 7, rest = tg >> 3, cog = rest % gco, cig = rest / gco;
+  const bool with_bias = valid && cig == 0;
+  const int cx = fine.nx / 2, cy = fine.ny / 2;
+  const int nc = cx * cy * (fine.nz / 2);
+  const int c0 = blockIdx.x * cells_per_split, c1 = min(nc, c0 + cells_per_split);
+  float acc[8][8], bs[8];
 #pragma unroll
-  for (int r = 0; r < kUpOut; ++r) acc[r] = 0.0f;
-  for (int c0 = blockIdx.x * kUpChunk; c0 < nc; c0 += gridDim.x * kUpChunk) {
-    __syncthreads();
-    // 16-byte pieces: the chunk's coarse inputs, then for each cell and child o its gradient
-    for (int i = threadIdx.x; i < kUpChunk * gx; i += blockDim.x) {
-      const int k = i / gx, q = i - k * gx;
-      const int v = c0 + k;
-      float* d = sx + k * cin + q * 8;
-      if (v < nc) {
-        const uint4 u = *reinterpret_cast<const uint4*>(x + (size_t)v * ldx + q * 8);
-        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+  for (int r = 0; r < 8; ++r) {
+    bs[r] = 0.0f;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 f = __bfloat1622float2(h[e]);
-          d[2 * e] = f.x, d[2 * e + 1] = f.y;
-        }
-      } else {
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0f;
+  }
+  if (valid) {
+#pragma unroll 2
+    for (int v = c0 + j; v < c1; v += ln) {
+      const int xx = v % cx, rr = v / cx;
+      const uint4 xq = __ldg(reinterpret_cast<const uint4*>(x + (size_t)v * ldx + cig * 8));
+      const uint4 gq =
+          __ldg(reinterpret_cast<const uint4*>(gu + (size_t)fine_of(fine, xx, rr % cy, rr / cy, o) * ldg + cog * 8));
+      const __nv_bfloat162* xh = reinterpret_cast<const __nv_bfloat162*>(&xq);
+      const __nv_bfloat162* gh = reinterpret_cast<const __nv_bfloat162*>(&gq);
+      float xv[8], gv[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) d[e] = 0.0f;
+      for (int e = 0; e < 4; ++e) {
+        const float2 fx = __bfloat1622float2(xh[e]), fg = __bfloat1622float2(gh[e]);
+        xv[2 * e] = fx.x, xv[2 * e + 1] = fx.y, gv[2 * e] = fg.x, gv[2 * e + 1] = fg.y;
       }
-    }
-    for (int i = threadIdx.x; i < kUpChunk * 8 * gg; i += blockDim.x) {
-      const int q = i % gg, r = i / gg, o = r & 7, k = r >> 3;
-      const int v = c0 + k;
-      float* d = sg + (k * 8 + o) * cout + q * 8;
-      if (v < nc) {
-        const int xx = v % cx, rr = v / cx;
-        const uint4 u = *reinterpret_cast<const uint4*>(gu + (size_t)fine_of(fine, xx, rr % cy, rr / cy, o) * ldg + q * 8);
-        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 f = __bfloat1622float2(h[e]);
-          d[2 * e] = f.x, d[2 * e + 1] = f.y;
-        }
-      } else {
+      for (int r = 0; r < 8; ++r) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) d[e] = 0.0f;
+        for (int c = 0; c < 8; ++c) acc[r][c] += gv[r] * xv[c];
+        if (with_bias) bs[r] += gv[r];
       }
-    }
-    __syncthreads();
-    int ci = (int)threadIdx.x % cin, rest = (int)threadIdx.x / cin;  // output threadIdx.x (r = 0)
-#pragma unroll 4
-    for (int r = 0; r < kUpOut; ++r) {
-      const int idx = threadIdx.x + r * blockDim.x;
-      if (idx >= n_out) break;
-      float s = 0.0f;
-      if (idx < n_w) {
-        const int go = (rest & 7) * cout + (rest >> 3);  // child o = rest % 8, channel co = rest / 8
-        for (int k = 0; k < kUpChunk; ++k) s += sx[k * cin + ci] * sg[k * 8 * cout + go];
-      } else {
-        const int co = idx - n_w;
-        for (int k = 0; k < kUpChunk * 8; ++k) s += sg[k * cout + co];
-      }
-      acc[r] += s;
-      ci += step_s;
-      rest += step_q;
-      if (ci >= cin) ci -= cin, ++rest;
     }
   }
-  for (int r = 0; r < kUpOut; ++r) {
-    const int idx = threadIdx.x + r * blockDim.x;
-    if (idx >= n_out) break;
-    part[(size_t)blockIdx.x * n_out + idx] = acc[r];
+  for (int m = ln >> 1; m >= 1; m >>= 1) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], m);
+      bs[r] += __shfl_xor_sync(0xffffffffu, bs[r], m);
+    }
+  }
+  const int n_w = 8 * cin * cout;
+  float* dst = part + (size_t)blockIdx.x * (n_w + cout);
+  if (valid) {
+    // lane j writes the rows r with r = j (ln >= 8) or r = j mod ln (ln < 8)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if ((ln >= 8 ? r : (r & (ln - 1))) != j) continue;
+      float4* d = reinterpret_cast<float4*>(dst + ((size_t)(cog * 8 + r) * 8 + o) * cin + cig * 8);
+      d[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+      d[1] = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+    }
+  }
+  if (j == 0 && tile < tb) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sb[tile][r] = bs[r];
+  }
+  __syncthreads();
+  // biases: the 8 tiles of one (co group, first ci group) pair, o = 0 .. 7 in order
+  if ((int)threadIdx.x < tb) {
+    const int q = threadIdx.x >> 3, r = threadIdx.x & 7;
+    const int t0 = blockIdx.y * tb + q * 8;
+    if (t0 < n_tiles && (t0 >> 3) / gco == 0) {
+      float sum = 0.0f;
+      for (int oo = 0; oo < 8; ++oo) sum += sb[q * 8 + oo][r];
+      dst[n_w + ((t0 >> 3) % gco) * 8 + r] = sum;
+    }
   }
 }
 
@@ -2260,10 +2263,24 @@ rb_status conv3_wgrad(rb_guess* g, const Layer& ly, const bf16* x, int ldx, cons
   return RB_OK;
 }
 
-int up_dw_grid(const rb_guess* g, const Layer& ly) {
-  const Dims& f = g->dims[ly.level];
-  const int nc = f.n() / 8;
-  return std::max(1, std::min(kRedGrid, (nc + kUpChunk - 1) / kUpChunk));
+// k_up_dw's launch: tiles of 8 x 8 outputs, up to 64 per block; lanes per tile the largest power
+// of two that keeps the block within 256 threads; one wave of two blocks per SM split into
+// equal ranges of coarse cells
+struct UpDwPlan {
+  int tb = 0, ln = 0, gy = 0, cells = 0, splits = 0;
+};
+UpDwPlan up_dw_plan(const rb_guess* g, const Layer& ly) {
+  UpDwPlan p;
+  const int nc = g->dims[ly.level].n() / 8;
+  const int n_tiles = ly.cout * ly.cin / 8;
+  p.tb = std::min(n_tiles, 64);
+  p.ln = 1;
+  while (p.ln * 2 * p.tb <= kUpDwThreads) p.ln *= 2;
+  p.gy = (n_tiles + p.tb - 1) / p.tb;
+  const int target = std::max(1, 2 * guess_sm_count() / p.gy);
+  p.cells = std::max(1, (nc + target - 1) / target);
+  p.splits = std::max(1, (nc + p.cells - 1) / p.cells);
+  return p;
 }
 
 size_t wpart_need(const rb_guess* g) {
@@ -2275,7 +2292,7 @@ size_t wpart_need(const rb_guess* g) {
       if (wgrad_lin_fits(ly, g->dims[ly.level]))
         need = std::max(need, (size_t)wgrad_lin_plan(ly, g->dims[ly.level]).splits * ly.mpad * ly.np);
     } else if (ly.kind == kUp) {
-      need = std::max(need, (size_t)up_dw_grid(g, ly) * (8 * ly.cin * ly.cout + ly.cout));
+      need = std::max(need, (size_t)up_dw_plan(g, ly).splits * (8 * ly.cin * ly.cout + ly.cout));
     }
   }
   return need;
@@ -2405,11 +2422,11 @@ rb_status backward(rb_guess* g, cudaStream_t s) {
     const size_t sm = (size_t)up.cout * 8 * up.cin * 2;
     k_up_dx<<<grid_for((int64_t)g->dims[l + 1].n() * (cc / 8)), 256, sm, s>>>(g->g_cat[l], 2 * c, c, up.wu, cc, upin,
                                                                                 cc, g->dims[l], gin, cc);
-    const int ug = up_dw_grid(g, up);
-    const size_t smw = (size_t)kUpChunk * (cc + 8 * c) * 4;
-    k_up_dw<<<ug, 256, smw, s>>>(upin, cc, cc, g->g_cat[l], 2 * c, c, g->dims[l], g->wpart);
+    const UpDwPlan up_p = up_dw_plan(g, up);
+    k_up_dw<<<dim3(up_p.splits, up_p.gy), up_p.tb * up_p.ln, 0, s>>>(upin, cc, cc, g->g_cat[l], 2 * c, c, g->dims[l],
+                                                                    up_p.tb, up_p.ln, up_p.cells, g->wpart);
     const int n_out = 8 * cc * c + c;
-    k_sum_parts<<<split_sum_blocks(n_out), split_sum_threads(ug), 0, s>>>(g->wpart, ug, n_out,
+    k_sum_parts<<<split_sum_blocks(n_out), split_sum_threads(up_p.splits), 0, s>>>(g->wpart, up_p.splits, n_out,
                                                                         g->grad + up.w_off);  // W then b, contiguous
     RB_CUDA(cudaGetLastError());
   }
@@ -2506,8 +2523,8 @@ extern "C" rb_status rb_guess_create(const rb_guess_cfg* cfg, rb_guess_t* out) {
     }
   }
   for (const Layer& ly : g->layers)
-    if (ly.kind == kUp && 8 * ly.cin * ly.cout + ly.cout > 256 * kUpOut) {
-      set_error("rb_guess_create: a %d -> %d up-sampling has too many weights", ly.cin, ly.cout);
+    if (ly.kind == kUp && (size_t)8 * ly.cin * ly.cout * sizeof(bf16) > 48 * 1024) {
+      set_error("rb_guess_create: a %d -> %d up-sampling's weights exceed 48 KB of shared memory", ly.cin, ly.cout);
       return fail(RB_EINVAL);
     }
   const int L = g->L;
