@@ -1537,27 +1537,33 @@ __global__ void k_sum_diff(const double* __restrict__ p, const double* __restric
 }
 
 // d = (y - mean y) - (t - mean t), t = (p - p1) / s_p; gy = 2 d / n; partial sums of d^2.
-// means[0] = mean y, means[2] = mean (p - p1)
+// means[0] = mean y, means[2] = mean (p - p1).  The difference of the two pressures and its
+// scaling in FP64 (they cancel), the rest in FP32 like y: this GPU's FP64 pipe runs about 1/60
+// of the FP32 rate, and a thread's few terms sum in FP32 before the FP64 block and grid sums.
 __global__ void k_loss(const double* __restrict__ p, const double* __restrict__ p1, const float* __restrict__ y, int n,
                        const double* __restrict__ scal, const double* __restrict__ means, float* __restrict__ gy,
                        double* part) {
-  const double isp = 1.0 / scal[1], my = means[0], mt = means[2] * isp;
-  double v[1] = {0.0};
+  const double isp = 1.0 / scal[1], mt = means[2] * isp;
+  const float my = (float)means[0], two_n = 2.0f / (float)n;
+  float acc = 0.0f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double d = ((double)y[i] - my) - ((p[i] - p1[i]) * isp - mt);
-    gy[i] = (float)(2.0 * d / n);
-    v[0] += d * d;
+    const float t = (float)((p[i] - p1[i]) * isp - mt);
+    const float d = (y[i] - my) - t;
+    gy[i] = two_n * d;
+    acc += d * d;
   }
+  double v[1] = {acc};
   block_sum_store<1>(v, part);
 }
 
-// head backward: partial sums of gy * x[c] (c < C) and of gy; g_pre = bf16(W[c] gy) masked by x > 0
+// head backward: partial sums of gy * x[c] (c < C) and of gy; g_pre = bf16(W[c] gy) masked by x > 0.
+// A thread's sums in FP32 (its few cells), the block and grid sums in FP64.
 template <int C>
 __global__ void k_head_bwd(const bf16* __restrict__ x, int ldx, const float* __restrict__ W,
                            const float* __restrict__ gy, int n, bf16* __restrict__ gpre, int ldg, double* part) {
-  double v[C + 1];
+  float v[C + 1];
 #pragma unroll
-  for (int q = 0; q <= C; ++q) v[q] = 0.0;
+  for (int q = 0; q <= C; ++q) v[q] = 0.0f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float g = gy[i];
 #pragma unroll
@@ -1569,8 +1575,8 @@ __global__ void k_head_bwd(const bf16* __restrict__ x, int ldx, const float* __r
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
         const float x0 = __bfloat162float(h[e]), x1 = __bfloat162float(h[e + 1]);
-        v[cc + e] += (double)g * x0;
-        v[cc + e + 1] += (double)g * x1;
+        v[cc + e] += g * x0;
+        v[cc + e + 1] += g * x1;
         __nv_bfloat162 r = __floats2bfloat162_rn(W[cc + e] * g, W[cc + e + 1] * g);
         if (!(x0 > 0.0f)) r.x = __float2bfloat16(0.0f);
         if (!(x1 > 0.0f)) r.y = __float2bfloat16(0.0f);
@@ -1580,7 +1586,10 @@ __global__ void k_head_bwd(const bf16* __restrict__ x, int ldx, const float* __r
     }
     v[C] += g;
   }
-  block_sum_store<C + 1>(v, part);
+  double vd[C + 1];
+#pragma unroll
+  for (int q = 0; q <= C; ++q) vd[q] = v[q];
+  block_sum_store<C + 1>(vd, part);
 }
 
 // encoder output gradient: bf16((g_skip + g_pool / 8) * (act > 0)); thread per (cell, 8 channels).
